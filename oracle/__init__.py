@@ -1,0 +1,209 @@
+"""FP64 CPU oracle of the discrete-velocity transport iteration (arXiv:1712.01132, Sec. 2-3).
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU-baseline leg of the
+benchmark may import this package.  It shares no code with the CUDA library: the solver is the
+plain C file ``dvm_oracle.c`` (built here with gcc), the velocity grid comes from
+``quadrature.py``.
+
+Parity status: every solver function here is pinned by the ``-m "not gpu"`` tests against
+closed forms, invariants, the paper's printed permeabilities and an independent dense
+linear solve (see ``tests/test_oracle_*.py``).
+"""
+import ctypes
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+from .quadrature import half_range_gauss_hermite, velocity_grid  # noqa: F401
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dvm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class _Cfg(ctypes.Structure):
+    _fields_ = [
+        ("dims", ctypes.c_int),
+        ("n", ctypes.c_int * 3),
+        ("solid", ctypes.c_void_p),
+        ("kn", ctypes.c_double),
+        ("jump", ctypes.c_double),
+        ("nv", ctypes.c_int),
+        ("v", ctypes.c_void_p),
+        ("w", ctypes.c_void_p),
+        ("order", ctypes.c_int),
+        ("lateral", ctypes.c_int),
+        ("form", ctypes.c_int),
+        ("traversal", ctypes.c_int),
+        ("dec", ctypes.c_int * 3),
+    ]
+
+
+def build(force=False):
+    """Compile dvm_oracle.c into oracle/_build/liboracle.so (gcc, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-D_GNU_SOURCE",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.ora_create.restype = ctypes.c_void_p
+            lib.ora_create.argtypes = [ctypes.POINTER(_Cfg)]
+            lib.ora_destroy.argtypes = [ctypes.c_void_p]
+            lib.ora_iterate.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
+            lib.ora_iter.restype = ctypes.c_long
+            lib.ora_iter.argtypes = [ctypes.c_void_p]
+            for f in ("ora_get_moments",):
+                getattr(lib, f).argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+            for f in ("ora_get_wall", "ora_get_flux"):
+                getattr(lib, f).argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+            lib.ora_set_uniform.argtypes = [ctypes.c_void_p, ctypes.c_double]
+            lib.ora_sweep_one.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Oracle:
+    """One problem: a solid mask (numpy bool/uint8, shape (n2, n1) or (n3, n2, n1), x1 fastest),
+    Knudsen number kn and a velocity grid (v [nv, dims], W [nv], sum W = 1).
+
+    form: "jump" (the paper's Eq. 7, default) or "source" (h' = h + J x1).
+    lateral: "specular" (Eq. 8, default) or "periodic".
+    order: 2 (Eq. 9 default) or 1.
+    traversal: "raster" (the paper's raster scan) or "wavefront".
+    decomposition: subdomain counts (c1, c2[, c3]) of the lagged-halo Omega_x decomposition.
+    """
+
+    def __init__(self, solid, kn, v, w, *, jump=1.0, order=2, lateral="specular", form="jump",
+                 traversal="raster", decomposition=(1, 1, 1), threads=0):
+        lib = _load()
+        solid = np.ascontiguousarray(np.asarray(solid).astype(np.uint8))
+        if solid.ndim not in (2, 3):
+            raise ValueError("mask must be 2D or 3D")
+        self.dims = solid.ndim
+        self.shape = solid.shape
+        self.solid = solid
+        self.v = np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(-1, self.dims))
+        self.w = np.ascontiguousarray(np.asarray(w, dtype=np.float64).reshape(-1))
+        self.kn = float(kn)
+        self.threads = int(threads)
+        cfg = _Cfg()
+        cfg.dims = self.dims
+        n = solid.shape[::-1]
+        for j in range(3):
+            cfg.n[j] = n[j] if j < self.dims else 1
+        cfg.solid = _ptr(self.solid)
+        cfg.kn = self.kn
+        cfg.jump = float(jump)
+        cfg.nv = self.v.shape[0]
+        cfg.v = _ptr(self.v)
+        cfg.w = _ptr(self.w)
+        cfg.order = int(order)
+        cfg.lateral = {"specular": 0, "periodic": 1}[lateral]
+        cfg.form = {"jump": 0, "source": 1}[form]
+        cfg.traversal = {"raster": 0, "wavefront": 1}[traversal]
+        dec = tuple(decomposition) + (1,) * (3 - len(decomposition))
+        for j in range(3):
+            cfg.dec[j] = int(dec[j])
+        self._cfg = cfg
+        self._h = lib.ora_create(ctypes.byref(cfg))
+        if not self._h:
+            raise ValueError("oracle rejected the configuration")
+        self._lib = lib
+        self.k_history = []    # k after every iteration
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._lib.ora_destroy(h)
+            self._h = None
+
+    @property
+    def iterations(self):
+        return int(self._lib.ora_iter(self._h))
+
+    def iterate(self, n):
+        """Run n iterations; returns k after each of them."""
+        out = np.zeros(max(n, 1))
+        self._lib.ora_iterate(self._h, int(n), _ptr(out), self.threads)
+        ks = out[:n].tolist()
+        self.k_history.extend(ks)
+        return np.array(ks)
+
+    def run(self, tol, max_iter, check_interval=100):
+        """Iterate until Err of Eq. 15 (checked every check_interval iterations) drops below tol or
+        max_iter iterations have run.  Returns (iterations, k, Err)."""
+        k_prev = self.permeability() if self.iterations else 0.0
+        err = math.inf
+        while self.iterations < max_iter:
+            n = min(check_interval, max_iter - self.iterations)
+            ks = self.iterate(n)
+            k = ks[-1]
+            err = abs((k - k_prev) / k) / check_interval if k != 0 else math.inf
+            k_prev = k
+            if err < tol:
+                break
+        return self.iterations, self.permeability(), err
+
+    def moments(self):
+        """(rho [shape], u [dims, *shape]) in the paper's (jump-form) variables; solid = 0."""
+        N = self.solid.size
+        rho = np.zeros(N)
+        u = np.zeros(N * self.dims)
+        self._lib.ora_get_moments(self._h, _ptr(rho), _ptr(u))
+        return rho.reshape(self.shape), u.reshape((self.dims,) + self.shape)
+
+    def wall(self):
+        """Wall densities [dims, 2, *shape] of faces (x, axis j, side -1/+1); 0 where no face."""
+        out = np.zeros(self.solid.size * self.dims * 2)
+        self._lib.ora_get_wall(self._h, _ptr(out))
+        return out.reshape((self.dims, 2) + self.shape)
+
+    def flux(self):
+        """x1 face fluxes sum_{cross-section} sum_k W_k v1 h_upwind of the last iteration [n1]."""
+        out = np.zeros(self.shape[-1])
+        self._lib.ora_get_flux(self._h, _ptr(out))
+        return out
+
+    def permeability(self):
+        """k = (2/sqrt(pi)) Kn G_p with G_p the mean of u1 over all points (Eq. 11-12)."""
+        _, u = self.moments()
+        return 2.0 / math.sqrt(math.pi) * self.kn * float(u[0].sum() / u[0].size)
+
+    def set_uniform(self, c):
+        self._lib.ora_set_uniform(self._h, float(c))
+
+    def sweep_one(self, k):
+        """Sweep velocity k from the current state without changing it; returns h [shape]."""
+        h = np.zeros(self.solid.size)
+        self._lib.ora_sweep_one(self._h, int(k), _ptr(h))
+        return h.reshape(self.shape)
+
+
+def effective_knudsen_factor(k_inf, porosity, dims):
+    """Kn*/Kn = 1/(L*/L) with L*/L of Eq. 14: sqrt(12 k_inf/eps) in 2D, sqrt(8 k_inf/(pi eps)) in 3D."""
+    if dims == 2:
+        ratio = math.sqrt(12.0 * k_inf / porosity)
+    else:
+        ratio = math.sqrt(8.0 * k_inf / (math.pi * porosity))
+    return 1.0 / ratio

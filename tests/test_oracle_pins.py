@@ -1,0 +1,318 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test would fail for a plausible mistake somewhere in the oracle: a wrong quadrature, a dropped
+stencil term, a wrong sign of the pressure jump, a mis-indexed ghost layer, a wrong wall
+denominator, a non-upwind read, or a broken boundary mapping.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from bruteforce import solve_dense
+from oracle import Oracle, effective_knudsen_factor, half_range_gauss_hermite, velocity_grid
+from paper_1712_01132_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _load(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+# --- quadrature (Sec. 2.2: half-range Gauss-Hermite grid) ------------------------------------
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 6, 8, 12, 16])
+def test_half_range_rule_is_exact_on_monomials(m):
+    """int_0^inf v^p exp(-v^2) dv = Gamma((p+1)/2)/2 exactly for p <= 2m-1."""
+    c, a = half_range_gauss_hermite(m)
+    assert np.all(c > 0) and np.all(a > 0) and np.all(np.diff(c) > 0)
+    for p in range(2 * m):
+        exact = math.gamma((p + 1) / 2) / 2
+        assert abs(np.sum(a * c ** p) - exact) <= 2e-15 * exact * (1 + p)
+    # degree 2m is not integrated exactly (a genuine m-point Gauss rule)
+    if m <= 8:
+        exact = math.gamma((2 * m + 1) / 2) / 2
+        assert abs(np.sum(a * c ** (2 * m)) - exact) > 1e-10 * exact
+
+
+def test_one_point_rule_closed_form():
+    c, a = half_range_gauss_hermite(1)
+    assert c[0] == pytest.approx(1 / math.sqrt(math.pi), rel=1e-15)
+    assert a[0] == pytest.approx(math.sqrt(math.pi) / 2, rel=1e-15)
+
+
+@pytest.mark.parametrize("dims,n", [(2, 8), (2, 16), (2, 24), (3, 8)])
+def test_velocity_grid_moments(dims, n):
+    """sum W = 1, sum W v = 0, sum W v_i v_j = delta_ij / 2, sum W v_1^4 = 3/4 (f_eq moments)."""
+    v, w = velocity_grid(dims, n)
+    assert len(w) == n ** dims
+    assert w.sum() == pytest.approx(1.0, abs=1e-14)
+    assert np.abs((w[:, None] * v).sum(0)).max() < 1e-15
+    second = np.einsum("k,ki,kj->ij", w, v, v)
+    assert np.abs(second - 0.5 * np.eye(dims)).max() < 1e-14
+    assert (w * v[:, 0] ** 4).sum() == pytest.approx(0.75, rel=1e-14)
+
+
+@pytest.mark.parametrize("n", [8, 16, 24, 32])
+def test_wall_denominator_closed_form(n):
+    """Denominator of Eq. 6: sum_{v_j > 0} W v_j = int_{v_j>0} v_j f_eq dv = 1/(2 sqrt(pi))."""
+    v, w = velocity_grid(2, n)
+    d = (w * np.where(v[:, 0] > 0, v[:, 0], 0.0)).sum()
+    assert d == pytest.approx(1.0 / (2.0 * math.sqrt(math.pi)), rel=1e-14)
+
+
+# --- single point updates by hand (Eq. 9-10) -------------------------------------------------
+
+def test_first_sweep_by_hand():
+    """First sweep of one velocity from the zero state on a 3x3 grid with a solid centre:
+    inflow ghosts carry the jump J = 1 (Eq. 7), all other boundary data are zero."""
+    solid = np.zeros((3, 3), bool)
+    solid[1, 1] = True
+    v = np.array([[0.7, 0.4], [-0.7, 0.4], [0.7, -0.4], [-0.7, -0.4]])
+    w = np.full(4, 0.25)
+    kn = 0.5
+    o = Oracle(solid, kn, v, w, threads=1)
+    h = o.sweep_one(0)            # v = (+0.7, +0.4)
+    nu = math.sqrt(math.pi) / (2 * kn)
+    dx = 1 / 3
+    a, b = 0.7 / dx, 0.4 / dx
+    den2 = nu + 1.5 * a + 1.5 * b
+    h00 = 1.5 * a / den2                         # both x1 upstream values are ghosts = 1
+    h10 = a * (2 * h00 - 0.5 * 1.0) / den2        # x1: h00 and ghost(-1) = 1
+    h20 = a * (2 * h10 - 0.5 * h00) / den2
+    h01 = (1.5 * a + b * 2 * h00) / den2          # x2 upstream: h00 and the zero ghost row
+    den_first = nu + a + 1.5 * b                  # x1 upstream (1,1) is solid: first order
+    h21 = (b * 2 * h20) / den_first               # wall value is zero initially
+    assert h[0, 0] == pytest.approx(h00, rel=1e-14)
+    assert h[0, 1] == pytest.approx(h10, rel=1e-14)
+    assert h[0, 2] == pytest.approx(h20, rel=1e-14)
+    assert h[1, 0] == pytest.approx(h01, rel=1e-14)
+    assert h[1, 2] == pytest.approx(h21, rel=1e-14)
+
+
+# --- brute-force dense solve on tiny grids --------------------------------------------------
+
+def _tiny_2d():
+    solid = np.zeros((6, 7), bool)
+    solid[2:4, 2:5] = True
+    solid[5, 6] = True
+    return solid
+
+
+@pytest.mark.parametrize("lateral", ["specular", "periodic"])
+@pytest.mark.parametrize("order", [2, 1])
+def test_fixed_point_matches_dense_solve_2d(lateral, order):
+    solid = _tiny_2d()
+    v, w = velocity_grid(2, 4)
+    rho, u, k, resid, delta = solve_dense(solid, 1.0, v, w, lateral=lateral, order=order)
+    assert resid < 1e-11
+    o = Oracle(solid, 1.0, v, w, lateral=lateral, order=order, threads=1)
+    o.iterate(3000)
+    r2, u2 = o.moments()
+    fluid = ~solid
+    assert np.abs(u - u2).max() < 1e-12
+    assert np.abs(rho - (r2 - r2[fluid].mean()) * fluid).max() < 1e-12
+    assert o.permeability() == pytest.approx(k, rel=1e-12)
+    # the constant mode drifts by exactly delta per iteration in the limit
+    m0 = r2[fluid].mean()
+    o.iterate(1)
+    r3, _ = o.moments()
+    assert r3[fluid].mean() - m0 == pytest.approx(delta, abs=1e-12)
+    if order == 1:
+        assert abs(delta) < 1e-14
+
+
+def test_fixed_point_matches_dense_solve_3d():
+    solid = np.zeros((3, 4, 4), bool)
+    solid[1, 1:3, 1:3] = True
+    v, w = velocity_grid(3, 4)
+    rho, u, k, resid, delta = solve_dense(solid, 1.0, v, w, lateral="specular", order=2)
+    assert resid < 1e-11
+    o = Oracle(solid, 1.0, v, w, lateral="specular", order=2, threads=1)
+    o.iterate(2000)
+    r2, u2 = o.moments()
+    assert np.abs(u - u2).max() < 1e-12
+    assert o.permeability() == pytest.approx(k, rel=1e-11)
+
+
+# --- exact invariants --------------------------------------------------------------------------
+
+def test_zero_jump_keeps_zero_state():
+    solid = inputs.cylinder_cell(16, 0.7)
+    v, w = velocity_grid(2, 8)
+    o = Oracle(solid, 0.2, v, w, jump=0.0, threads=1)
+    o.iterate(5)
+    rho, u = o.moments()
+    assert np.abs(rho).max() == 0.0 and np.abs(u).max() == 0.0
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_uniform_state_is_a_fixed_point(order):
+    """h = c everywhere solves the equations without a pressure jump."""
+    solid = inputs.cylinder_cell(16, 0.7)
+    v, w = velocity_grid(2, 8)
+    o = Oracle(solid, 0.2, v, w, jump=0.0, order=order, threads=1)
+    o.set_uniform(1.75)
+    o.iterate(3)
+    rho, u = o.moments()
+    assert np.abs(rho[~solid] - 1.75).max() < 1e-13
+    assert np.abs(u).max() < 1e-13
+
+
+def test_linear_in_jump_amplitude():
+    solid = inputs.random_discs(20, 12, seed=5, rmin=2, rmax=3, solid_fraction=0.3)
+    v, w = velocity_grid(2, 8)
+    a = Oracle(solid, 0.5, v, w, jump=1.0, threads=1)
+    b = Oracle(solid, 0.5, v, w, jump=2.5, threads=1)
+    a.iterate(25)
+    b.iterate(25)
+    ra, ua = a.moments()
+    rb, ub = b.moments()
+    assert np.abs(ub - 2.5 * ua).max() < 1e-13 * np.abs(ub).max() + 1e-15
+    assert np.abs(rb - 2.5 * ra).max() < 1e-12
+
+
+@pytest.mark.parametrize("lateral", ["specular", "periodic"])
+def test_jump_form_equals_source_form(lateral):
+    solid = inputs.random_discs(24, 16, seed=1, rmin=2, rmax=4, solid_fraction=0.35)
+    v, w = velocity_grid(2, 8)
+    a = Oracle(solid, 0.3, v, w, lateral=lateral, form="jump", threads=1)
+    b = Oracle(solid, 0.3, v, w, lateral=lateral, form="source", threads=1)
+    a.iterate(40)
+    b.iterate(40)
+    ra, ua = a.moments()
+    rb, ub = b.moments()
+    assert np.abs(ua - ub).max() < 1e-13
+    assert np.abs(ra - rb).max() < 1e-12
+    assert np.abs(a.wall() - b.wall()).max() < 1e-12
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_raster_equals_wavefront_bitwise(dims):
+    """Any order that visits upstream points first gives identical bits (dependency check)."""
+    if dims == 2:
+        solid = inputs.random_discs(20, 14, seed=2, rmin=2, rmax=3, solid_fraction=0.3)
+        v, w = velocity_grid(2, 8)
+    else:
+        rng = np.random.default_rng(4)
+        solid = rng.random((6, 7, 8)) < 0.2
+        v, w = velocity_grid(3, 4)
+    a = Oracle(solid, 0.4, v, w, traversal="raster", threads=1)
+    b = Oracle(solid, 0.4, v, w, traversal="wavefront", threads=1)
+    a.iterate(7)
+    b.iterate(7)
+    ra, ua = a.moments()
+    rb, ub = b.moments()
+    assert np.array_equal(ra, rb) and np.array_equal(ua, ub)
+    assert np.array_equal(a.wall(), b.wall())
+
+
+def test_thread_count_does_not_change_bits():
+    solid = inputs.random_discs(32, 24, seed=9, rmin=2, rmax=4, solid_fraction=0.3)
+    v, w = velocity_grid(2, 16)   # 256 velocities: several groups
+    a = Oracle(solid, 0.4, v, w, threads=1)
+    b = Oracle(solid, 0.4, v, w, threads=4)
+    a.iterate(3)
+    b.iterate(3)
+    assert np.array_equal(a.moments()[1], b.moments()[1])
+
+
+def test_mirror_symmetry_of_symmetric_cell():
+    """A geometry symmetric in x1 and x2 gives u1 even and u2 odd under both reflections."""
+    solid = inputs.cylinder_cell(32, 0.7)
+    v, w = velocity_grid(2, 8)
+    o = Oracle(solid, 0.1, v, w, threads=1)
+    o.iterate(37)
+    _, u = o.moments()
+    scale = np.abs(u).max()
+    assert np.abs(u[0] - u[0][::-1, :]).max() < 1e-14 * scale
+    assert np.abs(u[1] + u[1][::-1, :]).max() < 1e-14 * scale
+    assert np.abs(u[0] - u[0][:, ::-1]).max() < 1e-14 * scale
+    assert np.abs(u[1] + u[1][:, ::-1]).max() < 1e-14 * scale
+
+
+def test_specular_equals_periodic_on_mirrored_double():
+    """Specular lateral faces (Eq. 8) on G == periodic faces on [G; flip(G)] (first order, where
+    the steady system is consistent and the limit does not depend on the lag pattern)."""
+    g = inputs.random_discs(24, 16, seed=3, rmin=2, rmax=4, solid_fraction=0.3)
+    v, w = velocity_grid(2, 8)
+    a = Oracle(g, 0.3, v, w, lateral="specular", order=1, threads=1)
+    a.run(1e-13, 8000)
+    b = Oracle(np.concatenate([g, g[::-1]], axis=0), 0.3, v, w, lateral="periodic", order=1,
+               threads=1)
+    b.run(1e-13, 8000)
+    _, ua = a.moments()
+    _, ub = b.moments()
+    assert np.abs(ua - ub[:, :16]).max() < 1e-11
+    assert a.permeability() == pytest.approx(b.permeability(), rel=1e-11)
+
+
+def test_first_order_mass_flux_equal_across_sections():
+    """With the first-order stencil the scheme is conservative: at convergence the mass flux
+    through every x1 cross-section is the same (and the wall faces carry no flux, Eq. 6)."""
+    solid = inputs.cylinder_cell(32, 0.7)
+    v, w = velocity_grid(2, 8)
+    o = Oracle(solid, 0.1, v, w, order=1, threads=1)
+    o.run(1e-13, 5000)
+    f = o.flux()
+    assert (f.max() - f.min()) < 1e-11 * abs(f.mean())
+    # the flux per unit cross-section equals G_p up to the point/face offset: same sign, O(1)
+    _, u = o.moments()
+    assert f.mean() > 0 and u[0].sum() > 0
+
+
+def test_decomposition_does_not_change_converged_permeability():
+    """The paper's lagged-halo Omega_x decomposition (Sec. 3.2) converges to the same k."""
+    solid = inputs.cylinder_cell(32, 0.7)
+    v, w = velocity_grid(2, 8)
+    a = Oracle(solid, 0.1, v, w, threads=1)
+    _, ka, _ = a.run(1e-11, 5000)
+    b = Oracle(solid, 0.1, v, w, decomposition=(2, 2), threads=1)
+    _, kb, _ = b.run(1e-11, 5000)
+    assert kb == pytest.approx(ka, rel=1e-9)
+    # the history differs (one-iteration lag at the halos)
+    a2 = Oracle(solid, 0.1, v, w, threads=1)
+    b2 = Oracle(solid, 0.1, v, w, decomposition=(2, 2), threads=1)
+    assert not np.array_equal(a2.iterate(3), b2.iterate(3))
+
+
+# --- textbook limit ---------------------------------------------------------------------------
+
+def test_plane_poiseuille_flow_rate_matches_bgk_value():
+    """Plane channel between diffuse walls at delta = 1: the reduced flow rate, extrapolated in
+    the grid spacing (first-order wall error), matches the classical BGK value."""
+    ref = _load("textbook_values.json")["bgk_plane_poiseuille_flow_rate"]
+    v, w = velocity_grid(2, 32)
+    n1 = 4
+    dx = 1.0 / n1
+    qs = []
+    for hc in (40, 80):
+        solid = np.zeros((hc + 1, n1), bool)
+        solid[0, :] = True
+        H = (hc + 1) * dx                       # wall-to-wall distance (walls at solid nodes)
+        kn = math.sqrt(math.pi) * H / (2 * ref["delta"])
+        o = Oracle(solid, kn, v, w, lateral="periodic", threads=0)
+        o.run(1e-10, 20000, check_interval=50)
+        _, u = o.moments()
+        qs.append(2.0 * u[0][1:, :].sum() / n1 * dx / H ** 2)
+    q_extrap = 2 * qs[1] - qs[0]
+    assert q_extrap == pytest.approx(ref["Q"], rel=3e-3)
+    assert qs[0] < qs[1] < ref["Q"] * 1.003
+
+
+# --- post-processing printed by the paper --------------------------------------------------------
+
+def test_effective_knudsen_factors_match_paper():
+    for row in _load("paper_values.json")["effective_knudsen"]:
+        f = effective_knudsen_factor(row["k_inf"], row["porosity"], row["dims"])
+        assert f == pytest.approx(row["factor"], abs=0.006)
+
+
+def test_carpet_geometry_porosity():
+    s = inputs.sierpinski_carpet(540, 3)
+    assert 1 - s.mean() == pytest.approx((8 / 9) ** 3, abs=1e-12)
+    assert round(1 - s.mean(), 2) == _load("paper_values.json")["carpet_porosity"]["value"]
