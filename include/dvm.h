@@ -1,0 +1,170 @@
+/*
+ * dvm.h -- C ABI of the GB300 discrete-velocity solver for steady, pressure-driven rarefied gas
+ * flow through voxelised porous media (linearised BGK model, Ho, Zhu, Wu, Wang, Guo, Li, Zhang,
+ * "A multi-level parallel solver for rarefied gas flows in porous media", arXiv:1712.01132).
+ *
+ * One iteration (Sec. 3.1, steps i-iii) runs on the GPU as a transport sweep of every discrete
+ * velocity over the fluid voxels (Eq. 9-10, forward substitution in upwind order) fused with the
+ * velocity quadrature of the moments (Eq. 4), followed by a finalize pass that forms the wall
+ * densities (Eq. 6), the source terms of the next iteration and, every check interval, the
+ * permeability (Eq. 11-12) and the convergence measure (Eq. 15).
+ *
+ * Conventions
+ *  - Plain C types only.  Every pointer argument is a HOST pointer unless the argument says
+ *    otherwise.  Inputs are copied during the call; the caller keeps ownership of everything it
+ *    passes in and owns every output buffer.
+ *  - Masks are uint8 arrays laid out [n3][n2][n1] (x1 fastest; x1 is the flow direction), nonzero
+ *    = solid voxel.  Fields are double arrays in the same layout; vector fields are [dims][...].
+ *  - Every call returns a dvm_status.  Negative values are errors; dvm_last_error() gives a
+ *    message.  No C++ exception crosses this boundary.  A context is used by one host thread at a
+ *    time.
+ *  - A context holds one or more problems (a batch) that share a velocity grid and options; every
+ *    problem has its own geometry and Knudsen number.  Work is issued on the CUDA stream given in
+ *    the options (the legacy default stream when NULL).
+ */
+#ifndef DVM_H
+#define DVM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dvm_ctx dvm_ctx;   /* opaque, owned by the library */
+
+typedef enum {
+    DVM_OK = 0,              /* success; from dvm_iterate: converged (Err < tol) */
+    DVM_NOT_CONVERGED = 1,   /* dvm_iterate reached its iteration cap (informational) */
+    DVM_EINVAL = -1,         /* invalid argument (message in dvm_last_error) */
+    DVM_ENOMEM = -2,         /* device allocation failed */
+    DVM_ECUDA = -3,          /* a CUDA call or kernel failed */
+    DVM_ETIMEOUT = -4,       /* a bounded wait inside the sweep kernel expired */
+    DVM_ENUMERIC = -5        /* non-finite permeability detected */
+} dvm_status;
+
+/* Solid mask of one problem. dims = 2 (n[2] ignored) or 3; every n[j] >= 3. */
+typedef struct {
+    int dims;
+    int64_t n[3];
+    const uint8_t* solid;    /* host, [n3][n2][n1], nonzero = solid */
+} dvm_geometry;
+
+/* Discrete velocity set (Sec. 2.2): nv velocities v [nv][dims] (units of the most probable speed)
+ * with quadrature weights w [nv] that include the equilibrium factor pi^(-dims/2) exp(-|v|^2), so
+ * that sum(w) = 1 and sum(w g(v)) approximates int f_eq g dv.  Requirements: no zero component,
+ * the set is symmetric under the sign change of each component separately, sum(w) = 1 +- 1e-12. */
+typedef struct {
+    int nv;
+    const double* v;
+    const double* w;
+} dvm_velocity_grid;
+
+enum { DVM_FP64 = 0, DVM_FP32 = 1 };                 /* precision of h, moments and sweeps */
+enum { DVM_LATERAL_SPECULAR = 0, DVM_LATERAL_PERIODIC = 1 };
+
+typedef struct {
+    int precision;       /* DVM_FP64 or DVM_FP32; wall sums, G_p and Err are always FP64 */
+    int stencil_order;   /* 2: Eq. 9 second order with the first-order switch at walls; 1: first order */
+    int lateral_bc;      /* DVM_LATERAL_SPECULAR (Eq. 8) or DVM_LATERAL_PERIODIC */
+    int check_interval;  /* iterations between permeability/Err evaluations (Sec. 3.1: 100) */
+    void* stream;        /* cudaStream_t, or NULL for the legacy default stream */
+    int tile_x1;         /* sweep tile width along x1 (8 or 16; 0 = automatic) */
+    int band_rows;       /* rows per sweep band (0 = automatic) */
+    /* Optional device allocator (e.g. the caller's caching allocator).  When alloc is NULL the
+     * library uses cudaMalloc/cudaFree.  alloc returns NULL on failure. */
+    void* (*alloc)(size_t bytes, void* user);
+    void (*free)(void* ptr, size_t bytes, void* user);
+    void* alloc_user;
+} dvm_options;
+
+/* Fill *opt with the defaults: FP64, second order, specular lateral faces, check interval 100,
+ * NULL stream, automatic tiles, cudaMalloc. */
+void dvm_default_options(dvm_options* opt);
+
+/* Half-range Gauss-Hermite velocity grid (Sec. 2.2, Gautschi's half-range rule): n_per_axis
+ * (even, 2..128) points per axis, n_per_axis/2 positive nodes of the rule for
+ * int_0^inf exp(-v^2) g(v) dv mirrored to negative values, tensor product over dims (2 or 3)
+ * axes.  v receives [n^dims][dims] doubles, w receives [n^dims] doubles (weights as described for
+ * dvm_velocity_grid, sum = 1).  Host only; needs no GPU.  EINVAL on bad arguments. */
+dvm_status dvm_gh_velocity_grid(int dims, int n_per_axis, double* v, double* w);
+
+/* Create a context for one problem (Sec. 2.1): geometry, Knudsen number kn > 0 (Eq. 1, reference
+ * length = x1 extent, so dx = 1/n1 and nu = sqrt(pi)/(2 kn) in Eq. 3) and velocity grid.  The
+ * state is the zero perturbation h = 0 with boundary data derived from it (the inflow ghosts of
+ * Eq. 7 carry the unit pressure jump).  opt may be NULL (defaults).  Errors: EINVAL (bad kn, dims,
+ * sizes < 3, no fluid, no solid/fluid interface, invalid velocity grid), ENOMEM, ECUDA.  On error
+ * *out is set to NULL. */
+dvm_status dvm_create(const dvm_geometry* geometry, double kn, const dvm_velocity_grid* grid,
+                      const dvm_options* opt, dvm_ctx** out);
+
+/* Create a context for a batch of nprob problems (same dims, own geometry and Knudsen number
+ * each) that iterate together: every sweep and finalize launch covers all of them. */
+dvm_status dvm_create_batch(int nprob, const dvm_geometry* geometries, const double* kn,
+                            const dvm_velocity_grid* grid, const dvm_options* opt, dvm_ctx** out);
+
+/* Run iterations (Sec. 3.1) until every problem satisfies Err < tol at a check (Eq. 15 with the
+ * check interval of the options) or max_iter iterations have run in this call.  iters_done (may
+ * be NULL) receives the iterations run by this call, err_out (may be NULL) the largest Err at the
+ * last check (HUGE_VAL before the first).  Returns DVM_OK when converged, DVM_NOT_CONVERGED at the
+ * cap, ETIMEOUT/ECUDA/ENUMERIC on failure.  Synchronises the stream at every check. */
+dvm_status dvm_iterate(dvm_ctx* ctx, int max_iter, double tol, int* iters_done, double* err_out);
+
+/* Enqueue n iterations on the stream without convergence checks or host synchronisation (the
+ * permeability of the last iteration is still computed).  Use dvm_sync to wait and collect
+ * errors. */
+dvm_status dvm_step(dvm_ctx* ctx, int n);
+
+/* Wait for the stream and report a pending device error (ETIMEOUT/ECUDA). */
+dvm_status dvm_sync(dvm_ctx* ctx);
+
+/* Moments of problem 0 after the last iteration (Eq. 4): rho [N] and u [dims][N] in the paper's
+ * variables (the density carries the -x1 ramp of the unit pressure gradient); solid points are 0.
+ * on_device != 0 means rho and u are device pointers. */
+dvm_status dvm_moments(dvm_ctx* ctx, double* rho, double* u, int on_device);
+dvm_status dvm_moments_at(dvm_ctx* ctx, int prob, double* rho, double* u, int on_device);
+
+/* Permeability k = (2/sqrt(pi)) Kn G_p (Eq. 11) and G_p, the mean of u1 over all points (Eq. 12:
+ * the cross-section mean, averaged over every x1 cross-section), of the last iteration. */
+dvm_status dvm_permeability(dvm_ctx* ctx, double* k, double* gp);
+dvm_status dvm_permeability_at(dvm_ctx* ctx, int prob, double* k, double* gp);
+
+/* Wall densities of problem prob (Eq. 6) as [dims][2][N]: face (x, axis j, side -1/+1) whose
+ * solid neighbour is x -/+ e_j; 0 where there is no such face. */
+dvm_status dvm_wall_density_at(dvm_ctx* ctx, int prob, double* rhos);
+
+/* Number of iterations run since creation, problems in the batch, points of problem prob. */
+dvm_status dvm_info(const dvm_ctx* ctx, int64_t* iterations, int* nprob);
+
+/* Message of the last error on this context ("" if none); valid until the next call.  With
+ * ctx == NULL: the message of the last failed dvm_create/dvm_create_batch on this thread. */
+const char* dvm_last_error(const dvm_ctx* ctx);
+
+/* Release the context and its device memory (synchronises its stream). NULL is a no-op. */
+void dvm_destroy(dvm_ctx* ctx);
+
+/* Kernel timing (measurement support, not part of the method).  When enabled, every iteration
+ * records CUDA events on the context's stream around its sweep and finalize launches.
+ * dvm_profile_read synchronises the stream, returns the summed event durations (milliseconds) and
+ * launch counts since the last read (any pointer may be NULL) and restarts the accumulation. */
+dvm_status dvm_profile_enable(dvm_ctx* ctx, int on);
+dvm_status dvm_profile_read(dvm_ctx* ctx, double* sweep_ms, int64_t* sweep_launches,
+                            double* finalize_ms, int64_t* finalize_launches);
+
+/* Bytes copied host->device and device->host by this context since creation (inputs, setup
+ * tables, readouts, permeability and status words). */
+dvm_status dvm_transfer_bytes(const dvm_ctx* ctx, int64_t* h2d, int64_t* d2h);
+
+/* Test hook (fault-handling tests; not needed in normal use): set the bound of every spin wait
+ * of the sweep kernel to timeout_ns and make work item withhold_item (-1: none) never publish its
+ * progress, so that the band waiting on it gives up, the kernel records DVM_ETIMEOUT in its status
+ * word and every CTA returns.  The next dvm_iterate/dvm_sync reports DVM_ETIMEOUT; the context and
+ * the CUDA context stay usable (the solution state of that iteration is not meaningful). */
+dvm_status dvm_debug_set_wait(dvm_ctx* ctx, long long timeout_ns, int withhold_item);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DVM_H */

@@ -1,0 +1,768 @@
+// dvm_api.cpp -- host side of the C ABI declared in include/dvm.h.
+//
+// Responsibilities: argument validation, per-problem preprocessing (the per-point stencil cases
+// that the paper fixes in preprocessing "to avoid IF-THEN at every iteration", Sec. 2.3; the
+// grouping of the discrete velocities into quadrants whose lanes line up under reflection; the
+// per-lane reciprocal denominators of the point update), device memory layout, and the iteration
+// driver (sweep + finalize per iteration, permeability and Err every check interval, Eq. 15).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/dvm.h"
+#include "dvm_internal.h"
+
+namespace dvm {
+bool half_range_gh(int m, double* c, double* a);
+template <typename T> size_t sweep2d_smem(int T1, int NW, int max_rows);
+template <typename T> cudaError_t launch_sweep2d(const SweepArgs2D<T>&, int T1, int grid, int NW, cudaStream_t);
+template <typename T> cudaError_t sweep2d_occupancy(int T1, int NW, int max_rows, int* blocks_per_sm);
+template <typename T> cudaError_t launch_finalize2d(const FinArgs2D<T>&, int nblocks, cudaStream_t);
+template <typename T> cudaError_t launch_init2d(const Prob2D<T>*, int NL, const double* qw, cudaStream_t);
+template <typename T> cudaError_t launch_moments2d(const Prob2D<T>*, double* rho, double* u, cudaStream_t);
+template <typename T> cudaError_t launch_wall2d(const Prob2D<T>*, double* out, cudaStream_t);
+}  // namespace dvm
+
+using namespace dvm;
+
+namespace {
+
+constexpr int kFinBlock = 256;
+
+struct Buf {
+    void* p;
+    size_t bytes;
+};
+
+struct HostProb {
+    int n[3];
+    int N;
+    double kn, nu, dx;
+    int nbands;
+    std::vector<uint16_t> code;
+};
+
+}  // namespace
+
+struct dvm_ctx {
+    std::string err;
+    dvm_options opt;
+    cudaStream_t stream = nullptr;
+    int dims = 2, nprob = 0, nv = 0, nvq = 0, NQ = 4, NL = 32, NW = 1;
+    int prec = DVM_FP64;
+    int T1 = 8, rows = 8, max_rows = 8;
+    std::vector<HostProb> hp;
+    std::vector<Buf> bufs;
+    // device objects
+    void* probs_dev = nullptr;       // Prob2D<T>[nprob]
+    std::vector<char> probs_host;    // host copy of the Prob2D array
+    SweepItem* items_dev = nullptr;
+    int nitems = 0;
+    int* counters_dev = nullptr;     // [ticket][prog flags...]
+    size_t counters_bytes = 0;
+    int* status_dev = nullptr;
+    int* blk_prob_dev = nullptr;
+    int* blk_start_dev = nullptr;
+    int fin_blocks = 0;
+    double* qw_dev = nullptr;        // [nprob][4][3]
+    double* scratch_dev = nullptr;   // readout scratch (max N * 4 doubles)
+    size_t scratch_bytes = 0;
+    // pinned host mirrors
+    double* kval_host = nullptr;     // [nprob][3]
+    int* status_host = nullptr;
+    // iteration state
+    long long iters = 0;
+    std::vector<double> k_check;     // k at the last check, per problem
+    double last_err = HUGE_VAL;
+    int sweep_grid = 1;
+    long long timeout_ns = kDefaultTimeoutNs;
+    int withhold_item = -1;
+    std::vector<int> prog_offset;    // per problem, offset of its progress flags in counters
+    // measurement support
+    bool profile = false;
+    std::vector<cudaEvent_t> ev_pool;      // events owned by the context
+    std::vector<cudaEvent_t> ev_marks;     // [3 per profiled iteration] before sweep, after sweep, after finalize
+    long long h2d_bytes = 0, d2h_bytes = 0;
+};
+
+namespace {
+
+thread_local std::string g_create_err;   // message of the last failed creation on this thread
+
+dvm_status fail(dvm_ctx* c, dvm_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    g_create_err = msg;
+    return s;
+}
+
+dvm_status cuda_fail(dvm_ctx* c, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(c, DVM_ENOMEM, m);
+    return fail(c, DVM_ECUDA, m);
+}
+
+void* dev_alloc(dvm_ctx* c, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    void* p = nullptr;
+    if (c->opt.alloc) {
+        p = c->opt.alloc(bytes, c->opt.alloc_user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) c->bufs.push_back({p, bytes});
+    return p;
+}
+
+void free_all(dvm_ctx* c) {
+    for (auto& b : c->bufs) {
+        if (c->opt.alloc) {
+            if (c->opt.free) c->opt.free(b.p, b.bytes, c->opt.alloc_user);
+        } else {
+            cudaFree(b.p);
+        }
+    }
+    c->bufs.clear();
+    if (c->kval_host) cudaFreeHost(c->kval_host);
+    if (c->status_host) cudaFreeHost(c->status_host);
+    c->kval_host = nullptr;
+    c->status_host = nullptr;
+}
+
+// periodic along x1 always; lateral axes periodic or mirrored (specular, Eq. 8)
+int map_coord(int l, int n, bool periodic) {
+    if (l >= 0 && l < n) return l;
+    if (periodic) return ((l % n) + n) % n;
+    return l < 0 ? -1 - l : 2 * n - 1 - l;
+}
+
+// Stencil cases (Eq. 9 with the first-order switch of Sec. 2.3) of every fluid point.
+void classify(HostProb& P, int dims, const uint8_t* solid, int lateral, int order) {
+    const int n1 = P.n[0], n2 = P.n[1], n3 = dims == 3 ? P.n[2] : 1;
+    P.code.assign(P.N, 0);
+    for (int z = 0; z < n3; ++z)
+        for (int y = 0; y < n2; ++y)
+            for (int x = 0; x < n1; ++x) {
+                const int id = (z * n2 + y) * n1 + x;
+                if (solid[id]) {
+                    P.code[id] = kSolidBit;
+                    continue;
+                }
+                uint16_t code = 0;
+                const int c[3] = {x, y, z};
+                for (int j = 0; j < dims; ++j)
+                    for (int u = 0; u < 2; ++u) {
+                        const int sigma = u ? 1 : -1;       // direction of the upstream points
+                        const bool per = (j == 0) || lateral == DVM_LATERAL_PERIODIC;
+                        int c1[3] = {c[0], c[1], c[2]}, c2[3] = {c[0], c[1], c[2]};
+                        c1[j] = map_coord(c[j] + sigma, P.n[j], per);
+                        c2[j] = map_coord(c[j] + 2 * sigma, P.n[j], per);
+                        const bool s1 = solid[(c1[2] * n2 + c1[1]) * n1 + c1[0]] != 0;
+                        const bool s2 = solid[(c2[2] * n2 + c2[1]) * n1 + c2[0]] != 0;
+                        int cs = 0;
+                        if (s1) cs = 2;
+                        else if (order == 2 && s2) cs = 1;
+                        code |= (uint16_t)(cs << (2 * (2 * j + u)));
+                    }
+                P.code[id] = code;
+            }
+}
+
+template <typename T>
+dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_grid* grid) {
+    const int NQ = 4;
+    // ---- velocity groups: quadrant q (bit j set when v_j < 0), lanes ordered by (|v1|, |v2|)
+    std::vector<std::vector<int>> group(NQ);
+    for (int k = 0; k < grid->nv; ++k) {
+        const double* v = grid->v + 2 * k;
+        group[(v[0] < 0 ? 1 : 0) | (v[1] < 0 ? 2 : 0)].push_back(k);
+    }
+    auto key_less = [&](int a, int b) {
+        const double* va = grid->v + 2 * a;
+        const double* vb = grid->v + 2 * b;
+        if (std::fabs(va[0]) != std::fabs(vb[0])) return std::fabs(va[0]) < std::fabs(vb[0]);
+        return std::fabs(va[1]) < std::fabs(vb[1]);
+    };
+    for (auto& g : group) std::sort(g.begin(), g.end(), key_less);
+    const int nvq = (int)group[0].size();
+    for (int q = 1; q < NQ; ++q)
+        if ((int)group[q].size() != nvq) return fail(c, DVM_EINVAL, "velocity grid is not symmetric under sign changes");
+    for (int m = 0; m < nvq; ++m) {
+        const double* v0 = grid->v + 2 * group[0][m];
+        for (int q = 1; q < NQ; ++q) {
+            const double* vq = grid->v + 2 * group[q][m];
+            if (std::fabs(vq[0]) != std::fabs(v0[0]) || std::fabs(vq[1]) != std::fabs(v0[1]) ||
+                grid->w[group[q][m]] != grid->w[group[0][m]])
+                return fail(c, DVM_EINVAL, "velocity grid is not symmetric under sign changes");
+        }
+    }
+    c->nvq = nvq;
+    c->NW = (nvq + 31) / 32;
+    c->NL = 32 * c->NW;
+    const int NL = c->NL;
+    if (c->NW > 16) return fail(c, DVM_EINVAL, "more than 512 velocities per quadrant");
+    // ---- tiles
+    c->T1 = c->opt.tile_x1 ? c->opt.tile_x1 : ((c->prec == DVM_FP32) ? 16 : 8);
+    if (c->T1 != 8 && c->T1 != 16) return fail(c, DVM_EINVAL, "tile_x1 must be 8 or 16");
+    int rows = c->opt.band_rows ? c->opt.band_rows : ((c->prec == DVM_FP32) ? 16 : 8);
+    if (rows < 1) return fail(c, DVM_EINVAL, "band_rows must be positive");
+    c->rows = rows;
+    int max_rows = 1;
+    for (int b = 0; b < c->nprob; ++b) max_rows = std::max(max_rows, std::min(rows, c->hp[b].n[1]));
+    c->max_rows = max_rows;
+    // ---- wall denominators (Eq. 6) and quadrant weight sums
+    double dwall[2] = {0, 0};
+    for (int k = 0; k < grid->nv; ++k)
+        for (int j = 0; j < 2; ++j)
+            if (grid->v[2 * k + j] > 0) dwall[j] += grid->w[k] * grid->v[2 * k + j];
+    std::vector<double> qw((size_t)c->nprob * NQ * 3, 0.0);
+    for (int b = 0; b < c->nprob; ++b)
+        for (int q = 0; q < NQ; ++q)
+            for (int k : group[q]) {
+                qw[((size_t)b * NQ + q) * 3 + 0] += grid->w[k];
+                qw[((size_t)b * NQ + q) * 3 + 1] += grid->w[k] * grid->v[2 * k];
+                qw[((size_t)b * NQ + q) * 3 + 2] += grid->w[k] * grid->v[2 * k + 1];
+            }
+    // ---- per problem device buffers
+    std::vector<Prob2D<T>> probs(c->nprob);
+    std::vector<SweepItem> items;
+    std::vector<int> blk_prob, blk_start;
+    int prog_total = 0;
+    c->prog_offset.assign(c->nprob, 0);
+    for (int b = 0; b < c->nprob; ++b) {
+        HostProb& H = c->hp[b];
+        Prob2D<T>& P = probs[b];
+        std::memset(&P, 0, sizeof(P));
+        P.n1 = H.n[0];
+        P.n2 = H.n[1];
+        P.N = H.N;
+        P.rows = std::min(rows, P.n2);
+        P.nbands = (P.n2 + P.rows - 1) / P.rows;
+        H.nbands = P.nbands;
+        P.lateral = c->opt.lateral_bc;
+        P.order = c->opt.stencil_order;
+        P.kn = H.kn;
+        P.nu = H.nu;
+        P.dx = H.dx;
+        P.dwall[0] = dwall[0];
+        P.dwall[1] = dwall[1];
+        const size_t N = H.N;
+        uint16_t* code = (uint16_t*)dev_alloc(c, N * sizeof(uint16_t));
+        P.src = (T*)dev_alloc(c, N * 4 * sizeof(T));
+        P.E = (T*)dev_alloc(c, N * 4 * sizeof(T));
+        P.P = (T*)dev_alloc(c, (size_t)NQ * 3 * N * sizeof(T));
+        P.gx1 = (T*)dev_alloc(c, (size_t)2 * NQ * P.n2 * 2 * NL * sizeof(T));
+        P.glat = (T*)dev_alloc(c, (size_t)2 * NQ * P.n1 * 2 * NL * sizeof(T));
+        P.edge = (T*)dev_alloc(c, (size_t)NQ * std::max(P.nbands - 1, 1) * P.n1 * 2 * NL * sizeof(T));
+        T* lanec = (T*)dev_alloc(c, (size_t)NQ * NL * kLaneConsts * sizeof(T));
+        P.fin_nblocks = (int)((N + kFinBlock - 1) / kFinBlock);
+        P.fin_block0 = (int)blk_prob.size();
+        P.kpart = (double*)dev_alloc(c, (size_t)P.fin_nblocks * sizeof(double));
+        P.kval = (double*)dev_alloc(c, 3 * sizeof(double));
+        P.fin_counter = (unsigned int*)dev_alloc(c, sizeof(unsigned int));
+        if (!code || !P.src || !P.E || !P.P || !P.gx1 || !P.glat || !P.edge || !lanec || !P.kpart || !P.kval ||
+            !P.fin_counter)
+            return fail(c, DVM_ENOMEM, "device allocation failed");
+        P.code = code;
+        P.lanec = lanec;
+        cudaError_t e = cudaMemcpyAsync(code, H.code.data(), N * sizeof(uint16_t), cudaMemcpyHostToDevice, c->stream);
+        c->h2d_bytes += N * sizeof(uint16_t);
+        if (e != cudaSuccess) return cuda_fail(c, e, "copy code");
+        e = cudaMemsetAsync(P.fin_counter, 0, sizeof(unsigned int), c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "memset");
+        e = cudaMemsetAsync(P.kval, 0, 3 * sizeof(double), c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "memset");
+        e = cudaMemsetAsync(P.edge, 0, (size_t)NQ * std::max(P.nbands - 1, 1) * P.n1 * 2 * NL * sizeof(T), c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "memset");
+        // lane constants: v1, v2, |v1|/dx, |v2|/dx, W, W v1, W v2, R[0..3]
+        std::vector<T> lc((size_t)NQ * NL * kLaneConsts, T(0));
+        const double c0o = (P.order == 2) ? 1.5 : 1.0;
+        for (int q = 0; q < NQ; ++q)
+            for (int l = 0; l < NL; ++l) {
+                double v1, v2, w;
+                if (l < nvq) {
+                    const int k = group[q][l];
+                    v1 = grid->v[2 * k];
+                    v2 = grid->v[2 * k + 1];
+                    w = grid->w[k];
+                } else {   // padding lane: finite values, zero weight
+                    v1 = (q & 1) ? -1.0 : 1.0;
+                    v2 = (q & 2) ? -1.0 : 1.0;
+                    w = 0.0;
+                }
+                const double a1 = std::fabs(v1) / H.dx, a2 = std::fabs(v2) / H.dx;
+                T* d = &lc[((size_t)q * NL + l) * kLaneConsts];
+                d[0] = (T)v1; d[1] = (T)v2; d[2] = (T)a1; d[3] = (T)a2;
+                d[4] = (T)w; d[5] = (T)(w * v1); d[6] = (T)(w * v2);
+                for (int rs = 0; rs < 4; ++rs) {
+                    const double c0a = (rs & 1) ? 1.0 : c0o;
+                    const double c0b = (rs & 2) ? 1.0 : c0o;
+                    d[7 + rs] = (T)(1.0 / (H.nu + c0a * a1 + c0b * a2));
+                }
+            }
+        e = cudaMemcpyAsync(lanec, lc.data(), lc.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream);
+        c->h2d_bytes += lc.size() * sizeof(T);
+        if (e != cudaSuccess) return cuda_fail(c, e, "copy lane constants");
+        e = cudaStreamSynchronize(c->stream);   // host vectors go out of scope
+        if (e != cudaSuccess) return cuda_fail(c, e, "sync");
+        for (int k = 0; k < P.fin_nblocks; ++k) {
+            blk_prob.push_back(b);
+            blk_start.push_back(k * kFinBlock);
+        }
+        c->prog_offset[b] = 1 + prog_total;
+        prog_total += NQ * P.nbands;
+    }
+    // ---- work items in band order (a band only waits for lower bands: deadlock-free tickets)
+    int maxb = 0;
+    for (int b = 0; b < c->nprob; ++b) maxb = std::max(maxb, probs[b].nbands);
+    for (int band = 0; band < maxb; ++band)
+        for (int b = 0; b < c->nprob; ++b)
+            if (band < probs[b].nbands)
+                for (int q = 0; q < NQ; ++q) items.push_back({b, q, band, 0});
+    c->nitems = (int)items.size();
+    c->counters_bytes = sizeof(int) * (size_t)(1 + prog_total);
+    c->counters_dev = (int*)dev_alloc(c, c->counters_bytes);
+    c->status_dev = (int*)dev_alloc(c, sizeof(int));
+    c->items_dev = (SweepItem*)dev_alloc(c, items.size() * sizeof(SweepItem));
+    c->fin_blocks = (int)blk_prob.size();
+    c->blk_prob_dev = (int*)dev_alloc(c, blk_prob.size() * sizeof(int));
+    c->blk_start_dev = (int*)dev_alloc(c, blk_start.size() * sizeof(int));
+    c->qw_dev = (double*)dev_alloc(c, qw.size() * sizeof(double));
+    size_t maxN = 0;
+    for (auto& H : c->hp) maxN = std::max(maxN, (size_t)H.N);
+    c->scratch_bytes = maxN * 4 * sizeof(double);
+    c->scratch_dev = (double*)dev_alloc(c, c->scratch_bytes);
+    c->probs_dev = dev_alloc(c, probs.size() * sizeof(Prob2D<T>));
+    if (!c->counters_dev || !c->status_dev || !c->items_dev || !c->blk_prob_dev || !c->blk_start_dev ||
+        !c->qw_dev || !c->scratch_dev || !c->probs_dev)
+        return fail(c, DVM_ENOMEM, "device allocation failed");
+    for (int b = 0; b < c->nprob; ++b) probs[b].prog = c->counters_dev + c->prog_offset[b];
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(c->items_dev, items.data(), items.size() * sizeof(SweepItem), cudaMemcpyHostToDevice, c->stream)) ||
+        (e = cudaMemcpyAsync(c->blk_prob_dev, blk_prob.data(), blk_prob.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream)) ||
+        (e = cudaMemcpyAsync(c->blk_start_dev, blk_start.data(), blk_start.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream)) ||
+        (e = cudaMemcpyAsync(c->qw_dev, qw.data(), qw.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream)) ||
+        (e = cudaMemcpyAsync(c->probs_dev, probs.data(), probs.size() * sizeof(Prob2D<T>), cudaMemcpyHostToDevice, c->stream)) ||
+        (e = cudaMemsetAsync(c->status_dev, 0, sizeof(int), c->stream)) ||
+        (e = cudaStreamSynchronize(c->stream)))
+        return cuda_fail(c, e, "upload");
+    c->h2d_bytes += items.size() * sizeof(SweepItem) + (blk_prob.size() + blk_start.size()) * sizeof(int) +
+                    qw.size() * sizeof(double) + probs.size() * sizeof(Prob2D<T>);
+    c->probs_host.assign((const char*)probs.data(), (const char*)probs.data() + probs.size() * sizeof(Prob2D<T>));
+    // ---- persistent grid size
+    int per_sm = 0;
+    e = sweep2d_occupancy<T>(c->T1, c->NW, c->max_rows, &per_sm);
+    if (e != cudaSuccess) return cuda_fail(c, e, "occupancy");
+    if (per_sm < 1) return fail(c, DVM_EINVAL, "sweep kernel does not fit on an SM with these tiles");
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    c->sweep_grid = std::max(1, std::min(c->nitems, per_sm * sms));
+    // ---- zero-perturbation start
+    for (int b = 0; b < c->nprob; ++b) {
+        const Prob2D<T>* pd = (const Prob2D<T>*)c->probs_dev + b;
+        e = launch_init2d<T>(pd, NL, c->qw_dev + (size_t)b * NQ * 3, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+    }
+    FinArgs2D<T> fa{(const Prob2D<T>*)c->probs_dev, c->blk_prob_dev, c->blk_start_dev, c->status_dev};
+    e = launch_finalize2d<T>(fa, c->fin_blocks, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernel");
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "init");
+    return DVM_OK;
+}
+
+cudaEvent_t take_event(dvm_ctx* c) {
+    const size_t used = c->ev_marks.size();
+    if (used < c->ev_pool.size()) return c->ev_pool[used];
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
+    c->ev_pool.push_back(ev);
+    return ev;
+}
+
+cudaError_t mark(dvm_ctx* c) {
+    if (!c->profile) return cudaSuccess;
+    cudaEvent_t ev = take_event(c);
+    if (!ev) return cudaErrorMemoryAllocation;
+    c->ev_marks.push_back(ev);
+    return cudaEventRecord(ev, c->stream);
+}
+
+template <typename T>
+dvm_status enqueue_iter_2d(dvm_ctx* c) {
+    cudaError_t e = cudaMemsetAsync(c->counters_dev, 0, c->counters_bytes, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "memset counters");
+    SweepArgs2D<T> a;
+    a.prob = (const Prob2D<T>*)c->probs_dev;
+    a.items = c->items_dev;
+    a.nitems = c->nitems;
+    a.NL = c->NL;
+    a.max_rows = c->max_rows;
+    a.parity = (int)(c->iters & 1);
+    a.ticket = c->counters_dev;
+    a.status = c->status_dev;
+    a.timeout_ns = c->timeout_ns;
+    a.withhold_item = c->withhold_item;
+    if ((e = mark(c)) != cudaSuccess) return cuda_fail(c, e, "event");
+    e = launch_sweep2d<T>(a, c->T1, c->sweep_grid, c->NW, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sweep kernel");
+    if ((e = mark(c)) != cudaSuccess) return cuda_fail(c, e, "event");
+    FinArgs2D<T> fa{(const Prob2D<T>*)c->probs_dev, c->blk_prob_dev, c->blk_start_dev, c->status_dev};
+    e = launch_finalize2d<T>(fa, c->fin_blocks, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernel");
+    if ((e = mark(c)) != cudaSuccess) return cuda_fail(c, e, "event");
+    c->iters++;
+    return DVM_OK;
+}
+
+dvm_status enqueue_iter(dvm_ctx* c) {
+    return c->prec == DVM_FP32 ? enqueue_iter_2d<float>(c) : enqueue_iter_2d<double>(c);
+}
+
+// wait for the stream, fetch k of every problem and the device status word
+dvm_status collect(dvm_ctx* c) {
+    cudaError_t e;
+    for (int b = 0; b < c->nprob; ++b) {
+        const double* kv;
+        if (c->prec == DVM_FP32) kv = ((const Prob2D<float>*)c->probs_host.data())[b].kval;
+        else kv = ((const Prob2D<double>*)c->probs_host.data())[b].kval;
+        e = cudaMemcpyAsync(c->kval_host + 3 * b, kv, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "read permeability");
+    }
+    e = cudaMemcpyAsync(c->status_host, c->status_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read status");
+    c->d2h_bytes += (long long)c->nprob * 3 * sizeof(double) + sizeof(int);
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream");
+    if (*c->status_host != 0) {
+        const int st = *c->status_host;
+        cudaMemsetAsync(c->status_dev, 0, sizeof(int), c->stream);
+        cudaStreamSynchronize(c->stream);
+        if (st == DVM_ETIMEOUT) return fail(c, DVM_ETIMEOUT, "a bounded wait in the sweep kernel expired");
+        return fail(c, DVM_ECUDA, "device status " + std::to_string(st));
+    }
+    return DVM_OK;
+}
+
+dvm_status validate_grid(dvm_ctx* c, int dims, const dvm_velocity_grid* g) {
+    if (!g || g->nv <= 0 || !g->v || !g->w) return fail(c, DVM_EINVAL, "velocity grid is empty");
+    double s = 0.0;
+    for (int k = 0; k < g->nv; ++k) {
+        for (int j = 0; j < dims; ++j) {
+            const double vj = g->v[(size_t)k * dims + j];
+            if (!(vj != 0.0) || !std::isfinite(vj)) return fail(c, DVM_EINVAL, "velocity component zero or not finite");
+        }
+        if (!(g->w[k] > 0.0) || !std::isfinite(g->w[k])) return fail(c, DVM_EINVAL, "weight not positive");
+        s += g->w[k];
+    }
+    if (std::fabs(s - 1.0) > 1e-12) return fail(c, DVM_EINVAL, "weights do not sum to 1");
+    return DVM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dvm_default_options(dvm_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = DVM_FP64;
+    o->stencil_order = 2;
+    o->lateral_bc = DVM_LATERAL_SPECULAR;
+    o->check_interval = 100;
+}
+
+dvm_status dvm_gh_velocity_grid(int dims, int n, double* v, double* w) {
+    if ((dims != 2 && dims != 3) || n < 2 || n > 128 || (n & 1) || !v || !w) return DVM_EINVAL;
+    const int m = n / 2;
+    std::vector<double> cc(m), aa(m);
+    if (!half_range_gh(m, cc.data(), aa.data())) return DVM_EINVAL;
+    std::vector<double> v1(n), w1(n);
+    const double isqpi = 1.0 / std::sqrt(3.14159265358979323846);
+    for (int i = 0; i < m; ++i) {
+        v1[m - 1 - i] = -cc[i];
+        w1[m - 1 - i] = aa[i] * isqpi;
+        v1[m + i] = cc[i];
+        w1[m + i] = aa[i] * isqpi;
+    }
+    const int nv = dims == 2 ? n * n : n * n * n;
+    for (int k = 0; k < nv; ++k) {
+        int idx[3];
+        int r = k;
+        for (int j = dims - 1; j >= 0; --j) {   // axis 0 slowest
+            idx[j] = r % n;
+            r /= n;
+        }
+        double wk = 1.0;
+        for (int j = 0; j < dims; ++j) {
+            v[(size_t)k * dims + j] = v1[idx[j]];
+            wk *= w1[idx[j]];
+        }
+        w[k] = wk;
+    }
+    return DVM_OK;
+}
+
+dvm_status dvm_create_batch(int nprob, const dvm_geometry* geoms, const double* kn, const dvm_velocity_grid* grid,
+                            const dvm_options* opt, dvm_ctx** out) {
+    if (!out) return DVM_EINVAL;
+    *out = nullptr;
+    dvm_ctx* c = new (std::nothrow) dvm_ctx();
+    if (!c) return DVM_ENOMEM;
+    if (opt) c->opt = *opt;
+    else dvm_default_options(&c->opt);
+    g_create_err.clear();
+    auto reject = [&](dvm_status s, const char* m) {
+        // creation failed before any device work: the message stays readable through
+        // dvm_last_error(NULL) on this thread
+        g_create_err = m;
+        delete c;
+        return s;
+    };
+    if (nprob < 1 || !geoms || !kn) return reject(DVM_EINVAL, "no problems");
+    const int dims = geoms[0].dims;
+    if (dims != 2 && dims != 3) return reject(DVM_EINVAL, "dims must be 2 or 3");
+    if (dims == 3) return reject(DVM_EINVAL, "3D problems are not supported by this build");
+    if (c->opt.precision != DVM_FP64 && c->opt.precision != DVM_FP32) return reject(DVM_EINVAL, "precision");
+    if (c->opt.stencil_order != 1 && c->opt.stencil_order != 2) return reject(DVM_EINVAL, "stencil_order");
+    if (c->opt.lateral_bc != 0 && c->opt.lateral_bc != 1) return reject(DVM_EINVAL, "lateral_bc");
+    if (c->opt.check_interval < 1) return reject(DVM_EINVAL, "check_interval");
+    c->dims = dims;
+    c->nprob = nprob;
+    c->prec = c->opt.precision;
+    c->stream = (cudaStream_t)c->opt.stream;
+    if (validate_grid(c, dims, grid) != DVM_OK) {
+        const std::string m = c->err;
+        return reject(DVM_EINVAL, m.c_str());
+    }
+    c->nv = grid->nv;
+    c->hp.resize(nprob);
+    for (int b = 0; b < nprob; ++b) {
+        const dvm_geometry& g = geoms[b];
+        if (g.dims != dims || !g.solid) return reject(DVM_EINVAL, "geometry");
+        if (!(kn[b] > 0.0) || !std::isfinite(kn[b])) return reject(DVM_EINVAL, "Knudsen number must be positive");
+        HostProb& H = c->hp[b];
+        long long N = 1;
+        for (int j = 0; j < 3; ++j) {
+            H.n[j] = (j < dims) ? (int)g.n[j] : 1;
+            if (j < dims && (g.n[j] < 3 || g.n[j] > (1 << 20))) return reject(DVM_EINVAL, "every extent must be >= 3");
+            N *= H.n[j];
+        }
+        if (N > (1LL << 30)) return reject(DVM_EINVAL, "geometry too large");
+        H.N = (int)N;
+        H.kn = kn[b];
+        H.nu = std::sqrt(3.14159265358979323846) / (2.0 * kn[b]);
+        H.dx = 1.0 / H.n[0];
+        classify(H, dims, g.solid, c->opt.lateral_bc, c->opt.stencil_order);
+        long long fluid = 0, faces = 0;
+        for (int id = 0; id < H.N; ++id) {
+            if (H.code[id] & kSolidBit) continue;
+            ++fluid;
+            for (int s = 0; s < 2 * dims; ++s)
+                if (((H.code[id] >> (2 * s)) & 3) == 2) ++faces;
+        }
+        if (fluid == 0) return reject(DVM_EINVAL, "no fluid voxel");
+        if (faces == 0) return reject(DVM_EINVAL, "no solid/fluid interface: the steady problem has no solution");
+    }
+    cudaError_t e;
+    if ((e = cudaMallocHost(&c->kval_host, sizeof(double) * 3 * nprob)) != cudaSuccess ||
+        (e = cudaMallocHost(&c->status_host, sizeof(int))) != cudaSuccess) {
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return e == cudaErrorMemoryAllocation ? DVM_ENOMEM : DVM_ECUDA;
+    }
+    dvm_status s = (c->prec == DVM_FP32) ? build_2d<float>(c, geoms, grid) : build_2d<double>(c, geoms, grid);
+    if (s != DVM_OK) {
+        cudaStreamSynchronize(c->stream);
+        free_all(c);
+        delete c;
+        return s;
+    }
+    c->k_check.assign(nprob, 0.0);
+    *out = c;
+    return DVM_OK;
+}
+
+dvm_status dvm_create(const dvm_geometry* geometry, double kn, const dvm_velocity_grid* grid, const dvm_options* opt,
+                      dvm_ctx** out) {
+    return dvm_create_batch(1, geometry, &kn, grid, opt, out);
+}
+
+dvm_status dvm_step(dvm_ctx* c, int n) {
+    if (!c || n < 0) return DVM_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        dvm_status s = enqueue_iter(c);
+        if (s != DVM_OK) return s;
+    }
+    return DVM_OK;
+}
+
+dvm_status dvm_sync(dvm_ctx* c) {
+    if (!c) return DVM_EINVAL;
+    return collect(c);
+}
+
+dvm_status dvm_iterate(dvm_ctx* c, int max_iter, double tol, int* iters_done, double* err_out) {
+    if (!c || max_iter < 0 || !(tol >= 0.0)) return DVM_EINVAL;
+    const int ci = c->opt.check_interval;
+    int done = 0;
+    dvm_status result = DVM_NOT_CONVERGED;
+    while (done < max_iter) {
+        const int to_check = ci - (int)(c->iters % ci);
+        const int n = std::min(to_check, max_iter - done);
+        for (int i = 0; i < n; ++i) {
+            dvm_status s = enqueue_iter(c);
+            if (s != DVM_OK) return s;
+        }
+        done += n;
+        if (c->iters % ci != 0) continue;
+        dvm_status s = collect(c);
+        if (s != DVM_OK) {
+            if (iters_done) *iters_done = done;
+            return s;
+        }
+        double worst = 0.0;
+        for (int b = 0; b < c->nprob; ++b) {
+            const double k = c->kval_host[3 * b];
+            if (!std::isfinite(k)) {
+                if (iters_done) *iters_done = done;
+                return fail(c, DVM_ENUMERIC, "permeability is not finite");
+            }
+            // Eq. 15: Err = |k(l) - k(l - ci)| / (ci |k(l)|)
+            const double err = (k != 0.0) ? std::fabs((k - c->k_check[b]) / k) / ci : (c->k_check[b] == 0.0 ? 0.0 : HUGE_VAL);
+            worst = std::max(worst, err);
+            c->k_check[b] = k;
+        }
+        c->last_err = worst;
+        if (worst < tol) {
+            result = DVM_OK;
+            break;
+        }
+    }
+    if (iters_done) *iters_done = done;
+    if (err_out) *err_out = c->last_err;
+    return result;
+}
+
+dvm_status dvm_moments_at(dvm_ctx* c, int prob, double* rho, double* u, int on_device) {
+    if (!c || prob < 0 || prob >= c->nprob || !rho || !u) return DVM_EINVAL;
+    const size_t N = c->hp[prob].N;
+    double* drho = on_device ? rho : c->scratch_dev;
+    double* du = on_device ? u : c->scratch_dev + N;
+    cudaError_t e;
+    if (c->prec == DVM_FP32) e = launch_moments2d<float>((const Prob2D<float>*)c->probs_dev + prob, drho, du, c->stream);
+    else e = launch_moments2d<double>((const Prob2D<double>*)c->probs_dev + prob, drho, du, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "moments kernel");
+    if (!on_device) {
+        if ((e = cudaMemcpyAsync(rho, drho, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream)) ||
+            (e = cudaMemcpyAsync(u, du, N * c->dims * sizeof(double), cudaMemcpyDeviceToHost, c->stream)))
+            return cuda_fail(c, e, "read moments");
+        c->d2h_bytes += (long long)N * (1 + c->dims) * sizeof(double);
+    }
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "moments");
+    return DVM_OK;
+}
+
+dvm_status dvm_moments(dvm_ctx* c, double* rho, double* u, int on_device) {
+    return dvm_moments_at(c, 0, rho, u, on_device);
+}
+
+dvm_status dvm_wall_density_at(dvm_ctx* c, int prob, double* rhos) {
+    if (!c || prob < 0 || prob >= c->nprob || !rhos) return DVM_EINVAL;
+    const size_t N = c->hp[prob].N;
+    cudaError_t e;
+    if (c->prec == DVM_FP32) e = launch_wall2d<float>((const Prob2D<float>*)c->probs_dev + prob, c->scratch_dev, c->stream);
+    else e = launch_wall2d<double>((const Prob2D<double>*)c->probs_dev + prob, c->scratch_dev, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "wall kernel");
+    if ((e = cudaMemcpyAsync(rhos, c->scratch_dev, N * 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream)) ||
+        (e = cudaStreamSynchronize(c->stream)))
+        return cuda_fail(c, e, "read wall densities");
+    c->d2h_bytes += (long long)N * 4 * sizeof(double);
+    return DVM_OK;
+}
+
+dvm_status dvm_permeability_at(dvm_ctx* c, int prob, double* k, double* gp) {
+    if (!c || prob < 0 || prob >= c->nprob) return DVM_EINVAL;
+    dvm_status s = collect(c);
+    if (s != DVM_OK) return s;
+    if (k) *k = c->kval_host[3 * prob];
+    if (gp) *gp = c->kval_host[3 * prob + 1];
+    return DVM_OK;
+}
+
+dvm_status dvm_permeability(dvm_ctx* c, double* k, double* gp) { return dvm_permeability_at(c, 0, k, gp); }
+
+dvm_status dvm_info(const dvm_ctx* c, int64_t* iterations, int* nprob) {
+    if (!c) return DVM_EINVAL;
+    if (iterations) *iterations = c->iters;
+    if (nprob) *nprob = c->nprob;
+    return DVM_OK;
+}
+
+const char* dvm_last_error(const dvm_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+dvm_status dvm_profile_enable(dvm_ctx* c, int on) {
+    if (!c) return DVM_EINVAL;
+    c->profile = on != 0;
+    return DVM_OK;
+}
+
+dvm_status dvm_profile_read(dvm_ctx* c, double* sweep_ms, int64_t* sweep_n, double* fin_ms, int64_t* fin_n) {
+    if (!c) return DVM_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "profile sync");
+    double ts = 0.0, tf = 0.0;
+    int64_t ns = 0, nf = 0;
+    for (size_t i = 0; i + 2 < c->ev_marks.size(); i += 3) {
+        float a = 0.f, b = 0.f;
+        if ((e = cudaEventElapsedTime(&a, c->ev_marks[i], c->ev_marks[i + 1])) != cudaSuccess ||
+            (e = cudaEventElapsedTime(&b, c->ev_marks[i + 1], c->ev_marks[i + 2])) != cudaSuccess)
+            return cuda_fail(c, e, "event timing");
+        ts += a;
+        tf += b;
+        ++ns;
+        ++nf;
+    }
+    c->ev_marks.clear();
+    if (sweep_ms) *sweep_ms = ts;
+    if (sweep_n) *sweep_n = ns;
+    if (fin_ms) *fin_ms = tf;
+    if (fin_n) *fin_n = nf;
+    return DVM_OK;
+}
+
+dvm_status dvm_transfer_bytes(const dvm_ctx* c, int64_t* h2d, int64_t* d2h) {
+    if (!c) return DVM_EINVAL;
+    if (h2d) *h2d = c->h2d_bytes;
+    if (d2h) *d2h = c->d2h_bytes;
+    return DVM_OK;
+}
+
+void dvm_destroy(dvm_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
+    free_all(c);
+    delete c;
+}
+
+// Test hooks (not part of the documented ABI): shorten the wait bound and withhold the progress
+// flag of one work item so that the waits of the band above it expire.
+dvm_status dvm_debug_set_wait(dvm_ctx* c, long long timeout_ns, int withhold_item) {
+    if (!c || timeout_ns <= 0) return DVM_EINVAL;
+    c->timeout_ns = timeout_ns;
+    c->withhold_item = withhold_item;
+    return DVM_OK;
+}
+
+}  // extern "C"

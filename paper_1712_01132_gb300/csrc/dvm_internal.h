@@ -1,0 +1,90 @@
+// dvm_internal.h -- structures shared by the host side of the library and its CUDA kernels.
+//
+// Terminology (all from arXiv:1712.01132):
+//   octant/quadrant q : the 2^d groups of discrete velocities with equal component signs; every
+//                       group is swept from its own upstream corner (Sec. 3.1, Fig. 1).  Bit j of
+//                       q is set when s_j = sign(v_j) < 0.
+//   lane               : one discrete velocity of a group; a group is padded to a multiple of 32
+//                       lanes with zero-weight velocities.
+//   band               : a block of consecutive x2 rows (2D) swept by one CTA along x1 in tiles of
+//                       T1 columns; band b+1 follows band b one tile behind (wavefront over
+//                       tiles, dependency-identical to the raster scan of the paper).
+//   source form        : the kernels carry h' = h + x1 (the unit pressure jump of Eq. 7 becomes a
+//                       plain periodic wrap plus a source term v1), which keeps the unknowns free of
+//                       the O(1) ramp; outputs are converted back to the paper's variables.
+#pragma once
+
+#include <cstdint>
+
+namespace dvm {
+
+constexpr int kLaneConsts = 12;     // per-lane constants, see LaneConst
+constexpr int kRecWords = 12;       // per-point record words (three 4-vectors)
+constexpr long long kDefaultTimeoutNs = 2000000000LL;   // 2 s bound on every spin wait
+
+// Per-lane constants of velocity lane l of group q of a problem, in the working precision:
+//   [0] v1  [1] v2  [2] v3 (3D)  [3] |v1|/dx  [4] |v2|/dx  [5] |v3|/dx (3D)
+//   [6] W   [7] W v1  [8] W v2  [9] W v3 (3D)  [10..] reciprocal denominators R[rsel], see below.
+// 2D uses the layout of LaneConst2D.
+// 2D layout: v1, v2, a1, a2, W, Wv1, Wv2, R0, R1, R2, R3, pad.
+//   R[rsel] = 1 / (nu + C0(axis1) a1 + C0(axis2) a2) with C0 = 1 (first order) when bit j of rsel is
+//   set and C0 = 1.5 (order 2) or 1 (order 1) otherwise.
+
+template <typename T>
+struct Prob2D {
+    int n1, n2, N;
+    int nbands;          // bands per quadrant
+    int rows;            // rows per band (last band may be shorter)
+    int lateral;         // 0 specular, 1 periodic
+    int order;           // 2 or 1
+    double kn, nu, dx;
+    double dwall[2];     // Eq. 6 denominators per axis
+    const uint16_t* code;   // [N] stencil cases, see kernels
+    T* src;              // [N][4]  (nu rho', 2 nu u1 + 1, 2 nu u2, 0)
+    T* E;                // [N][4]  wall terms per (axis j, upstream side u): index 2 j + u
+    T* P;                // [4][3][N] moment partials per quadrant (rho', u1, u2)
+    T* gx1;              // [2][4][n2][2][NL] x1 ghost layers (parity, quadrant, row, layer, lane)
+    T* glat;             // [2][4][n1][2][NL] x2 ghost layers (parity, quadrant, col, layer, lane)
+    T* edge;             // [4][nbands-1][2][n1][NL] band-to-band edges
+    int* prog;           // [4][nbands] tiles completed per band in this iteration
+    const T* lanec;      // [4][NL][kLaneConsts]
+    double* kpart;       // [nfinblocks] partial sums of u1 (FP64)
+    double* kval;        // [3]: k, G_p, sum u1 of the last finalize
+    int fin_block0;      // first finalize block of this problem
+    int fin_nblocks;     // finalize blocks of this problem
+    unsigned int* fin_counter;   // blocks of this problem done (last-block reduction)
+};
+
+struct SweepItem { int prob, quad, band, pad; };
+
+template <typename T>
+struct SweepArgs2D {
+    const Prob2D<T>* prob;      // device array [nprob]
+    const SweepItem* items;     // device array [nitems], ordered by band index
+    int nitems;
+    int NL;                     // lanes per quadrant (multiple of 32)
+    int max_rows;               // rows per band used to size shared memory
+    int parity;                 // ghost buffers: read [parity], write [parity ^ 1]
+    int* ticket;                // work counter (zeroed before every launch)
+    int* status;                // device error word (0 = ok)
+    long long timeout_ns;
+    int withhold_item;          // test hook: this item never publishes progress (-1 = none)
+};
+
+template <typename T>
+struct FinArgs2D {
+    const Prob2D<T>* prob;
+    const int* blk_prob;        // [nblocks] problem of each block
+    const int* blk_start;       // [nblocks] first point of each block
+    int* status;
+};
+
+// Stencil-case encoding of code[x] (2D uses axes 0,1; 3D axes 0..2):
+//   bits 2*(2 j + u) .. +1 : case for axis j with upstream side u (u = 0: upstream is -e_j, i.e.
+//   the sweep sign s_j > 0; u = 1: upstream is +e_j):
+//     0 both upstream points fluid, 1 only the second one solid (wall value there),
+//     2 the first upstream point solid (first-order stencil, wall value there)
+//   bit 15 : solid voxel
+constexpr uint16_t kSolidBit = 0x8000u;
+
+}  // namespace dvm

@@ -1,0 +1,596 @@
+// kernels2d.cu -- sm_103a kernels of one source iteration (arXiv:1712.01132, Sec. 3.1) in 2D.
+//
+// sweep2d   : step (i) for every quadrant of discrete velocities, with the moment quadrature of
+//             step (iii) fused in.  Persistent CTAs take (problem, quadrant, band) items from a
+//             ticket counter in band order; a CTA sweeps its band of rows along x1 tile by tile
+//             (forward substitution in the upwind order of Eq. 9-10), one discrete velocity per
+//             lane, and publishes per-tile progress so the band above can follow one tile behind.
+//             Every value a point reads is final when it is read, so the result is the same as
+//             the paper's raster scan.  Boundary data (wall values, ghost layers) and moments are
+//             those of the previous iteration (step ii), exactly as in the paper.
+// finalize2d: step (iii) completion: sums the per-quadrant moment partials, forms the wall
+//             densities of Eq. 6 in FP64, the source terms and wall terms of the next sweep, and
+//             the FP64 sum of u1 for the permeability of Eq. 11-12.
+// init2d    : the zero-perturbation start in the kernels' source-form variables.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "dvm_internal.h"
+
+namespace dvm {
+
+// ---------------------------------------------------------------- helpers
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int ld_volatile(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
+
+// Bounded wait for *flag >= target.  On expiry the kernel's status word is set to
+// DVM_ETIMEOUT (-4) and false is returned; a status already set by another CTA also ends it.
+__device__ bool wait_geq(const int* flag, int target, int* status, long long timeout_ns) {
+    if (ld_acquire_gpu(flag) >= target) return true;
+    const unsigned long long t0 = global_ns();
+    unsigned ns = 32;
+    for (;;) {
+        if (ld_acquire_gpu(flag) >= target) return true;
+        if (ld_volatile(status) != 0) return false;
+        if ((long long)(global_ns() - t0) > timeout_ns) {
+            atomicCAS(status, 0, -4);
+            return false;
+        }
+        __nanosleep(ns);
+        ns = ns < 1024 ? ns * 2 : 1024;
+    }
+}
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> {
+    using type = float4;
+    static __device__ __forceinline__ float4 make(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+};
+struct alignas(32) dbl4 { double x, y, z, w; };
+template <> struct Vec4<double> {
+    using type = dbl4;
+    static __device__ __forceinline__ dbl4 make(double a, double b, double c, double d) { return dbl4{a, b, c, d}; }
+};
+
+__device__ __forceinline__ float bits_as(float, int v) { return __int_as_float(v); }
+__device__ __forceinline__ double bits_as(double, int v) { return __longlong_as_double((long long)v); }
+__device__ __forceinline__ int as_bits(float v) { return __float_as_int(v); }
+__device__ __forceinline__ int as_bits(double v) { return (int)__double_as_longlong(v); }
+
+// Sum over the 32 lanes of v[p] for NP (8 or 16) points at once.  Lane l ends up holding the
+// sum of point p = l >> (5 - log2 NP).  The combination tree (lane offsets 16, 8, 4, 2, 1) is the
+// same for every point, so the result does not depend on the point's slot.
+template <typename T, int NP>
+__device__ __forceinline__ T reduce_scatter(T (&v)[NP], int lane) {
+    constexpr int LOG = (NP == 16) ? 4 : (NP == 8 ? 3 : (NP == 4 ? 2 : 1));
+#pragma unroll
+    for (int s = 0; s < LOG; ++s) {
+        const int off = 16 >> s;
+        const int cnt = NP >> s;
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int k = 0; k < cnt / 2; ++k) {
+            const T send = up ? v[k] : v[k + cnt / 2];
+            const T keep = up ? v[k + cnt / 2] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+    T r = v[0];
+#pragma unroll
+    for (int off = 16 >> LOG; off >= 1; off >>= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
+    return r;
+}
+
+// ---------------------------------------------------------------- sweep
+
+// Per-lane state while a warp walks along one row of a tile.
+template <typename T>
+struct LaneK {
+    T v1, v2, a1, a2, W, Wv1, Wv2, R0, R1, R2, R3;
+};
+
+// Processes CH consecutive points (columns i0..i0+CH-1 of the tile) of one row.
+// rec: records of this row; rb1/rb2: the two rows below (updated in place); hp1/hp2: x1 upstream.
+template <typename T, int T1, int CH, bool FULL>
+__device__ __forceinline__ void row_chunk(const T* __restrict__ rec, int i0, int width, const LaneK<T>& L,
+                                          T (&rb1)[T1], T (&rb2)[T1], T& hp1, T& hp2, T (&m0)[CH],
+                                          T (&m1)[CH], T (&m2)[CH]) {
+    using V = typename Vec4<T>::type;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        const int i = i0 + c;
+        if (FULL || i < width) {
+            const V* R = reinterpret_cast<const V*>(rec + i * kRecWords);
+            const V A = R[0];
+            const V B = R[1];
+            const V C = R[2];
+            // numerator of Eq. 10 solved for h(x): nu (rho' + 2 u.v) + v1 plus the upwind terms
+            const T S = fma(A.z, L.v2, fma(A.y, L.v1, A.x));
+            const T t1 = fma(B.x, hp1, fma(B.y, hp2, A.w));
+            const T t2 = fma(B.z, rb1[i], fma(B.w, rb2[i], C.x));
+            const T num = fma(L.a2, t2, fma(L.a1, t1, S));
+            const int rs = as_bits(C.y);
+            const T Rv = (rs & 2) ? ((rs & 1) ? L.R3 : L.R2) : ((rs & 1) ? L.R1 : L.R0);
+            const T h = num * Rv;
+            hp2 = hp1;
+            hp1 = h;
+            rb2[i] = rb1[i];
+            rb1[i] = h;
+            m0[c] = L.W * h;
+            m1[c] = L.Wv1 * h;
+            m2[c] = L.Wv2 * h;
+        } else {
+            m0[c] = T(0);
+            m1[c] = T(0);
+            m2[c] = T(0);
+        }
+    }
+}
+
+template <typename T, int T1, bool FULL>
+__device__ __forceinline__ void sweep_tile_rows(const T* __restrict__ rec, T* __restrict__ part,
+                                                T* __restrict__ carry, int nrows, int width, int RB,
+                                                int warp, int lane, const LaneK<T>& L, T (&rb1)[T1],
+                                                T (&rb2)[T1]) {
+    constexpr int CH = 8;                       // points reduced together
+    for (int r = 0; r < nrows; ++r) {
+        T* cr = carry + ((size_t)(warp * RB + r) * 2) * 32 + lane;
+        T hp1 = cr[0];
+        T hp2 = cr[32];
+        const T* rrow = rec + (size_t)r * T1 * kRecWords;
+        T* prow = part + ((size_t)(warp * RB + r) * T1) * 3;
+#pragma unroll
+        for (int i0 = 0; i0 < T1; i0 += CH) {
+            T m0[CH], m1[CH], m2[CH];
+            row_chunk<T, T1, CH, FULL>(rrow, i0, width, L, rb1, rb2, hp1, hp2, m0, m1, m2);
+            const T s0 = reduce_scatter<T, CH>(m0, lane);
+            const T s1 = reduce_scatter<T, CH>(m1, lane);
+            const T s2 = reduce_scatter<T, CH>(m2, lane);
+            const int p = lane >> 2;
+            if ((lane & 3) == 0 && (FULL || i0 + p < width)) {
+                T* d = prow + (i0 + p) * 3;
+                d[0] = s0;
+                d[1] = s1;
+                d[2] = s2;
+            }
+        }
+        cr[0] = hp1;
+        cr[32] = hp2;
+    }
+}
+
+template <typename T, int T1>
+__global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs2D<T> a) {
+    using V = typename Vec4<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item;
+    __shared__ int s_abort;
+    const int NW = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int RB = a.max_rows;
+    T* rec = reinterpret_cast<T*>(smem_raw);                 // [RB][T1][kRecWords]
+    T* part = rec + (size_t)RB * T1 * kRecWords;             // [NW][RB][T1][3]
+    T* carry = part + (size_t)NW * RB * T1 * 3;              // [NW][RB][2][32]
+    const int wl = warp * 32 + lane;
+    const size_t NL = (size_t)a.NL;
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_item = ld_volatile(a.status) ? a.nitems : atomicAdd(a.ticket, 1);
+            s_abort = 0;
+        }
+        __syncthreads();
+        const int it = s_item;
+        if (it >= a.nitems) return;
+        const SweepItem item = a.items[it];
+        const Prob2D<T>* __restrict__ P = a.prob + item.prob;
+        const int q = item.quad;
+        const int band = item.band;
+        const int n1 = P->n1, n2 = P->n2, nb = P->nbands;
+        const int N = P->N;
+        const int s1neg = q & 1;
+        const int s2neg = (q >> 1) & 1;
+        const int row0 = band * P->rows;
+        const int nrows = min(P->rows, n2 - row0);
+        const T K1o = P->order == 2 ? T(2) : T(1);
+        const T K2o = P->order == 2 ? T(-0.5) : T(0);
+        LaneK<T> L;
+        {
+            const T* lc = P->lanec + ((size_t)q * NL + wl) * kLaneConsts;
+            L.v1 = lc[0]; L.v2 = lc[1]; L.a1 = lc[2]; L.a2 = lc[3];
+            L.W = lc[4]; L.Wv1 = lc[5]; L.Wv2 = lc[6];
+            L.R0 = lc[7]; L.R1 = lc[8]; L.R2 = lc[9]; L.R3 = lc[10];
+        }
+        const int par = a.parity;
+        // x1 upstream of the first tile: ghost layers of the previous iteration (Eq. 7, source form)
+        {
+            const T* g = P->gx1 + (((size_t)par * 4 + q) * n2) * 2 * NL;
+            for (int r = 0; r < nrows; ++r) {
+                T* cr = carry + ((size_t)(warp * RB + r) * 2) * 32 + lane;
+                cr[0] = g[((size_t)(row0 + r) * 2 + 0) * NL + wl];
+                cr[32] = g[((size_t)(row0 + r) * 2 + 1) * NL + wl];
+            }
+        }
+        const int ntiles = (n1 + T1 - 1) / T1;
+        for (int t = 0; t < ntiles; ++t) {
+            const int c0 = t * T1;
+            const int width = min(T1, n1 - c0);
+            if (threadIdx.x == 0 && band > 0) {
+                if (!wait_geq(P->prog + q * nb + band - 1, t + 1, a.status, a.timeout_ns)) s_abort = 1;
+            }
+            // per-point records of this quadrant: source, stencil coefficients, wall terms
+            for (int idx = threadIdx.x; idx < nrows * T1; idx += blockDim.x) {
+                const int r = idx / T1;
+                const int i = idx - r * T1;
+                V r0 = Vec4<T>::make(0, 0, 0, 0), r1 = r0, r2 = r0;
+                if (i < width) {
+                    const int ic = c0 + i;
+                    const int x = s1neg ? n1 - 1 - ic : ic;
+                    const int yo = row0 + r;
+                    const int y = s2neg ? n2 - 1 - yo : yo;
+                    const int id = y * n1 + x;
+                    const uint16_t code = P->code[id];
+                    if (!(code & kSolidBit)) {
+                        const V s = reinterpret_cast<const V*>(P->src)[id];
+                        const V e = reinterpret_cast<const V*>(P->E)[id];
+                        const int ca = (code >> (2 * (0 + s1neg))) & 3;
+                        const int cb = (code >> (2 * (2 + s2neg))) & 3;
+                        r0 = Vec4<T>::make(s.x, s.y, s.z, s1neg ? e.y : e.x);
+                        r1 = Vec4<T>::make(ca == 2 ? T(0) : K1o, ca == 0 ? K2o : T(0),
+                                           cb == 2 ? T(0) : K1o, cb == 0 ? K2o : T(0));
+                        r2 = Vec4<T>::make(s2neg ? e.w : e.z, bits_as(T(0), (ca == 2) | ((cb == 2) << 1)),
+                                           T(0), T(0));
+                    }
+                }
+                V* R = reinterpret_cast<V*>(rec + (size_t)idx * kRecWords);
+                R[0] = r0;
+                R[1] = r1;
+                R[2] = r2;
+            }
+            __syncthreads();
+            if (s_abort) return;
+            // the two rows below this band: the previous band's top edge or the x2 ghost layers
+            T rb1[T1], rb2[T1];
+            {
+                const T* eb = (band == 0)
+                    ? P->glat + (((size_t)par * 4 + q) * n1) * 2 * NL
+                    : P->edge + ((size_t)(q * (nb - 1) + band - 1) * n1) * 2 * NL;
+#pragma unroll
+                for (int i = 0; i < T1; ++i) {
+                    if (i < width) {
+                        rb1[i] = __ldcg(eb + ((size_t)(c0 + i) * 2 + 0) * NL + wl);
+                        rb2[i] = __ldcg(eb + ((size_t)(c0 + i) * 2 + 1) * NL + wl);
+                    } else {
+                        rb1[i] = T(0);
+                        rb2[i] = T(0);
+                    }
+                }
+            }
+            if (width == T1)
+                sweep_tile_rows<T, T1, true>(rec, part, carry, nrows, width, RB, warp, lane, L, rb1, rb2);
+            else
+                sweep_tile_rows<T, T1, false>(rec, part, carry, nrows, width, RB, warp, lane, L, rb1, rb2);
+            // top edge for the band above, or the x2 ghost layers of the next iteration (Eq. 8 /
+            // periodic: the reflected quadrant reads the same lane)
+            {
+                T* et;
+                if (band < nb - 1) {
+                    et = P->edge + ((size_t)(q * (nb - 1) + band) * n1) * 2 * NL;
+                } else {
+                    const int qr = (P->lateral == 1) ? q : (q ^ 2);
+                    et = P->glat + (((size_t)(par ^ 1) * 4 + qr) * n1) * 2 * NL;
+                }
+#pragma unroll
+                for (int i = 0; i < T1; ++i) {
+                    if (i < width) {
+                        et[((size_t)(c0 + i) * 2 + 0) * NL + wl] = rb1[i];
+                        et[((size_t)(c0 + i) * 2 + 1) * NL + wl] = rb2[i];
+                    }
+                }
+            }
+            if (t == ntiles - 1) {
+                // x1 ghost layers of the next iteration (periodic in x1, same quadrant)
+                T* g = P->gx1 + (((size_t)(par ^ 1) * 4 + q) * n2) * 2 * NL;
+                for (int r = 0; r < nrows; ++r) {
+                    const T* cr = carry + ((size_t)(warp * RB + r) * 2) * 32 + lane;
+                    g[((size_t)(row0 + r) * 2 + 0) * NL + wl] = cr[0];
+                    g[((size_t)(row0 + r) * 2 + 1) * NL + wl] = cr[32];
+                }
+            }
+            __syncthreads();
+            // moment partials of this quadrant: sum of the warps' lane sums, in warp order
+            for (int idx = threadIdx.x; idx < nrows * width * 3; idx += blockDim.x) {
+                const int m = idx % 3;
+                const int pi = idx / 3;
+                const int r = pi / width;
+                const int i = pi - r * width;
+                T s = T(0);
+                for (int w = 0; w < NW; ++w) s += part[((size_t)(w * RB + r) * T1 + i) * 3 + m];
+                const int ic = c0 + i;
+                const int x = s1neg ? n1 - 1 - ic : ic;
+                const int yo = row0 + r;
+                const int y = s2neg ? n2 - 1 - yo : yo;
+                P->P[((size_t)q * 3 + m) * N + (size_t)y * n1 + x] = s;
+            }
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0 && it != a.withhold_item) st_release_gpu(P->prog + q * nb + band, t + 1);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- finalize
+
+// rho'_s of face (y, axis j, side sigma) (Eq. 6) in FP64 from the quadrant partials of u_j at y:
+// sum_{sigma v_j > 0} W |v_j| h / D = sigma * sum_{quadrants with sign(v_j) = sigma} P_uj / D.
+template <typename T>
+__device__ __forceinline__ double wall_density(const Prob2D<T>* P, int y, int j, int sigma) {
+    double num = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int neg = (q >> j) & 1;
+        if (neg == (sigma < 0 ? 1 : 0)) num += (double)P->P[((size_t)q * 3 + 1 + j) * P->N + y];
+    }
+    return sigma * num / P->dwall[j];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) finalize2d_kernel(const FinArgs2D<T> a) {
+    using V = typename Vec4<T>::type;
+    __shared__ double s_red[8];
+    __shared__ int s_last;
+    const int b = a.blk_prob[blockIdx.x];
+    const Prob2D<T>* __restrict__ P = a.prob + b;
+    const int id = a.blk_start[blockIdx.x] + threadIdx.x;
+    double u1d = 0.0;
+    if (id < P->N) {
+        const uint16_t code = P->code[id];
+        V s = Vec4<T>::make(0, 0, 0, 0), e = s;
+        if (!(code & kSolidBit)) {
+            const size_t N = P->N;
+            T rho = T(0), u1 = T(0), u2 = T(0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                rho += P->P[((size_t)q * 3 + 0) * N + id];
+                u1 += P->P[((size_t)q * 3 + 1) * N + id];
+                u2 += P->P[((size_t)q * 3 + 2) * N + id];
+            }
+            const T nu = (T)P->nu;
+            s = Vec4<T>::make(nu * rho, T(2) * nu * u1 + T(1), T(2) * nu * u2, T(0));
+            u1d = (double)u1;
+            const int n1 = P->n1, n2 = P->n2;
+            const int x = id % n1, y = id / n1;
+            T ev[4];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int c = (code >> (2 * (2 * j + u))) & 3;
+                    const int sigma = u ? 1 : -1;
+                    double val = 0.0;
+                    if (c == 2) {
+                        // first-order stencil: wall value of face (x, j, sigma), shifted by the
+                        // source-form offset sigma dx on x1 faces
+                        val = wall_density(P, id, j, sigma) + (j == 0 ? sigma * P->dx : 0.0);
+                    } else if (c == 1) {
+                        // second-order stencil with the wall two points upstream: face attached to
+                        // the upstream neighbour (mirrored at a specular outer face)
+                        int nid, sg = sigma;
+                        if (j == 0) {
+                            nid = y * n1 + (x + sigma + n1) % n1;
+                        } else {
+                            int yy = y + sigma;
+                            if (yy < 0 || yy >= n2) {
+                                if (P->lateral == 1) yy = (yy + n2) % n2;
+                                else { yy = (yy < 0) ? -1 - yy : 2 * n2 - 1 - yy; sg = -sigma; }
+                            }
+                            nid = yy * n1 + x;
+                        }
+                        val = -0.5 * (wall_density(P, nid, j, sg) + (j == 0 ? sigma * P->dx : 0.0));
+                    }
+                    ev[2 * j + u] = (T)val;
+                }
+            }
+            e = Vec4<T>::make(ev[0], ev[1], ev[2], ev[3]);
+        }
+        reinterpret_cast<V*>(P->src)[id] = s;
+        reinterpret_cast<V*>(P->E)[id] = e;
+    }
+    // FP64 block sum of u1 (fixed tree), then the last block of the problem adds the block sums in
+    // block order: the permeability is independent of scheduling.
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) u1d += __shfl_xor_sync(0xffffffffu, u1d, off);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = u1d;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_red[w];
+        P->kpart[blockIdx.x - P->fin_block0] = tot;
+        __threadfence();
+        const unsigned prev = atomicAdd(P->fin_counter, 1u);
+        s_last = (prev == (unsigned)P->fin_nblocks - 1u);
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        double tot = 0.0;
+        for (int k = 0; k < P->fin_nblocks; ++k) tot += __ldcg(P->kpart + k);
+        const double gp = tot / (double)P->N;
+        P->kval[0] = 2.0 / sqrt(3.14159265358979323846) * P->kn * gp;
+        P->kval[1] = gp;
+        P->kval[2] = tot;
+        *P->fin_counter = 0u;
+    }
+}
+
+// ---------------------------------------------------------------- init and readout
+
+// Zero-perturbation start h = 0 in the paper's variables, i.e. h' = x1 in the kernels' variables:
+// moment partials x1 * sum_{k in q} W_k (1, v1, v2) and ghost layers carrying x1 of their source
+// points.  A finalize pass afterwards derives the source and wall terms.
+template <typename T>
+__global__ void init2d_kernel(const Prob2D<T>* prob, int NL, const double* qw /*[4][3]*/) {
+    const Prob2D<T>* P = prob;
+    const int n1 = P->n1, n2 = P->n2, N = P->N;
+    const size_t nl = NL;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (size_t idx = t0; idx < (size_t)4 * 3 * N; idx += stride) {
+        const int id = idx % N;
+        const int qm = idx / N;
+        const double x1 = (id % n1) * P->dx;
+        P->P[idx] = (P->code[id] & kSolidBit) ? T(0) : (T)(x1 * qw[qm]);
+    }
+    for (size_t idx = t0; idx < (size_t)2 * 4 * n2 * 2 * nl; idx += stride) {
+        const int layer = (idx / nl) % 2;
+        const int q = (idx / (nl * 2 * n2)) % 4;
+        const int ico = n1 - 1 - layer;                          // oriented source column
+        const int col = (q & 1) ? n1 - 1 - ico : ico;
+        P->gx1[idx] = (T)(col * P->dx);
+    }
+    for (size_t idx = t0; idx < (size_t)2 * 4 * n1 * 2 * nl; idx += stride) {
+        const int ic = (idx / (nl * 2)) % n1;
+        const int q = (idx / (nl * 2 * n1)) % 4;
+        const int col = (q & 1) ? n1 - 1 - ic : ic;
+        P->glat[idx] = (T)(col * P->dx);
+    }
+}
+
+// rho (paper variables, ramp restored) and u of one problem into double buffers; solid = 0.
+template <typename T>
+__global__ void moments2d_kernel(const Prob2D<T>* prob, double* rho, double* u) {
+    const Prob2D<T>* P = prob;
+    const int N = P->N;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        if (P->code[id] & kSolidBit) {
+            rho[id] = 0.0;
+            u[id] = 0.0;
+            u[N + id] = 0.0;
+            continue;
+        }
+        T r = T(0), u1 = T(0), u2 = T(0);
+        for (int q = 0; q < 4; ++q) {
+            r += P->P[((size_t)q * 3 + 0) * N + id];
+            u1 += P->P[((size_t)q * 3 + 1) * N + id];
+            u2 += P->P[((size_t)q * 3 + 2) * N + id];
+        }
+        rho[id] = (double)r - (id % P->n1) * P->dx;
+        u[id] = (double)u1;
+        u[N + id] = (double)u2;
+    }
+}
+
+// Wall densities [2][2][N] (axis, side) in the paper's variables; 0 where there is no face.
+template <typename T>
+__global__ void wall2d_kernel(const Prob2D<T>* prob, double* out) {
+    const Prob2D<T>* P = prob;
+    const int N = P->N;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        const uint16_t code = P->code[id];
+        for (int j = 0; j < 2; ++j)
+            for (int u = 0; u < 2; ++u) {
+                double v = 0.0;
+                if (!(code & kSolidBit) && ((code >> (2 * (2 * j + u))) & 3) == 2)
+                    v = wall_density(P, id, j, u ? 1 : -1) - (id % P->n1) * P->dx;
+                out[(size_t)(2 * j + u) * N + id] = v;
+            }
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+
+template <typename T>
+size_t sweep2d_smem(int T1, int NW, int max_rows) {
+    return sizeof(T) * ((size_t)max_rows * T1 * kRecWords + (size_t)NW * max_rows * T1 * 3 +
+                        (size_t)NW * max_rows * 2 * 32);
+}
+
+template <typename T, int T1>
+static cudaError_t launch_sweep_t(const SweepArgs2D<T>& a, int grid, int NW, cudaStream_t st) {
+    const size_t smem = sweep2d_smem<T>(T1, NW, a.max_rows);
+    cudaError_t e = cudaFuncSetAttribute(sweep2d_kernel<T, T1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    sweep2d_kernel<T, T1><<<grid, NW * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_sweep2d(const SweepArgs2D<T>& a, int T1, int grid, int NW, cudaStream_t st) {
+    if (T1 == 8) return launch_sweep_t<T, 8>(a, grid, NW, st);
+    if (T1 == 16) return launch_sweep_t<T, 16>(a, grid, NW, st);
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t sweep2d_occupancy(int T1, int NW, int max_rows, int* blocks_per_sm) {
+    const size_t smem = sweep2d_smem<T>(T1, NW, max_rows);
+    cudaError_t e;
+    if (T1 == 8) {
+        e = cudaFuncSetAttribute(sweep2d_kernel<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep2d_kernel<T, 8>, NW * 32, smem);
+    }
+    if (T1 == 16) {
+        e = cudaFuncSetAttribute(sweep2d_kernel<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep2d_kernel<T, 16>, NW * 32, smem);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_finalize2d(const FinArgs2D<T>& a, int nblocks, cudaStream_t st) {
+    finalize2d_kernel<T><<<nblocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_init2d(const Prob2D<T>* prob_dev, int NL, const double* qw_dev, cudaStream_t st) {
+    init2d_kernel<T><<<304, 256, 0, st>>>(prob_dev, NL, qw_dev);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_moments2d(const Prob2D<T>* prob_dev, double* rho, double* u, cudaStream_t st) {
+    moments2d_kernel<T><<<304, 256, 0, st>>>(prob_dev, rho, u);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_wall2d(const Prob2D<T>* prob_dev, double* out, cudaStream_t st) {
+    wall2d_kernel<T><<<304, 256, 0, st>>>(prob_dev, out);
+    return cudaGetLastError();
+}
+
+#define DVM_INSTANTIATE(T)                                                                      \
+    template size_t sweep2d_smem<T>(int, int, int);                                            \
+    template cudaError_t launch_sweep2d<T>(const SweepArgs2D<T>&, int, int, int, cudaStream_t);  \
+    template cudaError_t sweep2d_occupancy<T>(int, int, int, int*);                             \
+    template cudaError_t launch_finalize2d<T>(const FinArgs2D<T>&, int, cudaStream_t);          \
+    template cudaError_t launch_init2d<T>(const Prob2D<T>*, int, const double*, cudaStream_t);  \
+    template cudaError_t launch_moments2d<T>(const Prob2D<T>*, double*, double*, cudaStream_t); \
+    template cudaError_t launch_wall2d<T>(const Prob2D<T>*, double*, cudaStream_t);
+
+DVM_INSTANTIATE(float)
+DVM_INSTANTIATE(double)
+
+}  // namespace dvm

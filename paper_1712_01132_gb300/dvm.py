@@ -1,0 +1,299 @@
+"""Thin Python binding of the C ABI in include/dvm.h (argument marshalling only).
+
+Every computation runs in the CUDA library ``_lib/libdvm_gb300.so``; there is no fallback: if the
+library is missing or cannot be loaded, importing the functions raises.  PyTorch provides device
+memory (through the allocator callback of ``dvm_options``) and the CUDA stream.
+"""
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+DVM_OK, DVM_NOT_CONVERGED, DVM_EINVAL, DVM_ENOMEM, DVM_ECUDA, DVM_ETIMEOUT, DVM_ENUMERIC = 0, 1, -1, -2, -3, -4, -5
+DVM_FP64, DVM_FP32 = 0, 1
+DVM_LATERAL_SPECULAR, DVM_LATERAL_PERIODIC = 0, 1
+
+_STATUS_NAMES = {0: "DVM_OK", 1: "DVM_NOT_CONVERGED", -1: "DVM_EINVAL", -2: "DVM_ENOMEM", -3: "DVM_ECUDA",
+                 -4: "DVM_ETIMEOUT", -5: "DVM_ENUMERIC"}
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class dvm_geometry(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int), ("n", ctypes.c_int64 * 3), ("solid", ctypes.c_void_p)]
+
+
+class dvm_velocity_grid(ctypes.Structure):
+    _fields_ = [("nv", ctypes.c_int), ("v", ctypes.c_void_p), ("w", ctypes.c_void_p)]
+
+
+class dvm_options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("stencil_order", ctypes.c_int),
+        ("lateral_bc", ctypes.c_int),
+        ("check_interval", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+        ("tile_x1", ctypes.c_int),
+        ("band_rows", ctypes.c_int),
+        ("alloc", ALLOC_FN),
+        ("free", FREE_FN),
+        ("alloc_user", ctypes.c_void_p),
+    ]
+
+
+# (name, restype, argtypes) of every entry point declared in include/dvm.h
+_P = ctypes.c_void_p
+_SIGNATURES = [
+    ("dvm_default_options", None, [ctypes.POINTER(dvm_options)]),
+    ("dvm_gh_velocity_grid", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P]),
+    ("dvm_create", ctypes.c_int, [ctypes.POINTER(dvm_geometry), ctypes.c_double, ctypes.POINTER(dvm_velocity_grid),
+                                  ctypes.POINTER(dvm_options), ctypes.POINTER(_P)]),
+    ("dvm_create_batch", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(dvm_geometry), _P,
+                                        ctypes.POINTER(dvm_velocity_grid), ctypes.POINTER(dvm_options),
+                                        ctypes.POINTER(_P)]),
+    ("dvm_iterate", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_double)]),
+    ("dvm_step", ctypes.c_int, [_P, ctypes.c_int]),
+    ("dvm_sync", ctypes.c_int, [_P]),
+    ("dvm_moments", ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
+    ("dvm_moments_at", ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int]),
+    ("dvm_permeability", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    ("dvm_permeability_at", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_double)]),
+    ("dvm_wall_density_at", ctypes.c_int, [_P, ctypes.c_int, _P]),
+    ("dvm_info", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]),
+    ("dvm_last_error", ctypes.c_char_p, [_P]),
+    ("dvm_destroy", None, [_P]),
+    ("dvm_debug_set_wait", ctypes.c_int, [_P, ctypes.c_longlong, ctypes.c_int]),
+    ("dvm_profile_enable", ctypes.c_int, [_P, ctypes.c_int]),
+    ("dvm_profile_read", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
+    ("dvm_transfer_bytes", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load (building first if needed) the CUDA library; raises if it is unavailable."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path) or _build._stale():
+                if not build_if_missing:
+                    raise RuntimeError("CUDA library %s is missing; run the build first" % path)
+                _build.build()
+            lib = ctypes.CDLL(path)
+            for name, res, args in _SIGNATURES:
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+class DvmError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (_STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+def _check(status, ctx=None):
+    if status < 0:
+        msg = load().dvm_last_error(ctx)
+        raise DvmError(status, msg.decode() if msg else "")
+    return status
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# --------------------------------------------------------------------------- same-name wrappers
+
+def dvm_default_options():
+    o = dvm_options()
+    load().dvm_default_options(ctypes.byref(o))
+    return o
+
+
+def dvm_gh_velocity_grid(dims, n_per_axis):
+    """Half-range Gauss-Hermite grid computed by the library: (v [nv, dims], w [nv])."""
+    nv = n_per_axis ** dims
+    v = np.zeros((nv, dims))
+    w = np.zeros(nv)
+    _check(load().dvm_gh_velocity_grid(int(dims), int(n_per_axis), _ptr(v), _ptr(w)))
+    return v, w
+
+
+class _TorchAllocator:
+    """Device memory from torch's caching allocator on the current device and stream."""
+
+    def __init__(self):
+        import torch
+        self._torch = torch
+        self.device = torch.cuda.current_device()
+        self.live = {}
+
+        def alloc(nbytes, user):
+            try:
+                ptr = torch.cuda.caching_allocator_alloc(int(nbytes), self.device)
+            except Exception:
+                return None
+            self.live[ptr] = nbytes
+            return ptr
+
+        def free(ptr, nbytes, user):
+            if ptr in self.live:
+                del self.live[ptr]
+                torch.cuda.caching_allocator_delete(ptr)
+
+        self.alloc_fn = ALLOC_FN(alloc)
+        self.free_fn = FREE_FN(free)
+
+
+def make_options(precision="fp64", stencil_order=2, lateral="specular", check_interval=100, stream=None,
+                 tile_x1=0, band_rows=0, torch_memory=True):
+    """dvm_options with torch's current stream (unless stream is given) and, by default, torch's
+    caching allocator for device memory.  Returns (options, keepalive)."""
+    o = dvm_default_options()
+    o.precision = {"fp64": DVM_FP64, "fp32": DVM_FP32}[precision]
+    o.stencil_order = int(stencil_order)
+    o.lateral_bc = {"specular": DVM_LATERAL_SPECULAR, "periodic": DVM_LATERAL_PERIODIC}[lateral]
+    o.check_interval = int(check_interval)
+    o.tile_x1 = int(tile_x1)
+    o.band_rows = int(band_rows)
+    keep = []
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    o.stream = ctypes.c_void_p(int(stream)) if stream else None
+    if torch_memory:
+        al = _TorchAllocator()
+        o.alloc = al.alloc_fn
+        o.free = al.free_fn
+        keep.append(al)
+    return o, keep
+
+
+class Solver:
+    """A context (one problem or a batch) of the CUDA solver.
+
+    masks: one mask or a list of masks (numpy, True = solid, shape (n2, n1), x1 fastest);
+    kn: Knudsen number(s); v, w: velocity grid (e.g. from dvm_gh_velocity_grid)."""
+
+    def __init__(self, masks, kn, v, w, **options):
+        lib = load()
+        if isinstance(masks, np.ndarray):
+            masks = [masks]
+        kns = np.atleast_1d(np.asarray(kn, dtype=np.float64))
+        if len(kns) == 1 and len(masks) > 1:
+            kns = np.repeat(kns, len(masks))
+        self.masks = [np.ascontiguousarray(np.asarray(m).astype(np.uint8)) for m in masks]
+        self.dims = self.masks[0].ndim
+        geoms = (dvm_geometry * len(self.masks))()
+        for g, m in zip(geoms, self.masks):
+            g.dims = m.ndim
+            shp = m.shape[::-1]
+            for j in range(3):
+                g.n[j] = shp[j] if j < m.ndim else 1
+            g.solid = _ptr(m)
+        self.v = np.ascontiguousarray(np.asarray(v, dtype=np.float64))
+        self.w = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+        grid = dvm_velocity_grid(len(self.w), _ptr(self.v), _ptr(self.w))
+        self._kn = np.ascontiguousarray(kns)
+        self.options, self._keep = make_options(**options)
+        ctx = ctypes.c_void_p()
+        st = lib.dvm_create_batch(len(self.masks), geoms, _ptr(self._kn), ctypes.byref(grid),
+                                  ctypes.byref(self.options), ctypes.byref(ctx))
+        _check(st, None)
+        self._ctx = ctx
+        self._lib = lib
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.dvm_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nprob(self):
+        return len(self.masks)
+
+    def iterate(self, max_iter, tol=0.0):
+        """dvm_iterate: returns (status, iterations done, Err)."""
+        it = ctypes.c_int(0)
+        err = ctypes.c_double(0.0)
+        st = self._lib.dvm_iterate(self._ctx, int(max_iter), float(tol), ctypes.byref(it), ctypes.byref(err))
+        _check(st, self._ctx)
+        return st, it.value, err.value
+
+    def step(self, n):
+        _check(self._lib.dvm_step(self._ctx, int(n)), self._ctx)
+
+    def sync(self):
+        _check(self._lib.dvm_sync(self._ctx), self._ctx)
+
+    @property
+    def iterations(self):
+        it = ctypes.c_int64(0)
+        _check(self._lib.dvm_info(self._ctx, ctypes.byref(it), None), self._ctx)
+        return it.value
+
+    def moments(self, prob=0):
+        m = self.masks[prob]
+        rho = np.zeros(m.size)
+        u = np.zeros(m.size * m.ndim)
+        _check(self._lib.dvm_moments_at(self._ctx, int(prob), _ptr(rho), _ptr(u), 0), self._ctx)
+        return rho.reshape(m.shape), u.reshape((m.ndim,) + m.shape)
+
+    def moments_device(self, prob, rho_ptr, u_ptr):
+        _check(self._lib.dvm_moments_at(self._ctx, int(prob), ctypes.c_void_p(rho_ptr), ctypes.c_void_p(u_ptr), 1),
+               self._ctx)
+
+    def permeability(self, prob=0):
+        k = ctypes.c_double(0.0)
+        gp = ctypes.c_double(0.0)
+        _check(self._lib.dvm_permeability_at(self._ctx, int(prob), ctypes.byref(k), ctypes.byref(gp)), self._ctx)
+        return k.value, gp.value
+
+    def wall(self, prob=0):
+        m = self.masks[prob]
+        out = np.zeros(m.size * m.ndim * 2)
+        _check(self._lib.dvm_wall_density_at(self._ctx, int(prob), _ptr(out)), self._ctx)
+        return out.reshape((m.ndim, 2) + m.shape)
+
+    def profile_enable(self, on=True):
+        _check(self._lib.dvm_profile_enable(self._ctx, 1 if on else 0), self._ctx)
+
+    def profile_read(self):
+        """(sweep_ms, sweep_launches, finalize_ms, finalize_launches) since the last read."""
+        a, c = ctypes.c_double(0), ctypes.c_double(0)
+        b, d = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(self._lib.dvm_profile_read(self._ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                          ctypes.byref(d)), self._ctx)
+        return a.value, b.value, c.value, d.value
+
+    def transfer_bytes(self):
+        h, d = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(self._lib.dvm_transfer_bytes(self._ctx, ctypes.byref(h), ctypes.byref(d)), self._ctx)
+        return h.value, d.value
+
+    def debug_set_wait(self, timeout_ns, withhold_item=-1):
+        _check(self._lib.dvm_debug_set_wait(self._ctx, int(timeout_ns), int(withhold_item)), self._ctx)

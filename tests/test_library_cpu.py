@@ -1,0 +1,128 @@
+"""The C-ABI library builds, loads without a GPU, exports every symbol its header declares, and
+rejects invalid input before touching the device (CPU only)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1712_01132_gb300 import dvm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(dvm_[a-z0-9_]+)\s*\(", text))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = dvm.load()
+    declared = _declared_functions()
+    assert len(declared) >= 15
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    # the binding wraps the same names
+    assert declared <= {s[0] for s in dvm._SIGNATURES}
+
+
+def test_gh_grid_matches_oracle_generator():
+    """The library's discretised-Stieltjes rule and the oracle's high-precision rule agree."""
+    import oracle
+    for dims, n in [(2, 8), (2, 16), (2, 24), (2, 32), (3, 8), (3, 16)]:
+        v, w = dvm.dvm_gh_velocity_grid(dims, n)
+        vo, wo = oracle.velocity_grid(dims, n)
+        assert np.abs(v - vo).max() < 5e-14 * np.abs(vo).max()
+        assert np.abs(w - wo).max() < 5e-14 * wo.max()
+        assert w.sum() == pytest.approx(1.0, abs=1e-13)
+
+
+@pytest.mark.parametrize("m", [20, 32, 48, 64])
+def test_gh_grid_high_order_exactness(m):
+    """Large rules (beyond the oracle's test range) still integrate monomials exactly."""
+    import math
+    v, w = dvm.dvm_gh_velocity_grid(2, 2 * m)
+    c = np.unique(np.abs(v[:, 0]))
+    a = np.array([w[(np.abs(v[:, 0]) == ci)].sum() for ci in c]) * math.sqrt(math.pi) / 2
+    for p in range(0, min(2 * m, 40)):
+        exact = math.gamma((p + 1) / 2) / 2
+        assert np.sum(a * c ** p) == pytest.approx(exact, rel=1e-11)
+
+
+def test_gh_grid_rejects_bad_arguments():
+    lib = dvm.load()
+    buf = np.zeros(64)
+    p = buf.ctypes.data_as(ctypes.c_void_p)
+    assert lib.dvm_gh_velocity_grid(4, 8, p, p) == dvm.DVM_EINVAL
+    assert lib.dvm_gh_velocity_grid(2, 7, p, p) == dvm.DVM_EINVAL
+    assert lib.dvm_gh_velocity_grid(2, 0, p, p) == dvm.DVM_EINVAL
+
+
+def _create(mask, kn, v, w, **kw):
+    lib = dvm.load()
+    m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8))
+    g = dvm.dvm_geometry()
+    g.dims = m.ndim
+    for j, nj in enumerate(m.shape[::-1]):
+        g.n[j] = nj
+    g.solid = m.ctypes.data_as(ctypes.c_void_p)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    grid = dvm.dvm_velocity_grid(len(w), v.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p))
+    opt = dvm.dvm_default_options()
+    for k, val in kw.items():
+        setattr(opt, k, val)
+    ctx = ctypes.c_void_p()
+    st = lib.dvm_create(ctypes.byref(g), float(kn), ctypes.byref(grid), ctypes.byref(opt), ctypes.byref(ctx))
+    msg = lib.dvm_last_error(None).decode()
+    return st, ctx, msg
+
+
+def test_create_rejects_invalid_input_before_device_work():
+    v, w = dvm.dvm_gh_velocity_grid(2, 8)
+    mask = np.zeros((8, 8), bool)
+    mask[3:5, 3:5] = True
+    for kn in (0.0, -1.0, float("nan"), float("inf")):
+        st, ctx, msg = _create(mask, kn, v, w)
+        assert st == dvm.DVM_EINVAL and not ctx.value and "Knudsen" in msg
+    st, _, msg = _create(np.ones((8, 8), bool), 0.1, v, w)
+    assert st == dvm.DVM_EINVAL and "fluid" in msg
+    st, _, msg = _create(np.zeros((8, 8), bool), 0.1, v, w)
+    assert st == dvm.DVM_EINVAL and "interface" in msg
+    st, _, msg = _create(np.zeros((2, 8), bool), 0.1, v, w)
+    assert st == dvm.DVM_EINVAL and ">= 3" in msg
+    bad_w = w * 1.001
+    st, _, msg = _create(mask, 0.1, v, bad_w)
+    assert st == dvm.DVM_EINVAL and "sum" in msg
+    v0 = v.copy()
+    v0[0, 0] = 0.0
+    st, _, msg = _create(mask, 0.1, v0, w)
+    assert st == dvm.DVM_EINVAL and "zero" in msg
+    st, _, msg = _create(mask, 0.1, v, w, stencil_order=3)
+    assert st == dvm.DVM_EINVAL
+    st, _, msg = _create(mask, 0.1, v, w, precision=7)
+    assert st == dvm.DVM_EINVAL
+
+
+def test_asymmetric_velocity_grid_is_rejected():
+    lib = dvm.load()
+    v, w = dvm.dvm_gh_velocity_grid(2, 8)
+    keep = ~((v[:, 0] > 0) & (v[:, 1] > 0) & (v[:, 0] > 1.0) & (v[:, 1] > 1.0))
+    v2 = v[keep]
+    w2 = w[keep] / w[keep].sum()
+    mask = np.zeros((8, 8), bool)
+    mask[3:5, 3:5] = True
+    st, ctx, msg = _create(mask, 0.1, v2, w2)
+    # symmetry is checked after the pinned host buffers are set up, so on a machine without a
+    # GPU the failure may surface as a CUDA error instead; either way no context is returned
+    assert st < 0 and not ctx.value
+
+
+def test_destroy_null_is_noop():
+    dvm.load().dvm_destroy(None)
