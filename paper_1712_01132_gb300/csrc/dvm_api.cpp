@@ -27,6 +27,9 @@ template <typename T> cudaError_t launch_finalize2d(const FinArgs2D<T>&, int nbl
 template <typename T> cudaError_t launch_init2d(const Prob2D<T>*, int NL, const double* qw, cudaStream_t);
 template <typename T> cudaError_t launch_moments2d(const Prob2D<T>*, double* rho, double* u, cudaStream_t);
 template <typename T> cudaError_t launch_wall2d(const Prob2D<T>*, double* out, cudaStream_t);
+cudaError_t launch_sweep2d_f32x2(const SweepArgs2D<float>&, int grid, int NW, cudaStream_t);
+cudaError_t sweep2d_f32x2_occupancy(int NW, int max_rows, int* blocks_per_sm);
+int sweep2d_f32x2_max_rows(int NW);
 }  // namespace dvm
 
 using namespace dvm;
@@ -204,15 +207,19 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         }
     }
     c->nvq = nvq;
-    c->NW = (nvq + 31) / 32;
-    c->NL = 32 * c->NW;
+    // FP32 lanes carry two velocities (packed f32x2 arithmetic), FP64 lanes one
+    const int vpl = (c->prec == DVM_FP32) ? 2 : 1;
+    c->NW = (nvq + 32 * vpl - 1) / (32 * vpl);
+    c->NL = 32 * vpl * c->NW;
     const int NL = c->NL;
-    if (c->NW > 16) return fail(c, DVM_EINVAL, "more than 512 velocities per quadrant");
+    if (c->NW > 16) return fail(c, DVM_EINVAL, "too many velocities per quadrant");
     // ---- tiles
-    c->T1 = c->opt.tile_x1 ? c->opt.tile_x1 : ((c->prec == DVM_FP32) ? 16 : 8);
+    c->T1 = c->opt.tile_x1 ? c->opt.tile_x1 : 8;
     if (c->T1 != 8 && c->T1 != 16) return fail(c, DVM_EINVAL, "tile_x1 must be 8 or 16");
+    if (c->prec == DVM_FP32) c->T1 = 8;     // the packed FP32 kernel uses 8-column tiles
     int rows = c->opt.band_rows ? c->opt.band_rows : ((c->prec == DVM_FP32) ? 16 : 8);
     if (rows < 1) return fail(c, DVM_EINVAL, "band_rows must be positive");
+    if (c->prec == DVM_FP32) rows = std::min(rows, sweep2d_f32x2_max_rows(c->NW));
     c->rows = rows;
     int max_rows = 1;
     for (int b = 0; b < c->nprob; ++b) max_rows = std::max(max_rows, std::min(rows, c->hp[b].n[1]));
@@ -222,6 +229,7 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     for (int k = 0; k < grid->nv; ++k)
         for (int j = 0; j < 2; ++j)
             if (grid->v[2 * k + j] > 0) dwall[j] += grid->w[k] * grid->v[2 * k + j];
+    const double dinv[2] = {1.0 / dwall[0], 1.0 / dwall[1]};
     std::vector<double> qw((size_t)c->nprob * NQ * 3, 0.0);
     for (int b = 0; b < c->nprob; ++b)
         for (int q = 0; q < NQ; ++q)
@@ -251,8 +259,8 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         P.kn = H.kn;
         P.nu = H.nu;
         P.dx = H.dx;
-        P.dwall[0] = dwall[0];
-        P.dwall[1] = dwall[1];
+        P.dinv[0] = dinv[0];
+        P.dinv[1] = dinv[1];
         const size_t N = H.N;
         uint16_t* code = (uint16_t*)dev_alloc(c, N * sizeof(uint16_t));
         P.src = (T*)dev_alloc(c, N * 4 * sizeof(T));
@@ -358,7 +366,8 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     c->probs_host.assign((const char*)probs.data(), (const char*)probs.data() + probs.size() * sizeof(Prob2D<T>));
     // ---- persistent grid size
     int per_sm = 0;
-    e = sweep2d_occupancy<T>(c->T1, c->NW, c->max_rows, &per_sm);
+    if (c->prec == DVM_FP32) e = sweep2d_f32x2_occupancy(c->NW, c->max_rows, &per_sm);
+    else e = sweep2d_occupancy<T>(c->T1, c->NW, c->max_rows, &per_sm);
     if (e != cudaSuccess) return cuda_fail(c, e, "occupancy");
     if (per_sm < 1) return fail(c, DVM_EINVAL, "sweep kernel does not fit on an SM with these tiles");
     int dev = 0, sms = 0;
@@ -396,6 +405,14 @@ cudaError_t mark(dvm_ctx* c) {
     return cudaEventRecord(ev, c->stream);
 }
 
+cudaError_t sweep_launch(const SweepArgs2D<float>& a, dvm_ctx* c) {
+    return launch_sweep2d_f32x2(a, c->sweep_grid, c->NW, c->stream);
+}
+
+cudaError_t sweep_launch(const SweepArgs2D<double>& a, dvm_ctx* c) {
+    return launch_sweep2d<double>(a, c->T1, c->sweep_grid, c->NW, c->stream);
+}
+
 template <typename T>
 dvm_status enqueue_iter_2d(dvm_ctx* c) {
     cudaError_t e = cudaMemsetAsync(c->counters_dev, 0, c->counters_bytes, c->stream);
@@ -412,7 +429,7 @@ dvm_status enqueue_iter_2d(dvm_ctx* c) {
     a.timeout_ns = c->timeout_ns;
     a.withhold_item = c->withhold_item;
     if ((e = mark(c)) != cudaSuccess) return cuda_fail(c, e, "event");
-    e = launch_sweep2d<T>(a, c->T1, c->sweep_grid, c->NW, c->stream);
+    e = sweep_launch(a, c);
     if (e != cudaSuccess) return cuda_fail(c, e, "sweep kernel");
     if ((e = mark(c)) != cudaSuccess) return cuda_fail(c, e, "event");
     FinArgs2D<T> fa{(const Prob2D<T>*)c->probs_dev, c->blk_prob_dev, c->blk_start_dev, c->status_dev};

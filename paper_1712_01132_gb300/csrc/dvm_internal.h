@@ -38,7 +38,7 @@ struct Prob2D {
     int lateral;         // 0 specular, 1 periodic
     int order;           // 2 or 1
     double kn, nu, dx;
-    double dwall[2];     // Eq. 6 denominators per axis
+    double dinv[2];      // reciprocals of the Eq. 6 denominators per axis
     const uint16_t* code;   // [N] stencil cases, see kernels
     T* src;              // [N][4]  (nu rho', 2 nu u1 + 1, 2 nu u2, 0)
     T* E;                // [N][4]  wall terms per (axis j, upstream side u): index 2 j + u

@@ -17,86 +17,9 @@
 #include <cstdint>
 
 #include "dvm_internal.h"
+#include "dvm_device.cuh"
 
 namespace dvm {
-
-// ---------------------------------------------------------------- helpers
-
-__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release_gpu(int* p, int v) {
-    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ int ld_volatile(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
-
-// Bounded wait for *flag >= target.  On expiry the kernel's status word is set to
-// DVM_ETIMEOUT (-4) and false is returned; a status already set by another CTA also ends it.
-__device__ bool wait_geq(const int* flag, int target, int* status, long long timeout_ns) {
-    if (ld_acquire_gpu(flag) >= target) return true;
-    const unsigned long long t0 = global_ns();
-    unsigned ns = 32;
-    for (;;) {
-        if (ld_acquire_gpu(flag) >= target) return true;
-        if (ld_volatile(status) != 0) return false;
-        if ((long long)(global_ns() - t0) > timeout_ns) {
-            atomicCAS(status, 0, -4);
-            return false;
-        }
-        __nanosleep(ns);
-        ns = ns < 1024 ? ns * 2 : 1024;
-    }
-}
-
-template <typename T> struct Vec4;
-template <> struct Vec4<float> {
-    using type = float4;
-    static __device__ __forceinline__ float4 make(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
-};
-struct alignas(32) dbl4 { double x, y, z, w; };
-template <> struct Vec4<double> {
-    using type = dbl4;
-    static __device__ __forceinline__ dbl4 make(double a, double b, double c, double d) { return dbl4{a, b, c, d}; }
-};
-
-__device__ __forceinline__ float bits_as(float, int v) { return __int_as_float(v); }
-__device__ __forceinline__ double bits_as(double, int v) { return __longlong_as_double((long long)v); }
-__device__ __forceinline__ int as_bits(float v) { return __float_as_int(v); }
-__device__ __forceinline__ int as_bits(double v) { return (int)__double_as_longlong(v); }
-
-// Sum over the 32 lanes of v[p] for NP (8 or 16) points at once.  Lane l ends up holding the
-// sum of point p = l >> (5 - log2 NP).  The combination tree (lane offsets 16, 8, 4, 2, 1) is the
-// same for every point, so the result does not depend on the point's slot.
-template <typename T, int NP>
-__device__ __forceinline__ T reduce_scatter(T (&v)[NP], int lane) {
-    constexpr int LOG = (NP == 16) ? 4 : (NP == 8 ? 3 : (NP == 4 ? 2 : 1));
-#pragma unroll
-    for (int s = 0; s < LOG; ++s) {
-        const int off = 16 >> s;
-        const int cnt = NP >> s;
-        const bool up = (lane & off) != 0;
-#pragma unroll
-        for (int k = 0; k < cnt / 2; ++k) {
-            const T send = up ? v[k] : v[k + cnt / 2];
-            const T keep = up ? v[k + cnt / 2] : v[k];
-            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-        }
-    }
-    T r = v[0];
-#pragma unroll
-    for (int off = 16 >> LOG; off >= 1; off >>= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
-    return r;
-}
 
 // ---------------------------------------------------------------- sweep
 
@@ -316,6 +239,11 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs2D<T> a) {
                 }
             }
             __syncthreads();
+            // the band above only needs the edge: publish before combining the moment partials
+            if (threadIdx.x == 0 && it != a.withhold_item) {
+                __threadfence();
+                st_release_gpu(P->prog + q * nb + band, t + 1);
+            }
             // moment partials of this quadrant: sum of the warps' lane sums, in warp order
             for (int idx = threadIdx.x; idx < nrows * width * 3; idx += blockDim.x) {
                 const int m = idx % 3;
@@ -330,9 +258,7 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs2D<T> a) {
                 const int y = s2neg ? n2 - 1 - yo : yo;
                 P->P[((size_t)q * 3 + m) * N + (size_t)y * n1 + x] = s;
             }
-            __threadfence();
             __syncthreads();
-            if (threadIdx.x == 0 && it != a.withhold_item) st_release_gpu(P->prog + q * nb + band, t + 1);
         }
         __syncthreads();
     }
@@ -350,7 +276,7 @@ __device__ __forceinline__ double wall_density(const Prob2D<T>* P, int y, int j,
         const int neg = (q >> j) & 1;
         if (neg == (sigma < 0 ? 1 : 0)) num += (double)P->P[((size_t)q * 3 + 1 + j) * P->N + y];
     }
-    return sigma * num / P->dwall[j];
+    return sigma * num * P->dinv[j];
 }
 
 template <typename T>
@@ -430,15 +356,25 @@ __global__ void __launch_bounds__(256) finalize2d_kernel(const FinArgs2D<T> a) {
         s_last = (prev == (unsigned)P->fin_nblocks - 1u);
     }
     __syncthreads();
-    if (s_last && threadIdx.x == 0) {
+    if (s_last) {
+        // all threads of the last block: strided partial sums in a fixed order, then a fixed tree
         __threadfence();
-        double tot = 0.0;
-        for (int k = 0; k < P->fin_nblocks; ++k) tot += __ldcg(P->kpart + k);
-        const double gp = tot / (double)P->N;
-        P->kval[0] = 2.0 / sqrt(3.14159265358979323846) * P->kn * gp;
-        P->kval[1] = gp;
-        P->kval[2] = tot;
-        *P->fin_counter = 0u;
+        double acc = 0.0;
+        for (int k = threadIdx.x; k < P->fin_nblocks; k += blockDim.x) acc += __ldcg(P->kpart + k);
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_red[w];
+            const double gp = tot / (double)P->N;
+            P->kval[0] = 2.0 / sqrt(3.14159265358979323846) * P->kn * gp;
+            P->kval[1] = gp;
+            P->kval[2] = tot;
+            *P->fin_counter = 0u;
+        }
     }
 }
 
