@@ -60,7 +60,7 @@ def build(force=False, verbose=False):
         results = list(ex.map(compile_one, sources()))
     objs = [o for o, _ in results]
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
+    cmd = [nvcc] + ARCH + ["-shared", "-Xlinker", "-z", "-Xlinker", "defs", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))

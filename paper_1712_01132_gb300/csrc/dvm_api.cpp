@@ -30,6 +30,7 @@ template <typename T> cudaError_t launch_wall2d(const Prob2D<T>*, double* out, c
 cudaError_t launch_sweep2d_f32x2(const SweepArgs2D<float>&, int grid, int NW, cudaStream_t);
 cudaError_t sweep2d_f32x2_occupancy(int NW, int max_rows, int* blocks_per_sm);
 int sweep2d_f32x2_max_rows(int NW);
+int sweep2d_f32x2_velocities_per_lane();
 }  // namespace dvm
 
 using namespace dvm;
@@ -208,7 +209,7 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     }
     c->nvq = nvq;
     // FP32 lanes carry two velocities (packed f32x2 arithmetic), FP64 lanes one
-    const int vpl = (c->prec == DVM_FP32) ? 2 : 1;
+    const int vpl = (c->prec == DVM_FP32) ? sweep2d_f32x2_velocities_per_lane() : 1;
     c->NW = (nvq + 32 * vpl - 1) / (32 * vpl);
     c->NL = 32 * vpl * c->NW;
     const int NL = c->NL;

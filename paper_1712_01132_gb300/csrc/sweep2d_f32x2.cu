@@ -1,23 +1,22 @@
 // sweep2d_f32x2.cu -- FP32 transport sweep of one source iteration in 2D (arXiv:1712.01132,
-// Sec. 3.1 step i with the quadrature of step iii fused), two discrete velocities per lane.
+// Sec. 3.1 step i with the quadrature of step iii fused), four discrete velocities per lane.
 //
 // Schedule: persistent CTAs take (problem, quadrant, band) items from a ticket counter in band
 // order.  A CTA sweeps its band along x1 in tiles of 8 columns; band b starts tile t once band b-1
-// has published it.  Inside a tile every warp walks its rows two at a time, the upper row one
-// column behind the lower one, so a warp always has two independent dependency chains in flight.
-// Per-point arithmetic (Eq. 10 solved for h at the point, upwind stencil of Eq. 9):
+// has published it.  Inside a tile a warp walks its rows in order; every lane carries four
+// velocities as two packed pairs (two independent dependency chains per lane) updated with
+// fma.rn.f32x2.  Per-point arithmetic (Eq. 10 solved for h at the point, upwind stencil of Eq. 9):
 //   h = R * [ nu rho' + 2 nu u.v + v1 + a1 (K1x h(x-s1 e1) + K2x h(x-2 s1 e1) + E1)
 //                                     + a2 (K1y h(x-s2 e2) + K2y h(x-2 s2 e2) + E2) ]
-// with a_j = |v_j|/dx, the stencil weights (K1, K2) = (2, -1/2) (second order), wall terms E
-// where an upstream point is solid, and R the reciprocal denominator of the point's stencil case.
-// Each lane carries a pair of velocities and updates both with packed f32x2 FMAs; the per-point
-// scalars are stored duplicated in shared memory so they load as pairs.  Solid points carry zero
-// records (their h is 0 and no stencil reads it with a nonzero weight).
+// with a_j = |v_j|/dx, stencil weights (K1, K2) = (2, -1/2) (second order), wall terms E where an
+// upstream point is solid, and R the reciprocal denominator of the point's stencil case.
 //
-// Latency hiding: the next tile's records are loaded into registers while the current tile is
-// swept; progress is published as soon as the band edge is stored, before the moment partials
-// are combined.  The moment of a point is summed in a fixed order (the lane's pair, the lane
-// tree, the warps, the quadrants), so results do not depend on tile shapes or scheduling.
+// The per-point scalars are broadcast from a 10-word shared-memory record to every lane of the
+// warps of the quadrant; with four velocities per lane each broadcast serves 128 velocities.
+// Solid points carry zero records; tile rows without fluid are skipped.  The next tile's records
+// are loaded into registers while the current tile is swept, and progress is published as soon as
+// the band edge is stored.  The moment of a point is summed in a fixed order (the lane's four
+// velocities, the lane tree, the warps, the quadrants), so results do not depend on tile shapes.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -30,12 +29,13 @@ namespace dvm {
 
 namespace {
 
-constexpr int kRec2 = 20;   // floats per point record: five duplicated-pair float4s
+constexpr int kRecF = 12;   // floats per point record (10 used): {a b1 b2 roff} {E1 K1x K2x E2} {K1y K2y}
 constexpr int kT1 = 8;      // tile width along x1
-constexpr int kMaxRounds = 1;   // points prefetched per thread (bounds the rows per band)
+constexpr int kVL = 4;      // velocities per lane (two packed pairs)
+constexpr int kMaxRounds = 2;
 
-struct LaneP {
-    float2 v1, v2, a1, a2, W, Wv1, Wv2;
+struct LaneQ {
+    float2 v1[2], v2[2], a1[2], a2[2], W[2], Wv1[2], Wv2[2];
 };
 
 struct RawPoint {           // global data of one point needed to build its record
@@ -44,32 +44,6 @@ struct RawPoint {           // global data of one point needed to build its reco
 };
 
 __device__ __forceinline__ float2 dup(float x) { return make_float2(x, x); }
-
-// one point: returns h for the lane's two velocities
-__device__ __forceinline__ float2 point_update(const float* __restrict__ rp, const float* __restrict__ rtab,
-                                               const LaneP& L, float2 hp1, float2 hp2, float2 up1, float2 up2) {
-    const float4* R = reinterpret_cast<const float4*>(rp);
-    const float4 r0 = R[0];   // a a b1 b1
-    const float4 r1 = R[1];   // b2 b2 E1 E1
-    const float4 r2 = R[2];   // K1x K1x K2x K2x
-    const float4 r3 = R[3];   // E2 E2 K1y K1y
-    const float4 r4 = R[4];   // K2y K2y rtab-offset -
-    const float2 Rv = *reinterpret_cast<const float2*>(rtab + __float_as_int(r4.z));
-    const float2 S = fma2(make_float2(r1.x, r1.y), L.v2, fma2(make_float2(r0.z, r0.w), L.v1, make_float2(r0.x, r0.y)));
-    const float2 t2 = fma2(make_float2(r3.z, r3.w), up1, fma2(make_float2(r4.x, r4.y), up2, make_float2(r3.x, r3.y)));
-    const float2 base = fma2(L.a2, t2, S);
-    const float2 t1 = fma2(make_float2(r2.x, r2.y), hp1, fma2(make_float2(r2.z, r2.w), hp2, make_float2(r1.z, r1.w)));
-    return mul2(fma2(L.a1, t1, base), Rv);
-}
-
-__device__ __forceinline__ void moments_of(const LaneP& L, float2 h, float& m0, float& m1, float& m2) {
-    const float2 p0 = mul2(L.W, h);
-    const float2 p1 = mul2(L.Wv1, h);
-    const float2 p2 = mul2(L.Wv2, h);
-    m0 = p0.x + p0.y;
-    m1 = p1.x + p1.y;
-    m2 = p2.x + p2.y;
-}
 
 }  // namespace
 
@@ -82,14 +56,14 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int RB = a.max_rows;
-    float* rec = reinterpret_cast<float*>(smem_raw);                    // [2][RB][T1][kRec2]
-    float* part = rec + (size_t)2 * RB * T1 * kRec2;                     // [NW][RB][T1][3]
-    float* carry = part + (size_t)NW * RB * T1 * 3;                      // [NW][RB][2][64]
-    float* rtab = carry + (size_t)NW * RB * 2 * 64;                      // [NW][4][64]
-    unsigned* rmask = reinterpret_cast<unsigned*>(rtab + (size_t)NW * 4 * 64);   // [2][RB]
-    const int wl = warp * 32 + lane;            // lane index; velocities 2 wl, 2 wl + 1
+    float* rec = reinterpret_cast<float*>(smem_raw);                    // [2][RB][T1][kRecF]
+    float* part = rec + (size_t)2 * RB * T1 * kRecF;                     // [NW][RB][T1][3]
+    float* carry = part + (size_t)NW * RB * T1 * 3;                      // [NW][RB][2][128]
+    float* rtab = carry + (size_t)NW * RB * 2 * 128;                     // [NW][4][128]
+    unsigned* rmask = reinterpret_cast<unsigned*>(rtab + (size_t)NW * 4 * 128);  // [2][RB]
+    const int wl = warp * 32 + lane;            // lane index; velocities 4 wl .. 4 wl + 3
     const size_t NL = (size_t)a.NL;
-    float* my_rtab = rtab + (size_t)warp * 4 * 64;
+    const float* my_rtab = rtab + (size_t)warp * 4 * 128 + 4 * lane;
 
     for (;;) {
         if (threadIdx.x == 0) {
@@ -111,35 +85,40 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
         const int nrows = min(P->rows, n2 - row0);
         const float K1o = P->order == 2 ? 2.f : 1.f;
         const float K2o = P->order == 2 ? -0.5f : 0.f;
-        LaneP L;
+        LaneQ L;
         {
-            const float* la = P->lanec + ((size_t)q * NL + 2 * wl) * kLaneConsts;
-            const float* lb = la + kLaneConsts;
-            L.v1 = make_float2(la[0], lb[0]);
-            L.v2 = make_float2(la[1], lb[1]);
-            L.a1 = make_float2(la[2], lb[2]);
-            L.a2 = make_float2(la[3], lb[3]);
-            L.W = make_float2(la[4], lb[4]);
-            L.Wv1 = make_float2(la[5], lb[5]);
-            L.Wv2 = make_float2(la[6], lb[6]);
+            const float* lc = P->lanec + ((size_t)q * NL + (size_t)kVL * wl) * kLaneConsts;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const float* la = lc + (2 * k) * kLaneConsts;
+                const float* lb = la + kLaneConsts;
+                L.v1[k] = make_float2(la[0], lb[0]);
+                L.v2[k] = make_float2(la[1], lb[1]);
+                L.a1[k] = make_float2(la[2], lb[2]);
+                L.a2[k] = make_float2(la[3], lb[3]);
+                L.W[k] = make_float2(la[4], lb[4]);
+                L.Wv1[k] = make_float2(la[5], lb[5]);
+                L.Wv2[k] = make_float2(la[6], lb[6]);
+            }
+            float* rt = rtab + (size_t)warp * 4 * 128 + 4 * lane;
 #pragma unroll
             for (int rs = 0; rs < 4; ++rs)
-                *reinterpret_cast<float2*>(my_rtab + rs * 64 + 2 * lane) = make_float2(la[7 + rs], lb[7 + rs]);
+                *reinterpret_cast<float4*>(rt + rs * 128) =
+                    make_float4(lc[7 + rs], lc[kLaneConsts + 7 + rs], lc[2 * kLaneConsts + 7 + rs], lc[3 * kLaneConsts + 7 + rs]);
         }
         const int par = a.parity;
         {
             const float* g = P->gx1 + (((size_t)par * 4 + q) * n2) * 2 * NL;
             for (int r = 0; r < nrows; ++r) {
-                float* cr = carry + ((size_t)(warp * RB + r) * 2) * 64 + 2 * lane;
-                *reinterpret_cast<float2*>(cr) = *reinterpret_cast<const float2*>(g + ((size_t)(row0 + r) * 2 + 0) * NL + 2 * wl);
-                *reinterpret_cast<float2*>(cr + 64) = *reinterpret_cast<const float2*>(g + ((size_t)(row0 + r) * 2 + 1) * NL + 2 * wl);
+                float* cr = carry + ((size_t)(warp * RB + r) * 2) * 128 + 4 * lane;
+                *reinterpret_cast<float4*>(cr) = *reinterpret_cast<const float4*>(g + ((size_t)(row0 + r) * 2 + 0) * NL + kVL * wl);
+                *reinterpret_cast<float4*>(cr + 128) = *reinterpret_cast<const float4*>(g + ((size_t)(row0 + r) * 2 + 1) * NL + kVL * wl);
             }
         }
         const int ntiles = (n1 + T1 - 1) / T1;
         const int npts = nrows * T1;
         const int rounds = (npts + blockDim.x - 1) / blockDim.x;
 
-        // global data of the points this thread turns into records, for tile tt
         auto load_raw = [&](int tt, RawPoint (&raw)[kMaxRounds]) {
 #pragma unroll
             for (int k = 0; k < kMaxRounds; ++k) {
@@ -162,9 +141,8 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
                 }
             }
         };
-        // records (duplicated pairs; zero for solid points) and per-row fluid masks
         auto store_rec = [&](int buf, const RawPoint (&raw)[kMaxRounds]) {
-            float* rb = rec + (size_t)buf * RB * T1 * kRec2;
+            float* rb = rec + (size_t)buf * RB * T1 * kRecF;
             unsigned* mk = rmask + buf * RB;
 #pragma unroll
             for (int k = 0; k < kMaxRounds; ++k) {
@@ -172,28 +150,22 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
                 const int idx = k * blockDim.x + threadIdx.x;
                 const bool fluid = idx < npts && !(raw[k].code & kSolidBit);
                 if (idx < npts) {
-                    float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), o1 = o0, o2 = o0, o3 = o0, o4 = o0;
+                    float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), o1 = o0, o2 = o0;
                     if (fluid) {
                         const int code = raw[k].code;
                         const int ca = (code >> (2 * (0 + s1neg))) & 3;
                         const int cb = (code >> (2 * (2 + s2neg))) & 3;
                         const float E1 = s1neg ? raw[k].e.y : raw[k].e.x;
                         const float E2 = s2neg ? raw[k].e.w : raw[k].e.z;
-                        const float K1x = ca == 2 ? 0.f : K1o, K2x = ca == 0 ? K2o : 0.f;
-                        const float K1y = cb == 2 ? 0.f : K1o, K2y = cb == 0 ? K2o : 0.f;
                         const int rs = (ca == 2) | ((cb == 2) << 1);
-                        o0 = make_float4(raw[k].s.x, raw[k].s.x, raw[k].s.y, raw[k].s.y);
-                        o1 = make_float4(raw[k].s.z, raw[k].s.z, E1, E1);
-                        o2 = make_float4(K1x, K1x, K2x, K2x);
-                        o3 = make_float4(E2, E2, K1y, K1y);
-                        o4 = make_float4(K2y, K2y, __int_as_float(rs * 64), 0.f);
+                        o0 = make_float4(raw[k].s.x, raw[k].s.y, raw[k].s.z, __int_as_float(rs * 128));
+                        o1 = make_float4(E1, ca == 2 ? 0.f : K1o, ca == 0 ? K2o : 0.f, E2);
+                        o2 = make_float4(cb == 2 ? 0.f : K1o, cb == 0 ? K2o : 0.f, 0.f, 0.f);
                     }
-                    float4* R = reinterpret_cast<float4*>(rb + (size_t)idx * kRec2);
+                    float4* R = reinterpret_cast<float4*>(rb + (size_t)idx * kRecF);
                     R[0] = o0;
                     R[1] = o1;
                     R[2] = o2;
-                    R[3] = o3;
-                    R[4] = o4;
                 }
                 const unsigned bits = __ballot_sync(0xffffffffu, fluid);
                 if (lane == 0) {
@@ -223,9 +195,10 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
             }
             __syncthreads();
             if (s_abort) return;
-            const float* rbuf = rec + (size_t)buf * RB * T1 * kRec2;
+            const float* rbuf = rec + (size_t)buf * RB * T1 * kRecF;
             const unsigned* mk = rmask + buf * RB;
-            float2 rb1[T1], rb2[T1];
+            // the two rows below: previous band's top edge or the x2 ghost layers
+            float4 rb1[T1], rb2[T1];
             {
                 const float* eb = (band == 0)
                     ? P->glat + (((size_t)par * 4 + q) * n1) * 2 * NL
@@ -233,109 +206,67 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
 #pragma unroll
                 for (int i = 0; i < T1; ++i) {
                     if (i < width) {
-                        rb1[i] = __ldcg(reinterpret_cast<const float2*>(eb + ((size_t)(c0 + i) * 2 + 0) * NL + 2 * wl));
-                        rb2[i] = __ldcg(reinterpret_cast<const float2*>(eb + ((size_t)(c0 + i) * 2 + 1) * NL + 2 * wl));
+                        rb1[i] = __ldcg(reinterpret_cast<const float4*>(eb + ((size_t)(c0 + i) * 2 + 0) * NL + kVL * wl));
+                        rb2[i] = __ldcg(reinterpret_cast<const float4*>(eb + ((size_t)(c0 + i) * 2 + 1) * NL + kVL * wl));
                     } else {
-                        rb1[i] = make_float2(0.f, 0.f);
-                        rb2[i] = make_float2(0.f, 0.f);
+                        rb1[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        rb2[i] = rb1[i];
                     }
                 }
             }
-            const float* rt = my_rtab + 2 * lane;
-            // FULL: all T1 columns exist; otherwise columns >= width are skipped (uniform test) so
-            // the x1 carry keeps the last two points of the row
             auto walk_rows = [&](auto full_tag) {
                 constexpr bool FULL = decltype(full_tag)::value;
-                int r = 0;
-                for (; r + 1 < nrows; r += 2) {
-                    // rows r (lower) and r+1 (upper), the upper one column behind
-                    float* ca = carry + ((size_t)(warp * RB + r) * 2) * 64 + 2 * lane;
-                    float* cb = ca + 2 * 64;
-                    const unsigned fm = mk[r] | mk[r + 1];
-                    if (fm == 0u) continue;     // both rows solid in this tile: nothing reads them
-                    float2 ha1 = *reinterpret_cast<const float2*>(ca);
-                    float2 ha2 = *reinterpret_cast<const float2*>(ca + 64);
-                    float2 hb1 = *reinterpret_cast<const float2*>(cb);
-                    float2 hb2 = *reinterpret_cast<const float2*>(cb + 64);
-                    const float* ra = rbuf + (size_t)r * T1 * kRec2;
-                    const float* rbr = ra + T1 * kRec2;
-                    float ma0[T1], ma1[T1], ma2[T1], mb0[T1], mb1[T1], mb2[T1];
-#pragma unroll
-                    for (int s = 0; s <= T1; ++s) {
-                        if (s < T1) {
-                            if (FULL || s < width) {
-                                const float2 h = point_update(ra + s * kRec2, rt, L, ha1, ha2, rb1[s], rb2[s]);
-                                ha2 = ha1;
-                                ha1 = h;
-                                rb2[s] = rb1[s];
-                                rb1[s] = h;
-                                moments_of(L, h, ma0[s], ma1[s], ma2[s]);
-                            } else {
-                                ma0[s] = ma1[s] = ma2[s] = 0.f;
-                            }
-                        }
-                        if (s >= 1) {
-                            const int i = s - 1;
-                            if (FULL || i < width) {
-                                const float2 h = point_update(rbr + i * kRec2, rt, L, hb1, hb2, rb1[i], rb2[i]);
-                                hb2 = hb1;
-                                hb1 = h;
-                                rb2[i] = rb1[i];
-                                rb1[i] = h;
-                                moments_of(L, h, mb0[i], mb1[i], mb2[i]);
-                            } else {
-                                mb0[i] = mb1[i] = mb2[i] = 0.f;
-                            }
-                        }
-                        if (s == T1 - 1) {
-                            // lower row complete: reduce it while the upper row finishes
-                            const float s0 = reduce_scatter<float, T1>(ma0, lane);
-                            const float s1 = reduce_scatter<float, T1>(ma1, lane);
-                            const float s2 = reduce_scatter<float, T1>(ma2, lane);
-                            if ((lane & 3) == 0) {
-                                float* d = part + ((size_t)(warp * RB + r) * T1 + (lane >> 2)) * 3;
-                                d[0] = s0;
-                                d[1] = s1;
-                                d[2] = s2;
-                            }
-                        }
-                    }
-                    *reinterpret_cast<float2*>(ca) = ha1;
-                    *reinterpret_cast<float2*>(ca + 64) = ha2;
-                    *reinterpret_cast<float2*>(cb) = hb1;
-                    *reinterpret_cast<float2*>(cb + 64) = hb2;
-                    const float s0 = reduce_scatter<float, T1>(mb0, lane);
-                    const float s1 = reduce_scatter<float, T1>(mb1, lane);
-                    const float s2 = reduce_scatter<float, T1>(mb2, lane);
-                    if ((lane & 3) == 0) {
-                        float* d = part + ((size_t)(warp * RB + r + 1) * T1 + (lane >> 2)) * 3;
-                        d[0] = s0;
-                        d[1] = s1;
-                        d[2] = s2;
-                    }
-                }
-                if (r < nrows && mk[r] != 0u) {
-                    // last row of an odd band
-                    float* ca = carry + ((size_t)(warp * RB + r) * 2) * 64 + 2 * lane;
-                    float2 ha1 = *reinterpret_cast<const float2*>(ca);
-                    float2 ha2 = *reinterpret_cast<const float2*>(ca + 64);
-                    const float* ra = rbuf + (size_t)r * T1 * kRec2;
+                for (int r = 0; r < nrows; ++r) {
+                    const unsigned fm = mk[r];
+                    if (fm == 0u) continue;     // no fluid in this tile row: nothing reads it
+                    float* cr = carry + ((size_t)(warp * RB + r) * 2) * 128 + 4 * lane;
+                    const float4 c1 = *reinterpret_cast<const float4*>(cr);
+                    const float4 c2 = *reinterpret_cast<const float4*>(cr + 128);
+                    float2 hp1[2] = {make_float2(c1.x, c1.y), make_float2(c1.z, c1.w)};
+                    float2 hp2[2] = {make_float2(c2.x, c2.y), make_float2(c2.z, c2.w)};
+                    const float* rrow = rbuf + (size_t)r * T1 * kRecF;
                     float m0[T1], m1[T1], m2[T1];
 #pragma unroll
-                    for (int s = 0; s < T1; ++s) {
-                        if (FULL || s < width) {
-                            const float2 h = point_update(ra + s * kRec2, rt, L, ha1, ha2, rb1[s], rb2[s]);
-                            ha2 = ha1;
-                            ha1 = h;
-                            rb2[s] = rb1[s];
-                            rb1[s] = h;
-                            moments_of(L, h, m0[s], m1[s], m2[s]);
+                    for (int i = 0; i < T1; ++i) {
+                        if (FULL || i < width) {
+                            const float4* Rp = reinterpret_cast<const float4*>(rrow + i * kRecF);
+                            const float4 A = Rp[0];                 // a b1 b2 roff
+                            const float4 B = Rp[1];                 // E1 K1x K2x E2
+                            const float2 C = *reinterpret_cast<const float2*>(Rp + 2);   // K1y K2y
+                            const float4 Rv = *reinterpret_cast<const float4*>(my_rtab + __float_as_int(A.w));
+                            const float2 aP = dup(A.x), b1P = dup(A.y), b2P = dup(A.z);
+                            const float2 E1P = dup(B.x), K1xP = dup(B.y), K2xP = dup(B.z), E2P = dup(B.w);
+                            const float2 K1yP = dup(C.x), K2yP = dup(C.y);
+                            const float2 rb1a = make_float2(rb1[i].x, rb1[i].y), rb1b = make_float2(rb1[i].z, rb1[i].w);
+                            const float2 rb2a = make_float2(rb2[i].x, rb2[i].y), rb2b = make_float2(rb2[i].z, rb2[i].w);
+                            float2 h[2];
+#pragma unroll
+                            for (int k = 0; k < 2; ++k) {
+                                const float2 up1 = k ? rb1b : rb1a;
+                                const float2 up2 = k ? rb2b : rb2a;
+                                const float2 S = fma2(b2P, L.v2[k], fma2(b1P, L.v1[k], aP));
+                                const float2 t2 = fma2(K1yP, up1, fma2(K2yP, up2, E2P));
+                                const float2 base = fma2(L.a2[k], t2, S);
+                                const float2 t1 = fma2(K1xP, hp1[k], fma2(K2xP, hp2[k], E1P));
+                                const float2 Rk = k ? make_float2(Rv.z, Rv.w) : make_float2(Rv.x, Rv.y);
+                                h[k] = mul2(fma2(L.a1[k], t1, base), Rk);
+                                hp2[k] = hp1[k];
+                                hp1[k] = h[k];
+                            }
+                            rb2[i] = rb1[i];
+                            rb1[i] = make_float4(h[0].x, h[0].y, h[1].x, h[1].y);
+                            const float2 p0 = fma2(L.W[1], h[1], mul2(L.W[0], h[0]));
+                            const float2 p1 = fma2(L.Wv1[1], h[1], mul2(L.Wv1[0], h[0]));
+                            const float2 p2 = fma2(L.Wv2[1], h[1], mul2(L.Wv2[0], h[0]));
+                            m0[i] = p0.x + p0.y;
+                            m1[i] = p1.x + p1.y;
+                            m2[i] = p2.x + p2.y;
                         } else {
-                            m0[s] = m1[s] = m2[s] = 0.f;
+                            m0[i] = m1[i] = m2[i] = 0.f;
                         }
                     }
-                    *reinterpret_cast<float2*>(ca) = ha1;
-                    *reinterpret_cast<float2*>(ca + 64) = ha2;
+                    *reinterpret_cast<float4*>(cr) = make_float4(hp1[0].x, hp1[0].y, hp1[1].x, hp1[1].y);
+                    *reinterpret_cast<float4*>(cr + 128) = make_float4(hp2[0].x, hp2[0].y, hp2[1].x, hp2[1].y);
                     const float s0 = reduce_scatter<float, T1>(m0, lane);
                     const float s1 = reduce_scatter<float, T1>(m1, lane);
                     const float s2 = reduce_scatter<float, T1>(m2, lane);
@@ -362,8 +293,8 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
 #pragma unroll
                 for (int i = 0; i < T1; ++i) {
                     if (i < width) {
-                        *reinterpret_cast<float2*>(et + ((size_t)(c0 + i) * 2 + 0) * NL + 2 * wl) = rb1[i];
-                        *reinterpret_cast<float2*>(et + ((size_t)(c0 + i) * 2 + 1) * NL + 2 * wl) = rb2[i];
+                        *reinterpret_cast<float4*>(et + ((size_t)(c0 + i) * 2 + 0) * NL + kVL * wl) = rb1[i];
+                        *reinterpret_cast<float4*>(et + ((size_t)(c0 + i) * 2 + 1) * NL + kVL * wl) = rb2[i];
                     }
                 }
             }
@@ -371,9 +302,9 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
                 // x1 ghost layers of the next iteration (periodic in x1, same quadrant)
                 float* g = P->gx1 + (((size_t)(par ^ 1) * 4 + q) * n2) * 2 * NL;
                 for (int rr = 0; rr < nrows; ++rr) {
-                    const float* cr = carry + ((size_t)(warp * RB + rr) * 2) * 64 + 2 * lane;
-                    *reinterpret_cast<float2*>(g + ((size_t)(row0 + rr) * 2 + 0) * NL + 2 * wl) = *reinterpret_cast<const float2*>(cr);
-                    *reinterpret_cast<float2*>(g + ((size_t)(row0 + rr) * 2 + 1) * NL + 2 * wl) = *reinterpret_cast<const float2*>(cr + 64);
+                    const float* cr = carry + ((size_t)(warp * RB + rr) * 2) * 128 + 4 * lane;
+                    *reinterpret_cast<float4*>(g + ((size_t)(row0 + rr) * 2 + 0) * NL + kVL * wl) = *reinterpret_cast<const float4*>(cr);
+                    *reinterpret_cast<float4*>(g + ((size_t)(row0 + rr) * 2 + 1) * NL + kVL * wl) = *reinterpret_cast<const float4*>(cr + 128);
                 }
             }
             if (t + 1 < ntiles) store_rec(buf ^ 1, nxt);
@@ -403,12 +334,14 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
 }
 
 size_t sweep2d_f32x2_smem(int NW, int max_rows) {
-    return sizeof(float) * ((size_t)2 * max_rows * kT1 * kRec2 + (size_t)NW * max_rows * kT1 * 3 +
-                            (size_t)NW * max_rows * 2 * 64 + (size_t)NW * 4 * 64) +
+    return sizeof(float) * ((size_t)2 * max_rows * kT1 * kRecF + (size_t)NW * max_rows * kT1 * 3 +
+                            (size_t)NW * max_rows * 2 * 128 + (size_t)NW * 4 * 128) +
            sizeof(unsigned) * (size_t)2 * max_rows;
 }
 
 int sweep2d_f32x2_max_rows(int NW) { return kMaxRounds * NW * 32 / kT1; }
+
+int sweep2d_f32x2_velocities_per_lane() { return kVL; }
 
 cudaError_t launch_sweep2d_f32x2(const SweepArgs2D<float>& a, int grid, int NW, cudaStream_t st) {
     const size_t smem = sweep2d_f32x2_smem(NW, a.max_rows);
