@@ -31,6 +31,13 @@ cudaError_t launch_sweep2d_f32x2(const SweepArgs2D<float>&, int grid, int NW, cu
 cudaError_t sweep2d_f32x2_occupancy(int NW, int max_rows, int* blocks_per_sm);
 int sweep2d_f32x2_max_rows(int NW);
 int sweep2d_f32x2_velocities_per_lane();
+template <typename T> size_t sweep3d_smem(int T1, int NW, int R2, int R3);
+template <typename T> cudaError_t sweep3d_occupancy(int T1, int NW, int R2, int R3, int* blocks_per_sm);
+template <typename T> cudaError_t launch_sweep3d(const SweepArgs3D<T>&, int grid, int NW, cudaStream_t);
+template <typename T> cudaError_t launch_finalize3d(const FinArgs3D<T>&, int nblocks, cudaStream_t);
+template <typename T> cudaError_t launch_init3d(const Prob3D<T>*, int NL, const double* qw, cudaStream_t);
+template <typename T> cudaError_t launch_moments3d(const Prob3D<T>*, double* rho, double* u, cudaStream_t);
+template <typename T> cudaError_t launch_wall3d(const Prob3D<T>*, double* out, cudaStream_t);
 }  // namespace dvm
 
 using namespace dvm;
@@ -88,6 +95,9 @@ struct dvm_ctx {
     long long timeout_ns = kDefaultTimeoutNs;
     int withhold_item = -1;
     std::vector<int> prog_offset;    // per problem, offset of its progress flags in counters
+    std::vector<double*> kval_dev;   // per problem, device address of (k, G_p, sum u1)
+    int GL = 32, G = 1;              // 3D: lanes per velocity group, groups per octant
+    int R2 = 4, R3 = 4;              // 3D pencil rows
     // measurement support
     bool profile = false;
     std::vector<cudaEvent_t> ev_pool;      // events owned by the context
@@ -218,7 +228,7 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     c->T1 = c->opt.tile_x1 ? c->opt.tile_x1 : 8;
     if (c->T1 != 8 && c->T1 != 16) return fail(c, DVM_EINVAL, "tile_x1 must be 8 or 16");
     if (c->prec == DVM_FP32) c->T1 = 8;     // the packed FP32 kernel uses 8-column tiles
-    int rows = c->opt.band_rows ? c->opt.band_rows : ((c->prec == DVM_FP32) ? 16 : 8);
+    int rows = c->opt.band_rows ? c->opt.band_rows : 8;
     if (rows < 1) return fail(c, DVM_EINVAL, "band_rows must be positive");
     if (c->prec == DVM_FP32) rows = std::min(rows, sweep2d_f32x2_max_rows(c->NW));
     c->rows = rows;
@@ -327,6 +337,7 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         }
         c->prog_offset[b] = 1 + prog_total;
         prog_total += NQ * P.nbands;
+        c->kval_dev.push_back(P.kval);
     }
     // ---- work items in band order (a band only waits for lower bands: deadlock-free tickets)
     int maxb = 0;
@@ -389,6 +400,242 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     return DVM_OK;
 }
 
+
+template <typename T>
+dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_grid* grid) {
+    const int NO = 8;
+    // ---- velocity groups: octant q (bit j set when v_j < 0), lanes ordered by (|v1|, |v2|, |v3|)
+    std::vector<std::vector<int>> group(NO);
+    for (int k = 0; k < grid->nv; ++k) {
+        const double* v = grid->v + 3 * k;
+        group[(v[0] < 0 ? 1 : 0) | (v[1] < 0 ? 2 : 0) | (v[2] < 0 ? 4 : 0)].push_back(k);
+    }
+    auto key_less = [&](int a, int b) {
+        const double* va = grid->v + 3 * a;
+        const double* vb = grid->v + 3 * b;
+        for (int j = 0; j < 3; ++j)
+            if (std::fabs(va[j]) != std::fabs(vb[j])) return std::fabs(va[j]) < std::fabs(vb[j]);
+        return false;
+    };
+    for (auto& g : group) std::sort(g.begin(), g.end(), key_less);
+    const int nvo = (int)group[0].size();
+    for (int q = 1; q < NO; ++q)
+        if ((int)group[q].size() != nvo) return fail(c, DVM_EINVAL, "velocity grid is not symmetric under sign changes");
+    for (int m = 0; m < nvo; ++m) {
+        const double* v0 = grid->v + 3 * group[0][m];
+        for (int q = 1; q < NO; ++q) {
+            const double* vq = grid->v + 3 * group[q][m];
+            for (int j = 0; j < 3; ++j)
+                if (std::fabs(vq[j]) != std::fabs(v0[j])) return fail(c, DVM_EINVAL, "velocity grid is not symmetric under sign changes");
+            if (grid->w[group[q][m]] != grid->w[group[0][m]]) return fail(c, DVM_EINVAL, "velocity grid is not symmetric under sign changes");
+        }
+    }
+    c->nvq = nvo;
+    const int warps_total = (nvo + 31) / 32;
+    c->G = (warps_total + 7) / 8;                         // at most 8 warps per CTA
+    c->NW = (warps_total + c->G - 1) / c->G;
+    c->GL = 32 * c->NW;
+    c->NL = c->GL * c->G;
+    const int NL = c->NL, G = c->G;
+    c->T1 = (c->opt.tile_x1 == 4) ? 4 : 8;
+    const int R = c->opt.band_rows ? c->opt.band_rows : 4;
+    c->R2 = c->R3 = std::max(1, R);
+    {
+        // shrink the tile, then the pencil, until the CTA's shared memory fits the device limit
+        int dev = 0, smem_max = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (smem_max <= 0) smem_max = 227 * 1024;
+        const size_t lim = (size_t)smem_max - 1024;
+        while (sweep3d_smem<T>(c->T1, c->NW, c->R2, c->R3) > lim) {
+            if (c->T1 > 4) c->T1 = 4;
+            else if (c->R2 > 1) { c->R2--; c->R3 = c->R2; }
+            else return fail(c, DVM_EINVAL, "3D sweep does not fit in shared memory");
+        }
+    }
+    int mr2 = 1, mr3 = 1;
+    for (int b = 0; b < c->nprob; ++b) {
+        mr2 = std::max(mr2, std::min(c->R2, c->hp[b].n[1]));
+        mr3 = std::max(mr3, std::min(c->R3, c->hp[b].n[2]));
+    }
+    c->max_rows = mr2 * 1000 + mr3;   // packed (R2, R3) maxima
+    double dwall[3] = {0, 0, 0};
+    for (int k = 0; k < grid->nv; ++k)
+        for (int j = 0; j < 3; ++j)
+            if (grid->v[3 * k + j] > 0) dwall[j] += grid->w[k] * grid->v[3 * k + j];
+    const double dinv[3] = {1.0 / dwall[0], 1.0 / dwall[1], 1.0 / dwall[2]};
+    // group weight sums for the start state: [nprob][8][G][4]
+    std::vector<double> qw((size_t)c->nprob * NO * G * 4, 0.0);
+    for (int b = 0; b < c->nprob; ++b)
+        for (int q = 0; q < NO; ++q)
+            for (int m = 0; m < nvo; ++m) {
+                const int k = group[q][m];
+                const int gg = m / c->GL;
+                double* d = &qw[(((size_t)b * NO + q) * G + gg) * 4];
+                d[0] += grid->w[k];
+                for (int j = 0; j < 3; ++j) d[1 + j] += grid->w[k] * grid->v[3 * k + j];
+            }
+    std::vector<Prob3D<T>> probs(c->nprob);
+    std::vector<SweepItem3> items;
+    std::vector<int> blk_prob, blk_start;
+    int prog_total = 0;
+    c->prog_offset.assign(c->nprob, 0);
+    for (int b = 0; b < c->nprob; ++b) {
+        HostProb& H = c->hp[b];
+        Prob3D<T>& P = probs[b];
+        std::memset(&P, 0, sizeof(P));
+        P.n1 = H.n[0];
+        P.n2 = H.n[1];
+        P.n3 = H.n[2];
+        P.N = H.N;
+        P.R2 = std::min(c->R2, P.n2);
+        P.R3 = std::min(c->R3, P.n3);
+        P.np2 = (P.n2 + P.R2 - 1) / P.R2;
+        P.np3 = (P.n3 + P.R3 - 1) / P.R3;
+        P.ngroups = G;
+        P.lateral = c->opt.lateral_bc;
+        P.order = c->opt.stencil_order;
+        P.kn = H.kn;
+        P.nu = H.nu;
+        P.dx = H.dx;
+        for (int j = 0; j < 3; ++j) P.dinv[j] = dinv[j];
+        const size_t N = H.N;
+        const size_t n1 = P.n1, n2 = P.n2, n3 = P.n3;
+        uint16_t* code = (uint16_t*)dev_alloc(c, N * sizeof(uint16_t));
+        P.src = (T*)dev_alloc(c, N * 4 * sizeof(T));
+        P.E = (T*)dev_alloc(c, N * 8 * sizeof(T));
+        P.P = (T*)dev_alloc(c, (size_t)NO * G * 4 * N * sizeof(T));
+        P.gx1 = (T*)dev_alloc(c, (size_t)2 * NO * n3 * n2 * 2 * NL * sizeof(T));
+        P.gy = (T*)dev_alloc(c, (size_t)2 * NO * n3 * n1 * 2 * NL * sizeof(T));
+        P.gz = (T*)dev_alloc(c, (size_t)2 * NO * n2 * n1 * 2 * NL * sizeof(T));
+        const size_t ey_sz = (size_t)NO * P.np3 * std::max(P.np2 - 1, 1) * P.R3 * n1 * 2 * NL;
+        const size_t ez_sz = (size_t)NO * P.np2 * std::max(P.np3 - 1, 1) * P.R2 * n1 * 2 * NL;
+        P.ey = (T*)dev_alloc(c, ey_sz * sizeof(T));
+        P.ez = (T*)dev_alloc(c, ez_sz * sizeof(T));
+        T* lanec = (T*)dev_alloc(c, (size_t)NO * NL * kLaneConsts3 * sizeof(T));
+        P.fin_nblocks = (int)((N + kFinBlock - 1) / kFinBlock);
+        P.fin_block0 = (int)blk_prob.size();
+        P.kpart = (double*)dev_alloc(c, (size_t)P.fin_nblocks * sizeof(double));
+        P.kval = (double*)dev_alloc(c, 3 * sizeof(double));
+        P.fin_counter = (unsigned int*)dev_alloc(c, sizeof(unsigned int));
+        if (!code || !P.src || !P.E || !P.P || !P.gx1 || !P.gy || !P.gz || !P.ey || !P.ez || !lanec || !P.kpart ||
+            !P.kval || !P.fin_counter)
+            return fail(c, DVM_ENOMEM, "device allocation failed");
+        P.code = code;
+        P.lanec = lanec;
+        cudaError_t e;
+        if ((e = cudaMemcpyAsync(code, H.code.data(), N * sizeof(uint16_t), cudaMemcpyHostToDevice, c->stream)) ||
+            (e = cudaMemsetAsync(P.fin_counter, 0, sizeof(unsigned int), c->stream)) ||
+            (e = cudaMemsetAsync(P.kval, 0, 3 * sizeof(double), c->stream)) ||
+            (e = cudaMemsetAsync(P.ey, 0, ey_sz * sizeof(T), c->stream)) ||
+            (e = cudaMemsetAsync(P.ez, 0, ez_sz * sizeof(T), c->stream)))
+            return cuda_fail(c, e, "upload");
+        c->h2d_bytes += N * sizeof(uint16_t);
+        std::vector<T> lc((size_t)NO * NL * kLaneConsts3, T(0));
+        const double c0o = (P.order == 2) ? 1.5 : 1.0;
+        for (int q = 0; q < NO; ++q)
+            for (int l = 0; l < NL; ++l) {
+                double v[3], w;
+                if (l < nvo) {
+                    const int k = group[q][l];
+                    for (int j = 0; j < 3; ++j) v[j] = grid->v[3 * k + j];
+                    w = grid->w[k];
+                } else {   // padding lane: finite values, zero weight
+                    for (int j = 0; j < 3; ++j) v[j] = ((q >> j) & 1) ? -1.0 : 1.0;
+                    w = 0.0;
+                }
+                T* d = &lc[((size_t)q * NL + l) * kLaneConsts3];
+                double av[3];
+                for (int j = 0; j < 3; ++j) {
+                    av[j] = std::fabs(v[j]) / H.dx;
+                    d[j] = (T)v[j];
+                    d[3 + j] = (T)av[j];
+                    d[7 + j] = (T)(w * v[j]);
+                }
+                d[6] = (T)w;
+                for (int rs = 0; rs < 8; ++rs) {
+                    double den = H.nu;
+                    for (int j = 0; j < 3; ++j) den += (((rs >> j) & 1) ? 1.0 : c0o) * av[j];
+                    d[10 + rs] = (T)(1.0 / den);
+                }
+            }
+        if ((e = cudaMemcpyAsync(lanec, lc.data(), lc.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream)) ||
+            (e = cudaStreamSynchronize(c->stream)))
+            return cuda_fail(c, e, "upload lane constants");
+        c->h2d_bytes += lc.size() * sizeof(T);
+        for (int k = 0; k < P.fin_nblocks; ++k) {
+            blk_prob.push_back(b);
+            blk_start.push_back(k * kFinBlock);
+        }
+        c->prog_offset[b] = 1 + prog_total;
+        prog_total += NO * G * P.np3 * P.np2;
+        c->kval_dev.push_back(P.kval);
+    }
+    // ---- items ordered by pencil level (a pencil waits only on lower levels)
+    int maxlevel = 0;
+    for (int b = 0; b < c->nprob; ++b) maxlevel = std::max(maxlevel, probs[b].np2 + probs[b].np3 - 2);
+    for (int lev = 0; lev <= maxlevel; ++lev)
+        for (int b = 0; b < c->nprob; ++b)
+            for (int p3 = 0; p3 < probs[b].np3; ++p3) {
+                const int p2 = lev - p3;
+                if (p2 < 0 || p2 >= probs[b].np2) continue;
+                for (int q = 0; q < NO; ++q)
+                    for (int gg = 0; gg < G; ++gg) items.push_back({b, q, p2, p3, gg, 0, 0, 0});
+            }
+    c->nitems = (int)items.size();
+    c->counters_bytes = sizeof(int) * (size_t)(1 + prog_total);
+    c->counters_dev = (int*)dev_alloc(c, c->counters_bytes);
+    c->status_dev = (int*)dev_alloc(c, sizeof(int));
+    c->items_dev = (SweepItem*)dev_alloc(c, items.size() * sizeof(SweepItem3));
+    c->fin_blocks = (int)blk_prob.size();
+    c->blk_prob_dev = (int*)dev_alloc(c, blk_prob.size() * sizeof(int));
+    c->blk_start_dev = (int*)dev_alloc(c, blk_start.size() * sizeof(int));
+    c->qw_dev = (double*)dev_alloc(c, qw.size() * sizeof(double));
+    size_t maxN = 0;
+    for (auto& H : c->hp) maxN = std::max(maxN, (size_t)H.N);
+    c->scratch_bytes = maxN * 6 * sizeof(double);
+    c->scratch_dev = (double*)dev_alloc(c, c->scratch_bytes);
+    c->probs_dev = dev_alloc(c, probs.size() * sizeof(Prob3D<T>));
+    if (!c->counters_dev || !c->status_dev || !c->items_dev || !c->blk_prob_dev || !c->blk_start_dev ||
+        !c->qw_dev || !c->scratch_dev || !c->probs_dev)
+        return fail(c, DVM_ENOMEM, "device allocation failed");
+    for (int b = 0; b < c->nprob; ++b) probs[b].prog = c->counters_dev + c->prog_offset[b];
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(c->items_dev, items.data(), items.size() * sizeof(SweepItem3), cudaMemcpyHostToDevice, c->stream)) ||
+        (e = cudaMemcpyAsync(c->blk_prob_dev, blk_prob.data(), blk_prob.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream)) ||
+        (e = cudaMemcpyAsync(c->blk_start_dev, blk_start.data(), blk_start.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream)) ||
+        (e = cudaMemcpyAsync(c->qw_dev, qw.data(), qw.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream)) ||
+        (e = cudaMemcpyAsync(c->probs_dev, probs.data(), probs.size() * sizeof(Prob3D<T>), cudaMemcpyHostToDevice, c->stream)) ||
+        (e = cudaMemsetAsync(c->status_dev, 0, sizeof(int), c->stream)) ||
+        (e = cudaStreamSynchronize(c->stream)))
+        return cuda_fail(c, e, "upload");
+    c->h2d_bytes += items.size() * sizeof(SweepItem3) + (blk_prob.size() + blk_start.size()) * sizeof(int) +
+                    qw.size() * sizeof(double) + probs.size() * sizeof(Prob3D<T>);
+    c->probs_host.assign((const char*)probs.data(), (const char*)probs.data() + probs.size() * sizeof(Prob3D<T>));
+    int per_sm = 0;
+    e = sweep3d_occupancy<T>(c->T1, c->NW, mr2, mr3, &per_sm);
+    if (e != cudaSuccess) return cuda_fail(c, e, "occupancy");
+    if (per_sm < 1) return fail(c, DVM_EINVAL, "3D sweep kernel does not fit on an SM with these pencils");
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    c->sweep_grid = std::max(1, std::min(c->nitems, per_sm * sms));
+    for (int b = 0; b < c->nprob; ++b) {
+        const Prob3D<T>* pd = (const Prob3D<T>*)c->probs_dev + b;
+        e = launch_init3d<T>(pd, NL, c->qw_dev + (size_t)b * NO * G * 4, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+    }
+    FinArgs3D<T> fa{(const Prob3D<T>*)c->probs_dev, c->blk_prob_dev, c->blk_start_dev, c->status_dev};
+    e = launch_finalize3d<T>(fa, c->fin_blocks, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernel");
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "init");
+    return DVM_OK;
+}
+
+template <typename T>
+dvm_status enqueue_iter_3d(dvm_ctx* c);
+
 cudaEvent_t take_event(dvm_ctx* c) {
     const size_t used = c->ev_marks.size();
     if (used < c->ev_pool.size()) return c->ev_pool[used];
@@ -441,7 +688,38 @@ dvm_status enqueue_iter_2d(dvm_ctx* c) {
     return DVM_OK;
 }
 
+template <typename T>
+dvm_status enqueue_iter_3d(dvm_ctx* c) {
+    cudaError_t e = cudaMemsetAsync(c->counters_dev, 0, c->counters_bytes, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "memset counters");
+    SweepArgs3D<T> a;
+    a.prob = (const Prob3D<T>*)c->probs_dev;
+    a.items = (const SweepItem3*)c->items_dev;
+    a.nitems = c->nitems;
+    a.NL = c->NL;
+    a.GL = c->GL;
+    a.T1 = c->T1;
+    a.maxR2 = c->max_rows / 1000;
+    a.maxR3 = c->max_rows % 1000;
+    a.parity = (int)(c->iters & 1);
+    a.ticket = c->counters_dev;
+    a.status = c->status_dev;
+    a.timeout_ns = c->timeout_ns;
+    a.withhold_item = c->withhold_item;
+    if ((e = mark(c)) != cudaSuccess) return cuda_fail(c, e, "event");
+    e = launch_sweep3d<T>(a, c->sweep_grid, c->NW, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sweep kernel");
+    if ((e = mark(c)) != cudaSuccess) return cuda_fail(c, e, "event");
+    FinArgs3D<T> fa{(const Prob3D<T>*)c->probs_dev, c->blk_prob_dev, c->blk_start_dev, c->status_dev};
+    e = launch_finalize3d<T>(fa, c->fin_blocks, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernel");
+    if ((e = mark(c)) != cudaSuccess) return cuda_fail(c, e, "event");
+    c->iters++;
+    return DVM_OK;
+}
+
 dvm_status enqueue_iter(dvm_ctx* c) {
+    if (c->dims == 3) return c->prec == DVM_FP32 ? enqueue_iter_3d<float>(c) : enqueue_iter_3d<double>(c);
     return c->prec == DVM_FP32 ? enqueue_iter_2d<float>(c) : enqueue_iter_2d<double>(c);
 }
 
@@ -449,9 +727,7 @@ dvm_status enqueue_iter(dvm_ctx* c) {
 dvm_status collect(dvm_ctx* c) {
     cudaError_t e;
     for (int b = 0; b < c->nprob; ++b) {
-        const double* kv;
-        if (c->prec == DVM_FP32) kv = ((const Prob2D<float>*)c->probs_host.data())[b].kval;
-        else kv = ((const Prob2D<double>*)c->probs_host.data())[b].kval;
+        const double* kv = c->kval_dev[b];
         e = cudaMemcpyAsync(c->kval_host + 3 * b, kv, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "read permeability");
     }
@@ -548,7 +824,6 @@ dvm_status dvm_create_batch(int nprob, const dvm_geometry* geoms, const double* 
     if (nprob < 1 || !geoms || !kn) return reject(DVM_EINVAL, "no problems");
     const int dims = geoms[0].dims;
     if (dims != 2 && dims != 3) return reject(DVM_EINVAL, "dims must be 2 or 3");
-    if (dims == 3) return reject(DVM_EINVAL, "3D problems are not supported by this build");
     if (c->opt.precision != DVM_FP64 && c->opt.precision != DVM_FP32) return reject(DVM_EINVAL, "precision");
     if (c->opt.stencil_order != 1 && c->opt.stencil_order != 2) return reject(DVM_EINVAL, "stencil_order");
     if (c->opt.lateral_bc != 0 && c->opt.lateral_bc != 1) return reject(DVM_EINVAL, "lateral_bc");
@@ -598,7 +873,9 @@ dvm_status dvm_create_batch(int nprob, const dvm_geometry* geoms, const double* 
         delete c;
         return e == cudaErrorMemoryAllocation ? DVM_ENOMEM : DVM_ECUDA;
     }
-    dvm_status s = (c->prec == DVM_FP32) ? build_2d<float>(c, geoms, grid) : build_2d<double>(c, geoms, grid);
+    dvm_status s;
+    if (dims == 3) s = (c->prec == DVM_FP32) ? build_3d<float>(c, geoms, grid) : build_3d<double>(c, geoms, grid);
+    else s = (c->prec == DVM_FP32) ? build_2d<float>(c, geoms, grid) : build_2d<double>(c, geoms, grid);
     if (s != DVM_OK) {
         cudaStreamSynchronize(c->stream);
         free_all(c);
@@ -677,8 +954,14 @@ dvm_status dvm_moments_at(dvm_ctx* c, int prob, double* rho, double* u, int on_d
     double* drho = on_device ? rho : c->scratch_dev;
     double* du = on_device ? u : c->scratch_dev + N;
     cudaError_t e;
-    if (c->prec == DVM_FP32) e = launch_moments2d<float>((const Prob2D<float>*)c->probs_dev + prob, drho, du, c->stream);
-    else e = launch_moments2d<double>((const Prob2D<double>*)c->probs_dev + prob, drho, du, c->stream);
+    if (c->dims == 3) {
+        if (c->prec == DVM_FP32) e = launch_moments3d<float>((const Prob3D<float>*)c->probs_dev + prob, drho, du, c->stream);
+        else e = launch_moments3d<double>((const Prob3D<double>*)c->probs_dev + prob, drho, du, c->stream);
+    } else if (c->prec == DVM_FP32) {
+        e = launch_moments2d<float>((const Prob2D<float>*)c->probs_dev + prob, drho, du, c->stream);
+    } else {
+        e = launch_moments2d<double>((const Prob2D<double>*)c->probs_dev + prob, drho, du, c->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "moments kernel");
     if (!on_device) {
         if ((e = cudaMemcpyAsync(rho, drho, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream)) ||
@@ -699,13 +982,19 @@ dvm_status dvm_wall_density_at(dvm_ctx* c, int prob, double* rhos) {
     if (!c || prob < 0 || prob >= c->nprob || !rhos) return DVM_EINVAL;
     const size_t N = c->hp[prob].N;
     cudaError_t e;
-    if (c->prec == DVM_FP32) e = launch_wall2d<float>((const Prob2D<float>*)c->probs_dev + prob, c->scratch_dev, c->stream);
-    else e = launch_wall2d<double>((const Prob2D<double>*)c->probs_dev + prob, c->scratch_dev, c->stream);
+    if (c->dims == 3) {
+        if (c->prec == DVM_FP32) e = launch_wall3d<float>((const Prob3D<float>*)c->probs_dev + prob, c->scratch_dev, c->stream);
+        else e = launch_wall3d<double>((const Prob3D<double>*)c->probs_dev + prob, c->scratch_dev, c->stream);
+    } else if (c->prec == DVM_FP32) {
+        e = launch_wall2d<float>((const Prob2D<float>*)c->probs_dev + prob, c->scratch_dev, c->stream);
+    } else {
+        e = launch_wall2d<double>((const Prob2D<double>*)c->probs_dev + prob, c->scratch_dev, c->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "wall kernel");
-    if ((e = cudaMemcpyAsync(rhos, c->scratch_dev, N * 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream)) ||
+    if ((e = cudaMemcpyAsync(rhos, c->scratch_dev, N * 2 * c->dims * sizeof(double), cudaMemcpyDeviceToHost, c->stream)) ||
         (e = cudaStreamSynchronize(c->stream)))
         return cuda_fail(c, e, "read wall densities");
-    c->d2h_bytes += (long long)N * 4 * sizeof(double);
+    c->d2h_bytes += (long long)N * 2 * c->dims * sizeof(double);
     return DVM_OK;
 }
 

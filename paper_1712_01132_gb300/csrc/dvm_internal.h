@@ -79,6 +79,63 @@ struct FinArgs2D {
     int* status;
 };
 
+// 3D problem.  Octant q has bit j set when s_j < 0.  A pencil is R2 x R3 rows (x2 x x3) swept
+// along x1 in tiles of T1 columns; the velocities of an octant may be split into groups (each
+// group is an independent sweep with its own moment partials).
+template <typename T>
+struct Prob3D {
+    int n1, n2, n3, N;
+    int R2, R3, np2, np3;   // pencil rows and pencil counts
+    int ngroups;            // velocity groups per octant
+    int lateral, order;
+    double kn, nu, dx;
+    double dinv[3];
+    const uint16_t* code;   // [N]
+    T* src;                 // [N][4]  (nu rho', 2 nu u1 + 1, 2 nu u2, 2 nu u3)
+    T* E;                   // [N][8]  wall terms, index 2 j + u (6 used)
+    T* P;                   // [8][G][4][N] moment partials per octant and velocity group
+    T* gx1;                 // [2][8][n3 * n2][2][NL] x1 ghosts (parity, octant, row (k, j), layer, lane)
+    T* gy;                  // [2][8][n3 * n1][2][NL] x2 ghosts (row (k, i))
+    T* gz;                  // [2][8][n2 * n1][2][NL] x3 ghosts (row (j, i))
+    T* ey;                  // [8][np3][np2 - 1][R3][n1][2][NL] x2 edges between pencils
+    T* ez;                  // [8][np2][np3 - 1][R2][n1][2][NL] x3 edges between pencils
+    int* prog;              // [8][G][np3][np2] tiles completed
+    const T* lanec;         // [8][NL][kLaneConsts3]
+    double* kpart;
+    double* kval;
+    int fin_block0;
+    int fin_nblocks;
+    unsigned int* fin_counter;
+};
+
+constexpr int kLaneConsts3 = 20;    // v1 v2 v3 a1 a2 a3 W Wv1 Wv2 Wv3 R[8] pad pad
+
+struct SweepItem3 { int prob, oct, p2, p3, group, pad0, pad1, pad2; };
+
+template <typename T>
+struct SweepArgs3D {
+    const Prob3D<T>* prob;
+    const SweepItem3* items;
+    int nitems;
+    int NL;                     // lanes per octant (all groups)
+    int GL;                     // lanes per velocity group (= 32 x warps per CTA)
+    int T1;
+    int maxR2, maxR3;
+    int parity;
+    int* ticket;
+    int* status;
+    long long timeout_ns;
+    int withhold_item;
+};
+
+template <typename T>
+struct FinArgs3D {
+    const Prob3D<T>* prob;
+    const int* blk_prob;
+    const int* blk_start;
+    int* status;
+};
+
 // Stencil-case encoding of code[x] (2D uses axes 0,1; 3D axes 0..2):
 //   bits 2*(2 j + u) .. +1 : case for axis j with upstream side u (u = 0: upstream is -e_j, i.e.
 //   the sweep sign s_j > 0; u = 1: upstream is +e_j):

@@ -1,0 +1,562 @@
+// kernels3d.cu -- sm_103a kernels of one source iteration (arXiv:1712.01132, Sec. 3.1) in 3D.
+//
+// sweep3d   : step (i) for every octant of discrete velocities (Fig. 1 generalised to octants),
+//             with the quadrature of step (iii) fused in.  A work item is (problem, octant,
+//             velocity group, pencil); a pencil is R2 x R3 rows (x2 x x3) swept along x1 in tiles
+//             of T1 columns.  Items are ordered by pencil level p2 + p3: a pencil waits only on
+//             (p2-1, p3) and (p2, p3-1), which carry lower tickets, so the persistent schedule
+//             cannot deadlock.  One discrete velocity per lane.  Inside a tile the rows are walked
+//             plane by plane (x3), row by row (x2), x1 fastest: every value a point reads is final,
+//             so the result equals the paper's raster scan.
+// finalize3d: sums the octant/group moment partials, forms the FP64 wall densities (Eq. 6), the
+//             next sources and wall terms, and the FP64 sum of u1 for Eq. 11-12.
+// init3d, moments3d, wall3d: start state and readouts.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "dvm_device.cuh"
+#include "dvm_internal.h"
+
+namespace dvm {
+
+namespace {
+
+constexpr int kRec3 = 16;    // record: {a b1 b2 b3} {E1 E2 E3 rsel} {K1x K2x K1y K2y} {K1z K2z - -}
+
+template <typename T> struct V4t;
+template <> struct V4t<float> {
+    using type = float4;
+    static __device__ __forceinline__ float4 make(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+};
+struct alignas(32) d4 { double x, y, z, w; };
+template <> struct V4t<double> {
+    using type = d4;
+    static __device__ __forceinline__ d4 make(double a, double b, double c, double d) { return d4{a, b, c, d}; }
+};
+
+__device__ __forceinline__ float ibits(float, int v) { return __int_as_float(v); }
+__device__ __forceinline__ double ibits(double, int v) { return __longlong_as_double((long long)v); }
+__device__ __forceinline__ int tbits(float v) { return __float_as_int(v); }
+__device__ __forceinline__ int tbits(double v) { return (int)__double_as_longlong(v); }
+
+}  // namespace
+
+template <typename T, int T1>
+__global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
+    using V = typename V4t<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item;
+    __shared__ int s_abort;
+    const int NW = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int MR2 = a.maxR2, MR3 = a.maxR3;
+    const int MROWS = MR2 * MR3;
+    T* rec = reinterpret_cast<T*>(smem_raw);                         // [MROWS][T1][kRec3]
+    T* part = rec + (size_t)MROWS * T1 * kRec3;                      // [NW][MROWS][T1][4]
+    T* carry = part + (size_t)NW * MROWS * T1 * 4;                   // [NW][MROWS][2][32]
+    T* pb = carry + (size_t)NW * MROWS * 2 * 32;                     // [NW][MR2][2][T1][32]
+    T* rtab = pb + (size_t)NW * MR2 * 2 * T1 * 32;                   // [NW][8][32]
+    const size_t NL = (size_t)a.NL;
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_item = ld_volatile(a.status) ? a.nitems : atomicAdd(a.ticket, 1);
+            s_abort = 0;
+        }
+        __syncthreads();
+        const int it = s_item;
+        if (it >= a.nitems) return;
+        const SweepItem3 item = a.items[it];
+        const Prob3D<T>* __restrict__ P = a.prob + item.prob;
+        const int q = item.oct, g = item.group, p2 = item.p2, p3 = item.p3;
+        const int n1 = P->n1, n2 = P->n2, n3 = P->n3;
+        const int N = P->N;
+        const int np2 = P->np2, np3 = P->np3;
+        const int s1n = q & 1, s2n = (q >> 1) & 1, s3n = (q >> 2) & 1;
+        const int j0 = p2 * P->R2, k0 = p3 * P->R3;
+        const int nr2 = min(P->R2, n2 - j0), nr3 = min(P->R3, n3 - k0);
+        const T K1o = P->order == 2 ? T(2) : T(1);
+        const T K2o = P->order == 2 ? T(-0.5) : T(0);
+        const int lv = g * a.GL + warp * 32 + lane;      // velocity lane within the octant
+        const T* lcp = P->lanec + ((size_t)q * NL + lv) * kLaneConsts3;
+        const T v1 = lcp[0], v2 = lcp[1], v3 = lcp[2], a1 = lcp[3], a2 = lcp[4], a3 = lcp[5];
+        const T W = lcp[6], Wv1 = lcp[7], Wv2 = lcp[8], Wv3 = lcp[9];
+        T* my_rtab = rtab + (size_t)warp * 8 * 32 + lane;
+#pragma unroll
+        for (int rs = 0; rs < 8; ++rs) my_rtab[rs * 32] = lcp[10 + rs];
+        const int par = a.parity;
+        const int G = P->ngroups;
+        int* prog = P->prog + ((size_t)q * G + g) * np3 * np2;
+        // x1 upstream of the first tile: x1 ghost layers (oriented rows (k, j))
+        {
+            const T* gx = P->gx1 + (((size_t)par * 8 + q) * n3 * n2) * 2 * NL;
+            for (int kk = 0; kk < nr3; ++kk)
+                for (int jj = 0; jj < nr2; ++jj) {
+                    const size_t row = (size_t)(k0 + kk) * n2 + (j0 + jj);
+                    T* cr = carry + ((size_t)(warp * MROWS + kk * MR2 + jj) * 2) * 32 + lane;
+                    cr[0] = gx[(row * 2 + 0) * NL + lv];
+                    cr[32] = gx[(row * 2 + 1) * NL + lv];
+                }
+        }
+        const int ntiles = (n1 + T1 - 1) / T1;
+        for (int t = 0; t < ntiles; ++t) {
+            const int c0 = t * T1;
+            const int width = min(T1, n1 - c0);
+            if (threadIdx.x == 0) {
+                bool ok = true;
+                if (p2 > 0) ok = wait_geq(prog + p3 * np2 + p2 - 1, t + 1, a.status, a.timeout_ns);
+                if (ok && p3 > 0) ok = wait_geq(prog + (p3 - 1) * np2 + p2, t + 1, a.status, a.timeout_ns);
+                if (!ok) s_abort = 1;
+            }
+            // records of the tile's points for this octant
+            const int npts = nr3 * MR2 * T1;
+            for (int idx = threadIdx.x; idx < npts; idx += blockDim.x) {
+                const int kk = idx / (MR2 * T1);
+                const int rem = idx - kk * MR2 * T1;
+                const int jj = rem / T1;
+                const int i = rem - jj * T1;
+                V r0 = V4t<T>::make(0, 0, 0, 0), r1 = r0, r2 = r0, r3 = r0;
+                if (jj < nr2 && i < width) {
+                    const int ic = c0 + i;
+                    const int x = s1n ? n1 - 1 - ic : ic;
+                    const int y = s2n ? n2 - 1 - (j0 + jj) : (j0 + jj);
+                    const int z = s3n ? n3 - 1 - (k0 + kk) : (k0 + kk);
+                    const int id = (z * n2 + y) * n1 + x;
+                    const uint16_t code = P->code[id];
+                    if (!(code & kSolidBit)) {
+                        const V s = reinterpret_cast<const V*>(P->src)[id];
+                        const V e0 = reinterpret_cast<const V*>(P->E)[2 * (size_t)id];
+                        const V e1 = reinterpret_cast<const V*>(P->E)[2 * (size_t)id + 1];
+                        const int ca = (code >> (2 * (0 + s1n))) & 3;
+                        const int cb = (code >> (2 * (2 + s2n))) & 3;
+                        const int cc = (code >> (2 * (4 + s3n))) & 3;
+                        const T E1 = s1n ? e0.y : e0.x;
+                        const T E2 = s2n ? e0.w : e0.z;
+                        const T E3 = s3n ? e1.y : e1.x;
+                        const int rs = (ca == 2) | ((cb == 2) << 1) | ((cc == 2) << 2);
+                        r0 = V4t<T>::make(s.x, s.y, s.z, s.w);
+                        r1 = V4t<T>::make(E1, E2, E3, ibits(T(0), rs));
+                        r2 = V4t<T>::make(ca == 2 ? T(0) : K1o, ca == 0 ? K2o : T(0), cb == 2 ? T(0) : K1o,
+                                          cb == 0 ? K2o : T(0));
+                        r3 = V4t<T>::make(cc == 2 ? T(0) : K1o, cc == 0 ? K2o : T(0), T(0), T(0));
+                    }
+                }
+                V* R = reinterpret_cast<V*>(rec + (size_t)((kk * MR2 + jj) * T1 + i) * kRec3);
+                R[0] = r0;
+                R[1] = r1;
+                R[2] = r2;
+                R[3] = r3;
+            }
+            __syncthreads();
+            if (s_abort) return;
+            // x3 upstream planes of the first plane of the pencil: the pencil below in x3 or the
+            // x3 ghost layers (periodic or specular, Eq. 8)
+            {
+                const T* zb = (p3 == 0)
+                    ? P->gz + (((size_t)par * 8 + q) * n2 * n1) * 2 * NL
+                    : P->ez + ((((size_t)q * np2 + p2) * (np3 - 1) + (p3 - 1)) * P->R2 * n1) * 2 * NL;
+                for (int jj = 0; jj < nr2; ++jj)
+                    for (int i = 0; i < width; ++i) {
+                        const size_t row = (p3 == 0) ? ((size_t)(j0 + jj) * n1 + (c0 + i)) : ((size_t)jj * n1 + (c0 + i));
+                        T* d = pb + ((((size_t)warp * MR2 + jj) * 2) * T1 + i) * 32 + lane;
+                        d[0] = __ldcg(zb + (row * 2 + 0) * NL + lv);
+                        d[(size_t)T1 * 32] = __ldcg(zb + (row * 2 + 1) * NL + lv);
+                    }
+            }
+            for (int kk = 0; kk < nr3; ++kk) {
+                // x2 upstream rows of the first row of this plane
+                T rb1[T1], rb2[T1];
+                {
+                    const T* yb = (p2 == 0)
+                        ? P->gy + (((size_t)par * 8 + q) * n3 * n1) * 2 * NL
+                        : P->ey + ((((size_t)q * np3 + p3) * (np2 - 1) + (p2 - 1)) * P->R3 * n1) * 2 * NL;
+                    const size_t rowbase = (p2 == 0) ? (size_t)(k0 + kk) * n1 : (size_t)kk * n1;
+#pragma unroll
+                    for (int i = 0; i < T1; ++i) {
+                        if (i < width) {
+                            rb1[i] = __ldcg(yb + ((rowbase + c0 + i) * 2 + 0) * NL + lv);
+                            rb2[i] = __ldcg(yb + ((rowbase + c0 + i) * 2 + 1) * NL + lv);
+                        } else {
+                            rb1[i] = T(0);
+                            rb2[i] = T(0);
+                        }
+                    }
+                }
+                for (int jj = 0; jj < nr2; ++jj) {
+                    T* cr = carry + ((size_t)(warp * MROWS + kk * MR2 + jj) * 2) * 32 + lane;
+                    T hp1 = cr[0], hp2 = cr[32];
+                    T* zr = pb + ((((size_t)warp * MR2 + jj) * 2) * T1) * 32 + lane;   // [2][T1][32]
+                    const T* rrow = rec + (size_t)((kk * MR2 + jj) * T1) * kRec3;
+                    T* prow = part + ((size_t)(warp * MROWS + kk * MR2 + jj) * T1) * 4;
+#pragma unroll
+                    for (int i0 = 0; i0 < T1; i0 += 4) {
+                        T m0[4], m1[4], m2[4], m3[4];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const int i = i0 + c;
+                            if (i < width) {
+                                const V* R = reinterpret_cast<const V*>(rrow + i * kRec3);
+                                const V A = R[0], B = R[1], C = R[2], D = R[3];
+                                const T z1 = zr[(size_t)i * 32];
+                                const T z2 = zr[((size_t)T1 + i) * 32];
+                                const T S = fma(A.w, v3, fma(A.z, v2, fma(A.y, v1, A.x)));
+                                const T t1 = fma(C.x, hp1, fma(C.y, hp2, B.x));
+                                const T t2 = fma(C.z, rb1[i], fma(C.w, rb2[i], B.y));
+                                const T t3 = fma(D.x, z1, fma(D.y, z2, B.z));
+                                const T num = fma(a3, t3, fma(a2, t2, fma(a1, t1, S)));
+                                const T h = num * my_rtab[tbits(B.w) * 32];
+                                hp2 = hp1;
+                                hp1 = h;
+                                rb2[i] = rb1[i];
+                                rb1[i] = h;
+                                zr[((size_t)T1 + i) * 32] = z1;
+                                zr[(size_t)i * 32] = h;
+                                m0[c] = W * h;
+                                m1[c] = Wv1 * h;
+                                m2[c] = Wv2 * h;
+                                m3[c] = Wv3 * h;
+                            } else {
+                                m0[c] = m1[c] = m2[c] = m3[c] = T(0);
+                            }
+                        }
+                        const T r0 = reduce_scatter<T, 4>(m0, lane);
+                        const T r1 = reduce_scatter<T, 4>(m1, lane);
+                        const T r2 = reduce_scatter<T, 4>(m2, lane);
+                        const T r3 = reduce_scatter<T, 4>(m3, lane);
+                        const int p = lane >> 3;
+                        if ((lane & 7) == 0 && i0 + p < width) {
+                            T* d = prow + (i0 + p) * 4;
+                            d[0] = r0;
+                            d[1] = r1;
+                            d[2] = r2;
+                            d[3] = r3;
+                        }
+                    }
+                    cr[0] = hp1;
+                    cr[32] = hp2;
+                }
+                // x2 edge of this plane for the pencil above in x2, or the x2 ghost layers of the
+                // next iteration (periodic: same octant; specular: octant with s2 flipped)
+                {
+                    T* et;
+                    size_t rowbase;
+                    if (p2 < np2 - 1) {
+                        et = P->ey + ((((size_t)q * np3 + p3) * (np2 - 1) + p2) * P->R3 * n1) * 2 * NL;
+                        rowbase = (size_t)kk * n1;
+                    } else {
+                        const int qy = (P->lateral == 1) ? q : (q ^ 2);
+                        et = P->gy + (((size_t)(par ^ 1) * 8 + qy) * n3 * n1) * 2 * NL;
+                        rowbase = (size_t)(k0 + kk) * n1;
+                    }
+#pragma unroll
+                    for (int i = 0; i < T1; ++i) {
+                        if (i < width) {
+                            et[((rowbase + c0 + i) * 2 + 0) * NL + lv] = rb1[i];
+                            et[((rowbase + c0 + i) * 2 + 1) * NL + lv] = rb2[i];
+                        }
+                    }
+                }
+            }
+            // x3 edge for the pencil above in x3, or the x3 ghost layers of the next iteration
+            {
+                T* et;
+                const bool last = (p3 == np3 - 1);
+                if (!last) {
+                    et = P->ez + ((((size_t)q * np2 + p2) * (np3 - 1) + p3) * P->R2 * n1) * 2 * NL;
+                } else {
+                    const int qz = (P->lateral == 1) ? q : (q ^ 4);
+                    et = P->gz + (((size_t)(par ^ 1) * 8 + qz) * n2 * n1) * 2 * NL;
+                }
+                for (int jj = 0; jj < nr2; ++jj)
+                    for (int i = 0; i < width; ++i) {
+                        const size_t row = last ? ((size_t)(j0 + jj) * n1 + (c0 + i)) : ((size_t)jj * n1 + (c0 + i));
+                        const T* s = pb + ((((size_t)warp * MR2 + jj) * 2) * T1 + i) * 32 + lane;
+                        et[(row * 2 + 0) * NL + lv] = s[0];
+                        et[(row * 2 + 1) * NL + lv] = s[(size_t)T1 * 32];
+                    }
+            }
+            if (t == ntiles - 1) {
+                T* gx = P->gx1 + (((size_t)(par ^ 1) * 8 + q) * n3 * n2) * 2 * NL;
+                for (int kk = 0; kk < nr3; ++kk)
+                    for (int jj = 0; jj < nr2; ++jj) {
+                        const size_t row = (size_t)(k0 + kk) * n2 + (j0 + jj);
+                        const T* cr = carry + ((size_t)(warp * MROWS + kk * MR2 + jj) * 2) * 32 + lane;
+                        gx[(row * 2 + 0) * NL + lv] = cr[0];
+                        gx[(row * 2 + 1) * NL + lv] = cr[32];
+                    }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0 && it != a.withhold_item) {
+                __threadfence();
+                st_release_gpu(prog + p3 * np2 + p2, t + 1);
+            }
+            // moment partials of this octant and group: warp sums in warp order
+            const int tot = nr3 * nr2 * width * 4;
+            for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+                const int mm = idx & 3;
+                const int pi = idx >> 2;
+                const int i = pi % width;
+                const int r = pi / width;
+                const int jj = r % nr2;
+                const int kk = r / nr2;
+                T s = T(0);
+                for (int w = 0; w < NW; ++w) s += part[((size_t)(w * MROWS + kk * MR2 + jj) * T1 + i) * 4 + mm];
+                const int ic = c0 + i;
+                const int x = s1n ? n1 - 1 - ic : ic;
+                const int y = s2n ? n2 - 1 - (j0 + jj) : (j0 + jj);
+                const int z = s3n ? n3 - 1 - (k0 + kk) : (k0 + kk);
+                P->P[(((size_t)q * G + g) * 4 + mm) * N + ((size_t)z * n2 + y) * n1 + x] = s;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// rho'_s of face (y, axis j, side sigma) in FP64 from the octant/group partials of u_j at y
+template <typename T>
+__device__ __forceinline__ double wall_density3(const Prob3D<T>* P, int y, int j, int sigma) {
+    double num = 0.0;
+    const int G = P->ngroups;
+    for (int q = 0; q < 8; ++q) {
+        if (((q >> j) & 1) != (sigma < 0 ? 1 : 0)) continue;
+        for (int g = 0; g < G; ++g) num += (double)P->P[(((size_t)q * G + g) * 4 + 1 + j) * P->N + y];
+    }
+    return sigma * num * P->dinv[j];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) finalize3d_kernel(const FinArgs3D<T> a) {
+    using V = typename V4t<T>::type;
+    __shared__ double s_red[8];
+    __shared__ int s_last;
+    const int b = a.blk_prob[blockIdx.x];
+    const Prob3D<T>* __restrict__ P = a.prob + b;
+    const int id = a.blk_start[blockIdx.x] + threadIdx.x;
+    double u1d = 0.0;
+    if (id < P->N) {
+        const uint16_t code = P->code[id];
+        V s = V4t<T>::make(0, 0, 0, 0), e0 = s, e1 = s;
+        if (!(code & kSolidBit)) {
+            const size_t N = P->N;
+            const int G = P->ngroups;
+            T mo[4] = {T(0), T(0), T(0), T(0)};
+            for (int q = 0; q < 8; ++q)
+                for (int g = 0; g < G; ++g)
+#pragma unroll
+                    for (int mm = 0; mm < 4; ++mm) mo[mm] += P->P[(((size_t)q * G + g) * 4 + mm) * N + id];
+            const T nu = (T)P->nu;
+            s = V4t<T>::make(nu * mo[0], T(2) * nu * mo[1] + T(1), T(2) * nu * mo[2], T(2) * nu * mo[3]);
+            u1d = (double)mo[1];
+            const int n1 = P->n1, n2 = P->n2, n3 = P->n3;
+            const int c[3] = {id % n1, (id / n1) % n2, id / (n1 * n2)};
+            const int nn[3] = {n1, n2, n3};
+            T ev[6];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int cs = (code >> (2 * (2 * j + u))) & 3;
+                    const int sigma = u ? 1 : -1;
+                    double val = 0.0;
+                    if (cs == 2) {
+                        val = wall_density3(P, id, j, sigma) + (j == 0 ? sigma * P->dx : 0.0);
+                    } else if (cs == 1) {
+                        int cc[3] = {c[0], c[1], c[2]};
+                        int sg = sigma;
+                        int l = c[j] + sigma;
+                        if (l < 0 || l >= nn[j]) {
+                            if (j == 0 || P->lateral == 1) l = (l + nn[j]) % nn[j];
+                            else { l = (l < 0) ? -1 - l : 2 * nn[j] - 1 - l; sg = -sigma; }
+                        }
+                        cc[j] = l;
+                        const int nid = (cc[2] * n2 + cc[1]) * n1 + cc[0];
+                        val = -0.5 * (wall_density3(P, nid, j, sg) + (j == 0 ? sigma * P->dx : 0.0));
+                    }
+                    ev[2 * j + u] = (T)val;
+                }
+            }
+            e0 = V4t<T>::make(ev[0], ev[1], ev[2], ev[3]);
+            e1 = V4t<T>::make(ev[4], ev[5], T(0), T(0));
+        }
+        reinterpret_cast<V*>(P->src)[id] = s;
+        reinterpret_cast<V*>(P->E)[2 * (size_t)id] = e0;
+        reinterpret_cast<V*>(P->E)[2 * (size_t)id + 1] = e1;
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) u1d += __shfl_xor_sync(0xffffffffu, u1d, off);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = u1d;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_red[w];
+        P->kpart[blockIdx.x - P->fin_block0] = tot;
+        __threadfence();
+        const unsigned prev = atomicAdd(P->fin_counter, 1u);
+        s_last = (prev == (unsigned)P->fin_nblocks - 1u);
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        double acc = 0.0;
+        for (int k = threadIdx.x; k < P->fin_nblocks; k += blockDim.x) acc += __ldcg(P->kpart + k);
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_red[w];
+            const double gp = tot / (double)P->N;
+            P->kval[0] = 2.0 / sqrt(3.14159265358979323846) * P->kn * gp;
+            P->kval[1] = gp;
+            P->kval[2] = tot;
+            *P->fin_counter = 0u;
+        }
+    }
+}
+
+// Zero-perturbation start in the kernels' source-form variables (h' = x1).
+template <typename T>
+__global__ void init3d_kernel(const Prob3D<T>* P, int NL, const double* qw /*[8][G][4]*/) {
+    const int n1 = P->n1, n2 = P->n2, n3 = P->n3, N = P->N, G = P->ngroups;
+    const size_t nl = NL;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (size_t idx = t0; idx < (size_t)8 * G * 4 * N; idx += stride) {
+        const int id = idx % N;
+        const size_t qgm = idx / N;
+        const double x1 = (id % n1) * P->dx;
+        P->P[idx] = (P->code[id] & kSolidBit) ? T(0) : (T)(x1 * qw[qgm]);
+    }
+    for (size_t idx = t0; idx < (size_t)2 * 8 * n3 * n2 * 2 * nl; idx += stride) {
+        const int layer = (idx / nl) % 2;
+        const int q = (idx / (nl * 2 * n3 * n2)) % 8;
+        const int ico = n1 - 1 - layer;
+        const int col = (q & 1) ? n1 - 1 - ico : ico;
+        P->gx1[idx] = (T)(col * P->dx);
+    }
+    for (size_t idx = t0; idx < (size_t)2 * 8 * n3 * n1 * 2 * nl; idx += stride) {
+        const int ic = (idx / (nl * 2)) % n1;
+        const int q = (idx / (nl * 2 * n3 * n1)) % 8;
+        const int col = (q & 1) ? n1 - 1 - ic : ic;
+        P->gy[idx] = (T)(col * P->dx);
+    }
+    for (size_t idx = t0; idx < (size_t)2 * 8 * n2 * n1 * 2 * nl; idx += stride) {
+        const int ic = (idx / (nl * 2)) % n1;
+        const int q = (idx / (nl * 2 * n2 * n1)) % 8;
+        const int col = (q & 1) ? n1 - 1 - ic : ic;
+        P->gz[idx] = (T)(col * P->dx);
+    }
+}
+
+template <typename T>
+__global__ void moments3d_kernel(const Prob3D<T>* P, double* rho, double* u) {
+    const int N = P->N, G = P->ngroups;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        if (P->code[id] & kSolidBit) {
+            rho[id] = 0.0;
+            for (int j = 0; j < 3; ++j) u[(size_t)j * N + id] = 0.0;
+            continue;
+        }
+        T mo[4] = {T(0), T(0), T(0), T(0)};
+        for (int q = 0; q < 8; ++q)
+            for (int g = 0; g < G; ++g)
+                for (int mm = 0; mm < 4; ++mm) mo[mm] += P->P[(((size_t)q * G + g) * 4 + mm) * N + id];
+        rho[id] = (double)mo[0] - (id % P->n1) * P->dx;
+        for (int j = 0; j < 3; ++j) u[(size_t)j * N + id] = (double)mo[1 + j];
+    }
+}
+
+template <typename T>
+__global__ void wall3d_kernel(const Prob3D<T>* P, double* out) {
+    const int N = P->N;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        const uint16_t code = P->code[id];
+        for (int j = 0; j < 3; ++j)
+            for (int u = 0; u < 2; ++u) {
+                double v = 0.0;
+                if (!(code & kSolidBit) && ((code >> (2 * (2 * j + u))) & 3) == 2)
+                    v = wall_density3(P, id, j, u ? 1 : -1) - (id % P->n1) * P->dx;
+                out[(size_t)(2 * j + u) * N + id] = v;
+            }
+    }
+}
+
+template <typename T>
+size_t sweep3d_smem(int T1, int NW, int R2, int R3) {
+    const size_t rows = (size_t)R2 * R3;
+    return sizeof(T) * (rows * T1 * kRec3 + (size_t)NW * rows * T1 * 4 + (size_t)NW * rows * 2 * 32 +
+                        (size_t)NW * R2 * 2 * T1 * 32 + (size_t)NW * 8 * 32);
+}
+
+template <typename T, int T1>
+static cudaError_t occ3(int NW, int R2, int R3, int* blocks_per_sm) {
+    const size_t smem = sweep3d_smem<T>(T1, NW, R2, R3);
+    cudaError_t e = cudaFuncSetAttribute(sweep3d_kernel<T, T1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep3d_kernel<T, T1>, NW * 32, smem);
+}
+
+template <typename T>
+cudaError_t sweep3d_occupancy(int T1, int NW, int R2, int R3, int* blocks_per_sm) {
+    if (T1 == 4) return occ3<T, 4>(NW, R2, R3, blocks_per_sm);
+    if (T1 == 8) return occ3<T, 8>(NW, R2, R3, blocks_per_sm);
+    return cudaErrorInvalidValue;
+}
+
+template <typename T, int T1>
+static cudaError_t launch3(const SweepArgs3D<T>& a, int grid, int NW, cudaStream_t st) {
+    const size_t smem = sweep3d_smem<T>(T1, NW, a.maxR2, a.maxR3);
+    cudaError_t e = cudaFuncSetAttribute(sweep3d_kernel<T, T1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    sweep3d_kernel<T, T1><<<grid, NW * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_sweep3d(const SweepArgs3D<T>& a, int grid, int NW, cudaStream_t st) {
+    if (a.T1 == 4) return launch3<T, 4>(a, grid, NW, st);
+    if (a.T1 == 8) return launch3<T, 8>(a, grid, NW, st);
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_finalize3d(const FinArgs3D<T>& a, int nblocks, cudaStream_t st) {
+    finalize3d_kernel<T><<<nblocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_init3d(const Prob3D<T>* p, int NL, const double* qw, cudaStream_t st) {
+    init3d_kernel<T><<<608, 256, 0, st>>>(p, NL, qw);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_moments3d(const Prob3D<T>* p, double* rho, double* u, cudaStream_t st) {
+    moments3d_kernel<T><<<608, 256, 0, st>>>(p, rho, u);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_wall3d(const Prob3D<T>* p, double* out, cudaStream_t st) {
+    wall3d_kernel<T><<<608, 256, 0, st>>>(p, out);
+    return cudaGetLastError();
+}
+
+#define DVM_INSTANTIATE3(T)                                                                     \
+    template size_t sweep3d_smem<T>(int, int, int, int);                                       \
+    template cudaError_t sweep3d_occupancy<T>(int, int, int, int, int*);                       \
+    template cudaError_t launch_sweep3d<T>(const SweepArgs3D<T>&, int, int, cudaStream_t);     \
+    template cudaError_t launch_finalize3d<T>(const FinArgs3D<T>&, int, cudaStream_t);         \
+    template cudaError_t launch_init3d<T>(const Prob3D<T>*, int, const double*, cudaStream_t); \
+    template cudaError_t launch_moments3d<T>(const Prob3D<T>*, double*, double*, cudaStream_t); \
+    template cudaError_t launch_wall3d<T>(const Prob3D<T>*, double*, cudaStream_t);
+
+DVM_INSTANTIATE3(float)
+DVM_INSTANTIATE3(double)
+
+}  // namespace dvm

@@ -217,3 +217,70 @@ def test_bounded_wait_expires_with_status_and_context_survives():
     s.sync()
     rho, u = s.moments()
     assert np.isfinite(u).all()
+
+
+# ----------------------------------------------------------------------------------------- 3D
+
+def _rock3d(n3, n2, n1, seed, frac=0.25):
+    rng = np.random.default_rng(seed)
+    solid = rng.random((n3, n2, n1)) < frac
+    solid[:, :, 0] = False          # keep an open x1 path so the problem has flow
+    return solid
+
+
+@pytest.mark.parametrize("lateral", ["periodic", "specular"])
+def test_3d_fp64_matches_oracle(lateral):
+    """Octant sweeps, x2/x3 pencil edges and ghosts: 3D random medium, 8^3 velocities."""
+    mask = _rock3d(9, 10, 11, seed=3)
+    (v, w), (vo, wo) = _grid(3, 8)
+    s = dvm.Solver(mask, 0.4, v, w, precision="fp64", lateral=lateral, band_rows=3)
+    o = oracle.Oracle(mask, 0.4, vo, wo, lateral=lateral)
+    for n in (1, 6):
+        s.step(n)
+        s.sync()
+        o.iterate(n)
+        _compare_fp64(s, o)
+
+
+def test_3d_velocity_groups_fp64():
+    """16^3 velocities: 512 per octant are split into two independent velocity groups."""
+    mask = _rock3d(6, 7, 8, seed=5, frac=0.2)
+    (v, w), (vo, wo) = _grid(3, 16)
+    s = dvm.Solver(mask, 0.8, v, w, precision="fp64", lateral="periodic", band_rows=4)
+    o = oracle.Oracle(mask, 0.8, vo, wo, lateral="periodic")
+    s.step(4)
+    s.sync()
+    o.iterate(4)
+    _compare_fp64(s, o)
+
+
+def test_3d_pencil_shapes_give_identical_bits():
+    mask = _rock3d(10, 9, 13, seed=8)
+    (v, w), _ = _grid(3, 8)
+    for prec in ("fp64", "fp32"):
+        ref = None
+        for t1, rows in ((8, 4), (4, 2), (8, 3), (4, 10), (8, 1)):
+            s = dvm.Solver(mask, 0.3, v, w, precision=prec, tile_x1=t1, band_rows=rows)
+            s.step(5)
+            s.sync()
+            rho, u = s.moments()
+            if ref is None:
+                ref = (rho, u)
+            else:
+                assert np.array_equal(ref[0], rho) and np.array_equal(ref[1], u)
+            s.close()
+
+
+def test_3d_fp32_at_convergence():
+    mask = inputs.gaussian_rock(16, seed=2, corr_len=2.0, porosity=0.5)
+    (v, w), (vo, wo) = _grid(3, 8)
+    s = dvm.Solver(mask, 0.5, v, w, precision="fp32", lateral="periodic")
+    st, it, err = s.iterate(4000, 1e-7)
+    assert st == dvm.DVM_OK
+    o = oracle.Oracle(mask, 0.5, vo, wo, lateral="periodic")
+    o.run(1e-10, 20000)
+    k, _ = s.permeability()
+    assert abs(k - o.permeability()) <= 1e-4 * abs(o.permeability())
+    _, u = s.moments()
+    _, u_o = o.moments()
+    assert _rel(u, u_o) < 1e-3
