@@ -156,6 +156,23 @@ dvm_status dvm_profile_read(dvm_ctx* ctx, double* sweep_ms, int64_t* sweep_launc
  * tables, readouts, permeability and status words). */
 dvm_status dvm_transfer_bytes(const dvm_ctx* ctx, int64_t* h2d, int64_t* d2h);
 
+/* Permeability of a caller-held velocity field, without allocating device memory.  The paper has
+ * no counterpart: this is a service for callers that cannot allocate at the moment they need the
+ * result, e.g. code running while a stream is captured into a CUDA graph, plugins whose host
+ * framework owns all device memory, or allocation-free steady-state loops.
+ * u1_dev: DEVICE pointer to n doubles (the x1 velocity of every point, solid points 0, any layout);
+ * kn > 0; out_dev: DEVICE pointer to 2 doubles receiving k = (2/sqrt(pi)) kn mean(u1) and mean(u1),
+ * written asynchronously on `stream` (cudaStream_t, NULL = legacy default stream).
+ * Scratch: a file-scope device array sized for at most 2,097,152 points (8192 blocks of 256); larger
+ * n returns DVM_EINVAL.  Each GPU that loads the library holds the array until the process exits.
+ * The first call on a device looks up the array's address (cudaGetSymbolAddress) and caches it;
+ * make that first call before any stream capture.  Calls share the array: calls whose kernels can
+ * overlap on the GPU race, so order them on one stream.  Calls no cudaMalloc/cudaFree.  Errors:
+ * DVM_EINVAL (null pointer, n out of range, bad kn), DVM_ECUDA; message in
+ * dvm_noalloc_last_error(). */
+dvm_status dvm_permeability_noalloc(const double* u1_dev, int64_t n, double kn, double* out_dev, void* stream);
+const char* dvm_noalloc_last_error(void);
+
 /* Test hook (fault-handling tests; not needed in normal use): set the bound of every spin wait
  * of the sweep kernel to timeout_ns and make work item withhold_item (-1: none) never publish its
  * progress, so that the band waiting on it gives up, the kernel records DVM_ETIMEOUT in its status

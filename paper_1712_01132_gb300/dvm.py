@@ -74,6 +74,8 @@ _SIGNATURES = [
     ("dvm_profile_read", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     ("dvm_transfer_bytes", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    ("dvm_permeability_noalloc", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double, _P, _P]),
+    ("dvm_noalloc_last_error", ctypes.c_char_p, []),
 ]
 
 _lib = None
@@ -135,6 +137,17 @@ def dvm_gh_velocity_grid(dims, n_per_axis):
     w = np.zeros(nv)
     _check(load().dvm_gh_velocity_grid(int(dims), int(n_per_axis), _ptr(v), _ptr(w)))
     return v, w
+
+
+def dvm_permeability_noalloc(u1_ptr, n, kn, out_ptr, stream=None):
+    """Permeability of a device u1 field (n doubles at u1_ptr) into 2 device doubles at out_ptr,
+    without any device allocation (scratch lives in a static device array; see include/dvm.h)."""
+    lib = load()
+    st = lib.dvm_permeability_noalloc(ctypes.c_void_p(int(u1_ptr)), int(n), float(kn), ctypes.c_void_p(int(out_ptr)),
+                                      ctypes.c_void_p(int(stream)) if stream else None)
+    if st < 0:
+        raise DvmError(st, lib.dvm_noalloc_last_error().decode())
+    return st
 
 
 class _TorchAllocator:
