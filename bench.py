@@ -107,6 +107,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate_replicas(local_ms, units_per_rank, device=None):
+    """Whole-job throughput of independent replicas: every rank processed units_per_rank units in
+    local_ms; the job time is the maximum over ranks and the value is the units of all ranks / that
+    time.  Returns (value per second, max ms, world size).  Works with any torch.distributed
+    backend (NCCL on GPUs, gloo on CPU) or without an initialised process group."""
+    import torch
+    import torch.distributed as dist
+    ws = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units_per_rank)], dtype=torch.float64, device=device)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    return float(u.item()) / (ms_max * 1e-3), ms_max, ws
+
+
 def _workload():
     from paper_1712_01132_gb300 import inputs
     mask = inputs.random_discs(SIDE, SIDE, seed=0)
@@ -155,11 +172,7 @@ def run_gpu(args):
     s.profile_enable(False)
     ks = [s.permeability(b)[0] for b in range(len(KNS))]
     s.close()
-    t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = updates_per_step * args.steps * ws / (ms_max * 1e-3)
+    value, ms_max, _ = aggregate_replicas(ms_total, updates_per_step * args.steps, device="cuda")
 
     # ---------------- end to end through the public API with host buffers
     e2e_steps = max(1, min(args.steps, 3))

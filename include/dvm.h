@@ -70,8 +70,10 @@ typedef struct {
     int lateral_bc;      /* DVM_LATERAL_SPECULAR (Eq. 8) or DVM_LATERAL_PERIODIC */
     int check_interval;  /* iterations between permeability/Err evaluations (Sec. 3.1: 100) */
     void* stream;        /* cudaStream_t, or NULL for the legacy default stream */
-    int tile_x1;         /* sweep tile width along x1 (8 or 16; 0 = automatic) */
-    int band_rows;       /* rows per sweep band (0 = automatic) */
+    int tile_x1;         /* sweep tile width along x1: 8 or 16 in 2D (FP32 always 8), 4 or 8 in 3D;
+                            0 = automatic (8 in 2D, 4 in 3D) */
+    int band_rows;       /* rows per sweep band in 2D, pencil rows R2 = R3 in 3D (0 = automatic:
+                            8 in 2D, 4 in 3D; reduced until the tile fits shared memory) */
     /* Optional device allocator (e.g. the caller's caching allocator).  When alloc is NULL the
      * library uses cudaMalloc/cudaFree.  alloc returns NULL on failure. */
     void* (*alloc)(size_t bytes, void* user);
