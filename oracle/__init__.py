@@ -74,6 +74,7 @@ def _load():
             for f in ("ora_get_wall", "ora_get_flux"):
                 getattr(lib, f).argtypes = [ctypes.c_void_p, ctypes.c_void_p]
             lib.ora_set_uniform.argtypes = [ctypes.c_void_p, ctypes.c_double]
+            lib.ora_set_initial.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
             lib.ora_sweep_one.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
             _lib = lib
     return _lib
@@ -192,6 +193,14 @@ class Oracle:
 
     def set_uniform(self, c):
         self._lib.ora_set_uniform(self._h, float(c))
+
+    def set_initial(self, rho0, u0):
+        """Warm start: the state left by an iteration that produced h0 = rho0 + 2 u0 . v at every
+        fluid point (rho0 [shape], u0 [dims, *shape], jump-form variables)."""
+        r = np.ascontiguousarray(np.asarray(rho0, dtype=np.float64).reshape(-1))
+        u = np.ascontiguousarray(np.asarray(u0, dtype=np.float64).reshape(-1))
+        assert r.size == self.solid.size and u.size == self.solid.size * self.dims
+        self._lib.ora_set_initial(self._h, _ptr(r), _ptr(u))
 
     def sweep_one(self, k):
         """Sweep velocity k from the current state without changing it; returns h [shape]."""

@@ -561,6 +561,56 @@ void ora_set_uniform(ora* o, double c) {
         for (size_t i = 0; i < (size_t)o->nv * o->N; ++i) o->full[0][i] = c;
 }
 
+/* Warm start (the paper always starts from h = 0; this is an extension whose fixed point is the
+ * same): replace the state by the one an iteration leaves when it has produced
+ *     h0(x, v_k) = rho0(x) + 2 u0(x) . v_k     (jump-form variables; + J x1 in the source form)
+ * at every fluid point, i.e. the source term of Eq. 10 evaluated at (rho0, u0).  Exactly the
+ * post-sweep steps of an iteration are applied to h0: the quadrature of Eq. 4 (ascending velocity
+ * order at every point), the wall numerators and densities of Eq. 6 at the faces, and the ghost
+ * capture of step (ii) for the boundary conditions of Eq. 7 and Eq. 8.  rho0 is [N], u0 [d][N];
+ * values at solid points are ignored.  The iteration counter is not changed. */
+void ora_set_initial(ora* o, const double* rho0, const double* u0) {
+    const size_t N = o->N;
+    const int d = o->d;
+    double* h = (double*)malloc(sizeof(double) * N);
+    double* rho_n = (double*)calloc(N, sizeof(double));
+    double* u_n = (double*)calloc(N * d, sizeof(double));
+    double* num_n = (double*)calloc(N * d * 2, sizeof(double));
+    for (int k = 0; k < o->nv; ++k) {
+        const double* vk = o->v + (size_t)k * d;
+        for (size_t id = 0; id < N; ++id) {
+            if (o->solid[id]) { h[id] = 0.0; continue; }
+            double dot = 0.0;
+            for (int j = 0; j < d; ++j) dot += u0[(size_t)j * N + id] * vk[j];
+            double x1 = (o->c.form == 1) ? o->J * (double)(id % o->n1) * o->dx : 0.0;
+            h[id] = rho0[id] + 2.0 * dot + x1;
+        }
+        capture_ghosts(o, k, h);
+        if (o->decomposed) memcpy(o->full[1] + (size_t)k * N, h, sizeof(double) * N);
+        for (size_t id = 0; id < N; ++id) {
+            if (o->solid[id]) continue;
+            double wk = o->w[k];
+            rho_n[id] += wk * h[id];
+            for (int j = 0; j < d; ++j) u_n[(size_t)j * N + id] += wk * vk[j] * h[id];
+            for (int j = 0; j < d; ++j)
+                for (int sd = 0; sd < 2; ++sd) {
+                    int side = sd ? 1 : -1;
+                    if (side * vk[j] > 0 && (o->facemask[id] >> (2 * j + sd) & 1))
+                        num_n[((size_t)j * 2 + sd) * N + id] += wk * fabs(vk[j]) * h[id];
+                }
+        }
+    }
+    for (int j = 0; j < d; ++j)
+        for (int sd = 0; sd < 2; ++sd)
+            for (size_t id = 0; id < N; ++id)
+                o->rhos[((size_t)j * 2 + sd) * N + id] = num_n[((size_t)j * 2 + sd) * N + id] / o->dface[j][sd];
+    memcpy(o->rho, rho_n, sizeof(double) * N);
+    memcpy(o->u, u_n, sizeof(double) * N * d);
+    double* t = o->lag[0]; o->lag[0] = o->lag[1]; o->lag[1] = t;
+    if (o->decomposed) { t = o->full[0]; o->full[0] = o->full[1]; o->full[1] = t; }
+    free(h); free(rho_n); free(u_n); free(num_n);
+}
+
 /* One sweep of velocity k from the current state, without updating the state (point-update
  * tests): h receives [N] values in the working variables. */
 void ora_sweep_one(const ora* o, int k, double* h) { sweep(o, k, h); }
