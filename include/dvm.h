@@ -136,6 +136,35 @@ dvm_status dvm_permeability_at(dvm_ctx* ctx, int prob, double* k, double* gp);
  * solid neighbour is x -/+ e_j; 0 where there is no such face. */
 dvm_status dvm_wall_density_at(dvm_ctx* ctx, int prob, double* rhos);
 
+/* Warm start of problem prob (0 for dvm_set_initial).  The paper always starts from h = 0
+ * (Sec. 3.1); a warm start changes only the iteration count, never the converged answer, because
+ * the steady solution is the unique fixed point of the iteration (up to the constant density of
+ * each closed fluid region).  The new state is the one an iteration leaves when it has produced
+ * the local linearised equilibrium h0(x, v) = rho0(x) + 2 u0(x) . v at every fluid point (the
+ * source term of Eq. 10 evaluated at rho0, u0): the moments are the quadrature (Eq. 4) of h0, the
+ * wall densities follow from h0 by Eq. 6, and the lagged boundary data of Eq. 7 (x1, periodic
+ * with the unit jump) and Eq. 8 (specular) or periodic lateral faces are h0 at the image points.
+ * rho0: HOST pointer to [N] doubles, u0: HOST pointer to [dims][N] doubles, both in the paper's
+ * variables (the layout dvm_moments returns; values at solid points are ignored).  The
+ * caller keeps both buffers.  The context's iteration count keeps running; the next convergence
+ * check of this problem compares with k = 0 (a restart of the Eq. 15 history).  Synchronises the
+ * stream.  EINVAL (bad prob, NULL, non-finite value at a fluid point), ECUDA. */
+dvm_status dvm_set_initial(dvm_ctx* ctx, const double* rho0, const double* u0);
+dvm_status dvm_set_initial_at(dvm_ctx* ctx, int prob, const double* rho0, const double* u0);
+
+/* Checkpoint / resume (no counterpart in the paper).  The iteration state is everything the next
+ * iteration reads from the previous one (Sec. 3.1): the per-octant moment partials (from which the
+ * moments, the wall densities of Eq. 6 and the permeability are rebuilt) and the lagged ghost
+ * layers of Eq. 7/8, plus the iteration count and the Eq. 15 history.  dvm_get_state writes it to
+ * the HOST buffer buf: with buf == NULL it only stores the required size in *bytes; with a buffer
+ * smaller than that it stores the size and returns EINVAL.  dvm_set_state loads a state written by
+ * a context with the same geometries, Knudsen numbers, velocity grid, precision, stencil order and
+ * lateral condition (EINVAL otherwise) and rebuilds the derived quantities, so that the following
+ * iterations are bit-for-bit those the saved context would have run.  Both synchronise the
+ * stream; the caller owns buf.  The blob is native-endian and not meant as an archive format. */
+dvm_status dvm_get_state(dvm_ctx* ctx, void* buf, size_t* bytes);
+dvm_status dvm_set_state(dvm_ctx* ctx, const void* buf, size_t bytes);
+
 /* Number of iterations run since creation, problems in the batch, points of problem prob. */
 dvm_status dvm_info(const dvm_ctx* ctx, int64_t* iterations, int* nprob);
 

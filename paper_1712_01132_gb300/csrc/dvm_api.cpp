@@ -27,6 +27,9 @@ template <typename T> cudaError_t launch_finalize2d(const FinArgs2D<T>&, int nbl
 template <typename T> cudaError_t launch_init2d(const Prob2D<T>*, int NL, const double* qw, cudaStream_t);
 template <typename T> cudaError_t launch_moments2d(const Prob2D<T>*, double* rho, double* u, cudaStream_t);
 template <typename T> cudaError_t launch_wall2d(const Prob2D<T>*, double* out, cudaStream_t);
+template <typename T>
+cudaError_t launch_warm2d(const Prob2D<T>*, int NL, int par, const double* qw2, const double* vel, const double* rho0,
+                          const double* u0, cudaStream_t);
 cudaError_t launch_sweep2d_f32x2(const SweepArgs2D<float>&, int grid, int NW, cudaStream_t);
 cudaError_t sweep2d_f32x2_occupancy(int NW, int max_rows, int* blocks_per_sm);
 int sweep2d_f32x2_max_rows(int NW);
@@ -38,6 +41,9 @@ template <typename T> cudaError_t launch_finalize3d(const FinArgs3D<T>&, int nbl
 template <typename T> cudaError_t launch_init3d(const Prob3D<T>*, int NL, const double* qw, cudaStream_t);
 template <typename T> cudaError_t launch_moments3d(const Prob3D<T>*, double* rho, double* u, cudaStream_t);
 template <typename T> cudaError_t launch_wall3d(const Prob3D<T>*, double* out, cudaStream_t);
+template <typename T>
+cudaError_t launch_warm3d(const Prob3D<T>*, int NL, int par, const double* qw2, const double* vel, const double* rho0,
+                          const double* u0, cudaStream_t);
 }  // namespace dvm
 
 using namespace dvm;
@@ -82,6 +88,8 @@ struct dvm_ctx {
     int* blk_start_dev = nullptr;
     int fin_blocks = 0;
     double* qw_dev = nullptr;        // [nprob][4][3]
+    double* qw2_dev = nullptr;       // warm start: [octant][group][d+1][d+1] sums of W phi_m psi_n
+    double* vel_dev = nullptr;       // warm start: [octant][NL][dims] velocity of every lane (FP64)
     double* scratch_dev = nullptr;   // readout scratch (max N * 4 doubles)
     size_t scratch_bytes = 0;
     // pinned host mirrors
@@ -249,6 +257,28 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
                 qw[((size_t)b * NQ + q) * 3 + 1] += grid->w[k] * grid->v[2 * k];
                 qw[((size_t)b * NQ + q) * 3 + 2] += grid->w[k] * grid->v[2 * k + 1];
             }
+    // ---- warm-start tables: lane velocities and quadrant sums of W phi_m psi_n, phi = psi = (1, v)
+    std::vector<double> qw2((size_t)NQ * 3 * 3, 0.0), vel((size_t)NQ * NL * 2, 0.0);
+    for (int q = 0; q < NQ; ++q)
+        for (int l = 0; l < nvq; ++l) {
+            const int k = group[q][l];
+            const double ph[3] = {1.0, grid->v[2 * k], grid->v[2 * k + 1]};
+            vel[((size_t)q * NL + l) * 2 + 0] = ph[1];
+            vel[((size_t)q * NL + l) * 2 + 1] = ph[2];
+            for (int m = 0; m < 3; ++m)
+                for (int n = 0; n < 3; ++n) qw2[((size_t)q * 3 + m) * 3 + n] += grid->w[k] * ph[m] * ph[n];
+        }
+    c->qw2_dev = (double*)dev_alloc(c, qw2.size() * sizeof(double));
+    c->vel_dev = (double*)dev_alloc(c, vel.size() * sizeof(double));
+    if (!c->qw2_dev || !c->vel_dev) return fail(c, DVM_ENOMEM, "device allocation failed");
+    {
+        cudaError_t e;
+        if ((e = cudaMemcpyAsync(c->qw2_dev, qw2.data(), qw2.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream)) ||
+            (e = cudaMemcpyAsync(c->vel_dev, vel.data(), vel.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream)) ||
+            (e = cudaStreamSynchronize(c->stream)))
+            return cuda_fail(c, e, "upload warm-start tables");
+        c->h2d_bytes += (qw2.size() + vel.size()) * sizeof(double);
+    }
     // ---- per problem device buffers
     std::vector<Prob2D<T>> probs(c->nprob);
     std::vector<SweepItem> items;
@@ -477,6 +507,29 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
                 d[0] += grid->w[k];
                 for (int j = 0; j < 3; ++j) d[1 + j] += grid->w[k] * grid->v[3 * k + j];
             }
+    // ---- warm-start tables: lane velocities and group sums of W phi_m psi_n, phi = psi = (1, v)
+    std::vector<double> qw2((size_t)NO * G * 4 * 4, 0.0), vel((size_t)NO * NL * 3, 0.0);
+    for (int q = 0; q < NO; ++q)
+        for (int m = 0; m < nvo; ++m) {
+            const int k = group[q][m];
+            const int gg = m / c->GL;
+            const double ph[4] = {1.0, grid->v[3 * k], grid->v[3 * k + 1], grid->v[3 * k + 2]};
+            for (int j = 0; j < 3; ++j) vel[((size_t)q * NL + m) * 3 + j] = ph[1 + j];
+            for (int a = 0; a < 4; ++a)
+                for (int b2 = 0; b2 < 4; ++b2)
+                    qw2[(((size_t)q * G + gg) * 4 + a) * 4 + b2] += grid->w[k] * ph[a] * ph[b2];
+        }
+    c->qw2_dev = (double*)dev_alloc(c, qw2.size() * sizeof(double));
+    c->vel_dev = (double*)dev_alloc(c, vel.size() * sizeof(double));
+    if (!c->qw2_dev || !c->vel_dev) return fail(c, DVM_ENOMEM, "device allocation failed");
+    {
+        cudaError_t e;
+        if ((e = cudaMemcpyAsync(c->qw2_dev, qw2.data(), qw2.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream)) ||
+            (e = cudaMemcpyAsync(c->vel_dev, vel.data(), vel.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream)) ||
+            (e = cudaStreamSynchronize(c->stream)))
+            return cuda_fail(c, e, "upload warm-start tables");
+        c->h2d_bytes += (qw2.size() + vel.size()) * sizeof(double);
+    }
     std::vector<Prob3D<T>> probs(c->nprob);
     std::vector<SweepItem3> items;
     std::vector<int> blk_prob, blk_start;
@@ -748,6 +801,106 @@ dvm_status collect(dvm_ctx* c) {
     return DVM_OK;
 }
 
+// Rebuild sources, wall terms and permeability of every problem from the moment partials.
+dvm_status run_finalize(dvm_ctx* c) {
+    cudaError_t e;
+    if (c->dims == 3) {
+        if (c->prec == DVM_FP32) {
+            FinArgs3D<float> fa{(const Prob3D<float>*)c->probs_dev, c->blk_prob_dev, c->blk_start_dev, c->status_dev};
+            e = launch_finalize3d<float>(fa, c->fin_blocks, c->stream);
+        } else {
+            FinArgs3D<double> fa{(const Prob3D<double>*)c->probs_dev, c->blk_prob_dev, c->blk_start_dev, c->status_dev};
+            e = launch_finalize3d<double>(fa, c->fin_blocks, c->stream);
+        }
+    } else if (c->prec == DVM_FP32) {
+        FinArgs2D<float> fa{(const Prob2D<float>*)c->probs_dev, c->blk_prob_dev, c->blk_start_dev, c->status_dev};
+        e = launch_finalize2d<float>(fa, c->fin_blocks, c->stream);
+    } else {
+        FinArgs2D<double> fa{(const Prob2D<double>*)c->probs_dev, c->blk_prob_dev, c->blk_start_dev, c->status_dev};
+        e = launch_finalize2d<double>(fa, c->fin_blocks, c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernel");
+    return DVM_OK;
+}
+
+// ---- iteration state (checkpoint / resume): moment partials + ghost layers of the read parity
+
+struct Seg {
+    void* p;
+    size_t bytes;
+};
+
+template <typename T>
+void state_segs_2d(const Prob2D<T>& P, size_t NL, int par, std::vector<Seg>& out) {
+    const size_t gx = (size_t)4 * P.n2 * 2 * NL, gl = (size_t)4 * P.n1 * 2 * NL;
+    out.push_back({P.P, (size_t)4 * 3 * P.N * sizeof(T)});
+    out.push_back({P.gx1 + par * gx, gx * sizeof(T)});
+    out.push_back({P.glat + par * gl, gl * sizeof(T)});
+}
+
+template <typename T>
+void state_segs_3d(const Prob3D<T>& P, size_t NL, int par, std::vector<Seg>& out) {
+    const size_t gx = (size_t)8 * P.n3 * P.n2 * 2 * NL;
+    const size_t gy = (size_t)8 * P.n3 * P.n1 * 2 * NL;
+    const size_t gz = (size_t)8 * P.n2 * P.n1 * 2 * NL;
+    out.push_back({P.P, (size_t)8 * P.ngroups * 4 * P.N * sizeof(T)});
+    out.push_back({P.gx1 + par * gx, gx * sizeof(T)});
+    out.push_back({P.gy + par * gy, gy * sizeof(T)});
+    out.push_back({P.gz + par * gz, gz * sizeof(T)});
+}
+
+std::vector<Seg> state_segments(const dvm_ctx* c, int par) {
+    std::vector<Seg> out;
+    for (int b = 0; b < c->nprob; ++b) {
+        if (c->dims == 3) {
+            if (c->prec == DVM_FP32) state_segs_3d(((const Prob3D<float>*)c->probs_host.data())[b], c->NL, par, out);
+            else state_segs_3d(((const Prob3D<double>*)c->probs_host.data())[b], c->NL, par, out);
+        } else {
+            if (c->prec == DVM_FP32) state_segs_2d(((const Prob2D<float>*)c->probs_host.data())[b], c->NL, par, out);
+            else state_segs_2d(((const Prob2D<double>*)c->probs_host.data())[b], c->NL, par, out);
+        }
+    }
+    return out;
+}
+
+struct StateHeader {
+    char magic[8];
+    int32_t version, dims, precision, nprob, nv, NL, G, order, lateral, pad;
+    int64_t iters;
+    double last_err;
+};
+
+struct StateProb {
+    int64_t n[3];
+    double kn, k_check;
+};
+
+constexpr char kStateMagic[8] = {'D', 'V', 'M', 'S', 'T', 'A', 'T', 'E'};
+
+StateHeader state_header(const dvm_ctx* c) {
+    StateHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, kStateMagic, 8);
+    h.version = 1;
+    h.dims = c->dims;
+    h.precision = c->prec;
+    h.nprob = c->nprob;
+    h.nv = c->nv;
+    h.NL = c->NL;
+    h.G = c->G;
+    h.order = c->opt.stencil_order;
+    h.lateral = c->opt.lateral_bc;
+    h.iters = c->iters;
+    h.last_err = c->last_err;
+    return h;
+}
+
+size_t state_bytes(const dvm_ctx* c) {
+    size_t n = sizeof(StateHeader) + (size_t)c->nprob * sizeof(StateProb);
+    for (const Seg& sg : state_segments(c, 0)) n += sg.bytes;
+    return n;
+}
+
 dvm_status validate_grid(dvm_ctx* c, int dims, const dvm_velocity_grid* g) {
     if (!g || g->nv <= 0 || !g->v || !g->w) return fail(c, DVM_EINVAL, "velocity grid is empty");
     double s = 0.0;
@@ -1010,6 +1163,122 @@ dvm_status dvm_permeability_at(dvm_ctx* c, int prob, double* k, double* gp) {
 }
 
 dvm_status dvm_permeability(dvm_ctx* c, double* k, double* gp) { return dvm_permeability_at(c, 0, k, gp); }
+
+dvm_status dvm_set_initial_at(dvm_ctx* c, int prob, const double* rho0, const double* u0) {
+    if (!c || prob < 0 || prob >= c->nprob || !rho0 || !u0) return DVM_EINVAL;
+    const HostProb& H = c->hp[prob];
+    const size_t N = H.N;
+    for (size_t i = 0; i < N; ++i) {
+        if (H.code[i] & kSolidBit) continue;
+        bool ok = std::isfinite(rho0[i]);
+        for (int j = 0; j < c->dims; ++j) ok = ok && std::isfinite(u0[(size_t)j * N + i]);
+        if (!ok) return fail(c, DVM_EINVAL, "warm start: value not finite at a fluid point");
+    }
+    double* d_rho = c->scratch_dev;
+    double* d_u = c->scratch_dev + N;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(d_rho, rho0, N * sizeof(double), cudaMemcpyHostToDevice, c->stream)) ||
+        (e = cudaMemcpyAsync(d_u, u0, N * c->dims * sizeof(double), cudaMemcpyHostToDevice, c->stream)))
+        return cuda_fail(c, e, "upload warm start");
+    c->h2d_bytes += (long long)N * (1 + c->dims) * sizeof(double);
+    const int par = (int)(c->iters & 1);
+    if (c->dims == 3) {
+        if (c->prec == DVM_FP32)
+            e = launch_warm3d<float>((const Prob3D<float>*)c->probs_dev + prob, c->NL, par, c->qw2_dev, c->vel_dev, d_rho, d_u, c->stream);
+        else
+            e = launch_warm3d<double>((const Prob3D<double>*)c->probs_dev + prob, c->NL, par, c->qw2_dev, c->vel_dev, d_rho, d_u, c->stream);
+    } else if (c->prec == DVM_FP32) {
+        e = launch_warm2d<float>((const Prob2D<float>*)c->probs_dev + prob, c->NL, par, c->qw2_dev, c->vel_dev, d_rho, d_u, c->stream);
+    } else {
+        e = launch_warm2d<double>((const Prob2D<double>*)c->probs_dev + prob, c->NL, par, c->qw2_dev, c->vel_dev, d_rho, d_u, c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "warm-start kernel");
+    dvm_status s = run_finalize(c);
+    if (s != DVM_OK) return s;
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "warm start");
+    c->k_check[prob] = 0.0;
+    return DVM_OK;
+}
+
+dvm_status dvm_set_initial(dvm_ctx* c, const double* rho0, const double* u0) {
+    return dvm_set_initial_at(c, 0, rho0, u0);
+}
+
+dvm_status dvm_get_state(dvm_ctx* c, void* buf, size_t* bytes) {
+    if (!c || !bytes) return DVM_EINVAL;
+    const size_t need = state_bytes(c);
+    if (!buf) {
+        *bytes = need;
+        return DVM_OK;
+    }
+    if (*bytes < need) {
+        *bytes = need;
+        return fail(c, DVM_EINVAL, "state buffer too small");
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "get state");
+    char* out = static_cast<char*>(buf);
+    const StateHeader h = state_header(c);
+    std::memcpy(out, &h, sizeof(h));
+    out += sizeof(h);
+    for (int b = 0; b < c->nprob; ++b) {
+        StateProb sp;
+        for (int j = 0; j < 3; ++j) sp.n[j] = c->hp[b].n[j];
+        sp.kn = c->hp[b].kn;
+        sp.k_check = c->k_check[b];
+        std::memcpy(out, &sp, sizeof(sp));
+        out += sizeof(sp);
+    }
+    for (const Seg& sg : state_segments(c, (int)(c->iters & 1))) {
+        if ((e = cudaMemcpyAsync(out, sg.p, sg.bytes, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+            return cuda_fail(c, e, "read state");
+        out += sg.bytes;
+        c->d2h_bytes += (long long)sg.bytes;
+    }
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "read state");
+    *bytes = need;
+    return DVM_OK;
+}
+
+dvm_status dvm_set_state(dvm_ctx* c, const void* buf, size_t bytes) {
+    if (!c || !buf) return DVM_EINVAL;
+    if (bytes != state_bytes(c)) return fail(c, DVM_EINVAL, "state size does not match this context");
+    const char* in = static_cast<const char*>(buf);
+    StateHeader h;
+    std::memcpy(&h, in, sizeof(h));
+    in += sizeof(h);
+    const StateHeader mine = state_header(c);
+    if (std::memcmp(h.magic, kStateMagic, 8) != 0 || h.version != 1)
+        return fail(c, DVM_EINVAL, "not a state written by dvm_get_state");
+    if (h.dims != mine.dims || h.precision != mine.precision || h.nprob != mine.nprob || h.nv != mine.nv ||
+        h.NL != mine.NL || h.G != mine.G || h.order != mine.order || h.lateral != mine.lateral || h.iters < 0)
+        return fail(c, DVM_EINVAL, "state was written by a context with other options or velocity grid");
+    std::vector<double> kc(c->nprob);
+    for (int b = 0; b < c->nprob; ++b) {
+        StateProb sp;
+        std::memcpy(&sp, in, sizeof(sp));
+        in += sizeof(sp);
+        for (int j = 0; j < 3; ++j)
+            if (sp.n[j] != c->hp[b].n[j]) return fail(c, DVM_EINVAL, "state was written for other geometries");
+        if (sp.kn != c->hp[b].kn) return fail(c, DVM_EINVAL, "state was written for other Knudsen numbers");
+        kc[b] = sp.k_check;
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set state");
+    for (const Seg& sg : state_segments(c, (int)(h.iters & 1))) {
+        if ((e = cudaMemcpyAsync(sg.p, in, sg.bytes, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+            return cuda_fail(c, e, "write state");
+        in += sg.bytes;
+        c->h2d_bytes += (long long)sg.bytes;
+    }
+    dvm_status s = run_finalize(c);
+    if (s != DVM_OK) return s;
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "write state");
+    c->iters = h.iters;
+    c->last_err = h.last_err;
+    c->k_check = kc;
+    return DVM_OK;
+}
 
 dvm_status dvm_info(const dvm_ctx* c, int64_t* iterations, int* nprob) {
     if (!c) return DVM_EINVAL;

@@ -411,6 +411,61 @@ __global__ void init2d_kernel(const Prob2D<T>* prob, int NL, const double* qw /*
     }
 }
 
+// Warm start: the state an iteration leaves when it produced the local linearised equilibrium
+// h0 = rho0 + 2 u0 . v at every fluid point (source form: h0' = h0 + x1).  Moment partials are the
+// quadrant quadratures of h0' (closed form through qw2[q][m][n] = sum_{k in q} W phi_m psi_n with
+// phi = psi = (1, v1, v2)); the lagged ghost layers read at parity `par` hold h0' at the points the
+// sweep would have captured them from (same slot layout as the sweep kernels write).
+template <typename T>
+__global__ void warm2d_kernel(const Prob2D<T>* P, int NL, int par, const double* __restrict__ qw2,
+                              const double* __restrict__ vel, const double* __restrict__ rho0,
+                              const double* __restrict__ u0) {
+    const int n1 = P->n1, n2 = P->n2, N = P->N;
+    const size_t nl = NL;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    auto h0 = [&](int x, int y, const double* v) -> double {
+        const int id = y * n1 + x;
+        if (P->code[id] & kSolidBit) return 0.0;
+        return rho0[id] + x * P->dx + 2.0 * (u0[id] * v[0] + u0[N + id] * v[1]);
+    };
+    for (size_t idx = t0; idx < (size_t)4 * 3 * N; idx += stride) {
+        const int id = idx % N;
+        const int qm = idx / N;
+        double val = 0.0;
+        if (!(P->code[id] & kSolidBit)) {
+            const double* c = qw2 + (size_t)qm * 3;
+            const double r = rho0[id] + (id % n1) * P->dx;
+            val = r * c[0] + 2.0 * (u0[id] * c[1] + u0[N + id] * c[2]);
+        }
+        P->P[idx] = (T)val;
+    }
+    // x1 ghosts: slot (q, oriented row, layer) holds h at oriented column n1 - 1 - layer
+    for (size_t idx = t0; idx < (size_t)4 * n2 * 2 * nl; idx += stride) {
+        const int l = idx % nl;
+        const int layer = (idx / nl) % 2;
+        const int yo = (idx / (nl * 2)) % n2;
+        const int q = idx / (nl * 2 * n2);
+        const int ico = n1 - 1 - layer;
+        const int x = (q & 1) ? n1 - 1 - ico : ico;
+        const int y = (q & 2) ? n2 - 1 - yo : yo;
+        P->gx1[(size_t)par * 4 * n2 * 2 * nl + idx] = (T)h0(x, y, vel + ((size_t)q * nl + l) * 2);
+    }
+    // x2 ghosts: quadrant q writes its oriented rows n2 - 1 - layer into the slots of the quadrant
+    // that reads them (itself when periodic, the x2-reflected quadrant when specular)
+    for (size_t idx = t0; idx < (size_t)4 * n1 * 2 * nl; idx += stride) {
+        const int l = idx % nl;
+        const int layer = (idx / nl) % 2;
+        const int ic = (idx / (nl * 2)) % n1;
+        const int q = idx / (nl * 2 * n1);
+        const int x = (q & 1) ? n1 - 1 - ic : ic;
+        const int yo = n2 - 1 - layer;
+        const int y = (q & 2) ? n2 - 1 - yo : yo;
+        const int qr = (P->lateral == 1) ? q : (q ^ 2);
+        P->glat[((((size_t)par * 4 + qr) * n1 + ic) * 2 + layer) * nl + l] = (T)h0(x, y, vel + ((size_t)q * nl + l) * 2);
+    }
+}
+
 // rho (paper variables, ramp restored) and u of one problem into double buffers; solid = 0.
 template <typename T>
 __global__ void moments2d_kernel(const Prob2D<T>* prob, double* rho, double* u) {
@@ -506,6 +561,13 @@ cudaError_t launch_init2d(const Prob2D<T>* prob_dev, int NL, const double* qw_de
 }
 
 template <typename T>
+cudaError_t launch_warm2d(const Prob2D<T>* prob_dev, int NL, int par, const double* qw2, const double* vel,
+                          const double* rho0, const double* u0, cudaStream_t st) {
+    warm2d_kernel<T><<<304, 256, 0, st>>>(prob_dev, NL, par, qw2, vel, rho0, u0);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_moments2d(const Prob2D<T>* prob_dev, double* rho, double* u, cudaStream_t st) {
     moments2d_kernel<T><<<304, 256, 0, st>>>(prob_dev, rho, u);
     return cudaGetLastError();
@@ -523,6 +585,8 @@ cudaError_t launch_wall2d(const Prob2D<T>* prob_dev, double* out, cudaStream_t s
     template cudaError_t sweep2d_occupancy<T>(int, int, int, int*);                             \
     template cudaError_t launch_finalize2d<T>(const FinArgs2D<T>&, int, cudaStream_t);          \
     template cudaError_t launch_init2d<T>(const Prob2D<T>*, int, const double*, cudaStream_t);  \
+    template cudaError_t launch_warm2d<T>(const Prob2D<T>*, int, int, const double*, const double*, \
+                                          const double*, const double*, cudaStream_t);            \
     template cudaError_t launch_moments2d<T>(const Prob2D<T>*, double*, double*, cudaStream_t); \
     template cudaError_t launch_wall2d<T>(const Prob2D<T>*, double*, cudaStream_t);
 

@@ -452,6 +452,68 @@ __global__ void init3d_kernel(const Prob3D<T>* P, int NL, const double* qw /*[8]
     }
 }
 
+// Warm start (3D): the state an iteration leaves when it produced h0 = rho0 + 2 u0 . v at every
+// fluid point (source form h0' = h0 + x1).  Partials per octant and velocity group through
+// qw2[q][g][m][n] = sum W phi_m psi_n with phi = psi = (1, v1, v2, v3); ghost layers read at parity
+// `par` hold h0' where the sweep would have captured them (same slot layout as the sweep writes).
+template <typename T>
+__global__ void warm3d_kernel(const Prob3D<T>* P, int NL, int par, const double* __restrict__ qw2,
+                              const double* __restrict__ vel, const double* __restrict__ rho0,
+                              const double* __restrict__ u0) {
+    const int n1 = P->n1, n2 = P->n2, n3 = P->n3, N = P->N, G = P->ngroups;
+    const size_t nl = NL;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    auto h0 = [&](int q, int io, int jo, int ko, const double* v) -> double {
+        const int x = (q & 1) ? n1 - 1 - io : io;
+        const int y = (q & 2) ? n2 - 1 - jo : jo;
+        const int z = (q & 4) ? n3 - 1 - ko : ko;
+        const size_t id = ((size_t)z * n2 + y) * n1 + x;
+        if (P->code[id] & kSolidBit) return 0.0;
+        return rho0[id] + x * P->dx + 2.0 * (u0[id] * v[0] + u0[N + id] * v[1] + u0[2 * (size_t)N + id] * v[2]);
+    };
+    for (size_t idx = t0; idx < (size_t)8 * G * 4 * N; idx += stride) {
+        const size_t id = idx % N;
+        const size_t qgm = idx / N;
+        double val = 0.0;
+        if (!(P->code[id] & kSolidBit)) {
+            const double* c = qw2 + qgm * 4;
+            const double r = rho0[id] + (id % n1) * P->dx;
+            val = r * c[0] + 2.0 * (u0[id] * c[1] + u0[N + id] * c[2] + u0[2 * (size_t)N + id] * c[3]);
+        }
+        P->P[idx] = (T)val;
+    }
+    // x1 ghosts: slot (q, oriented row (k, j), layer) holds h at oriented column n1 - 1 - layer
+    for (size_t idx = t0; idx < (size_t)8 * n3 * n2 * 2 * nl; idx += stride) {
+        const int l = idx % nl;
+        const int layer = (idx / nl) % 2;
+        const int row = (idx / (nl * 2)) % ((size_t)n3 * n2);
+        const int q = idx / (nl * 2 * n3 * n2);
+        P->gx1[(size_t)par * 8 * n3 * n2 * 2 * nl + idx] =
+            (T)h0(q, n1 - 1 - layer, row % n2, row / n2, vel + ((size_t)q * nl + l) * 3);
+    }
+    // x2 ghosts: octant q writes its oriented rows n2 - 1 - layer for the octant that reads them
+    for (size_t idx = t0; idx < (size_t)8 * n3 * n1 * 2 * nl; idx += stride) {
+        const int l = idx % nl;
+        const int layer = (idx / nl) % 2;
+        const int row = (idx / (nl * 2)) % ((size_t)n3 * n1);
+        const int q = idx / (nl * 2 * n3 * n1);
+        const int qy = (P->lateral == 1) ? q : (q ^ 2);
+        P->gy[((((size_t)par * 8 + qy) * n3 * n1 + row) * 2 + layer) * nl + l] =
+            (T)h0(q, row % n1, n2 - 1 - layer, row / n1, vel + ((size_t)q * nl + l) * 3);
+    }
+    // x3 ghosts: octant q writes its oriented planes n3 - 1 - layer for the octant that reads them
+    for (size_t idx = t0; idx < (size_t)8 * n2 * n1 * 2 * nl; idx += stride) {
+        const int l = idx % nl;
+        const int layer = (idx / nl) % 2;
+        const int row = (idx / (nl * 2)) % ((size_t)n2 * n1);
+        const int q = idx / (nl * 2 * n2 * n1);
+        const int qz = (P->lateral == 1) ? q : (q ^ 4);
+        P->gz[((((size_t)par * 8 + qz) * n2 * n1 + row) * 2 + layer) * nl + l] =
+            (T)h0(q, row % n1, row / n1, n3 - 1 - layer, vel + ((size_t)q * nl + l) * 3);
+    }
+}
+
 template <typename T>
 __global__ void moments3d_kernel(const Prob3D<T>* P, double* rho, double* u) {
     const int N = P->N, G = P->ngroups;
@@ -536,6 +598,13 @@ cudaError_t launch_init3d(const Prob3D<T>* p, int NL, const double* qw, cudaStre
 }
 
 template <typename T>
+cudaError_t launch_warm3d(const Prob3D<T>* p, int NL, int par, const double* qw2, const double* vel,
+                          const double* rho0, const double* u0, cudaStream_t st) {
+    warm3d_kernel<T><<<608, 256, 0, st>>>(p, NL, par, qw2, vel, rho0, u0);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_moments3d(const Prob3D<T>* p, double* rho, double* u, cudaStream_t st) {
     moments3d_kernel<T><<<608, 256, 0, st>>>(p, rho, u);
     return cudaGetLastError();
@@ -553,6 +622,8 @@ cudaError_t launch_wall3d(const Prob3D<T>* p, double* out, cudaStream_t st) {
     template cudaError_t launch_sweep3d<T>(const SweepArgs3D<T>&, int, int, cudaStream_t);     \
     template cudaError_t launch_finalize3d<T>(const FinArgs3D<T>&, int, cudaStream_t);         \
     template cudaError_t launch_init3d<T>(const Prob3D<T>*, int, const double*, cudaStream_t); \
+    template cudaError_t launch_warm3d<T>(const Prob3D<T>*, int, int, const double*, const double*, \
+                                          const double*, const double*, cudaStream_t);            \
     template cudaError_t launch_moments3d<T>(const Prob3D<T>*, double*, double*, cudaStream_t); \
     template cudaError_t launch_wall3d<T>(const Prob3D<T>*, double*, cudaStream_t);
 

@@ -74,6 +74,10 @@ _SIGNATURES = [
     ("dvm_profile_read", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     ("dvm_transfer_bytes", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    ("dvm_set_initial", ctypes.c_int, [_P, _P, _P]),
+    ("dvm_set_initial_at", ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    ("dvm_get_state", ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
+    ("dvm_set_state", ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     ("dvm_permeability_noalloc", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double, _P, _P]),
     ("dvm_noalloc_last_error", ctypes.c_char_p, []),
 ]
@@ -291,6 +295,27 @@ class Solver:
         out = np.zeros(m.size * m.ndim * 2)
         _check(self._lib.dvm_wall_density_at(self._ctx, int(prob), _ptr(out)), self._ctx)
         return out.reshape((m.ndim, 2) + m.shape)
+
+    def set_initial(self, rho0, u0, prob=0):
+        """dvm_set_initial_at: warm start of problem prob from rho0 (mask shape) and u0 ((dims,) +
+        mask shape), both in the variables moments() returns."""
+        m = self.masks[prob]
+        r = np.ascontiguousarray(np.asarray(rho0, dtype=np.float64).reshape(m.size))
+        u = np.ascontiguousarray(np.asarray(u0, dtype=np.float64).reshape(m.ndim * m.size))
+        _check(self._lib.dvm_set_initial_at(self._ctx, int(prob), _ptr(r), _ptr(u)), self._ctx)
+
+    def get_state(self):
+        """dvm_get_state: the iteration state as bytes."""
+        n = ctypes.c_size_t(0)
+        _check(self._lib.dvm_get_state(self._ctx, None, ctypes.byref(n)), self._ctx)
+        buf = ctypes.create_string_buffer(n.value)
+        _check(self._lib.dvm_get_state(self._ctx, buf, ctypes.byref(n)), self._ctx)
+        return buf.raw[:n.value]
+
+    def set_state(self, blob):
+        """dvm_set_state: resume from bytes written by get_state of a matching context."""
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        _check(self._lib.dvm_set_state(self._ctx, buf, len(blob)), self._ctx)
 
     def profile_enable(self, on=True):
         _check(self._lib.dvm_profile_enable(self._ctx, 1 if on else 0), self._ctx)
