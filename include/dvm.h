@@ -79,6 +79,13 @@ typedef struct {
     void* (*alloc)(size_t bytes, void* user);
     void (*free)(void* ptr, size_t bytes, void* user);
     void* alloc_user;
+    /* Nonzero: dvm_iterate and dvm_step capture each run of iterations between two convergence
+     * checks (memset, sweep and finalize launches) into a CUDA graph once and replay it (one graph
+     * per run length and starting ghost parity, kept until the context is destroyed).  Needs a
+     * non-NULL stream (the legacy default stream cannot be captured) and is not used while kernel
+     * timing is enabled; in both cases the launches are issued one by one.  The results are the
+     * same bits either way. */
+    int use_graph;
 } dvm_options;
 
 /* Fill *opt with the defaults: FP64, second order, specular lateral faces, check interval 100,
@@ -135,6 +142,19 @@ dvm_status dvm_permeability_at(dvm_ctx* ctx, int prob, double* k, double* gp);
 /* Wall densities of problem prob (Eq. 6) as [dims][2][N]: face (x, axis j, side -1/+1) whose
  * solid neighbour is x -/+ e_j; 0 where there is no such face. */
 dvm_status dvm_wall_density_at(dvm_ctx* ctx, int prob, double* rhos);
+
+/* Tile autotuner (no counterpart in the paper, whose kernel has no tiles): times `iters`
+ * iterations (after two untimed ones) of every candidate sweep tile shape on the given problems,
+ * with the options in *opt otherwise, and writes the fastest into opt->tile_x1 and
+ * opt->band_rows.  Candidates: 2D FP32 band rows {2, 4, 6, 8, 12, 16} (x1 tile 8); 2D FP64 x1 tile
+ * {8, 16} x band rows {4, 8, 12, 16}; 3D x1 tile {4, 8} x pencil rows {2, 3, 4, 6, 8}; shapes that
+ * do not fit the device are skipped.  Because every tile shape runs the same dependency-exact
+ * wavefront, the choice changes the speed and never the result.  Each candidate context is created
+ * and destroyed in turn (device memory of one context at a time); kernels run on opt->stream.
+ * best_ms (may be NULL) receives the fastest time per iteration.  Errors: those of dvm_create_batch
+ * and dvm_iterate; EINVAL when no candidate fits. */
+dvm_status dvm_autotune(int nprob, const dvm_geometry* geometries, const double* kn,
+                        const dvm_velocity_grid* grid, dvm_options* opt, int iters, double* best_ms);
 
 /* Warm start of problem prob (0 for dvm_set_initial).  The paper always starts from h = 0
  * (Sec. 3.1); a warm start changes only the iteration count, never the converged answer, because

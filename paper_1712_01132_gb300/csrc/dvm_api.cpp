@@ -111,6 +111,12 @@ struct dvm_ctx {
     std::vector<cudaEvent_t> ev_pool;      // events owned by the context
     std::vector<cudaEvent_t> ev_marks;     // [3 per profiled iteration] before sweep, after sweep, after finalize
     long long h2d_bytes = 0, d2h_bytes = 0;
+    // CUDA graphs of runs of iterations, keyed by run length and starting ghost parity
+    struct Graph {
+        int n, parity;
+        cudaGraphExec_t exec;
+    };
+    std::vector<Graph> graphs;
 };
 
 namespace {
@@ -778,6 +784,52 @@ dvm_status enqueue_iter(dvm_ctx* c) {
     return c->prec == DVM_FP32 ? enqueue_iter_2d<float>(c) : enqueue_iter_2d<double>(c);
 }
 
+void drop_graphs(dvm_ctx* c) {
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
+}
+
+// n iterations: one by one, or through a captured CUDA graph (same launches, same bits)
+dvm_status run_iterations(dvm_ctx* c, int n) {
+    if (n <= 0) return DVM_OK;
+    if (!c->opt.use_graph || c->profile || c->stream == nullptr) {
+        for (int i = 0; i < n; ++i) {
+            dvm_status s = enqueue_iter(c);
+            if (s != DVM_OK) return s;
+        }
+        return DVM_OK;
+    }
+    const int par = (int)(c->iters & 1);
+    cudaError_t e;
+    for (auto& g : c->graphs)
+        if (g.n == n && g.parity == par) {
+            if ((e = cudaGraphLaunch(g.exec, c->stream)) != cudaSuccess) return cuda_fail(c, e, "graph launch");
+            c->iters += n;
+            return DVM_OK;
+        }
+    const long long it0 = c->iters;
+    if ((e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+        return cuda_fail(c, e, "begin capture");
+    dvm_status s = DVM_OK;
+    for (int i = 0; i < n && s == DVM_OK; ++i) s = enqueue_iter(c);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(c->stream, &graph);
+    c->iters = it0;     // the captured launches have not run yet
+    if (s != DVM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+    c->graphs.push_back({n, par, exec});
+    if ((e = cudaGraphLaunch(exec, c->stream)) != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    c->iters += n;
+    return DVM_OK;
+}
+
 // wait for the stream, fetch k of every problem and the device status word
 dvm_status collect(dvm_ctx* c) {
     cudaError_t e;
@@ -1049,11 +1101,7 @@ dvm_status dvm_create(const dvm_geometry* geometry, double kn, const dvm_velocit
 
 dvm_status dvm_step(dvm_ctx* c, int n) {
     if (!c || n < 0) return DVM_EINVAL;
-    for (int i = 0; i < n; ++i) {
-        dvm_status s = enqueue_iter(c);
-        if (s != DVM_OK) return s;
-    }
-    return DVM_OK;
+    return run_iterations(c, n);
 }
 
 dvm_status dvm_sync(dvm_ctx* c) {
@@ -1069,8 +1117,8 @@ dvm_status dvm_iterate(dvm_ctx* c, int max_iter, double tol, int* iters_done, do
     while (done < max_iter) {
         const int to_check = ci - (int)(c->iters % ci);
         const int n = std::min(to_check, max_iter - done);
-        for (int i = 0; i < n; ++i) {
-            dvm_status s = enqueue_iter(c);
+        {
+            dvm_status s = run_iterations(c, n);
             if (s != DVM_OK) return s;
         }
         done += n;
@@ -1163,6 +1211,76 @@ dvm_status dvm_permeability_at(dvm_ctx* c, int prob, double* k, double* gp) {
 }
 
 dvm_status dvm_permeability(dvm_ctx* c, double* k, double* gp) { return dvm_permeability_at(c, 0, k, gp); }
+
+dvm_status dvm_autotune(int nprob, const dvm_geometry* geoms, const double* kn, const dvm_velocity_grid* grid,
+                        dvm_options* opt, int iters, double* best_ms) {
+    if (!opt || iters < 1 || nprob < 1 || !geoms) return DVM_EINVAL;
+    const int dims = geoms[0].dims;
+    std::vector<std::pair<int, int>> cand;   // (tile_x1, band_rows)
+    if (dims == 3) {
+        for (int t : {4, 8})
+            for (int r : {2, 3, 4, 6, 8}) cand.push_back({t, r});
+    } else if (opt->precision == DVM_FP32) {
+        for (int r : {2, 4, 6, 8, 12, 16}) cand.push_back({8, r});
+    } else {
+        for (int t : {8, 16})
+            for (int r : {4, 8, 12, 16}) cand.push_back({t, r});
+    }
+    cudaStream_t st = (cudaStream_t)opt->stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        g_create_err = "autotune: event creation failed";
+        return DVM_ECUDA;
+    }
+    double best = HUGE_VAL;
+    int best_t = 0, best_r = 0;
+    std::vector<std::pair<int, int>> seen;    // effective shapes after the library's clamping
+    std::string last_reject;
+    dvm_status result = DVM_OK;
+    for (auto [t, r] : cand) {
+        dvm_options o = *opt;
+        o.tile_x1 = t;
+        o.band_rows = r;
+        o.use_graph = 0;                     // time the launches, not a first capture
+        dvm_ctx* c = nullptr;
+        dvm_status s = dvm_create_batch(nprob, geoms, kn, grid, &o, &c);
+        if (s == DVM_EINVAL) {               // does not fit (or invalid input: reported below)
+            last_reject = g_create_err;
+            continue;
+        }
+        if (s != DVM_OK) { result = s; break; }
+        const std::pair<int, int> eff{c->T1, dims == 3 ? c->R2 : c->rows};
+        bool dup = false;
+        for (auto& x : seen) dup = dup || (x == eff);
+        if (dup) { dvm_destroy(c); continue; }
+        seen.push_back(eff);
+        float ms = 0.f;
+        s = dvm_step(c, 2);
+        if (s == DVM_OK) s = dvm_sync(c);
+        if (s == DVM_OK && cudaEventRecord(e0, st) != cudaSuccess) s = DVM_ECUDA;
+        if (s == DVM_OK) s = dvm_step(c, iters);
+        if (s == DVM_OK && cudaEventRecord(e1, st) != cudaSuccess) s = DVM_ECUDA;
+        if (s == DVM_OK) s = dvm_sync(c);
+        if (s == DVM_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) s = DVM_ECUDA;
+        if (s != DVM_OK) g_create_err = std::string("autotune: ") + c->err;
+        dvm_destroy(c);
+        if (s != DVM_OK) { result = s; break; }
+        const double per = ms / iters;
+        if (per < best) { best = per; best_t = t; best_r = r; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (result != DVM_OK) return result;
+    if (!(best < HUGE_VAL)) {
+        g_create_err = "autotune: no candidate tile shape was accepted (last reason: " + last_reject + ")";
+        return DVM_EINVAL;
+    }
+    opt->tile_x1 = best_t;
+    opt->band_rows = best_r;
+    if (best_ms) *best_ms = best;
+    return DVM_OK;
+}
 
 dvm_status dvm_set_initial_at(dvm_ctx* c, int prob, const double* rho0, const double* u0) {
     if (!c || prob < 0 || prob >= c->nprob || !rho0 || !u0) return DVM_EINVAL;
@@ -1329,6 +1447,7 @@ dvm_status dvm_transfer_bytes(const dvm_ctx* c, int64_t* h2d, int64_t* d2h) {
 void dvm_destroy(dvm_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
     for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
     free_all(c);
     delete c;
@@ -1340,6 +1459,7 @@ dvm_status dvm_debug_set_wait(dvm_ctx* c, long long timeout_ns, int withhold_ite
     if (!c || timeout_ns <= 0) return DVM_EINVAL;
     c->timeout_ns = timeout_ns;
     c->withhold_item = withhold_item;
+    drop_graphs(c);     // the captured launches carry the old settings
     return DVM_OK;
 }
 

@@ -43,6 +43,7 @@ class dvm_options(ctypes.Structure):
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
         ("alloc_user", ctypes.c_void_p),
+        ("use_graph", ctypes.c_int),
     ]
 
 
@@ -74,6 +75,8 @@ _SIGNATURES = [
     ("dvm_profile_read", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     ("dvm_transfer_bytes", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    ("dvm_autotune", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(dvm_geometry), _P, ctypes.POINTER(dvm_velocity_grid),
+                                    ctypes.POINTER(dvm_options), ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     ("dvm_set_initial", ctypes.c_int, [_P, _P, _P]),
     ("dvm_set_initial_at", ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     ("dvm_get_state", ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
@@ -181,7 +184,7 @@ class _TorchAllocator:
 
 
 def make_options(precision="fp64", stencil_order=2, lateral="specular", check_interval=100, stream=None,
-                 tile_x1=0, band_rows=0, torch_memory=True):
+                 tile_x1=0, band_rows=0, torch_memory=True, use_graph=False):
     """dvm_options with torch's current stream (unless stream is given) and, by default, torch's
     caching allocator for device memory.  Returns (options, keepalive)."""
     o = dvm_default_options()
@@ -191,6 +194,7 @@ def make_options(precision="fp64", stencil_order=2, lateral="specular", check_in
     o.check_interval = int(check_interval)
     o.tile_x1 = int(tile_x1)
     o.band_rows = int(band_rows)
+    o.use_graph = 1 if use_graph else 0
     keep = []
     if stream is None:
         import torch
@@ -204,6 +208,40 @@ def make_options(precision="fp64", stencil_order=2, lateral="specular", check_in
     return o, keep
 
 
+def _geometries(masks, kn):
+    """(uint8 masks, dvm_geometry array, Kn array) of one mask or a list of masks."""
+    if isinstance(masks, np.ndarray):
+        masks = [masks]
+    kns = np.atleast_1d(np.asarray(kn, dtype=np.float64))
+    if len(kns) == 1 and len(masks) > 1:
+        kns = np.repeat(kns, len(masks))
+    masks = [np.ascontiguousarray(np.asarray(m).astype(np.uint8)) for m in masks]
+    geoms = (dvm_geometry * len(masks))()
+    for g, m in zip(geoms, masks):
+        g.dims = m.ndim
+        shp = m.shape[::-1]
+        for j in range(3):
+            g.n[j] = shp[j] if j < m.ndim else 1
+        g.solid = _ptr(m)
+    return masks, geoms, np.ascontiguousarray(kns)
+
+
+def autotune(masks, kn, v, w, iters=10, **options):
+    """dvm_autotune: the fastest (tile_x1, band_rows) for these problems and options, and its
+    time per iteration in ms."""
+    lib = load()
+    masks, geoms, kns = _geometries(masks, kn)
+    v = np.ascontiguousarray(np.asarray(v, dtype=np.float64))
+    w = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+    grid = dvm_velocity_grid(len(w), _ptr(v), _ptr(w))
+    opt, keep = make_options(**options)
+    best = ctypes.c_double(0.0)
+    st = lib.dvm_autotune(len(masks), geoms, _ptr(kns), ctypes.byref(grid), ctypes.byref(opt), int(iters),
+                          ctypes.byref(best))
+    _check(st, None)
+    return opt.tile_x1, opt.band_rows, best.value
+
+
 class Solver:
     """A context (one problem or a batch) of the CUDA solver.
 
@@ -212,24 +250,11 @@ class Solver:
 
     def __init__(self, masks, kn, v, w, **options):
         lib = load()
-        if isinstance(masks, np.ndarray):
-            masks = [masks]
-        kns = np.atleast_1d(np.asarray(kn, dtype=np.float64))
-        if len(kns) == 1 and len(masks) > 1:
-            kns = np.repeat(kns, len(masks))
-        self.masks = [np.ascontiguousarray(np.asarray(m).astype(np.uint8)) for m in masks]
+        self.masks, geoms, self._kn = _geometries(masks, kn)
         self.dims = self.masks[0].ndim
-        geoms = (dvm_geometry * len(self.masks))()
-        for g, m in zip(geoms, self.masks):
-            g.dims = m.ndim
-            shp = m.shape[::-1]
-            for j in range(3):
-                g.n[j] = shp[j] if j < m.ndim else 1
-            g.solid = _ptr(m)
         self.v = np.ascontiguousarray(np.asarray(v, dtype=np.float64))
         self.w = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
         grid = dvm_velocity_grid(len(self.w), _ptr(self.v), _ptr(self.w))
-        self._kn = np.ascontiguousarray(kns)
         self.options, self._keep = make_options(**options)
         ctx = ctypes.c_void_p()
         st = lib.dvm_create_batch(len(self.masks), geoms, _ptr(self._kn), ctypes.byref(grid),

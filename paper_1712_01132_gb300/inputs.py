@@ -16,6 +16,8 @@ Workloads (the paper's digital-rock images are not available, so these stand in 
   * ``sierpinski_carpet``  -- the level-3 carpet of Sec. 4.1 (removed squares are solid).
   * ``sphere_quadrant``    -- the quadrant of the cubic sphere array of Sec. 4.2.
   * ``keep_percolating``   -- fills every fluid region that does not connect x1-periodic images.
+  * ``disc_batch``         -- many disc packings of uneven sizes and porosities, each with its own
+                              Knudsen number (the batched workload).
 """
 import math
 
@@ -49,6 +51,28 @@ def random_discs(n1, n2, seed, rmin=6.0, rmax=20.0, solid_fraction=0.5, percolat
     if percolating:
         solid = keep_percolating(solid)
     return solid
+
+
+def disc_batch(count=64, seed0=1000, nmin=64, nmax=512, eps=(0.4, 0.7), rmin=6.0, rmax=20.0,
+               kn_log10=(-2.0, 1.0)):
+    """``count`` seeded disc packings: for seed = seed0, seed0 + 1, ..., n1 and n2 uniform integers
+    in [nmin, nmax], target porosity uniform in ``eps``, disc radii uniform in [rmin, rmax],
+    Kn = 10**U(kn_log10).  A packing with no fluid path along x1 (nothing left after
+    ``keep_percolating``) has k = 0 and is skipped; the next seed takes its place.  Returns a list
+    of (mask, kn, seed)."""
+    out = []
+    seed = seed0
+    while len(out) < count:
+        rng = np.random.default_rng(seed)
+        n1 = int(rng.integers(nmin, nmax + 1))
+        n2 = int(rng.integers(nmin, nmax + 1))
+        porosity = float(rng.uniform(*eps))
+        kn = float(10.0 ** rng.uniform(*kn_log10))
+        mask = random_discs(n1, n2, seed=seed, rmin=rmin, rmax=rmax, solid_fraction=1.0 - porosity)
+        if not mask.all():
+            out.append((mask, kn, seed))
+        seed += 1
+    return out
 
 
 def gaussian_rock(n, seed, corr_len=8.0, porosity=0.35, percolating=True):

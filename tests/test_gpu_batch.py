@@ -1,0 +1,135 @@
+"""GPU tests of the batched path: CUDA-graph replay of the iteration loop, the tile autotuner and
+the 64-geometry disc-packing batch (uneven sizes, own Kn each, 24 x 24 velocities) against the
+oracle."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle
+from paper_1712_01132_gb300 import dvm, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _small_batch():
+    return [(inputs.random_discs(n1, n2, seed=s, rmin=2, rmax=5, solid_fraction=0.45), kn)
+            for (n1, n2, s, kn) in [(40, 33, 1, 0.05), (71, 24, 2, 0.8), (29, 58, 3, 3.0)]]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("check_interval", [100, 7])
+def test_graph_replay_is_bitwise_2d(precision, check_interval):
+    batch = _small_batch()
+    masks, kns = [b[0] for b in batch], [b[1] for b in batch]
+    v, w = dvm.dvm_gh_velocity_grid(2, 24)
+    a = dvm.Solver(masks, kns, v, w, precision=precision, lateral="periodic", check_interval=check_interval)
+    b = dvm.Solver(masks, kns, v, w, precision=precision, lateral="periodic", check_interval=check_interval,
+                   use_graph=True)
+    for n in (30, 121):
+        sa = a.iterate(n, 0.0)
+        sb = b.iterate(n, 0.0)
+        assert sa == sb
+    b.step(3)                              # odd run length through dvm_step
+    a.step(3)
+    assert a.iterations == b.iterations
+    for p in range(len(masks)):
+        ra, ua = a.moments(p)
+        rb, ub = b.moments(p)
+        assert np.array_equal(ra, rb) and np.array_equal(ua, ub)
+        assert a.permeability(p) == b.permeability(p)
+
+
+def test_graph_replay_is_bitwise_3d():
+    mask = inputs.gaussian_rock(12, seed=5, corr_len=1.5, porosity=0.5)
+    v, w = dvm.dvm_gh_velocity_grid(3, 8)
+    a = dvm.Solver(mask, 0.4, v, w, precision="fp32", lateral="specular", check_interval=10)
+    b = dvm.Solver(mask, 0.4, v, w, precision="fp32", lateral="specular", check_interval=10, use_graph=True)
+    assert a.iterate(35, 0.0) == b.iterate(35, 0.0)
+    ra, ua = a.moments()
+    rb, ub = b.moments()
+    assert np.array_equal(ra, rb) and np.array_equal(ua, ub)
+
+
+def test_graph_replay_after_resume_and_warm_start():
+    batch = _small_batch()
+    masks, kns = [b[0] for b in batch], [b[1] for b in batch]
+    v, w = dvm.dvm_gh_velocity_grid(2, 16)
+    a = dvm.Solver(masks, kns, v, w, precision="fp32", check_interval=20, use_graph=True)
+    b = dvm.Solver(masks, kns, v, w, precision="fp32", check_interval=20, use_graph=False)
+    rng = np.random.default_rng(0)
+    r0 = 0.1 * rng.standard_normal(masks[1].shape)
+    u0 = 0.01 * rng.standard_normal((2,) + masks[1].shape)
+    for s in (a, b):
+        s.iterate(40, 0.0)
+        s.set_initial(r0, u0, prob=1)
+        s.iterate(40, 0.0)
+    blob = a.get_state()
+    a.iterate(20, 0.0)
+    a.set_state(blob)
+    a.iterate(20, 0.0)
+    b.iterate(20, 0.0)
+    for p in range(len(masks)):
+        assert np.array_equal(a.moments(p)[1], b.moments(p)[1])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_autotuner_picks_a_candidate_with_identical_results(precision):
+    batch = _small_batch()
+    masks, kns = [b[0] for b in batch], [b[1] for b in batch]
+    v, w = dvm.dvm_gh_velocity_grid(2, 24)
+    t1, rows, ms = dvm.autotune(masks, kns, v, w, iters=5, precision=precision, lateral="periodic")
+    assert ms > 0
+    if precision == "fp32":
+        assert t1 == 8 and rows in (2, 4, 6, 8, 12, 16)
+    else:
+        assert t1 in (8, 16) and rows in (4, 8, 12, 16)
+    a = dvm.Solver(masks, kns, v, w, precision=precision, lateral="periodic")
+    b = dvm.Solver(masks, kns, v, w, precision=precision, lateral="periodic", tile_x1=t1, band_rows=rows,
+                   use_graph=True)
+    a.iterate(50, 0.0)
+    b.iterate(50, 0.0)
+    for p in range(len(masks)):
+        assert np.array_equal(a.moments(p)[1], b.moments(p)[1])
+
+
+def test_autotuner_3d():
+    mask = inputs.gaussian_rock(16, seed=3, corr_len=2.0, porosity=0.5)
+    v, w = dvm.dvm_gh_velocity_grid(3, 8)
+    t1, rows, ms = dvm.autotune(mask, 0.5, v, w, iters=3, precision="fp32", lateral="periodic")
+    assert t1 in (4, 8) and rows in (2, 3, 4, 6, 8) and ms > 0
+
+
+def test_disc_batch_64_fp32_first_iterations():
+    """The batched workload as one context with the graph loop: 64 seeded disc packings, sides
+    64-512, porosity 0.4-0.7, Kn log-uniform in [0.01, 10], 24 x 24 velocities, FP32.  Three problems
+    (the smallest, the largest and one in between) are compared element-wise with the oracle after
+    two iterations; every problem's permeability must be finite and positive."""
+    batch = inputs.disc_batch(64, seed0=1000)
+    masks, kns = [b[0] for b in batch], [b[1] for b in batch]
+    assert len(masks) == 64 and all((~m).any() for m in masks)
+    v, w = dvm.dvm_gh_velocity_grid(2, 24)
+    vo, wo = oracle.velocity_grid(2, 24)
+    s = dvm.Solver(masks, kns, v, w, precision="fp32", lateral="periodic", use_graph=True)
+    s.step(2)
+    s.sync()
+    sizes = [m.size for m in masks]
+    picks = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), 17})
+    for p in picks:
+        o = oracle.Oracle(masks[p], kns[p], vo, wo, lateral="periodic")
+        o.iterate(2)
+        rho, u = s.moments(p)
+        rho_o, u_o = o.moments()
+        assert _rel(u, u_o) < 1e-4
+        assert np.abs(rho - rho_o).max() < 1e-5 * max(1.0, np.abs(rho_o).max())
+        k, _ = s.permeability(p)
+        assert abs(k - o.permeability()) <= 1e-4 * abs(o.permeability())
+    for p in range(len(masks)):
+        k, _ = s.permeability(p)
+        assert np.isfinite(k) and k > 0

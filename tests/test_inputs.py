@@ -58,3 +58,18 @@ def test_gaussian_rock_porosity_and_percolation():
 def test_sphere_quadrant_porosity():
     s = inputs.sphere_quadrant(40, 20, 20, porosity=0.75)
     assert 1 - s.mean() == pytest.approx(0.75, abs=0.01)
+
+
+def test_disc_batch_recipe():
+    """Sides in [64, 512], porosity at most the drawn target (filling non-percolating pockets only
+    lowers it), Kn in [0.01, 10], no geometry without a fluid path, deterministic."""
+    a = inputs.disc_batch(6, seed0=1000)
+    b = inputs.disc_batch(6, seed0=1000)
+    assert len(a) == 6
+    for (m, kn, seed), (m2, kn2, seed2) in zip(a, b):
+        assert np.array_equal(m, m2) and kn == kn2 and seed == seed2
+        assert 64 <= m.shape[0] <= 512 and 64 <= m.shape[1] <= 512
+        assert 0.01 <= kn <= 10.0
+        assert (~m).any() and 1.0 - m.mean() <= 0.7 + 1e-9
+    seeds = [s for _, _, s in a]
+    assert seeds == sorted(seeds) and seeds[0] == 1000
