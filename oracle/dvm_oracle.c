@@ -11,8 +11,8 @@
  *   (i)   for every discrete velocity v_k, a forward-substitution ("raster scan") sweep over the
  *         fluid points starting at the upstream corner of v_k's octant, solving the discretised
  *         linearised BGK equation (Eq. 10, the discretised form of Eq. 3) at each point with the
- *         upwind stencil of Eq. 9: (C0,C1,C2) = (1.5,-2,0.5)/dx by default, (1,-1,0)/dx when the
- *         immediate upstream point along that axis is solid;
+ *         upwind stencil of Eq. 9: (C0,C1,C2) = (1.5,-2,0.5)/dx by default, (1,-1,0)/dx when
+ *         either upstream point of that stencil along the axis is solid;
  *   (ii)  boundary data for the next iteration: diffuse walls (Eq. 5 with alpha = 1), the pressure
  *         jump periodic condition in x1 (Eq. 7), specular (Eq. 8) or periodic lateral faces;
  *   (iii) moments rho, u (Eq. 4, tau omitted as in Sec. 4) and wall densities (Eq. 6);
@@ -23,8 +23,12 @@
  *
  * Readings of points the paper leaves open (each is listed with its reason in the design notes):
  *   - Eq. 10 sums over the axis index j (Einstein convention).
- *   - First order is used along axis j iff the immediate upstream point x - s_j e_j is solid; if
- *     only x - 2 s_j e_j is solid the second-order stencil is kept with the wall value there.
+ *   - First order is used along axis j iff one of the two upstream points of the second-order
+ *     stencil, x - s_j e_j or x - 2 s_j e_j, is solid ("the upstream grid point is located on the
+ *     boundary surfaces").  When x - s_j e_j is solid the upstream value is the wall value of that
+ *     face; when only x - 2 s_j e_j is solid it is h(x - s_j e_j).  (Keeping the second-order
+ *     stencil with a wall value at x - 2 s_j e_j makes the iteration diverge on two-voxel
+ *     channels.)
  *   - A wall value belongs to a face (fluid point y, axis j, side sigma) whose solid neighbour is
  *     y + sigma e_j; its density (Eq. 6) is evaluated from h at the fluid point y.  A solid corner
  *     therefore carries one value per normal, as Sec. 3.1 requires.
@@ -196,15 +200,15 @@ static void point_update(const ora* o, int k, const int c[3], double* h) {
             den += av * C0;
         } else {
             double U1 = h_value(o, k, j, c, l1, h, c);
-            if (o->c.order == 1) {
+            if (o->c.order == 1 || is_solid_at(o, j, c, l2)) {
+                /* first order: everywhere, or because the second upstream point of the
+                 * second-order stencil lies in the solid */
                 double C0 = 1.0 / o->dx, C1 = -1.0 / o->dx;
                 num -= av * C1 * U1;
                 den += av * C0;
             } else {
                 double C0 = 1.5 / o->dx, C1 = -2.0 / o->dx, C2 = 0.5 / o->dx;
-                double U2;
-                if (is_solid_at(o, j, c, l2)) U2 = wall_value(o, j, c, l1, -s);
-                else U2 = h_value(o, k, j, c, l2, h, c);
+                double U2 = h_value(o, k, j, c, l2, h, c);
                 num -= av * (C1 * U1 + C2 * U2);
                 den += av * C0;
             }

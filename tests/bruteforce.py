@@ -114,17 +114,13 @@ def solve_dense(solid, kn, v, w, jump=1.0, order=2, lateral="specular"):
                 if is_solid(c, j, c[j] - s):
                     C0, C1 = 1.0 / dx, -1.0 / dx
                     terms.append((a * C1, wall_term(c, j, c[j], -s)))
+                elif order == 1 or is_solid(c, j, c[j] - 2 * s):
+                    C0, C1 = 1.0 / dx, -1.0 / dx
+                    terms.append((a * C1, h_term(c, j, c[j] - s, k)))
                 else:
-                    if order == 1:
-                        C0, C1 = 1.0 / dx, -1.0 / dx
-                        terms.append((a * C1, h_term(c, j, c[j] - s, k)))
-                    else:
-                        C0, C1, C2 = 1.5 / dx, -2.0 / dx, 0.5 / dx
-                        terms.append((a * C1, h_term(c, j, c[j] - s, k)))
-                        if is_solid(c, j, c[j] - 2 * s):
-                            terms.append((a * C2, wall_term(c, j, c[j] - s, -s)))
-                        else:
-                            terms.append((a * C2, h_term(c, j, c[j] - 2 * s, k)))
+                    C0, C1, C2 = 1.5 / dx, -2.0 / dx, 0.5 / dx
+                    terms.append((a * C1, h_term(c, j, c[j] - s, k)))
+                    terms.append((a * C2, h_term(c, j, c[j] - 2 * s, k)))
                 diag += a * C0
                 for coef, (lin, const, lagged) in terms:
                     for cidx, cv in lin.items():
