@@ -1,21 +1,28 @@
 """Benchmark of the DVM transport hot path on one GB300 (replicas on N GPUs).
 
-Workload (one step = one check interval of the source iteration, Sec. 3.1: 100 iterations of
-sweep + quadrature + wall/source update, then the permeability and Err check of Eq. 15):
-  2D random porous medium, 512 x 512 overlapping discs (seed 0, radii uniform in [6, 20] cells,
-  solid fraction 0.5, periodic, non-percolating fluid filled), 32 x 32 half-range Gauss-Hermite
-  velocities (1024), the Knudsen sweep {0.01, 0.1, 1, 10} as one batched context, FP32 h and
-  moments, FP64 wall sums, G_p and Err.
-Metric: cell-velocity updates per second = (fluid cells) x (velocities) x (iterations) x (problems)
-/ time.
+One step = one check interval of the source iteration (Sec. 3.1): 100 iterations of sweep +
+quadrature + wall/source update, then the permeability and the Err check of Eq. 15.
+Metric: cell-velocity updates per second = (fluid cells) x (velocities) x (iterations) / time,
+summed over the problems of the batch.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Workloads (--workload):
+  kn_sweep_512  (default) 2D random porous medium, 512 x 512 overlapping discs (seed 0, radii uniform
+                in [6, 20] cells, solid fraction 0.5, periodic, non-percolating fluid filled),
+                32 x 32 half-range Gauss-Hermite velocities (1024), Kn in {0.01, 0.1, 1, 10} as one
+                batched context; FP32 h and moments, FP64 wall sums, G_p and Err.
+  disc_batch_64 64 seeded disc packings (seeds from 1000, sides uniform in 64..512, porosity
+                0.4-0.7, radii 6-20, Kn log-uniform in [0.01, 10]) in one batched context,
+                24 x 24 velocities, FP32.
+  rock_128      3D Gaussian-field rock 128^3 (seed 0, correlation length 8, porosity 0.35,
+                percolating cluster), 16^3 = 4096 velocities, Kn = 0.5, FP32.
+Tile shapes are chosen by the library's autotuner before the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
 
 --impl reference times the FP64 CPU oracle (the reference arm of this build) on the host cores.
 """
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -28,17 +35,38 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-KNS = [0.01, 0.1, 1.0, 10.0]
-N_AXIS = 32
-SIDE = 512
 ITERS_PER_STEP = 100
 METRIC = "cell·velocity updates/s"
-WORKLOAD = ("2D random discs 512x512 (seed 0, r 6-20, solid fraction 0.5, periodic, percolating), "
-            "32x32 Gauss-Hermite velocities, Kn {0.01,0.1,1,10} batched, FP32")
-# algorithmic work of one cell-velocity update of the sweep (2D): source 2 FMA, upwind terms
-# 2 x (2 FMA) + 2 FMA, one multiply by the reciprocal denominator, quadrature 3 MUL + 3 ADD
-FLOPS_PER_UPDATE = 2 * 2 + 6 * 2 + 1 + 3 + 3
 SMS, FP32_LANES_PER_SM = 152, 128
+
+WORKLOADS = {
+    "kn_sweep_512": {
+        "dims": 2, "n_axis": 32,
+        "desc": "2D random discs 512x512 (seed 0, r 6-20, solid fraction 0.5, periodic, percolating), "
+                "32x32 Gauss-Hermite velocities, Kn {0.01,0.1,1,10} batched, FP32",
+        # source 2 FMA, upwind 2 x (2 FMA) + 2 FMA, reciprocal 1 MUL, quadrature 3 MUL + 3 ADD
+        "flops_per_update": 2 * 2 + 6 * 2 + 1 + 3 + 3,
+        "kernel": "dvm::sweep2d_f32x2_kernel",
+        "l2": "working set per iteration > L2 (band edges and ghosts ~0.6 GB, moment partials 13 MB)",
+    },
+    "disc_batch_64": {
+        "dims": 2, "n_axis": 24,
+        "desc": "64 disc packings (seeds 1000+, sides 64-512, porosity 0.4-0.7, r 6-20, "
+                "Kn log-uniform [0.01,10]) batched, 24x24 Gauss-Hermite velocities, FP32",
+        "flops_per_update": 2 * 2 + 6 * 2 + 1 + 3 + 3,
+        "kernel": "dvm::sweep2d_f32x2_kernel",
+        "l2": "working set per iteration > L2 (band edges and ghosts of 64 problems ~2 GB)",
+    },
+    "rock_128": {
+        "dims": 3, "n_axis": 16,
+        "desc": "3D Gaussian-field rock 128^3 (seed 0, correlation length 8, porosity 0.35, percolating), "
+                "16^3 Gauss-Hermite velocities, Kn 0.5, FP32",
+        # source 3 FMA, upwind 3 x (2 FMA) + 3 FMA, reciprocal 1 MUL, quadrature 4 MUL + 4 ADD
+        "flops_per_update": 3 * 2 + 9 * 2 + 1 + 4 + 4,
+        "kernel": "dvm::sweep3d_kernel<float,T1>",
+        "l2": "working set per iteration > L2 (pencil edges and ghosts ~30 GB)",
+    },
+}
 
 
 def _dist():
@@ -54,6 +82,10 @@ def _peaks():
             return json.load(f)
     except OSError:
         return {}
+
+
+def _cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
 
 
 class ClockSampler:
@@ -124,10 +156,21 @@ def aggregate_replicas(local_ms, units_per_rank, device=None):
     return float(u.item()) / (ms_max * 1e-3), ms_max, ws
 
 
-def _workload():
+def problems(name):
+    """(masks, Knudsen numbers, fluid cells per problem) of a workload."""
     from paper_1712_01132_gb300 import inputs
-    mask = inputs.random_discs(SIDE, SIDE, seed=0)
-    return mask, int((~mask).sum())
+    if name == "kn_sweep_512":
+        mask = inputs.random_discs(512, 512, seed=0)
+        kns = [0.01, 0.1, 1.0, 10.0]
+        masks = [mask] * len(kns)
+    elif name == "disc_batch_64":
+        batch = inputs.disc_batch(64, seed0=1000)
+        masks, kns = [b[0] for b in batch], [b[1] for b in batch]
+    elif name == "rock_128":
+        masks, kns = [inputs.gaussian_rock(128, seed=0, corr_len=8.0, porosity=0.35)], [0.5]
+    else:
+        raise ValueError(name)
+    return masks, kns, [int((~m).sum()) for m in masks]
 
 
 def run_gpu(args):
@@ -135,26 +178,33 @@ def run_gpu(args):
     import torch.distributed as dist
     from paper_1712_01132_gb300 import dvm
 
+    W = WORKLOADS[args.workload]
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    mask, nf = _workload()
-    v, w = dvm.dvm_gh_velocity_grid(2, N_AXIS)
+    masks, kns, nfs = problems(args.workload)
+    v, w = dvm.dvm_gh_velocity_grid(W["dims"], W["n_axis"])
     nv = len(w)
-    updates_per_step = nf * nv * ITERS_PER_STEP * len(KNS)
+    updates_per_iter = sum(nfs) * nv
+    updates_per_step = updates_per_iter * ITERS_PER_STEP
     stream = torch.cuda.current_stream()
+    base = dict(precision="fp32", lateral="periodic")
 
     def barrier():
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
+    # ---------------- tile shape from the autotuner (untimed setup)
+    t1, rows, tune_ms = dvm.autotune(masks, kns, v, w, iters=5 if W["dims"] == 2 else 2, **base)
+    opts = dict(base, tile_x1=t1, band_rows=rows, use_graph=True)
+
     # ---------------- device-resident timing: inputs already in HBM
-    s = dvm.Solver([mask] * len(KNS), KNS, v, w, precision="fp32", lateral="periodic")
+    s = dvm.Solver(masks, kns, v, w, **opts)
     for _ in range(args.warmup):
         s.iterate(ITERS_PER_STEP, 0.0)
-    s.profile_enable(True)
+    s.profile_enable(True)                      # per-launch events (launches issued one by one)
     s.profile_read()
     sampler = ClockSampler(local)
     sampler.start()
@@ -170,7 +220,7 @@ def run_gpu(args):
     ms_total = e0.elapsed_time(e1)
     sweep_ms, sweep_n, fin_ms, fin_n = s.profile_read()
     s.profile_enable(False)
-    ks = [s.permeability(b)[0] for b in range(len(KNS))]
+    ks = [s.permeability(b)[0] for b in range(len(masks))]
     s.close()
     value, ms_max, _ = aggregate_replicas(ms_total, updates_per_step * args.steps, device="cuda")
 
@@ -182,9 +232,9 @@ def run_gpu(args):
     h2d = d2h = 0
     h0.record(stream)
     for _ in range(e2e_steps):
-        se = dvm.Solver([mask] * len(KNS), KNS, v, w, precision="fp32", lateral="periodic")
+        se = dvm.Solver(masks, kns, v, w, **opts)
         se.iterate(ITERS_PER_STEP, 0.0)
-        for b in range(len(KNS)):
+        for b in range(len(masks)):
             se.moments(b)
             se.permeability(b)
         hb, db = se.transfer_bytes()
@@ -194,21 +244,22 @@ def run_gpu(args):
     h1.record(stream)
     barrier()
     e2e_ms = h0.elapsed_time(h1)
-    e2e_value = updates_per_step * e2e_steps * ws / (e2e_ms * 1e-3)
+    e2e_value, _, _ = aggregate_replicas(e2e_ms, updates_per_step * e2e_steps, device="cuda")
 
     # ---------------- roofline of the dominant kernel (sweep), FP32 ALU bound
     peaks = _peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     peak_tflops = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    per_launch_updates = nf * nv * len(KNS)
     sweep_avg_s = (sweep_ms / max(sweep_n, 1)) * 1e-3
-    achieved = per_launch_updates * FLOPS_PER_UPDATE / sweep_avg_s / 1e12
+    achieved = updates_per_iter * W["flops_per_update"] / sweep_avg_s / 1e12
+    kernel = W["kernel"].replace("T1", str(t1))
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 2), "unit": "TFLOP/s",
                 "frac": round(achieved / peak_tflops, 4), "traffic": None,
-                "kernel": "dvm::sweep2d_kernel<float,16>", "avg_launch_ms": round(sweep_avg_s * 1e3, 4),
+                "kernel": kernel, "avg_launch_ms": round(sweep_avg_s * 1e3, 4),
                 "share_of_step": round(sweep_ms / max(sweep_ms + fin_ms, 1e-9), 4),
-                "peak_basis": "FP32 FMA issue, 152 SMs x 128 lanes x 2 flop x %.0f MHz (derived)" % sm_max,
-                "flops_per_update": FLOPS_PER_UPDATE}
+                "peak_basis": "FP32 FMA issue, 152 SMs x 128 lanes x 2 flop x %.0f MHz (derived from the "
+                              "measured max SM clock in MEASURED_PEAKS.json)" % sm_max,
+                "flops_per_update": W["flops_per_update"], "updates_per_launch": updates_per_iter}
 
     out = None
     if rank == 0:
@@ -216,10 +267,11 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "fluid_cells": nf, "velocities": nv, "problems": len(KNS),
-                       "iterations_per_step": ITERS_PER_STEP,
+            "config": {"workload": args.workload, "description": W["desc"], "fluid_cells": sum(nfs),
+                       "velocities": nv, "problems": len(masks), "iterations_per_step": ITERS_PER_STEP,
                        "step": "100 source iterations (sweep+quadrature+finalize) + permeability/Err check",
-                       "l2": "working set per iteration > L2 (band edge buffers ~0.5 GB, moments 50 MB)",
+                       "tiles": {"tile_x1": t1, "band_rows": rows, "autotuned_ms_per_iteration": round(tune_ms, 4)},
+                       "l2": W["l2"],
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": int(h2d // e2e_steps),
                     "d2h_bytes_per_step": int(d2h // e2e_steps),
@@ -227,52 +279,75 @@ def run_gpu(args):
             "gpu_launches": int(2 * ITERS_PER_STEP * args.steps),
             "roofline": roofline,
             "clocks": clocks,
-            "permeability": dict(zip([str(k) for k in KNS], ks)),
+            "permeability": [float(k) for k in ks] if len(ks) > 8 else dict(zip([str(k) for k in kns], ks)),
         }
     if ws > 1:
         dist.destroy_process_group()
     return out
 
 
-def cpu_baseline_sample(iters=1, kn=0.1):
-    """The oracle as it stands, on the host cores, on a bounded sample: `iters` iterations of one
-    Knudsen number of the same 512x512, 1024-velocity problem."""
+def _oracle_sample(name, budget_iters=None):
+    """A bounded sample of the workload for the oracle: (list of (mask, kn), iterations, text)."""
+    masks, kns, nfs = problems(name)
+    if name == "kn_sweep_512":
+        it = budget_iters or 25
+        return [(masks[1], kns[1])], it, "%d FP64 oracle iterations of the Kn=0.1 problem (512x512, 1024 velocities)" % it
+    if name == "disc_batch_64":
+        it = budget_iters or 2
+        return list(zip(masks, kns)), it, "%d FP64 oracle iteration(s) of each of the 64 problems (576 velocities)" % it
+    it = budget_iters or 1
+    return [(masks[0], kns[0])], it, "%d FP64 oracle iteration(s) of the 128^3 rock (4096 velocities)" % it
+
+
+def _time_oracle(sample, iters, dims, n_axis):
     import oracle
-    mask, nf = _workload()
-    v, w = oracle.velocity_grid(2, N_AXIS)
-    o = oracle.Oracle(mask, kn, v, w, lateral="periodic")
-    t0 = time.perf_counter()
-    o.iterate(iters)
-    dt = time.perf_counter() - t0
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": nf * len(w) * iters / dt, "unit": "updates/s", "cores": cores, "kind": "oracle",
-            "sample": "%d FP64 oracle iteration(s) of the Kn=%g problem (512x512, 1024 velocities), %.1f s"
-                      % (iters, kn, dt)}
+    v, w = oracle.velocity_grid(dims, n_axis)
+    units, dt = 0, 0.0
+    for mask, kn in sample:
+        o = oracle.Oracle(mask, kn, v, w, lateral="periodic")
+        t0 = time.perf_counter()
+        o.iterate(iters)
+        dt += time.perf_counter() - t0
+        units += int((~mask).sum()) * len(w) * iters
+        del o
+    return units, dt
+
+
+def cpu_baseline_sample(name):
+    """The oracle as it stands, on the host cores, on a bounded sample of the same workload."""
+    W = WORKLOADS[name]
+    sample, iters, text = _oracle_sample(name)
+    units, dt = _time_oracle(sample, iters, W["dims"], W["n_axis"])
+    return {"value": units / dt, "unit": "updates/s", "cores": _cores(), "kind": "oracle",
+            "sample": "%s, %.1f s" % (text, dt)}
 
 
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return None
-    import oracle
-    mask, nf = _workload()
-    v, w = oracle.velocity_grid(2, N_AXIS)
-    o = oracle.Oracle(mask, 0.1, v, w, lateral="periodic")
+    W = WORKLOADS[args.workload]
+    sample, _, _ = _oracle_sample(args.workload, budget_iters=1)
+    if args.workload == "disc_batch_64":
+        sample = sample[:8]                       # a bounded slice of the batch per step
     for _ in range(args.warmup):
-        o.iterate(1)
-    t0 = time.perf_counter()
+        _time_oracle(sample[:1], 1, W["dims"], W["n_axis"])
+    units, dt = 0, 0.0
     for _ in range(args.steps):
-        o.iterate(1)
-    dt = time.perf_counter() - t0
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    value = nf * len(w) * args.steps / dt
+        u, d = _time_oracle(sample, 1, W["dims"], W["n_axis"])
+        units += u
+        dt += d
+    value = units / dt
+    text = "per step one FP64 oracle iteration of %s" % (
+        "the Kn=0.1 problem" if args.workload == "kn_sweep_512" else
+        "problems 0-7 of the batch" if args.workload == "disc_batch_64" else "the 128^3 rock")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "fluid_cells": nf, "velocities": len(w),
-                       "step": "one FP64 oracle iteration of the Kn=0.1 problem (bounded sample of the workload)"},
-            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": cores, "kind": "oracle",
-                             "sample": "%d oracle iterations, Kn=0.1, 512x512, 1024 velocities" % args.steps},
+            "config": {"workload": args.workload, "description": W["desc"],
+                       "step": text + " (bounded sample of the workload)"},
+            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": _cores(), "kind": "oracle",
+                             "sample": "%d steps: %s" % (args.steps, text)},
             "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -281,6 +356,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="kn_sweep_512", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -288,8 +364,8 @@ def main():
         out = run_reference(args)
     else:
         out = run_gpu(args)
-        if out is not None and not args.no_cpu_baseline and args.gpus == 1:
-            out["cpu_baseline"] = cpu_baseline_sample()
+        if out is not None and not args.no_cpu_baseline and out["n_gpus"] == 1:
+            out["cpu_baseline"] = cpu_baseline_sample(args.workload)
     if out is not None:
         print(json.dumps(out))
 

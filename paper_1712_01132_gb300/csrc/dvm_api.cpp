@@ -171,7 +171,8 @@ int map_coord(int l, int n, bool periodic) {
     return l < 0 ? -1 - l : 2 * n - 1 - l;
 }
 
-// Stencil cases (Eq. 9 with the first-order switch of Sec. 2.3) of every fluid point.
+// Stencil cases (Eq. 9 with the first-order switch of Sec. 3.1: first order when either upstream
+// point of the second-order stencil is solid) of every fluid point.
 void classify(HostProb& P, int dims, const uint8_t* solid, int lateral, int order) {
     const int n1 = P.n[0], n2 = P.n[1], n3 = dims == 3 ? P.n[2] : 1;
     P.code.assign(P.N, 0);

@@ -139,8 +139,9 @@ struct FinArgs3D {
 // Stencil-case encoding of code[x] (2D uses axes 0,1; 3D axes 0..2):
 //   bits 2*(2 j + u) .. +1 : case for axis j with upstream side u (u = 0: upstream is -e_j, i.e.
 //   the sweep sign s_j > 0; u = 1: upstream is +e_j):
-//     0 both upstream points fluid, 1 only the second one solid (wall value there),
-//     2 the first upstream point solid (first-order stencil, wall value there)
+//     0 both upstream points fluid (second-order stencil of Eq. 9),
+//     1 only the second one solid (first-order stencil on the fluid neighbour),
+//     2 the first upstream point solid (first-order stencil on the wall value of that face)
 //   bit 15 : solid voxel
 constexpr uint16_t kSolidBit = 0x8000u;
 

@@ -177,9 +177,10 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs2D<T> a) {
                         const int ca = (code >> (2 * (0 + s1neg))) & 3;
                         const int cb = (code >> (2 * (2 + s2neg))) & 3;
                         r0 = Vec4<T>::make(s.x, s.y, s.z, s1neg ? e.y : e.x);
-                        r1 = Vec4<T>::make(ca == 2 ? T(0) : K1o, ca == 0 ? K2o : T(0),
-                                           cb == 2 ? T(0) : K1o, cb == 0 ? K2o : T(0));
-                        r2 = Vec4<T>::make(s2neg ? e.w : e.z, bits_as(T(0), (ca == 2) | ((cb == 2) << 1)),
+                        // case 1 (second upstream point solid): first order on h(x - s e_j)
+                        r1 = Vec4<T>::make(ca == 2 ? T(0) : (ca == 1 ? T(1) : K1o), ca == 0 ? K2o : T(0),
+                                           cb == 2 ? T(0) : (cb == 1 ? T(1) : K1o), cb == 0 ? K2o : T(0));
+                        r2 = Vec4<T>::make(s2neg ? e.w : e.z, bits_as(T(0), (ca != 0) | ((cb != 0) << 1)),
                                            T(0), T(0));
                     }
                 }
@@ -303,8 +304,6 @@ __global__ void __launch_bounds__(256) finalize2d_kernel(const FinArgs2D<T> a) {
             const T nu = (T)P->nu;
             s = Vec4<T>::make(nu * rho, T(2) * nu * u1 + T(1), T(2) * nu * u2, T(0));
             u1d = (double)u1;
-            const int n1 = P->n1, n2 = P->n2;
-            const int x = id % n1, y = id / n1;
             T ev[4];
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
@@ -317,22 +316,9 @@ __global__ void __launch_bounds__(256) finalize2d_kernel(const FinArgs2D<T> a) {
                         // first-order stencil: wall value of face (x, j, sigma), shifted by the
                         // source-form offset sigma dx on x1 faces
                         val = wall_density(P, id, j, sigma) + (j == 0 ? sigma * P->dx : 0.0);
-                    } else if (c == 1) {
-                        // second-order stencil with the wall two points upstream: face attached to
-                        // the upstream neighbour (mirrored at a specular outer face)
-                        int nid, sg = sigma;
-                        if (j == 0) {
-                            nid = y * n1 + (x + sigma + n1) % n1;
-                        } else {
-                            int yy = y + sigma;
-                            if (yy < 0 || yy >= n2) {
-                                if (P->lateral == 1) yy = (yy + n2) % n2;
-                                else { yy = (yy < 0) ? -1 - yy : 2 * n2 - 1 - yy; sg = -sigma; }
-                            }
-                            nid = yy * n1 + x;
-                        }
-                        val = -0.5 * (wall_density(P, nid, j, sg) + (j == 0 ? sigma * P->dx : 0.0));
                     }
+                    // case 1 (only the second upstream point solid) is first order on the fluid
+                    // neighbour: no wall term
                     ev[2 * j + u] = (T)val;
                 }
             }

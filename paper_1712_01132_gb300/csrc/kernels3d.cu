@@ -135,12 +135,13 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                         const T E1 = s1n ? e0.y : e0.x;
                         const T E2 = s2n ? e0.w : e0.z;
                         const T E3 = s3n ? e1.y : e1.x;
-                        const int rs = (ca == 2) | ((cb == 2) << 1) | ((cc == 2) << 2);
+                        // first-order denominator when either upstream point is solid (cases 1, 2)
+                        const int rs = (ca != 0) | ((cb != 0) << 1) | ((cc != 0) << 2);
                         r0 = V4t<T>::make(s.x, s.y, s.z, s.w);
                         r1 = V4t<T>::make(E1, E2, E3, ibits(T(0), rs));
-                        r2 = V4t<T>::make(ca == 2 ? T(0) : K1o, ca == 0 ? K2o : T(0), cb == 2 ? T(0) : K1o,
-                                          cb == 0 ? K2o : T(0));
-                        r3 = V4t<T>::make(cc == 2 ? T(0) : K1o, cc == 0 ? K2o : T(0), T(0), T(0));
+                        r2 = V4t<T>::make(ca == 2 ? T(0) : (ca == 1 ? T(1) : K1o), ca == 0 ? K2o : T(0),
+                                          cb == 2 ? T(0) : (cb == 1 ? T(1) : K1o), cb == 0 ? K2o : T(0));
+                        r3 = V4t<T>::make(cc == 2 ? T(0) : (cc == 1 ? T(1) : K1o), cc == 0 ? K2o : T(0), T(0), T(0));
                     }
                 }
                 V* R = reinterpret_cast<V*>(rec + (size_t)((kk * MR2 + jj) * T1 + i) * kRec3);
@@ -349,9 +350,6 @@ __global__ void __launch_bounds__(256) finalize3d_kernel(const FinArgs3D<T> a) {
             const T nu = (T)P->nu;
             s = V4t<T>::make(nu * mo[0], T(2) * nu * mo[1] + T(1), T(2) * nu * mo[2], T(2) * nu * mo[3]);
             u1d = (double)mo[1];
-            const int n1 = P->n1, n2 = P->n2, n3 = P->n3;
-            const int c[3] = {id % n1, (id / n1) % n2, id / (n1 * n2)};
-            const int nn[3] = {n1, n2, n3};
             T ev[6];
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
@@ -362,18 +360,9 @@ __global__ void __launch_bounds__(256) finalize3d_kernel(const FinArgs3D<T> a) {
                     double val = 0.0;
                     if (cs == 2) {
                         val = wall_density3(P, id, j, sigma) + (j == 0 ? sigma * P->dx : 0.0);
-                    } else if (cs == 1) {
-                        int cc[3] = {c[0], c[1], c[2]};
-                        int sg = sigma;
-                        int l = c[j] + sigma;
-                        if (l < 0 || l >= nn[j]) {
-                            if (j == 0 || P->lateral == 1) l = (l + nn[j]) % nn[j];
-                            else { l = (l < 0) ? -1 - l : 2 * nn[j] - 1 - l; sg = -sigma; }
-                        }
-                        cc[j] = l;
-                        const int nid = (cc[2] * n2 + cc[1]) * n1 + cc[0];
-                        val = -0.5 * (wall_density3(P, nid, j, sg) + (j == 0 ? sigma * P->dx : 0.0));
                     }
+                    // case 1 (only the second upstream point solid) is first order on the fluid
+                    // neighbour: no wall term
                     ev[2 * j + u] = (T)val;
                 }
             }

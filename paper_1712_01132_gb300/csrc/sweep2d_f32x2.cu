@@ -157,10 +157,11 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
                         const int cb = (code >> (2 * (2 + s2neg))) & 3;
                         const float E1 = s1neg ? raw[k].e.y : raw[k].e.x;
                         const float E2 = s2neg ? raw[k].e.w : raw[k].e.z;
-                        const int rs = (ca == 2) | ((cb == 2) << 1);
+                        // first-order denominator when either upstream point is solid (cases 1, 2)
+                        const int rs = (ca != 0) | ((cb != 0) << 1);
                         o0 = make_float4(raw[k].s.x, raw[k].s.y, raw[k].s.z, __int_as_float(rs * 128));
-                        o1 = make_float4(E1, ca == 2 ? 0.f : K1o, ca == 0 ? K2o : 0.f, E2);
-                        o2 = make_float4(cb == 2 ? 0.f : K1o, cb == 0 ? K2o : 0.f, 0.f, 0.f);
+                        o1 = make_float4(E1, ca == 2 ? 0.f : (ca == 1 ? 1.f : K1o), ca == 0 ? K2o : 0.f, E2);
+                        o2 = make_float4(cb == 2 ? 0.f : (cb == 1 ? 1.f : K1o), cb == 0 ? K2o : 0.f, 0.f, 0.f);
                     }
                     float4* R = reinterpret_cast<float4*>(rb + (size_t)idx * kRecF);
                     R[0] = o0;
