@@ -70,7 +70,7 @@ typedef struct {
     int lateral_bc;      /* DVM_LATERAL_SPECULAR (Eq. 8) or DVM_LATERAL_PERIODIC */
     int check_interval;  /* iterations between permeability/Err evaluations (Sec. 3.1: 100) */
     void* stream;        /* cudaStream_t, or NULL for the legacy default stream */
-    int tile_x1;         /* sweep tile width along x1: 8 or 16 in 2D (FP32 always 8), 4 or 8 in 3D;
+    int tile_x1;         /* sweep tile width along x1: 2D FP64 8 or 16, 2D FP32 4 or 8, 3D 4 or 8;
                             0 = automatic (8 in 2D, 4 in 3D) */
     int band_rows;       /* rows per sweep band in 2D, pencil rows R2 = R3 in 3D (0 = automatic:
                             8 in 2D, 4 in 3D; reduced until the tile fits shared memory) */
@@ -146,7 +146,7 @@ dvm_status dvm_wall_density_at(dvm_ctx* ctx, int prob, double* rhos);
 /* Tile autotuner (no counterpart in the paper, whose kernel has no tiles): times `iters`
  * iterations (after two untimed ones) of every candidate sweep tile shape on the given problems,
  * with the options in *opt otherwise, and writes the fastest into opt->tile_x1 and
- * opt->band_rows.  Candidates: 2D FP32 band rows {2, 4, 6, 8, 12, 16} (x1 tile 8); 2D FP64 x1 tile
+ * opt->band_rows.  Candidates: 2D FP32 x1 tile {8, 4} x band rows {4, 8, 12, 16}; 2D FP64 x1 tile
  * {8, 16} x band rows {4, 8, 12, 16}; 3D x1 tile {4, 8} x pencil rows {2, 3, 4, 6, 8}; shapes that
  * do not fit the device are skipped.  Because every tile shape runs the same dependency-exact
  * wavefront, the choice changes the speed and never the result.  Each candidate context is created

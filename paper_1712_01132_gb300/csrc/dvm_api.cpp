@@ -30,9 +30,9 @@ template <typename T> cudaError_t launch_wall2d(const Prob2D<T>*, double* out, c
 template <typename T>
 cudaError_t launch_warm2d(const Prob2D<T>*, int NL, int par, const double* qw2, const double* vel, const double* rho0,
                           const double* u0, cudaStream_t);
-cudaError_t launch_sweep2d_f32x2(const SweepArgs2D<float>&, int grid, int NW, cudaStream_t);
-cudaError_t sweep2d_f32x2_occupancy(int NW, int max_rows, int* blocks_per_sm);
-int sweep2d_f32x2_max_rows(int NW);
+cudaError_t launch_sweep2d_f32x2(const SweepArgs2D<float>&, int T1, int grid, int NW, cudaStream_t);
+cudaError_t sweep2d_f32x2_occupancy(int T1, int NW, int max_rows, int* blocks_per_sm);
+int sweep2d_f32x2_max_rows(int T1, int NW);
 int sweep2d_f32x2_velocities_per_lane();
 template <typename T> size_t sweep3d_smem(int T1, int NW, int R2, int R3);
 template <typename T> cudaError_t sweep3d_occupancy(int T1, int NW, int R2, int R3, int* blocks_per_sm);
@@ -241,11 +241,14 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     if (c->NW > 16) return fail(c, DVM_EINVAL, "too many velocities per quadrant");
     // ---- tiles
     c->T1 = c->opt.tile_x1 ? c->opt.tile_x1 : 8;
-    if (c->T1 != 8 && c->T1 != 16) return fail(c, DVM_EINVAL, "tile_x1 must be 8 or 16");
-    if (c->prec == DVM_FP32) c->T1 = 8;     // the packed FP32 kernel uses 8-column tiles
+    if (c->prec == DVM_FP32) {               // the packed FP32 kernel has 4- and 8-column tiles
+        if (c->T1 != 4 && c->T1 != 8) return fail(c, DVM_EINVAL, "tile_x1 must be 4 or 8 for FP32");
+    } else if (c->T1 != 8 && c->T1 != 16) {
+        return fail(c, DVM_EINVAL, "tile_x1 must be 8 or 16 for FP64");
+    }
     int rows = c->opt.band_rows ? c->opt.band_rows : 8;
     if (rows < 1) return fail(c, DVM_EINVAL, "band_rows must be positive");
-    if (c->prec == DVM_FP32) rows = std::min(rows, sweep2d_f32x2_max_rows(c->NW));
+    if (c->prec == DVM_FP32) rows = std::min(rows, sweep2d_f32x2_max_rows(c->T1, c->NW));
     c->rows = rows;
     int max_rows = 1;
     for (int b = 0; b < c->nprob; ++b) max_rows = std::max(max_rows, std::min(rows, c->hp[b].n[1]));
@@ -415,7 +418,7 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     c->probs_host.assign((const char*)probs.data(), (const char*)probs.data() + probs.size() * sizeof(Prob2D<T>));
     // ---- persistent grid size
     int per_sm = 0;
-    if (c->prec == DVM_FP32) e = sweep2d_f32x2_occupancy(c->NW, c->max_rows, &per_sm);
+    if (c->prec == DVM_FP32) e = sweep2d_f32x2_occupancy(c->T1, c->NW, c->max_rows, &per_sm);
     else e = sweep2d_occupancy<T>(c->T1, c->NW, c->max_rows, &per_sm);
     if (e != cudaSuccess) return cuda_fail(c, e, "occupancy");
     if (per_sm < 1) return fail(c, DVM_EINVAL, "sweep kernel does not fit on an SM with these tiles");
@@ -716,7 +719,7 @@ cudaError_t mark(dvm_ctx* c) {
 }
 
 cudaError_t sweep_launch(const SweepArgs2D<float>& a, dvm_ctx* c) {
-    return launch_sweep2d_f32x2(a, c->sweep_grid, c->NW, c->stream);
+    return launch_sweep2d_f32x2(a, c->T1, c->sweep_grid, c->NW, c->stream);
 }
 
 cudaError_t sweep_launch(const SweepArgs2D<double>& a, dvm_ctx* c) {
@@ -1222,7 +1225,8 @@ dvm_status dvm_autotune(int nprob, const dvm_geometry* geoms, const double* kn, 
         for (int t : {4, 8})
             for (int r : {2, 3, 4, 6, 8}) cand.push_back({t, r});
     } else if (opt->precision == DVM_FP32) {
-        for (int r : {2, 4, 6, 8, 12, 16}) cand.push_back({8, r});
+        for (int t : {8, 4})
+            for (int r : {4, 8, 12, 16}) cand.push_back({t, r});
     } else {
         for (int t : {8, 16})
             for (int r : {4, 8, 12, 16}) cand.push_back({t, r});

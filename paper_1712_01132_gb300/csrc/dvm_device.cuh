@@ -18,6 +18,13 @@ __device__ __forceinline__ void st_release_gpu(int* p, int v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Publish a progress value after a __syncthreads() of the writing CTA: an acq_rel fence at GPU
+// scope (cumulative over the CTA's writes ordered before it by the barrier) followed by a
+// relaxed store, i.e. the PTX release pattern.
+__device__ __forceinline__ void publish_gpu(int* p, int v) {
+    asm volatile("fence.acq_rel.gpu;\n\tst.relaxed.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -31,16 +38,18 @@ __device__ __forceinline__ int ld_volatile(const int* p) { return *reinterpret_c
 static __device__ bool wait_geq(const int* flag, int target, int* status, long long timeout_ns) {
     if (ld_acquire_gpu(flag) >= target) return true;
     const unsigned long long t0 = global_ns();
-    unsigned ns = 16;
-    for (;;) {
+    // tight acquire spin (a flag normally flips within microseconds); the status word and the
+    // clock are read every 64 polls, and long waits back off
+    for (unsigned it = 1;; ++it) {
         if (ld_acquire_gpu(flag) >= target) return true;
-        if (ld_volatile(status) != 0) return false;
-        if ((long long)(global_ns() - t0) > timeout_ns) {
-            atomicCAS(status, 0, -4);
-            return false;
+        if ((it & 63u) == 0u) {
+            if (ld_volatile(status) != 0) return false;
+            if ((long long)(global_ns() - t0) > timeout_ns) {
+                atomicCAS(status, 0, -4);
+                return false;
+            }
+            if (it >= 4096u) __nanosleep(256);
         }
-        __nanosleep(ns);
-        ns = ns < 256 ? ns * 2 : 256;
     }
 }
 

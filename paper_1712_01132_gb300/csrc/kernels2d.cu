@@ -242,8 +242,7 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs2D<T> a) {
             __syncthreads();
             // the band above only needs the edge: publish before combining the moment partials
             if (threadIdx.x == 0 && it != a.withhold_item) {
-                __threadfence();
-                st_release_gpu(P->prog + q * nb + band, t + 1);
+                publish_gpu(P->prog + q * nb + band, t + 1);
             }
             // moment partials of this quadrant: sum of the warps' lane sums, in warp order
             for (int idx = threadIdx.x; idx < nrows * width * 3; idx += blockDim.x) {

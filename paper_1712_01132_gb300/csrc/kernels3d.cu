@@ -290,8 +290,7 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
             }
             __syncthreads();
             if (threadIdx.x == 0 && it != a.withhold_item) {
-                __threadfence();
-                st_release_gpu(prog + p3 * np2 + p2, t + 1);
+                publish_gpu(prog + p3 * np2 + p2, t + 1);
             }
             // moment partials of this octant and group: warp sums in warp order
             const int tot = nr3 * nr2 * width * 4;

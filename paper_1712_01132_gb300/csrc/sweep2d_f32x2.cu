@@ -30,7 +30,7 @@ namespace dvm {
 namespace {
 
 constexpr int kRecF = 12;   // floats per point record (10 used): {a b1 b2 roff} {E1 K1x K2x E2} {K1y K2y}
-constexpr int kT1 = 8;      // tile width along x1
+// tile width along x1: 4 or 8 columns (template parameter of the kernel)
 constexpr int kVL = 4;      // velocities per lane (two packed pairs)
 constexpr int kMaxRounds = 2;
 
@@ -47,8 +47,9 @@ __device__ __forceinline__ float2 dup(float x) { return make_float2(x, x); }
 
 }  // namespace
 
+template <int T1>
 __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<float> a) {
-    constexpr int T1 = kT1;
+    constexpr int kLPP = 32 / T1;               // lanes per point after the reduce-scatter
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
     __shared__ int s_abort;
@@ -271,8 +272,8 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
                     const float s0 = reduce_scatter<float, T1>(m0, lane);
                     const float s1 = reduce_scatter<float, T1>(m1, lane);
                     const float s2 = reduce_scatter<float, T1>(m2, lane);
-                    if ((lane & 3) == 0) {
-                        float* d = part + ((size_t)(warp * RB + r) * T1 + (lane >> 2)) * 3;
+                    if ((lane & (kLPP - 1)) == 0) {
+                        float* d = part + ((size_t)(warp * RB + r) * T1 + lane / kLPP) * 3;
                         d[0] = s0;
                         d[1] = s1;
                         d[2] = s2;
@@ -334,29 +335,43 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
     }
 }
 
-size_t sweep2d_f32x2_smem(int NW, int max_rows) {
-    return sizeof(float) * ((size_t)2 * max_rows * kT1 * kRecF + (size_t)NW * max_rows * kT1 * 3 +
+size_t sweep2d_f32x2_smem(int T1, int NW, int max_rows) {
+    return sizeof(float) * ((size_t)2 * max_rows * T1 * kRecF + (size_t)NW * max_rows * T1 * 3 +
                             (size_t)NW * max_rows * 2 * 128 + (size_t)NW * 4 * 128) +
            sizeof(unsigned) * (size_t)2 * max_rows;
 }
 
-int sweep2d_f32x2_max_rows(int NW) { return kMaxRounds * NW * 32 / kT1; }
+int sweep2d_f32x2_max_rows(int T1, int NW) { return kMaxRounds * NW * 32 / T1; }
 
 int sweep2d_f32x2_velocities_per_lane() { return kVL; }
 
-cudaError_t launch_sweep2d_f32x2(const SweepArgs2D<float>& a, int grid, int NW, cudaStream_t st) {
-    const size_t smem = sweep2d_f32x2_smem(NW, a.max_rows);
-    cudaError_t e = cudaFuncSetAttribute(sweep2d_f32x2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int T1>
+static cudaError_t launch_f32x2_t(const SweepArgs2D<float>& a, int grid, int NW, cudaStream_t st) {
+    const size_t smem = sweep2d_f32x2_smem(T1, NW, a.max_rows);
+    cudaError_t e = cudaFuncSetAttribute(sweep2d_f32x2_kernel<T1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    sweep2d_f32x2_kernel<<<grid, NW * 32, smem, st>>>(a);
+    sweep2d_f32x2_kernel<T1><<<grid, NW * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t sweep2d_f32x2_occupancy(int NW, int max_rows, int* blocks_per_sm) {
-    const size_t smem = sweep2d_f32x2_smem(NW, max_rows);
-    cudaError_t e = cudaFuncSetAttribute(sweep2d_f32x2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t launch_sweep2d_f32x2(const SweepArgs2D<float>& a, int T1, int grid, int NW, cudaStream_t st) {
+    if (T1 == 8) return launch_f32x2_t<8>(a, grid, NW, st);
+    if (T1 == 4) return launch_f32x2_t<4>(a, grid, NW, st);
+    return cudaErrorInvalidValue;
+}
+
+template <int T1>
+static cudaError_t occupancy_f32x2_t(int NW, int max_rows, int* blocks_per_sm) {
+    const size_t smem = sweep2d_f32x2_smem(T1, NW, max_rows);
+    cudaError_t e = cudaFuncSetAttribute(sweep2d_f32x2_kernel<T1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep2d_f32x2_kernel, NW * 32, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep2d_f32x2_kernel<T1>, NW * 32, smem);
+}
+
+cudaError_t sweep2d_f32x2_occupancy(int T1, int NW, int max_rows, int* blocks_per_sm) {
+    if (T1 == 8) return occupancy_f32x2_t<8>(NW, max_rows, blocks_per_sm);
+    if (T1 == 4) return occupancy_f32x2_t<4>(NW, max_rows, blocks_per_sm);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace dvm

@@ -117,9 +117,11 @@ def test_tile_and_band_shapes_give_identical_bits():
     mask = inputs.random_discs(53, 35, seed=7, rmin=2, rmax=5, solid_fraction=0.4)
     (v, w), _ = _grid(2, 16)
     ref = None
+    shapes = {"fp64": ((8, 8), (16, 3), (8, 35), (16, 1), (8, 17)),
+              "fp32": ((8, 8), (4, 3), (8, 35), (4, 1), (8, 17), (4, 32))}
     for prec in ("fp64", "fp32"):
         ref = None
-        for t1, rows in ((8, 8), (16, 3), (8, 35), (16, 1), (8, 17)):
+        for t1, rows in shapes[prec]:
             s = dvm.Solver(mask, 0.2, v, w, precision=prec, tile_x1=t1, band_rows=rows)
             s.step(9)
             s.sync()
