@@ -86,6 +86,14 @@ typedef struct {
      * timing is enabled; in both cases the launches are issued one by one.  The results are the
      * same bits either way. */
     int use_graph;
+    /* Lagged-halo domain decomposition of Sec. 3.2 (the paper's MPI subdomains, emulated): the
+     * domain is cut into c1 x c2 x c3 blocks (block s along axis j holds the points l with
+     * floor(l c_j / n_j) = s); an upstream point in another block takes its value from the previous
+     * iteration instead of the current sweep, so blocks sweep independently.  This changes the
+     * iteration history (more iterations to converge) but not the fixed point.  0 or 1 = no cut
+     * (the exact serial iteration, the default).  Implemented: c2 in 2D, each block at least two
+     * rows; other values are rejected with DVM_EINVAL. */
+    int subdomains[3];
 } dvm_options;
 
 /* Fill *opt with the defaults: FP64, second order, specular lateral faces, check interval 100,

@@ -62,6 +62,7 @@ struct HostProb {
     int N;
     double kn, nu, dx;
     int nbands;
+    std::vector<int> qbands;     // 2D: bands of every quadrant
     std::vector<uint16_t> code;
 };
 
@@ -303,8 +304,48 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         P.n2 = H.n[1];
         P.N = H.N;
         P.rows = std::min(rows, P.n2);
-        P.nbands = (P.n2 + P.rows - 1) / P.rows;
+        // ---- bands per quadrant in oriented rows; with c2 x2 subdomains (lagged-halo
+        // decomposition, Sec. 3.2) no band straddles a subdomain boundary
+        const int c2 = std::max(1, c->opt.subdomains[1]);
+        std::vector<int> Y(c2 + 1);
+        for (int s = 0; s <= c2; ++s) Y[s] = (s * P.n2 + c2 - 1) / c2;    // subdomain s: [Y_s, Y_s+1)
+        std::vector<std::vector<int4>> qb(NQ);
+        std::vector<int> slot_row((size_t)NQ * c2);
+        for (int q = 0; q < NQ; ++q) {
+            const bool s2neg = (q >> 1) & 1;
+            for (int sp = 0; sp < c2; ++sp) {            // oriented subdomain order
+                const int lo = s2neg ? P.n2 - Y[c2 - sp] : Y[sp];
+                const int hi = s2neg ? P.n2 - Y[c2 - 1 - sp] : Y[sp + 1];
+                slot_row[(size_t)q * c2 + sp] = sp == 0 ? P.n2 : lo;
+                for (int r0 = lo; r0 < hi; r0 += P.rows) {
+                    const int nr = std::min(P.rows, hi - r0);
+                    qb[q].push_back(make_int4(r0, nr, r0 == lo ? sp : -1, r0 + nr == hi ? (sp + 1) % c2 : -1));
+                }
+            }
+        }
+        P.nbands = 0;
+        for (int q = 0; q < NQ; ++q) P.nbands = std::max(P.nbands, (int)qb[q].size());
+        P.nslots = c2;
         H.nbands = P.nbands;
+        H.qbands.assign(NQ, 0);
+        std::vector<int4> btab((size_t)NQ * P.nbands, make_int4(0, 0, -1, -1));
+        for (int q = 0; q < NQ; ++q) {
+            H.qbands[q] = (int)qb[q].size();
+            for (size_t k = 0; k < qb[q].size(); ++k) btab[(size_t)q * P.nbands + k] = qb[q][k];
+        }
+        int4* bands_dev = (int4*)dev_alloc(c, btab.size() * sizeof(int4));
+        int* slot_dev = (int*)dev_alloc(c, slot_row.size() * sizeof(int));
+        if (!bands_dev || !slot_dev) return fail(c, DVM_ENOMEM, "device allocation failed");
+        {
+            cudaError_t e;
+            if ((e = cudaMemcpyAsync(bands_dev, btab.data(), btab.size() * sizeof(int4), cudaMemcpyHostToDevice, c->stream)) ||
+                (e = cudaMemcpyAsync(slot_dev, slot_row.data(), slot_row.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream)) ||
+                (e = cudaStreamSynchronize(c->stream)))
+                return cuda_fail(c, e, "upload band tables");
+            c->h2d_bytes += btab.size() * sizeof(int4) + slot_row.size() * sizeof(int);
+        }
+        P.bands = bands_dev;
+        P.slot_row = slot_dev;
         P.lateral = c->opt.lateral_bc;
         P.order = c->opt.stencil_order;
         P.kn = H.kn;
@@ -318,7 +359,7 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         P.E = (T*)dev_alloc(c, N * 4 * sizeof(T));
         P.P = (T*)dev_alloc(c, (size_t)NQ * 3 * N * sizeof(T));
         P.gx1 = (T*)dev_alloc(c, (size_t)2 * NQ * P.n2 * 2 * NL * sizeof(T));
-        P.glat = (T*)dev_alloc(c, (size_t)2 * NQ * P.n1 * 2 * NL * sizeof(T));
+        P.glat = (T*)dev_alloc(c, (size_t)2 * NQ * P.nslots * P.n1 * 2 * NL * sizeof(T));
         P.edge = (T*)dev_alloc(c, (size_t)NQ * std::max(P.nbands - 1, 1) * P.n1 * 2 * NL * sizeof(T));
         T* lanec = (T*)dev_alloc(c, (size_t)NQ * NL * kLaneConsts * sizeof(T));
         P.fin_nblocks = (int)((N + kFinBlock - 1) / kFinBlock);
@@ -384,8 +425,8 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     for (int b = 0; b < c->nprob; ++b) maxb = std::max(maxb, probs[b].nbands);
     for (int band = 0; band < maxb; ++band)
         for (int b = 0; b < c->nprob; ++b)
-            if (band < probs[b].nbands)
-                for (int q = 0; q < NQ; ++q) items.push_back({b, q, band, 0});
+            for (int q = 0; q < NQ; ++q)
+                if (band < c->hp[b].qbands[q]) items.push_back({b, q, band, 0});
     c->nitems = (int)items.size();
     c->counters_bytes = sizeof(int) * (size_t)(1 + prog_total);
     c->counters_dev = (int*)dev_alloc(c, c->counters_bytes);
@@ -888,7 +929,7 @@ struct Seg {
 
 template <typename T>
 void state_segs_2d(const Prob2D<T>& P, size_t NL, int par, std::vector<Seg>& out) {
-    const size_t gx = (size_t)4 * P.n2 * 2 * NL, gl = (size_t)4 * P.n1 * 2 * NL;
+    const size_t gx = (size_t)4 * P.n2 * 2 * NL, gl = (size_t)4 * P.nslots * P.n1 * 2 * NL;
     out.push_back({P.P, (size_t)4 * 3 * P.N * sizeof(T)});
     out.push_back({P.gx1 + par * gx, gx * sizeof(T)});
     out.push_back({P.glat + par * gl, gl * sizeof(T)});
@@ -1039,6 +1080,10 @@ dvm_status dvm_create_batch(int nprob, const dvm_geometry* geoms, const double* 
     if (c->opt.stencil_order != 1 && c->opt.stencil_order != 2) return reject(DVM_EINVAL, "stencil_order");
     if (c->opt.lateral_bc != 0 && c->opt.lateral_bc != 1) return reject(DVM_EINVAL, "lateral_bc");
     if (c->opt.check_interval < 1) return reject(DVM_EINVAL, "check_interval");
+    for (int j = 0; j < 3; ++j)
+        if (c->opt.subdomains[j] < 0) return reject(DVM_EINVAL, "subdomain counts must not be negative");
+    if (c->opt.subdomains[0] > 1 || c->opt.subdomains[2] > 1 || (dims == 3 && c->opt.subdomains[1] > 1))
+        return reject(DVM_EINVAL, "lagged-halo subdomains are implemented along x2 of 2D problems only");
     c->dims = dims;
     c->nprob = nprob;
     c->prec = c->opt.precision;
@@ -1061,6 +1106,8 @@ dvm_status dvm_create_batch(int nprob, const dvm_geometry* geoms, const double* 
             N *= H.n[j];
         }
         if (N > (1LL << 30)) return reject(DVM_EINVAL, "geometry too large");
+        if (dims == 2 && c->opt.subdomains[1] > 1 && g.n[1] < 2LL * c->opt.subdomains[1])
+            return reject(DVM_EINVAL, "every x2 subdomain needs at least two rows");
         H.N = (int)N;
         H.kn = kn[b];
         H.nu = std::sqrt(3.14159265358979323846) / (2.0 * kn[b]);

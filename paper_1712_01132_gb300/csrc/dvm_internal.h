@@ -33,8 +33,13 @@ constexpr long long kDefaultTimeoutNs = 2000000000LL;   // 2 s bound on every sp
 template <typename T>
 struct Prob2D {
     int n1, n2, N;
-    int nbands;          // bands per quadrant
-    int rows;            // rows per band (last band may be shorter)
+    int nbands;          // bands per quadrant (the largest count over the quadrants)
+    int rows;            // rows per band (bands at subdomain ends may be shorter)
+    int nslots;          // lagged x2 slots per quadrant: slot 0 is the domain face, slot s >= 1 the
+                         // bottom of the s-th x2 subdomain (lagged-halo decomposition, Sec. 3.2)
+    const int4* bands;   // [4][nbands] per quadrant, in oriented rows: {first row, rows, below,
+                         // above}; below/above = -1: a live band edge, s >= 0: lagged slot s
+    const int* slot_row; // [4][nslots] oriented row just above the layers a slot holds (slot 0: n2)
     int lateral;         // 0 specular, 1 periodic
     int order;           // 2 or 1
     double kn, nu, dx;
@@ -44,7 +49,8 @@ struct Prob2D {
     T* E;                // [N][4]  wall terms per (axis j, upstream side u): index 2 j + u
     T* P;                // [4][3][N] moment partials per quadrant (rho', u1, u2)
     T* gx1;              // [2][4][n2][2][NL] x1 ghost layers (parity, quadrant, row, layer, lane)
-    T* glat;             // [2][4][n1][2][NL] x2 ghost layers (parity, quadrant, col, layer, lane)
+    T* glat;             // [2][4][nslots][n1][2][NL] lagged x2 layers (parity, quadrant, slot, col,
+                         // layer, lane): the x2 ghosts (slot 0) and the subdomain halos
     T* edge;             // [4][nbands-1][2][n1][NL] band-to-band edges
     int* prog;           // [4][nbands] tiles completed per band in this iteration
     const T* lanec;      // [4][NL][kLaneConsts]

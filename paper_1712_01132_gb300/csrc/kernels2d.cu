@@ -131,8 +131,8 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs2D<T> a) {
         const int N = P->N;
         const int s1neg = q & 1;
         const int s2neg = (q >> 1) & 1;
-        const int row0 = band * P->rows;
-        const int nrows = min(P->rows, n2 - row0);
+        const int4 binfo = P->bands[q * nb + band];
+        const int row0 = binfo.x, nrows = binfo.y, below = binfo.z, above = binfo.w;
         const T K1o = P->order == 2 ? T(2) : T(1);
         const T K2o = P->order == 2 ? T(-0.5) : T(0);
         LaneK<T> L;
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs2D<T> a) {
         for (int t = 0; t < ntiles; ++t) {
             const int c0 = t * T1;
             const int width = min(T1, n1 - c0);
-            if (threadIdx.x == 0 && band > 0) {
+            if (threadIdx.x == 0 && below < 0) {
                 if (!wait_geq(P->prog + q * nb + band - 1, t + 1, a.status, a.timeout_ns)) s_abort = 1;
             }
             // per-point records of this quadrant: source, stencil coefficients, wall terms
@@ -191,11 +191,12 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs2D<T> a) {
             }
             __syncthreads();
             if (s_abort) return;
-            // the two rows below this band: the previous band's top edge or the x2 ghost layers
+            // the two rows below this band: the previous band's top edge, or lagged layers (the x2
+            // ghosts at the domain face, the previous iteration's halo at a subdomain boundary)
             T rb1[T1], rb2[T1];
             {
-                const T* eb = (band == 0)
-                    ? P->glat + (((size_t)par * 4 + q) * n1) * 2 * NL
+                const T* eb = (below >= 0)
+                    ? P->glat + (((size_t)(par * 4 + q) * P->nslots + below) * n1) * 2 * NL
                     : P->edge + ((size_t)(q * (nb - 1) + band - 1) * n1) * 2 * NL;
 #pragma unroll
                 for (int i = 0; i < T1; ++i) {
@@ -216,11 +217,11 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs2D<T> a) {
             // periodic: the reflected quadrant reads the same lane)
             {
                 T* et;
-                if (band < nb - 1) {
+                if (above < 0) {
                     et = P->edge + ((size_t)(q * (nb - 1) + band) * n1) * 2 * NL;
                 } else {
-                    const int qr = (P->lateral == 1) ? q : (q ^ 2);
-                    et = P->glat + (((size_t)(par ^ 1) * 4 + qr) * n1) * 2 * NL;
+                    const int qd = (above > 0 || P->lateral == 1) ? q : (q ^ 2);
+                    et = P->glat + (((size_t)((par ^ 1) * 4 + qd) * P->nslots + above) * n1) * 2 * NL;
                 }
 #pragma unroll
                 for (int i = 0; i < T1; ++i) {
@@ -388,9 +389,9 @@ __global__ void init2d_kernel(const Prob2D<T>* prob, int NL, const double* qw /*
         const int col = (q & 1) ? n1 - 1 - ico : ico;
         P->gx1[idx] = (T)(col * P->dx);
     }
-    for (size_t idx = t0; idx < (size_t)2 * 4 * n1 * 2 * nl; idx += stride) {
+    for (size_t idx = t0; idx < (size_t)2 * 4 * P->nslots * n1 * 2 * nl; idx += stride) {
         const int ic = (idx / (nl * 2)) % n1;
-        const int q = (idx / (nl * 2 * n1)) % 4;
+        const int q = (idx / (nl * 2 * n1 * P->nslots)) % 4;
         const int col = (q & 1) ? n1 - 1 - ic : ic;
         P->glat[idx] = (T)(col * P->dx);
     }
@@ -436,18 +437,22 @@ __global__ void warm2d_kernel(const Prob2D<T>* P, int NL, int par, const double*
         const int y = (q & 2) ? n2 - 1 - yo : yo;
         P->gx1[(size_t)par * 4 * n2 * 2 * nl + idx] = (T)h0(x, y, vel + ((size_t)q * nl + l) * 2);
     }
-    // x2 ghosts: quadrant q writes its oriented rows n2 - 1 - layer into the slots of the quadrant
-    // that reads them (itself when periodic, the x2-reflected quadrant when specular)
-    for (size_t idx = t0; idx < (size_t)4 * n1 * 2 * nl; idx += stride) {
+    // lagged x2 layers: quadrant q writes the oriented rows below slot s (slot 0: its top rows
+    // n2 - 1 - layer) into the slot of the quadrant that reads them (slot 0: itself when periodic,
+    // the x2-reflected quadrant when specular; subdomain slots: itself)
+    const int ns = P->nslots;
+    for (size_t idx = t0; idx < (size_t)4 * ns * n1 * 2 * nl; idx += stride) {
         const int l = idx % nl;
         const int layer = (idx / nl) % 2;
         const int ic = (idx / (nl * 2)) % n1;
-        const int q = idx / (nl * 2 * n1);
+        const int sl = (idx / (nl * 2 * n1)) % ns;
+        const int q = idx / (nl * 2 * n1 * ns);
         const int x = (q & 1) ? n1 - 1 - ic : ic;
-        const int yo = n2 - 1 - layer;
+        const int yo = P->slot_row[q * ns + sl] - 1 - layer;
         const int y = (q & 2) ? n2 - 1 - yo : yo;
-        const int qr = (P->lateral == 1) ? q : (q ^ 2);
-        P->glat[((((size_t)par * 4 + qr) * n1 + ic) * 2 + layer) * nl + l] = (T)h0(x, y, vel + ((size_t)q * nl + l) * 2);
+        const int qd = (sl > 0 || P->lateral == 1) ? q : (q ^ 2);
+        P->glat[(((((size_t)par * 4 + qd) * ns + sl) * n1 + ic) * 2 + layer) * nl + l] =
+            (T)h0(x, y, vel + ((size_t)q * nl + l) * 2);
     }
 }
 

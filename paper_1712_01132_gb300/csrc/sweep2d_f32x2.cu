@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
     __shared__ int s_abort;
+    __shared__ int s_binfo[4];                  // band of the current item: row0, rows, below, above
     const int NW = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -70,6 +71,15 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
         if (threadIdx.x == 0) {
             s_item = ld_volatile(a.status) ? a.nitems : atomicAdd(a.ticket, 1);
             s_abort = 0;
+            if (s_item < a.nitems) {
+                const SweepItem itm = a.items[s_item];
+                const Prob2D<float>& Pi = a.prob[itm.prob];
+                const int4 bi = Pi.bands[itm.quad * Pi.nbands + itm.band];
+                s_binfo[0] = bi.x;
+                s_binfo[1] = bi.y;
+                s_binfo[2] = bi.z;
+                s_binfo[3] = bi.w;
+            }
         }
         __syncthreads();
         const int it = s_item;
@@ -82,8 +92,7 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
         const int N = P->N;
         const int s1neg = q & 1;
         const int s2neg = (q >> 1) & 1;
-        const int row0 = band * P->rows;
-        const int nrows = min(P->rows, n2 - row0);
+        const int row0 = s_binfo[0], nrows = s_binfo[1];
         const float K1o = P->order == 2 ? 2.f : 1.f;
         const float K2o = P->order == 2 ? -0.5f : 0.f;
         LaneQ L;
@@ -192,7 +201,7 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
             const int buf = t & 1;
             RawPoint nxt[kMaxRounds];
             if (t + 1 < ntiles) load_raw(t + 1, nxt);
-            if (threadIdx.x == 0 && band > 0) {
+            if (threadIdx.x == 0 && s_binfo[2] < 0) {
                 if (!wait_geq(P->prog + q * nb + band - 1, t + 1, a.status, a.timeout_ns)) s_abort = 1;
             }
             __syncthreads();
@@ -202,8 +211,9 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
             // the two rows below: previous band's top edge or the x2 ghost layers
             float4 rb1[T1], rb2[T1];
             {
-                const float* eb = (band == 0)
-                    ? P->glat + (((size_t)par * 4 + q) * n1) * 2 * NL
+                const int below = s_binfo[2];
+                const float* eb = (below >= 0)
+                    ? P->glat + (((size_t)(par * 4 + q) * P->nslots + below) * n1) * 2 * NL
                     : P->edge + ((size_t)(q * (nb - 1) + band - 1) * n1) * 2 * NL;
 #pragma unroll
                 for (int i = 0; i < T1; ++i) {
@@ -286,11 +296,12 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
             // periodic: the reflected quadrant reads the same lane)
             {
                 float* et;
-                if (band < nb - 1) {
+                const int above = s_binfo[3];
+                if (above < 0) {
                     et = P->edge + ((size_t)(q * (nb - 1) + band) * n1) * 2 * NL;
                 } else {
-                    const int qr = (P->lateral == 1) ? q : (q ^ 2);
-                    et = P->glat + (((size_t)(par ^ 1) * 4 + qr) * n1) * 2 * NL;
+                    const int qd = (above > 0 || P->lateral == 1) ? q : (q ^ 2);
+                    et = P->glat + (((size_t)((par ^ 1) * 4 + qd) * P->nslots + above) * n1) * 2 * NL;
                 }
 #pragma unroll
                 for (int i = 0; i < T1; ++i) {

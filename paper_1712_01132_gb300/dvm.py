@@ -44,6 +44,7 @@ class dvm_options(ctypes.Structure):
         ("free", FREE_FN),
         ("alloc_user", ctypes.c_void_p),
         ("use_graph", ctypes.c_int),
+        ("subdomains", ctypes.c_int * 3),
     ]
 
 
@@ -184,7 +185,7 @@ class _TorchAllocator:
 
 
 def make_options(precision="fp64", stencil_order=2, lateral="specular", check_interval=100, stream=None,
-                 tile_x1=0, band_rows=0, torch_memory=True, use_graph=False):
+                 tile_x1=0, band_rows=0, torch_memory=True, use_graph=False, subdomains=(1, 1, 1)):
     """dvm_options with torch's current stream (unless stream is given) and, by default, torch's
     caching allocator for device memory.  Returns (options, keepalive)."""
     o = dvm_default_options()
@@ -195,6 +196,8 @@ def make_options(precision="fp64", stencil_order=2, lateral="specular", check_in
     o.tile_x1 = int(tile_x1)
     o.band_rows = int(band_rows)
     o.use_graph = 1 if use_graph else 0
+    for j in range(3):
+        o.subdomains[j] = int(subdomains[j])
     keep = []
     if stream is None:
         import torch
