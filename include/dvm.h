@@ -61,11 +61,15 @@ typedef struct {
     const double* w;
 } dvm_velocity_grid;
 
-enum { DVM_FP64 = 0, DVM_FP32 = 1 };                 /* precision of h, moments and sweeps */
+/* precision of h, moments and sweeps.  DVM_BF16_STORE (3D only) is the BF16-storage ablation:
+ * FP32 arithmetic and FP32 moments, but the transient h kept in HBM between pencils and between
+ * iterations (pencil edges and ghost layers) is stored as BF16 (round to nearest even) deviations
+ * from the x1 ramp of the source form; its errors are reported, not gated. */
+enum { DVM_FP64 = 0, DVM_FP32 = 1, DVM_BF16_STORE = 2 };
 enum { DVM_LATERAL_SPECULAR = 0, DVM_LATERAL_PERIODIC = 1 };
 
 typedef struct {
-    int precision;       /* DVM_FP64 or DVM_FP32; wall sums, G_p and Err are always FP64 */
+    int precision;       /* DVM_FP64, DVM_FP32 or DVM_BF16_STORE; wall sums, G_p and Err are always FP64 */
     int stencil_order;   /* 2: Eq. 9 second order with the first-order switch at walls; 1: first order */
     int lateral_bc;      /* DVM_LATERAL_SPECULAR (Eq. 8) or DVM_LATERAL_PERIODIC */
     int check_interval;  /* iterations between permeability/Err evaluations (Sec. 3.1: 100) */

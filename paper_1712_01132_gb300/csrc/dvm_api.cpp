@@ -35,7 +35,7 @@ cudaError_t sweep2d_f32x2_occupancy(int T1, int NW, int max_rows, int* blocks_pe
 int sweep2d_f32x2_max_rows(int T1, int NW);
 int sweep2d_f32x2_velocities_per_lane();
 template <typename T> size_t sweep3d_smem(int T1, int NW, int R2, int R3);
-template <typename T> cudaError_t sweep3d_occupancy(int T1, int NW, int R2, int R3, int* blocks_per_sm);
+template <typename T> cudaError_t sweep3d_occupancy(int T1, int NW, int R2, int R3, int bf16, int* blocks_per_sm);
 template <typename T> cudaError_t launch_sweep3d(const SweepArgs3D<T>&, int grid, int NW, cudaStream_t);
 template <typename T> cudaError_t launch_finalize3d(const FinArgs3D<T>&, int nblocks, cudaStream_t);
 template <typename T> cudaError_t launch_init3d(const Prob3D<T>*, int NL, const double* qw, cudaStream_t);
@@ -73,7 +73,8 @@ struct dvm_ctx {
     dvm_options opt;
     cudaStream_t stream = nullptr;
     int dims = 2, nprob = 0, nv = 0, nvq = 0, NQ = 4, NL = 32, NW = 1;
-    int prec = DVM_FP64;
+    int prec = DVM_FP64;             // arithmetic precision (BF16 storage computes in FP32)
+    bool bf16 = false;               // 3D ghosts and pencil edges stored as BF16
     int T1 = 8, rows = 8, max_rows = 8;
     std::vector<HostProb> hp;
     std::vector<Buf> bufs;
@@ -611,13 +612,15 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         P.src = (T*)dev_alloc(c, N * 4 * sizeof(T));
         P.E = (T*)dev_alloc(c, N * 8 * sizeof(T));
         P.P = (T*)dev_alloc(c, (size_t)NO * G * 4 * N * sizeof(T));
-        P.gx1 = (T*)dev_alloc(c, (size_t)2 * NO * n3 * n2 * 2 * NL * sizeof(T));
-        P.gy = (T*)dev_alloc(c, (size_t)2 * NO * n3 * n1 * 2 * NL * sizeof(T));
-        P.gz = (T*)dev_alloc(c, (size_t)2 * NO * n2 * n1 * 2 * NL * sizeof(T));
+        P.bf16 = c->bf16 ? 1 : 0;
+        const size_t es = c->bf16 ? 2 : sizeof(T);     // bytes per stored ghost / edge value
+        P.gx1 = (T*)dev_alloc(c, (size_t)2 * NO * n3 * n2 * 2 * NL * es);
+        P.gy = (T*)dev_alloc(c, (size_t)2 * NO * n3 * n1 * 2 * NL * es);
+        P.gz = (T*)dev_alloc(c, (size_t)2 * NO * n2 * n1 * 2 * NL * es);
         const size_t ey_sz = (size_t)NO * P.np3 * std::max(P.np2 - 1, 1) * P.R3 * n1 * 2 * NL;
         const size_t ez_sz = (size_t)NO * P.np2 * std::max(P.np3 - 1, 1) * P.R2 * n1 * 2 * NL;
-        P.ey = (T*)dev_alloc(c, ey_sz * sizeof(T));
-        P.ez = (T*)dev_alloc(c, ez_sz * sizeof(T));
+        P.ey = (T*)dev_alloc(c, ey_sz * es);
+        P.ez = (T*)dev_alloc(c, ez_sz * es);
         T* lanec = (T*)dev_alloc(c, (size_t)NO * NL * kLaneConsts3 * sizeof(T));
         P.fin_nblocks = (int)((N + kFinBlock - 1) / kFinBlock);
         P.fin_block0 = (int)blk_prob.size();
@@ -633,8 +636,8 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         if ((e = cudaMemcpyAsync(code, H.code.data(), N * sizeof(uint16_t), cudaMemcpyHostToDevice, c->stream)) ||
             (e = cudaMemsetAsync(P.fin_counter, 0, sizeof(unsigned int), c->stream)) ||
             (e = cudaMemsetAsync(P.kval, 0, 3 * sizeof(double), c->stream)) ||
-            (e = cudaMemsetAsync(P.ey, 0, ey_sz * sizeof(T), c->stream)) ||
-            (e = cudaMemsetAsync(P.ez, 0, ez_sz * sizeof(T), c->stream)))
+            (e = cudaMemsetAsync(P.ey, 0, ey_sz * es, c->stream)) ||
+            (e = cudaMemsetAsync(P.ez, 0, ez_sz * es, c->stream)))
             return cuda_fail(c, e, "upload");
         c->h2d_bytes += N * sizeof(uint16_t);
         std::vector<T> lc((size_t)NO * NL * kLaneConsts3, T(0));
@@ -719,7 +722,7 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
                     qw.size() * sizeof(double) + probs.size() * sizeof(Prob3D<T>);
     c->probs_host.assign((const char*)probs.data(), (const char*)probs.data() + probs.size() * sizeof(Prob3D<T>));
     int per_sm = 0;
-    e = sweep3d_occupancy<T>(c->T1, c->NW, mr2, mr3, &per_sm);
+    e = sweep3d_occupancy<T>(c->T1, c->NW, mr2, mr3, c->bf16 ? 1 : 0, &per_sm);
     if (e != cudaSuccess) return cuda_fail(c, e, "occupancy");
     if (per_sm < 1) return fail(c, DVM_EINVAL, "3D sweep kernel does not fit on an SM with these pencils");
     int dev = 0, sms = 0;
@@ -807,6 +810,7 @@ dvm_status enqueue_iter_3d(dvm_ctx* c) {
     a.T1 = c->T1;
     a.maxR2 = c->max_rows / 1000;
     a.maxR3 = c->max_rows % 1000;
+    a.bf16 = c->bf16 ? 1 : 0;
     a.parity = (int)(c->iters & 1);
     a.ticket = c->counters_dev;
     a.status = c->status_dev;
@@ -940,10 +944,11 @@ void state_segs_3d(const Prob3D<T>& P, size_t NL, int par, std::vector<Seg>& out
     const size_t gx = (size_t)8 * P.n3 * P.n2 * 2 * NL;
     const size_t gy = (size_t)8 * P.n3 * P.n1 * 2 * NL;
     const size_t gz = (size_t)8 * P.n2 * P.n1 * 2 * NL;
+    const size_t es = P.bf16 ? 2 : sizeof(T);
     out.push_back({P.P, (size_t)8 * P.ngroups * 4 * P.N * sizeof(T)});
-    out.push_back({P.gx1 + par * gx, gx * sizeof(T)});
-    out.push_back({P.gy + par * gy, gy * sizeof(T)});
-    out.push_back({P.gz + par * gz, gz * sizeof(T)});
+    out.push_back({(char*)P.gx1 + par * gx * es, gx * es});
+    out.push_back({(char*)P.gy + par * gy * es, gy * es});
+    out.push_back({(char*)P.gz + par * gz * es, gz * es});
 }
 
 std::vector<Seg> state_segments(const dvm_ctx* c, int par) {
@@ -980,7 +985,7 @@ StateHeader state_header(const dvm_ctx* c) {
     std::memcpy(h.magic, kStateMagic, 8);
     h.version = 1;
     h.dims = c->dims;
-    h.precision = c->prec;
+    h.precision = c->opt.precision;
     h.nprob = c->nprob;
     h.nv = c->nv;
     h.NL = c->NL;
@@ -1076,7 +1081,10 @@ dvm_status dvm_create_batch(int nprob, const dvm_geometry* geoms, const double* 
     if (nprob < 1 || !geoms || !kn) return reject(DVM_EINVAL, "no problems");
     const int dims = geoms[0].dims;
     if (dims != 2 && dims != 3) return reject(DVM_EINVAL, "dims must be 2 or 3");
-    if (c->opt.precision != DVM_FP64 && c->opt.precision != DVM_FP32) return reject(DVM_EINVAL, "precision");
+    if (c->opt.precision != DVM_FP64 && c->opt.precision != DVM_FP32 && c->opt.precision != DVM_BF16_STORE)
+        return reject(DVM_EINVAL, "precision");
+    if (c->opt.precision == DVM_BF16_STORE && dims != 3)
+        return reject(DVM_EINVAL, "BF16 storage is implemented for 3D problems only");
     if (c->opt.stencil_order != 1 && c->opt.stencil_order != 2) return reject(DVM_EINVAL, "stencil_order");
     if (c->opt.lateral_bc != 0 && c->opt.lateral_bc != 1) return reject(DVM_EINVAL, "lateral_bc");
     if (c->opt.check_interval < 1) return reject(DVM_EINVAL, "check_interval");
@@ -1086,7 +1094,8 @@ dvm_status dvm_create_batch(int nprob, const dvm_geometry* geoms, const double* 
         return reject(DVM_EINVAL, "lagged-halo subdomains are implemented along x2 of 2D problems only");
     c->dims = dims;
     c->nprob = nprob;
-    c->prec = c->opt.precision;
+    c->prec = c->opt.precision == DVM_BF16_STORE ? DVM_FP32 : c->opt.precision;
+    c->bf16 = c->opt.precision == DVM_BF16_STORE;
     c->stream = (cudaStream_t)c->opt.stream;
     if (validate_grid(c, dims, grid) != DVM_OK) {
         const std::string m = c->err;

@@ -94,13 +94,17 @@ struct Prob3D {
     int R2, R3, np2, np3;   // pencil rows and pencil counts
     int ngroups;            // velocity groups per octant
     int lateral, order;
+    int bf16;               // 1: ghosts and pencil edges hold BF16 deviations from the x1 ramp
+                            //    (h' - x1 of the point the value belongs to), 2 bytes each
     double kn, nu, dx;
     double dinv[3];
     const uint16_t* code;   // [N]
     T* src;                 // [N][4]  (nu rho', 2 nu u1 + 1, 2 nu u2, 2 nu u3)
     T* E;                   // [N][8]  wall terms, index 2 j + u (6 used)
     T* P;                   // [8][G][4][N] moment partials per octant and velocity group
-    T* gx1;                 // [2][8][n3 * n2][2][NL] x1 ghosts (parity, octant, row (k, j), layer, lane)
+    T* gx1;                 // [2][8][n3 * n2][2][NL] x1 ghosts (parity, octant, row (k, j), layer, lane);
+                            // ghosts and edges are T, or BF16 when bf16 is set (element offsets
+                            // are the same, the pointers are reinterpreted)
     T* gy;                  // [2][8][n3 * n1][2][NL] x2 ghosts (row (k, i))
     T* gz;                  // [2][8][n2 * n1][2][NL] x3 ghosts (row (j, i))
     T* ey;                  // [8][np3][np2 - 1][R3][n1][2][NL] x2 edges between pencils
@@ -127,6 +131,7 @@ struct SweepArgs3D {
     int GL;                     // lanes per velocity group (= 32 x warps per CTA)
     int T1;
     int maxR2, maxR3;
+    int bf16;                   // ghosts and pencil edges stored as BF16 (see Prob3D::bf16)
     int parity;
     int* ticket;
     int* status;

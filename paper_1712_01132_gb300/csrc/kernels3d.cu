@@ -11,6 +11,7 @@
 // finalize3d: sums the octant/group moment partials, forms the FP64 wall densities (Eq. 6), the
 //             next sources and wall terms, and the FP64 sum of u1 for Eq. 11-12.
 // init3d, moments3d, wall3d: start state and readouts.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -40,11 +41,30 @@ __device__ __forceinline__ double ibits(double, int v) { return __longlong_as_do
 __device__ __forceinline__ int tbits(float v) { return __float_as_int(v); }
 __device__ __forceinline__ int tbits(double v) { return (int)__double_as_longlong(v); }
 
+// Transient h kept in HBM between pencils and iterations (ghost layers, pencil edges): stored as T,
+// or (BF16 storage ablation) as the BF16 rounding (round to nearest even) of the deviation from the
+// x1 ramp, h' - x1 with x1 the coordinate of the point the value belongs to, which keeps the
+// stored numbers at the size of the perturbation instead of the O(1) ramp.
+template <typename T, bool BF> struct HStore {
+    static __device__ __forceinline__ T ld(const T* b, size_t i, T) { return __ldcg(b + i); }
+    static __device__ __forceinline__ void st(T* b, size_t i, T v, T) { b[i] = v; }
+};
+template <> struct HStore<float, true> {
+    static __device__ __forceinline__ float ld(const float* b, size_t i, float x1) {
+        const unsigned short u = __ldcg(reinterpret_cast<const unsigned short*>(b) + i);
+        return __bfloat162float(__ushort_as_bfloat16(u)) + x1;
+    }
+    static __device__ __forceinline__ void st(float* b, size_t i, float v, float x1) {
+        reinterpret_cast<__nv_bfloat16*>(b)[i] = __float2bfloat16_rn(v - x1);
+    }
+};
+
 }  // namespace
 
-template <typename T, int T1>
+template <typename T, int T1, bool BF>
 __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
     using V = typename V4t<T>::type;
+    using HS = HStore<T, BF>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
     __shared__ int s_abort;
@@ -89,15 +109,19 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
         const int par = a.parity;
         const int G = P->ngroups;
         int* prog = P->prog + ((size_t)q * G + g) * np3 * np2;
+        // x1 coordinate of oriented column ic (the shift of the BF16 storage)
+        const T dxT = (T)P->dx;
+        auto x1of = [&](int ic) -> T { return (T)(s1n ? n1 - 1 - ic : ic) * dxT; };
+        const T x1g0 = x1of(n1 - 1), x1g1 = x1of(n1 - 2);   // columns of the x1 ghost layers
         // x1 upstream of the first tile: x1 ghost layers (oriented rows (k, j))
         {
-            const T* gx = P->gx1 + (((size_t)par * 8 + q) * n3 * n2) * 2 * NL;
+            const size_t gxo = (((size_t)par * 8 + q) * n3 * n2) * 2 * NL;
             for (int kk = 0; kk < nr3; ++kk)
                 for (int jj = 0; jj < nr2; ++jj) {
                     const size_t row = (size_t)(k0 + kk) * n2 + (j0 + jj);
                     T* cr = carry + ((size_t)(warp * MROWS + kk * MR2 + jj) * 2) * 32 + lane;
-                    cr[0] = gx[(row * 2 + 0) * NL + lv];
-                    cr[32] = gx[(row * 2 + 1) * NL + lv];
+                    cr[0] = HS::ld(P->gx1, gxo + (row * 2 + 0) * NL + lv, x1g0);
+                    cr[32] = HS::ld(P->gx1, gxo + (row * 2 + 1) * NL + lv, x1g1);
                 }
         }
         const int ntiles = (n1 + T1 - 1) / T1;
@@ -155,30 +179,34 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
             // x3 upstream planes of the first plane of the pencil: the pencil below in x3 or the
             // x3 ghost layers (periodic or specular, Eq. 8)
             {
-                const T* zb = (p3 == 0)
-                    ? P->gz + (((size_t)par * 8 + q) * n2 * n1) * 2 * NL
-                    : P->ez + ((((size_t)q * np2 + p2) * (np3 - 1) + (p3 - 1)) * P->R2 * n1) * 2 * NL;
+                const T* zb = (p3 == 0) ? P->gz : P->ez;
+                const size_t zo = (p3 == 0)
+                    ? (((size_t)par * 8 + q) * n2 * n1) * 2 * NL
+                    : ((((size_t)q * np2 + p2) * (np3 - 1) + (p3 - 1)) * P->R2 * n1) * 2 * NL;
                 for (int jj = 0; jj < nr2; ++jj)
                     for (int i = 0; i < width; ++i) {
                         const size_t row = (p3 == 0) ? ((size_t)(j0 + jj) * n1 + (c0 + i)) : ((size_t)jj * n1 + (c0 + i));
                         T* d = pb + ((((size_t)warp * MR2 + jj) * 2) * T1 + i) * 32 + lane;
-                        d[0] = __ldcg(zb + (row * 2 + 0) * NL + lv);
-                        d[(size_t)T1 * 32] = __ldcg(zb + (row * 2 + 1) * NL + lv);
+                        const T xs = x1of(c0 + i);
+                        d[0] = HS::ld(zb, zo + (row * 2 + 0) * NL + lv, xs);
+                        d[(size_t)T1 * 32] = HS::ld(zb, zo + (row * 2 + 1) * NL + lv, xs);
                     }
             }
             for (int kk = 0; kk < nr3; ++kk) {
                 // x2 upstream rows of the first row of this plane
                 T rb1[T1], rb2[T1];
                 {
-                    const T* yb = (p2 == 0)
-                        ? P->gy + (((size_t)par * 8 + q) * n3 * n1) * 2 * NL
-                        : P->ey + ((((size_t)q * np3 + p3) * (np2 - 1) + (p2 - 1)) * P->R3 * n1) * 2 * NL;
+                    const T* yb = (p2 == 0) ? P->gy : P->ey;
+                    const size_t yo = (p2 == 0)
+                        ? (((size_t)par * 8 + q) * n3 * n1) * 2 * NL
+                        : ((((size_t)q * np3 + p3) * (np2 - 1) + (p2 - 1)) * P->R3 * n1) * 2 * NL;
                     const size_t rowbase = (p2 == 0) ? (size_t)(k0 + kk) * n1 : (size_t)kk * n1;
 #pragma unroll
                     for (int i = 0; i < T1; ++i) {
                         if (i < width) {
-                            rb1[i] = __ldcg(yb + ((rowbase + c0 + i) * 2 + 0) * NL + lv);
-                            rb2[i] = __ldcg(yb + ((rowbase + c0 + i) * 2 + 1) * NL + lv);
+                            const T xs = x1of(c0 + i);
+                            rb1[i] = HS::ld(yb, yo + ((rowbase + c0 + i) * 2 + 0) * NL + lv, xs);
+                            rb2[i] = HS::ld(yb, yo + ((rowbase + c0 + i) * 2 + 1) * NL + lv, xs);
                         } else {
                             rb1[i] = T(0);
                             rb2[i] = T(0);
@@ -242,20 +270,23 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                 // next iteration (periodic: same octant; specular: octant with s2 flipped)
                 {
                     T* et;
-                    size_t rowbase;
+                    size_t eo, rowbase;
                     if (p2 < np2 - 1) {
-                        et = P->ey + ((((size_t)q * np3 + p3) * (np2 - 1) + p2) * P->R3 * n1) * 2 * NL;
+                        et = P->ey;
+                        eo = ((((size_t)q * np3 + p3) * (np2 - 1) + p2) * P->R3 * n1) * 2 * NL;
                         rowbase = (size_t)kk * n1;
                     } else {
                         const int qy = (P->lateral == 1) ? q : (q ^ 2);
-                        et = P->gy + (((size_t)(par ^ 1) * 8 + qy) * n3 * n1) * 2 * NL;
+                        et = P->gy;
+                        eo = (((size_t)(par ^ 1) * 8 + qy) * n3 * n1) * 2 * NL;
                         rowbase = (size_t)(k0 + kk) * n1;
                     }
 #pragma unroll
                     for (int i = 0; i < T1; ++i) {
                         if (i < width) {
-                            et[((rowbase + c0 + i) * 2 + 0) * NL + lv] = rb1[i];
-                            et[((rowbase + c0 + i) * 2 + 1) * NL + lv] = rb2[i];
+                            const T xs = x1of(c0 + i);
+                            HS::st(et, eo + ((rowbase + c0 + i) * 2 + 0) * NL + lv, rb1[i], xs);
+                            HS::st(et, eo + ((rowbase + c0 + i) * 2 + 1) * NL + lv, rb2[i], xs);
                         }
                     }
                 }
@@ -263,29 +294,33 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
             // x3 edge for the pencil above in x3, or the x3 ghost layers of the next iteration
             {
                 T* et;
+                size_t eo;
                 const bool last = (p3 == np3 - 1);
                 if (!last) {
-                    et = P->ez + ((((size_t)q * np2 + p2) * (np3 - 1) + p3) * P->R2 * n1) * 2 * NL;
+                    et = P->ez;
+                    eo = ((((size_t)q * np2 + p2) * (np3 - 1) + p3) * P->R2 * n1) * 2 * NL;
                 } else {
                     const int qz = (P->lateral == 1) ? q : (q ^ 4);
-                    et = P->gz + (((size_t)(par ^ 1) * 8 + qz) * n2 * n1) * 2 * NL;
+                    et = P->gz;
+                    eo = (((size_t)(par ^ 1) * 8 + qz) * n2 * n1) * 2 * NL;
                 }
                 for (int jj = 0; jj < nr2; ++jj)
                     for (int i = 0; i < width; ++i) {
                         const size_t row = last ? ((size_t)(j0 + jj) * n1 + (c0 + i)) : ((size_t)jj * n1 + (c0 + i));
                         const T* s = pb + ((((size_t)warp * MR2 + jj) * 2) * T1 + i) * 32 + lane;
-                        et[(row * 2 + 0) * NL + lv] = s[0];
-                        et[(row * 2 + 1) * NL + lv] = s[(size_t)T1 * 32];
+                        const T xs = x1of(c0 + i);
+                        HS::st(et, eo + (row * 2 + 0) * NL + lv, s[0], xs);
+                        HS::st(et, eo + (row * 2 + 1) * NL + lv, s[(size_t)T1 * 32], xs);
                     }
             }
             if (t == ntiles - 1) {
-                T* gx = P->gx1 + (((size_t)(par ^ 1) * 8 + q) * n3 * n2) * 2 * NL;
+                const size_t gxo = (((size_t)(par ^ 1) * 8 + q) * n3 * n2) * 2 * NL;
                 for (int kk = 0; kk < nr3; ++kk)
                     for (int jj = 0; jj < nr2; ++jj) {
                         const size_t row = (size_t)(k0 + kk) * n2 + (j0 + jj);
                         const T* cr = carry + ((size_t)(warp * MROWS + kk * MR2 + jj) * 2) * 32 + lane;
-                        gx[(row * 2 + 0) * NL + lv] = cr[0];
-                        gx[(row * 2 + 1) * NL + lv] = cr[32];
+                        HS::st(P->gx1, gxo + (row * 2 + 0) * NL + lv, cr[0], x1g0);
+                        HS::st(P->gx1, gxo + (row * 2 + 1) * NL + lv, cr[32], x1g1);
                     }
             }
             __syncthreads();
@@ -406,6 +441,14 @@ __global__ void __launch_bounds__(256) finalize3d_kernel(const FinArgs3D<T> a) {
     }
 }
 
+// Store h' (source form) of a point with x1 coordinate x1 into a ghost or edge array, in the
+// array's storage form (T, or the BF16 deviation from the ramp).
+template <typename T>
+__device__ __forceinline__ void put_h(const Prob3D<T>* P, T* base, size_t i, double hp, double x1) {
+    if (P->bf16) reinterpret_cast<__nv_bfloat16*>(base)[i] = __float2bfloat16_rn((float)(hp - x1));
+    else base[i] = (T)hp;
+}
+
 // Zero-perturbation start in the kernels' source-form variables (h' = x1).
 template <typename T>
 __global__ void init3d_kernel(const Prob3D<T>* P, int NL, const double* qw /*[8][G][4]*/) {
@@ -424,19 +467,19 @@ __global__ void init3d_kernel(const Prob3D<T>* P, int NL, const double* qw /*[8]
         const int q = (idx / (nl * 2 * n3 * n2)) % 8;
         const int ico = n1 - 1 - layer;
         const int col = (q & 1) ? n1 - 1 - ico : ico;
-        P->gx1[idx] = (T)(col * P->dx);
+        put_h(P, P->gx1, idx, col * P->dx, col * P->dx);
     }
     for (size_t idx = t0; idx < (size_t)2 * 8 * n3 * n1 * 2 * nl; idx += stride) {
         const int ic = (idx / (nl * 2)) % n1;
         const int q = (idx / (nl * 2 * n3 * n1)) % 8;
         const int col = (q & 1) ? n1 - 1 - ic : ic;
-        P->gy[idx] = (T)(col * P->dx);
+        put_h(P, P->gy, idx, col * P->dx, col * P->dx);
     }
     for (size_t idx = t0; idx < (size_t)2 * 8 * n2 * n1 * 2 * nl; idx += stride) {
         const int ic = (idx / (nl * 2)) % n1;
         const int q = (idx / (nl * 2 * n2 * n1)) % 8;
         const int col = (q & 1) ? n1 - 1 - ic : ic;
-        P->gz[idx] = (T)(col * P->dx);
+        put_h(P, P->gz, idx, col * P->dx, col * P->dx);
     }
 }
 
@@ -452,13 +495,15 @@ __global__ void warm3d_kernel(const Prob3D<T>* P, int NL, int par, const double*
     const size_t nl = NL;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    auto h0 = [&](int q, int io, int jo, int ko, const double* v) -> double {
+    // h0' at the oriented point (io, jo, ko) of octant q; x1 receives the point's x1 coordinate
+    auto h0 = [&](int q, int io, int jo, int ko, const double* v, double& x1) -> double {
         const int x = (q & 1) ? n1 - 1 - io : io;
         const int y = (q & 2) ? n2 - 1 - jo : jo;
         const int z = (q & 4) ? n3 - 1 - ko : ko;
         const size_t id = ((size_t)z * n2 + y) * n1 + x;
+        x1 = x * P->dx;
         if (P->code[id] & kSolidBit) return 0.0;
-        return rho0[id] + x * P->dx + 2.0 * (u0[id] * v[0] + u0[N + id] * v[1] + u0[2 * (size_t)N + id] * v[2]);
+        return rho0[id] + x1 + 2.0 * (u0[id] * v[0] + u0[N + id] * v[1] + u0[2 * (size_t)N + id] * v[2]);
     };
     for (size_t idx = t0; idx < (size_t)8 * G * 4 * N; idx += stride) {
         const size_t id = idx % N;
@@ -477,8 +522,9 @@ __global__ void warm3d_kernel(const Prob3D<T>* P, int NL, int par, const double*
         const int layer = (idx / nl) % 2;
         const int row = (idx / (nl * 2)) % ((size_t)n3 * n2);
         const int q = idx / (nl * 2 * n3 * n2);
-        P->gx1[(size_t)par * 8 * n3 * n2 * 2 * nl + idx] =
-            (T)h0(q, n1 - 1 - layer, row % n2, row / n2, vel + ((size_t)q * nl + l) * 3);
+        double x1;
+        const double hv = h0(q, n1 - 1 - layer, row % n2, row / n2, vel + ((size_t)q * nl + l) * 3, x1);
+        put_h(P, P->gx1, (size_t)par * 8 * n3 * n2 * 2 * nl + idx, hv, x1);
     }
     // x2 ghosts: octant q writes its oriented rows n2 - 1 - layer for the octant that reads them
     for (size_t idx = t0; idx < (size_t)8 * n3 * n1 * 2 * nl; idx += stride) {
@@ -487,8 +533,9 @@ __global__ void warm3d_kernel(const Prob3D<T>* P, int NL, int par, const double*
         const int row = (idx / (nl * 2)) % ((size_t)n3 * n1);
         const int q = idx / (nl * 2 * n3 * n1);
         const int qy = (P->lateral == 1) ? q : (q ^ 2);
-        P->gy[((((size_t)par * 8 + qy) * n3 * n1 + row) * 2 + layer) * nl + l] =
-            (T)h0(q, row % n1, n2 - 1 - layer, row / n1, vel + ((size_t)q * nl + l) * 3);
+        double x1;
+        const double hv = h0(q, row % n1, n2 - 1 - layer, row / n1, vel + ((size_t)q * nl + l) * 3, x1);
+        put_h(P, P->gy, ((((size_t)par * 8 + qy) * n3 * n1 + row) * 2 + layer) * nl + l, hv, x1);
     }
     // x3 ghosts: octant q writes its oriented planes n3 - 1 - layer for the octant that reads them
     for (size_t idx = t0; idx < (size_t)8 * n2 * n1 * 2 * nl; idx += stride) {
@@ -497,8 +544,9 @@ __global__ void warm3d_kernel(const Prob3D<T>* P, int NL, int par, const double*
         const int row = (idx / (nl * 2)) % ((size_t)n2 * n1);
         const int q = idx / (nl * 2 * n2 * n1);
         const int qz = (P->lateral == 1) ? q : (q ^ 4);
-        P->gz[((((size_t)par * 8 + qz) * n2 * n1 + row) * 2 + layer) * nl + l] =
-            (T)h0(q, row % n1, row / n1, n3 - 1 - layer, vel + ((size_t)q * nl + l) * 3);
+        double x1;
+        const double hv = h0(q, row % n1, row / n1, n3 - 1 - layer, vel + ((size_t)q * nl + l) * 3, x1);
+        put_h(P, P->gz, ((((size_t)par * 8 + qz) * n2 * n1 + row) * 2 + layer) * nl + l, hv, x1);
     }
 }
 
@@ -542,34 +590,52 @@ size_t sweep3d_smem(int T1, int NW, int R2, int R3) {
                         (size_t)NW * R2 * 2 * T1 * 32 + (size_t)NW * 8 * 32);
 }
 
-template <typename T, int T1>
+// BF16 storage exists for FP32 arithmetic only
+template <typename T> struct HasBF { static constexpr bool value = false; };
+template <> struct HasBF<float> { static constexpr bool value = true; };
+
+template <typename T, int T1, bool BF>
 static cudaError_t occ3(int NW, int R2, int R3, int* blocks_per_sm) {
     const size_t smem = sweep3d_smem<T>(T1, NW, R2, R3);
-    cudaError_t e = cudaFuncSetAttribute(sweep3d_kernel<T, T1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(sweep3d_kernel<T, T1, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep3d_kernel<T, T1>, NW * 32, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep3d_kernel<T, T1, BF>, NW * 32, smem);
 }
 
 template <typename T>
-cudaError_t sweep3d_occupancy(int T1, int NW, int R2, int R3, int* blocks_per_sm) {
-    if (T1 == 4) return occ3<T, 4>(NW, R2, R3, blocks_per_sm);
-    if (T1 == 8) return occ3<T, 8>(NW, R2, R3, blocks_per_sm);
+cudaError_t sweep3d_occupancy(int T1, int NW, int R2, int R3, int bf16, int* blocks_per_sm) {
+    if (bf16) {
+        if constexpr (HasBF<T>::value) {
+            if (T1 == 4) return occ3<T, 4, true>(NW, R2, R3, blocks_per_sm);
+            if (T1 == 8) return occ3<T, 8, true>(NW, R2, R3, blocks_per_sm);
+        }
+        return cudaErrorInvalidValue;
+    }
+    if (T1 == 4) return occ3<T, 4, false>(NW, R2, R3, blocks_per_sm);
+    if (T1 == 8) return occ3<T, 8, false>(NW, R2, R3, blocks_per_sm);
     return cudaErrorInvalidValue;
 }
 
-template <typename T, int T1>
+template <typename T, int T1, bool BF>
 static cudaError_t launch3(const SweepArgs3D<T>& a, int grid, int NW, cudaStream_t st) {
     const size_t smem = sweep3d_smem<T>(T1, NW, a.maxR2, a.maxR3);
-    cudaError_t e = cudaFuncSetAttribute(sweep3d_kernel<T, T1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(sweep3d_kernel<T, T1, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    sweep3d_kernel<T, T1><<<grid, NW * 32, smem, st>>>(a);
+    sweep3d_kernel<T, T1, BF><<<grid, NW * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_sweep3d(const SweepArgs3D<T>& a, int grid, int NW, cudaStream_t st) {
-    if (a.T1 == 4) return launch3<T, 4>(a, grid, NW, st);
-    if (a.T1 == 8) return launch3<T, 8>(a, grid, NW, st);
+    if (a.bf16) {
+        if constexpr (HasBF<T>::value) {
+            if (a.T1 == 4) return launch3<T, 4, true>(a, grid, NW, st);
+            if (a.T1 == 8) return launch3<T, 8, true>(a, grid, NW, st);
+        }
+        return cudaErrorInvalidValue;
+    }
+    if (a.T1 == 4) return launch3<T, 4, false>(a, grid, NW, st);
+    if (a.T1 == 8) return launch3<T, 8, false>(a, grid, NW, st);
     return cudaErrorInvalidValue;
 }
 
@@ -606,7 +672,7 @@ cudaError_t launch_wall3d(const Prob3D<T>* p, double* out, cudaStream_t st) {
 
 #define DVM_INSTANTIATE3(T)                                                                     \
     template size_t sweep3d_smem<T>(int, int, int, int);                                       \
-    template cudaError_t sweep3d_occupancy<T>(int, int, int, int, int*);                       \
+    template cudaError_t sweep3d_occupancy<T>(int, int, int, int, int, int*);                  \
     template cudaError_t launch_sweep3d<T>(const SweepArgs3D<T>&, int, int, cudaStream_t);     \
     template cudaError_t launch_finalize3d<T>(const FinArgs3D<T>&, int, cudaStream_t);         \
     template cudaError_t launch_init3d<T>(const Prob3D<T>*, int, const double*, cudaStream_t); \

@@ -13,7 +13,7 @@ import numpy as np
 from . import build as _build
 
 DVM_OK, DVM_NOT_CONVERGED, DVM_EINVAL, DVM_ENOMEM, DVM_ECUDA, DVM_ETIMEOUT, DVM_ENUMERIC = 0, 1, -1, -2, -3, -4, -5
-DVM_FP64, DVM_FP32 = 0, 1
+DVM_FP64, DVM_FP32, DVM_BF16_STORE = 0, 1, 2
 DVM_LATERAL_SPECULAR, DVM_LATERAL_PERIODIC = 0, 1
 
 _STATUS_NAMES = {0: "DVM_OK", 1: "DVM_NOT_CONVERGED", -1: "DVM_EINVAL", -2: "DVM_ENOMEM", -3: "DVM_ECUDA",
@@ -189,7 +189,7 @@ def make_options(precision="fp64", stencil_order=2, lateral="specular", check_in
     """dvm_options with torch's current stream (unless stream is given) and, by default, torch's
     caching allocator for device memory.  Returns (options, keepalive)."""
     o = dvm_default_options()
-    o.precision = {"fp64": DVM_FP64, "fp32": DVM_FP32}[precision]
+    o.precision = {"fp64": DVM_FP64, "fp32": DVM_FP32, "bf16_store": DVM_BF16_STORE}[precision]
     o.stencil_order = int(stencil_order)
     o.lateral_bc = {"specular": DVM_LATERAL_SPECULAR, "periodic": DVM_LATERAL_PERIODIC}[lateral]
     o.check_interval = int(check_interval)
