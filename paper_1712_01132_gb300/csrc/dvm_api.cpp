@@ -318,9 +318,15 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
                 const int lo = s2neg ? P.n2 - Y[c2 - sp] : Y[sp];
                 const int hi = s2neg ? P.n2 - Y[c2 - 1 - sp] : Y[sp + 1];
                 slot_row[(size_t)q * c2 + sp] = sp == 0 ? P.n2 : lo;
-                for (int r0 = lo; r0 < hi; r0 += P.rows) {
+                // live edges use ring slots 2 sp + (local band & 1): two suffice, since band j + 2
+                // of a subdomain reaches tile t only after band j + 1 consumed band j's edge of
+                // tile t; every subdomain has its own pair because its first band does not wait
+                int j = 0;
+                for (int r0 = lo; r0 < hi; r0 += P.rows, ++j) {
                     const int nr = std::min(P.rows, hi - r0);
-                    qb[q].push_back(make_int4(r0, nr, r0 == lo ? sp : -1, r0 + nr == hi ? (sp + 1) % c2 : -1));
+                    const int below = r0 == lo ? sp : -1 - (2 * sp + ((j - 1) & 1));
+                    const int above = r0 + nr == hi ? (sp + 1) % c2 : -1 - (2 * sp + (j & 1));
+                    qb[q].push_back(make_int4(r0, nr, below, above));
                 }
             }
         }
@@ -361,7 +367,7 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         P.P = (T*)dev_alloc(c, (size_t)NQ * 3 * N * sizeof(T));
         P.gx1 = (T*)dev_alloc(c, (size_t)2 * NQ * P.n2 * 2 * NL * sizeof(T));
         P.glat = (T*)dev_alloc(c, (size_t)2 * NQ * P.nslots * P.n1 * 2 * NL * sizeof(T));
-        P.edge = (T*)dev_alloc(c, (size_t)NQ * std::max(P.nbands - 1, 1) * P.n1 * 2 * NL * sizeof(T));
+        P.edge = (T*)dev_alloc(c, (size_t)NQ * 2 * P.nslots * P.n1 * 2 * NL * sizeof(T));
         T* lanec = (T*)dev_alloc(c, (size_t)NQ * NL * kLaneConsts * sizeof(T));
         P.fin_nblocks = (int)((N + kFinBlock - 1) / kFinBlock);
         P.fin_block0 = (int)blk_prob.size();
@@ -380,7 +386,7 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         if (e != cudaSuccess) return cuda_fail(c, e, "memset");
         e = cudaMemsetAsync(P.kval, 0, 3 * sizeof(double), c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "memset");
-        e = cudaMemsetAsync(P.edge, 0, (size_t)NQ * std::max(P.nbands - 1, 1) * P.n1 * 2 * NL * sizeof(T), c->stream);
+        e = cudaMemsetAsync(P.edge, 0, (size_t)NQ * 2 * P.nslots * P.n1 * 2 * NL * sizeof(T), c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "memset");
         // lane constants: v1, v2, |v1|/dx, |v2|/dx, W, W v1, W v2, R[0..3]
         std::vector<T> lc((size_t)NQ * NL * kLaneConsts, T(0));
@@ -617,8 +623,10 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         P.gx1 = (T*)dev_alloc(c, (size_t)2 * NO * n3 * n2 * 2 * NL * es);
         P.gy = (T*)dev_alloc(c, (size_t)2 * NO * n3 * n1 * 2 * NL * es);
         P.gz = (T*)dev_alloc(c, (size_t)2 * NO * n2 * n1 * 2 * NL * es);
-        const size_t ey_sz = (size_t)NO * P.np3 * std::max(P.np2 - 1, 1) * P.R3 * n1 * 2 * NL;
-        const size_t ez_sz = (size_t)NO * P.np2 * std::max(P.np3 - 1, 1) * P.R2 * n1 * 2 * NL;
+        // pencil edges: two slots per pencil column suffice (pencil p + 2 reaches tile t only after
+        // pencil p + 1 has consumed pencil p's edge of tile t)
+        const size_t ey_sz = (size_t)NO * P.np3 * 2 * P.R3 * n1 * 2 * NL;
+        const size_t ez_sz = (size_t)NO * P.np2 * 2 * P.R2 * n1 * 2 * NL;
         P.ey = (T*)dev_alloc(c, ey_sz * es);
         P.ez = (T*)dev_alloc(c, ez_sz * es);
         T* lanec = (T*)dev_alloc(c, (size_t)NO * NL * kLaneConsts3 * sizeof(T));

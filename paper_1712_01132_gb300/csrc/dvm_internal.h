@@ -38,7 +38,8 @@ struct Prob2D {
     int nslots;          // lagged x2 slots per quadrant: slot 0 is the domain face, slot s >= 1 the
                          // bottom of the s-th x2 subdomain (lagged-halo decomposition, Sec. 3.2)
     const int4* bands;   // [4][nbands] per quadrant, in oriented rows: {first row, rows, below,
-                         // above}; below/above = -1: a live band edge, s >= 0: lagged slot s
+                         // above}; below/above = s >= 0: lagged slot s; -1 - e: live band edge in
+                         // ring slot e (two slots per subdomain, alternating between its bands)
     const int* slot_row; // [4][nslots] oriented row just above the layers a slot holds (slot 0: n2)
     int lateral;         // 0 specular, 1 periodic
     int order;           // 2 or 1
@@ -51,7 +52,7 @@ struct Prob2D {
     T* gx1;              // [2][4][n2][2][NL] x1 ghost layers (parity, quadrant, row, layer, lane)
     T* glat;             // [2][4][nslots][n1][2][NL] lagged x2 layers (parity, quadrant, slot, col,
                          // layer, lane): the x2 ghosts (slot 0) and the subdomain halos
-    T* edge;             // [4][nbands-1][2][n1][NL] band-to-band edges
+    T* edge;             // [4][2 nslots][n1][2][NL] band-to-band edges (ring slots, see bands)
     int* prog;           // [4][nbands] tiles completed per band in this iteration
     const T* lanec;      // [4][NL][kLaneConsts]
     double* kpart;       // [nfinblocks] partial sums of u1 (FP64)
@@ -107,8 +108,8 @@ struct Prob3D {
                             // are the same, the pointers are reinterpreted)
     T* gy;                  // [2][8][n3 * n1][2][NL] x2 ghosts (row (k, i))
     T* gz;                  // [2][8][n2 * n1][2][NL] x3 ghosts (row (j, i))
-    T* ey;                  // [8][np3][np2 - 1][R3][n1][2][NL] x2 edges between pencils
-    T* ez;                  // [8][np2][np3 - 1][R2][n1][2][NL] x3 edges between pencils
+    T* ey;                  // [8][np3][2][R3][n1][2][NL] x2 edges between pencils (slot p2 & 1)
+    T* ez;                  // [8][np2][2][R2][n1][2][NL] x3 edges between pencils (slot p3 & 1)
     int* prog;              // [8][G][np3][np2] tiles completed
     const T* lanec;         // [8][NL][kLaneConsts3]
     double* kpart;

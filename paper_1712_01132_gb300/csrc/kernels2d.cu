@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs2D<T> a) {
             {
                 const T* eb = (below >= 0)
                     ? P->glat + (((size_t)(par * 4 + q) * P->nslots + below) * n1) * 2 * NL
-                    : P->edge + ((size_t)(q * (nb - 1) + band - 1) * n1) * 2 * NL;
+                    : P->edge + ((size_t)(q * 2 * P->nslots + (-1 - below)) * n1) * 2 * NL;
 #pragma unroll
                 for (int i = 0; i < T1; ++i) {
                     if (i < width) {
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs2D<T> a) {
             {
                 T* et;
                 if (above < 0) {
-                    et = P->edge + ((size_t)(q * (nb - 1) + band) * n1) * 2 * NL;
+                    et = P->edge + ((size_t)(q * 2 * P->nslots + (-1 - above)) * n1) * 2 * NL;
                 } else {
                     const int qd = (above > 0 || P->lateral == 1) ? q : (q ^ 2);
                     et = P->glat + (((size_t)((par ^ 1) * 4 + qd) * P->nslots + above) * n1) * 2 * NL;

@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                 const T* zb = (p3 == 0) ? P->gz : P->ez;
                 const size_t zo = (p3 == 0)
                     ? (((size_t)par * 8 + q) * n2 * n1) * 2 * NL
-                    : ((((size_t)q * np2 + p2) * (np3 - 1) + (p3 - 1)) * P->R2 * n1) * 2 * NL;
+                    : ((((size_t)q * np2 + p2) * 2 + ((p3 - 1) & 1)) * P->R2 * n1) * 2 * NL;
                 for (int jj = 0; jj < nr2; ++jj)
                     for (int i = 0; i < width; ++i) {
                         const size_t row = (p3 == 0) ? ((size_t)(j0 + jj) * n1 + (c0 + i)) : ((size_t)jj * n1 + (c0 + i));
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                     const T* yb = (p2 == 0) ? P->gy : P->ey;
                     const size_t yo = (p2 == 0)
                         ? (((size_t)par * 8 + q) * n3 * n1) * 2 * NL
-                        : ((((size_t)q * np3 + p3) * (np2 - 1) + (p2 - 1)) * P->R3 * n1) * 2 * NL;
+                        : ((((size_t)q * np3 + p3) * 2 + ((p2 - 1) & 1)) * P->R3 * n1) * 2 * NL;
                     const size_t rowbase = (p2 == 0) ? (size_t)(k0 + kk) * n1 : (size_t)kk * n1;
 #pragma unroll
                     for (int i = 0; i < T1; ++i) {
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                     size_t eo, rowbase;
                     if (p2 < np2 - 1) {
                         et = P->ey;
-                        eo = ((((size_t)q * np3 + p3) * (np2 - 1) + p2) * P->R3 * n1) * 2 * NL;
+                        eo = ((((size_t)q * np3 + p3) * 2 + (p2 & 1)) * P->R3 * n1) * 2 * NL;
                         rowbase = (size_t)kk * n1;
                     } else {
                         const int qy = (P->lateral == 1) ? q : (q ^ 2);
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                 const bool last = (p3 == np3 - 1);
                 if (!last) {
                     et = P->ez;
-                    eo = ((((size_t)q * np2 + p2) * (np3 - 1) + p3) * P->R2 * n1) * 2 * NL;
+                    eo = ((((size_t)q * np2 + p2) * 2 + (p3 & 1)) * P->R2 * n1) * 2 * NL;
                 } else {
                     const int qz = (P->lateral == 1) ? q : (q ^ 4);
                     et = P->gz;

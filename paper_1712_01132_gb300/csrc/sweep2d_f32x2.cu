@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
                 const int below = s_binfo[2];
                 const float* eb = (below >= 0)
                     ? P->glat + (((size_t)(par * 4 + q) * P->nslots + below) * n1) * 2 * NL
-                    : P->edge + ((size_t)(q * (nb - 1) + band - 1) * n1) * 2 * NL;
+                    : P->edge + ((size_t)(q * 2 * P->nslots + (-1 - below)) * n1) * 2 * NL;
 #pragma unroll
                 for (int i = 0; i < T1; ++i) {
                     if (i < width) {
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
                 float* et;
                 const int above = s_binfo[3];
                 if (above < 0) {
-                    et = P->edge + ((size_t)(q * (nb - 1) + band) * n1) * 2 * NL;
+                    et = P->edge + ((size_t)(q * 2 * P->nslots + (-1 - above)) * n1) * 2 * NL;
                 } else {
                     const int qd = (above > 0 || P->lateral == 1) ? q : (q ^ 2);
                     et = P->glat + (((size_t)((par ^ 1) * 4 + qd) * P->nslots + above) * n1) * 2 * NL;
