@@ -77,7 +77,8 @@ typedef struct {
     int tile_x1;         /* sweep tile width along x1: 2D FP64 8 or 16, 2D FP32 4 or 8, 3D 4 or 8;
                             0 = automatic (8 in 2D, 4 in 3D) */
     int band_rows;       /* rows per sweep band in 2D, pencil rows R2 = R3 in 3D (0 = automatic:
-                            8 in 2D, 4 in 3D; reduced until the tile fits shared memory) */
+                            8 in 2D, 3D 8 for FP32 and 4 for FP64; reduced until the tile fits
+                            shared memory) */
     /* Optional device allocator (e.g. the caller's caching allocator).  When alloc is NULL the
      * library uses cudaMalloc/cudaFree.  alloc returns NULL on failure. */
     void* (*alloc)(size_t bytes, void* user);

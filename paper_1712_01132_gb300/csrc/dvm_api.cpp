@@ -13,6 +13,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/dvm.h"
@@ -35,6 +36,10 @@ cudaError_t sweep2d_f32x2_occupancy(int T1, int NW, int max_rows, int* blocks_pe
 int sweep2d_f32x2_max_rows(int T1, int NW);
 int sweep2d_f32x2_velocities_per_lane();
 template <typename T> size_t sweep3d_smem(int T1, int NW, int R2, int R3);
+size_t sweep3d_f32x2_smem(int T1, int NW, int R2, int R3);
+int sweep3d_f32x2_velocities_per_lane();
+cudaError_t launch_sweep3d_f32x2(const SweepArgs3D<float>&, int grid, int NW, cudaStream_t);
+cudaError_t sweep3d_f32x2_occupancy(int T1, int NW, int R2, int R3, int bf16, int* blocks_per_sm);
 template <typename T> cudaError_t sweep3d_occupancy(int T1, int NW, int R2, int R3, int bf16, int* blocks_per_sm);
 template <typename T> cudaError_t launch_sweep3d(const SweepArgs3D<T>&, int grid, int NW, cudaStream_t);
 template <typename T> cudaError_t launch_finalize3d(const FinArgs3D<T>&, int nblocks, cudaStream_t);
@@ -519,16 +524,21 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         }
     }
     c->nvq = nvo;
-    const int warps_total = (nvo + 31) / 32;
+    // FP32 lanes carry two velocity slots (packed f32x2 kernel), FP64 lanes one
+    const int vpl = (c->prec == DVM_FP32) ? sweep3d_f32x2_velocities_per_lane() : 1;
+    const int warps_total = (nvo + 32 * vpl - 1) / (32 * vpl);
     c->G = (warps_total + 7) / 8;                         // at most 8 warps per CTA
     c->NW = (warps_total + c->G - 1) / c->G;
-    c->GL = 32 * c->NW;
+    c->GL = 32 * vpl * c->NW;                             // velocity slots per group
     c->NL = c->GL * c->G;
     const int NL = c->NL, G = c->G;
     // 4-column x1 tiles by default: on a 128^3 medium with 16^3 velocities they sweep 1.4x faster
     // than 8-column tiles (more pencils in flight per level, half the carry registers)
     c->T1 = (c->opt.tile_x1 == 8) ? 8 : 4;
-    const int R = c->opt.band_rows ? c->opt.band_rows : 4;
+    // default pencils: FP32 asks for 8 x 8 rows, shrunk below to the largest that fits shared
+    // memory (5 x 5 with 512 velocities per octant: 1.19x faster than 4 x 4 on a 128^3 rock);
+    // FP64 4 x 4
+    const int R = c->opt.band_rows ? c->opt.band_rows : (c->prec == DVM_FP32 ? 8 : 4);
     c->R2 = c->R3 = std::max(1, R);
     {
         // shrink the tile, then the pencil, until the CTA's shared memory fits the device limit
@@ -537,7 +547,11 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (smem_max <= 0) smem_max = 227 * 1024;
         const size_t lim = (size_t)smem_max - 1024;
-        while (sweep3d_smem<T>(c->T1, c->NW, c->R2, c->R3) > lim) {
+        auto smem_of = [&]() -> size_t {
+            if constexpr (std::is_same<T, float>::value) return sweep3d_f32x2_smem(c->T1, c->NW, c->R2, c->R3);
+            else return sweep3d_smem<T>(c->T1, c->NW, c->R2, c->R3);
+        };
+        while (smem_of() > lim) {
             if (c->T1 > 4) c->T1 = 4;
             else if (c->R2 > 1) { c->R2--; c->R3 = c->R2; }
             else return fail(c, DVM_EINVAL, "3D sweep does not fit in shared memory");
@@ -730,7 +744,8 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
                     qw.size() * sizeof(double) + probs.size() * sizeof(Prob3D<T>);
     c->probs_host.assign((const char*)probs.data(), (const char*)probs.data() + probs.size() * sizeof(Prob3D<T>));
     int per_sm = 0;
-    e = sweep3d_occupancy<T>(c->T1, c->NW, mr2, mr3, c->bf16 ? 1 : 0, &per_sm);
+    if constexpr (std::is_same<T, float>::value) e = sweep3d_f32x2_occupancy(c->T1, c->NW, mr2, mr3, c->bf16 ? 1 : 0, &per_sm);
+    else e = sweep3d_occupancy<T>(c->T1, c->NW, mr2, mr3, 0, &per_sm);
     if (e != cudaSuccess) return cuda_fail(c, e, "occupancy");
     if (per_sm < 1) return fail(c, DVM_EINVAL, "3D sweep kernel does not fit on an SM with these pencils");
     int dev = 0, sms = 0;
@@ -805,6 +820,14 @@ dvm_status enqueue_iter_2d(dvm_ctx* c) {
     return DVM_OK;
 }
 
+cudaError_t sweep3d_launch(const SweepArgs3D<float>& a, dvm_ctx* c) {
+    return launch_sweep3d_f32x2(a, c->sweep_grid, c->NW, c->stream);
+}
+
+cudaError_t sweep3d_launch(const SweepArgs3D<double>& a, dvm_ctx* c) {
+    return launch_sweep3d<double>(a, c->sweep_grid, c->NW, c->stream);
+}
+
 template <typename T>
 dvm_status enqueue_iter_3d(dvm_ctx* c) {
     cudaError_t e = cudaMemsetAsync(c->counters_dev, 0, c->counters_bytes, c->stream);
@@ -825,7 +848,7 @@ dvm_status enqueue_iter_3d(dvm_ctx* c) {
     a.timeout_ns = c->timeout_ns;
     a.withhold_item = c->withhold_item;
     if ((e = mark(c)) != cudaSuccess) return cuda_fail(c, e, "event");
-    e = launch_sweep3d<T>(a, c->sweep_grid, c->NW, c->stream);
+    e = sweep3d_launch(a, c);
     if (e != cudaSuccess) return cuda_fail(c, e, "sweep kernel");
     if ((e = mark(c)) != cudaSuccess) return cuda_fail(c, e, "event");
     FinArgs3D<T> fa{(const Prob3D<T>*)c->probs_dev, c->blk_prob_dev, c->blk_start_dev, c->status_dev};

@@ -590,10 +590,6 @@ size_t sweep3d_smem(int T1, int NW, int R2, int R3) {
                         (size_t)NW * R2 * 2 * T1 * 32 + (size_t)NW * 8 * 32);
 }
 
-// BF16 storage exists for FP32 arithmetic only
-template <typename T> struct HasBF { static constexpr bool value = false; };
-template <> struct HasBF<float> { static constexpr bool value = true; };
-
 template <typename T, int T1, bool BF>
 static cudaError_t occ3(int NW, int R2, int R3, int* blocks_per_sm) {
     const size_t smem = sweep3d_smem<T>(T1, NW, R2, R3);
@@ -602,15 +598,11 @@ static cudaError_t occ3(int NW, int R2, int R3, int* blocks_per_sm) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep3d_kernel<T, T1, BF>, NW * 32, smem);
 }
 
+// The scalar kernel serves the FP64 path (FP32 and its BF16-storage ablation use the packed kernel
+// of sweep3d_f32x2.cu); its BF16 flag stays false.
 template <typename T>
 cudaError_t sweep3d_occupancy(int T1, int NW, int R2, int R3, int bf16, int* blocks_per_sm) {
-    if (bf16) {
-        if constexpr (HasBF<T>::value) {
-            if (T1 == 4) return occ3<T, 4, true>(NW, R2, R3, blocks_per_sm);
-            if (T1 == 8) return occ3<T, 8, true>(NW, R2, R3, blocks_per_sm);
-        }
-        return cudaErrorInvalidValue;
-    }
+    if (bf16) return cudaErrorInvalidValue;
     if (T1 == 4) return occ3<T, 4, false>(NW, R2, R3, blocks_per_sm);
     if (T1 == 8) return occ3<T, 8, false>(NW, R2, R3, blocks_per_sm);
     return cudaErrorInvalidValue;
@@ -627,13 +619,7 @@ static cudaError_t launch3(const SweepArgs3D<T>& a, int grid, int NW, cudaStream
 
 template <typename T>
 cudaError_t launch_sweep3d(const SweepArgs3D<T>& a, int grid, int NW, cudaStream_t st) {
-    if (a.bf16) {
-        if constexpr (HasBF<T>::value) {
-            if (a.T1 == 4) return launch3<T, 4, true>(a, grid, NW, st);
-            if (a.T1 == 8) return launch3<T, 8, true>(a, grid, NW, st);
-        }
-        return cudaErrorInvalidValue;
-    }
+    if (a.bf16) return cudaErrorInvalidValue;
     if (a.T1 == 4) return launch3<T, 4, false>(a, grid, NW, st);
     if (a.T1 == 8) return launch3<T, 8, false>(a, grid, NW, st);
     return cudaErrorInvalidValue;
@@ -670,10 +656,11 @@ cudaError_t launch_wall3d(const Prob3D<T>* p, double* out, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+template size_t sweep3d_smem<double>(int, int, int, int);
+template cudaError_t sweep3d_occupancy<double>(int, int, int, int, int, int*);
+template cudaError_t launch_sweep3d<double>(const SweepArgs3D<double>&, int, int, cudaStream_t);
+
 #define DVM_INSTANTIATE3(T)                                                                     \
-    template size_t sweep3d_smem<T>(int, int, int, int);                                       \
-    template cudaError_t sweep3d_occupancy<T>(int, int, int, int, int, int*);                  \
-    template cudaError_t launch_sweep3d<T>(const SweepArgs3D<T>&, int, int, cudaStream_t);     \
     template cudaError_t launch_finalize3d<T>(const FinArgs3D<T>&, int, cudaStream_t);         \
     template cudaError_t launch_init3d<T>(const Prob3D<T>*, int, const double*, cudaStream_t); \
     template cudaError_t launch_warm3d<T>(const Prob3D<T>*, int, int, const double*, const double*, \

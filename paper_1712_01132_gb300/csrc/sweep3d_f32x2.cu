@@ -1,0 +1,383 @@
+// sweep3d_f32x2.cu -- FP32 transport sweep of one source iteration in 3D (arXiv:1712.01132,
+// Sec. 3.1 step i with the quadrature of step iii fused), two discrete velocities per lane.
+//
+// Same schedule and data layout as sweep3d_kernel (work items (problem, octant, velocity group,
+// pencil) in pencil-level order, pencils of R2 x R3 rows swept along x1 in tiles of T1 columns,
+// waits on the x2 and x3 neighbour pencils), but every lane carries the two consecutive velocity
+// slots 2 l and 2 l + 1 of its group as one packed pair, updated with fma.rn.f32x2: the per-point
+// record loads and the cross-lane quadrature are shared by two velocities.  Per point and pair:
+//   h = R * [ S + a1 (K1x h(x - s1 e1) + K2x h(x - 2 s1 e1) + E1)
+//               + a2 (K1y ... + E2) + a3 (K1z ... + E3) ],  S = a + b1 v1 + b2 v2 + b3 v3
+// (Eq. 10 solved for h with the upwind stencil of Eq. 9, source form).  The moment sums of a point
+// are formed in a fixed order (pair, lane tree, warps), independent of tile and pencil shapes.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "dvm_device.cuh"
+#include "dvm_internal.h"
+
+namespace dvm {
+
+namespace {
+
+constexpr int kRec = 16;    // record floats: {a b1 b2 b3} {E1 E2 E3 rsel} {K1x K2x K1y K2y} {K1z K2z - -}
+constexpr int kPL = 64;     // velocity slots per warp (32 lanes x 2)
+
+// transient h in HBM (ghost layers, pencil edges) as float pairs, or the BF16 deviations from the
+// x1 ramp (the BF16-storage ablation): h' - x1 of the point the pair belongs to
+template <bool BF> struct PairStore {
+    static __device__ __forceinline__ float2 ld(const float* b, size_t i, float) {
+        return __ldcg(reinterpret_cast<const float2*>(b + i));
+    }
+    static __device__ __forceinline__ void st(float* b, size_t i, float2 v, float) {
+        *reinterpret_cast<float2*>(b + i) = v;
+    }
+};
+template <> struct PairStore<true> {
+    static __device__ __forceinline__ float2 ld(const float* b, size_t i, float x1) {
+        const unsigned u = __ldcg(reinterpret_cast<const unsigned*>(reinterpret_cast<const __nv_bfloat16*>(b) + i));
+        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
+        return make_float2(f.x + x1, f.y + x1);
+    }
+    static __device__ __forceinline__ void st(float* b, size_t i, float2 v, float x1) {
+        *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(b) + i) =
+            __floats2bfloat162_rn(v.x - x1, v.y - x1);
+    }
+};
+
+__device__ __forceinline__ float2 dup2(float x) { return make_float2(x, x); }
+
+}  // namespace
+
+template <int T1, bool BF>
+__global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<float> a) {
+    using PS = PairStore<BF>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item;
+    __shared__ int s_abort;
+    const int NW = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int MR2 = a.maxR2, MR3 = a.maxR3;
+    const int MROWS = MR2 * MR3;
+    float* rec = reinterpret_cast<float*>(smem_raw);                      // [MROWS][T1][kRec]
+    float* part = rec + (size_t)MROWS * T1 * kRec;                        // [NW][MROWS][T1][4]
+    float* carry = part + (size_t)NW * MROWS * T1 * 4;                    // [NW][MROWS][2][64]
+    float* pb = carry + (size_t)NW * MROWS * 2 * kPL;                     // [NW][MR2][2][T1][64]
+    float* rtab = pb + (size_t)NW * MR2 * 2 * T1 * kPL;                   // [NW][8][64]
+    const size_t NL = (size_t)a.NL;
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_item = ld_volatile(a.status) ? a.nitems : atomicAdd(a.ticket, 1);
+            s_abort = 0;
+        }
+        __syncthreads();
+        const int it = s_item;
+        if (it >= a.nitems) return;
+        const SweepItem3 item = a.items[it];
+        const Prob3D<float>* __restrict__ P = a.prob + item.prob;
+        const int q = item.oct, g = item.group, p2 = item.p2, p3 = item.p3;
+        const int n1 = P->n1, n2 = P->n2, n3 = P->n3;
+        const int N = P->N;
+        const int np2 = P->np2, np3 = P->np3;
+        const int s1n = q & 1, s2n = (q >> 1) & 1, s3n = (q >> 2) & 1;
+        const int j0 = p2 * P->R2, k0 = p3 * P->R3;
+        const int nr2 = min(P->R2, n2 - j0), nr3 = min(P->R3, n3 - k0);
+        const float K1o = P->order == 2 ? 2.f : 1.f;
+        const float K2o = P->order == 2 ? -0.5f : 0.f;
+        const int lv = g * a.GL + kPL * warp + 2 * lane;      // first velocity slot of this lane
+        const float* la = P->lanec + ((size_t)q * NL + lv) * kLaneConsts3;
+        const float* lb = la + kLaneConsts3;
+        const float2 v1 = make_float2(la[0], lb[0]), v2 = make_float2(la[1], lb[1]), v3 = make_float2(la[2], lb[2]);
+        const float2 a1 = make_float2(la[3], lb[3]), a2 = make_float2(la[4], lb[4]), a3 = make_float2(la[5], lb[5]);
+        const float2 W = make_float2(la[6], lb[6]), Wv1 = make_float2(la[7], lb[7]);
+        const float2 Wv2 = make_float2(la[8], lb[8]), Wv3 = make_float2(la[9], lb[9]);
+        float* my_rtab = rtab + (size_t)warp * 8 * kPL + 2 * lane;
+#pragma unroll
+        for (int rs = 0; rs < 8; ++rs)
+            *reinterpret_cast<float2*>(my_rtab + rs * kPL) = make_float2(la[10 + rs], lb[10 + rs]);
+        const int par = a.parity;
+        const int G = P->ngroups;
+        int* prog = P->prog + ((size_t)q * G + g) * np3 * np2;
+        const float dxf = (float)P->dx;
+        auto x1of = [&](int ic) -> float { return (float)(s1n ? n1 - 1 - ic : ic) * dxf; };
+        const float x1g0 = x1of(n1 - 1), x1g1 = x1of(n1 - 2);   // columns of the x1 ghost layers
+        // x1 upstream of the first tile: x1 ghost layers (oriented rows (k, j))
+        {
+            const size_t gxo = (((size_t)par * 8 + q) * n3 * n2) * 2 * NL;
+            for (int kk = 0; kk < nr3; ++kk)
+                for (int jj = 0; jj < nr2; ++jj) {
+                    const size_t row = (size_t)(k0 + kk) * n2 + (j0 + jj);
+                    float* cr = carry + ((size_t)(warp * MROWS + kk * MR2 + jj) * 2) * kPL + 2 * lane;
+                    *reinterpret_cast<float2*>(cr) = PS::ld(P->gx1, gxo + (row * 2 + 0) * NL + lv, x1g0);
+                    *reinterpret_cast<float2*>(cr + kPL) = PS::ld(P->gx1, gxo + (row * 2 + 1) * NL + lv, x1g1);
+                }
+        }
+        const int ntiles = (n1 + T1 - 1) / T1;
+        for (int t = 0; t < ntiles; ++t) {
+            const int c0 = t * T1;
+            const int width = min(T1, n1 - c0);
+            if (threadIdx.x == 0) {
+                bool ok = true;
+                if (p2 > 0) ok = wait_geq(prog + p3 * np2 + p2 - 1, t + 1, a.status, a.timeout_ns);
+                if (ok && p3 > 0) ok = wait_geq(prog + (p3 - 1) * np2 + p2, t + 1, a.status, a.timeout_ns);
+                if (!ok) s_abort = 1;
+            }
+            // records of the tile's points for this octant (shared by all lanes and velocities)
+            const int npts = nr3 * MR2 * T1;
+            for (int idx = threadIdx.x; idx < npts; idx += blockDim.x) {
+                const int kk = idx / (MR2 * T1);
+                const int rem = idx - kk * MR2 * T1;
+                const int jj = rem / T1;
+                const int i = rem - jj * T1;
+                float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
+                if (jj < nr2 && i < width) {
+                    const int ic = c0 + i;
+                    const int x = s1n ? n1 - 1 - ic : ic;
+                    const int y = s2n ? n2 - 1 - (j0 + jj) : (j0 + jj);
+                    const int z = s3n ? n3 - 1 - (k0 + kk) : (k0 + kk);
+                    const int id = (z * n2 + y) * n1 + x;
+                    const uint16_t code = P->code[id];
+                    if (!(code & kSolidBit)) {
+                        const float4 s = reinterpret_cast<const float4*>(P->src)[id];
+                        const float4 e0 = reinterpret_cast<const float4*>(P->E)[2 * (size_t)id];
+                        const float4 e1 = reinterpret_cast<const float4*>(P->E)[2 * (size_t)id + 1];
+                        const int ca = (code >> (2 * (0 + s1n))) & 3;
+                        const int cb = (code >> (2 * (2 + s2n))) & 3;
+                        const int cc = (code >> (2 * (4 + s3n))) & 3;
+                        // first-order denominator when either upstream point is solid (cases 1, 2)
+                        const int rs = (ca != 0) | ((cb != 0) << 1) | ((cc != 0) << 2);
+                        r0 = s;
+                        r1 = make_float4(s1n ? e0.y : e0.x, s2n ? e0.w : e0.z, s3n ? e1.y : e1.x,
+                                         __int_as_float(rs * kPL));
+                        r2 = make_float4(ca == 2 ? 0.f : (ca == 1 ? 1.f : K1o), ca == 0 ? K2o : 0.f,
+                                         cb == 2 ? 0.f : (cb == 1 ? 1.f : K1o), cb == 0 ? K2o : 0.f);
+                        r3 = make_float4(cc == 2 ? 0.f : (cc == 1 ? 1.f : K1o), cc == 0 ? K2o : 0.f, 0.f, 0.f);
+                    }
+                }
+                float4* R = reinterpret_cast<float4*>(rec + (size_t)((kk * MR2 + jj) * T1 + i) * kRec);
+                R[0] = r0;
+                R[1] = r1;
+                R[2] = r2;
+                R[3] = r3;
+            }
+            __syncthreads();
+            if (s_abort) return;
+            // x3 upstream planes of the first plane of the pencil: the pencil below in x3 (ring
+            // slot) or the x3 ghost layers (periodic or specular, Eq. 8)
+            {
+                const float* zb = (p3 == 0) ? P->gz : P->ez;
+                const size_t zo = (p3 == 0)
+                    ? (((size_t)par * 8 + q) * n2 * n1) * 2 * NL
+                    : ((((size_t)q * np2 + p2) * 2 + ((p3 - 1) & 1)) * P->R2 * n1) * 2 * NL;
+                for (int jj = 0; jj < nr2; ++jj)
+                    for (int i = 0; i < width; ++i) {
+                        const size_t row = (p3 == 0) ? ((size_t)(j0 + jj) * n1 + (c0 + i)) : ((size_t)jj * n1 + (c0 + i));
+                        float* d = pb + ((((size_t)warp * MR2 + jj) * 2) * T1 + i) * kPL + 2 * lane;
+                        const float xs = x1of(c0 + i);
+                        *reinterpret_cast<float2*>(d) = PS::ld(zb, zo + (row * 2 + 0) * NL + lv, xs);
+                        *reinterpret_cast<float2*>(d + (size_t)T1 * kPL) = PS::ld(zb, zo + (row * 2 + 1) * NL + lv, xs);
+                    }
+            }
+            for (int kk = 0; kk < nr3; ++kk) {
+                // x2 upstream rows of the first row of this plane
+                float2 rb1[T1], rb2[T1];
+                {
+                    const float* yb = (p2 == 0) ? P->gy : P->ey;
+                    const size_t yo = (p2 == 0)
+                        ? (((size_t)par * 8 + q) * n3 * n1) * 2 * NL
+                        : ((((size_t)q * np3 + p3) * 2 + ((p2 - 1) & 1)) * P->R3 * n1) * 2 * NL;
+                    const size_t rowbase = (p2 == 0) ? (size_t)(k0 + kk) * n1 : (size_t)kk * n1;
+#pragma unroll
+                    for (int i = 0; i < T1; ++i) {
+                        if (i < width) {
+                            const float xs = x1of(c0 + i);
+                            rb1[i] = PS::ld(yb, yo + ((rowbase + c0 + i) * 2 + 0) * NL + lv, xs);
+                            rb2[i] = PS::ld(yb, yo + ((rowbase + c0 + i) * 2 + 1) * NL + lv, xs);
+                        } else {
+                            rb1[i] = make_float2(0.f, 0.f);
+                            rb2[i] = rb1[i];
+                        }
+                    }
+                }
+                for (int jj = 0; jj < nr2; ++jj) {
+                    float* cr = carry + ((size_t)(warp * MROWS + kk * MR2 + jj) * 2) * kPL + 2 * lane;
+                    float2 hp1 = *reinterpret_cast<const float2*>(cr);
+                    float2 hp2 = *reinterpret_cast<const float2*>(cr + kPL);
+                    float* zr = pb + ((((size_t)warp * MR2 + jj) * 2) * T1) * kPL + 2 * lane;   // [2][T1][64]
+                    const float* rrow = rec + (size_t)((kk * MR2 + jj) * T1) * kRec;
+                    float* prow = part + ((size_t)(warp * MROWS + kk * MR2 + jj) * T1) * 4;
+#pragma unroll
+                    for (int i0 = 0; i0 < T1; i0 += 4) {
+                        float m0[4], m1[4], m2[4], m3[4];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const int i = i0 + c;
+                            if (i < width) {
+                                const float4* R = reinterpret_cast<const float4*>(rrow + i * kRec);
+                                const float4 A = R[0], B = R[1], C = R[2], D = R[3];
+                                const float2 z1 = *reinterpret_cast<const float2*>(zr + (size_t)i * kPL);
+                                const float2 z2 = *reinterpret_cast<const float2*>(zr + ((size_t)T1 + i) * kPL);
+                                const float2 Rk = *reinterpret_cast<const float2*>(my_rtab + __float_as_int(B.w));
+                                const float2 S = fma2(dup2(A.w), v3, fma2(dup2(A.z), v2, fma2(dup2(A.y), v1, dup2(A.x))));
+                                const float2 t1 = fma2(dup2(C.x), hp1, fma2(dup2(C.y), hp2, dup2(B.x)));
+                                const float2 t2 = fma2(dup2(C.z), rb1[i], fma2(dup2(C.w), rb2[i], dup2(B.y)));
+                                const float2 t3 = fma2(dup2(D.x), z1, fma2(dup2(D.y), z2, dup2(B.z)));
+                                const float2 num = fma2(a3, t3, fma2(a2, t2, fma2(a1, t1, S)));
+                                const float2 h = mul2(num, Rk);
+                                hp2 = hp1;
+                                hp1 = h;
+                                rb2[i] = rb1[i];
+                                rb1[i] = h;
+                                *reinterpret_cast<float2*>(zr + ((size_t)T1 + i) * kPL) = z1;
+                                *reinterpret_cast<float2*>(zr + (size_t)i * kPL) = h;
+                                const float2 p0 = mul2(W, h), p1 = mul2(Wv1, h), p2v = mul2(Wv2, h), p3v = mul2(Wv3, h);
+                                m0[c] = p0.x + p0.y;
+                                m1[c] = p1.x + p1.y;
+                                m2[c] = p2v.x + p2v.y;
+                                m3[c] = p3v.x + p3v.y;
+                            } else {
+                                m0[c] = m1[c] = m2[c] = m3[c] = 0.f;
+                            }
+                        }
+                        const float r0 = reduce_scatter<float, 4>(m0, lane);
+                        const float r1 = reduce_scatter<float, 4>(m1, lane);
+                        const float r2 = reduce_scatter<float, 4>(m2, lane);
+                        const float r3 = reduce_scatter<float, 4>(m3, lane);
+                        const int p = lane >> 3;
+                        if ((lane & 7) == 0 && i0 + p < width) {
+                            float* d = prow + (i0 + p) * 4;
+                            d[0] = r0;
+                            d[1] = r1;
+                            d[2] = r2;
+                            d[3] = r3;
+                        }
+                    }
+                    *reinterpret_cast<float2*>(cr) = hp1;
+                    *reinterpret_cast<float2*>(cr + kPL) = hp2;
+                }
+                // x2 edge of this plane for the pencil above in x2 (ring slot p2 & 1), or the x2
+                // ghost layers of the next iteration (periodic: same octant; specular: s2 flipped)
+                {
+                    float* et;
+                    size_t eo, rowbase;
+                    if (p2 < np2 - 1) {
+                        et = P->ey;
+                        eo = ((((size_t)q * np3 + p3) * 2 + (p2 & 1)) * P->R3 * n1) * 2 * NL;
+                        rowbase = (size_t)kk * n1;
+                    } else {
+                        const int qy = (P->lateral == 1) ? q : (q ^ 2);
+                        et = P->gy;
+                        eo = (((size_t)(par ^ 1) * 8 + qy) * n3 * n1) * 2 * NL;
+                        rowbase = (size_t)(k0 + kk) * n1;
+                    }
+#pragma unroll
+                    for (int i = 0; i < T1; ++i) {
+                        if (i < width) {
+                            const float xs = x1of(c0 + i);
+                            PS::st(et, eo + ((rowbase + c0 + i) * 2 + 0) * NL + lv, rb1[i], xs);
+                            PS::st(et, eo + ((rowbase + c0 + i) * 2 + 1) * NL + lv, rb2[i], xs);
+                        }
+                    }
+                }
+            }
+            // x3 edge for the pencil above in x3 (ring slot p3 & 1), or the x3 ghost layers
+            {
+                float* et;
+                size_t eo;
+                const bool last = (p3 == np3 - 1);
+                if (!last) {
+                    et = P->ez;
+                    eo = ((((size_t)q * np2 + p2) * 2 + (p3 & 1)) * P->R2 * n1) * 2 * NL;
+                } else {
+                    const int qz = (P->lateral == 1) ? q : (q ^ 4);
+                    et = P->gz;
+                    eo = (((size_t)(par ^ 1) * 8 + qz) * n2 * n1) * 2 * NL;
+                }
+                for (int jj = 0; jj < nr2; ++jj)
+                    for (int i = 0; i < width; ++i) {
+                        const size_t row = last ? ((size_t)(j0 + jj) * n1 + (c0 + i)) : ((size_t)jj * n1 + (c0 + i));
+                        const float* s = pb + ((((size_t)warp * MR2 + jj) * 2) * T1 + i) * kPL + 2 * lane;
+                        const float xs = x1of(c0 + i);
+                        PS::st(et, eo + (row * 2 + 0) * NL + lv, *reinterpret_cast<const float2*>(s), xs);
+                        PS::st(et, eo + (row * 2 + 1) * NL + lv, *reinterpret_cast<const float2*>(s + (size_t)T1 * kPL), xs);
+                    }
+            }
+            if (t == ntiles - 1) {
+                const size_t gxo = (((size_t)(par ^ 1) * 8 + q) * n3 * n2) * 2 * NL;
+                for (int kk = 0; kk < nr3; ++kk)
+                    for (int jj = 0; jj < nr2; ++jj) {
+                        const size_t row = (size_t)(k0 + kk) * n2 + (j0 + jj);
+                        const float* cr = carry + ((size_t)(warp * MROWS + kk * MR2 + jj) * 2) * kPL + 2 * lane;
+                        PS::st(P->gx1, gxo + (row * 2 + 0) * NL + lv, *reinterpret_cast<const float2*>(cr), x1g0);
+                        PS::st(P->gx1, gxo + (row * 2 + 1) * NL + lv, *reinterpret_cast<const float2*>(cr + kPL), x1g1);
+                    }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0 && it != a.withhold_item) {
+                publish_gpu(prog + p3 * np2 + p2, t + 1);
+            }
+            // moment partials of this octant and group: warp sums in warp order
+            const int tot = nr3 * nr2 * width * 4;
+            for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+                const int mm = idx & 3;
+                const int pi = idx >> 2;
+                const int i = pi % width;
+                const int r = pi / width;
+                const int jj = r % nr2;
+                const int kk = r / nr2;
+                float s = 0.f;
+                for (int w = 0; w < NW; ++w) s += part[((size_t)(w * MROWS + kk * MR2 + jj) * T1 + i) * 4 + mm];
+                const int ic = c0 + i;
+                const int x = s1n ? n1 - 1 - ic : ic;
+                const int y = s2n ? n2 - 1 - (j0 + jj) : (j0 + jj);
+                const int z = s3n ? n3 - 1 - (k0 + kk) : (k0 + kk);
+                P->P[(((size_t)q * G + g) * 4 + mm) * N + ((size_t)z * n2 + y) * n1 + x] = s;
+            }
+            __syncthreads();
+        }
+        __syncthreads();
+    }
+}
+
+size_t sweep3d_f32x2_smem(int T1, int NW, int R2, int R3) {
+    const size_t rows = (size_t)R2 * R3;
+    return sizeof(float) * (rows * T1 * kRec + (size_t)NW * rows * T1 * 4 + (size_t)NW * rows * 2 * kPL +
+                            (size_t)NW * R2 * 2 * T1 * kPL + (size_t)NW * 8 * kPL);
+}
+
+int sweep3d_f32x2_velocities_per_lane() { return 2; }
+
+template <int T1, bool BF>
+static cudaError_t launch_t(const SweepArgs3D<float>& a, int grid, int NW, cudaStream_t st) {
+    const size_t smem = sweep3d_f32x2_smem(T1, NW, a.maxR2, a.maxR3);
+    cudaError_t e = cudaFuncSetAttribute(sweep3d_f32x2_kernel<T1, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    sweep3d_f32x2_kernel<T1, BF><<<grid, NW * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep3d_f32x2(const SweepArgs3D<float>& a, int grid, int NW, cudaStream_t st) {
+    if (a.T1 == 4) return a.bf16 ? launch_t<4, true>(a, grid, NW, st) : launch_t<4, false>(a, grid, NW, st);
+    if (a.T1 == 8) return a.bf16 ? launch_t<8, true>(a, grid, NW, st) : launch_t<8, false>(a, grid, NW, st);
+    return cudaErrorInvalidValue;
+}
+
+template <int T1, bool BF>
+static cudaError_t occ_t(int NW, int R2, int R3, int* blocks_per_sm) {
+    const size_t smem = sweep3d_f32x2_smem(T1, NW, R2, R3);
+    cudaError_t e = cudaFuncSetAttribute(sweep3d_f32x2_kernel<T1, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep3d_f32x2_kernel<T1, BF>, NW * 32, smem);
+}
+
+cudaError_t sweep3d_f32x2_occupancy(int T1, int NW, int R2, int R3, int bf16, int* blocks_per_sm) {
+    if (T1 == 4) return bf16 ? occ_t<4, true>(NW, R2, R3, blocks_per_sm) : occ_t<4, false>(NW, R2, R3, blocks_per_sm);
+    if (T1 == 8) return bf16 ? occ_t<8, true>(NW, R2, R3, blocks_per_sm) : occ_t<8, false>(NW, R2, R3, blocks_per_sm);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace dvm
