@@ -156,8 +156,8 @@ def aggregate_replicas(local_ms, units_per_rank, device=None):
     return float(u.item()) / (ms_max * 1e-3), ms_max, ws
 
 
-def problems(name):
-    """(masks, Knudsen numbers, fluid cells per problem) of a workload."""
+def problems(name, side=128):
+    """(masks, Knudsen numbers, fluid cells per problem) of a workload (side: rock edge length)."""
     from paper_1712_01132_gb300 import inputs
     if name == "kn_sweep_512":
         mask = inputs.random_discs(512, 512, seed=0)
@@ -167,7 +167,7 @@ def problems(name):
         batch = inputs.disc_batch(64, seed0=1000)
         masks, kns = [b[0] for b in batch], [b[1] for b in batch]
     elif name == "rock_128":
-        masks, kns = [inputs.gaussian_rock(128, seed=0, corr_len=8.0, porosity=0.35)], [0.5]
+        masks, kns = [inputs.gaussian_rock(side, seed=0, corr_len=8.0, porosity=0.35)], [0.5]
     else:
         raise ValueError(name)
     return masks, kns, [int((~m).sum()) for m in masks]
@@ -183,7 +183,7 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    masks, kns, nfs = problems(args.workload)
+    masks, kns, nfs = problems(args.workload, args.side)
     v, w = dvm.dvm_gh_velocity_grid(W["dims"], W["n_axis"])
     nv = len(w)
     updates_per_iter = sum(nfs) * nv
@@ -267,7 +267,8 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "description": W["desc"], "fluid_cells": sum(nfs),
+            "config": {"workload": args.workload if args.side == 128 else "%s_side%d" % (args.workload, args.side),
+                       "description": W["desc"], "fluid_cells": sum(nfs),
                        "velocities": nv, "problems": len(masks), "iterations_per_step": ITERS_PER_STEP,
                        "step": "100 source iterations (sweep+quadrature+finalize) + permeability/Err check",
                        "tiles": {"tile_x1": t1, "band_rows": rows, "autotuned_ms_per_iteration": round(tune_ms, 4)},
@@ -359,6 +360,8 @@ def main():
     ap.add_argument("--workload", default="kn_sweep_512", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--side", type=int, default=128,
+                    help="edge length of the rock_128 geometry (smaller only for profiling captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)
