@@ -63,8 +63,8 @@ WORKLOADS = {
                 "16^3 Gauss-Hermite velocities, Kn 0.5, FP32",
         # source 3 FMA, upwind 3 x (2 FMA) + 3 FMA, reciprocal 1 MUL, quadrature 4 MUL + 4 ADD
         "flops_per_update": 3 * 2 + 9 * 2 + 1 + 4 + 4,
-        "kernel": "dvm::sweep3d_kernel<float,T1>",
-        "l2": "working set per iteration > L2 (pencil edges and ghosts ~30 GB)",
+        "kernel": "dvm::sweep3d_f32x2_kernel<T1,0>",
+        "l2": "working set per iteration > L2 (pencil edges and ghosts ~6 GB)",
     },
 }
 
@@ -82,6 +82,32 @@ def _peaks():
             return json.load(f)
     except OSError:
         return {}
+
+
+KERNEL_SOURCES = ("paper_1712_01132_gb300/csrc/sweep2d_f32x2.cu", "paper_1712_01132_gb300/csrc/dvm_device.cuh",
+                  "paper_1712_01132_gb300/csrc/dvm_internal.h")
+
+
+def measured_traffic(workload, tiles):
+    """DRAM bytes per sweep launch from the committed ncu summary of the default workload, or None
+    when the workload or tile shape differs or the kernel sources changed since the capture."""
+    import hashlib
+    if workload != "kn_sweep_512":
+        return None
+    try:
+        text = open(os.path.join(ROOT, "profiles", "sweep2d_f32x2_kn_sweep_512.md")).read()
+        fields = dict(line.split(": ", 1) for line in text.splitlines() if line.startswith("traffic_"))
+        h = hashlib.sha256()
+        for f in KERNEL_SOURCES:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+        if fields.get("traffic_source_sha256") != h.hexdigest():
+            return None
+        if fields.get("traffic_tiles") != "%d %d" % tiles:
+            return None
+        return int(fields["traffic_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def _cores():
@@ -254,7 +280,8 @@ def run_gpu(args):
     achieved = updates_per_iter * W["flops_per_update"] / sweep_avg_s / 1e12
     kernel = W["kernel"].replace("T1", str(t1))
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / peak_tflops, 4), "traffic": None,
+                "frac": round(achieved / peak_tflops, 4),
+                "traffic": measured_traffic(args.workload if args.side == 128 else "", (t1, rows)),
                 "kernel": kernel, "avg_launch_ms": round(sweep_avg_s * 1e3, 4),
                 "share_of_step": round(sweep_ms / max(sweep_ms + fin_ms, 1e-9), 4),
                 "peak_basis": "FP32 FMA issue, 152 SMs x 128 lanes x 2 flop x %.0f MHz (derived from the "
