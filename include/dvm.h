@@ -237,6 +237,53 @@ dvm_status dvm_transfer_bytes(const dvm_ctx* ctx, int64_t* h2d, int64_t* d2h);
 dvm_status dvm_permeability_noalloc(const double* u1_dev, int64_t n, double kn, double* out_dev, void* stream);
 const char* dvm_noalloc_last_error(void);
 
+/* ---- Learned warm start: kernels of a small 3D convolutional network -------------------------
+ * The paper has no counterpart.  A network predicts the initial density and velocity fields
+ * (the input of dvm_set_initial) from the solid mask, a signed distance and log Kn; it changes
+ * only where the source iteration of Sec. 3.1 starts, never its fixed point.  All pointers are
+ * DEVICE pointers to FP32 single-sample tensors in channel-major layout t[c][z][y][x] (x fastest,
+ * d x h x w voxels); work is enqueued on `stream` (cudaStream_t, NULL = legacy default stream) and
+ * nothing is allocated.  Convolutions are 3 x 3 x 3 with periodic padding, weights w[co][ci][27]
+ * with tap index (kz * 3 + ky) * 3 + kx for offsets kz, ky, kx in -1..1, biases b[co] (may be
+ * NULL), FP32 accumulation.  accumulate != 0 adds into the output instead of overwriting it.
+ * Errors: DVM_EINVAL (NULL pointer, non-positive size, odd extent for the 2x resampling, scratch
+ * too small), DVM_ECUDA (launch failure). */
+/* y = conv(x, w) + b: y[co][v] = b[co] + sum_ci sum_k w[co][ci][k] x[ci][v + off(k)] */
+dvm_status dvm_nn_conv3d(const float* x, const float* w, const float* b, float* y, int cin, int cout,
+                         int d, int h, int w_, int accumulate, void* stream);
+/* data gradient: dx[ci][v] (+)= sum_co sum_k w[co][ci][k] dy[co][v - off(k)] */
+dvm_status dvm_nn_conv3d_dgrad(const float* dy, const float* w, float* dx, int cin, int cout, int d,
+                               int h, int w_, int accumulate, void* stream);
+/* weight and bias gradients: dw[co][ci][k] (+)= sum_v dy[co][v] x[ci][v + off(k)], db[co] (+)=
+ * sum_v dy[co][v] (db may be NULL); summed in a fixed order.  scratch: device buffer of at least
+ * dvm_nn_wgrad_scratch_floats(...) floats. */
+dvm_status dvm_nn_conv3d_wgrad(const float* x, const float* dy, float* dw, float* db, float* scratch,
+                               int64_t scratch_floats, int cin, int cout, int d, int h, int w_,
+                               int accumulate, void* stream);
+int64_t dvm_nn_wgrad_scratch_floats(int cin, int cout, int d, int h, int w_);
+/* y = max(y, 0) in place; relu_bwd: dy = 0 where y <= 0 (in place on dy) */
+dvm_status dvm_nn_relu(float* y, int64_t n, void* stream);
+dvm_status dvm_nn_relu_bwd(const float* y, float* dy, int64_t n, void* stream);
+/* 2 x 2 x 2 mean pooling of x (c channels, d x h x w, all even) into y (d/2 x h/2 x w/2) and its
+ * gradient; nearest-neighbour 2x upsampling of x (d/2 x h/2 x w/2) into y (d x h x w) and its
+ * gradient (the sum over the 8 children) */
+dvm_status dvm_nn_pool2(const float* x, float* y, int c, int d, int h, int w_, void* stream);
+dvm_status dvm_nn_pool2_bwd(const float* dy, float* dx, int c, int d, int h, int w_, int accumulate,
+                            void* stream);
+dvm_status dvm_nn_up2(const float* x, float* y, int c, int d, int h, int w_, void* stream);
+dvm_status dvm_nn_up2_bwd(const float* dy, float* dx, int c, int d, int h, int w_, void* stream);
+/* masked squared error: partial[b] = block sums of (mask[v] (y - t))^2 over the c x v values
+ * (dvm_nn_mse_partials(c, v) blocks) and, when dy is not NULL, dy = 2 mask (y - t) inv_count */
+dvm_status dvm_nn_mse(const float* y, const float* t, const float* mask, float* dy, float* partial,
+                      int c, int64_t v, float inv_count, void* stream);
+int64_t dvm_nn_mse_partials(int c, int64_t v);
+/* Adam step (bias-corrected, step >= 1) on FP32 master weights w with moments m, v and gradient
+ * g * grad_scale; wq receives the BF16 rounding of w (as FP32), the weights forward and backward
+ * use.  round_bf16: wq = BF16 rounding of w. */
+dvm_status dvm_nn_adam(float* w, float* wq, const float* g, float* m, float* v, int64_t n, float lr,
+                       float beta1, float beta2, float eps, int64_t step, float grad_scale, void* stream);
+dvm_status dvm_nn_round_bf16(const float* w, float* wq, int64_t n, void* stream);
+
 /* Test hook (fault-handling tests; not needed in normal use): set the bound of every spin wait
  * of the sweep kernel to timeout_ns and make work item withhold_item (-1: none) never publish its
  * progress, so that the band waiting on it gives up, the kernel records DVM_ETIMEOUT in its status

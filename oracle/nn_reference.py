@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY: only the test suite and the smoke check use this module; the product
 path runs the CUDA kernels of the library.  It shares no code with them.
 
-The network maps (solid mask, signed distance, log Kn) to (rho', Kn u1, Kn u2, Kn u3) on a periodic
+The network maps (solid mask, signed distance, log Kn n1) to scaled (rho', u1, u2, u3) on a periodic
 grid: a U-Net with L levels and C_l = C 2^l channels at level l, 3 x 3 x 3 periodic convolutions
 with biases, ReLU, 2 x 2 x 2 mean pooling and nearest-neighbour upsampling:
 

@@ -83,6 +83,21 @@ _SIGNATURES = [
     ("dvm_get_state", ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
     ("dvm_set_state", ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     ("dvm_permeability_noalloc", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double, _P, _P]),
+    ("dvm_nn_conv3d", ctypes.c_int, [_P, _P, _P, _P] + [ctypes.c_int] * 6 + [_P]),
+    ("dvm_nn_conv3d_dgrad", ctypes.c_int, [_P, _P, _P] + [ctypes.c_int] * 6 + [_P]),
+    ("dvm_nn_conv3d_wgrad", ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int64] + [ctypes.c_int] * 6 + [_P]),
+    ("dvm_nn_wgrad_scratch_floats", ctypes.c_int64, [ctypes.c_int] * 5),
+    ("dvm_nn_relu", ctypes.c_int, [_P, ctypes.c_int64, _P]),
+    ("dvm_nn_relu_bwd", ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
+    ("dvm_nn_pool2", ctypes.c_int, [_P, _P] + [ctypes.c_int] * 4 + [_P]),
+    ("dvm_nn_pool2_bwd", ctypes.c_int, [_P, _P] + [ctypes.c_int] * 5 + [_P]),
+    ("dvm_nn_up2", ctypes.c_int, [_P, _P] + [ctypes.c_int] * 4 + [_P]),
+    ("dvm_nn_up2_bwd", ctypes.c_int, [_P, _P] + [ctypes.c_int] * 4 + [_P]),
+    ("dvm_nn_mse", ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int, ctypes.c_int64, ctypes.c_float, _P]),
+    ("dvm_nn_mse_partials", ctypes.c_int64, [ctypes.c_int, ctypes.c_int64]),
+    ("dvm_nn_adam", ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
+                                   ctypes.c_float, ctypes.c_float, ctypes.c_int64, ctypes.c_float, _P]),
+    ("dvm_nn_round_bf16", ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
     ("dvm_noalloc_last_error", ctypes.c_char_p, []),
 ]
 
