@@ -45,15 +45,17 @@ def layer_shapes(levels, base, cin, cout):
     return shapes
 
 
-def signed_distance(mask):
+def signed_distance(mask, cap=16):
     """Distance (voxels) to the nearest solid voxel in the fluid, minus the distance to the nearest
-    fluid voxel in the solid, on the periodic grid (computed on a 3x3x3 tiling)."""
+    fluid voxel in the solid, on the periodic grid, clipped to +-cap (a periodic margin of cap
+    voxels around the grid makes every distance up to cap exact)."""
     from scipy import ndimage
-    tiled = np.tile(mask, (3,) * mask.ndim)
-    dfl = ndimage.distance_transform_edt(~tiled)
-    dso = ndimage.distance_transform_edt(tiled)
-    sl = tuple(slice(n, 2 * n) for n in mask.shape)
-    return (dfl - dso)[sl]
+    m = min(cap, *mask.shape)
+    padded = np.pad(mask, m, mode="wrap")
+    dfl = ndimage.distance_transform_edt(~padded)
+    dso = ndimage.distance_transform_edt(padded)
+    sl = tuple(slice(m, m + n) for n in mask.shape)
+    return np.clip((dfl - dso)[sl], -cap, cap)
 
 
 def features(mask, kn):
@@ -115,6 +117,10 @@ class UNet:
         self.vb = [torch.zeros_like(b) for b in self.b]
         self.bq = [torch.empty_like(b) for b in self.b]
         self.steps = 0
+        # per-channel standardisation of the targets (set from the training set): the network
+        # learns (target - shift) / scale
+        self.out_shift = np.zeros(cout, np.float32)
+        self.out_scale = np.ones(cout, np.float32)
         self._requantize()
 
     # -- helpers
@@ -268,8 +274,31 @@ class UNet:
         return float(np.sum(part.cpu().numpy(), dtype=np.float64) / count), dy
 
     # -- persistence
+    def set_standardisation(self, targets_and_masks):
+        """Per-channel mean and standard deviation of the targets over the fluid voxels."""
+        acc = np.zeros((self.cout, 3))
+        for t, m in targets_and_masks:
+            fl = m.reshape(t.shape[1:]) > 0
+            for c in range(self.cout):
+                x = t[c][fl].astype(np.float64)
+                acc[c] += (x.size, x.sum(), (x * x).sum())
+        mean = acc[:, 1] / acc[:, 0]
+        self.out_shift = mean.astype(np.float32)
+        self.out_scale = np.sqrt(np.maximum(acc[:, 2] / acc[:, 0] - mean ** 2, 1e-12)).astype(np.float32)
+
+    def standardise(self, t):
+        """Device target -> standardised device target."""
+        sh = self.torch.tensor(self.out_shift, device="cuda")[:, None, None, None]
+        sc = self.torch.tensor(self.out_scale, device="cuda")[:, None, None, None]
+        return ((t - sh) / sc).contiguous()
+
+    def destandardise(self, y):
+        """Host network output -> target units."""
+        return y * self.out_scale[:, None, None, None] + self.out_shift[:, None, None, None]
+
     def state(self):
         return {"levels": self.levels, "base": self.base, "cin": self.cin, "cout": self.cout,
+                "out_shift": self.out_shift, "out_scale": self.out_scale,
                 "w": [w.cpu().numpy() for w in self.w], "b": [b.cpu().numpy() for b in self.b]}
 
     def load_state(self, st):
@@ -286,7 +315,7 @@ def predict(net, mask, kn):
     x = torch.from_numpy(features(mask, kn)).cuda()
     y = net.forward(x)
     net._rec = None
-    return y.cpu().numpy()
+    return net.destandardise(y.cpu().numpy())
 
 
 def solve_to(mask, kn, v, w, tol, max_iter, initial=None, **options):
@@ -333,6 +362,8 @@ def run_pipeline(train=48, side=64, eval_side=128, eval_seeds=(10000, 10001), ev
     t_data = time.perf_counter() - t0
     log("training set: %d runs in %.1f s" % (train, t_data))
     net = UNet(levels=levels, base=base, seed=seed)
+    net.set_standardisation([(t.cpu().numpy(), m.cpu().numpy()) for _, t, m in data])
+    data = [(x, net.standardise(t), m) for x, t, m in data]
     losses = []
     t0 = time.perf_counter()
     for step in range(steps):
@@ -341,7 +372,7 @@ def run_pipeline(train=48, side=64, eval_side=128, eval_seeds=(10000, 10001), ev
         y = net.forward(x)
         loss, dy = net.loss_and_grad(y, t, m)
         net.backward(dy)
-        net.step(lr=lr * (0.1 if step >= 0.8 * steps else 1.0))
+        net.step(lr=lr * 0.5 * (1.0 + math.cos(math.pi * step / steps)))
         losses.append(loss)
         if step % 200 == 0:
             log("step %d loss %.4e" % (step, loss))
@@ -354,16 +385,23 @@ def run_pipeline(train=48, side=64, eval_side=128, eval_seeds=(10000, 10001), ev
     for sd in eval_seeds:
         mask = inputs.gaussian_rock(eval_side, seed=sd, corr_len=8.0, porosity=0.35)
         for kn in eval_kns:
-            it0, dt0, k0, _, _, st0 = solve_to(mask, kn, v, w, 1e-6, 20000, **opts)
+            it0, dt0, k0, rho_c, u_c, st0 = solve_to(mask, kn, v, w, 1e-6, 20000, **opts)
             torch.cuda.synchronize()
             ta = time.perf_counter()
             init = to_initial(mask, kn, predict(net, mask, kn))
             torch.cuda.synchronize()
             t_inf = time.perf_counter() - ta
+            fl = ~mask
+            x1 = np.broadcast_to(np.arange(mask.shape[-1]) / mask.shape[-1], mask.shape)
+            rc = (rho_c + x1)[fl]
+            rp = (init[0] + x1)[fl]
+            pred_err = {"u": float(np.linalg.norm((init[1] - u_c)[:, fl]) / np.linalg.norm(u_c[:, fl])),
+                        "rho": float(np.linalg.norm((rp - rp.mean()) - (rc - rc.mean())) / np.linalg.norm(rc - rc.mean())),
+                        "k_pred_over_k": float(init[1][0].mean() / u_c[0].mean())}
             it1, dt1, k1, _, _, st1 = solve_to(mask, kn, v, w, 1e-6, 20000, initial=init, **opts)
             row = {"seed": sd, "kn": kn, "plain_fp32": {"iterations": it0, "seconds": dt0, "k": k0, "status": st0},
                    "warm_fp32": {"iterations": it1, "seconds": dt1 + t_inf, "inference_seconds": t_inf, "k": k1,
-                                 "status": st1}, "k_rel_diff": abs(k1 - k0) / abs(k0)}
+                                 "status": st1}, "k_rel_diff": abs(k1 - k0) / abs(k0), "prediction_error": pred_err}
             if fp64_cap > 0:
                 s = dvm.Solver(mask, kn, v, w, precision="fp64", lateral="periodic")
                 torch.cuda.synchronize()

@@ -37,6 +37,8 @@ def test_trained_network_reduces_iterations_and_keeps_the_answer():
         m = torch.from_numpy((~mask).astype(np.float32).ravel()).cuda()
         train.append((x, t, m))
     net = warmstart.UNet(levels=2, base=8, seed=1)
+    net.set_standardisation([(t.cpu().numpy(), m.cpu().numpy()) for _, t, m in train])
+    train = [(x, net.standardise(t), m) for x, t, m in train]
     losses = []
     for step in range(900):
         x, t, m = train[step % len(train)]
