@@ -96,8 +96,8 @@ typedef struct {
      * floor(l c_j / n_j) = s); an upstream point in another block takes its value from the previous
      * iteration instead of the current sweep, so blocks sweep independently.  This changes the
      * iteration history (more iterations to converge) but not the fixed point.  0 or 1 = no cut
-     * (the exact serial iteration, the default).  Implemented: c2 in 2D, each block at least two
-     * rows; other values are rejected with DVM_EINVAL. */
+     * (the exact serial iteration, the default).  Implemented: c1 and c2 in 2D, each block at least
+     * two points wide; c3 and 3D cuts are rejected with DVM_EINVAL. */
     int subdomains[3];
 } dvm_options;
 

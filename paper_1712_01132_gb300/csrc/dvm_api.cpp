@@ -22,8 +22,8 @@
 namespace dvm {
 bool half_range_gh(int m, double* c, double* a);
 template <typename T> size_t sweep2d_smem(int T1, int NW, int max_rows);
-template <typename T> cudaError_t launch_sweep2d(const SweepArgs2D<T>&, int T1, int grid, int NW, cudaStream_t);
-template <typename T> cudaError_t sweep2d_occupancy(int T1, int NW, int max_rows, int* blocks_per_sm);
+template <typename T> cudaError_t launch_sweep2d(const SweepArgs2D<T>&, int T1, int xs, int grid, int NW, cudaStream_t);
+template <typename T> cudaError_t sweep2d_occupancy(int T1, int xs, int NW, int max_rows, int* blocks_per_sm);
 template <typename T> cudaError_t launch_finalize2d(const FinArgs2D<T>&, int nblocks, cudaStream_t);
 template <typename T> cudaError_t launch_init2d(const Prob2D<T>*, int NL, const double* qw, cudaStream_t);
 template <typename T> cudaError_t launch_moments2d(const Prob2D<T>*, double* rho, double* u, cudaStream_t);
@@ -31,8 +31,8 @@ template <typename T> cudaError_t launch_wall2d(const Prob2D<T>*, double* out, c
 template <typename T>
 cudaError_t launch_warm2d(const Prob2D<T>*, int NL, int par, const double* qw2, const double* vel, const double* rho0,
                           const double* u0, cudaStream_t);
-cudaError_t launch_sweep2d_f32x2(const SweepArgs2D<float>&, int T1, int grid, int NW, cudaStream_t);
-cudaError_t sweep2d_f32x2_occupancy(int T1, int NW, int max_rows, int* blocks_per_sm);
+cudaError_t launch_sweep2d_f32x2(const SweepArgs2D<float>&, int T1, int xs, int grid, int NW, cudaStream_t);
+cudaError_t sweep2d_f32x2_occupancy(int T1, int xs, int NW, int max_rows, int* blocks_per_sm);
 int sweep2d_f32x2_max_rows(int T1, int NW);
 int sweep2d_f32x2_velocities_per_lane();
 template <typename T> size_t sweep3d_smem(int T1, int NW, int R2, int R3);
@@ -80,6 +80,7 @@ struct dvm_ctx {
     int dims = 2, nprob = 0, nv = 0, nvq = 0, NQ = 4, NL = 32, NW = 1;
     int prec = DVM_FP64;             // arithmetic precision (BF16 storage computes in FP32)
     bool bf16 = false;               // 3D ghosts and pencil edges stored as BF16
+    bool xsub = false;               // 2D x1 subdomains (tile tables, lagged x1 halos)
     int T1 = 8, rows = 8, max_rows = 8;
     std::vector<HostProb> hp;
     std::vector<Buf> bufs;
@@ -358,6 +359,55 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         }
         P.bands = bands_dev;
         P.slot_row = slot_dev;
+        // ---- x1 tiles per quadrant; with c1 x1 subdomains no tile straddles a subdomain boundary,
+        // the first tile of a subdomain takes its x1 carry from lagged slot sp (slot 0: the x1
+        // ghosts) and the last one writes the carry into the slot of the next subdomain
+        const int c1 = std::max(1, c->opt.subdomains[0]);
+        std::vector<int> xslot((size_t)NQ * c1);
+        std::vector<std::vector<int4>> qt(NQ);
+        {
+            std::vector<int> X(c1 + 1);
+            for (int s = 0; s <= c1; ++s) X[s] = (s * P.n1 + c1 - 1) / c1;
+            for (int q = 0; q < NQ; ++q) {
+                const bool s1neg = q & 1;
+                for (int sp = 0; sp < c1; ++sp) {
+                    const int lo = s1neg ? P.n1 - X[c1 - sp] : X[sp];
+                    const int hi = s1neg ? P.n1 - X[c1 - 1 - sp] : X[sp + 1];
+                    xslot[(size_t)q * c1 + sp] = sp == 0 ? P.n1 : lo;
+                    for (int cc = lo; cc < hi; cc += c->T1) {
+                        const int wd = std::min(c->T1, hi - cc);
+                        qt[q].push_back(make_int4(cc, wd, cc == lo ? sp : -1, cc + wd == hi ? (sp + 1) % c1 : -1));
+                    }
+                }
+            }
+        }
+        P.nxslots = c1;
+        P.ntiles = 0;
+        for (int q = 0; q < NQ; ++q) {
+            P.ntq[q] = (int)qt[q].size();
+            P.ntiles = std::max(P.ntiles, P.ntq[q]);
+        }
+        {
+            int* xs_dev = (int*)dev_alloc(c, xslot.size() * sizeof(int));
+            if (!xs_dev) return fail(c, DVM_ENOMEM, "device allocation failed");
+            cudaError_t e = cudaMemcpyAsync(xs_dev, xslot.data(), xslot.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream);
+            P.xslot_col = xs_dev;
+            P.tiles = nullptr;
+            if (e == cudaSuccess && c->xsub) {
+                std::vector<int4> ttab((size_t)NQ * P.ntiles, make_int4(0, 0, -1, -1));
+                for (int q = 0; q < NQ; ++q)
+                    for (size_t k = 0; k < qt[q].size(); ++k) ttab[(size_t)q * P.ntiles + k] = qt[q][k];
+                int4* t_dev = (int4*)dev_alloc(c, ttab.size() * sizeof(int4));
+                if (!t_dev) return fail(c, DVM_ENOMEM, "device allocation failed");
+                e = cudaMemcpyAsync(t_dev, ttab.data(), ttab.size() * sizeof(int4), cudaMemcpyHostToDevice, c->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+                P.tiles = t_dev;
+                c->h2d_bytes += ttab.size() * sizeof(int4);
+            }
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "upload tile tables");
+            c->h2d_bytes += xslot.size() * sizeof(int);
+        }
         P.lateral = c->opt.lateral_bc;
         P.order = c->opt.stencil_order;
         P.kn = H.kn;
@@ -370,7 +420,7 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         P.src = (T*)dev_alloc(c, N * 4 * sizeof(T));
         P.E = (T*)dev_alloc(c, N * 4 * sizeof(T));
         P.P = (T*)dev_alloc(c, (size_t)NQ * 3 * N * sizeof(T));
-        P.gx1 = (T*)dev_alloc(c, (size_t)2 * NQ * P.n2 * 2 * NL * sizeof(T));
+        P.gx1 = (T*)dev_alloc(c, (size_t)2 * NQ * P.nxslots * P.n2 * 2 * NL * sizeof(T));
         P.glat = (T*)dev_alloc(c, (size_t)2 * NQ * P.nslots * P.n1 * 2 * NL * sizeof(T));
         P.edge = (T*)dev_alloc(c, (size_t)NQ * 2 * P.nslots * P.n1 * 2 * NL * sizeof(T));
         T* lanec = (T*)dev_alloc(c, (size_t)NQ * NL * kLaneConsts * sizeof(T));
@@ -471,8 +521,8 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     c->probs_host.assign((const char*)probs.data(), (const char*)probs.data() + probs.size() * sizeof(Prob2D<T>));
     // ---- persistent grid size
     int per_sm = 0;
-    if (c->prec == DVM_FP32) e = sweep2d_f32x2_occupancy(c->T1, c->NW, c->max_rows, &per_sm);
-    else e = sweep2d_occupancy<T>(c->T1, c->NW, c->max_rows, &per_sm);
+    if (c->prec == DVM_FP32) e = sweep2d_f32x2_occupancy(c->T1, c->xsub, c->NW, c->max_rows, &per_sm);
+    else e = sweep2d_occupancy<T>(c->T1, c->xsub, c->NW, c->max_rows, &per_sm);
     if (e != cudaSuccess) return cuda_fail(c, e, "occupancy");
     if (per_sm < 1) return fail(c, DVM_EINVAL, "sweep kernel does not fit on an SM with these tiles");
     int dev = 0, sms = 0;
@@ -786,11 +836,11 @@ cudaError_t mark(dvm_ctx* c) {
 }
 
 cudaError_t sweep_launch(const SweepArgs2D<float>& a, dvm_ctx* c) {
-    return launch_sweep2d_f32x2(a, c->T1, c->sweep_grid, c->NW, c->stream);
+    return launch_sweep2d_f32x2(a, c->T1, c->xsub, c->sweep_grid, c->NW, c->stream);
 }
 
 cudaError_t sweep_launch(const SweepArgs2D<double>& a, dvm_ctx* c) {
-    return launch_sweep2d<double>(a, c->T1, c->sweep_grid, c->NW, c->stream);
+    return launch_sweep2d<double>(a, c->T1, c->xsub, c->sweep_grid, c->NW, c->stream);
 }
 
 template <typename T>
@@ -964,7 +1014,7 @@ struct Seg {
 
 template <typename T>
 void state_segs_2d(const Prob2D<T>& P, size_t NL, int par, std::vector<Seg>& out) {
-    const size_t gx = (size_t)4 * P.n2 * 2 * NL, gl = (size_t)4 * P.nslots * P.n1 * 2 * NL;
+    const size_t gx = (size_t)4 * P.nxslots * P.n2 * 2 * NL, gl = (size_t)4 * P.nslots * P.n1 * 2 * NL;
     out.push_back({P.P, (size_t)4 * 3 * P.N * sizeof(T)});
     out.push_back({P.gx1 + par * gx, gx * sizeof(T)});
     out.push_back({P.glat + par * gl, gl * sizeof(T)});
@@ -1121,8 +1171,9 @@ dvm_status dvm_create_batch(int nprob, const dvm_geometry* geoms, const double* 
     if (c->opt.check_interval < 1) return reject(DVM_EINVAL, "check_interval");
     for (int j = 0; j < 3; ++j)
         if (c->opt.subdomains[j] < 0) return reject(DVM_EINVAL, "subdomain counts must not be negative");
-    if (c->opt.subdomains[0] > 1 || c->opt.subdomains[2] > 1 || (dims == 3 && c->opt.subdomains[1] > 1))
-        return reject(DVM_EINVAL, "lagged-halo subdomains are implemented along x2 of 2D problems only");
+    if (c->opt.subdomains[2] > 1 || (dims == 3 && (c->opt.subdomains[0] > 1 || c->opt.subdomains[1] > 1)))
+        return reject(DVM_EINVAL, "lagged-halo subdomains are implemented along x1 and x2 of 2D problems only");
+    c->xsub = dims == 2 && c->opt.subdomains[0] > 1;
     c->dims = dims;
     c->nprob = nprob;
     c->prec = c->opt.precision == DVM_BF16_STORE ? DVM_FP32 : c->opt.precision;
@@ -1148,6 +1199,8 @@ dvm_status dvm_create_batch(int nprob, const dvm_geometry* geoms, const double* 
         if (N > (1LL << 30)) return reject(DVM_EINVAL, "geometry too large");
         if (dims == 2 && c->opt.subdomains[1] > 1 && g.n[1] < 2LL * c->opt.subdomains[1])
             return reject(DVM_EINVAL, "every x2 subdomain needs at least two rows");
+        if (dims == 2 && c->opt.subdomains[0] > 1 && g.n[0] < 2LL * c->opt.subdomains[0])
+            return reject(DVM_EINVAL, "every x1 subdomain needs at least two columns");
         H.N = (int)N;
         H.kn = kn[b];
         H.nu = std::sqrt(3.14159265358979323846) / (2.0 * kn[b]);

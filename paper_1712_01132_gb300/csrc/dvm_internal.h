@@ -41,6 +41,14 @@ struct Prob2D {
                          // above}; below/above = s >= 0: lagged slot s; -1 - e: live band edge in
                          // ring slot e (two slots per subdomain, alternating between its bands)
     const int* slot_row; // [4][nslots] oriented row just above the layers a slot holds (slot 0: n2)
+    int nxslots;         // lagged x1 slots per quadrant: slot 0 is the periodic x1 face, slot s >= 1
+                         // the start of the s-th x1 subdomain (1 without x1 subdomains)
+    int ntiles;          // x1 tiles per quadrant (largest count) when x1 subdomains are used
+    int ntq[4];          // x1 tiles of each quadrant
+    const int4* tiles;   // [4][ntiles] with x1 subdomains: {first oriented column, width, lagged
+                         // slot the carry is read from before the tile or -1, slot written after it
+                         // or -1}; NULL without x1 subdomains (uniform tiles)
+    const int* xslot_col;  // [4][nxslots] oriented column just after the layers a slot holds
     int lateral;         // 0 specular, 1 periodic
     int order;           // 2 or 1
     double kn, nu, dx;
@@ -49,7 +57,8 @@ struct Prob2D {
     T* src;              // [N][4]  (nu rho', 2 nu u1 + 1, 2 nu u2, 0)
     T* E;                // [N][4]  wall terms per (axis j, upstream side u): index 2 j + u
     T* P;                // [4][3][N] moment partials per quadrant (rho', u1, u2)
-    T* gx1;              // [2][4][n2][2][NL] x1 ghost layers (parity, quadrant, row, layer, lane)
+    T* gx1;              // [2][4][nxslots][n2][2][NL] lagged x1 layers (parity, quadrant, slot, row,
+                         // layer, lane): the x1 ghosts (slot 0) and the x1 subdomain halos
     T* glat;             // [2][4][nslots][n1][2][NL] lagged x2 layers (parity, quadrant, slot, col,
                          // layer, lane): the x2 ghosts (slot 0) and the subdomain halos
     T* edge;             // [4][2 nslots][n1][2][NL] band-to-band edges (ring slots, see bands)

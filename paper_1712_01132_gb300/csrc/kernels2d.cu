@@ -99,7 +99,7 @@ __device__ __forceinline__ void sweep_tile_rows(const T* __restrict__ rec, T* __
     }
 }
 
-template <typename T, int T1>
+template <typename T, int T1, bool XS>
 __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs2D<T> a) {
     using V = typename Vec4<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -143,19 +143,37 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs2D<T> a) {
             L.R0 = lc[7]; L.R1 = lc[8]; L.R2 = lc[9]; L.R3 = lc[10];
         }
         const int par = a.parity;
-        // x1 upstream of the first tile: ghost layers of the previous iteration (Eq. 7, source form)
-        {
-            const T* g = P->gx1 + (((size_t)par * 4 + q) * n2) * 2 * NL;
+        // x1 upstream of a tile from a lagged slot: the x1 ghost layers of the previous iteration
+        // (Eq. 7, source form; slot 0) or, with x1 subdomains, a subdomain halo; and the carry of the
+        // last tile into the slot the next iteration reads
+        auto carry_in = [&](int slot) {
+            const T* g = P->gx1 + (((size_t)(par * 4 + q) * P->nxslots + slot) * n2) * 2 * NL;
             for (int r = 0; r < nrows; ++r) {
                 T* cr = carry + ((size_t)(warp * RB + r) * 2) * 32 + lane;
                 cr[0] = g[((size_t)(row0 + r) * 2 + 0) * NL + wl];
                 cr[32] = g[((size_t)(row0 + r) * 2 + 1) * NL + wl];
             }
-        }
-        const int ntiles = (n1 + T1 - 1) / T1;
+        };
+        auto carry_out = [&](int slot) {
+            T* g = P->gx1 + (((size_t)((par ^ 1) * 4 + q) * P->nxslots + slot) * n2) * 2 * NL;
+            for (int r = 0; r < nrows; ++r) {
+                const T* cr = carry + ((size_t)(warp * RB + r) * 2) * 32 + lane;
+                g[((size_t)(row0 + r) * 2 + 0) * NL + wl] = cr[0];
+                g[((size_t)(row0 + r) * 2 + 1) * NL + wl] = cr[32];
+            }
+        };
+        if constexpr (!XS) carry_in(0);
+        const int ntiles = XS ? P->ntq[q] : (n1 + T1 - 1) / T1;
         for (int t = 0; t < ntiles; ++t) {
-            const int c0 = t * T1;
-            const int width = min(T1, n1 - c0);
+            int4 tcur;
+            if constexpr (XS) {
+                tcur = __ldg(P->tiles + (size_t)q * P->ntiles + t);
+                if (tcur.z >= 0) carry_in(tcur.z);
+            } else {
+                tcur = make_int4(t * T1, min(T1, n1 - t * T1), t == 0 ? 0 : -1, t == ntiles - 1 ? 0 : -1);
+            }
+            const int c0 = tcur.x;
+            const int width = tcur.y;
             if (threadIdx.x == 0 && below < 0) {
                 if (!wait_geq(P->prog + q * nb + band - 1, t + 1, a.status, a.timeout_ns)) s_abort = 1;
             }
@@ -231,15 +249,9 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs2D<T> a) {
                     }
                 }
             }
-            if (t == ntiles - 1) {
-                // x1 ghost layers of the next iteration (periodic in x1, same quadrant)
-                T* g = P->gx1 + (((size_t)(par ^ 1) * 4 + q) * n2) * 2 * NL;
-                for (int r = 0; r < nrows; ++r) {
-                    const T* cr = carry + ((size_t)(warp * RB + r) * 2) * 32 + lane;
-                    g[((size_t)(row0 + r) * 2 + 0) * NL + wl] = cr[0];
-                    g[((size_t)(row0 + r) * 2 + 1) * NL + wl] = cr[32];
-                }
-            }
+            // x1 ghost layers of the next iteration (periodic in x1, same quadrant) or the halo of
+            // the next x1 subdomain
+            if (tcur.w >= 0) carry_out(tcur.w);
             __syncthreads();
             // the band above only needs the edge: publish before combining the moment partials
             if (threadIdx.x == 0 && it != a.withhold_item) {
@@ -382,10 +394,12 @@ __global__ void init2d_kernel(const Prob2D<T>* prob, int NL, const double* qw /*
         const double x1 = (id % n1) * P->dx;
         P->P[idx] = (P->code[id] & kSolidBit) ? T(0) : (T)(x1 * qw[qm]);
     }
-    for (size_t idx = t0; idx < (size_t)2 * 4 * n2 * 2 * nl; idx += stride) {
+    const int nxs = P->nxslots;
+    for (size_t idx = t0; idx < (size_t)2 * 4 * nxs * n2 * 2 * nl; idx += stride) {
         const int layer = (idx / nl) % 2;
-        const int q = (idx / (nl * 2 * n2)) % 4;
-        const int ico = n1 - 1 - layer;                          // oriented source column
+        const int sl = (idx / (nl * 2 * n2)) % nxs;
+        const int q = (idx / (nl * 2 * n2 * nxs)) % 4;
+        const int ico = P->xslot_col[q * nxs + sl] - 1 - layer;     // oriented source column
         const int col = (q & 1) ? n1 - 1 - ico : ico;
         P->gx1[idx] = (T)(col * P->dx);
     }
@@ -426,16 +440,19 @@ __global__ void warm2d_kernel(const Prob2D<T>* P, int NL, int par, const double*
         }
         P->P[idx] = (T)val;
     }
-    // x1 ghosts: slot (q, oriented row, layer) holds h at oriented column n1 - 1 - layer
-    for (size_t idx = t0; idx < (size_t)4 * n2 * 2 * nl; idx += stride) {
+    // lagged x1 layers: slot (q, s, oriented row, layer) holds h at the oriented column
+    // xslot_col[q][s] - 1 - layer (slot 0: the x1 ghosts, columns n1 - 1 - layer)
+    const int nxs = P->nxslots;
+    for (size_t idx = t0; idx < (size_t)4 * nxs * n2 * 2 * nl; idx += stride) {
         const int l = idx % nl;
         const int layer = (idx / nl) % 2;
         const int yo = (idx / (nl * 2)) % n2;
-        const int q = idx / (nl * 2 * n2);
-        const int ico = n1 - 1 - layer;
+        const int sl = (idx / (nl * 2 * n2)) % nxs;
+        const int q = idx / (nl * 2 * n2 * nxs);
+        const int ico = P->xslot_col[q * nxs + sl] - 1 - layer;
         const int x = (q & 1) ? n1 - 1 - ico : ico;
         const int y = (q & 2) ? n2 - 1 - yo : yo;
-        P->gx1[(size_t)par * 4 * n2 * 2 * nl + idx] = (T)h0(x, y, vel + ((size_t)q * nl + l) * 2);
+        P->gx1[(size_t)par * 4 * nxs * n2 * 2 * nl + idx] = (T)h0(x, y, vel + ((size_t)q * nl + l) * 2);
     }
     // lagged x2 layers: quadrant q writes the oriented rows below slot s (slot 0: its top rows
     // n2 - 1 - layer) into the slot of the quadrant that reads them (slot 0: itself when periodic,
@@ -505,36 +522,35 @@ size_t sweep2d_smem(int T1, int NW, int max_rows) {
                         (size_t)NW * max_rows * 2 * 32);
 }
 
-template <typename T, int T1>
+template <typename T, int T1, bool XS>
 static cudaError_t launch_sweep_t(const SweepArgs2D<T>& a, int grid, int NW, cudaStream_t st) {
     const size_t smem = sweep2d_smem<T>(T1, NW, a.max_rows);
-    cudaError_t e = cudaFuncSetAttribute(sweep2d_kernel<T, T1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(sweep2d_kernel<T, T1, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    sweep2d_kernel<T, T1><<<grid, NW * 32, smem, st>>>(a);
+    sweep2d_kernel<T, T1, XS><<<grid, NW * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
+// xs: x1 subdomains (tile tables and lagged x1 halos)
 template <typename T>
-cudaError_t launch_sweep2d(const SweepArgs2D<T>& a, int T1, int grid, int NW, cudaStream_t st) {
-    if (T1 == 8) return launch_sweep_t<T, 8>(a, grid, NW, st);
-    if (T1 == 16) return launch_sweep_t<T, 16>(a, grid, NW, st);
+cudaError_t launch_sweep2d(const SweepArgs2D<T>& a, int T1, int xs, int grid, int NW, cudaStream_t st) {
+    if (T1 == 8) return xs ? launch_sweep_t<T, 8, true>(a, grid, NW, st) : launch_sweep_t<T, 8, false>(a, grid, NW, st);
+    if (T1 == 16) return xs ? launch_sweep_t<T, 16, true>(a, grid, NW, st) : launch_sweep_t<T, 16, false>(a, grid, NW, st);
     return cudaErrorInvalidValue;
 }
 
-template <typename T>
-cudaError_t sweep2d_occupancy(int T1, int NW, int max_rows, int* blocks_per_sm) {
+template <typename T, int T1, bool XS>
+static cudaError_t occ2(int NW, int max_rows, int* blocks_per_sm) {
     const size_t smem = sweep2d_smem<T>(T1, NW, max_rows);
-    cudaError_t e;
-    if (T1 == 8) {
-        e = cudaFuncSetAttribute(sweep2d_kernel<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep2d_kernel<T, 8>, NW * 32, smem);
-    }
-    if (T1 == 16) {
-        e = cudaFuncSetAttribute(sweep2d_kernel<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep2d_kernel<T, 16>, NW * 32, smem);
-    }
+    cudaError_t e = cudaFuncSetAttribute(sweep2d_kernel<T, T1, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep2d_kernel<T, T1, XS>, NW * 32, smem);
+}
+
+template <typename T>
+cudaError_t sweep2d_occupancy(int T1, int xs, int NW, int max_rows, int* blocks_per_sm) {
+    if (T1 == 8) return xs ? occ2<T, 8, true>(NW, max_rows, blocks_per_sm) : occ2<T, 8, false>(NW, max_rows, blocks_per_sm);
+    if (T1 == 16) return xs ? occ2<T, 16, true>(NW, max_rows, blocks_per_sm) : occ2<T, 16, false>(NW, max_rows, blocks_per_sm);
     return cudaErrorInvalidValue;
 }
 
@@ -571,8 +587,8 @@ cudaError_t launch_wall2d(const Prob2D<T>* prob_dev, double* out, cudaStream_t s
 
 #define DVM_INSTANTIATE(T)                                                                      \
     template size_t sweep2d_smem<T>(int, int, int);                                            \
-    template cudaError_t launch_sweep2d<T>(const SweepArgs2D<T>&, int, int, int, cudaStream_t);  \
-    template cudaError_t sweep2d_occupancy<T>(int, int, int, int*);                             \
+    template cudaError_t launch_sweep2d<T>(const SweepArgs2D<T>&, int, int, int, int, cudaStream_t); \
+    template cudaError_t sweep2d_occupancy<T>(int, int, int, int, int*);                       \
     template cudaError_t launch_finalize2d<T>(const FinArgs2D<T>&, int, cudaStream_t);          \
     template cudaError_t launch_init2d<T>(const Prob2D<T>*, int, const double*, cudaStream_t);  \
     template cudaError_t launch_warm2d<T>(const Prob2D<T>*, int, int, const double*, const double*, \

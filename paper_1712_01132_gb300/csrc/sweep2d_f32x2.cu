@@ -47,7 +47,7 @@ __device__ __forceinline__ float2 dup(float x) { return make_float2(x, x); }
 
 }  // namespace
 
-template <int T1>
+template <int T1, bool XS>
 __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<float> a) {
     constexpr int kLPP = 32 / T1;               // lanes per point after the reduce-scatter
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -117,15 +117,31 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
                     make_float4(lc[7 + rs], lc[kLaneConsts + 7 + rs], lc[2 * kLaneConsts + 7 + rs], lc[3 * kLaneConsts + 7 + rs]);
         }
         const int par = a.parity;
-        {
-            const float* g = P->gx1 + (((size_t)par * 4 + q) * n2) * 2 * NL;
+        // x1 carry from a lagged slot (the x1 ghosts, or with x1 subdomains a subdomain halo of the
+        // previous iteration) / into a slot for the next iteration
+        auto carry_in = [&](int slot) {
+            const float* g = XS ? P->gx1 + (((size_t)(par * 4 + q) * P->nxslots + slot) * n2) * 2 * NL
+                                : P->gx1 + (((size_t)par * 4 + q) * n2) * 2 * NL;
             for (int r = 0; r < nrows; ++r) {
                 float* cr = carry + ((size_t)(warp * RB + r) * 2) * 128 + 4 * lane;
                 *reinterpret_cast<float4*>(cr) = *reinterpret_cast<const float4*>(g + ((size_t)(row0 + r) * 2 + 0) * NL + kVL * wl);
                 *reinterpret_cast<float4*>(cr + 128) = *reinterpret_cast<const float4*>(g + ((size_t)(row0 + r) * 2 + 1) * NL + kVL * wl);
             }
-        }
-        const int ntiles = (n1 + T1 - 1) / T1;
+        };
+        auto carry_out = [&](int slot) {
+            float* g = XS ? P->gx1 + (((size_t)((par ^ 1) * 4 + q) * P->nxslots + slot) * n2) * 2 * NL
+                          : P->gx1 + (((size_t)(par ^ 1) * 4 + q) * n2) * 2 * NL;
+            for (int rr = 0; rr < nrows; ++rr) {
+                const float* cr = carry + ((size_t)(warp * RB + rr) * 2) * 128 + 4 * lane;
+                *reinterpret_cast<float4*>(g + ((size_t)(row0 + rr) * 2 + 0) * NL + kVL * wl) = *reinterpret_cast<const float4*>(cr);
+                *reinterpret_cast<float4*>(g + ((size_t)(row0 + rr) * 2 + 1) * NL + kVL * wl) = *reinterpret_cast<const float4*>(cr + 128);
+            }
+        };
+        if constexpr (!XS) carry_in(0);
+        const int ntiles = XS ? P->ntq[q] : (n1 + T1 - 1) / T1;
+        // with x1 subdomains, tile tt of this quadrant: {first oriented column, width, carry slot
+        // in, carry slot out}; otherwise tiles are uniform
+        auto tinfo = [&](int tt) -> int4 { return __ldg(P->tiles + (size_t)q * P->ntiles + tt); };
         const int npts = nrows * T1;
         const int rounds = (npts + blockDim.x - 1) / blockDim.x;
 
@@ -136,8 +152,17 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
                 const int idx = k * blockDim.x + threadIdx.x;
                 if (k < rounds && idx < npts) {
                     const int r = idx / T1;
-                    const int ic = tt * T1 + (idx - r * T1);
-                    if (ic < n1) {
+                    int ic;
+                    bool inside;
+                    if constexpr (XS) {
+                        const int4 ti = tinfo(tt);
+                        ic = ti.x + (idx - r * T1);
+                        inside = idx - r * T1 < ti.y;
+                    } else {
+                        ic = tt * T1 + (idx - r * T1);
+                        inside = ic < n1;
+                    }
+                    if (inside) {
                         const int x = s1neg ? n1 - 1 - ic : ic;
                         const int yo = row0 + r;
                         const int y = s2neg ? n2 - 1 - yo : yo;
@@ -196,8 +221,18 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
             store_rec(0, raw);
         }
         for (int t = 0; t < ntiles; ++t) {
-            const int c0 = t * T1;
-            const int width = min(T1, n1 - c0);
+            int c0, width, cout_slot;
+            if constexpr (XS) {
+                const int4 tcur = tinfo(t);
+                c0 = tcur.x;
+                width = tcur.y;
+                cout_slot = tcur.w;
+                if (tcur.z >= 0) carry_in(tcur.z);
+            } else {
+                c0 = t * T1;
+                width = min(T1, n1 - c0);
+                cout_slot = (t == ntiles - 1) ? 0 : -1;
+            }
             const int buf = t & 1;
             RawPoint nxt[kMaxRounds];
             if (t + 1 < ntiles) load_raw(t + 1, nxt);
@@ -311,15 +346,9 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
                     }
                 }
             }
-            if (t == ntiles - 1) {
-                // x1 ghost layers of the next iteration (periodic in x1, same quadrant)
-                float* g = P->gx1 + (((size_t)(par ^ 1) * 4 + q) * n2) * 2 * NL;
-                for (int rr = 0; rr < nrows; ++rr) {
-                    const float* cr = carry + ((size_t)(warp * RB + rr) * 2) * 128 + 4 * lane;
-                    *reinterpret_cast<float4*>(g + ((size_t)(row0 + rr) * 2 + 0) * NL + kVL * wl) = *reinterpret_cast<const float4*>(cr);
-                    *reinterpret_cast<float4*>(g + ((size_t)(row0 + rr) * 2 + 1) * NL + kVL * wl) = *reinterpret_cast<const float4*>(cr + 128);
-                }
-            }
+            // x1 ghost layers of the next iteration (periodic in x1, same quadrant) or the halo of
+            // the next x1 subdomain
+            if (cout_slot >= 0) carry_out(cout_slot);
             if (t + 1 < ntiles) store_rec(buf ^ 1, nxt);
             __syncthreads();
             if (threadIdx.x == 0 && it != a.withhold_item) {
@@ -356,32 +385,33 @@ int sweep2d_f32x2_max_rows(int T1, int NW) { return kMaxRounds * NW * 32 / T1; }
 
 int sweep2d_f32x2_velocities_per_lane() { return kVL; }
 
-template <int T1>
+template <int T1, bool XS>
 static cudaError_t launch_f32x2_t(const SweepArgs2D<float>& a, int grid, int NW, cudaStream_t st) {
     const size_t smem = sweep2d_f32x2_smem(T1, NW, a.max_rows);
-    cudaError_t e = cudaFuncSetAttribute(sweep2d_f32x2_kernel<T1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(sweep2d_f32x2_kernel<T1, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    sweep2d_f32x2_kernel<T1><<<grid, NW * 32, smem, st>>>(a);
+    sweep2d_f32x2_kernel<T1, XS><<<grid, NW * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_sweep2d_f32x2(const SweepArgs2D<float>& a, int T1, int grid, int NW, cudaStream_t st) {
-    if (T1 == 8) return launch_f32x2_t<8>(a, grid, NW, st);
-    if (T1 == 4) return launch_f32x2_t<4>(a, grid, NW, st);
+// xs: x1 subdomains (tile tables and lagged x1 halos)
+cudaError_t launch_sweep2d_f32x2(const SweepArgs2D<float>& a, int T1, int xs, int grid, int NW, cudaStream_t st) {
+    if (T1 == 8) return xs ? launch_f32x2_t<8, true>(a, grid, NW, st) : launch_f32x2_t<8, false>(a, grid, NW, st);
+    if (T1 == 4) return xs ? launch_f32x2_t<4, true>(a, grid, NW, st) : launch_f32x2_t<4, false>(a, grid, NW, st);
     return cudaErrorInvalidValue;
 }
 
-template <int T1>
+template <int T1, bool XS>
 static cudaError_t occupancy_f32x2_t(int NW, int max_rows, int* blocks_per_sm) {
     const size_t smem = sweep2d_f32x2_smem(T1, NW, max_rows);
-    cudaError_t e = cudaFuncSetAttribute(sweep2d_f32x2_kernel<T1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(sweep2d_f32x2_kernel<T1, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep2d_f32x2_kernel<T1>, NW * 32, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep2d_f32x2_kernel<T1, XS>, NW * 32, smem);
 }
 
-cudaError_t sweep2d_f32x2_occupancy(int T1, int NW, int max_rows, int* blocks_per_sm) {
-    if (T1 == 8) return occupancy_f32x2_t<8>(NW, max_rows, blocks_per_sm);
-    if (T1 == 4) return occupancy_f32x2_t<4>(NW, max_rows, blocks_per_sm);
+cudaError_t sweep2d_f32x2_occupancy(int T1, int xs, int NW, int max_rows, int* blocks_per_sm) {
+    if (T1 == 8) return xs ? occupancy_f32x2_t<8, true>(NW, max_rows, blocks_per_sm) : occupancy_f32x2_t<8, false>(NW, max_rows, blocks_per_sm);
+    if (T1 == 4) return xs ? occupancy_f32x2_t<4, true>(NW, max_rows, blocks_per_sm) : occupancy_f32x2_t<4, false>(NW, max_rows, blocks_per_sm);
     return cudaErrorInvalidValue;
 }
 

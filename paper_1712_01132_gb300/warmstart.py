@@ -337,7 +337,7 @@ def solve_to(mask, kn, v, w, tol, max_iter, initial=None, **options):
 
 
 def run_pipeline(train=48, side=64, eval_side=128, eval_seeds=(10000, 10001), eval_kns=(0.05, 0.5),
-                 levels=4, base=16, steps=1500, lr=2e-3, nv=16, fp64_cap=0, seed=0, log=print):
+                 levels=4, base=16, steps=1500, lr=2e-3, nv=16, fp64_cap=0, seed=0, log=print, constant_lr=False):
     """The learned-warm-start experiment: solver runs on `train` seeded side^3 Gaussian-field rocks
     (correlation length 8, porosity 0.35, Kn log-uniform in [0.05, 5], nv^3 velocities, FP32,
     Err < 1e-6) give the training set; the network is trained with Adam; held-out eval_side^3 rocks
@@ -372,7 +372,7 @@ def run_pipeline(train=48, side=64, eval_side=128, eval_seeds=(10000, 10001), ev
         y = net.forward(x)
         loss, dy = net.loss_and_grad(y, t, m)
         net.backward(dy)
-        net.step(lr=lr * 0.5 * (1.0 + math.cos(math.pi * step / steps)))
+        net.step(lr=lr if constant_lr else lr * 0.5 * (1.0 + math.cos(math.pi * step / steps)))
         losses.append(loss)
         if step % 200 == 0:
             log("step %d loss %.4e" % (step, loss))
@@ -432,10 +432,11 @@ def main():
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--nv", type=int, default=16)
     ap.add_argument("--fp64-cap", type=int, default=0)
+    ap.add_argument("--constant-lr", action="store_true")
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
     res = run_pipeline(a.train, a.side, a.eval_side, tuple(a.eval_seeds), tuple(a.eval_kns), a.levels, a.base,
-                       a.steps, a.lr, a.nv, a.fp64_cap)
+                       a.steps, a.lr, a.nv, a.fp64_cap, constant_lr=a.constant_lr)
     text = json.dumps(res, indent=1)
     if a.out:
         with open(a.out, "w") as f:
