@@ -99,6 +99,12 @@ typedef struct {
      * (the exact serial iteration, the default).  Implemented: c1 and c2 in 2D, each block at least
      * two points wide; c3 and 3D cuts are rejected with DVM_EINVAL. */
     int subdomains[3];
+    /* Nonzero (2D FP32 without subdomains, at most 512 velocities per quadrant): every CTA of the
+     * sweep takes two consecutive bands, the upper one sweeping one tile behind the lower, and the
+     * lower band's top edge reaches the upper band through shared memory instead of HBM and a
+     * progress flag.  No counterpart in the paper; the same arithmetic in the same order, so the
+     * same result bits.  0 (default): one band per CTA.  Other configurations: DVM_EINVAL. */
+    int band_pairs;
 } dvm_options;
 
 /* Fill *opt with the defaults: FP64, second order, specular lateral faces, check interval 100,

@@ -34,6 +34,8 @@ cudaError_t launch_warm2d(const Prob2D<T>*, int NL, int par, const double* qw2, 
 cudaError_t launch_sweep2d_f32x2(const SweepArgs2D<float>&, int T1, int xs, int grid, int NW, cudaStream_t);
 cudaError_t sweep2d_f32x2_occupancy(int T1, int xs, int NW, int max_rows, int* blocks_per_sm);
 int sweep2d_f32x2_max_rows(int T1, int NW);
+cudaError_t launch_sweep2d_pair(const SweepArgs2D<float>&, int T1, int grid, int NW, cudaStream_t);
+cudaError_t sweep2d_pair_occupancy(int T1, int NW, int max_rows, int NL, int* blocks_per_sm);
 int sweep2d_f32x2_velocities_per_lane();
 template <typename T> size_t sweep3d_smem(int T1, int NW, int R2, int R3);
 size_t sweep3d_f32x2_smem(int T1, int NW, int R2, int R3);
@@ -81,6 +83,7 @@ struct dvm_ctx {
     int prec = DVM_FP64;             // arithmetic precision (BF16 storage computes in FP32)
     bool bf16 = false;               // 3D ghosts and pencil edges stored as BF16
     bool xsub = false;               // 2D x1 subdomains (tile tables, lagged x1 halos)
+    bool pairs = false;              // 2D FP32: two consecutive bands per CTA
     int T1 = 8, rows = 8, max_rows = 8;
     std::vector<HostProb> hp;
     std::vector<Buf> bufs;
@@ -247,6 +250,7 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     c->NL = 32 * vpl * c->NW;
     const int NL = c->NL;
     if (c->NW > 16) return fail(c, DVM_EINVAL, "too many velocities per quadrant");
+    if (c->pairs && 2 * c->NW > 8) return fail(c, DVM_EINVAL, "band pairs need at most 512 velocities per quadrant");
     // ---- tiles
     c->T1 = c->opt.tile_x1 ? c->opt.tile_x1 : 8;
     if (c->prec == DVM_FP32) {               // the packed FP32 kernel has 4- and 8-column tiles
@@ -485,10 +489,12 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     // ---- work items in band order (a band only waits for lower bands: deadlock-free tickets)
     int maxb = 0;
     for (int b = 0; b < c->nprob; ++b) maxb = std::max(maxb, probs[b].nbands);
-    for (int band = 0; band < maxb; ++band)
+    // (with band pairs an item is the pair of bands 2 band, 2 band + 1)
+    const int step = c->pairs ? 2 : 1;
+    for (int band = 0; band * step < maxb; ++band)
         for (int b = 0; b < c->nprob; ++b)
             for (int q = 0; q < NQ; ++q)
-                if (band < c->hp[b].qbands[q]) items.push_back({b, q, band, 0});
+                if (band * step < c->hp[b].qbands[q]) items.push_back({b, q, band, 0});
     c->nitems = (int)items.size();
     c->counters_bytes = sizeof(int) * (size_t)(1 + prog_total);
     c->counters_dev = (int*)dev_alloc(c, c->counters_bytes);
@@ -521,7 +527,8 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     c->probs_host.assign((const char*)probs.data(), (const char*)probs.data() + probs.size() * sizeof(Prob2D<T>));
     // ---- persistent grid size
     int per_sm = 0;
-    if (c->prec == DVM_FP32) e = sweep2d_f32x2_occupancy(c->T1, c->xsub, c->NW, c->max_rows, &per_sm);
+    if (c->pairs) e = sweep2d_pair_occupancy(c->T1, 2 * c->NW, c->max_rows, c->NL, &per_sm);
+    else if (c->prec == DVM_FP32) e = sweep2d_f32x2_occupancy(c->T1, c->xsub, c->NW, c->max_rows, &per_sm);
     else e = sweep2d_occupancy<T>(c->T1, c->xsub, c->NW, c->max_rows, &per_sm);
     if (e != cudaSuccess) return cuda_fail(c, e, "occupancy");
     if (per_sm < 1) return fail(c, DVM_EINVAL, "sweep kernel does not fit on an SM with these tiles");
@@ -836,6 +843,7 @@ cudaError_t mark(dvm_ctx* c) {
 }
 
 cudaError_t sweep_launch(const SweepArgs2D<float>& a, dvm_ctx* c) {
+    if (c->pairs) return launch_sweep2d_pair(a, c->T1, c->sweep_grid, 2 * c->NW, c->stream);
     return launch_sweep2d_f32x2(a, c->T1, c->xsub, c->sweep_grid, c->NW, c->stream);
 }
 
@@ -1174,6 +1182,10 @@ dvm_status dvm_create_batch(int nprob, const dvm_geometry* geoms, const double* 
     if (c->opt.subdomains[2] > 1 || (dims == 3 && (c->opt.subdomains[0] > 1 || c->opt.subdomains[1] > 1)))
         return reject(DVM_EINVAL, "lagged-halo subdomains are implemented along x1 and x2 of 2D problems only");
     c->xsub = dims == 2 && c->opt.subdomains[0] > 1;
+    if (c->opt.band_pairs && (dims != 2 || c->opt.precision != DVM_FP32 || c->opt.subdomains[0] > 1 ||
+                              c->opt.subdomains[1] > 1))
+        return reject(DVM_EINVAL, "band pairs are implemented for 2D FP32 problems without subdomains");
+    c->pairs = c->opt.band_pairs != 0;
     c->dims = dims;
     c->nprob = nprob;
     c->prec = c->opt.precision == DVM_BF16_STORE ? DVM_FP32 : c->opt.precision;

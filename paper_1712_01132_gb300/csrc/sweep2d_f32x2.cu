@@ -351,10 +351,7 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
             if (cout_slot >= 0) carry_out(cout_slot);
             if (t + 1 < ntiles) store_rec(buf ^ 1, nxt);
             __syncthreads();
-            if (threadIdx.x == 0 && it != a.withhold_item) {
-                __threadfence();
-                st_release_gpu(P->prog + q * nb + band, t + 1);
-            }
+            if (threadIdx.x == 0 && it != a.withhold_item) publish_gpu(P->prog + q * nb + band, t + 1);
             // moment partials of this quadrant: sum of the warps' lane sums, in warp order
             for (int idx = threadIdx.x; idx < nrows * width * 3; idx += blockDim.x) {
                 const int m = idx % 3;

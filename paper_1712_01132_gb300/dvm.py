@@ -45,6 +45,7 @@ class dvm_options(ctypes.Structure):
         ("alloc_user", ctypes.c_void_p),
         ("use_graph", ctypes.c_int),
         ("subdomains", ctypes.c_int * 3),
+        ("band_pairs", ctypes.c_int),
     ]
 
 
@@ -200,7 +201,8 @@ class _TorchAllocator:
 
 
 def make_options(precision="fp64", stencil_order=2, lateral="specular", check_interval=100, stream=None,
-                 tile_x1=0, band_rows=0, torch_memory=True, use_graph=False, subdomains=(1, 1, 1)):
+                 tile_x1=0, band_rows=0, torch_memory=True, use_graph=False, subdomains=(1, 1, 1),
+                 band_pairs=False):
     """dvm_options with torch's current stream (unless stream is given) and, by default, torch's
     caching allocator for device memory.  Returns (options, keepalive)."""
     o = dvm_default_options()
@@ -211,6 +213,7 @@ def make_options(precision="fp64", stencil_order=2, lateral="specular", check_in
     o.tile_x1 = int(tile_x1)
     o.band_rows = int(band_rows)
     o.use_graph = 1 if use_graph else 0
+    o.band_pairs = 1 if band_pairs else 0
     for j in range(3):
         o.subdomains[j] = int(subdomains[j])
     keep = []
