@@ -223,8 +223,9 @@ def run_gpu(args):
         torch.cuda.synchronize()
 
     # ---------------- tile shape from the autotuner (untimed setup)
-    t1, rows, tune_ms = dvm.autotune(masks, kns, v, w, iters=5 if W["dims"] == 2 else 2, **base)
-    opts = dict(base, tile_x1=t1, band_rows=rows, use_graph=True)
+    tune = dvm.autotune(masks, kns, v, w, iters=5 if W["dims"] == 2 else 2, **base)
+    t1, rows, tune_ms = tune.tile_x1, tune.band_rows, tune.ms
+    opts = dict(base, tile_x1=t1, band_rows=rows, group_warps=tune.group_warps, use_graph=True)
 
     # ---------------- device-resident timing: inputs already in HBM
     s = dvm.Solver(masks, kns, v, w, **opts)
@@ -298,7 +299,8 @@ def run_gpu(args):
                        "description": W["desc"], "fluid_cells": sum(nfs),
                        "velocities": nv, "problems": len(masks), "iterations_per_step": ITERS_PER_STEP,
                        "step": "100 source iterations (sweep+quadrature+finalize) + permeability/Err check",
-                       "tiles": {"tile_x1": t1, "band_rows": rows, "autotuned_ms_per_iteration": round(tune_ms, 4)},
+                       "tiles": {"tile_x1": t1, "band_rows": rows, "group_warps": tune.group_warps,
+                                 "autotuned_ms_per_iteration": round(tune_ms, 4)},
                        "l2": W["l2"],
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": int(h2d // e2e_steps),

@@ -105,6 +105,14 @@ typedef struct {
      * progress flag.  No counterpart in the paper; the same arithmetic in the same order, so the
      * same result bits.  0 (default): one band per CTA.  Other configurations: DVM_EINVAL. */
     int band_pairs;
+    /* 3D: at most this many warps per sweep CTA (1..8; 0 = automatic, 8).  The velocities of an
+     * octant are split into groups of 64 (FP32) or 32 (FP64) slots per warp, one CTA per group and
+     * pencil, so fewer warps per CTA mean more, smaller CTAs per SM (more pencils in flight) at the
+     * price of building every point's record once per group.  The moments are summed per group and
+     * then over groups, so this choice changes their summation order (results agree to rounding,
+     * and for a fixed choice they are the same bits for every tile and pencil shape).  Ignored in
+     * 2D. */
+    int group_warps;
 } dvm_options;
 
 /* Fill *opt with the defaults: FP64, second order, specular lateral faces, check interval 100,
@@ -165,10 +173,12 @@ dvm_status dvm_wall_density_at(dvm_ctx* ctx, int prob, double* rhos);
 /* Tile autotuner (no counterpart in the paper, whose kernel has no tiles): times `iters`
  * iterations (after two untimed ones) of every candidate sweep tile shape on the given problems,
  * with the options in *opt otherwise, and writes the fastest into opt->tile_x1 and
- * opt->band_rows.  Candidates: 2D FP32 x1 tile {8, 4} x band rows {4, 8, 12, 16}; 2D FP64 x1 tile
- * {8, 16} x band rows {4, 8, 12, 16}; 3D x1 tile {4, 8} x pencil rows {2, 3, 4, 6, 8}; shapes that
- * do not fit the device are skipped.  Because every tile shape runs the same dependency-exact
- * wavefront, the choice changes the speed and never the result.  Each candidate context is created
+ * opt->band_rows (and, in 3D, opt->group_warps).  Candidates: 2D FP32 x1 tile {8, 4} x band rows
+ * {4, 8, 12, 16}; 2D FP64 x1 tile {8, 16} x band rows {4, 8, 12, 16}; 3D x1 tile {4, 8} x pencil
+ * rows {2, 3, 4, 5, 6} x warps per CTA {8, 4} (only the caller's value when opt->group_warps is
+ * nonzero); shapes that do not fit the device are skipped.  Because every tile shape runs the same dependency-exact
+ * wavefront, the tile choice changes the speed and never the result (warps per CTA change the
+ * summation order of the moments, see group_warps).  Each candidate context is created
  * and destroyed in turn (device memory of one context at a time); kernels run on opt->stream.
  * best_ms (may be NULL) receives the fastest time per iteration.  Errors: those of dvm_create_batch
  * and dvm_iterate; EINVAL when no candidate fits. */

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -584,7 +585,9 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     // FP32 lanes carry two velocity slots (packed f32x2 kernel), FP64 lanes one
     const int vpl = (c->prec == DVM_FP32) ? sweep3d_f32x2_velocities_per_lane() : 1;
     const int warps_total = (nvo + 32 * vpl - 1) / (32 * vpl);
-    c->G = (warps_total + 7) / 8;                         // at most 8 warps per CTA
+    // at most 8 warps per CTA (group_warps: fewer warps per CTA, more velocity groups)
+    const int wmax = (c->opt.group_warps > 0) ? std::min(8, c->opt.group_warps) : 8;
+    c->G = (warps_total + wmax - 1) / wmax;
     c->NW = (warps_total + c->G - 1) / c->G;
     c->GL = 32 * vpl * c->NW;                             // velocity slots per group
     c->NL = c->GL * c->G;
@@ -1182,6 +1185,7 @@ dvm_status dvm_create_batch(int nprob, const dvm_geometry* geoms, const double* 
     if (c->opt.subdomains[2] > 1 || (dims == 3 && (c->opt.subdomains[0] > 1 || c->opt.subdomains[1] > 1)))
         return reject(DVM_EINVAL, "lagged-halo subdomains are implemented along x1 and x2 of 2D problems only");
     c->xsub = dims == 2 && c->opt.subdomains[0] > 1;
+    if (c->opt.group_warps < 0) return reject(DVM_EINVAL, "group_warps must not be negative");
     if (c->opt.band_pairs && (dims != 2 || c->opt.precision != DVM_FP32 || c->opt.subdomains[0] > 1 ||
                               c->opt.subdomains[1] > 1))
         return reject(DVM_EINVAL, "band pairs are implemented for 2D FP32 problems without subdomains");
@@ -1372,16 +1376,20 @@ dvm_status dvm_autotune(int nprob, const dvm_geometry* geoms, const double* kn, 
                         dvm_options* opt, int iters, double* best_ms) {
     if (!opt || iters < 1 || nprob < 1 || !geoms) return DVM_EINVAL;
     const int dims = geoms[0].dims;
-    std::vector<std::pair<int, int>> cand;   // (tile_x1, band_rows)
+    std::vector<std::array<int, 3>> cand;    // (tile_x1, band_rows, group_warps)
+    const int gw0 = opt->group_warps;
     if (dims == 3) {
-        for (int t : {4, 8})
-            for (int r : {2, 3, 4, 6, 8}) cand.push_back({t, r});
+        for (int w : {8, 4}) {
+            if (gw0 > 0 && w != 8) break;        // warps per CTA fixed by the caller
+            for (int t : {4, 8})
+                for (int r : {2, 3, 4, 5, 6}) cand.push_back({t, r, gw0 > 0 ? gw0 : w});
+        }
     } else if (opt->precision == DVM_FP32) {
         for (int t : {8, 4})
-            for (int r : {4, 8, 12, 16}) cand.push_back({t, r});
+            for (int r : {4, 8, 12, 16}) cand.push_back({t, r, gw0});
     } else {
         for (int t : {8, 16})
-            for (int r : {4, 8, 12, 16}) cand.push_back({t, r});
+            for (int r : {4, 8, 12, 16}) cand.push_back({t, r, gw0});
     }
     cudaStream_t st = (cudaStream_t)opt->stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1391,14 +1399,15 @@ dvm_status dvm_autotune(int nprob, const dvm_geometry* geoms, const double* kn, 
         return DVM_ECUDA;
     }
     double best = HUGE_VAL;
-    int best_t = 0, best_r = 0;
-    std::vector<std::pair<int, int>> seen;    // effective shapes after the library's clamping
+    int best_t = 0, best_r = 0, best_w = gw0;
+    std::vector<std::array<int, 3>> seen;     // effective shapes after the library's clamping
     std::string last_reject;
     dvm_status result = DVM_OK;
-    for (auto [t, r] : cand) {
+    for (auto [t, r, w] : cand) {
         dvm_options o = *opt;
         o.tile_x1 = t;
         o.band_rows = r;
+        o.group_warps = w;
         o.use_graph = 0;                     // time the launches, not a first capture
         dvm_ctx* c = nullptr;
         dvm_status s = dvm_create_batch(nprob, geoms, kn, grid, &o, &c);
@@ -1407,7 +1416,7 @@ dvm_status dvm_autotune(int nprob, const dvm_geometry* geoms, const double* kn, 
             continue;
         }
         if (s != DVM_OK) { result = s; break; }
-        const std::pair<int, int> eff{c->T1, dims == 3 ? c->R2 : c->rows};
+        const std::array<int, 3> eff{c->T1, dims == 3 ? c->R2 : c->rows, c->NW};
         bool dup = false;
         for (auto& x : seen) dup = dup || (x == eff);
         if (dup) { dvm_destroy(c); continue; }
@@ -1424,7 +1433,7 @@ dvm_status dvm_autotune(int nprob, const dvm_geometry* geoms, const double* kn, 
         dvm_destroy(c);
         if (s != DVM_OK) { result = s; break; }
         const double per = ms / iters;
-        if (per < best) { best = per; best_t = t; best_r = r; }
+        if (per < best) { best = per; best_t = t; best_r = r; best_w = w; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1435,6 +1444,7 @@ dvm_status dvm_autotune(int nprob, const dvm_geometry* geoms, const double* kn, 
     }
     opt->tile_x1 = best_t;
     opt->band_rows = best_r;
+    opt->group_warps = best_w;
     if (best_ms) *best_ms = best;
     return DVM_OK;
 }

@@ -18,11 +18,11 @@ __device__ __forceinline__ void st_release_gpu(int* p, int v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Publish a progress value after a __syncthreads() of the writing CTA: an acq_rel fence at GPU
-// scope (cumulative over the CTA's writes ordered before it by the barrier) followed by a
-// relaxed store, i.e. the PTX release pattern.
+// Publish a progress value after a __syncthreads() of the writing CTA: a release store at GPU
+// scope, cumulative over the CTA's writes that the barrier ordered before it.  (Measured slightly
+// faster than an acq_rel fence followed by a relaxed store, the other PTX release pattern.)
 __device__ __forceinline__ void publish_gpu(int* p, int v) {
-    asm volatile("fence.acq_rel.gpu;\n\tst.relaxed.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {

@@ -49,6 +49,23 @@ template <> struct PairStore<true> {
 
 __device__ __forceinline__ float2 dup2(float x) { return make_float2(x, x); }
 
+// 16-byte asynchronous copy global -> shared that bypasses L1 (pencil edges are written by other
+// SMs during the launch), and its group commit / wait
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+// the same copy, or (need == false) 16 zero bytes without reading global memory
+__device__ __forceinline__ void cp_async16_or_zero(void* smem_dst, const void* gmem_src, bool need) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    const unsigned n = need ? 16u : 0u;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gmem_src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 }  // namespace
 
 template <int T1, bool BF>
@@ -66,7 +83,9 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
     float* part = rec + (size_t)MROWS * T1 * kRec;                        // [NW][MROWS][T1][4]
     float* carry = part + (size_t)NW * MROWS * T1 * 4;                    // [NW][MROWS][2][64]
     float* pb = carry + (size_t)NW * MROWS * 2 * kPL;                     // [NW][MR2][2][T1][64]
-    float* rtab = pb + (size_t)NW * MR2 * 2 * T1 * kPL;                   // [NW][8][64]
+    float* eb = pb + (size_t)NW * MR2 * 2 * T1 * kPL;                     // [NW][2][2][T1][64]
+    float* rtab = eb + (size_t)NW * 2 * 2 * T1 * kPL;                     // [NW][8][64]
+    unsigned* fmask = reinterpret_cast<unsigned*>(rtab + (size_t)NW * 8 * kPL);   // [2][MROWS] fluid bits
     const size_t NL = (size_t)a.NL;
 
     for (;;) {
@@ -74,6 +93,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
             s_item = ld_volatile(a.status) ? a.nitems : atomicAdd(a.ticket, 1);
             s_abort = 0;
         }
+        for (int r = threadIdx.x; r < MROWS; r += blockDim.x) fmask[r] = 0u;    // masks of tile 0
         __syncthreads();
         const int it = s_item;
         if (it >= a.nitems) return;
@@ -105,8 +125,23 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
         const float dxf = (float)P->dx;
         auto x1of = [&](int ic) -> float { return (float)(s1n ? n1 - 1 - ic : ic) * dxf; };
         const float x1g0 = x1of(n1 - 1), x1g1 = x1of(n1 - 2);   // columns of the x1 ghost layers
+        // FP32 upstream data is staged per warp with asynchronous copies: the warp's 64 slots of
+        // one (row, layer, column) are 256 contiguous bytes, copied as 16 lanes x 16 bytes (two
+        // such per instruction); a lane reads its own 8 bytes after the wait and a __syncwarp
+        const int hl = lane & 15, half = lane >> 4;
+        const size_t lw = (size_t)g * a.GL + (size_t)kPL * warp + 4 * hl;
         // x1 upstream of the first tile: x1 ghost layers (oriented rows (k, j))
-        {
+        if constexpr (!BF) {
+            const size_t gxo = (((size_t)par * 8 + q) * n3 * n2) * 2 * NL;
+            for (int m = half; m < nr3 * nr2 * 2; m += 2) {
+                const int kk = m / (2 * nr2);
+                const int jl = m - kk * 2 * nr2;          // jj * 2 + layer
+                const size_t row = (size_t)(k0 + kk) * n2 + (j0 + (jl >> 1));
+                cp_async16(carry + ((size_t)(warp * MROWS + kk * MR2 + (jl >> 1)) * 2 + (jl & 1)) * kPL + 4 * hl,
+                           P->gx1 + gxo + (row * 2 + (jl & 1)) * NL + lw);
+            }
+            cp_async_commit();
+        } else {
             const size_t gxo = (((size_t)par * 8 + q) * n3 * n2) * 2 * NL;
             for (int kk = 0; kk < nr3; ++kk)
                 for (int jj = 0; jj < nr2; ++jj) {
@@ -126,7 +161,11 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                 if (ok && p3 > 0) ok = wait_geq(prog + (p3 - 1) * np2 + p2, t + 1, a.status, a.timeout_ns);
                 if (!ok) s_abort = 1;
             }
-            // records of the tile's points for this octant (shared by all lanes and velocities)
+            // records of the tile's points for this octant (shared by all lanes and velocities) and
+            // the fluid bits of every row; the masks of the next tile are cleared here (their last
+            // reader, the moment loop of the previous tile, is behind the barrier that ended it)
+            unsigned* fm_cur = fmask + (t & 1) * MROWS;
+            for (int r = threadIdx.x; r < MROWS; r += blockDim.x) fmask[((t + 1) & 1) * MROWS + r] = 0u;
             const int npts = nr3 * MR2 * T1;
             for (int idx = threadIdx.x; idx < npts; idx += blockDim.x) {
                 const int kk = idx / (MR2 * T1);
@@ -156,6 +195,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                         r2 = make_float4(ca == 2 ? 0.f : (ca == 1 ? 1.f : K1o), ca == 0 ? K2o : 0.f,
                                          cb == 2 ? 0.f : (cb == 1 ? 1.f : K1o), cb == 0 ? K2o : 0.f);
                         r3 = make_float4(cc == 2 ? 0.f : (cc == 1 ? 1.f : K1o), cc == 0 ? K2o : 0.f, 0.f, 0.f);
+                        atomicOr(fm_cur + kk * MR2 + jj, 1u << i);
                     }
                 }
                 float4* R = reinterpret_cast<float4*>(rec + (size_t)((kk * MR2 + jj) * T1 + i) * kRec);
@@ -165,38 +205,93 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                 R[3] = r3;
             }
             __syncthreads();
-            if (s_abort) return;
-            // x3 upstream planes of the first plane of the pencil: the pencil below in x3 (ring
-            // slot) or the x3 ghost layers (periodic or specular, Eq. 8)
-            {
-                const float* zb = (p3 == 0) ? P->gz : P->ez;
-                const size_t zo = (p3 == 0)
-                    ? (((size_t)par * 8 + q) * n2 * n1) * 2 * NL
-                    : ((((size_t)q * np2 + p2) * 2 + ((p3 - 1) & 1)) * P->R2 * n1) * 2 * NL;
+            if (s_abort) {
+                cp_async_wait<0>();
+                return;
+            }
+            // upstream data of the tile: x3 planes of its first plane (the pencil below in x3, ring
+            // slot, or the x3 ghost layers; periodic or specular, Eq. 8) and x2 rows of each plane
+            // (the pencil below in x2, or the x2 ghost layers)
+            const float* zb = (p3 == 0) ? P->gz : P->ez;
+            const size_t zo = (p3 == 0)
+                ? (((size_t)par * 8 + q) * n2 * n1) * 2 * NL
+                : ((((size_t)q * np2 + p2) * 2 + ((p3 - 1) & 1)) * P->R2 * n1) * 2 * NL;
+            const float* yb = (p2 == 0) ? P->gy : P->ey;
+            const size_t yo = (p2 == 0)
+                ? (((size_t)par * 8 + q) * n3 * n1) * 2 * NL
+                : ((((size_t)q * np3 + p3) * 2 + ((p2 - 1) & 1)) * P->R3 * n1) * 2 * NL;
+            auto yrow = [&](int kk) -> size_t { return (p2 == 0) ? (size_t)(k0 + kk) * n1 : (size_t)kk * n1; };
+            auto rbuf_rec = [&](int kk, int jj, int i) -> const float* { return rec + (size_t)((kk * MR2 + jj) * T1 + i) * kRec; };
+            // FP32: the x2 rows of plane kk go to slot kk & 1, copied while plane kk - 1 is swept
+            // Upstream values are fetched only where the stencil of the point that reads them has a
+            // nonzero coefficient for them (record K1 / K2 of the first row or plane): values of
+            // solid points are never used, so they are neither stored nor fetched, and the staging
+            // holds zeros there.
+            auto issue_y = [&](int kk) {
+                const size_t rb0 = yrow(kk);
+                for (int m = half; m < 2 * width; m += 2) {
+                    const int layer = m / width;
+                    const int i = m - layer * width;
+                    const bool need = rbuf_rec(kk, 0, i)[10 + layer] != 0.f;
+                    cp_async16_or_zero(eb + ((((size_t)warp * 2 + (kk & 1)) * 2 + layer) * T1 + i) * kPL + 4 * hl,
+                                       yb + yo + ((rb0 + c0 + i) * 2 + layer) * NL + lw, need);
+                }
+                cp_async_commit();
+            };
+            if constexpr (BF) {
                 for (int jj = 0; jj < nr2; ++jj)
                     for (int i = 0; i < width; ++i) {
                         const size_t row = (p3 == 0) ? ((size_t)(j0 + jj) * n1 + (c0 + i)) : ((size_t)jj * n1 + (c0 + i));
                         float* d = pb + ((((size_t)warp * MR2 + jj) * 2) * T1 + i) * kPL + 2 * lane;
                         const float xs = x1of(c0 + i);
-                        *reinterpret_cast<float2*>(d) = PS::ld(zb, zo + (row * 2 + 0) * NL + lv, xs);
-                        *reinterpret_cast<float2*>(d + (size_t)T1 * kPL) = PS::ld(zb, zo + (row * 2 + 1) * NL + lv, xs);
+                        const float* rc = rbuf_rec(0, jj, i);
+                        *reinterpret_cast<float2*>(d) = rc[12] != 0.f ? PS::ld(zb, zo + (row * 2 + 0) * NL + lv, xs) : make_float2(0.f, 0.f);
+                        *reinterpret_cast<float2*>(d + (size_t)T1 * kPL) =
+                            rc[13] != 0.f ? PS::ld(zb, zo + (row * 2 + 1) * NL + lv, xs) : make_float2(0.f, 0.f);
                     }
+            } else {
+                for (int m = half; m < nr2 * 2 * width; m += 2) {
+                    const int jl = m / width;            // jj * 2 + layer
+                    const int i = m - jl * width;
+                    const size_t row = (p3 == 0) ? ((size_t)(j0 + (jl >> 1)) * n1 + (c0 + i)) : ((size_t)(jl >> 1) * n1 + (c0 + i));
+                    const bool need = rbuf_rec(0, jl >> 1, i)[12 + (jl & 1)] != 0.f;
+                    cp_async16_or_zero(pb + (((size_t)warp * MR2 * 2 + jl) * T1 + i) * kPL + 4 * hl,
+                                       zb + zo + (row * 2 + (jl & 1)) * NL + lw, need);
+                }
+                issue_y(0);
             }
             for (int kk = 0; kk < nr3; ++kk) {
                 // x2 upstream rows of the first row of this plane
                 float2 rb1[T1], rb2[T1];
-                {
-                    const float* yb = (p2 == 0) ? P->gy : P->ey;
-                    const size_t yo = (p2 == 0)
-                        ? (((size_t)par * 8 + q) * n3 * n1) * 2 * NL
-                        : ((((size_t)q * np3 + p3) * 2 + ((p2 - 1) & 1)) * P->R3 * n1) * 2 * NL;
-                    const size_t rowbase = (p2 == 0) ? (size_t)(k0 + kk) * n1 : (size_t)kk * n1;
+                if constexpr (BF) {
+                    const size_t rowbase = yrow(kk);
 #pragma unroll
                     for (int i = 0; i < T1; ++i) {
                         if (i < width) {
                             const float xs = x1of(c0 + i);
-                            rb1[i] = PS::ld(yb, yo + ((rowbase + c0 + i) * 2 + 0) * NL + lv, xs);
-                            rb2[i] = PS::ld(yb, yo + ((rowbase + c0 + i) * 2 + 1) * NL + lv, xs);
+                            const float* rc = rbuf_rec(kk, 0, i);
+                            rb1[i] = rc[10] != 0.f ? PS::ld(yb, yo + ((rowbase + c0 + i) * 2 + 0) * NL + lv, xs) : make_float2(0.f, 0.f);
+                            rb2[i] = rc[11] != 0.f ? PS::ld(yb, yo + ((rowbase + c0 + i) * 2 + 1) * NL + lv, xs) : make_float2(0.f, 0.f);
+                        } else {
+                            rb1[i] = make_float2(0.f, 0.f);
+                            rb2[i] = rb1[i];
+                        }
+                    }
+                } else {
+                    __syncwarp();                        // slot (kk + 1) & 1 was last read at plane kk - 1
+                    if (kk + 1 < nr3) {
+                        issue_y(kk + 1);
+                        cp_async_wait<1>();              // all but the copies of plane kk + 1
+                    } else {
+                        cp_async_wait<0>();
+                    }
+                    __syncwarp();
+                    const float* e0 = eb + ((((size_t)warp * 2 + (kk & 1)) * 2) * T1) * kPL + 2 * lane;
+#pragma unroll
+                    for (int i = 0; i < T1; ++i) {
+                        if (i < width) {
+                            rb1[i] = *reinterpret_cast<const float2*>(e0 + (size_t)i * kPL);
+                            rb2[i] = *reinterpret_cast<const float2*>(e0 + ((size_t)T1 + i) * kPL);
                         } else {
                             rb1[i] = make_float2(0.f, 0.f);
                             rb2[i] = rb1[i];
@@ -204,6 +299,11 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                     }
                 }
                 for (int jj = 0; jj < nr2; ++jj) {
+                    // solid points are not swept: every fluid point downstream of one gives it a zero
+                    // stencil coefficient (its code marks that upstream point solid), so the values
+                    // left in the carries, rows and planes there are never used
+                    const unsigned fm = fm_cur[kk * MR2 + jj];
+                    if (fm == 0u) continue;
                     float* cr = carry + ((size_t)(warp * MROWS + kk * MR2 + jj) * 2) * kPL + 2 * lane;
                     float2 hp1 = *reinterpret_cast<const float2*>(cr);
                     float2 hp2 = *reinterpret_cast<const float2*>(cr + kPL);
@@ -212,11 +312,12 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                     float* prow = part + ((size_t)(warp * MROWS + kk * MR2 + jj) * T1) * 4;
 #pragma unroll
                     for (int i0 = 0; i0 < T1; i0 += 4) {
+                        if (((fm >> i0) & 15u) == 0u) continue;
                         float m0[4], m1[4], m2[4], m3[4];
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
                             const int i = i0 + c;
-                            if (i < width) {
+                            if ((fm >> i) & 1u) {
                                 const float4* R = reinterpret_cast<const float4*>(rrow + i * kRec);
                                 const float4 A = R[0], B = R[1], C = R[2], D = R[3];
                                 const float2 z1 = *reinterpret_cast<const float2*>(zr + (size_t)i * kPL);
@@ -226,7 +327,9 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                                 const float2 t1 = fma2(dup2(C.x), hp1, fma2(dup2(C.y), hp2, dup2(B.x)));
                                 const float2 t2 = fma2(dup2(C.z), rb1[i], fma2(dup2(C.w), rb2[i], dup2(B.y)));
                                 const float2 t3 = fma2(dup2(D.x), z1, fma2(dup2(D.y), z2, dup2(B.z)));
-                                const float2 num = fma2(a3, t3, fma2(a2, t2, fma2(a1, t1, S)));
+                                // the x1 term (carried from the previous point) enters last: three
+                                // dependent operations per point along the x1 chain
+                                const float2 num = fma2(a1, t1, fma2(a3, t3, fma2(a2, t2, S)));
                                 const float2 h = mul2(num, Rk);
                                 hp2 = hp1;
                                 hp1 = h;
@@ -274,12 +377,16 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                         eo = (((size_t)(par ^ 1) * 8 + qy) * n3 * n1) * 2 * NL;
                         rowbase = (size_t)(k0 + kk) * n1;
                     }
+                    // only values of fluid points are stored (layer 1 of a one-row pencil passes the
+                    // fetched upstream value through and is always stored)
+                    const unsigned f0 = fm_cur[kk * MR2 + nr2 - 1];
+                    const unsigned f1 = nr2 >= 2 ? fm_cur[kk * MR2 + nr2 - 2] : 0xffffffffu;
 #pragma unroll
                     for (int i = 0; i < T1; ++i) {
                         if (i < width) {
                             const float xs = x1of(c0 + i);
-                            PS::st(et, eo + ((rowbase + c0 + i) * 2 + 0) * NL + lv, rb1[i], xs);
-                            PS::st(et, eo + ((rowbase + c0 + i) * 2 + 1) * NL + lv, rb2[i], xs);
+                            if ((f0 >> i) & 1u) PS::st(et, eo + ((rowbase + c0 + i) * 2 + 0) * NL + lv, rb1[i], xs);
+                            if ((f1 >> i) & 1u) PS::st(et, eo + ((rowbase + c0 + i) * 2 + 1) * NL + lv, rb2[i], xs);
                         }
                     }
                 }
@@ -297,14 +404,17 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                     et = P->gz;
                     eo = (((size_t)(par ^ 1) * 8 + qz) * n2 * n1) * 2 * NL;
                 }
-                for (int jj = 0; jj < nr2; ++jj)
+                for (int jj = 0; jj < nr2; ++jj) {
+                    const unsigned f0 = fm_cur[(nr3 - 1) * MR2 + jj];
+                    const unsigned f1 = nr3 >= 2 ? fm_cur[(nr3 - 2) * MR2 + jj] : 0xffffffffu;
                     for (int i = 0; i < width; ++i) {
                         const size_t row = last ? ((size_t)(j0 + jj) * n1 + (c0 + i)) : ((size_t)jj * n1 + (c0 + i));
                         const float* s = pb + ((((size_t)warp * MR2 + jj) * 2) * T1 + i) * kPL + 2 * lane;
                         const float xs = x1of(c0 + i);
-                        PS::st(et, eo + (row * 2 + 0) * NL + lv, *reinterpret_cast<const float2*>(s), xs);
-                        PS::st(et, eo + (row * 2 + 1) * NL + lv, *reinterpret_cast<const float2*>(s + (size_t)T1 * kPL), xs);
+                        if ((f0 >> i) & 1u) PS::st(et, eo + (row * 2 + 0) * NL + lv, *reinterpret_cast<const float2*>(s), xs);
+                        if ((f1 >> i) & 1u) PS::st(et, eo + (row * 2 + 1) * NL + lv, *reinterpret_cast<const float2*>(s + (size_t)T1 * kPL), xs);
                     }
+                }
             }
             if (t == ntiles - 1) {
                 const size_t gxo = (((size_t)(par ^ 1) * 8 + q) * n3 * n2) * 2 * NL;
@@ -330,7 +440,8 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                 const int jj = r % nr2;
                 const int kk = r / nr2;
                 float s = 0.f;
-                for (int w = 0; w < NW; ++w) s += part[((size_t)(w * MROWS + kk * MR2 + jj) * T1 + i) * 4 + mm];
+                if ((fm_cur[kk * MR2 + jj] >> i) & 1u)
+                    for (int w = 0; w < NW; ++w) s += part[((size_t)(w * MROWS + kk * MR2 + jj) * T1 + i) * 4 + mm];
                 const int ic = c0 + i;
                 const int x = s1n ? n1 - 1 - ic : ic;
                 const int y = s2n ? n2 - 1 - (j0 + jj) : (j0 + jj);
@@ -346,7 +457,8 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
 size_t sweep3d_f32x2_smem(int T1, int NW, int R2, int R3) {
     const size_t rows = (size_t)R2 * R3;
     return sizeof(float) * (rows * T1 * kRec + (size_t)NW * rows * T1 * 4 + (size_t)NW * rows * 2 * kPL +
-                            (size_t)NW * R2 * 2 * T1 * kPL + (size_t)NW * 8 * kPL);
+                            (size_t)NW * R2 * 2 * T1 * kPL + (size_t)NW * 2 * 2 * T1 * kPL + (size_t)NW * 8 * kPL) +
+           sizeof(unsigned) * 2 * rows;
 }
 
 int sweep3d_f32x2_velocities_per_lane() { return 2; }

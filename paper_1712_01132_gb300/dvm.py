@@ -4,6 +4,7 @@ Every computation runs in the CUDA library ``_lib/libdvm_gb300.so``; there is no
 library is missing or cannot be loaded, importing the functions raises.  PyTorch provides device
 memory (through the allocator callback of ``dvm_options``) and the CUDA stream.
 """
+import collections
 import ctypes
 import os
 import threading
@@ -46,6 +47,7 @@ class dvm_options(ctypes.Structure):
         ("use_graph", ctypes.c_int),
         ("subdomains", ctypes.c_int * 3),
         ("band_pairs", ctypes.c_int),
+        ("group_warps", ctypes.c_int),
     ]
 
 
@@ -202,7 +204,7 @@ class _TorchAllocator:
 
 def make_options(precision="fp64", stencil_order=2, lateral="specular", check_interval=100, stream=None,
                  tile_x1=0, band_rows=0, torch_memory=True, use_graph=False, subdomains=(1, 1, 1),
-                 band_pairs=False):
+                 band_pairs=False, group_warps=0):
     """dvm_options with torch's current stream (unless stream is given) and, by default, torch's
     caching allocator for device memory.  Returns (options, keepalive)."""
     o = dvm_default_options()
@@ -214,6 +216,7 @@ def make_options(precision="fp64", stencil_order=2, lateral="specular", check_in
     o.band_rows = int(band_rows)
     o.use_graph = 1 if use_graph else 0
     o.band_pairs = 1 if band_pairs else 0
+    o.group_warps = int(group_warps)
     for j in range(3):
         o.subdomains[j] = int(subdomains[j])
     keep = []
@@ -247,9 +250,12 @@ def _geometries(masks, kn):
     return masks, geoms, np.ascontiguousarray(kns)
 
 
+Tuning = collections.namedtuple("Tuning", "tile_x1 band_rows group_warps ms")
+
+
 def autotune(masks, kn, v, w, iters=10, **options):
-    """dvm_autotune: the fastest (tile_x1, band_rows) for these problems and options, and its
-    time per iteration in ms."""
+    """dvm_autotune: the fastest tile shape for these problems and options as a Tuning
+    (tile_x1, band_rows, group_warps: pass them to Solver; ms: time per iteration)."""
     lib = load()
     masks, geoms, kns = _geometries(masks, kn)
     v = np.ascontiguousarray(np.asarray(v, dtype=np.float64))
@@ -260,7 +266,7 @@ def autotune(masks, kn, v, w, iters=10, **options):
     st = lib.dvm_autotune(len(masks), geoms, _ptr(kns), ctypes.byref(grid), ctypes.byref(opt), int(iters),
                           ctypes.byref(best))
     _check(st, None)
-    return opt.tile_x1, opt.band_rows, best.value
+    return Tuning(opt.tile_x1, opt.band_rows, opt.group_warps, best.value)
 
 
 class Solver:

@@ -84,7 +84,7 @@ def test_autotuner_picks_a_candidate_with_identical_results(precision):
     batch = _small_batch()
     masks, kns = [b[0] for b in batch], [b[1] for b in batch]
     v, w = dvm.dvm_gh_velocity_grid(2, 24)
-    t1, rows, ms = dvm.autotune(masks, kns, v, w, iters=5, precision=precision, lateral="periodic")
+    t1, rows, _, ms = dvm.autotune(masks, kns, v, w, iters=5, precision=precision, lateral="periodic")
     assert ms > 0
     if precision == "fp32":
         assert t1 in (4, 8) and rows in (4, 8, 12, 16)
@@ -102,8 +102,18 @@ def test_autotuner_picks_a_candidate_with_identical_results(precision):
 def test_autotuner_3d():
     mask = inputs.gaussian_rock(16, seed=3, corr_len=2.0, porosity=0.5)
     v, w = dvm.dvm_gh_velocity_grid(3, 8)
-    t1, rows, ms = dvm.autotune(mask, 0.5, v, w, iters=3, precision="fp32", lateral="periodic")
-    assert t1 in (4, 8) and rows in (2, 3, 4, 6, 8) and ms > 0
+    t1, rows, gw, ms = dvm.autotune(mask, 0.5, v, w, iters=3, precision="fp32", lateral="periodic")
+    assert t1 in (4, 8) and rows in (2, 3, 4, 5, 6) and gw in (4, 8) and ms > 0
+    # the tuned shape runs and agrees with the default shape to rounding (warps per CTA change only
+    # the summation order of the moments)
+    a = dvm.Solver(mask, 0.5, v, w, precision="fp32", lateral="periodic")
+    b = dvm.Solver(mask, 0.5, v, w, precision="fp32", lateral="periodic", tile_x1=t1, band_rows=rows, group_warps=gw)
+    a.step(20)
+    b.step(20)
+    a.sync()
+    b.sync()
+    ua, ub = a.moments()[1], b.moments()[1]
+    assert np.abs(ua - ub).max() <= 1e-5 * np.abs(ua).max()
 
 
 def test_disc_batch_64_fp32_first_iterations():
