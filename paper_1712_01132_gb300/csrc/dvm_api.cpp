@@ -42,8 +42,8 @@ template <typename T> size_t sweep3d_smem(int T1, int NW, int R2, int R3);
 size_t sweep3d_f32x2_smem(int T1, int NW, int R2, int R3);
 int sweep3d_f32x2_velocities_per_lane();
 cudaError_t launch_sweep3d_f32x2(const SweepArgs3D<float>&, int grid, int NW, cudaStream_t);
-cudaError_t sweep3d_f32x2_occupancy(int T1, int NW, int R2, int R3, int bf16, int* blocks_per_sm);
-template <typename T> cudaError_t sweep3d_occupancy(int T1, int NW, int R2, int R3, int bf16, int* blocks_per_sm);
+cudaError_t sweep3d_f32x2_occupancy(int T1, int NW, int R2, int R3, int bf16, int sub, int* blocks_per_sm);
+template <typename T> cudaError_t sweep3d_occupancy(int T1, int NW, int R2, int R3, int bf16, int sub, int* blocks_per_sm);
 template <typename T> cudaError_t launch_sweep3d(const SweepArgs3D<T>&, int grid, int NW, cudaStream_t);
 template <typename T> cudaError_t launch_finalize3d(const FinArgs3D<T>&, int nblocks, cudaStream_t);
 template <typename T> cudaError_t launch_init3d(const Prob3D<T>*, int NL, const double* qw, cudaStream_t);
@@ -85,6 +85,7 @@ struct dvm_ctx {
     bool bf16 = false;               // 3D ghosts and pencil edges stored as BF16
     bool xsub = false;               // 2D x1 subdomains (tile tables, lagged x1 halos)
     bool pairs = false;              // 2D FP32: two consecutive bands per CTA
+    bool sub3 = false;               // 3D lagged-halo subdomains (pencil and tile tables)
     int T1 = 8, rows = 8, max_rows = 8;
     std::vector<HostProb> hp;
     std::vector<Buf> bufs;
@@ -552,6 +553,32 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
 }
 
 
+// Blocks of the lagged-halo decomposition along one axis of n points (Sec. 3.2: block s holds the
+// points l with floor(l c / n) = s), split into pieces of at most R points, for both orientations
+// (o = 1: the axis is swept from its high end).  Entry {first oriented index, count, below, above}:
+// below = s (ghost slot of block s) for the first piece of oriented block s, else -1 - ring slot;
+// above = (s + 1) mod c for its last piece, else -1 - ring slot; ring slots 2 s + (piece & 1).
+// slot[o][s] = the oriented index that follows the two layers held in ghost slot s.
+static void axis_blocks(int n, int c, int R, std::vector<int4> (&tab)[2], std::vector<int>& slot) {
+    std::vector<int> Y(c + 1);
+    for (int s = 0; s <= c; ++s) Y[s] = (int)(((long long)s * n + c - 1) / c);
+    slot.assign((size_t)2 * c, 0);
+    for (int o = 0; o < 2; ++o) {
+        tab[o].clear();
+        for (int sp = 0; sp < c; ++sp) {
+            const int lo = o ? n - Y[c - sp] : Y[sp];
+            const int hi = o ? n - Y[c - 1 - sp] : Y[sp + 1];
+            slot[(size_t)o * c + sp] = sp == 0 ? n : lo;
+            int jl = 0;
+            for (int r0 = lo; r0 < hi; r0 += R, ++jl) {
+                const int nr = std::min(R, hi - r0);
+                tab[o].push_back(make_int4(r0, nr, r0 == lo ? sp : -1 - (2 * sp + ((jl - 1) & 1)),
+                                           r0 + nr == hi ? (sp + 1) % c : -1 - (2 * sp + (jl & 1))));
+            }
+        }
+    }
+}
+
 template <typename T>
 dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_grid* grid) {
     const int NO = 8;
@@ -677,8 +704,45 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         P.N = H.N;
         P.R2 = std::min(c->R2, P.n2);
         P.R3 = std::min(c->R3, P.n3);
-        P.np2 = (P.n2 + P.R2 - 1) / P.R2;
-        P.np3 = (P.n3 + P.R3 - 1) / P.R3;
+        // pencils along x2 and x3 and tiles along x1, per orientation; with c_j lagged-halo blocks
+        // (Sec. 3.2) no pencil or tile straddles a block boundary
+        P.ns1 = std::max(1, c->opt.subdomains[0]);
+        P.ns2 = std::max(1, c->opt.subdomains[1]);
+        P.ns3 = std::max(1, c->opt.subdomains[2]);
+        std::vector<int4> t1[2], t2[2], t3[2];
+        std::vector<int> sc1, sr2, sr3;
+        axis_blocks(P.n1, P.ns1, c->T1, t1, sc1);
+        axis_blocks(P.n2, P.ns2, P.R2, t2, sr2);
+        axis_blocks(P.n3, P.ns3, P.R3, t3, sr3);
+        for (auto& tab : t1)
+            for (auto& e : tab) {   // tiles: carry-in / carry-out ghost slot or -1
+                e.z = e.z >= 0 ? e.z : -1;
+                e.w = e.w >= 0 ? e.w : -1;
+            }
+        P.nt1 = (int)t1[0].size();
+        P.np2 = (int)t2[0].size();
+        P.np3 = (int)t3[0].size();
+        {
+            std::vector<int4> tabs;
+            for (auto* t : {&t2[0], &t2[1], &t3[0], &t3[1], &t1[0], &t1[1]}) tabs.insert(tabs.end(), t->begin(), t->end());
+            std::vector<int> slots;
+            for (auto* t : {&sr2, &sr3, &sc1}) slots.insert(slots.end(), t->begin(), t->end());
+            int4* tabs_dev = (int4*)dev_alloc(c, tabs.size() * sizeof(int4));
+            int* slots_dev = (int*)dev_alloc(c, slots.size() * sizeof(int));
+            if (!tabs_dev || !slots_dev) return fail(c, DVM_ENOMEM, "device allocation failed");
+            cudaError_t e;
+            if ((e = cudaMemcpyAsync(tabs_dev, tabs.data(), tabs.size() * sizeof(int4), cudaMemcpyHostToDevice, c->stream)) ||
+                (e = cudaMemcpyAsync(slots_dev, slots.data(), slots.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream)) ||
+                (e = cudaStreamSynchronize(c->stream)))
+                return cuda_fail(c, e, "upload pencil tables");
+            c->h2d_bytes += tabs.size() * sizeof(int4) + slots.size() * sizeof(int);
+            P.pen2 = tabs_dev;
+            P.pen3 = tabs_dev + 2 * P.np2;
+            P.tiles1 = tabs_dev + 2 * P.np2 + 2 * P.np3;
+            P.slot_row2 = slots_dev;
+            P.slot_row3 = slots_dev + 2 * P.ns2;
+            P.slot_col1 = slots_dev + 2 * P.ns2 + 2 * P.ns3;
+        }
         P.ngroups = G;
         P.lateral = c->opt.lateral_bc;
         P.order = c->opt.stencil_order;
@@ -694,13 +758,14 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         P.P = (T*)dev_alloc(c, (size_t)NO * G * 4 * N * sizeof(T));
         P.bf16 = c->bf16 ? 1 : 0;
         const size_t es = c->bf16 ? 2 : sizeof(T);     // bytes per stored ghost / edge value
-        P.gx1 = (T*)dev_alloc(c, (size_t)2 * NO * n3 * n2 * 2 * NL * es);
-        P.gy = (T*)dev_alloc(c, (size_t)2 * NO * n3 * n1 * 2 * NL * es);
-        P.gz = (T*)dev_alloc(c, (size_t)2 * NO * n2 * n1 * 2 * NL * es);
-        // pencil edges: two slots per pencil column suffice (pencil p + 2 reaches tile t only after
-        // pencil p + 1 has consumed pencil p's edge of tile t)
-        const size_t ey_sz = (size_t)NO * P.np3 * 2 * P.R3 * n1 * 2 * NL;
-        const size_t ez_sz = (size_t)NO * P.np2 * 2 * P.R2 * n1 * 2 * NL;
+        P.gx1 = (T*)dev_alloc(c, (size_t)2 * NO * P.ns1 * n3 * n2 * 2 * NL * es);
+        P.gy = (T*)dev_alloc(c, (size_t)2 * NO * P.ns2 * n3 * n1 * 2 * NL * es);
+        P.gz = (T*)dev_alloc(c, (size_t)2 * NO * P.ns3 * n2 * n1 * 2 * NL * es);
+        // pencil edges: two slots per pencil column and block suffice (pencil p + 2 reaches tile t
+        // only after pencil p + 1 has consumed pencil p's edge of tile t; the first pencil of a block
+        // does not wait, so every block has its own pair)
+        const size_t ey_sz = (size_t)NO * P.np3 * 2 * P.ns2 * P.R3 * n1 * 2 * NL;
+        const size_t ez_sz = (size_t)NO * P.np2 * 2 * P.ns3 * P.R2 * n1 * 2 * NL;
         P.ey = (T*)dev_alloc(c, ey_sz * es);
         P.ez = (T*)dev_alloc(c, ez_sz * es);
         T* lanec = (T*)dev_alloc(c, (size_t)NO * NL * kLaneConsts3 * sizeof(T));
@@ -804,8 +869,8 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
                     qw.size() * sizeof(double) + probs.size() * sizeof(Prob3D<T>);
     c->probs_host.assign((const char*)probs.data(), (const char*)probs.data() + probs.size() * sizeof(Prob3D<T>));
     int per_sm = 0;
-    if constexpr (std::is_same<T, float>::value) e = sweep3d_f32x2_occupancy(c->T1, c->NW, mr2, mr3, c->bf16 ? 1 : 0, &per_sm);
-    else e = sweep3d_occupancy<T>(c->T1, c->NW, mr2, mr3, 0, &per_sm);
+    if constexpr (std::is_same<T, float>::value) e = sweep3d_f32x2_occupancy(c->T1, c->NW, mr2, mr3, c->bf16 ? 1 : 0, c->sub3 ? 1 : 0, &per_sm);
+    else e = sweep3d_occupancy<T>(c->T1, c->NW, mr2, mr3, 0, c->sub3 ? 1 : 0, &per_sm);
     if (e != cudaSuccess) return cuda_fail(c, e, "occupancy");
     if (per_sm < 1) return fail(c, DVM_EINVAL, "3D sweep kernel does not fit on an SM with these pencils");
     int dev = 0, sms = 0;
@@ -903,6 +968,7 @@ dvm_status enqueue_iter_3d(dvm_ctx* c) {
     a.maxR2 = c->max_rows / 1000;
     a.maxR3 = c->max_rows % 1000;
     a.bf16 = c->bf16 ? 1 : 0;
+    a.sub = c->sub3 ? 1 : 0;
     a.parity = (int)(c->iters & 1);
     a.ticket = c->counters_dev;
     a.status = c->status_dev;
@@ -1033,9 +1099,9 @@ void state_segs_2d(const Prob2D<T>& P, size_t NL, int par, std::vector<Seg>& out
 
 template <typename T>
 void state_segs_3d(const Prob3D<T>& P, size_t NL, int par, std::vector<Seg>& out) {
-    const size_t gx = (size_t)8 * P.n3 * P.n2 * 2 * NL;
-    const size_t gy = (size_t)8 * P.n3 * P.n1 * 2 * NL;
-    const size_t gz = (size_t)8 * P.n2 * P.n1 * 2 * NL;
+    const size_t gx = (size_t)8 * P.ns1 * P.n3 * P.n2 * 2 * NL;
+    const size_t gy = (size_t)8 * P.ns2 * P.n3 * P.n1 * 2 * NL;
+    const size_t gz = (size_t)8 * P.ns3 * P.n2 * P.n1 * 2 * NL;
     const size_t es = P.bf16 ? 2 : sizeof(T);
     out.push_back({P.P, (size_t)8 * P.ngroups * 4 * P.N * sizeof(T)});
     out.push_back({(char*)P.gx1 + par * gx * es, gx * es});
@@ -1182,9 +1248,11 @@ dvm_status dvm_create_batch(int nprob, const dvm_geometry* geoms, const double* 
     if (c->opt.check_interval < 1) return reject(DVM_EINVAL, "check_interval");
     for (int j = 0; j < 3; ++j)
         if (c->opt.subdomains[j] < 0) return reject(DVM_EINVAL, "subdomain counts must not be negative");
-    if (c->opt.subdomains[2] > 1 || (dims == 3 && (c->opt.subdomains[0] > 1 || c->opt.subdomains[1] > 1)))
-        return reject(DVM_EINVAL, "lagged-halo subdomains are implemented along x1 and x2 of 2D problems only");
+    if (dims == 2 && c->opt.subdomains[2] > 1) return reject(DVM_EINVAL, "a 2D problem has no x3 subdomains");
     c->xsub = dims == 2 && c->opt.subdomains[0] > 1;
+    c->sub3 = dims == 3 && (c->opt.subdomains[0] > 1 || c->opt.subdomains[1] > 1 || c->opt.subdomains[2] > 1);
+    if (c->sub3 && c->opt.precision == DVM_BF16_STORE)
+        return reject(DVM_EINVAL, "BF16 storage is not implemented with subdomains");
     if (c->opt.group_warps < 0) return reject(DVM_EINVAL, "group_warps must not be negative");
     if (c->opt.band_pairs && (dims != 2 || c->opt.precision != DVM_FP32 || c->opt.subdomains[0] > 1 ||
                               c->opt.subdomains[1] > 1))
@@ -1213,10 +1281,12 @@ dvm_status dvm_create_batch(int nprob, const dvm_geometry* geoms, const double* 
             N *= H.n[j];
         }
         if (N > (1LL << 30)) return reject(DVM_EINVAL, "geometry too large");
-        if (dims == 2 && c->opt.subdomains[1] > 1 && g.n[1] < 2LL * c->opt.subdomains[1])
+        if (c->opt.subdomains[1] > 1 && g.n[1] < 2LL * c->opt.subdomains[1])
             return reject(DVM_EINVAL, "every x2 subdomain needs at least two rows");
-        if (dims == 2 && c->opt.subdomains[0] > 1 && g.n[0] < 2LL * c->opt.subdomains[0])
+        if (c->opt.subdomains[0] > 1 && g.n[0] < 2LL * c->opt.subdomains[0])
             return reject(DVM_EINVAL, "every x1 subdomain needs at least two columns");
+        if (dims == 3 && c->opt.subdomains[2] > 1 && g.n[2] < 2LL * c->opt.subdomains[2])
+            return reject(DVM_EINVAL, "every x3 subdomain needs at least two planes");
         H.N = (int)N;
         H.kn = kn[b];
         H.nu = std::sqrt(3.14159265358979323846) / (2.0 * kn[b]);

@@ -112,13 +112,32 @@ struct Prob3D {
     T* src;                 // [N][4]  (nu rho', 2 nu u1 + 1, 2 nu u2, 2 nu u3)
     T* E;                   // [N][8]  wall terms, index 2 j + u (6 used)
     T* P;                   // [8][G][4][N] moment partials per octant and velocity group
-    T* gx1;                 // [2][8][n3 * n2][2][NL] x1 ghosts (parity, octant, row (k, j), layer, lane);
-                            // ghosts and edges are T, or BF16 when bf16 is set (element offsets
-                            // are the same, the pointers are reinterpreted)
-    T* gy;                  // [2][8][n3 * n1][2][NL] x2 ghosts (row (k, i))
-    T* gz;                  // [2][8][n2 * n1][2][NL] x3 ghosts (row (j, i))
-    T* ey;                  // [8][np3][2][R3][n1][2][NL] x2 edges between pencils (slot p2 & 1)
-    T* ez;                  // [8][np2][2][R2][n1][2][NL] x3 edges between pencils (slot p3 & 1)
+    // Lagged-halo subdomains (Sec. 3.2): ns_j = c_j blocks along axis j (1: none).  Slot s of a
+    // ghost array holds the two layers upstream of oriented block s from the previous iteration
+    // (slot 0: the domain's own ghost layers); the last pencil / tile of block s writes slot
+    // (s + 1) mod ns_j for the next iteration.
+    int ns1, ns2, ns3;
+    T* gx1;                 // [2][8][ns1][n3 * n2][2][NL] x1 ghosts (parity, octant, slot, row (k, j), layer,
+                            // lane); ghosts and edges are T, or BF16 when bf16 is set (element
+                            // offsets are the same, the pointers are reinterpreted)
+    T* gy;                  // [2][8][ns2][n3 * n1][2][NL] x2 ghosts (row (k, i))
+    T* gz;                  // [2][8][ns3][n2 * n1][2][NL] x3 ghosts (row (j, i))
+    T* ey;                  // [8][np3][2 ns2][R3][n1][2][NL] x2 edges between pencils: two ring slots per
+                            // x2 block (slot 2 s + (local pencil index & 1))
+    T* ez;                  // [8][np2][2 ns3][R2][n1][2][NL] x3 edges between pencils
+    // Pencils per orientation (s_j < 0 or not): {first oriented row, rows, below, above}; below >= 0:
+    // the pencil's upstream rows come from ghost slot `below` (previous iteration), below < 0: from
+    // ring slot -1 - below, written by the pencil before it in this sweep; above likewise for the
+    // rows it writes (>= 0: ghost slot of the next iteration).  x1 tiles per orientation: {first
+    // oriented column, width, carry-in slot or -1, carry-out slot or -1}.  Read by the kernels only
+    // with subdomains; without them the same values follow from p * R and t * T1.
+    int nt1;                // x1 tiles of a pencil
+    const int4* pen2;       // [2][np2]
+    const int4* pen3;       // [2][np3]
+    const int4* tiles1;     // [2][nt1]
+    const int* slot_row2;   // [2][ns2] oriented row that follows the layers held in slot s
+    const int* slot_row3;   // [2][ns3]
+    const int* slot_col1;   // [2][ns1] oriented column that follows the layers held in slot s
     int* prog;              // [8][G][np3][np2] tiles completed
     const T* lanec;         // [8][NL][kLaneConsts3]
     double* kpart;
@@ -142,6 +161,7 @@ struct SweepArgs3D {
     int T1;
     int maxR2, maxR3;
     int bf16;                   // ghosts and pencil edges stored as BF16 (see Prob3D::bf16)
+    int sub;                    // lagged-halo subdomains: pencils and tiles from the Prob3D tables
     int parity;
     int* ticket;
     int* status;

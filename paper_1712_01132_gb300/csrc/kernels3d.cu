@@ -61,7 +61,7 @@ template <> struct HStore<float, true> {
 
 }  // namespace
 
-template <typename T, int T1, bool BF>
+template <typename T, int T1, bool BF, bool SUB>
 __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
     using V = typename V4t<T>::type;
     using HS = HStore<T, BF>;
@@ -95,8 +95,18 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
         const int N = P->N;
         const int np2 = P->np2, np3 = P->np3;
         const int s1n = q & 1, s2n = (q >> 1) & 1, s3n = (q >> 2) & 1;
-        const int j0 = p2 * P->R2, k0 = p3 * P->R3;
-        const int nr2 = min(P->R2, n2 - j0), nr3 = min(P->R3, n3 - k0);
+        // the pencil's rows and where its upstream rows come from / its top rows go (Prob3D)
+        int4 pi2, pi3;
+        if constexpr (SUB) {
+            pi2 = P->pen2[s2n * np2 + p2];
+            pi3 = P->pen3[s3n * np3 + p3];
+        } else {
+            pi2 = make_int4(p2 * P->R2, min(P->R2, n2 - p2 * P->R2), p2 == 0 ? 0 : -1 - ((p2 - 1) & 1),
+                            p2 == np2 - 1 ? 0 : -1 - (p2 & 1));
+            pi3 = make_int4(p3 * P->R3, min(P->R3, n3 - p3 * P->R3), p3 == 0 ? 0 : -1 - ((p3 - 1) & 1),
+                            p3 == np3 - 1 ? 0 : -1 - (p3 & 1));
+        }
+        const int j0 = pi2.x, nr2 = pi2.y, k0 = pi3.x, nr3 = pi3.y;
         const T K1o = P->order == 2 ? T(2) : T(1);
         const T K2o = P->order == 2 ? T(-0.5) : T(0);
         const int lv = g * a.GL + warp * 32 + lane;      // velocity lane within the octant
@@ -113,25 +123,18 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
         const T dxT = (T)P->dx;
         auto x1of = [&](int ic) -> T { return (T)(s1n ? n1 - 1 - ic : ic) * dxT; };
         const T x1g0 = x1of(n1 - 1), x1g1 = x1of(n1 - 2);   // columns of the x1 ghost layers
-        // x1 upstream of the first tile: x1 ghost layers (oriented rows (k, j))
-        {
-            const size_t gxo = (((size_t)par * 8 + q) * n3 * n2) * 2 * NL;
-            for (int kk = 0; kk < nr3; ++kk)
-                for (int jj = 0; jj < nr2; ++jj) {
-                    const size_t row = (size_t)(k0 + kk) * n2 + (j0 + jj);
-                    T* cr = carry + ((size_t)(warp * MROWS + kk * MR2 + jj) * 2) * 32 + lane;
-                    cr[0] = HS::ld(P->gx1, gxo + (row * 2 + 0) * NL + lv, x1g0);
-                    cr[32] = HS::ld(P->gx1, gxo + (row * 2 + 1) * NL + lv, x1g1);
-                }
-        }
-        const int ntiles = (n1 + T1 - 1) / T1;
+        const int ntiles = SUB ? P->nt1 : (n1 + T1 - 1) / T1;
         for (int t = 0; t < ntiles; ++t) {
-            const int c0 = t * T1;
-            const int width = min(T1, n1 - c0);
+            // tile: first oriented column, width, x1 carry-in and carry-out ghost slots (or -1)
+            int4 ti;
+            if constexpr (SUB) ti = P->tiles1[s1n * ntiles + t];
+            else ti = make_int4(t * T1, min(T1, n1 - t * T1), t == 0 ? 0 : -1, t == ntiles - 1 ? 0 : -1);
+            const int c0 = ti.x;
+            const int width = ti.y;
             if (threadIdx.x == 0) {
                 bool ok = true;
-                if (p2 > 0) ok = wait_geq(prog + p3 * np2 + p2 - 1, t + 1, a.status, a.timeout_ns);
-                if (ok && p3 > 0) ok = wait_geq(prog + (p3 - 1) * np2 + p2, t + 1, a.status, a.timeout_ns);
+                if (pi2.z < 0) ok = wait_geq(prog + p3 * np2 + p2 - 1, t + 1, a.status, a.timeout_ns);
+                if (ok && pi3.z < 0) ok = wait_geq(prog + (p3 - 1) * np2 + p2, t + 1, a.status, a.timeout_ns);
                 if (!ok) s_abort = 1;
             }
             // records of the tile's points for this octant
@@ -176,16 +179,30 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
             }
             __syncthreads();
             if (s_abort) return;
-            // x3 upstream planes of the first plane of the pencil: the pencil below in x3 or the
-            // x3 ghost layers (periodic or specular, Eq. 8)
+            // x1 upstream of the tile's first column when it starts a block: x1 ghost layers of
+            // the previous iteration in slot ti.z (oriented rows (k, j))
+            if (ti.z >= 0) {
+                const size_t gxo = ((((size_t)par * 8 + q) * P->ns1 + ti.z) * n3 * n2) * 2 * NL;
+                for (int kk = 0; kk < nr3; ++kk)
+                    for (int jj = 0; jj < nr2; ++jj) {
+                        const size_t row = (size_t)(k0 + kk) * n2 + (j0 + jj);
+                        T* cr = carry + ((size_t)(warp * MROWS + kk * MR2 + jj) * 2) * 32 + lane;
+                        cr[0] = HS::ld(P->gx1, gxo + (row * 2 + 0) * NL + lv, x1g0);
+                        cr[32] = HS::ld(P->gx1, gxo + (row * 2 + 1) * NL + lv, x1g1);
+                    }
+            }
+            // x3 upstream planes of the first plane of the pencil: the pencil below in x3 (ring
+            // slot) or ghost slot pi3.z (x3 ghost layers, periodic or specular, Eq. 8, or the
+            // lagged halo of the block below)
             {
-                const T* zb = (p3 == 0) ? P->gz : P->ez;
-                const size_t zo = (p3 == 0)
-                    ? (((size_t)par * 8 + q) * n2 * n1) * 2 * NL
-                    : ((((size_t)q * np2 + p2) * 2 + ((p3 - 1) & 1)) * P->R2 * n1) * 2 * NL;
+                const bool zg = pi3.z >= 0;
+                const T* zb = zg ? P->gz : P->ez;
+                const size_t zo = zg
+                    ? ((((size_t)par * 8 + q) * P->ns3 + pi3.z) * n2 * n1) * 2 * NL
+                    : ((((size_t)q * np2 + p2) * 2 * P->ns3 + (-1 - pi3.z)) * P->R2 * n1) * 2 * NL;
                 for (int jj = 0; jj < nr2; ++jj)
                     for (int i = 0; i < width; ++i) {
-                        const size_t row = (p3 == 0) ? ((size_t)(j0 + jj) * n1 + (c0 + i)) : ((size_t)jj * n1 + (c0 + i));
+                        const size_t row = zg ? ((size_t)(j0 + jj) * n1 + (c0 + i)) : ((size_t)jj * n1 + (c0 + i));
                         T* d = pb + ((((size_t)warp * MR2 + jj) * 2) * T1 + i) * 32 + lane;
                         const T xs = x1of(c0 + i);
                         d[0] = HS::ld(zb, zo + (row * 2 + 0) * NL + lv, xs);
@@ -196,11 +213,12 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                 // x2 upstream rows of the first row of this plane
                 T rb1[T1], rb2[T1];
                 {
-                    const T* yb = (p2 == 0) ? P->gy : P->ey;
-                    const size_t yo = (p2 == 0)
-                        ? (((size_t)par * 8 + q) * n3 * n1) * 2 * NL
-                        : ((((size_t)q * np3 + p3) * 2 + ((p2 - 1) & 1)) * P->R3 * n1) * 2 * NL;
-                    const size_t rowbase = (p2 == 0) ? (size_t)(k0 + kk) * n1 : (size_t)kk * n1;
+                    const bool yg = pi2.z >= 0;
+                    const T* yb = yg ? P->gy : P->ey;
+                    const size_t yo = yg
+                        ? ((((size_t)par * 8 + q) * P->ns2 + pi2.z) * n3 * n1) * 2 * NL
+                        : ((((size_t)q * np3 + p3) * 2 * P->ns2 + (-1 - pi2.z)) * P->R3 * n1) * 2 * NL;
+                    const size_t rowbase = yg ? (size_t)(k0 + kk) * n1 : (size_t)kk * n1;
 #pragma unroll
                     for (int i = 0; i < T1; ++i) {
                         if (i < width) {
@@ -266,19 +284,20 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                     cr[0] = hp1;
                     cr[32] = hp2;
                 }
-                // x2 edge of this plane for the pencil above in x2, or the x2 ghost layers of the
-                // next iteration (periodic: same octant; specular: octant with s2 flipped)
+                // x2 edge of this plane for the pencil above in x2 (ring slot), or ghost slot pi2.w
+                // of the next iteration: the halo of the next block, or at the domain face the x2
+                // ghost layers (periodic: same octant; specular: octant with s2 flipped)
                 {
                     T* et;
                     size_t eo, rowbase;
-                    if (p2 < np2 - 1) {
+                    if (pi2.w < 0) {
                         et = P->ey;
-                        eo = ((((size_t)q * np3 + p3) * 2 + (p2 & 1)) * P->R3 * n1) * 2 * NL;
+                        eo = ((((size_t)q * np3 + p3) * 2 * P->ns2 + (-1 - pi2.w)) * P->R3 * n1) * 2 * NL;
                         rowbase = (size_t)kk * n1;
                     } else {
-                        const int qy = (P->lateral == 1) ? q : (q ^ 2);
+                        const int qy = (pi2.w > 0 || P->lateral == 1) ? q : (q ^ 2);
                         et = P->gy;
-                        eo = (((size_t)(par ^ 1) * 8 + qy) * n3 * n1) * 2 * NL;
+                        eo = ((((size_t)(par ^ 1) * 8 + qy) * P->ns2 + pi2.w) * n3 * n1) * 2 * NL;
                         rowbase = (size_t)(k0 + kk) * n1;
                     }
 #pragma unroll
@@ -291,18 +310,19 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                     }
                 }
             }
-            // x3 edge for the pencil above in x3, or the x3 ghost layers of the next iteration
+            // x3 edge for the pencil above in x3 (ring slot), or ghost slot pi3.w of the next
+            // iteration
             {
                 T* et;
                 size_t eo;
-                const bool last = (p3 == np3 - 1);
+                const bool last = pi3.w >= 0;
                 if (!last) {
                     et = P->ez;
-                    eo = ((((size_t)q * np2 + p2) * 2 + (p3 & 1)) * P->R2 * n1) * 2 * NL;
+                    eo = ((((size_t)q * np2 + p2) * 2 * P->ns3 + (-1 - pi3.w)) * P->R2 * n1) * 2 * NL;
                 } else {
-                    const int qz = (P->lateral == 1) ? q : (q ^ 4);
+                    const int qz = (pi3.w > 0 || P->lateral == 1) ? q : (q ^ 4);
                     et = P->gz;
-                    eo = (((size_t)(par ^ 1) * 8 + qz) * n2 * n1) * 2 * NL;
+                    eo = ((((size_t)(par ^ 1) * 8 + qz) * P->ns3 + pi3.w) * n2 * n1) * 2 * NL;
                 }
                 for (int jj = 0; jj < nr2; ++jj)
                     for (int i = 0; i < width; ++i) {
@@ -313,8 +333,8 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                         HS::st(et, eo + (row * 2 + 1) * NL + lv, s[(size_t)T1 * 32], xs);
                     }
             }
-            if (t == ntiles - 1) {
-                const size_t gxo = (((size_t)(par ^ 1) * 8 + q) * n3 * n2) * 2 * NL;
+            if (ti.w >= 0) {   // x1 carry into ghost slot ti.w of the next iteration
+                const size_t gxo = ((((size_t)(par ^ 1) * 8 + q) * P->ns1 + ti.w) * n3 * n2) * 2 * NL;
                 for (int kk = 0; kk < nr3; ++kk)
                     for (int jj = 0; jj < nr2; ++jj) {
                         const size_t row = (size_t)(k0 + kk) * n2 + (j0 + jj);
@@ -462,22 +482,25 @@ __global__ void init3d_kernel(const Prob3D<T>* P, int NL, const double* qw /*[8]
         const double x1 = (id % n1) * P->dx;
         P->P[idx] = (P->code[id] & kSolidBit) ? T(0) : (T)(x1 * qw[qgm]);
     }
-    for (size_t idx = t0; idx < (size_t)2 * 8 * n3 * n2 * 2 * nl; idx += stride) {
+    // ghost slot s of the x1 ghosts holds the two columns before oriented column slot_col1[s]
+    const int ns1 = P->ns1, ns2 = P->ns2, ns3 = P->ns3;
+    for (size_t idx = t0; idx < (size_t)2 * 8 * ns1 * n3 * n2 * 2 * nl; idx += stride) {
         const int layer = (idx / nl) % 2;
-        const int q = (idx / (nl * 2 * n3 * n2)) % 8;
-        const int ico = n1 - 1 - layer;
+        const int slot = (idx / (nl * 2 * n3 * n2)) % ns1;
+        const int q = (idx / (nl * 2 * n3 * n2 * ns1)) % 8;
+        const int ico = P->slot_col1[(q & 1) * ns1 + slot] - 1 - layer;
         const int col = (q & 1) ? n1 - 1 - ico : ico;
         put_h(P, P->gx1, idx, col * P->dx, col * P->dx);
     }
-    for (size_t idx = t0; idx < (size_t)2 * 8 * n3 * n1 * 2 * nl; idx += stride) {
+    for (size_t idx = t0; idx < (size_t)2 * 8 * ns2 * n3 * n1 * 2 * nl; idx += stride) {
         const int ic = (idx / (nl * 2)) % n1;
-        const int q = (idx / (nl * 2 * n3 * n1)) % 8;
+        const int q = (idx / (nl * 2 * n3 * n1 * ns2)) % 8;
         const int col = (q & 1) ? n1 - 1 - ic : ic;
         put_h(P, P->gy, idx, col * P->dx, col * P->dx);
     }
-    for (size_t idx = t0; idx < (size_t)2 * 8 * n2 * n1 * 2 * nl; idx += stride) {
+    for (size_t idx = t0; idx < (size_t)2 * 8 * ns3 * n2 * n1 * 2 * nl; idx += stride) {
         const int ic = (idx / (nl * 2)) % n1;
-        const int q = (idx / (nl * 2 * n2 * n1)) % 8;
+        const int q = (idx / (nl * 2 * n2 * n1 * ns3)) % 8;
         const int col = (q & 1) ? n1 - 1 - ic : ic;
         put_h(P, P->gz, idx, col * P->dx, col * P->dx);
     }
@@ -516,37 +539,46 @@ __global__ void warm3d_kernel(const Prob3D<T>* P, int NL, int par, const double*
         }
         P->P[idx] = (T)val;
     }
-    // x1 ghosts: slot (q, oriented row (k, j), layer) holds h at oriented column n1 - 1 - layer
-    for (size_t idx = t0; idx < (size_t)8 * n3 * n2 * 2 * nl; idx += stride) {
+    const int ns1 = P->ns1, ns2 = P->ns2, ns3 = P->ns3;
+    // x1 ghosts: (q, slot s, oriented row (k, j), layer) holds h at oriented column
+    // slot_col1[s] - 1 - layer (slot 0: n1 - 1 - layer, the periodic wrap)
+    for (size_t idx = t0; idx < (size_t)8 * ns1 * n3 * n2 * 2 * nl; idx += stride) {
         const int l = idx % nl;
         const int layer = (idx / nl) % 2;
         const int row = (idx / (nl * 2)) % ((size_t)n3 * n2);
-        const int q = idx / (nl * 2 * n3 * n2);
+        const int slot = (idx / (nl * 2 * n3 * n2)) % ns1;
+        const int q = idx / (nl * 2 * n3 * n2 * ns1);
+        const int ico = P->slot_col1[(q & 1) * ns1 + slot] - 1 - layer;
         double x1;
-        const double hv = h0(q, n1 - 1 - layer, row % n2, row / n2, vel + ((size_t)q * nl + l) * 3, x1);
-        put_h(P, P->gx1, (size_t)par * 8 * n3 * n2 * 2 * nl + idx, hv, x1);
+        const double hv = h0(q, ico, row % n2, row / n2, vel + ((size_t)q * nl + l) * 3, x1);
+        put_h(P, P->gx1, (size_t)par * 8 * ns1 * n3 * n2 * 2 * nl + idx, hv, x1);
     }
-    // x2 ghosts: octant q writes its oriented rows n2 - 1 - layer for the octant that reads them
-    for (size_t idx = t0; idx < (size_t)8 * n3 * n1 * 2 * nl; idx += stride) {
+    // x2 ghosts: octant q writes its oriented rows slot_row2[s] - 1 - layer into slot s of the
+    // octant that reads them (slot 0 at the domain face: periodic same octant, specular s2 flipped)
+    for (size_t idx = t0; idx < (size_t)8 * ns2 * n3 * n1 * 2 * nl; idx += stride) {
         const int l = idx % nl;
         const int layer = (idx / nl) % 2;
         const int row = (idx / (nl * 2)) % ((size_t)n3 * n1);
-        const int q = idx / (nl * 2 * n3 * n1);
-        const int qy = (P->lateral == 1) ? q : (q ^ 2);
+        const int slot = (idx / (nl * 2 * n3 * n1)) % ns2;
+        const int q = idx / (nl * 2 * n3 * n1 * ns2);
+        const int qy = (slot > 0 || P->lateral == 1) ? q : (q ^ 2);
+        const int jo = P->slot_row2[((q >> 1) & 1) * ns2 + slot] - 1 - layer;
         double x1;
-        const double hv = h0(q, row % n1, n2 - 1 - layer, row / n1, vel + ((size_t)q * nl + l) * 3, x1);
-        put_h(P, P->gy, ((((size_t)par * 8 + qy) * n3 * n1 + row) * 2 + layer) * nl + l, hv, x1);
+        const double hv = h0(q, row % n1, jo, row / n1, vel + ((size_t)q * nl + l) * 3, x1);
+        put_h(P, P->gy, (((((size_t)par * 8 + qy) * ns2 + slot) * n3 * n1 + row) * 2 + layer) * nl + l, hv, x1);
     }
-    // x3 ghosts: octant q writes its oriented planes n3 - 1 - layer for the octant that reads them
-    for (size_t idx = t0; idx < (size_t)8 * n2 * n1 * 2 * nl; idx += stride) {
+    // x3 ghosts: the same with oriented planes slot_row3[s] - 1 - layer
+    for (size_t idx = t0; idx < (size_t)8 * ns3 * n2 * n1 * 2 * nl; idx += stride) {
         const int l = idx % nl;
         const int layer = (idx / nl) % 2;
         const int row = (idx / (nl * 2)) % ((size_t)n2 * n1);
-        const int q = idx / (nl * 2 * n2 * n1);
-        const int qz = (P->lateral == 1) ? q : (q ^ 4);
+        const int slot = (idx / (nl * 2 * n2 * n1)) % ns3;
+        const int q = idx / (nl * 2 * n2 * n1 * ns3);
+        const int qz = (slot > 0 || P->lateral == 1) ? q : (q ^ 4);
+        const int ko = P->slot_row3[((q >> 2) & 1) * ns3 + slot] - 1 - layer;
         double x1;
-        const double hv = h0(q, row % n1, row / n1, n3 - 1 - layer, vel + ((size_t)q * nl + l) * 3, x1);
-        put_h(P, P->gz, ((((size_t)par * 8 + qz) * n2 * n1 + row) * 2 + layer) * nl + l, hv, x1);
+        const double hv = h0(q, row % n1, row / n1, ko, vel + ((size_t)q * nl + l) * 3, x1);
+        put_h(P, P->gz, (((((size_t)par * 8 + qz) * ns3 + slot) * n2 * n1 + row) * 2 + layer) * nl + l, hv, x1);
     }
 }
 
@@ -590,38 +622,39 @@ size_t sweep3d_smem(int T1, int NW, int R2, int R3) {
                         (size_t)NW * R2 * 2 * T1 * 32 + (size_t)NW * 8 * 32);
 }
 
-template <typename T, int T1, bool BF>
+template <typename T, int T1, bool SUB>
 static cudaError_t occ3(int NW, int R2, int R3, int* blocks_per_sm) {
     const size_t smem = sweep3d_smem<T>(T1, NW, R2, R3);
-    cudaError_t e = cudaFuncSetAttribute(sweep3d_kernel<T, T1, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(sweep3d_kernel<T, T1, false, SUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep3d_kernel<T, T1, BF>, NW * 32, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep3d_kernel<T, T1, false, SUB>, NW * 32, smem);
 }
 
 // The scalar kernel serves the FP64 path (FP32 and its BF16-storage ablation use the packed kernel
-// of sweep3d_f32x2.cu); its BF16 flag stays false.
+// of sweep3d_f32x2.cu); its BF16 flag stays false.  sub: lagged-halo subdomains (table-driven
+// pencils and tiles).
 template <typename T>
-cudaError_t sweep3d_occupancy(int T1, int NW, int R2, int R3, int bf16, int* blocks_per_sm) {
+cudaError_t sweep3d_occupancy(int T1, int NW, int R2, int R3, int bf16, int sub, int* blocks_per_sm) {
     if (bf16) return cudaErrorInvalidValue;
-    if (T1 == 4) return occ3<T, 4, false>(NW, R2, R3, blocks_per_sm);
-    if (T1 == 8) return occ3<T, 8, false>(NW, R2, R3, blocks_per_sm);
+    if (T1 == 4) return sub ? occ3<T, 4, true>(NW, R2, R3, blocks_per_sm) : occ3<T, 4, false>(NW, R2, R3, blocks_per_sm);
+    if (T1 == 8) return sub ? occ3<T, 8, true>(NW, R2, R3, blocks_per_sm) : occ3<T, 8, false>(NW, R2, R3, blocks_per_sm);
     return cudaErrorInvalidValue;
 }
 
-template <typename T, int T1, bool BF>
+template <typename T, int T1, bool SUB>
 static cudaError_t launch3(const SweepArgs3D<T>& a, int grid, int NW, cudaStream_t st) {
     const size_t smem = sweep3d_smem<T>(T1, NW, a.maxR2, a.maxR3);
-    cudaError_t e = cudaFuncSetAttribute(sweep3d_kernel<T, T1, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(sweep3d_kernel<T, T1, false, SUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    sweep3d_kernel<T, T1, BF><<<grid, NW * 32, smem, st>>>(a);
+    sweep3d_kernel<T, T1, false, SUB><<<grid, NW * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_sweep3d(const SweepArgs3D<T>& a, int grid, int NW, cudaStream_t st) {
     if (a.bf16) return cudaErrorInvalidValue;
-    if (a.T1 == 4) return launch3<T, 4, false>(a, grid, NW, st);
-    if (a.T1 == 8) return launch3<T, 8, false>(a, grid, NW, st);
+    if (a.T1 == 4) return a.sub ? launch3<T, 4, true>(a, grid, NW, st) : launch3<T, 4, false>(a, grid, NW, st);
+    if (a.T1 == 8) return a.sub ? launch3<T, 8, true>(a, grid, NW, st) : launch3<T, 8, false>(a, grid, NW, st);
     return cudaErrorInvalidValue;
 }
 
@@ -657,7 +690,7 @@ cudaError_t launch_wall3d(const Prob3D<T>* p, double* out, cudaStream_t st) {
 }
 
 template size_t sweep3d_smem<double>(int, int, int, int);
-template cudaError_t sweep3d_occupancy<double>(int, int, int, int, int, int*);
+template cudaError_t sweep3d_occupancy<double>(int, int, int, int, int, int, int*);
 template cudaError_t launch_sweep3d<double>(const SweepArgs3D<double>&, int, int, cudaStream_t);
 
 #define DVM_INSTANTIATE3(T)                                                                     \

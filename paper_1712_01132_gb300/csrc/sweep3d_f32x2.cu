@@ -68,7 +68,7 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 
 }  // namespace
 
-template <int T1, bool BF>
+template <int T1, bool BF, bool SUB>
 __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<float> a) {
     using PS = PairStore<BF>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -104,8 +104,18 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
         const int N = P->N;
         const int np2 = P->np2, np3 = P->np3;
         const int s1n = q & 1, s2n = (q >> 1) & 1, s3n = (q >> 2) & 1;
-        const int j0 = p2 * P->R2, k0 = p3 * P->R3;
-        const int nr2 = min(P->R2, n2 - j0), nr3 = min(P->R3, n3 - k0);
+        // the pencil's rows and where its upstream rows come from / its top rows go (Prob3D)
+        int4 pi2, pi3;
+        if constexpr (SUB) {
+            pi2 = P->pen2[s2n * np2 + p2];
+            pi3 = P->pen3[s3n * np3 + p3];
+        } else {
+            pi2 = make_int4(p2 * P->R2, min(P->R2, n2 - p2 * P->R2), p2 == 0 ? 0 : -1 - ((p2 - 1) & 1),
+                            p2 == np2 - 1 ? 0 : -1 - (p2 & 1));
+            pi3 = make_int4(p3 * P->R3, min(P->R3, n3 - p3 * P->R3), p3 == 0 ? 0 : -1 - ((p3 - 1) & 1),
+                            p3 == np3 - 1 ? 0 : -1 - (p3 & 1));
+        }
+        const int j0 = pi2.x, nr2 = pi2.y, k0 = pi3.x, nr3 = pi3.y;
         const float K1o = P->order == 2 ? 2.f : 1.f;
         const float K2o = P->order == 2 ? -0.5f : 0.f;
         const int lv = g * a.GL + kPL * warp + 2 * lane;      // first velocity slot of this lane
@@ -130,35 +140,18 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
         // such per instruction); a lane reads its own 8 bytes after the wait and a __syncwarp
         const int hl = lane & 15, half = lane >> 4;
         const size_t lw = (size_t)g * a.GL + (size_t)kPL * warp + 4 * hl;
-        // x1 upstream of the first tile: x1 ghost layers (oriented rows (k, j))
-        if constexpr (!BF) {
-            const size_t gxo = (((size_t)par * 8 + q) * n3 * n2) * 2 * NL;
-            for (int m = half; m < nr3 * nr2 * 2; m += 2) {
-                const int kk = m / (2 * nr2);
-                const int jl = m - kk * 2 * nr2;          // jj * 2 + layer
-                const size_t row = (size_t)(k0 + kk) * n2 + (j0 + (jl >> 1));
-                cp_async16(carry + ((size_t)(warp * MROWS + kk * MR2 + (jl >> 1)) * 2 + (jl & 1)) * kPL + 4 * hl,
-                           P->gx1 + gxo + (row * 2 + (jl & 1)) * NL + lw);
-            }
-            cp_async_commit();
-        } else {
-            const size_t gxo = (((size_t)par * 8 + q) * n3 * n2) * 2 * NL;
-            for (int kk = 0; kk < nr3; ++kk)
-                for (int jj = 0; jj < nr2; ++jj) {
-                    const size_t row = (size_t)(k0 + kk) * n2 + (j0 + jj);
-                    float* cr = carry + ((size_t)(warp * MROWS + kk * MR2 + jj) * 2) * kPL + 2 * lane;
-                    *reinterpret_cast<float2*>(cr) = PS::ld(P->gx1, gxo + (row * 2 + 0) * NL + lv, x1g0);
-                    *reinterpret_cast<float2*>(cr + kPL) = PS::ld(P->gx1, gxo + (row * 2 + 1) * NL + lv, x1g1);
-                }
-        }
-        const int ntiles = (n1 + T1 - 1) / T1;
+        const int ntiles = SUB ? P->nt1 : (n1 + T1 - 1) / T1;
         for (int t = 0; t < ntiles; ++t) {
-            const int c0 = t * T1;
-            const int width = min(T1, n1 - c0);
+            // tile: first oriented column, width, x1 carry-in and carry-out ghost slots (or -1)
+            int4 ti;
+            if constexpr (SUB) ti = P->tiles1[s1n * ntiles + t];
+            else ti = make_int4(t * T1, min(T1, n1 - t * T1), t == 0 ? 0 : -1, t == ntiles - 1 ? 0 : -1);
+            const int c0 = ti.x;
+            const int width = ti.y;
             if (threadIdx.x == 0) {
                 bool ok = true;
-                if (p2 > 0) ok = wait_geq(prog + p3 * np2 + p2 - 1, t + 1, a.status, a.timeout_ns);
-                if (ok && p3 > 0) ok = wait_geq(prog + (p3 - 1) * np2 + p2, t + 1, a.status, a.timeout_ns);
+                if (pi2.z < 0) ok = wait_geq(prog + p3 * np2 + p2 - 1, t + 1, a.status, a.timeout_ns);
+                if (ok && pi3.z < 0) ok = wait_geq(prog + (p3 - 1) * np2 + p2, t + 1, a.status, a.timeout_ns);
                 if (!ok) s_abort = 1;
             }
             // records of the tile's points for this octant (shared by all lanes and velocities) and
@@ -209,18 +202,41 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                 cp_async_wait<0>();
                 return;
             }
+            // x1 upstream of the tile's first column when it starts a block: x1 ghost layers of
+            // the previous iteration in slot ti.z (oriented rows (k, j))
+            if (ti.z >= 0) {
+                const size_t gxo = ((((size_t)par * 8 + q) * P->ns1 + ti.z) * n3 * n2) * 2 * NL;
+                if constexpr (!BF) {
+                    for (int m = half; m < nr3 * nr2 * 2; m += 2) {
+                        const int kk = m / (2 * nr2);
+                        const int jl = m - kk * 2 * nr2;          // jj * 2 + layer
+                        const size_t row = (size_t)(k0 + kk) * n2 + (j0 + (jl >> 1));
+                        cp_async16(carry + ((size_t)(warp * MROWS + kk * MR2 + (jl >> 1)) * 2 + (jl & 1)) * kPL + 4 * hl,
+                                   P->gx1 + gxo + (row * 2 + (jl & 1)) * NL + lw);
+                    }
+                } else {
+                    for (int kk = 0; kk < nr3; ++kk)
+                        for (int jj = 0; jj < nr2; ++jj) {
+                            const size_t row = (size_t)(k0 + kk) * n2 + (j0 + jj);
+                            float* cr = carry + ((size_t)(warp * MROWS + kk * MR2 + jj) * 2) * kPL + 2 * lane;
+                            *reinterpret_cast<float2*>(cr) = PS::ld(P->gx1, gxo + (row * 2 + 0) * NL + lv, x1g0);
+                            *reinterpret_cast<float2*>(cr + kPL) = PS::ld(P->gx1, gxo + (row * 2 + 1) * NL + lv, x1g1);
+                        }
+                }
+            }
             // upstream data of the tile: x3 planes of its first plane (the pencil below in x3, ring
-            // slot, or the x3 ghost layers; periodic or specular, Eq. 8) and x2 rows of each plane
-            // (the pencil below in x2, or the x2 ghost layers)
-            const float* zb = (p3 == 0) ? P->gz : P->ez;
-            const size_t zo = (p3 == 0)
-                ? (((size_t)par * 8 + q) * n2 * n1) * 2 * NL
-                : ((((size_t)q * np2 + p2) * 2 + ((p3 - 1) & 1)) * P->R2 * n1) * 2 * NL;
-            const float* yb = (p2 == 0) ? P->gy : P->ey;
-            const size_t yo = (p2 == 0)
-                ? (((size_t)par * 8 + q) * n3 * n1) * 2 * NL
-                : ((((size_t)q * np3 + p3) * 2 + ((p2 - 1) & 1)) * P->R3 * n1) * 2 * NL;
-            auto yrow = [&](int kk) -> size_t { return (p2 == 0) ? (size_t)(k0 + kk) * n1 : (size_t)kk * n1; };
+            // slot, or ghost slot pi3.z: the x3 ghost layers, periodic or specular, Eq. 8, or the
+            // lagged halo of the block below) and x2 rows of each plane (likewise with pi2.z)
+            const bool zg = pi3.z >= 0, yg = pi2.z >= 0;
+            const float* zb = zg ? P->gz : P->ez;
+            const size_t zo = zg
+                ? ((((size_t)par * 8 + q) * P->ns3 + pi3.z) * n2 * n1) * 2 * NL
+                : ((((size_t)q * np2 + p2) * 2 * P->ns3 + (-1 - pi3.z)) * P->R2 * n1) * 2 * NL;
+            const float* yb = yg ? P->gy : P->ey;
+            const size_t yo = yg
+                ? ((((size_t)par * 8 + q) * P->ns2 + pi2.z) * n3 * n1) * 2 * NL
+                : ((((size_t)q * np3 + p3) * 2 * P->ns2 + (-1 - pi2.z)) * P->R3 * n1) * 2 * NL;
+            auto yrow = [&](int kk) -> size_t { return yg ? (size_t)(k0 + kk) * n1 : (size_t)kk * n1; };
             auto rbuf_rec = [&](int kk, int jj, int i) -> const float* { return rec + (size_t)((kk * MR2 + jj) * T1 + i) * kRec; };
             // FP32: the x2 rows of plane kk go to slot kk & 1, copied while plane kk - 1 is swept
             // Upstream values are fetched only where the stencil of the point that reads them has a
@@ -241,7 +257,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
             if constexpr (BF) {
                 for (int jj = 0; jj < nr2; ++jj)
                     for (int i = 0; i < width; ++i) {
-                        const size_t row = (p3 == 0) ? ((size_t)(j0 + jj) * n1 + (c0 + i)) : ((size_t)jj * n1 + (c0 + i));
+                        const size_t row = zg ? ((size_t)(j0 + jj) * n1 + (c0 + i)) : ((size_t)jj * n1 + (c0 + i));
                         float* d = pb + ((((size_t)warp * MR2 + jj) * 2) * T1 + i) * kPL + 2 * lane;
                         const float xs = x1of(c0 + i);
                         const float* rc = rbuf_rec(0, jj, i);
@@ -253,7 +269,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                 for (int m = half; m < nr2 * 2 * width; m += 2) {
                     const int jl = m / width;            // jj * 2 + layer
                     const int i = m - jl * width;
-                    const size_t row = (p3 == 0) ? ((size_t)(j0 + (jl >> 1)) * n1 + (c0 + i)) : ((size_t)(jl >> 1) * n1 + (c0 + i));
+                    const size_t row = zg ? ((size_t)(j0 + (jl >> 1)) * n1 + (c0 + i)) : ((size_t)(jl >> 1) * n1 + (c0 + i));
                     const bool need = rbuf_rec(0, jl >> 1, i)[12 + (jl & 1)] != 0.f;
                     cp_async16_or_zero(pb + (((size_t)warp * MR2 * 2 + jl) * T1 + i) * kPL + 4 * hl,
                                        zb + zo + (row * 2 + (jl & 1)) * NL + lw, need);
@@ -362,19 +378,20 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                     *reinterpret_cast<float2*>(cr) = hp1;
                     *reinterpret_cast<float2*>(cr + kPL) = hp2;
                 }
-                // x2 edge of this plane for the pencil above in x2 (ring slot p2 & 1), or the x2
-                // ghost layers of the next iteration (periodic: same octant; specular: s2 flipped)
+                // x2 edge of this plane for the pencil above in x2 (ring slot), or ghost slot pi2.w
+                // of the next iteration: the halo of the next block, or at the domain face the x2
+                // ghost layers (periodic: same octant; specular: s2 flipped)
                 {
                     float* et;
                     size_t eo, rowbase;
-                    if (p2 < np2 - 1) {
+                    if (pi2.w < 0) {
                         et = P->ey;
-                        eo = ((((size_t)q * np3 + p3) * 2 + (p2 & 1)) * P->R3 * n1) * 2 * NL;
+                        eo = ((((size_t)q * np3 + p3) * 2 * P->ns2 + (-1 - pi2.w)) * P->R3 * n1) * 2 * NL;
                         rowbase = (size_t)kk * n1;
                     } else {
-                        const int qy = (P->lateral == 1) ? q : (q ^ 2);
+                        const int qy = (pi2.w > 0 || P->lateral == 1) ? q : (q ^ 2);
                         et = P->gy;
-                        eo = (((size_t)(par ^ 1) * 8 + qy) * n3 * n1) * 2 * NL;
+                        eo = ((((size_t)(par ^ 1) * 8 + qy) * P->ns2 + pi2.w) * n3 * n1) * 2 * NL;
                         rowbase = (size_t)(k0 + kk) * n1;
                     }
                     // only values of fluid points are stored (layer 1 of a one-row pencil passes the
@@ -391,18 +408,19 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                     }
                 }
             }
-            // x3 edge for the pencil above in x3 (ring slot p3 & 1), or the x3 ghost layers
+            // x3 edge for the pencil above in x3 (ring slot), or ghost slot pi3.w of the next
+            // iteration
             {
                 float* et;
                 size_t eo;
-                const bool last = (p3 == np3 - 1);
+                const bool last = pi3.w >= 0;
                 if (!last) {
                     et = P->ez;
-                    eo = ((((size_t)q * np2 + p2) * 2 + (p3 & 1)) * P->R2 * n1) * 2 * NL;
+                    eo = ((((size_t)q * np2 + p2) * 2 * P->ns3 + (-1 - pi3.w)) * P->R2 * n1) * 2 * NL;
                 } else {
-                    const int qz = (P->lateral == 1) ? q : (q ^ 4);
+                    const int qz = (pi3.w > 0 || P->lateral == 1) ? q : (q ^ 4);
                     et = P->gz;
-                    eo = (((size_t)(par ^ 1) * 8 + qz) * n2 * n1) * 2 * NL;
+                    eo = ((((size_t)(par ^ 1) * 8 + qz) * P->ns3 + pi3.w) * n2 * n1) * 2 * NL;
                 }
                 for (int jj = 0; jj < nr2; ++jj) {
                     const unsigned f0 = fm_cur[(nr3 - 1) * MR2 + jj];
@@ -416,8 +434,8 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                     }
                 }
             }
-            if (t == ntiles - 1) {
-                const size_t gxo = (((size_t)(par ^ 1) * 8 + q) * n3 * n2) * 2 * NL;
+            if (ti.w >= 0) {   // x1 carry into ghost slot ti.w of the next iteration
+                const size_t gxo = ((((size_t)(par ^ 1) * 8 + q) * P->ns1 + ti.w) * n3 * n2) * 2 * NL;
                 for (int kk = 0; kk < nr3; ++kk)
                     for (int jj = 0; jj < nr2; ++jj) {
                         const size_t row = (size_t)(k0 + kk) * n2 + (j0 + jj);
@@ -463,32 +481,39 @@ size_t sweep3d_f32x2_smem(int T1, int NW, int R2, int R3) {
 
 int sweep3d_f32x2_velocities_per_lane() { return 2; }
 
-template <int T1, bool BF>
+template <int T1, bool BF, bool SUB>
 static cudaError_t launch_t(const SweepArgs3D<float>& a, int grid, int NW, cudaStream_t st) {
     const size_t smem = sweep3d_f32x2_smem(T1, NW, a.maxR2, a.maxR3);
-    cudaError_t e = cudaFuncSetAttribute(sweep3d_f32x2_kernel<T1, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(sweep3d_f32x2_kernel<T1, BF, SUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    sweep3d_f32x2_kernel<T1, BF><<<grid, NW * 32, smem, st>>>(a);
+    sweep3d_f32x2_kernel<T1, BF, SUB><<<grid, NW * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
+// instantiations: FP32 and BF16 storage without subdomains, FP32 with subdomains
 cudaError_t launch_sweep3d_f32x2(const SweepArgs3D<float>& a, int grid, int NW, cudaStream_t st) {
-    if (a.T1 == 4) return a.bf16 ? launch_t<4, true>(a, grid, NW, st) : launch_t<4, false>(a, grid, NW, st);
-    if (a.T1 == 8) return a.bf16 ? launch_t<8, true>(a, grid, NW, st) : launch_t<8, false>(a, grid, NW, st);
+    if (a.sub && a.bf16) return cudaErrorInvalidValue;
+    if (a.T1 == 4) return a.sub ? launch_t<4, false, true>(a, grid, NW, st)
+                                : (a.bf16 ? launch_t<4, true, false>(a, grid, NW, st) : launch_t<4, false, false>(a, grid, NW, st));
+    if (a.T1 == 8) return a.sub ? launch_t<8, false, true>(a, grid, NW, st)
+                                : (a.bf16 ? launch_t<8, true, false>(a, grid, NW, st) : launch_t<8, false, false>(a, grid, NW, st));
     return cudaErrorInvalidValue;
 }
 
-template <int T1, bool BF>
+template <int T1, bool BF, bool SUB>
 static cudaError_t occ_t(int NW, int R2, int R3, int* blocks_per_sm) {
     const size_t smem = sweep3d_f32x2_smem(T1, NW, R2, R3);
-    cudaError_t e = cudaFuncSetAttribute(sweep3d_f32x2_kernel<T1, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(sweep3d_f32x2_kernel<T1, BF, SUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep3d_f32x2_kernel<T1, BF>, NW * 32, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep3d_f32x2_kernel<T1, BF, SUB>, NW * 32, smem);
 }
 
-cudaError_t sweep3d_f32x2_occupancy(int T1, int NW, int R2, int R3, int bf16, int* blocks_per_sm) {
-    if (T1 == 4) return bf16 ? occ_t<4, true>(NW, R2, R3, blocks_per_sm) : occ_t<4, false>(NW, R2, R3, blocks_per_sm);
-    if (T1 == 8) return bf16 ? occ_t<8, true>(NW, R2, R3, blocks_per_sm) : occ_t<8, false>(NW, R2, R3, blocks_per_sm);
+cudaError_t sweep3d_f32x2_occupancy(int T1, int NW, int R2, int R3, int bf16, int sub, int* blocks_per_sm) {
+    if (sub && bf16) return cudaErrorInvalidValue;
+    if (T1 == 4) return sub ? occ_t<4, false, true>(NW, R2, R3, blocks_per_sm)
+                            : (bf16 ? occ_t<4, true, false>(NW, R2, R3, blocks_per_sm) : occ_t<4, false, false>(NW, R2, R3, blocks_per_sm));
+    if (T1 == 8) return sub ? occ_t<8, false, true>(NW, R2, R3, blocks_per_sm)
+                            : (bf16 ? occ_t<8, true, false>(NW, R2, R3, blocks_per_sm) : occ_t<8, false, false>(NW, R2, R3, blocks_per_sm));
     return cudaErrorInvalidValue;
 }
 

@@ -156,10 +156,7 @@ def test_x1_subdomains_warm_start_and_fp32_tiles():
 def test_subdomain_options_are_validated():
     mask = inputs.cylinder_cell(16, 0.7)
     (v, w), _ = _grid(2, 4)
-    for sub in ((9, 1, 1), (1, 9, 1), (1, 1, 2), (1, -1, 1)):
+    for sub in ((9, 1, 1), (1, 9, 1), (1, 1, 2), (1, -1, 1)):   # (1, 1, 2): a 2D problem has no x3
         with pytest.raises(dvm.DvmError):
             dvm.Solver(mask, 0.2, v, w, subdomains=sub)
-    rock = inputs.gaussian_rock(8, seed=1, corr_len=1.5, porosity=0.6)
-    v3, w3 = dvm.dvm_gh_velocity_grid(3, 4)
-    with pytest.raises(dvm.DvmError):
-        dvm.Solver(rock, 0.2, v3, w3, subdomains=(1, 2, 1))
+
