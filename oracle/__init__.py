@@ -42,6 +42,7 @@ class _Cfg(ctypes.Structure):
         ("form", ctypes.c_int),
         ("traversal", ctypes.c_int),
         ("dec", ctypes.c_int * 3),
+        ("tau", ctypes.c_int),
     ]
 
 
@@ -71,7 +72,7 @@ def _load():
             lib.ora_iter.argtypes = [ctypes.c_void_p]
             for f in ("ora_get_moments",):
                 getattr(lib, f).argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
-            for f in ("ora_get_wall", "ora_get_flux"):
+            for f in ("ora_get_wall", "ora_get_flux", "ora_get_tau"):
                 getattr(lib, f).argtypes = [ctypes.c_void_p, ctypes.c_void_p]
             lib.ora_set_uniform.argtypes = [ctypes.c_void_p, ctypes.c_double]
             lib.ora_set_initial.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
@@ -93,10 +94,12 @@ class Oracle:
     order: 2 (Eq. 9 default) or 1.
     traversal: "raster" (the paper's raster scan) or "wavefront".
     decomposition: subdomain counts (c1, c2[, c3]) of the lagged-halo Omega_x decomposition.
+    tau: keep the temperature term tau (|v|^2 - 3/2) of Eq. 2 with tau from Eq. 4 (3D only; the
+    paper drops it for its isothermal flows).
     """
 
     def __init__(self, solid, kn, v, w, *, jump=1.0, order=2, lateral="specular", form="jump",
-                 traversal="raster", decomposition=(1, 1, 1), threads=0):
+                 traversal="raster", decomposition=(1, 1, 1), threads=0, tau=False):
         lib = _load()
         solid = np.ascontiguousarray(np.asarray(solid).astype(np.uint8))
         if solid.ndim not in (2, 3):
@@ -126,6 +129,7 @@ class Oracle:
         dec = tuple(decomposition) + (1,) * (3 - len(decomposition))
         for j in range(3):
             cfg.dec[j] = int(dec[j])
+        cfg.tau = 1 if tau else 0
         self._cfg = cfg
         self._h = lib.ora_create(ctypes.byref(cfg))
         if not self._h:
@@ -179,6 +183,12 @@ class Oracle:
         out = np.zeros(self.solid.size * self.dims * 2)
         self._lib.ora_get_wall(self._h, _ptr(out))
         return out.reshape((self.dims, 2) + self.shape)
+
+    def temperature(self):
+        """Temperature tau of Eq. 4 [shape] (zero without the tau option; solid = 0)."""
+        out = np.zeros(self.solid.size)
+        self._lib.ora_get_tau(self._h, _ptr(out))
+        return out.reshape(self.shape)
 
     def flux(self):
         """x1 face fluxes sum_{cross-section} sum_k W_k v1 h_upwind of the last iteration [n1]."""

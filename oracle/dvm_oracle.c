@@ -15,7 +15,9 @@
  *         either upstream point of that stencil along the axis is solid;
  *   (ii)  boundary data for the next iteration: diffuse walls (Eq. 5 with alpha = 1), the pressure
  *         jump periodic condition in x1 (Eq. 7), specular (Eq. 8) or periodic lateral faces;
- *   (iii) moments rho, u (Eq. 4, tau omitted as in Sec. 4) and wall densities (Eq. 6);
+ *   (iii) moments rho, u (Eq. 4) and wall densities (Eq. 6); the temperature tau of Eq. 4 and its
+ *         source term tau (|v|^2 - 3/2) in Eq. 2 / Eq. 10 are dropped as in Sec. 4 unless the tau
+ *         option is set (3D only: Eq. 2 and Eq. 4 are written for three velocity components);
  *   (iv)  permeability k = (2/sqrt(pi)) Kn G_p (Eq. 11-12);
  *   (v)   Err of Eq. 15 is formed by the caller from the k history.
  * Moments, wall densities and all boundary (ghost) data used in a sweep are those of the previous
@@ -75,6 +77,7 @@ typedef struct {
     int form;              /* 0 jump form (paper), 1 source form */
     int traversal;         /* 0 raster scan (paper), 1 wavefront over hyperplanes */
     int dec[3];            /* subdomain counts c1, c2, c3 of the lagged-halo decomposition */
+    int tau;               /* 1: keep the temperature term of Eq. 2 (3D only); 0: drop it (Sec. 4) */
 } ora_cfg;
 
 typedef struct {
@@ -86,6 +89,8 @@ typedef struct {
     int* refl;             /* [3][nv] index of the velocity reflected in axis j */
     double dface[3][2];    /* Eq. 6 denominator per (axis, side) */
     double *rho, *u;       /* [N], [d][N] (stored in the working form's variables) */
+    double* tau;           /* [N] temperature of Eq. 4 (the same in both forms), with the tau option */
+    double sw2;            /* sum_k W_k |v_k|^2 (3/2 when the rule integrates v^2 exactly) */
     double* rhos;          /* [d][2][N] wall density of face (x, j, side) ; side 0: -1, 1: +1 */
     int area[3];           /* transverse face area per axis */
     double* lag[2];        /* [nv][d][2 layers][area] lagged ghost values, current / next */
@@ -185,6 +190,11 @@ static void point_update(const ora* o, int k, const int c[3], double* h) {
     double dot = 0.0;
     for (int j = 0; j < o->d; ++j) dot += o->u[(size_t)j * o->N + id] * vk[j];
     double num = o->nu * (o->rho[id] + 2.0 * dot);
+    if (o->c.tau) {
+        double vv = 0.0;
+        for (int j = 0; j < o->d; ++j) vv += vk[j] * vk[j];
+        num += o->nu * o->tau[id] * (vv - 1.5);
+    }
     if (o->c.form == 1) num += o->J * vk[0];
     double den = o->nu;
     for (int j = 0; j < o->d; ++j) {
@@ -277,6 +287,7 @@ static void init_state(ora* o) {
     /* h = 0 (jump form) everywhere; in the source form h' = J x1 */
     size_t N = o->N;
     memset(o->u, 0, sizeof(double) * N * o->d);
+    memset(o->tau, 0, sizeof(double) * N);   /* tau of h = 0 */
     for (int id = 0; id < o->N; ++id) {
         int i1 = id % o->n1;
         double x1 = (o->c.form == 1) ? o->J * i1 * o->dx : 0.0;
@@ -321,6 +332,7 @@ static void init_state(ora* o) {
 
 ora* ora_create(const ora_cfg* cfg) {
     if (!cfg || (cfg->dims != 2 && cfg->dims != 3) || cfg->nv <= 0 || cfg->kn <= 0) return NULL;
+    if (cfg->tau && cfg->dims != 3) return NULL;
     ora* o = (ora*)calloc(1, sizeof(ora));
     o->c = *cfg;
     o->d = cfg->dims;
@@ -341,6 +353,9 @@ ora* ora_create(const ora_cfg* cfg) {
     o->nu = sqrt(M_PI) / (2.0 * cfg->kn);     /* collision frequency of Eq. 3 */
     o->dx = 1.0 / o->n1;                       /* L = x1 extent (Sec. 2.1) */
     o->J = cfg->jump;
+    o->sw2 = 0.0;
+    for (int k = 0; k < o->nv; ++k)
+        for (int j = 0; j < o->d; ++j) o->sw2 += o->w[k] * o->v[(size_t)k * o->d + j] * o->v[(size_t)k * o->d + j];
     o->refl = (int*)malloc(sizeof(int) * 3 * o->nv);
     for (int j = 0; j < 3; ++j)
         for (int k = 0; k < o->nv; ++k) {
@@ -368,6 +383,7 @@ ora* ora_create(const ora_cfg* cfg) {
         }
     o->rho = (double*)calloc(o->N, sizeof(double));
     o->u = (double*)calloc((size_t)o->N * o->d, sizeof(double));
+    o->tau = (double*)calloc(o->N, sizeof(double));
     o->rhos = (double*)calloc((size_t)o->N * o->d * 2, sizeof(double));
     o->area[0] = o->n2 * o->n3;
     o->area[1] = o->n1 * o->n3;
@@ -410,7 +426,7 @@ ora* ora_create(const ora_cfg* cfg) {
 void ora_destroy(ora* o) {
     if (!o) return;
     free(o->solid); free(o->v); free(o->w); free(o->refl);
-    free(o->rho); free(o->u); free(o->rhos);
+    free(o->rho); free(o->u); free(o->tau); free(o->rhos);
     free(o->lag[0]); free(o->lag[1]);
     free(o->full[0]); free(o->full[1]);
     for (int j = 0; j < 3; ++j) free(o->sub[j]);
@@ -439,12 +455,24 @@ static double upwind_face_value(const ora* o, int k, const int c[3], int i, cons
 }
 
 /* One iteration (steps i-iii).  Returns 0. */
+/* tau = (2/3) sum W |v|^2 h - rho (Eq. 4) at every fluid point from e = sum W |v|^2 h and the new
+ * rho, both in the working variables.  In the source form h' = h + J x1, so
+ * tau = (2/3) e' - rho' + J x1 (1 - (2/3) sum W |v|^2): the paper's tau in either form. */
+static void update_tau(ora* o, const double* e) {
+    for (int id = 0; id < o->N; ++id) {
+        if (o->solid[id]) { o->tau[id] = 0.0; continue; }
+        double x1 = (o->c.form == 1) ? o->J * (id % o->n1) * o->dx : 0.0;
+        o->tau[id] = 2.0 / 3.0 * e[id] - o->rho[id] + x1 * (1.0 - 2.0 / 3.0 * o->sw2);
+    }
+}
+
 static void iterate_once(ora* o) {
     const size_t N = o->N;
     const int d = o->d;
     double* rho_n = (double*)calloc(N, sizeof(double));
     double* u_n = (double*)calloc(N * d, sizeof(double));
     double* num_n = (double*)calloc(N * d * 2, sizeof(double));
+    double* e_n = (double*)calloc(N, sizeof(double));          /* sum W |v|^2 h (tau option) */
     memset(o->flux, 0, sizeof(double) * o->n1);
     for (int g0 = 0; g0 < o->nv; g0 += ORA_GROUP) {
         int gn = o->nv - g0 < ORA_GROUP ? o->nv - g0 : ORA_GROUP;
@@ -465,6 +493,11 @@ static void iterate_once(ora* o) {
                 double hk = o->H[(size_t)kk * N + id];
                 double wk = o->w[k];
                 rho_n[id] += wk * hk;
+                if (o->c.tau) {
+                    double vv = 0.0;
+                    for (int j = 0; j < d; ++j) vv += o->v[(size_t)k * d + j] * o->v[(size_t)k * d + j];
+                    e_n[id] += wk * vv * hk;
+                }
                 for (int j = 0; j < d; ++j) {
                     double vj = o->v[(size_t)k * d + j];
                     u_n[(size_t)j * N + id] += wk * vj * hk;
@@ -501,9 +534,10 @@ static void iterate_once(ora* o) {
                 o->rhos[((size_t)j * 2 + sd) * N + id] = num_n[((size_t)j * 2 + sd) * N + id] / o->dface[j][sd];
     memcpy(o->rho, rho_n, sizeof(double) * N);
     memcpy(o->u, u_n, sizeof(double) * N * d);
+    if (o->c.tau) update_tau(o, e_n);
     double* t = o->lag[0]; o->lag[0] = o->lag[1]; o->lag[1] = t;
     if (o->decomposed) { t = o->full[0]; o->full[0] = o->full[1]; o->full[1] = t; }
-    free(rho_n); free(u_n); free(num_n);
+    free(rho_n); free(u_n); free(num_n); free(e_n);
     o->iter++;
 }
 
@@ -550,6 +584,9 @@ void ora_get_wall(const ora* o, double* rhos) {
 
 void ora_get_flux(const ora* o, double* flux) { memcpy(flux, o->flux, sizeof(double) * o->n1); }
 
+/* Temperature tau of Eq. 4 [N] (zero without the tau option and at solid points). */
+void ora_get_tau(const ora* o, double* tau) { memcpy(tau, o->tau, sizeof(double) * o->N); }
+
 /* Overwrite the state with a uniform value c in the working variables (jump = 0 tests). */
 void ora_set_uniform(ora* o, double c) {
     for (int id = 0; id < o->N; ++id) {
@@ -559,6 +596,7 @@ void ora_set_uniform(ora* o, double c) {
             for (int sd = 0; sd < 2; ++sd)
                 o->rhos[((size_t)j * 2 + sd) * o->N + id] = (o->facemask[id] >> (2 * j + sd) & 1) ? c : 0.0;
     }
+    for (int id = 0; id < o->N; ++id) o->tau[id] = o->solid[id] ? 0.0 : c * (2.0 / 3.0 * o->sw2 - 1.0);
     size_t lagsz = (size_t)o->nv * o->d * 2 * o->area[0];
     for (size_t i = 0; i < lagsz; ++i) o->lag[0][i] = c;
     if (o->decomposed)
@@ -580,8 +618,11 @@ void ora_set_initial(ora* o, const double* rho0, const double* u0) {
     double* rho_n = (double*)calloc(N, sizeof(double));
     double* u_n = (double*)calloc(N * d, sizeof(double));
     double* num_n = (double*)calloc(N * d * 2, sizeof(double));
+    double* e_n = (double*)calloc(N, sizeof(double));
     for (int k = 0; k < o->nv; ++k) {
         const double* vk = o->v + (size_t)k * d;
+        double vv = 0.0;
+        for (int j = 0; j < d; ++j) vv += vk[j] * vk[j];
         for (size_t id = 0; id < N; ++id) {
             if (o->solid[id]) { h[id] = 0.0; continue; }
             double dot = 0.0;
@@ -595,6 +636,7 @@ void ora_set_initial(ora* o, const double* rho0, const double* u0) {
             if (o->solid[id]) continue;
             double wk = o->w[k];
             rho_n[id] += wk * h[id];
+            e_n[id] += wk * vv * h[id];
             for (int j = 0; j < d; ++j) u_n[(size_t)j * N + id] += wk * vk[j] * h[id];
             for (int j = 0; j < d; ++j)
                 for (int sd = 0; sd < 2; ++sd) {
@@ -610,9 +652,10 @@ void ora_set_initial(ora* o, const double* rho0, const double* u0) {
                 o->rhos[((size_t)j * 2 + sd) * N + id] = num_n[((size_t)j * 2 + sd) * N + id] / o->dface[j][sd];
     memcpy(o->rho, rho_n, sizeof(double) * N);
     memcpy(o->u, u_n, sizeof(double) * N * d);
+    if (o->c.tau) update_tau(o, e_n);
     double* t = o->lag[0]; o->lag[0] = o->lag[1]; o->lag[1] = t;
     if (o->decomposed) { t = o->full[0]; o->full[0] = o->full[1]; o->full[1] = t; }
-    free(h); free(rho_n); free(u_n); free(num_n);
+    free(h); free(rho_n); free(u_n); free(num_n); free(e_n);
 }
 
 /* One sweep of velocity k from the current state, without updating the state (point-update

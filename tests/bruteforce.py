@@ -20,7 +20,9 @@ import math
 import numpy as np
 
 
-def solve_dense(solid, kn, v, w, jump=1.0, order=2, lateral="specular"):
+def solve_dense(solid, kn, v, w, jump=1.0, order=2, lateral="specular", tau=False):
+    """tau: keep the temperature term tau (|v|^2 - 3/2) of Eq. 2 with tau = (2/3) sum W |v|^2 h - rho
+    (Eq. 4), a linear functional of the unknowns at the same point like rho and u."""
     solid = np.asarray(solid, dtype=bool)
     dims = solid.ndim
     shape = solid.shape
@@ -101,9 +103,12 @@ def solve_dense(solid, kn, v, w, jump=1.0, order=2, lateral="specular"):
     for f, c in enumerate(fluid_coords):
         for k in range(nv):
             row = col(f, k)
-            # -nu (rho + 2 u.v_k)
+            # -nu (rho + 2 u.v_k [+ tau (|v_k|^2 - 3/2)])
+            vk2 = float(np.dot(v[k], v[k]))
             for kk in range(nv):
                 cv = nu * w[kk] * (1.0 + 2.0 * float(np.dot(v[kk], v[k])))
+                if tau:
+                    cv += nu * w[kk] * (2.0 / 3.0 * float(np.dot(v[kk], v[kk])) - 1.0) * (vk2 - 1.5)
                 A[row, col(f, kk)] -= cv
                 lag1[row] -= cv
             diag = nu
@@ -139,10 +144,15 @@ def solve_dense(solid, kn, v, w, jump=1.0, order=2, lateral="specular"):
     H = sol[:U].reshape(nf, nv)
     rho = np.zeros(shape)
     u = np.zeros((dims,) + shape)
+    temp = np.zeros(shape)
+    vv = (v * v).sum(axis=1)
     for f, c in enumerate(fluid_coords):
         rho[arr_index(c)] = float(np.dot(w, H[f]))
+        temp[arr_index(c)] = 2.0 / 3.0 * float(np.dot(w * vv, H[f])) - rho[arr_index(c)]
         for j in range(dims):
             u[(j,) + arr_index(c)] = float(np.dot(w * v[:, j], H[f]))
     k_perm = 2.0 / math.sqrt(math.pi) * kn * float(u[0].sum() / u[0].size)
     resid = float(np.abs(A[:U] @ sol - b[:U]).max())
+    if tau:
+        return rho, u, k_perm, resid, delta, temp
     return rho, u, k_perm, resid, delta
