@@ -113,6 +113,12 @@ typedef struct {
      * and for a fixed choice they are the same bits for every tile and pencil shape).  Ignored in
      * 2D. */
     int group_warps;
+    /* Nonzero (3D only): keep the temperature term of the linearised BGK equation (Eq. 2): the
+     * source gains tau (|v|^2 - 3/2) with the temperature perturbation tau = (2/3) sum_k W_k
+     * |v_k|^2 h - rho (Eq. 4).  The paper drops it (Sec. 4: no influence on the permeability of its
+     * isothermal flows); the walls re-emit at the wall temperature either way (Eq. 5).  0 (default):
+     * dropped.  2D problems and BF16 storage reject it with DVM_EINVAL. */
+    int temperature_term;
 } dvm_options;
 
 /* Fill *opt with the defaults: FP64, second order, specular lateral faces, check interval 100,
@@ -160,6 +166,11 @@ dvm_status dvm_sync(dvm_ctx* ctx);
  * on_device != 0 means rho and u are device pointers. */
 dvm_status dvm_moments(dvm_ctx* ctx, double* rho, double* u, int on_device);
 dvm_status dvm_moments_at(dvm_ctx* ctx, int prob, double* rho, double* u, int on_device);
+
+/* Temperature perturbation tau of Eq. 4 of problem prob after the last iteration, [N] doubles (solid
+ * points 0), with the temperature term enabled (dvm_options.temperature_term); on_device != 0 means
+ * tau is a device pointer.  EINVAL when the term is off. */
+dvm_status dvm_temperature_at(dvm_ctx* ctx, int prob, double* tau, int on_device);
 
 /* Permeability k = (2/sqrt(pi)) Kn G_p (Eq. 11) and G_p, the mean of u1 over all points (Eq. 12:
  * the cross-section mean, averaged over every x1 cross-section), of the last iteration. */

@@ -38,20 +38,21 @@ int sweep2d_f32x2_max_rows(int T1, int NW);
 cudaError_t launch_sweep2d_pair(const SweepArgs2D<float>&, int T1, int grid, int NW, cudaStream_t);
 cudaError_t sweep2d_pair_occupancy(int T1, int NW, int max_rows, int NL, int* blocks_per_sm);
 int sweep2d_f32x2_velocities_per_lane();
-template <typename T> size_t sweep3d_smem(int T1, int NW, int R2, int R3);
-size_t sweep3d_f32x2_smem(int T1, int NW, int R2, int R3);
+template <typename T> size_t sweep3d_smem(int T1, int NW, int R2, int R3, int tau);
+size_t sweep3d_f32x2_smem(int T1, int NW, int R2, int R3, int tau);
 int sweep3d_f32x2_velocities_per_lane();
 cudaError_t launch_sweep3d_f32x2(const SweepArgs3D<float>&, int grid, int NW, cudaStream_t);
-cudaError_t sweep3d_f32x2_occupancy(int T1, int NW, int R2, int R3, int bf16, int sub, int* blocks_per_sm);
-template <typename T> cudaError_t sweep3d_occupancy(int T1, int NW, int R2, int R3, int bf16, int sub, int* blocks_per_sm);
+cudaError_t sweep3d_f32x2_occupancy(int T1, int NW, int R2, int R3, int bf16, int sub, int tau, int* blocks_per_sm);
+template <typename T> cudaError_t sweep3d_occupancy(int T1, int NW, int R2, int R3, int bf16, int sub, int tau, int* blocks_per_sm);
 template <typename T> cudaError_t launch_sweep3d(const SweepArgs3D<T>&, int grid, int NW, cudaStream_t);
 template <typename T> cudaError_t launch_finalize3d(const FinArgs3D<T>&, int nblocks, cudaStream_t);
-template <typename T> cudaError_t launch_init3d(const Prob3D<T>*, int NL, const double* qw, cudaStream_t);
+template <typename T> cudaError_t launch_init3d(const Prob3D<T>*, int NL, const double* qw, const double* qwt, cudaStream_t);
 template <typename T> cudaError_t launch_moments3d(const Prob3D<T>*, double* rho, double* u, cudaStream_t);
+template <typename T> cudaError_t launch_temperature3d(const Prob3D<T>*, double* tau, cudaStream_t);
 template <typename T> cudaError_t launch_wall3d(const Prob3D<T>*, double* out, cudaStream_t);
 template <typename T>
-cudaError_t launch_warm3d(const Prob3D<T>*, int NL, int par, const double* qw2, const double* vel, const double* rho0,
-                          const double* u0, cudaStream_t);
+cudaError_t launch_warm3d(const Prob3D<T>*, int NL, int par, const double* qw2, const double* qwt, const double* vel,
+                          const double* rho0, const double* u0, cudaStream_t);
 }  // namespace dvm
 
 using namespace dvm;
@@ -86,6 +87,8 @@ struct dvm_ctx {
     bool xsub = false;               // 2D x1 subdomains (tile tables, lagged x1 halos)
     bool pairs = false;              // 2D FP32: two consecutive bands per CTA
     bool sub3 = false;               // 3D lagged-halo subdomains (pencil and tile tables)
+    bool tau3 = false;               // 3D temperature term of Eq. 2
+    double* qwt_dev = nullptr;       // 3D: [octant][group][4] sums of W |v|^2 (1, v)
     int T1 = 8, rows = 8, max_rows = 8;
     std::vector<HostProb> hp;
     std::vector<Buf> bufs;
@@ -635,8 +638,8 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         if (smem_max <= 0) smem_max = 227 * 1024;
         const size_t lim = (size_t)smem_max - 1024;
         auto smem_of = [&]() -> size_t {
-            if constexpr (std::is_same<T, float>::value) return sweep3d_f32x2_smem(c->T1, c->NW, c->R2, c->R3);
-            else return sweep3d_smem<T>(c->T1, c->NW, c->R2, c->R3);
+            if constexpr (std::is_same<T, float>::value) return sweep3d_f32x2_smem(c->T1, c->NW, c->R2, c->R3, c->tau3);
+            else return sweep3d_smem<T>(c->T1, c->NW, c->R2, c->R3, c->tau3);
         };
         while (smem_of() > lim) {
             if (c->T1 > 4) c->T1 = 4;
@@ -667,7 +670,8 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
                 for (int j = 0; j < 3; ++j) d[1 + j] += grid->w[k] * grid->v[3 * k + j];
             }
     // ---- warm-start tables: lane velocities and group sums of W phi_m psi_n, phi = psi = (1, v)
-    std::vector<double> qw2((size_t)NO * G * 4 * 4, 0.0), vel((size_t)NO * NL * 3, 0.0);
+    // (qwt: the same with phi = |v|^2, for the temperature term; sw2 = sum of W |v|^2 over the grid)
+    std::vector<double> qw2((size_t)NO * G * 4 * 4, 0.0), vel((size_t)NO * NL * 3, 0.0), qwt((size_t)NO * G * 4, 0.0);
     for (int q = 0; q < NO; ++q)
         for (int m = 0; m < nvo; ++m) {
             const int k = group[q][m];
@@ -677,17 +681,24 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
             for (int a = 0; a < 4; ++a)
                 for (int b2 = 0; b2 < 4; ++b2)
                     qw2[(((size_t)q * G + gg) * 4 + a) * 4 + b2] += grid->w[k] * ph[a] * ph[b2];
+            const double vv = ph[1] * ph[1] + ph[2] * ph[2] + ph[3] * ph[3];
+            for (int b2 = 0; b2 < 4; ++b2) qwt[((size_t)q * G + gg) * 4 + b2] += grid->w[k] * vv * ph[b2];
         }
+    double sw2 = 0.0;
+    for (int k = 0; k < grid->nv; ++k)
+        for (int j = 0; j < 3; ++j) sw2 += grid->w[k] * grid->v[3 * k + j] * grid->v[3 * k + j];
     c->qw2_dev = (double*)dev_alloc(c, qw2.size() * sizeof(double));
     c->vel_dev = (double*)dev_alloc(c, vel.size() * sizeof(double));
-    if (!c->qw2_dev || !c->vel_dev) return fail(c, DVM_ENOMEM, "device allocation failed");
+    c->qwt_dev = (double*)dev_alloc(c, qwt.size() * sizeof(double));
+    if (!c->qw2_dev || !c->vel_dev || !c->qwt_dev) return fail(c, DVM_ENOMEM, "device allocation failed");
     {
         cudaError_t e;
         if ((e = cudaMemcpyAsync(c->qw2_dev, qw2.data(), qw2.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream)) ||
             (e = cudaMemcpyAsync(c->vel_dev, vel.data(), vel.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream)) ||
+            (e = cudaMemcpyAsync(c->qwt_dev, qwt.data(), qwt.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream)) ||
             (e = cudaStreamSynchronize(c->stream)))
             return cuda_fail(c, e, "upload warm-start tables");
-        c->h2d_bytes += (qw2.size() + vel.size()) * sizeof(double);
+        c->h2d_bytes += (qw2.size() + vel.size() + qwt.size()) * sizeof(double);
     }
     std::vector<Prob3D<T>> probs(c->nprob);
     std::vector<SweepItem3> items;
@@ -756,6 +767,13 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         P.src = (T*)dev_alloc(c, N * 4 * sizeof(T));
         P.E = (T*)dev_alloc(c, N * 8 * sizeof(T));
         P.P = (T*)dev_alloc(c, (size_t)NO * G * 4 * N * sizeof(T));
+        P.tau = c->tau3 ? 1 : 0;
+        P.sw2 = sw2;
+        if (P.tau) {
+            P.Pt = (T*)dev_alloc(c, (size_t)NO * G * N * sizeof(T));
+            P.srct = (T*)dev_alloc(c, N * sizeof(T));
+            if (!P.Pt || !P.srct) return fail(c, DVM_ENOMEM, "device allocation failed");
+        }
         P.bf16 = c->bf16 ? 1 : 0;
         const size_t es = c->bf16 ? 2 : sizeof(T);     // bytes per stored ghost / edge value
         P.gx1 = (T*)dev_alloc(c, (size_t)2 * NO * P.ns1 * n3 * n2 * 2 * NL * es);
@@ -809,6 +827,9 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
                     d[7 + j] = (T)(w * v[j]);
                 }
                 d[6] = (T)w;
+                const double vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+                d[18] = (T)(vv - 1.5);    // temperature term: |v|^2 - 3/2 and W |v|^2
+                d[19] = (T)(w * vv);
                 for (int rs = 0; rs < 8; ++rs) {
                     double den = H.nu;
                     for (int j = 0; j < 3; ++j) den += (((rs >> j) & 1) ? 1.0 : c0o) * av[j];
@@ -869,8 +890,9 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
                     qw.size() * sizeof(double) + probs.size() * sizeof(Prob3D<T>);
     c->probs_host.assign((const char*)probs.data(), (const char*)probs.data() + probs.size() * sizeof(Prob3D<T>));
     int per_sm = 0;
-    if constexpr (std::is_same<T, float>::value) e = sweep3d_f32x2_occupancy(c->T1, c->NW, mr2, mr3, c->bf16 ? 1 : 0, c->sub3 ? 1 : 0, &per_sm);
-    else e = sweep3d_occupancy<T>(c->T1, c->NW, mr2, mr3, 0, c->sub3 ? 1 : 0, &per_sm);
+    if constexpr (std::is_same<T, float>::value)
+        e = sweep3d_f32x2_occupancy(c->T1, c->NW, mr2, mr3, c->bf16 ? 1 : 0, c->sub3 ? 1 : 0, c->tau3 ? 1 : 0, &per_sm);
+    else e = sweep3d_occupancy<T>(c->T1, c->NW, mr2, mr3, 0, c->sub3 ? 1 : 0, c->tau3 ? 1 : 0, &per_sm);
     if (e != cudaSuccess) return cuda_fail(c, e, "occupancy");
     if (per_sm < 1) return fail(c, DVM_EINVAL, "3D sweep kernel does not fit on an SM with these pencils");
     int dev = 0, sms = 0;
@@ -879,7 +901,7 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     c->sweep_grid = std::max(1, std::min(c->nitems, per_sm * sms));
     for (int b = 0; b < c->nprob; ++b) {
         const Prob3D<T>* pd = (const Prob3D<T>*)c->probs_dev + b;
-        e = launch_init3d<T>(pd, NL, c->qw_dev + (size_t)b * NO * G * 4, c->stream);
+        e = launch_init3d<T>(pd, NL, c->qw_dev + (size_t)b * NO * G * 4, c->qwt_dev, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
     }
     FinArgs3D<T> fa{(const Prob3D<T>*)c->probs_dev, c->blk_prob_dev, c->blk_start_dev, c->status_dev};
@@ -969,6 +991,7 @@ dvm_status enqueue_iter_3d(dvm_ctx* c) {
     a.maxR3 = c->max_rows % 1000;
     a.bf16 = c->bf16 ? 1 : 0;
     a.sub = c->sub3 ? 1 : 0;
+    a.tau = c->tau3 ? 1 : 0;
     a.parity = (int)(c->iters & 1);
     a.ticket = c->counters_dev;
     a.status = c->status_dev;
@@ -1104,6 +1127,7 @@ void state_segs_3d(const Prob3D<T>& P, size_t NL, int par, std::vector<Seg>& out
     const size_t gz = (size_t)8 * P.ns3 * P.n2 * P.n1 * 2 * NL;
     const size_t es = P.bf16 ? 2 : sizeof(T);
     out.push_back({P.P, (size_t)8 * P.ngroups * 4 * P.N * sizeof(T)});
+    if (P.tau) out.push_back({P.Pt, (size_t)8 * P.ngroups * P.N * sizeof(T)});
     out.push_back({(char*)P.gx1 + par * gx * es, gx * es});
     out.push_back({(char*)P.gy + par * gy * es, gy * es});
     out.push_back({(char*)P.gz + par * gz * es, gz * es});
@@ -1253,6 +1277,11 @@ dvm_status dvm_create_batch(int nprob, const dvm_geometry* geoms, const double* 
     c->sub3 = dims == 3 && (c->opt.subdomains[0] > 1 || c->opt.subdomains[1] > 1 || c->opt.subdomains[2] > 1);
     if (c->sub3 && c->opt.precision == DVM_BF16_STORE)
         return reject(DVM_EINVAL, "BF16 storage is not implemented with subdomains");
+    if (c->opt.temperature_term && dims != 3)
+        return reject(DVM_EINVAL, "the temperature term is implemented for 3D problems (Eq. 2 has three velocity components)");
+    if (c->opt.temperature_term && c->opt.precision == DVM_BF16_STORE)
+        return reject(DVM_EINVAL, "BF16 storage is not implemented with the temperature term");
+    c->tau3 = dims == 3 && c->opt.temperature_term != 0;
     if (c->opt.group_warps < 0) return reject(DVM_EINVAL, "group_warps must not be negative");
     if (c->opt.band_pairs && (dims != 2 || c->opt.precision != DVM_FP32 || c->opt.subdomains[0] > 1 ||
                               c->opt.subdomains[1] > 1))
@@ -1411,6 +1440,25 @@ dvm_status dvm_moments(dvm_ctx* c, double* rho, double* u, int on_device) {
     return dvm_moments_at(c, 0, rho, u, on_device);
 }
 
+dvm_status dvm_temperature_at(dvm_ctx* c, int prob, double* tau, int on_device) {
+    if (!c || prob < 0 || prob >= c->nprob || !tau) return DVM_EINVAL;
+    if (!c->tau3) return fail(c, DVM_EINVAL, "the temperature term is not enabled");
+    const size_t N = c->hp[prob].N;
+    double* dt = on_device ? tau : c->scratch_dev;
+    cudaError_t e;
+    if (c->prec == DVM_FP32) e = launch_temperature3d<float>((const Prob3D<float>*)c->probs_dev + prob, dt, c->stream);
+    else e = launch_temperature3d<double>((const Prob3D<double>*)c->probs_dev + prob, dt, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "temperature kernel");
+    if (!on_device) {
+        if ((e = cudaMemcpyAsync(tau, dt, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+            return cuda_fail(c, e, "read temperature");
+        c->d2h_bytes += (long long)N * sizeof(double);
+    }
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "temperature");
+    return DVM_OK;
+}
+
 dvm_status dvm_wall_density_at(dvm_ctx* c, int prob, double* rhos) {
     if (!c || prob < 0 || prob >= c->nprob || !rhos) return DVM_EINVAL;
     const size_t N = c->hp[prob].N;
@@ -1539,9 +1587,9 @@ dvm_status dvm_set_initial_at(dvm_ctx* c, int prob, const double* rho0, const do
     const int par = (int)(c->iters & 1);
     if (c->dims == 3) {
         if (c->prec == DVM_FP32)
-            e = launch_warm3d<float>((const Prob3D<float>*)c->probs_dev + prob, c->NL, par, c->qw2_dev, c->vel_dev, d_rho, d_u, c->stream);
+            e = launch_warm3d<float>((const Prob3D<float>*)c->probs_dev + prob, c->NL, par, c->qw2_dev, c->qwt_dev, c->vel_dev, d_rho, d_u, c->stream);
         else
-            e = launch_warm3d<double>((const Prob3D<double>*)c->probs_dev + prob, c->NL, par, c->qw2_dev, c->vel_dev, d_rho, d_u, c->stream);
+            e = launch_warm3d<double>((const Prob3D<double>*)c->probs_dev + prob, c->NL, par, c->qw2_dev, c->qwt_dev, c->vel_dev, d_rho, d_u, c->stream);
     } else if (c->prec == DVM_FP32) {
         e = launch_warm2d<float>((const Prob2D<float>*)c->probs_dev + prob, c->NL, par, c->qw2_dev, c->vel_dev, d_rho, d_u, c->stream);
     } else {

@@ -112,6 +112,11 @@ struct Prob3D {
     T* src;                 // [N][4]  (nu rho', 2 nu u1 + 1, 2 nu u2, 2 nu u3)
     T* E;                   // [N][8]  wall terms, index 2 j + u (6 used)
     T* P;                   // [8][G][4][N] moment partials per octant and velocity group
+    // temperature term of Eq. 2 (option; 3D): tau = (2/3) sum W |v|^2 h - rho (Eq. 4)
+    int tau;                // 1: the source carries tau (|v|^2 - 3/2)
+    double sw2;             // sum over the grid of W |v|^2 (3/2 for a rule exact on v^2)
+    T* Pt;                  // [8][G][N] partials of sum W |v|^2 h' (with tau)
+    T* srct;                // [N] nu tau of the last iteration, read by the sweep (with tau)
     // Lagged-halo subdomains (Sec. 3.2): ns_j = c_j blocks along axis j (1: none).  Slot s of a
     // ghost array holds the two layers upstream of oriented block s from the previous iteration
     // (slot 0: the domain's own ghost layers); the last pencil / tile of block s writes slot
@@ -147,7 +152,7 @@ struct Prob3D {
     unsigned int* fin_counter;
 };
 
-constexpr int kLaneConsts3 = 20;    // v1 v2 v3 a1 a2 a3 W Wv1 Wv2 Wv3 R[8] pad pad
+constexpr int kLaneConsts3 = 20;    // v1 v2 v3 a1 a2 a3 W Wv1 Wv2 Wv3 R[8] |v|^2-3/2 W|v|^2
 
 struct SweepItem3 { int prob, oct, p2, p3, group, pad0, pad1, pad2; };
 
@@ -162,6 +167,7 @@ struct SweepArgs3D {
     int maxR2, maxR3;
     int bf16;                   // ghosts and pencil edges stored as BF16 (see Prob3D::bf16)
     int sub;                    // lagged-halo subdomains: pencils and tiles from the Prob3D tables
+    int tau;                    // temperature term (Prob3D::tau)
     int parity;
     int* ticket;
     int* status;

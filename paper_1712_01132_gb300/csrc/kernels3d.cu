@@ -61,10 +61,11 @@ template <> struct HStore<float, true> {
 
 }  // namespace
 
-template <typename T, int T1, bool BF, bool SUB>
+template <typename T, int T1, bool BF, bool SUB, bool TAU>
 __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
     using V = typename V4t<T>::type;
     using HS = HStore<T, BF>;
+    constexpr int NM = TAU ? 5 : 4;         // moments per point: rho, u1..u3 (, sum W |v|^2 h)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
     __shared__ int s_abort;
@@ -74,8 +75,8 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
     const int MR2 = a.maxR2, MR3 = a.maxR3;
     const int MROWS = MR2 * MR3;
     T* rec = reinterpret_cast<T*>(smem_raw);                         // [MROWS][T1][kRec3]
-    T* part = rec + (size_t)MROWS * T1 * kRec3;                      // [NW][MROWS][T1][4]
-    T* carry = part + (size_t)NW * MROWS * T1 * 4;                   // [NW][MROWS][2][32]
+    T* part = rec + (size_t)MROWS * T1 * kRec3;                      // [NW][MROWS][T1][NM]
+    T* carry = part + (size_t)NW * MROWS * T1 * NM;                  // [NW][MROWS][2][32]
     T* pb = carry + (size_t)NW * MROWS * 2 * 32;                     // [NW][MR2][2][T1][32]
     T* rtab = pb + (size_t)NW * MR2 * 2 * T1 * 32;                   // [NW][8][32]
     const size_t NL = (size_t)a.NL;
@@ -113,6 +114,7 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
         const T* lcp = P->lanec + ((size_t)q * NL + lv) * kLaneConsts3;
         const T v1 = lcp[0], v2 = lcp[1], v3 = lcp[2], a1 = lcp[3], a2 = lcp[4], a3 = lcp[5];
         const T W = lcp[6], Wv1 = lcp[7], Wv2 = lcp[8], Wv3 = lcp[9];
+        const T vq = lcp[18], Wvv = lcp[19];             // |v|^2 - 3/2 and W |v|^2 (temperature term)
         T* my_rtab = rtab + (size_t)warp * 8 * 32 + lane;
 #pragma unroll
         for (int rs = 0; rs < 8; ++rs) my_rtab[rs * 32] = lcp[10 + rs];
@@ -168,7 +170,8 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                         r1 = V4t<T>::make(E1, E2, E3, ibits(T(0), rs));
                         r2 = V4t<T>::make(ca == 2 ? T(0) : (ca == 1 ? T(1) : K1o), ca == 0 ? K2o : T(0),
                                           cb == 2 ? T(0) : (cb == 1 ? T(1) : K1o), cb == 0 ? K2o : T(0));
-                        r3 = V4t<T>::make(cc == 2 ? T(0) : (cc == 1 ? T(1) : K1o), cc == 0 ? K2o : T(0), T(0), T(0));
+                        r3 = V4t<T>::make(cc == 2 ? T(0) : (cc == 1 ? T(1) : K1o), cc == 0 ? K2o : T(0),
+                                          TAU ? P->srct[id] : T(0), T(0));
                     }
                 }
                 V* R = reinterpret_cast<V*>(rec + (size_t)((kk * MR2 + jj) * T1 + i) * kRec3);
@@ -236,10 +239,10 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                     T hp1 = cr[0], hp2 = cr[32];
                     T* zr = pb + ((((size_t)warp * MR2 + jj) * 2) * T1) * 32 + lane;   // [2][T1][32]
                     const T* rrow = rec + (size_t)((kk * MR2 + jj) * T1) * kRec3;
-                    T* prow = part + ((size_t)(warp * MROWS + kk * MR2 + jj) * T1) * 4;
+                    T* prow = part + ((size_t)(warp * MROWS + kk * MR2 + jj) * T1) * NM;
 #pragma unroll
                     for (int i0 = 0; i0 < T1; i0 += 4) {
-                        T m0[4], m1[4], m2[4], m3[4];
+                        T m0[4], m1[4], m2[4], m3[4], m4[4];
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
                             const int i = i0 + c;
@@ -248,7 +251,8 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                                 const V A = R[0], B = R[1], C = R[2], D = R[3];
                                 const T z1 = zr[(size_t)i * 32];
                                 const T z2 = zr[((size_t)T1 + i) * 32];
-                                const T S = fma(A.w, v3, fma(A.z, v2, fma(A.y, v1, A.x)));
+                                T S = fma(A.w, v3, fma(A.z, v2, fma(A.y, v1, A.x)));
+                                if constexpr (TAU) S = fma(D.z, vq, S);   // nu tau (|v|^2 - 3/2)
                                 const T t1 = fma(C.x, hp1, fma(C.y, hp2, B.x));
                                 const T t2 = fma(C.z, rb1[i], fma(C.w, rb2[i], B.y));
                                 const T t3 = fma(D.x, z1, fma(D.y, z2, B.z));
@@ -264,21 +268,25 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                                 m1[c] = Wv1 * h;
                                 m2[c] = Wv2 * h;
                                 m3[c] = Wv3 * h;
+                                m4[c] = Wvv * h;
                             } else {
-                                m0[c] = m1[c] = m2[c] = m3[c] = T(0);
+                                m0[c] = m1[c] = m2[c] = m3[c] = m4[c] = T(0);
                             }
                         }
                         const T r0 = reduce_scatter<T, 4>(m0, lane);
                         const T r1 = reduce_scatter<T, 4>(m1, lane);
                         const T r2 = reduce_scatter<T, 4>(m2, lane);
                         const T r3 = reduce_scatter<T, 4>(m3, lane);
+                        T r4 = T(0);
+                        if constexpr (TAU) r4 = reduce_scatter<T, 4>(m4, lane);
                         const int p = lane >> 3;
                         if ((lane & 7) == 0 && i0 + p < width) {
-                            T* d = prow + (i0 + p) * 4;
+                            T* d = prow + (i0 + p) * NM;
                             d[0] = r0;
                             d[1] = r1;
                             d[2] = r2;
                             d[3] = r3;
+                            if constexpr (TAU) d[4] = r4;
                         }
                     }
                     cr[0] = hp1;
@@ -348,21 +356,22 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                 publish_gpu(prog + p3 * np2 + p2, t + 1);
             }
             // moment partials of this octant and group: warp sums in warp order
-            const int tot = nr3 * nr2 * width * 4;
+            const int tot = nr3 * nr2 * width * NM;
             for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-                const int mm = idx & 3;
-                const int pi = idx >> 2;
+                const int mm = idx % NM;
+                const int pi = idx / NM;
                 const int i = pi % width;
                 const int r = pi / width;
                 const int jj = r % nr2;
                 const int kk = r / nr2;
                 T s = T(0);
-                for (int w = 0; w < NW; ++w) s += part[((size_t)(w * MROWS + kk * MR2 + jj) * T1 + i) * 4 + mm];
+                for (int w = 0; w < NW; ++w) s += part[((size_t)(w * MROWS + kk * MR2 + jj) * T1 + i) * NM + mm];
                 const int ic = c0 + i;
                 const int x = s1n ? n1 - 1 - ic : ic;
                 const int y = s2n ? n2 - 1 - (j0 + jj) : (j0 + jj);
                 const int z = s3n ? n3 - 1 - (k0 + kk) : (k0 + kk);
-                P->P[(((size_t)q * G + g) * 4 + mm) * N + ((size_t)z * n2 + y) * n1 + x] = s;
+                if (!TAU || mm < 4) P->P[(((size_t)q * G + g) * 4 + mm) * N + ((size_t)z * n2 + y) * n1 + x] = s;
+                else P->Pt[((size_t)q * G + g) * N + ((size_t)z * n2 + y) * n1 + x] = s;
             }
             __syncthreads();
         }
@@ -404,6 +413,16 @@ __global__ void __launch_bounds__(256) finalize3d_kernel(const FinArgs3D<T> a) {
             const T nu = (T)P->nu;
             s = V4t<T>::make(nu * mo[0], T(2) * nu * mo[1] + T(1), T(2) * nu * mo[2], T(2) * nu * mo[3]);
             u1d = (double)mo[1];
+            if (P->tau) {
+                // tau = (2/3) e - rho (Eq. 4) from the shifted moments e' = sum W |v|^2 h' and rho':
+                // tau = (2/3) e' - rho' + x1 (1 - (2/3) sum W |v|^2), the same in both forms
+                T e = T(0);
+                for (int q = 0; q < 8; ++q)
+                    for (int g = 0; g < G; ++g) e += P->Pt[((size_t)q * G + g) * N + id];
+                const T x1 = (T)((id % P->n1) * P->dx);
+                const T tau = T(2.0 / 3.0) * e - mo[0] + x1 * (T)(1.0 - 2.0 / 3.0 * P->sw2);
+                P->srct[id] = nu * tau;
+            }
             T ev[6];
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
@@ -471,7 +490,8 @@ __device__ __forceinline__ void put_h(const Prob3D<T>* P, T* base, size_t i, dou
 
 // Zero-perturbation start in the kernels' source-form variables (h' = x1).
 template <typename T>
-__global__ void init3d_kernel(const Prob3D<T>* P, int NL, const double* qw /*[8][G][4]*/) {
+__global__ void init3d_kernel(const Prob3D<T>* P, int NL, const double* qw /*[8][G][4]*/,
+                              const double* qwt /*[8][G][4]: sum W |v|^2 (1, v)*/) {
     const int n1 = P->n1, n2 = P->n2, n3 = P->n3, N = P->N, G = P->ngroups;
     const size_t nl = NL;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -482,6 +502,12 @@ __global__ void init3d_kernel(const Prob3D<T>* P, int NL, const double* qw /*[8]
         const double x1 = (id % n1) * P->dx;
         P->P[idx] = (P->code[id] & kSolidBit) ? T(0) : (T)(x1 * qw[qgm]);
     }
+    if (P->tau)   // sum W |v|^2 h' of h' = x1
+        for (size_t idx = t0; idx < (size_t)8 * G * N; idx += stride) {
+            const int id = idx % N;
+            const double x1 = (id % n1) * P->dx;
+            P->Pt[idx] = (P->code[id] & kSolidBit) ? T(0) : (T)(x1 * qwt[(idx / N) * 4]);
+        }
     // ghost slot s of the x1 ghosts holds the two columns before oriented column slot_col1[s]
     const int ns1 = P->ns1, ns2 = P->ns2, ns3 = P->ns3;
     for (size_t idx = t0; idx < (size_t)2 * 8 * ns1 * n3 * n2 * 2 * nl; idx += stride) {
@@ -512,8 +538,8 @@ __global__ void init3d_kernel(const Prob3D<T>* P, int NL, const double* qw /*[8]
 // `par` hold h0' where the sweep would have captured them (same slot layout as the sweep writes).
 template <typename T>
 __global__ void warm3d_kernel(const Prob3D<T>* P, int NL, int par, const double* __restrict__ qw2,
-                              const double* __restrict__ vel, const double* __restrict__ rho0,
-                              const double* __restrict__ u0) {
+                              const double* __restrict__ qwt, const double* __restrict__ vel,
+                              const double* __restrict__ rho0, const double* __restrict__ u0) {
     const int n1 = P->n1, n2 = P->n2, n3 = P->n3, N = P->N, G = P->ngroups;
     const size_t nl = NL;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -539,6 +565,18 @@ __global__ void warm3d_kernel(const Prob3D<T>* P, int NL, int par, const double*
         }
         P->P[idx] = (T)val;
     }
+    // temperature term: sum W |v|^2 h0' through qwt[q][g][n] = sum W |v|^2 psi_n, psi = (1, v)
+    if (P->tau)
+        for (size_t idx = t0; idx < (size_t)8 * G * N; idx += stride) {
+            const size_t id = idx % N;
+            double val = 0.0;
+            if (!(P->code[id] & kSolidBit)) {
+                const double* c = qwt + (idx / N) * 4;
+                const double r = rho0[id] + (id % n1) * P->dx;
+                val = r * c[0] + 2.0 * (u0[id] * c[1] + u0[N + id] * c[2] + u0[2 * (size_t)N + id] * c[3]);
+            }
+            P->Pt[idx] = (T)val;
+        }
     const int ns1 = P->ns1, ns2 = P->ns2, ns3 = P->ns3;
     // x1 ghosts: (q, slot s, oriented row (k, j), layer) holds h at oriented column
     // slot_col1[s] - 1 - layer (slot 0: n1 - 1 - layer, the periodic wrap)
@@ -600,6 +638,27 @@ __global__ void moments3d_kernel(const Prob3D<T>* P, double* rho, double* u) {
     }
 }
 
+// Temperature of Eq. 4 per point (FP64 sums of the partials): tau = (2/3) e' - rho' +
+// x1 (1 - (2/3) sum W |v|^2), the paper's tau (solid points 0).
+template <typename T>
+__global__ void temperature3d_kernel(const Prob3D<T>* P, double* tau) {
+    const int N = P->N, G = P->ngroups;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        if (P->code[id] & kSolidBit) {
+            tau[id] = 0.0;
+            continue;
+        }
+        double e = 0.0, r = 0.0;
+        for (int q = 0; q < 8; ++q)
+            for (int g = 0; g < G; ++g) {
+                e += (double)P->Pt[((size_t)q * G + g) * N + id];
+                r += (double)P->P[(((size_t)q * G + g) * 4) * N + id];
+            }
+        const double x1 = (id % P->n1) * P->dx;
+        tau[id] = 2.0 / 3.0 * e - r + x1 * (1.0 - 2.0 / 3.0 * P->sw2);
+    }
+}
+
 template <typename T>
 __global__ void wall3d_kernel(const Prob3D<T>* P, double* out) {
     const int N = P->N;
@@ -616,45 +675,57 @@ __global__ void wall3d_kernel(const Prob3D<T>* P, double* out) {
 }
 
 template <typename T>
-size_t sweep3d_smem(int T1, int NW, int R2, int R3) {
+size_t sweep3d_smem(int T1, int NW, int R2, int R3, int tau) {
     const size_t rows = (size_t)R2 * R3;
-    return sizeof(T) * (rows * T1 * kRec3 + (size_t)NW * rows * T1 * 4 + (size_t)NW * rows * 2 * 32 +
+    return sizeof(T) * (rows * T1 * kRec3 + (size_t)NW * rows * T1 * (tau ? 5 : 4) + (size_t)NW * rows * 2 * 32 +
                         (size_t)NW * R2 * 2 * T1 * 32 + (size_t)NW * 8 * 32);
 }
 
-template <typename T, int T1, bool SUB>
+template <typename T, int T1, bool SUB, bool TAU>
 static cudaError_t occ3(int NW, int R2, int R3, int* blocks_per_sm) {
-    const size_t smem = sweep3d_smem<T>(T1, NW, R2, R3);
-    cudaError_t e = cudaFuncSetAttribute(sweep3d_kernel<T, T1, false, SUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = sweep3d_smem<T>(T1, NW, R2, R3, TAU);
+    cudaError_t e = cudaFuncSetAttribute(sweep3d_kernel<T, T1, false, SUB, TAU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep3d_kernel<T, T1, false, SUB>, NW * 32, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep3d_kernel<T, T1, false, SUB, TAU>, NW * 32, smem);
+}
+
+template <typename T, int T1>
+static cudaError_t occ3_t(int NW, int R2, int R3, int sub, int tau, int* bps) {
+    if (sub) return tau ? occ3<T, T1, true, true>(NW, R2, R3, bps) : occ3<T, T1, true, false>(NW, R2, R3, bps);
+    return tau ? occ3<T, T1, false, true>(NW, R2, R3, bps) : occ3<T, T1, false, false>(NW, R2, R3, bps);
 }
 
 // The scalar kernel serves the FP64 path (FP32 and its BF16-storage ablation use the packed kernel
 // of sweep3d_f32x2.cu); its BF16 flag stays false.  sub: lagged-halo subdomains (table-driven
-// pencils and tiles).
+// pencils and tiles); tau: the temperature term.
 template <typename T>
-cudaError_t sweep3d_occupancy(int T1, int NW, int R2, int R3, int bf16, int sub, int* blocks_per_sm) {
+cudaError_t sweep3d_occupancy(int T1, int NW, int R2, int R3, int bf16, int sub, int tau, int* blocks_per_sm) {
     if (bf16) return cudaErrorInvalidValue;
-    if (T1 == 4) return sub ? occ3<T, 4, true>(NW, R2, R3, blocks_per_sm) : occ3<T, 4, false>(NW, R2, R3, blocks_per_sm);
-    if (T1 == 8) return sub ? occ3<T, 8, true>(NW, R2, R3, blocks_per_sm) : occ3<T, 8, false>(NW, R2, R3, blocks_per_sm);
+    if (T1 == 4) return occ3_t<T, 4>(NW, R2, R3, sub, tau, blocks_per_sm);
+    if (T1 == 8) return occ3_t<T, 8>(NW, R2, R3, sub, tau, blocks_per_sm);
     return cudaErrorInvalidValue;
 }
 
-template <typename T, int T1, bool SUB>
+template <typename T, int T1, bool SUB, bool TAU>
 static cudaError_t launch3(const SweepArgs3D<T>& a, int grid, int NW, cudaStream_t st) {
-    const size_t smem = sweep3d_smem<T>(T1, NW, a.maxR2, a.maxR3);
-    cudaError_t e = cudaFuncSetAttribute(sweep3d_kernel<T, T1, false, SUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = sweep3d_smem<T>(T1, NW, a.maxR2, a.maxR3, TAU);
+    cudaError_t e = cudaFuncSetAttribute(sweep3d_kernel<T, T1, false, SUB, TAU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    sweep3d_kernel<T, T1, false, SUB><<<grid, NW * 32, smem, st>>>(a);
+    sweep3d_kernel<T, T1, false, SUB, TAU><<<grid, NW * 32, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+template <typename T, int T1>
+static cudaError_t launch3_t(const SweepArgs3D<T>& a, int grid, int NW, cudaStream_t st) {
+    if (a.sub) return a.tau ? launch3<T, T1, true, true>(a, grid, NW, st) : launch3<T, T1, true, false>(a, grid, NW, st);
+    return a.tau ? launch3<T, T1, false, true>(a, grid, NW, st) : launch3<T, T1, false, false>(a, grid, NW, st);
 }
 
 template <typename T>
 cudaError_t launch_sweep3d(const SweepArgs3D<T>& a, int grid, int NW, cudaStream_t st) {
     if (a.bf16) return cudaErrorInvalidValue;
-    if (a.T1 == 4) return a.sub ? launch3<T, 4, true>(a, grid, NW, st) : launch3<T, 4, false>(a, grid, NW, st);
-    if (a.T1 == 8) return a.sub ? launch3<T, 8, true>(a, grid, NW, st) : launch3<T, 8, false>(a, grid, NW, st);
+    if (a.T1 == 4) return launch3_t<T, 4>(a, grid, NW, st);
+    if (a.T1 == 8) return launch3_t<T, 8>(a, grid, NW, st);
     return cudaErrorInvalidValue;
 }
 
@@ -665,15 +736,15 @@ cudaError_t launch_finalize3d(const FinArgs3D<T>& a, int nblocks, cudaStream_t s
 }
 
 template <typename T>
-cudaError_t launch_init3d(const Prob3D<T>* p, int NL, const double* qw, cudaStream_t st) {
-    init3d_kernel<T><<<608, 256, 0, st>>>(p, NL, qw);
+cudaError_t launch_init3d(const Prob3D<T>* p, int NL, const double* qw, const double* qwt, cudaStream_t st) {
+    init3d_kernel<T><<<608, 256, 0, st>>>(p, NL, qw, qwt);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_warm3d(const Prob3D<T>* p, int NL, int par, const double* qw2, const double* vel,
-                          const double* rho0, const double* u0, cudaStream_t st) {
-    warm3d_kernel<T><<<608, 256, 0, st>>>(p, NL, par, qw2, vel, rho0, u0);
+cudaError_t launch_warm3d(const Prob3D<T>* p, int NL, int par, const double* qw2, const double* qwt,
+                          const double* vel, const double* rho0, const double* u0, cudaStream_t st) {
+    warm3d_kernel<T><<<608, 256, 0, st>>>(p, NL, par, qw2, qwt, vel, rho0, u0);
     return cudaGetLastError();
 }
 
@@ -684,21 +755,28 @@ cudaError_t launch_moments3d(const Prob3D<T>* p, double* rho, double* u, cudaStr
 }
 
 template <typename T>
+cudaError_t launch_temperature3d(const Prob3D<T>* p, double* tau, cudaStream_t st) {
+    temperature3d_kernel<T><<<608, 256, 0, st>>>(p, tau);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_wall3d(const Prob3D<T>* p, double* out, cudaStream_t st) {
     wall3d_kernel<T><<<608, 256, 0, st>>>(p, out);
     return cudaGetLastError();
 }
 
-template size_t sweep3d_smem<double>(int, int, int, int);
-template cudaError_t sweep3d_occupancy<double>(int, int, int, int, int, int, int*);
+template size_t sweep3d_smem<double>(int, int, int, int, int);
+template cudaError_t sweep3d_occupancy<double>(int, int, int, int, int, int, int, int*);
 template cudaError_t launch_sweep3d<double>(const SweepArgs3D<double>&, int, int, cudaStream_t);
 
-#define DVM_INSTANTIATE3(T)                                                                     \
-    template cudaError_t launch_finalize3d<T>(const FinArgs3D<T>&, int, cudaStream_t);         \
-    template cudaError_t launch_init3d<T>(const Prob3D<T>*, int, const double*, cudaStream_t); \
-    template cudaError_t launch_warm3d<T>(const Prob3D<T>*, int, int, const double*, const double*, \
-                                          const double*, const double*, cudaStream_t);            \
-    template cudaError_t launch_moments3d<T>(const Prob3D<T>*, double*, double*, cudaStream_t); \
+#define DVM_INSTANTIATE3(T)                                                                                  \
+    template cudaError_t launch_finalize3d<T>(const FinArgs3D<T>&, int, cudaStream_t);                      \
+    template cudaError_t launch_init3d<T>(const Prob3D<T>*, int, const double*, const double*, cudaStream_t); \
+    template cudaError_t launch_warm3d<T>(const Prob3D<T>*, int, int, const double*, const double*,          \
+                                          const double*, const double*, const double*, cudaStream_t);        \
+    template cudaError_t launch_moments3d<T>(const Prob3D<T>*, double*, double*, cudaStream_t);              \
+    template cudaError_t launch_temperature3d<T>(const Prob3D<T>*, double*, cudaStream_t);                   \
     template cudaError_t launch_wall3d<T>(const Prob3D<T>*, double*, cudaStream_t);
 
 DVM_INSTANTIATE3(float)

@@ -68,9 +68,10 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 
 }  // namespace
 
-template <int T1, bool BF, bool SUB>
+template <int T1, bool BF, bool SUB, bool TAU>
 __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<float> a) {
     using PS = PairStore<BF>;
+    constexpr int NM = TAU ? 5 : 4;         // moments per point: rho, u1..u3 (, sum W |v|^2 h)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
     __shared__ int s_abort;
@@ -80,8 +81,8 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
     const int MR2 = a.maxR2, MR3 = a.maxR3;
     const int MROWS = MR2 * MR3;
     float* rec = reinterpret_cast<float*>(smem_raw);                      // [MROWS][T1][kRec]
-    float* part = rec + (size_t)MROWS * T1 * kRec;                        // [NW][MROWS][T1][4]
-    float* carry = part + (size_t)NW * MROWS * T1 * 4;                    // [NW][MROWS][2][64]
+    float* part = rec + (size_t)MROWS * T1 * kRec;                        // [NW][MROWS][T1][NM]
+    float* carry = part + (size_t)NW * MROWS * T1 * NM;                   // [NW][MROWS][2][64]
     float* pb = carry + (size_t)NW * MROWS * 2 * kPL;                     // [NW][MR2][2][T1][64]
     float* eb = pb + (size_t)NW * MR2 * 2 * T1 * kPL;                     // [NW][2][2][T1][64]
     float* rtab = eb + (size_t)NW * 2 * 2 * T1 * kPL;                     // [NW][8][64]
@@ -125,6 +126,8 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
         const float2 a1 = make_float2(la[3], lb[3]), a2 = make_float2(la[4], lb[4]), a3 = make_float2(la[5], lb[5]);
         const float2 W = make_float2(la[6], lb[6]), Wv1 = make_float2(la[7], lb[7]);
         const float2 Wv2 = make_float2(la[8], lb[8]), Wv3 = make_float2(la[9], lb[9]);
+        // temperature term: |v|^2 - 3/2 and W |v|^2
+        const float2 vq = make_float2(la[18], lb[18]), Wvv = make_float2(la[19], lb[19]);
         float* my_rtab = rtab + (size_t)warp * 8 * kPL + 2 * lane;
 #pragma unroll
         for (int rs = 0; rs < 8; ++rs)
@@ -187,7 +190,8 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                                          __int_as_float(rs * kPL));
                         r2 = make_float4(ca == 2 ? 0.f : (ca == 1 ? 1.f : K1o), ca == 0 ? K2o : 0.f,
                                          cb == 2 ? 0.f : (cb == 1 ? 1.f : K1o), cb == 0 ? K2o : 0.f);
-                        r3 = make_float4(cc == 2 ? 0.f : (cc == 1 ? 1.f : K1o), cc == 0 ? K2o : 0.f, 0.f, 0.f);
+                        r3 = make_float4(cc == 2 ? 0.f : (cc == 1 ? 1.f : K1o), cc == 0 ? K2o : 0.f,
+                                         TAU ? P->srct[id] : 0.f, 0.f);
                         atomicOr(fm_cur + kk * MR2 + jj, 1u << i);
                     }
                 }
@@ -325,11 +329,11 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                     float2 hp2 = *reinterpret_cast<const float2*>(cr + kPL);
                     float* zr = pb + ((((size_t)warp * MR2 + jj) * 2) * T1) * kPL + 2 * lane;   // [2][T1][64]
                     const float* rrow = rec + (size_t)((kk * MR2 + jj) * T1) * kRec;
-                    float* prow = part + ((size_t)(warp * MROWS + kk * MR2 + jj) * T1) * 4;
+                    float* prow = part + ((size_t)(warp * MROWS + kk * MR2 + jj) * T1) * NM;
 #pragma unroll
                     for (int i0 = 0; i0 < T1; i0 += 4) {
                         if (((fm >> i0) & 15u) == 0u) continue;
-                        float m0[4], m1[4], m2[4], m3[4];
+                        float m0[4], m1[4], m2[4], m3[4], m4[4];
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
                             const int i = i0 + c;
@@ -339,7 +343,8 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                                 const float2 z1 = *reinterpret_cast<const float2*>(zr + (size_t)i * kPL);
                                 const float2 z2 = *reinterpret_cast<const float2*>(zr + ((size_t)T1 + i) * kPL);
                                 const float2 Rk = *reinterpret_cast<const float2*>(my_rtab + __float_as_int(B.w));
-                                const float2 S = fma2(dup2(A.w), v3, fma2(dup2(A.z), v2, fma2(dup2(A.y), v1, dup2(A.x))));
+                                float2 S = fma2(dup2(A.w), v3, fma2(dup2(A.z), v2, fma2(dup2(A.y), v1, dup2(A.x))));
+                                if constexpr (TAU) S = fma2(dup2(D.z), vq, S);   // nu tau (|v|^2 - 3/2)
                                 const float2 t1 = fma2(dup2(C.x), hp1, fma2(dup2(C.y), hp2, dup2(B.x)));
                                 const float2 t2 = fma2(dup2(C.z), rb1[i], fma2(dup2(C.w), rb2[i], dup2(B.y)));
                                 const float2 t3 = fma2(dup2(D.x), z1, fma2(dup2(D.y), z2, dup2(B.z)));
@@ -358,21 +363,30 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                                 m1[c] = p1.x + p1.y;
                                 m2[c] = p2v.x + p2v.y;
                                 m3[c] = p3v.x + p3v.y;
+                                if constexpr (TAU) {
+                                    const float2 p4v = mul2(Wvv, h);
+                                    m4[c] = p4v.x + p4v.y;
+                                } else {
+                                    m4[c] = 0.f;
+                                }
                             } else {
-                                m0[c] = m1[c] = m2[c] = m3[c] = 0.f;
+                                m0[c] = m1[c] = m2[c] = m3[c] = m4[c] = 0.f;
                             }
                         }
                         const float r0 = reduce_scatter<float, 4>(m0, lane);
                         const float r1 = reduce_scatter<float, 4>(m1, lane);
                         const float r2 = reduce_scatter<float, 4>(m2, lane);
                         const float r3 = reduce_scatter<float, 4>(m3, lane);
+                        float r4 = 0.f;
+                        if constexpr (TAU) r4 = reduce_scatter<float, 4>(m4, lane);
                         const int p = lane >> 3;
                         if ((lane & 7) == 0 && i0 + p < width) {
-                            float* d = prow + (i0 + p) * 4;
+                            float* d = prow + (i0 + p) * NM;
                             d[0] = r0;
                             d[1] = r1;
                             d[2] = r2;
                             d[3] = r3;
+                            if constexpr (TAU) d[4] = r4;
                         }
                     }
                     *reinterpret_cast<float2*>(cr) = hp1;
@@ -449,22 +463,23 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                 publish_gpu(prog + p3 * np2 + p2, t + 1);
             }
             // moment partials of this octant and group: warp sums in warp order
-            const int tot = nr3 * nr2 * width * 4;
+            const int tot = nr3 * nr2 * width * NM;
             for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-                const int mm = idx & 3;
-                const int pi = idx >> 2;
+                const int mm = idx % NM;
+                const int pi = idx / NM;
                 const int i = pi % width;
                 const int r = pi / width;
                 const int jj = r % nr2;
                 const int kk = r / nr2;
                 float s = 0.f;
                 if ((fm_cur[kk * MR2 + jj] >> i) & 1u)
-                    for (int w = 0; w < NW; ++w) s += part[((size_t)(w * MROWS + kk * MR2 + jj) * T1 + i) * 4 + mm];
+                    for (int w = 0; w < NW; ++w) s += part[((size_t)(w * MROWS + kk * MR2 + jj) * T1 + i) * NM + mm];
                 const int ic = c0 + i;
                 const int x = s1n ? n1 - 1 - ic : ic;
                 const int y = s2n ? n2 - 1 - (j0 + jj) : (j0 + jj);
                 const int z = s3n ? n3 - 1 - (k0 + kk) : (k0 + kk);
-                P->P[(((size_t)q * G + g) * 4 + mm) * N + ((size_t)z * n2 + y) * n1 + x] = s;
+                if (!TAU || mm < 4) P->P[(((size_t)q * G + g) * 4 + mm) * N + ((size_t)z * n2 + y) * n1 + x] = s;
+                else P->Pt[((size_t)q * G + g) * N + ((size_t)z * n2 + y) * n1 + x] = s;
             }
             __syncthreads();
         }
@@ -472,48 +487,59 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
     }
 }
 
-size_t sweep3d_f32x2_smem(int T1, int NW, int R2, int R3) {
+size_t sweep3d_f32x2_smem(int T1, int NW, int R2, int R3, int tau) {
     const size_t rows = (size_t)R2 * R3;
-    return sizeof(float) * (rows * T1 * kRec + (size_t)NW * rows * T1 * 4 + (size_t)NW * rows * 2 * kPL +
+    return sizeof(float) * (rows * T1 * kRec + (size_t)NW * rows * T1 * (tau ? 5 : 4) + (size_t)NW * rows * 2 * kPL +
                             (size_t)NW * R2 * 2 * T1 * kPL + (size_t)NW * 2 * 2 * T1 * kPL + (size_t)NW * 8 * kPL) +
            sizeof(unsigned) * 2 * rows;
 }
 
 int sweep3d_f32x2_velocities_per_lane() { return 2; }
 
-template <int T1, bool BF, bool SUB>
+template <int T1, bool BF, bool SUB, bool TAU>
 static cudaError_t launch_t(const SweepArgs3D<float>& a, int grid, int NW, cudaStream_t st) {
-    const size_t smem = sweep3d_f32x2_smem(T1, NW, a.maxR2, a.maxR3);
-    cudaError_t e = cudaFuncSetAttribute(sweep3d_f32x2_kernel<T1, BF, SUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = sweep3d_f32x2_smem(T1, NW, a.maxR2, a.maxR3, TAU);
+    cudaError_t e = cudaFuncSetAttribute(sweep3d_f32x2_kernel<T1, BF, SUB, TAU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    sweep3d_f32x2_kernel<T1, BF, SUB><<<grid, NW * 32, smem, st>>>(a);
+    sweep3d_f32x2_kernel<T1, BF, SUB, TAU><<<grid, NW * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-// instantiations: FP32 and BF16 storage without subdomains, FP32 with subdomains
+template <int T1>
+static cudaError_t launch_tt(const SweepArgs3D<float>& a, int grid, int NW, cudaStream_t st) {
+    if (a.bf16) return launch_t<T1, true, false, false>(a, grid, NW, st);
+    if (a.sub) return a.tau ? launch_t<T1, false, true, true>(a, grid, NW, st) : launch_t<T1, false, true, false>(a, grid, NW, st);
+    return a.tau ? launch_t<T1, false, false, true>(a, grid, NW, st) : launch_t<T1, false, false, false>(a, grid, NW, st);
+}
+
+// instantiations: FP32 with or without subdomains and the temperature term; BF16 storage without
+// either
 cudaError_t launch_sweep3d_f32x2(const SweepArgs3D<float>& a, int grid, int NW, cudaStream_t st) {
-    if (a.sub && a.bf16) return cudaErrorInvalidValue;
-    if (a.T1 == 4) return a.sub ? launch_t<4, false, true>(a, grid, NW, st)
-                                : (a.bf16 ? launch_t<4, true, false>(a, grid, NW, st) : launch_t<4, false, false>(a, grid, NW, st));
-    if (a.T1 == 8) return a.sub ? launch_t<8, false, true>(a, grid, NW, st)
-                                : (a.bf16 ? launch_t<8, true, false>(a, grid, NW, st) : launch_t<8, false, false>(a, grid, NW, st));
+    if (a.bf16 && (a.sub || a.tau)) return cudaErrorInvalidValue;
+    if (a.T1 == 4) return launch_tt<4>(a, grid, NW, st);
+    if (a.T1 == 8) return launch_tt<8>(a, grid, NW, st);
     return cudaErrorInvalidValue;
 }
 
-template <int T1, bool BF, bool SUB>
+template <int T1, bool BF, bool SUB, bool TAU>
 static cudaError_t occ_t(int NW, int R2, int R3, int* blocks_per_sm) {
-    const size_t smem = sweep3d_f32x2_smem(T1, NW, R2, R3);
-    cudaError_t e = cudaFuncSetAttribute(sweep3d_f32x2_kernel<T1, BF, SUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = sweep3d_f32x2_smem(T1, NW, R2, R3, TAU);
+    cudaError_t e = cudaFuncSetAttribute(sweep3d_f32x2_kernel<T1, BF, SUB, TAU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep3d_f32x2_kernel<T1, BF, SUB>, NW * 32, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep3d_f32x2_kernel<T1, BF, SUB, TAU>, NW * 32, smem);
 }
 
-cudaError_t sweep3d_f32x2_occupancy(int T1, int NW, int R2, int R3, int bf16, int sub, int* blocks_per_sm) {
-    if (sub && bf16) return cudaErrorInvalidValue;
-    if (T1 == 4) return sub ? occ_t<4, false, true>(NW, R2, R3, blocks_per_sm)
-                            : (bf16 ? occ_t<4, true, false>(NW, R2, R3, blocks_per_sm) : occ_t<4, false, false>(NW, R2, R3, blocks_per_sm));
-    if (T1 == 8) return sub ? occ_t<8, false, true>(NW, R2, R3, blocks_per_sm)
-                            : (bf16 ? occ_t<8, true, false>(NW, R2, R3, blocks_per_sm) : occ_t<8, false, false>(NW, R2, R3, blocks_per_sm));
+template <int T1>
+static cudaError_t occ_tt(int NW, int R2, int R3, int bf16, int sub, int tau, int* bps) {
+    if (bf16) return occ_t<T1, true, false, false>(NW, R2, R3, bps);
+    if (sub) return tau ? occ_t<T1, false, true, true>(NW, R2, R3, bps) : occ_t<T1, false, true, false>(NW, R2, R3, bps);
+    return tau ? occ_t<T1, false, false, true>(NW, R2, R3, bps) : occ_t<T1, false, false, false>(NW, R2, R3, bps);
+}
+
+cudaError_t sweep3d_f32x2_occupancy(int T1, int NW, int R2, int R3, int bf16, int sub, int tau, int* blocks_per_sm) {
+    if (bf16 && (sub || tau)) return cudaErrorInvalidValue;
+    if (T1 == 4) return occ_tt<4>(NW, R2, R3, bf16, sub, tau, blocks_per_sm);
+    if (T1 == 8) return occ_tt<8>(NW, R2, R3, bf16, sub, tau, blocks_per_sm);
     return cudaErrorInvalidValue;
 }
 

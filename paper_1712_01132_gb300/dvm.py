@@ -48,6 +48,7 @@ class dvm_options(ctypes.Structure):
         ("subdomains", ctypes.c_int * 3),
         ("band_pairs", ctypes.c_int),
         ("group_warps", ctypes.c_int),
+        ("temperature_term", ctypes.c_int),
     ]
 
 
@@ -67,6 +68,7 @@ _SIGNATURES = [
     ("dvm_sync", ctypes.c_int, [_P]),
     ("dvm_moments", ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     ("dvm_moments_at", ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int]),
+    ("dvm_temperature_at", ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int]),
     ("dvm_permeability", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("dvm_permeability_at", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_double)]),
@@ -204,7 +206,7 @@ class _TorchAllocator:
 
 def make_options(precision="fp64", stencil_order=2, lateral="specular", check_interval=100, stream=None,
                  tile_x1=0, band_rows=0, torch_memory=True, use_graph=False, subdomains=(1, 1, 1),
-                 band_pairs=False, group_warps=0):
+                 band_pairs=False, group_warps=0, temperature_term=False):
     """dvm_options with torch's current stream (unless stream is given) and, by default, torch's
     caching allocator for device memory.  Returns (options, keepalive)."""
     o = dvm_default_options()
@@ -217,6 +219,7 @@ def make_options(precision="fp64", stencil_order=2, lateral="specular", check_in
     o.use_graph = 1 if use_graph else 0
     o.band_pairs = 1 if band_pairs else 0
     o.group_warps = int(group_warps)
+    o.temperature_term = 1 if temperature_term else 0
     for j in range(3):
         o.subdomains[j] = int(subdomains[j])
     keep = []
@@ -331,6 +334,13 @@ class Solver:
         u = np.zeros(m.size * m.ndim)
         _check(self._lib.dvm_moments_at(self._ctx, int(prob), _ptr(rho), _ptr(u), 0), self._ctx)
         return rho.reshape(m.shape), u.reshape((m.ndim,) + m.shape)
+
+    def temperature(self, prob=0):
+        """Temperature perturbation tau (Eq. 4) of problem prob; needs temperature_term=True."""
+        m = self.masks[prob]
+        tau = np.zeros(m.size)
+        _check(self._lib.dvm_temperature_at(self._ctx, int(prob), _ptr(tau), 0), self._ctx)
+        return tau.reshape(m.shape)
 
     def moments_device(self, prob, rho_ptr, u_ptr):
         _check(self._lib.dvm_moments_at(self._ctx, int(prob), ctypes.c_void_p(rho_ptr), ctypes.c_void_p(u_ptr), 1),
