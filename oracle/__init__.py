@@ -43,6 +43,7 @@ class _Cfg(ctypes.Structure):
         ("traversal", ctypes.c_int),
         ("dec", ctypes.c_int * 3),
         ("tau", ctypes.c_int),
+        ("alpha", ctypes.c_double),
     ]
 
 
@@ -96,10 +97,12 @@ class Oracle:
     decomposition: subdomain counts (c1, c2[, c3]) of the lagged-halo Omega_x decomposition.
     tau: keep the temperature term tau (|v|^2 - 3/2) of Eq. 2 with tau from Eq. 4 (3D only; the
     paper drops it for its isothermal flows).
+    alpha: tangential momentum accommodation coefficient of the Maxwell wall condition (Eq. 5);
+    1 (fully diffuse) is the paper's setting.
     """
 
     def __init__(self, solid, kn, v, w, *, jump=1.0, order=2, lateral="specular", form="jump",
-                 traversal="raster", decomposition=(1, 1, 1), threads=0, tau=False):
+                 traversal="raster", decomposition=(1, 1, 1), threads=0, tau=False, alpha=1.0):
         lib = _load()
         solid = np.ascontiguousarray(np.asarray(solid).astype(np.uint8))
         if solid.ndim not in (2, 3):
@@ -130,6 +133,7 @@ class Oracle:
         for j in range(3):
             cfg.dec[j] = int(dec[j])
         cfg.tau = 1 if tau else 0
+        cfg.alpha = float(alpha)
         self._cfg = cfg
         self._h = lib.ora_create(ctypes.byref(cfg))
         if not self._h:

@@ -13,8 +13,9 @@
  *         linearised BGK equation (Eq. 10, the discretised form of Eq. 3) at each point with the
  *         upwind stencil of Eq. 9: (C0,C1,C2) = (1.5,-2,0.5)/dx by default, (1,-1,0)/dx when
  *         either upstream point of that stencil along the axis is solid;
- *   (ii)  boundary data for the next iteration: diffuse walls (Eq. 5 with alpha = 1), the pressure
- *         jump periodic condition in x1 (Eq. 7), specular (Eq. 8) or periodic lateral faces;
+ *   (ii)  boundary data for the next iteration: Maxwell diffuse-specular walls (Eq. 5; alpha = 1,
+ *         fully diffuse, is the paper's setting and the default), the pressure jump periodic
+ *         condition in x1 (Eq. 7), specular (Eq. 8) or periodic lateral faces;
  *   (iii) moments rho, u (Eq. 4) and wall densities (Eq. 6); the temperature tau of Eq. 4 and its
  *         source term tau (|v|^2 - 3/2) in Eq. 2 / Eq. 10 are dropped as in Sec. 4 unless the tau
  *         option is set (3D only: Eq. 2 and Eq. 4 are written for three velocity components);
@@ -78,6 +79,7 @@ typedef struct {
     int traversal;         /* 0 raster scan (paper), 1 wavefront over hyperplanes */
     int dec[3];            /* subdomain counts c1, c2, c3 of the lagged-halo decomposition */
     int tau;               /* 1: keep the temperature term of Eq. 2 (3D only); 0: drop it (Sec. 4) */
+    double alpha;          /* tangential momentum accommodation coefficient of Eq. 5 (1: diffuse) */
 } ora_cfg;
 
 typedef struct {
@@ -97,6 +99,7 @@ typedef struct {
     double* full[2];       /* [nv][N] lagged h, only with a decomposition */
     int* sub[3];           /* [n_j] subdomain index of each coordinate */
     int decomposed;
+    int keep_full;         /* lagged h of every velocity kept: decomposition or alpha < 1 */
     double* H;             /* [ORA_GROUP][N] scratch */
     double* flux;          /* [n1] x1 face flux of the last iteration (jump-form variables) */
     uint8_t* facemask;     /* [N] bit (2 j + side) set when face (x, j, side) exists */
@@ -203,9 +206,17 @@ static void point_update(const ora* o, int k, const int c[3], double* h) {
         int l0 = c[j];
         int l1 = l0 - s, l2 = l0 - 2 * s;
         if (is_solid_at(o, j, c, l1)) {
-            /* first-order stencil, upstream value = diffuse wall value of face (x, j, -s) */
+            /* first-order stencil, upstream value = wall value of face (x, j, -s): Eq. 5, the
+             * diffuse part alpha rho_s plus, for alpha < 1, the specular part (1 - alpha)
+             * h(v - 2 n (v.n)) of the molecules reaching the face, taken (like rho_s) at the
+             * fluid point of the face and from the previous iteration, with the same source-form
+             * shift */
             double C0 = 1.0 / o->dx, C1 = -1.0 / o->dx;
             double U1 = wall_value(o, j, c, l0, -s);
+            if (o->c.alpha < 1.0) {
+                double hr = o->full[0][(size_t)o->refl[j * o->nv + k] * o->N + id];
+                U1 = o->c.alpha * U1 + (1.0 - o->c.alpha) * (hr + wall_shift(o, j, -s));
+            }
             num -= av * C1 * U1;
             den += av * C0;
         } else {
@@ -321,7 +332,7 @@ static void init_state(ora* o) {
                             dst[transverse(o, j, cc)] = x1;
                         }
             }
-    if (o->decomposed) {
+    if (o->keep_full) {
         for (int k = 0; k < o->nv; ++k)
             for (int id = 0; id < o->N; ++id)
                 o->full[0][(size_t)k * N + id] =
@@ -332,6 +343,7 @@ static void init_state(ora* o) {
 
 ora* ora_create(const ora_cfg* cfg) {
     if (!cfg || (cfg->dims != 2 && cfg->dims != 3) || cfg->nv <= 0 || cfg->kn <= 0) return NULL;
+    if (!(cfg->alpha >= 0.0 && cfg->alpha <= 1.0)) return NULL;
     if (cfg->tau && cfg->dims != 3) return NULL;
     ora* o = (ora*)calloc(1, sizeof(ora));
     o->c = *cfg;
@@ -405,7 +417,8 @@ ora* ora_create(const ora_cfg* cfg) {
         o->sub[j] = (int*)malloc(sizeof(int) * n);
         for (int l = 0; l < n; ++l) o->sub[j][l] = (j < o->d) ? (int)(((long)l * cj) / n) : 0;
     }
-    if (o->decomposed) {
+    o->keep_full = o->decomposed || cfg->alpha < 1.0;
+    if (o->keep_full) {
         o->full[0] = (double*)calloc((size_t)o->nv * o->N, sizeof(double));
         o->full[1] = (double*)calloc((size_t)o->nv * o->N, sizeof(double));
     }
@@ -482,7 +495,7 @@ static void iterate_once(ora* o) {
             double* h = o->H + (size_t)kk * N;
             sweep(o, k, h);
             capture_ghosts(o, k, h);
-            if (o->decomposed) memcpy(o->full[1] + (size_t)k * N, h, sizeof(double) * N);
+            if (o->keep_full) memcpy(o->full[1] + (size_t)k * N, h, sizeof(double) * N);
         }
         /* step (iii): quadrature, accumulated in ascending velocity order at every point */
 #pragma omp parallel for schedule(static)
@@ -536,7 +549,7 @@ static void iterate_once(ora* o) {
     memcpy(o->u, u_n, sizeof(double) * N * d);
     if (o->c.tau) update_tau(o, e_n);
     double* t = o->lag[0]; o->lag[0] = o->lag[1]; o->lag[1] = t;
-    if (o->decomposed) { t = o->full[0]; o->full[0] = o->full[1]; o->full[1] = t; }
+    if (o->keep_full) { t = o->full[0]; o->full[0] = o->full[1]; o->full[1] = t; }
     free(rho_n); free(u_n); free(num_n); free(e_n);
     o->iter++;
 }
@@ -599,7 +612,7 @@ void ora_set_uniform(ora* o, double c) {
     for (int id = 0; id < o->N; ++id) o->tau[id] = o->solid[id] ? 0.0 : c * (2.0 / 3.0 * o->sw2 - 1.0);
     size_t lagsz = (size_t)o->nv * o->d * 2 * o->area[0];
     for (size_t i = 0; i < lagsz; ++i) o->lag[0][i] = c;
-    if (o->decomposed)
+    if (o->keep_full)
         for (size_t i = 0; i < (size_t)o->nv * o->N; ++i) o->full[0][i] = c;
 }
 
@@ -631,7 +644,7 @@ void ora_set_initial(ora* o, const double* rho0, const double* u0) {
             h[id] = rho0[id] + 2.0 * dot + x1;
         }
         capture_ghosts(o, k, h);
-        if (o->decomposed) memcpy(o->full[1] + (size_t)k * N, h, sizeof(double) * N);
+        if (o->keep_full) memcpy(o->full[1] + (size_t)k * N, h, sizeof(double) * N);
         for (size_t id = 0; id < N; ++id) {
             if (o->solid[id]) continue;
             double wk = o->w[k];
@@ -654,7 +667,7 @@ void ora_set_initial(ora* o, const double* rho0, const double* u0) {
     memcpy(o->u, u_n, sizeof(double) * N * d);
     if (o->c.tau) update_tau(o, e_n);
     double* t = o->lag[0]; o->lag[0] = o->lag[1]; o->lag[1] = t;
-    if (o->decomposed) { t = o->full[0]; o->full[0] = o->full[1]; o->full[1] = t; }
+    if (o->keep_full) { t = o->full[0]; o->full[0] = o->full[1]; o->full[1] = t; }
     free(h); free(rho_n); free(u_n); free(num_n); free(e_n);
 }
 

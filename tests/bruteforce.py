@@ -20,9 +20,11 @@ import math
 import numpy as np
 
 
-def solve_dense(solid, kn, v, w, jump=1.0, order=2, lateral="specular", tau=False):
+def solve_dense(solid, kn, v, w, jump=1.0, order=2, lateral="specular", tau=False, alpha=1.0):
     """tau: keep the temperature term tau (|v|^2 - 3/2) of Eq. 2 with tau = (2/3) sum W |v|^2 h - rho
-    (Eq. 4), a linear functional of the unknowns at the same point like rho and u."""
+    (Eq. 4), a linear functional of the unknowns at the same point like rho and u.
+    alpha: Maxwell accommodation of Eq. 5; the wall value of velocity k is alpha rho_s + (1 - alpha)
+    h(x_f, reflected k) with h at the wall's fluid point x_f (lagged, like rho_s)."""
     solid = np.asarray(solid, dtype=bool)
     dims = solid.ndim
     shape = solid.shape
@@ -85,7 +87,7 @@ def solve_dense(solid, kn, v, w, jump=1.0, order=2, lateral="specular", tau=Fals
         f = fid[moved(c, j, lb)]
         return {col(f, kk): 1.0}, -r * jump, lb != l
 
-    def wall_term(c, j, l, side):
+    def wall_term(c, j, l, side, k0):
         lb, r, mir = map_coord(j, l)
         sd = -side if mir else side
         f = fid[moved(c, j, lb)]
@@ -93,7 +95,10 @@ def solve_dense(solid, kn, v, w, jump=1.0, order=2, lateral="specular", tau=Fals
         coefs = {}
         for k in range(nv):
             if sd * v[k, j] > 0:
-                coefs[col(f, k)] = w[k] * abs(v[k, j]) / denom[j, sdi]
+                coefs[col(f, k)] = alpha * w[k] * abs(v[k, j]) / denom[j, sdi]
+        if alpha < 1.0:
+            kr = refl[j, k0] if not mir else k0
+            coefs[col(f, kr)] = coefs.get(col(f, kr), 0.0) + (1.0 - alpha)
         return coefs, -r * jump, True
 
     U = nf * nv
@@ -118,7 +123,7 @@ def solve_dense(solid, kn, v, w, jump=1.0, order=2, lateral="specular", tau=Fals
                 terms = []
                 if is_solid(c, j, c[j] - s):
                     C0, C1 = 1.0 / dx, -1.0 / dx
-                    terms.append((a * C1, wall_term(c, j, c[j], -s)))
+                    terms.append((a * C1, wall_term(c, j, c[j], -s, k)))
                 elif order == 1 or is_solid(c, j, c[j] - 2 * s):
                     C0, C1 = 1.0 / dx, -1.0 / dx
                     terms.append((a * C1, h_term(c, j, c[j] - s, k)))
