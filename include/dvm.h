@@ -119,6 +119,12 @@ typedef struct {
      * isothermal flows); the walls re-emit at the wall temperature either way (Eq. 5).  0 (default):
      * dropped.  2D problems and BF16 storage reject it with DVM_EINVAL. */
     int temperature_term;
+    /* Maxwell diffuse-specular walls (Eq. 5): 1 - alpha, the specular fraction of the molecules
+     * leaving a wall, whose h is h(v - 2 n (v.n)) of the molecules reaching it (taken, like the
+     * wall density, at the wall's fluid point from the previous iteration).  0 (default): fully
+     * diffuse, the paper's setting (alpha = 1).  Implemented in 2D; values outside [0, 1], 3D
+     * problems and band pairs reject it with DVM_EINVAL. */
+    double specular_fraction;
 } dvm_options;
 
 /* Fill *opt with the defaults: FP64, second order, specular lateral faces, check interval 100,

@@ -22,9 +22,9 @@
 
 namespace dvm {
 bool half_range_gh(int m, double* c, double* a);
-template <typename T> size_t sweep2d_smem(int T1, int NW, int max_rows);
+template <typename T> size_t sweep2d_smem(int T1, int NW, int max_rows, int spec);
 template <typename T> cudaError_t launch_sweep2d(const SweepArgs2D<T>&, int T1, int xs, int grid, int NW, cudaStream_t);
-template <typename T> cudaError_t sweep2d_occupancy(int T1, int xs, int NW, int max_rows, int* blocks_per_sm);
+template <typename T> cudaError_t sweep2d_occupancy(int T1, int xs, int spec, int NW, int max_rows, int* blocks_per_sm);
 template <typename T> cudaError_t launch_finalize2d(const FinArgs2D<T>&, int nblocks, cudaStream_t);
 template <typename T> cudaError_t launch_init2d(const Prob2D<T>*, int NL, const double* qw, cudaStream_t);
 template <typename T> cudaError_t launch_moments2d(const Prob2D<T>*, double* rho, double* u, cudaStream_t);
@@ -33,7 +33,7 @@ template <typename T>
 cudaError_t launch_warm2d(const Prob2D<T>*, int NL, int par, const double* qw2, const double* vel, const double* rho0,
                           const double* u0, cudaStream_t);
 cudaError_t launch_sweep2d_f32x2(const SweepArgs2D<float>&, int T1, int xs, int grid, int NW, cudaStream_t);
-cudaError_t sweep2d_f32x2_occupancy(int T1, int xs, int NW, int max_rows, int* blocks_per_sm);
+cudaError_t sweep2d_f32x2_occupancy(int T1, int xs, int spec, int NW, int max_rows, int* blocks_per_sm);
 int sweep2d_f32x2_max_rows(int T1, int NW);
 cudaError_t launch_sweep2d_pair(const SweepArgs2D<float>&, int T1, int grid, int NW, cudaStream_t);
 cudaError_t sweep2d_pair_occupancy(int T1, int NW, int max_rows, int NL, int* blocks_per_sm);
@@ -88,6 +88,7 @@ struct dvm_ctx {
     bool pairs = false;              // 2D FP32: two consecutive bands per CTA
     bool sub3 = false;               // 3D lagged-halo subdomains (pencil and tile tables)
     bool tau3 = false;               // 3D temperature term of Eq. 2
+    bool spec2 = false;              // 2D Maxwell walls with alpha < 1 (Eq. 5)
     double* qwt_dev = nullptr;       // 3D: [octant][group][4] sums of W |v|^2 (1, v)
     int T1 = 8, rows = 8, max_rows = 8;
     std::vector<HostProb> hp;
@@ -443,6 +444,34 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
             return fail(c, DVM_ENOMEM, "device allocation failed");
         P.code = code;
         P.lanec = lanec;
+        // Maxwell walls with alpha < 1 (Eq. 5): wall faces (fluid point, axis, side) where the
+        // point's code marks the neighbour solid, and the store of their specular parts
+        P.spec = c->opt.specular_fraction;
+        if (c->spec2) {
+            std::vector<int> fid((size_t)4 * N, -1), faces;
+            for (size_t id = 0; id < N; ++id) {
+                if (H.code[id] & kSolidBit) continue;
+                for (int ju = 0; ju < 4; ++ju)
+                    if (((H.code[id] >> (2 * ju)) & 3) == 2) {
+                        fid[(size_t)ju * N + id] = (int)faces.size();
+                        faces.push_back((int)(id * 4 + ju));
+                    }
+            }
+            P.nfaces = (int)faces.size();
+            int* fid_dev = (int*)dev_alloc(c, fid.size() * sizeof(int));
+            int* faces_dev = (int*)dev_alloc(c, std::max<size_t>(1, faces.size()) * sizeof(int));
+            P.F = (T*)dev_alloc(c, std::max<size_t>(1, (size_t)2 * P.nfaces * 2 * NL) * sizeof(T));
+            if (!fid_dev || !faces_dev || !P.F) return fail(c, DVM_ENOMEM, "device allocation failed");
+            cudaError_t e2;
+            if ((e2 = cudaMemcpyAsync(fid_dev, fid.data(), fid.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream)) ||
+                (!faces.empty() && (e2 = cudaMemcpyAsync(faces_dev, faces.data(), faces.size() * sizeof(int),
+                                                         cudaMemcpyHostToDevice, c->stream))) ||
+                (e2 = cudaStreamSynchronize(c->stream)))
+                return cuda_fail(c, e2, "upload face tables");
+            c->h2d_bytes += (fid.size() + faces.size()) * sizeof(int);
+            P.face_id = fid_dev;
+            P.faces = faces_dev;
+        }
         cudaError_t e = cudaMemcpyAsync(code, H.code.data(), N * sizeof(uint16_t), cudaMemcpyHostToDevice, c->stream);
         c->h2d_bytes += N * sizeof(uint16_t);
         if (e != cudaSuccess) return cuda_fail(c, e, "copy code");
@@ -533,8 +562,8 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     // ---- persistent grid size
     int per_sm = 0;
     if (c->pairs) e = sweep2d_pair_occupancy(c->T1, 2 * c->NW, c->max_rows, c->NL, &per_sm);
-    else if (c->prec == DVM_FP32) e = sweep2d_f32x2_occupancy(c->T1, c->xsub, c->NW, c->max_rows, &per_sm);
-    else e = sweep2d_occupancy<T>(c->T1, c->xsub, c->NW, c->max_rows, &per_sm);
+    else if (c->prec == DVM_FP32) e = sweep2d_f32x2_occupancy(c->T1, c->xsub, c->spec2 ? 1 : 0, c->NW, c->max_rows, &per_sm);
+    else e = sweep2d_occupancy<T>(c->T1, c->xsub, c->spec2 ? 1 : 0, c->NW, c->max_rows, &per_sm);
     if (e != cudaSuccess) return cuda_fail(c, e, "occupancy");
     if (per_sm < 1) return fail(c, DVM_EINVAL, "sweep kernel does not fit on an SM with these tiles");
     int dev = 0, sms = 0;
@@ -946,6 +975,7 @@ dvm_status enqueue_iter_2d(dvm_ctx* c) {
     cudaError_t e = cudaMemsetAsync(c->counters_dev, 0, c->counters_bytes, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "memset counters");
     SweepArgs2D<T> a;
+    a.spec = c->spec2 ? 1 : 0;
     a.prob = (const Prob2D<T>*)c->probs_dev;
     a.items = c->items_dev;
     a.nitems = c->nitems;
@@ -1118,6 +1148,10 @@ void state_segs_2d(const Prob2D<T>& P, size_t NL, int par, std::vector<Seg>& out
     out.push_back({P.P, (size_t)4 * 3 * P.N * sizeof(T)});
     out.push_back({P.gx1 + par * gx, gx * sizeof(T)});
     out.push_back({P.glat + par * gl, gl * sizeof(T)});
+    if (P.spec > 0.0 && P.nfaces > 0) {
+        const size_t fs = (size_t)P.nfaces * 2 * NL;
+        out.push_back({P.F + par * fs, fs * sizeof(T)});
+    }
 }
 
 template <typename T>
@@ -1282,6 +1316,13 @@ dvm_status dvm_create_batch(int nprob, const dvm_geometry* geoms, const double* 
     if (c->opt.temperature_term && c->opt.precision == DVM_BF16_STORE)
         return reject(DVM_EINVAL, "BF16 storage is not implemented with the temperature term");
     c->tau3 = dims == 3 && c->opt.temperature_term != 0;
+    if (!(c->opt.specular_fraction >= 0.0 && c->opt.specular_fraction <= 1.0))
+        return reject(DVM_EINVAL, "specular_fraction (1 - alpha of Eq. 5) must lie in [0, 1]");
+    if (c->opt.specular_fraction > 0.0 && dims != 2)
+        return reject(DVM_EINVAL, "walls with alpha < 1 are implemented for 2D problems");
+    if (c->opt.specular_fraction > 0.0 && c->opt.band_pairs)
+        return reject(DVM_EINVAL, "band pairs are not implemented with alpha < 1");
+    c->spec2 = dims == 2 && c->opt.specular_fraction > 0.0;
     if (c->opt.group_warps < 0) return reject(DVM_EINVAL, "group_warps must not be negative");
     if (c->opt.band_pairs && (dims != 2 || c->opt.precision != DVM_FP32 || c->opt.subdomains[0] > 1 ||
                               c->opt.subdomains[1] > 1))

@@ -57,6 +57,17 @@ struct Prob2D {
     T* src;              // [N][4]  (nu rho', 2 nu u1 + 1, 2 nu u2, 0)
     T* E;                // [N][4]  wall terms per (axis j, upstream side u): index 2 j + u
     T* P;                // [4][3][N] moment partials per quadrant (rho', u1, u2)
+    // Maxwell diffuse-specular walls (Eq. 5) with accommodation alpha < 1: the wall value of a
+    // molecule leaving a wall is alpha rho_s + (1 - alpha) h(x_f, reflected v), the second part
+    // from the previous iteration, kept per wall face (fluid point, axis j, side u with a solid
+    // neighbour at x + (2u - 1) e_j).  spec = 1 - alpha (0: fully diffuse, the paper's setting).
+    double spec;
+    int nfaces;
+    const int* face_id;  // [4][N] face of (axis j, side u) at a point, index 2 j + u, or -1
+    const int* faces;    // [nfaces] point id * 4 + 2 j + u
+    T* F;                // [2][nfaces][2][NL] h' of the molecules moving into each face (parity,
+                         // face, sign bit of the other axis, velocity slot), written by the sweep
+                         // moving into the face, read by the reflected quadrant next iteration
     T* gx1;              // [2][4][nxslots][n2][2][NL] lagged x1 layers (parity, quadrant, slot, row,
                          // layer, lane): the x1 ghosts (slot 0) and the x1 subdomain halos
     T* glat;             // [2][4][nslots][n1][2][NL] lagged x2 layers (parity, quadrant, slot, col,
@@ -81,6 +92,7 @@ struct SweepArgs2D {
     int NL;                     // lanes per quadrant (multiple of 32)
     int max_rows;               // rows per band used to size shared memory
     int parity;                 // ghost buffers: read [parity], write [parity ^ 1]
+    int spec;                   // specular wall parts (Prob2D::spec > 0)
     int* ticket;                // work counter (zeroed before every launch)
     int* status;                // device error word (0 = ok)
     long long timeout_ns;

@@ -29,29 +29,57 @@ struct LaneK {
     T v1, v2, a1, a2, W, Wv1, Wv2, R0, R1, R2, R3;
 };
 
+// Specular wall parts (Eq. 5, alpha < 1) of one lane: face stores of the previous iteration (read
+// where the upstream point of an axis is solid) and of this one (written where the downstream point
+// is solid), each already offset to this lane's slot and the quadrant's other-axis sign bit; face f
+// is at f * stride.
+template <typename T>
+struct SpecLane {
+    const T* prev1;
+    const T* prev2;
+    T* next1;
+    T* next2;
+    size_t stride;
+    T spec;          // 1 - alpha
+};
+
 // Processes CH consecutive points (columns i0..i0+CH-1 of the tile) of one row.
 // rec: records of this row; rb1/rb2: the two rows below (updated in place); hp1/hp2: x1 upstream.
-template <typename T, int T1, int CH, bool FULL>
+template <typename T, int T1, int CH, bool FULL, bool SPEC>
 __device__ __forceinline__ void row_chunk(const T* __restrict__ rec, int i0, int width, const LaneK<T>& L,
                                           T (&rb1)[T1], T (&rb2)[T1], T& hp1, T& hp2, T (&m0)[CH],
-                                          T (&m1)[CH], T (&m2)[CH]) {
+                                          T (&m1)[CH], T (&m2)[CH], const SpecLane<T>& SL) {
     using V = typename Vec4<T>::type;
+    constexpr int RW = SPEC ? 16 : kRecWords;
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
         const int i = i0 + c;
         if (FULL || i < width) {
-            const V* R = reinterpret_cast<const V*>(rec + i * kRecWords);
+            const V* R = reinterpret_cast<const V*>(rec + i * RW);
             const V A = R[0];
             const V B = R[1];
             const V C = R[2];
             // numerator of Eq. 10 solved for h(x): nu (rho' + 2 u.v) + v1 plus the upwind terms
             const T S = fma(A.z, L.v2, fma(A.y, L.v1, A.x));
-            const T t1 = fma(B.x, hp1, fma(B.y, hp2, A.w));
-            const T t2 = fma(B.z, rb1[i], fma(B.w, rb2[i], C.x));
+            T t1 = fma(B.x, hp1, fma(B.y, hp2, A.w));
+            T t2 = fma(B.z, rb1[i], fma(B.w, rb2[i], C.x));
+            V D;
+            if constexpr (SPEC) {
+                // the wall term holds alpha rho_s' (+ shift); add (1 - alpha) h'(x, reflected v)
+                D = R[3];
+                const int fu1 = as_bits(D.x), fu2 = as_bits(D.y);
+                if (fu1 >= 0) t1 = fma(SL.spec, SL.prev1[(size_t)fu1 * SL.stride], t1);
+                if (fu2 >= 0) t2 = fma(SL.spec, SL.prev2[(size_t)fu2 * SL.stride], t2);
+            }
             const T num = fma(L.a2, t2, fma(L.a1, t1, S));
             const int rs = as_bits(C.y);
             const T Rv = (rs & 2) ? ((rs & 1) ? L.R3 : L.R2) : ((rs & 1) ? L.R1 : L.R0);
             const T h = num * Rv;
+            if constexpr (SPEC) {   // molecules moving into a face downstream: kept for its reflection
+                const int fd1 = as_bits(D.z), fd2 = as_bits(D.w);
+                if (fd1 >= 0) SL.next1[(size_t)fd1 * SL.stride] = h;
+                if (fd2 >= 0) SL.next2[(size_t)fd2 * SL.stride] = h;
+            }
             hp2 = hp1;
             hp1 = h;
             rb2[i] = rb1[i];
@@ -67,22 +95,23 @@ __device__ __forceinline__ void row_chunk(const T* __restrict__ rec, int i0, int
     }
 }
 
-template <typename T, int T1, bool FULL>
+template <typename T, int T1, bool FULL, bool SPEC>
 __device__ __forceinline__ void sweep_tile_rows(const T* __restrict__ rec, T* __restrict__ part,
                                                 T* __restrict__ carry, int nrows, int width, int RB,
                                                 int warp, int lane, const LaneK<T>& L, T (&rb1)[T1],
-                                                T (&rb2)[T1]) {
+                                                T (&rb2)[T1], const SpecLane<T>& SL) {
     constexpr int CH = 8;                       // points reduced together
+    constexpr int RW = SPEC ? 16 : kRecWords;
     for (int r = 0; r < nrows; ++r) {
         T* cr = carry + ((size_t)(warp * RB + r) * 2) * 32 + lane;
         T hp1 = cr[0];
         T hp2 = cr[32];
-        const T* rrow = rec + (size_t)r * T1 * kRecWords;
+        const T* rrow = rec + (size_t)r * T1 * RW;
         T* prow = part + ((size_t)(warp * RB + r) * T1) * 3;
 #pragma unroll
         for (int i0 = 0; i0 < T1; i0 += CH) {
             T m0[CH], m1[CH], m2[CH];
-            row_chunk<T, T1, CH, FULL>(rrow, i0, width, L, rb1, rb2, hp1, hp2, m0, m1, m2);
+            row_chunk<T, T1, CH, FULL, SPEC>(rrow, i0, width, L, rb1, rb2, hp1, hp2, m0, m1, m2, SL);
             const T s0 = reduce_scatter<T, CH>(m0, lane);
             const T s1 = reduce_scatter<T, CH>(m1, lane);
             const T s2 = reduce_scatter<T, CH>(m2, lane);
@@ -99,9 +128,10 @@ __device__ __forceinline__ void sweep_tile_rows(const T* __restrict__ rec, T* __
     }
 }
 
-template <typename T, int T1, bool XS>
+template <typename T, int T1, bool XS, bool SPEC>
 __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs2D<T> a) {
     using V = typename Vec4<T>::type;
+    constexpr int RW = SPEC ? 16 : kRecWords;   // record words (face ids in a fourth vector)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
     __shared__ int s_abort;
@@ -109,8 +139,8 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs2D<T> a) {
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int RB = a.max_rows;
-    T* rec = reinterpret_cast<T*>(smem_raw);                 // [RB][T1][kRecWords]
-    T* part = rec + (size_t)RB * T1 * kRecWords;             // [NW][RB][T1][3]
+    T* rec = reinterpret_cast<T*>(smem_raw);                 // [RB][T1][RW]
+    T* part = rec + (size_t)RB * T1 * RW;                    // [NW][RB][T1][3]
     T* carry = part + (size_t)NW * RB * T1 * 3;              // [NW][RB][2][32]
     const int wl = warp * 32 + lane;
     const size_t NL = (size_t)a.NL;
@@ -143,6 +173,17 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs2D<T> a) {
             L.R0 = lc[7]; L.R1 = lc[8]; L.R2 = lc[9]; L.R3 = lc[10];
         }
         const int par = a.parity;
+        SpecLane<T> SL{};
+        if constexpr (SPEC) {
+            // x1 faces are told apart by the x2 sign bit of the quadrant, x2 faces by the x1 bit
+            const size_t plane = (size_t)P->nfaces * 2 * NL;
+            SL.stride = 2 * NL;
+            SL.prev1 = P->F + par * plane + (size_t)s2neg * NL + wl;
+            SL.prev2 = P->F + par * plane + (size_t)s1neg * NL + wl;
+            SL.next1 = P->F + (par ^ 1) * plane + (size_t)s2neg * NL + wl;
+            SL.next2 = P->F + (par ^ 1) * plane + (size_t)s1neg * NL + wl;
+            SL.spec = (T)P->spec;
+        }
         // x1 upstream of a tile from a lagged slot: the x1 ghost layers of the previous iteration
         // (Eq. 7, source form; slot 0) or, with x1 subdomains, a subdomain halo; and the carry of the
         // last tile into the slot the next iteration reads
@@ -182,6 +223,7 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs2D<T> a) {
                 const int r = idx / T1;
                 const int i = idx - r * T1;
                 V r0 = Vec4<T>::make(0, 0, 0, 0), r1 = r0, r2 = r0;
+                V r3 = Vec4<T>::make(bits_as(T(0), -1), bits_as(T(0), -1), bits_as(T(0), -1), bits_as(T(0), -1));
                 if (i < width) {
                     const int ic = c0 + i;
                     const int x = s1neg ? n1 - 1 - ic : ic;
@@ -200,12 +242,20 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs2D<T> a) {
                                            cb == 2 ? T(0) : (cb == 1 ? T(1) : K1o), cb == 0 ? K2o : T(0));
                         r2 = Vec4<T>::make(s2neg ? e.w : e.z, bits_as(T(0), (ca != 0) | ((cb != 0) << 1)),
                                            T(0), T(0));
+                        if constexpr (SPEC) {
+                            // faces: upstream (read) and downstream (written) along x1 and x2
+                            const int* fi = P->face_id;
+                            const size_t Nn = (size_t)N;
+                            r3 = Vec4<T>::make(bits_as(T(0), fi[(0 + s1neg) * Nn + id]), bits_as(T(0), fi[(2 + s2neg) * Nn + id]),
+                                               bits_as(T(0), fi[(1 - s1neg) * Nn + id]), bits_as(T(0), fi[(3 - s2neg) * Nn + id]));
+                        }
                     }
                 }
-                V* R = reinterpret_cast<V*>(rec + (size_t)idx * kRecWords);
+                V* R = reinterpret_cast<V*>(rec + (size_t)idx * RW);
                 R[0] = r0;
                 R[1] = r1;
                 R[2] = r2;
+                if constexpr (SPEC) R[3] = r3;
             }
             __syncthreads();
             if (s_abort) return;
@@ -228,9 +278,9 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs2D<T> a) {
                 }
             }
             if (width == T1)
-                sweep_tile_rows<T, T1, true>(rec, part, carry, nrows, width, RB, warp, lane, L, rb1, rb2);
+                sweep_tile_rows<T, T1, true, SPEC>(rec, part, carry, nrows, width, RB, warp, lane, L, rb1, rb2, SL);
             else
-                sweep_tile_rows<T, T1, false>(rec, part, carry, nrows, width, RB, warp, lane, L, rb1, rb2);
+                sweep_tile_rows<T, T1, false, SPEC>(rec, part, carry, nrows, width, RB, warp, lane, L, rb1, rb2, SL);
             // top edge for the band above, or the x2 ghost layers of the next iteration (Eq. 8 /
             // periodic: the reflected quadrant reads the same lane)
             {
@@ -327,7 +377,9 @@ __global__ void __launch_bounds__(256) finalize2d_kernel(const FinArgs2D<T> a) {
                     if (c == 2) {
                         // first-order stencil: wall value of face (x, j, sigma), shifted by the
                         // source-form offset sigma dx on x1 faces
-                        val = wall_density(P, id, j, sigma) + (j == 0 ? sigma * P->dx : 0.0);
+                        // (Eq. 5: alpha times the diffuse value; the specular part is added per
+                        // velocity by the sweep)
+                        val = (1.0 - P->spec) * wall_density(P, id, j, sigma) + (j == 0 ? sigma * P->dx : 0.0);
                     }
                     // case 1 (only the second upstream point solid) is first order on the fluid
                     // neighbour: no wall term
@@ -409,6 +461,11 @@ __global__ void init2d_kernel(const Prob2D<T>* prob, int NL, const double* qw /*
         const int col = (q & 1) ? n1 - 1 - ic : ic;
         P->glat[idx] = (T)(col * P->dx);
     }
+    if (P->spec > 0.0)   // face stores of both parities: h' = x1 at the face's fluid point
+        for (size_t idx = t0; idx < (size_t)2 * P->nfaces * 2 * nl; idx += stride) {
+            const int id = P->faces[(idx / (2 * nl)) % P->nfaces] >> 2;
+            P->F[idx] = (T)((id % n1) * P->dx);
+        }
 }
 
 // Warm start: the state an iteration leaves when it produced the local linearised equilibrium
@@ -471,6 +528,17 @@ __global__ void warm2d_kernel(const Prob2D<T>* P, int NL, int par, const double*
         P->glat[(((((size_t)par * 4 + qd) * ns + sl) * n1 + ic) * 2 + layer) * nl + l] =
             (T)h0(x, y, vel + ((size_t)q * nl + l) * 2);
     }
+    // face stores (specular wall part, Eq. 5): h0' at the face's fluid point for the velocity slot
+    // of the quadrant that moves into the face (s_j = the face side, other-axis sign bit o)
+    if (P->spec > 0.0)
+        for (size_t idx = t0; idx < (size_t)P->nfaces * 2 * nl; idx += stride) {
+            const int l = idx % nl;
+            const int o = (idx / nl) % 2;
+            const int f = P->faces[idx / (2 * nl)];
+            const int id = f >> 2, j = (f >> 1) & 1, u = f & 1;
+            const int qw = (j == 0) ? ((1 - u) | (o << 1)) : (o | ((1 - u) << 1));
+            P->F[(size_t)par * P->nfaces * 2 * nl + idx] = (T)h0(id % n1, id / n1, vel + ((size_t)qw * nl + l) * 2);
+        }
 }
 
 // rho (paper variables, ramp restored) and u of one problem into double buffers; solid = 0.
@@ -517,40 +585,52 @@ __global__ void wall2d_kernel(const Prob2D<T>* prob, double* out) {
 // ---------------------------------------------------------------- launchers
 
 template <typename T>
-size_t sweep2d_smem(int T1, int NW, int max_rows) {
-    return sizeof(T) * ((size_t)max_rows * T1 * kRecWords + (size_t)NW * max_rows * T1 * 3 +
+size_t sweep2d_smem(int T1, int NW, int max_rows, int spec) {
+    return sizeof(T) * ((size_t)max_rows * T1 * (spec ? 16 : kRecWords) + (size_t)NW * max_rows * T1 * 3 +
                         (size_t)NW * max_rows * 2 * 32);
 }
 
-template <typename T, int T1, bool XS>
+template <typename T, int T1, bool XS, bool SPEC>
 static cudaError_t launch_sweep_t(const SweepArgs2D<T>& a, int grid, int NW, cudaStream_t st) {
-    const size_t smem = sweep2d_smem<T>(T1, NW, a.max_rows);
-    cudaError_t e = cudaFuncSetAttribute(sweep2d_kernel<T, T1, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = sweep2d_smem<T>(T1, NW, a.max_rows, SPEC);
+    cudaError_t e = cudaFuncSetAttribute(sweep2d_kernel<T, T1, XS, SPEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    sweep2d_kernel<T, T1, XS><<<grid, NW * 32, smem, st>>>(a);
+    sweep2d_kernel<T, T1, XS, SPEC><<<grid, NW * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-// xs: x1 subdomains (tile tables and lagged x1 halos)
+template <typename T, int T1>
+static cudaError_t launch_sweep_tt(const SweepArgs2D<T>& a, int xs, int grid, int NW, cudaStream_t st) {
+    if (a.spec) return xs ? launch_sweep_t<T, T1, true, true>(a, grid, NW, st) : launch_sweep_t<T, T1, false, true>(a, grid, NW, st);
+    return xs ? launch_sweep_t<T, T1, true, false>(a, grid, NW, st) : launch_sweep_t<T, T1, false, false>(a, grid, NW, st);
+}
+
+// xs: x1 subdomains (tile tables and lagged x1 halos); a.spec: specular wall parts (Eq. 5)
 template <typename T>
 cudaError_t launch_sweep2d(const SweepArgs2D<T>& a, int T1, int xs, int grid, int NW, cudaStream_t st) {
-    if (T1 == 8) return xs ? launch_sweep_t<T, 8, true>(a, grid, NW, st) : launch_sweep_t<T, 8, false>(a, grid, NW, st);
-    if (T1 == 16) return xs ? launch_sweep_t<T, 16, true>(a, grid, NW, st) : launch_sweep_t<T, 16, false>(a, grid, NW, st);
+    if (T1 == 8) return launch_sweep_tt<T, 8>(a, xs, grid, NW, st);
+    if (T1 == 16) return launch_sweep_tt<T, 16>(a, xs, grid, NW, st);
     return cudaErrorInvalidValue;
 }
 
-template <typename T, int T1, bool XS>
+template <typename T, int T1, bool XS, bool SPEC>
 static cudaError_t occ2(int NW, int max_rows, int* blocks_per_sm) {
-    const size_t smem = sweep2d_smem<T>(T1, NW, max_rows);
-    cudaError_t e = cudaFuncSetAttribute(sweep2d_kernel<T, T1, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = sweep2d_smem<T>(T1, NW, max_rows, SPEC);
+    cudaError_t e = cudaFuncSetAttribute(sweep2d_kernel<T, T1, XS, SPEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep2d_kernel<T, T1, XS>, NW * 32, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep2d_kernel<T, T1, XS, SPEC>, NW * 32, smem);
+}
+
+template <typename T, int T1>
+static cudaError_t occ2_t(int xs, int spec, int NW, int max_rows, int* bps) {
+    if (spec) return xs ? occ2<T, T1, true, true>(NW, max_rows, bps) : occ2<T, T1, false, true>(NW, max_rows, bps);
+    return xs ? occ2<T, T1, true, false>(NW, max_rows, bps) : occ2<T, T1, false, false>(NW, max_rows, bps);
 }
 
 template <typename T>
-cudaError_t sweep2d_occupancy(int T1, int xs, int NW, int max_rows, int* blocks_per_sm) {
-    if (T1 == 8) return xs ? occ2<T, 8, true>(NW, max_rows, blocks_per_sm) : occ2<T, 8, false>(NW, max_rows, blocks_per_sm);
-    if (T1 == 16) return xs ? occ2<T, 16, true>(NW, max_rows, blocks_per_sm) : occ2<T, 16, false>(NW, max_rows, blocks_per_sm);
+cudaError_t sweep2d_occupancy(int T1, int xs, int spec, int NW, int max_rows, int* blocks_per_sm) {
+    if (T1 == 8) return occ2_t<T, 8>(xs, spec, NW, max_rows, blocks_per_sm);
+    if (T1 == 16) return occ2_t<T, 16>(xs, spec, NW, max_rows, blocks_per_sm);
     return cudaErrorInvalidValue;
 }
 
@@ -586,9 +666,9 @@ cudaError_t launch_wall2d(const Prob2D<T>* prob_dev, double* out, cudaStream_t s
 }
 
 #define DVM_INSTANTIATE(T)                                                                      \
-    template size_t sweep2d_smem<T>(int, int, int);                                            \
+    template size_t sweep2d_smem<T>(int, int, int, int);                                       \
     template cudaError_t launch_sweep2d<T>(const SweepArgs2D<T>&, int, int, int, int, cudaStream_t); \
-    template cudaError_t sweep2d_occupancy<T>(int, int, int, int, int*);                       \
+    template cudaError_t sweep2d_occupancy<T>(int, int, int, int, int, int*);                  \
     template cudaError_t launch_finalize2d<T>(const FinArgs2D<T>&, int, cudaStream_t);          \
     template cudaError_t launch_init2d<T>(const Prob2D<T>*, int, const double*, cudaStream_t);  \
     template cudaError_t launch_warm2d<T>(const Prob2D<T>*, int, int, const double*, const double*, \

@@ -41,15 +41,17 @@ struct LaneQ {
 struct RawPoint {           // global data of one point needed to build its record
     float4 s, e;
     int code;
+    int4 f;                 // wall faces (specular parts): upstream x1, x2; downstream x1, x2
 };
 
 __device__ __forceinline__ float2 dup(float x) { return make_float2(x, x); }
 
 }  // namespace
 
-template <int T1, bool XS>
+template <int T1, bool XS, bool SPEC>
 __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<float> a) {
     constexpr int kLPP = 32 / T1;               // lanes per point after the reduce-scatter
+    constexpr int RF = SPEC ? 16 : kRecF;       // record floats (face ids in the last four)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
     __shared__ int s_abort;
@@ -58,8 +60,8 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int RB = a.max_rows;
-    float* rec = reinterpret_cast<float*>(smem_raw);                    // [2][RB][T1][kRecF]
-    float* part = rec + (size_t)2 * RB * T1 * kRecF;                     // [NW][RB][T1][3]
+    float* rec = reinterpret_cast<float*>(smem_raw);                    // [2][RB][T1][RF]
+    float* part = rec + (size_t)2 * RB * T1 * RF;                        // [NW][RB][T1][3]
     float* carry = part + (size_t)NW * RB * T1 * 3;                      // [NW][RB][2][128]
     float* rtab = carry + (size_t)NW * RB * 2 * 128;                     // [NW][4][128]
     unsigned* rmask = reinterpret_cast<unsigned*>(rtab + (size_t)NW * 4 * 128);  // [2][RB]
@@ -117,6 +119,22 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
                     make_float4(lc[7 + rs], lc[kLaneConsts + 7 + rs], lc[2 * kLaneConsts + 7 + rs], lc[3 * kLaneConsts + 7 + rs]);
         }
         const int par = a.parity;
+        // specular wall parts (Eq. 5, alpha < 1): face stores of the previous iteration (read) and
+        // of this one (written), at this lane's four slots; x1 faces are told apart by the
+        // quadrant's x2 sign bit, x2 faces by its x1 bit
+        const float* fprev1 = nullptr;
+        const float* fprev2 = nullptr;
+        float* fnext1 = nullptr;
+        float* fnext2 = nullptr;
+        float2 specP = make_float2(0.f, 0.f);
+        if constexpr (SPEC) {
+            const size_t plane = (size_t)P->nfaces * 2 * NL;
+            fprev1 = P->F + par * plane + (size_t)s2neg * NL + kVL * wl;
+            fprev2 = P->F + par * plane + (size_t)s1neg * NL + kVL * wl;
+            fnext1 = P->F + (par ^ 1) * plane + (size_t)s2neg * NL + kVL * wl;
+            fnext2 = P->F + (par ^ 1) * plane + (size_t)s1neg * NL + kVL * wl;
+            specP = dup((float)P->spec);
+        }
         // x1 carry from a lagged slot (the x1 ghosts, or with x1 subdomains a subdomain halo of the
         // previous iteration) / into a slot for the next iteration
         auto carry_in = [&](int slot) {
@@ -171,13 +189,19 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
                         if (!(raw[k].code & kSolidBit)) {
                             raw[k].s = reinterpret_cast<const float4*>(P->src)[id];
                             raw[k].e = reinterpret_cast<const float4*>(P->E)[id];
+                            if constexpr (SPEC) {
+                                const int* fi = P->face_id;
+                                const size_t Nn = (size_t)N;
+                                raw[k].f = make_int4(fi[(0 + s1neg) * Nn + id], fi[(2 + s2neg) * Nn + id],
+                                                     fi[(1 - s1neg) * Nn + id], fi[(3 - s2neg) * Nn + id]);
+                            }
                         }
                     }
                 }
             }
         };
         auto store_rec = [&](int buf, const RawPoint (&raw)[kMaxRounds]) {
-            float* rb = rec + (size_t)buf * RB * T1 * kRecF;
+            float* rb = rec + (size_t)buf * RB * T1 * RF;
             unsigned* mk = rmask + buf * RB;
 #pragma unroll
             for (int k = 0; k < kMaxRounds; ++k) {
@@ -198,10 +222,12 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
                         o1 = make_float4(E1, ca == 2 ? 0.f : (ca == 1 ? 1.f : K1o), ca == 0 ? K2o : 0.f, E2);
                         o2 = make_float4(cb == 2 ? 0.f : (cb == 1 ? 1.f : K1o), cb == 0 ? K2o : 0.f, 0.f, 0.f);
                     }
-                    float4* R = reinterpret_cast<float4*>(rb + (size_t)idx * kRecF);
+                    float4* R = reinterpret_cast<float4*>(rb + (size_t)idx * RF);
                     R[0] = o0;
                     R[1] = o1;
                     R[2] = o2;
+                    if constexpr (SPEC)
+                        reinterpret_cast<int4*>(R)[3] = fluid ? raw[k].f : make_int4(-1, -1, -1, -1);
                 }
                 const unsigned bits = __ballot_sync(0xffffffffu, fluid);
                 if (lane == 0) {
@@ -241,7 +267,7 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
             }
             __syncthreads();
             if (s_abort) return;
-            const float* rbuf = rec + (size_t)buf * RB * T1 * kRecF;
+            const float* rbuf = rec + (size_t)buf * RB * T1 * RF;
             const unsigned* mk = rmask + buf * RB;
             // the two rows below: previous band's top edge or the x2 ghost layers
             float4 rb1[T1], rb2[T1];
@@ -271,15 +297,23 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
                     const float4 c2 = *reinterpret_cast<const float4*>(cr + 128);
                     float2 hp1[2] = {make_float2(c1.x, c1.y), make_float2(c1.z, c1.w)};
                     float2 hp2[2] = {make_float2(c2.x, c2.y), make_float2(c2.z, c2.w)};
-                    const float* rrow = rbuf + (size_t)r * T1 * kRecF;
+                    const float* rrow = rbuf + (size_t)r * T1 * RF;
                     float m0[T1], m1[T1], m2[T1];
 #pragma unroll
                     for (int i = 0; i < T1; ++i) {
                         if (FULL || i < width) {
-                            const float4* Rp = reinterpret_cast<const float4*>(rrow + i * kRecF);
+                            const float4* Rp = reinterpret_cast<const float4*>(rrow + i * RF);
                             const float4 A = Rp[0];                 // a b1 b2 roff
                             const float4 B = Rp[1];                 // E1 K1x K2x E2
                             const float2 C = *reinterpret_cast<const float2*>(Rp + 2);   // K1y K2y
+                            // specular parts of the upstream wall values: (1 - alpha) h'(x, reflected v)
+                            int4 Fi = make_int4(-1, -1, -1, -1);
+                            float4 Fx = make_float4(0.f, 0.f, 0.f, 0.f), Fy = Fx;
+                            if constexpr (SPEC) {
+                                Fi = reinterpret_cast<const int4*>(Rp)[3];
+                                if (Fi.x >= 0) Fx = *reinterpret_cast<const float4*>(fprev1 + (size_t)Fi.x * 2 * NL);
+                                if (Fi.y >= 0) Fy = *reinterpret_cast<const float4*>(fprev2 + (size_t)Fi.y * 2 * NL);
+                            }
                             const float4 Rv = *reinterpret_cast<const float4*>(my_rtab + __float_as_int(A.w));
                             const float2 aP = dup(A.x), b1P = dup(A.y), b2P = dup(A.z);
                             const float2 E1P = dup(B.x), K1xP = dup(B.y), K2xP = dup(B.z), E2P = dup(B.w);
@@ -292,9 +326,11 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
                                 const float2 up1 = k ? rb1b : rb1a;
                                 const float2 up2 = k ? rb2b : rb2a;
                                 const float2 S = fma2(b2P, L.v2[k], fma2(b1P, L.v1[k], aP));
-                                const float2 t2 = fma2(K1yP, up1, fma2(K2yP, up2, E2P));
+                                float2 t2 = fma2(K1yP, up1, fma2(K2yP, up2, E2P));
+                                if constexpr (SPEC) t2 = fma2(specP, k ? make_float2(Fy.z, Fy.w) : make_float2(Fy.x, Fy.y), t2);
                                 const float2 base = fma2(L.a2[k], t2, S);
-                                const float2 t1 = fma2(K1xP, hp1[k], fma2(K2xP, hp2[k], E1P));
+                                float2 t1 = fma2(K1xP, hp1[k], fma2(K2xP, hp2[k], E1P));
+                                if constexpr (SPEC) t1 = fma2(specP, k ? make_float2(Fx.z, Fx.w) : make_float2(Fx.x, Fx.y), t1);
                                 const float2 Rk = k ? make_float2(Rv.z, Rv.w) : make_float2(Rv.x, Rv.y);
                                 h[k] = mul2(fma2(L.a1[k], t1, base), Rk);
                                 hp2[k] = hp1[k];
@@ -302,6 +338,10 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
                             }
                             rb2[i] = rb1[i];
                             rb1[i] = make_float4(h[0].x, h[0].y, h[1].x, h[1].y);
+                            if constexpr (SPEC) {   // molecules moving into a downstream face
+                                if (Fi.z >= 0) *reinterpret_cast<float4*>(fnext1 + (size_t)Fi.z * 2 * NL) = rb1[i];
+                                if (Fi.w >= 0) *reinterpret_cast<float4*>(fnext2 + (size_t)Fi.w * 2 * NL) = rb1[i];
+                            }
                             const float2 p0 = fma2(L.W[1], h[1], mul2(L.W[0], h[0]));
                             const float2 p1 = fma2(L.Wv1[1], h[1], mul2(L.Wv1[0], h[0]));
                             const float2 p2 = fma2(L.Wv2[1], h[1], mul2(L.Wv2[0], h[0]));
@@ -372,8 +412,8 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
     }
 }
 
-size_t sweep2d_f32x2_smem(int T1, int NW, int max_rows) {
-    return sizeof(float) * ((size_t)2 * max_rows * T1 * kRecF + (size_t)NW * max_rows * T1 * 3 +
+size_t sweep2d_f32x2_smem(int T1, int NW, int max_rows, int spec) {
+    return sizeof(float) * ((size_t)2 * max_rows * T1 * (spec ? 16 : kRecF) + (size_t)NW * max_rows * T1 * 3 +
                             (size_t)NW * max_rows * 2 * 128 + (size_t)NW * 4 * 128) +
            sizeof(unsigned) * (size_t)2 * max_rows;
 }
@@ -382,33 +422,45 @@ int sweep2d_f32x2_max_rows(int T1, int NW) { return kMaxRounds * NW * 32 / T1; }
 
 int sweep2d_f32x2_velocities_per_lane() { return kVL; }
 
-template <int T1, bool XS>
+template <int T1, bool XS, bool SPEC>
 static cudaError_t launch_f32x2_t(const SweepArgs2D<float>& a, int grid, int NW, cudaStream_t st) {
-    const size_t smem = sweep2d_f32x2_smem(T1, NW, a.max_rows);
-    cudaError_t e = cudaFuncSetAttribute(sweep2d_f32x2_kernel<T1, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = sweep2d_f32x2_smem(T1, NW, a.max_rows, SPEC);
+    cudaError_t e = cudaFuncSetAttribute(sweep2d_f32x2_kernel<T1, XS, SPEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    sweep2d_f32x2_kernel<T1, XS><<<grid, NW * 32, smem, st>>>(a);
+    sweep2d_f32x2_kernel<T1, XS, SPEC><<<grid, NW * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-// xs: x1 subdomains (tile tables and lagged x1 halos)
+template <int T1>
+static cudaError_t launch_f32x2_tt(const SweepArgs2D<float>& a, int xs, int grid, int NW, cudaStream_t st) {
+    if (a.spec) return xs ? launch_f32x2_t<T1, true, true>(a, grid, NW, st) : launch_f32x2_t<T1, false, true>(a, grid, NW, st);
+    return xs ? launch_f32x2_t<T1, true, false>(a, grid, NW, st) : launch_f32x2_t<T1, false, false>(a, grid, NW, st);
+}
+
+// xs: x1 subdomains (tile tables and lagged x1 halos); a.spec: specular wall parts
 cudaError_t launch_sweep2d_f32x2(const SweepArgs2D<float>& a, int T1, int xs, int grid, int NW, cudaStream_t st) {
-    if (T1 == 8) return xs ? launch_f32x2_t<8, true>(a, grid, NW, st) : launch_f32x2_t<8, false>(a, grid, NW, st);
-    if (T1 == 4) return xs ? launch_f32x2_t<4, true>(a, grid, NW, st) : launch_f32x2_t<4, false>(a, grid, NW, st);
+    if (T1 == 8) return launch_f32x2_tt<8>(a, xs, grid, NW, st);
+    if (T1 == 4) return launch_f32x2_tt<4>(a, xs, grid, NW, st);
     return cudaErrorInvalidValue;
 }
 
-template <int T1, bool XS>
+template <int T1, bool XS, bool SPEC>
 static cudaError_t occupancy_f32x2_t(int NW, int max_rows, int* blocks_per_sm) {
-    const size_t smem = sweep2d_f32x2_smem(T1, NW, max_rows);
-    cudaError_t e = cudaFuncSetAttribute(sweep2d_f32x2_kernel<T1, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = sweep2d_f32x2_smem(T1, NW, max_rows, SPEC);
+    cudaError_t e = cudaFuncSetAttribute(sweep2d_f32x2_kernel<T1, XS, SPEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep2d_f32x2_kernel<T1, XS>, NW * 32, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep2d_f32x2_kernel<T1, XS, SPEC>, NW * 32, smem);
 }
 
-cudaError_t sweep2d_f32x2_occupancy(int T1, int xs, int NW, int max_rows, int* blocks_per_sm) {
-    if (T1 == 8) return xs ? occupancy_f32x2_t<8, true>(NW, max_rows, blocks_per_sm) : occupancy_f32x2_t<8, false>(NW, max_rows, blocks_per_sm);
-    if (T1 == 4) return xs ? occupancy_f32x2_t<4, true>(NW, max_rows, blocks_per_sm) : occupancy_f32x2_t<4, false>(NW, max_rows, blocks_per_sm);
+template <int T1>
+static cudaError_t occupancy_f32x2_tt(int xs, int spec, int NW, int max_rows, int* bps) {
+    if (spec) return xs ? occupancy_f32x2_t<T1, true, true>(NW, max_rows, bps) : occupancy_f32x2_t<T1, false, true>(NW, max_rows, bps);
+    return xs ? occupancy_f32x2_t<T1, true, false>(NW, max_rows, bps) : occupancy_f32x2_t<T1, false, false>(NW, max_rows, bps);
+}
+
+cudaError_t sweep2d_f32x2_occupancy(int T1, int xs, int spec, int NW, int max_rows, int* blocks_per_sm) {
+    if (T1 == 8) return occupancy_f32x2_tt<8>(xs, spec, NW, max_rows, blocks_per_sm);
+    if (T1 == 4) return occupancy_f32x2_tt<4>(xs, spec, NW, max_rows, blocks_per_sm);
     return cudaErrorInvalidValue;
 }
 

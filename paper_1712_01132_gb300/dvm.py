@@ -49,6 +49,7 @@ class dvm_options(ctypes.Structure):
         ("band_pairs", ctypes.c_int),
         ("group_warps", ctypes.c_int),
         ("temperature_term", ctypes.c_int),
+        ("specular_fraction", ctypes.c_double),
     ]
 
 
@@ -206,7 +207,7 @@ class _TorchAllocator:
 
 def make_options(precision="fp64", stencil_order=2, lateral="specular", check_interval=100, stream=None,
                  tile_x1=0, band_rows=0, torch_memory=True, use_graph=False, subdomains=(1, 1, 1),
-                 band_pairs=False, group_warps=0, temperature_term=False):
+                 band_pairs=False, group_warps=0, temperature_term=False, specular_fraction=0.0):
     """dvm_options with torch's current stream (unless stream is given) and, by default, torch's
     caching allocator for device memory.  Returns (options, keepalive)."""
     o = dvm_default_options()
@@ -220,6 +221,7 @@ def make_options(precision="fp64", stencil_order=2, lateral="specular", check_in
     o.band_pairs = 1 if band_pairs else 0
     o.group_warps = int(group_warps)
     o.temperature_term = 1 if temperature_term else 0
+    o.specular_fraction = float(specular_fraction)
     for j in range(3):
         o.subdomains[j] = int(subdomains[j])
     keep = []
