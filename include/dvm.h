@@ -122,8 +122,8 @@ typedef struct {
     /* Maxwell diffuse-specular walls (Eq. 5): 1 - alpha, the specular fraction of the molecules
      * leaving a wall, whose h is h(v - 2 n (v.n)) of the molecules reaching it (taken, like the
      * wall density, at the wall's fluid point from the previous iteration).  0 (default): fully
-     * diffuse, the paper's setting (alpha = 1).  Implemented in 2D; values outside [0, 1], 3D
-     * problems and band pairs reject it with DVM_EINVAL. */
+     * diffuse, the paper's setting (alpha = 1).  Values outside [0, 1], BF16 storage and band
+     * pairs reject it with DVM_EINVAL. */
     double specular_fraction;
 } dvm_options;
 

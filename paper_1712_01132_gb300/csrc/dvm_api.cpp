@@ -38,12 +38,12 @@ int sweep2d_f32x2_max_rows(int T1, int NW);
 cudaError_t launch_sweep2d_pair(const SweepArgs2D<float>&, int T1, int grid, int NW, cudaStream_t);
 cudaError_t sweep2d_pair_occupancy(int T1, int NW, int max_rows, int NL, int* blocks_per_sm);
 int sweep2d_f32x2_velocities_per_lane();
-template <typename T> size_t sweep3d_smem(int T1, int NW, int R2, int R3, int tau);
-size_t sweep3d_f32x2_smem(int T1, int NW, int R2, int R3, int tau);
+template <typename T> size_t sweep3d_smem(int T1, int NW, int R2, int R3, int tau, int spec);
+size_t sweep3d_f32x2_smem(int T1, int NW, int R2, int R3, int tau, int spec);
 int sweep3d_f32x2_velocities_per_lane();
 cudaError_t launch_sweep3d_f32x2(const SweepArgs3D<float>&, int grid, int NW, cudaStream_t);
-cudaError_t sweep3d_f32x2_occupancy(int T1, int NW, int R2, int R3, int bf16, int sub, int tau, int* blocks_per_sm);
-template <typename T> cudaError_t sweep3d_occupancy(int T1, int NW, int R2, int R3, int bf16, int sub, int tau, int* blocks_per_sm);
+cudaError_t sweep3d_f32x2_occupancy(int T1, int NW, int R2, int R3, int bf16, int sub, int tau, int spec, int* blocks_per_sm);
+template <typename T> cudaError_t sweep3d_occupancy(int T1, int NW, int R2, int R3, int bf16, int sub, int tau, int spec, int* blocks_per_sm);
 template <typename T> cudaError_t launch_sweep3d(const SweepArgs3D<T>&, int grid, int NW, cudaStream_t);
 template <typename T> cudaError_t launch_finalize3d(const FinArgs3D<T>&, int nblocks, cudaStream_t);
 template <typename T> cudaError_t launch_init3d(const Prob3D<T>*, int NL, const double* qw, const double* qwt, cudaStream_t);
@@ -88,7 +88,7 @@ struct dvm_ctx {
     bool pairs = false;              // 2D FP32: two consecutive bands per CTA
     bool sub3 = false;               // 3D lagged-halo subdomains (pencil and tile tables)
     bool tau3 = false;               // 3D temperature term of Eq. 2
-    bool spec2 = false;              // 2D Maxwell walls with alpha < 1 (Eq. 5)
+    bool spec2 = false;              // Maxwell walls with alpha < 1 (Eq. 5)
     double* qwt_dev = nullptr;       // 3D: [octant][group][4] sums of W |v|^2 (1, v)
     int T1 = 8, rows = 8, max_rows = 8;
     std::vector<HostProb> hp;
@@ -667,8 +667,8 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         if (smem_max <= 0) smem_max = 227 * 1024;
         const size_t lim = (size_t)smem_max - 1024;
         auto smem_of = [&]() -> size_t {
-            if constexpr (std::is_same<T, float>::value) return sweep3d_f32x2_smem(c->T1, c->NW, c->R2, c->R3, c->tau3);
-            else return sweep3d_smem<T>(c->T1, c->NW, c->R2, c->R3, c->tau3);
+            if constexpr (std::is_same<T, float>::value) return sweep3d_f32x2_smem(c->T1, c->NW, c->R2, c->R3, c->tau3, c->spec2);
+            else return sweep3d_smem<T>(c->T1, c->NW, c->R2, c->R3, c->tau3, c->spec2);
         };
         while (smem_of() > lim) {
             if (c->T1 > 4) c->T1 = 4;
@@ -803,6 +803,33 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
             P.srct = (T*)dev_alloc(c, N * sizeof(T));
             if (!P.Pt || !P.srct) return fail(c, DVM_ENOMEM, "device allocation failed");
         }
+        // Maxwell walls with alpha < 1 (Eq. 5): wall faces from the point codes and their store
+        P.spec = c->opt.specular_fraction;
+        if (c->spec2) {
+            std::vector<int> fid((size_t)6 * N, -1), faces;
+            for (size_t id = 0; id < N; ++id) {
+                if (H.code[id] & kSolidBit) continue;
+                for (int ju = 0; ju < 6; ++ju)
+                    if (((H.code[id] >> (2 * ju)) & 3) == 2) {
+                        fid[(size_t)ju * N + id] = (int)faces.size();
+                        faces.push_back((int)(id * 8 + ju));
+                    }
+            }
+            P.nfaces = (int)faces.size();
+            int* fid_dev = (int*)dev_alloc(c, fid.size() * sizeof(int));
+            int* faces_dev = (int*)dev_alloc(c, std::max<size_t>(1, faces.size()) * sizeof(int));
+            P.F = (T*)dev_alloc(c, std::max<size_t>(1, (size_t)2 * P.nfaces * 4 * NL) * sizeof(T));
+            if (!fid_dev || !faces_dev || !P.F) return fail(c, DVM_ENOMEM, "device allocation failed");
+            cudaError_t e2;
+            if ((e2 = cudaMemcpyAsync(fid_dev, fid.data(), fid.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream)) ||
+                (!faces.empty() && (e2 = cudaMemcpyAsync(faces_dev, faces.data(), faces.size() * sizeof(int),
+                                                         cudaMemcpyHostToDevice, c->stream))) ||
+                (e2 = cudaStreamSynchronize(c->stream)))
+                return cuda_fail(c, e2, "upload face tables");
+            c->h2d_bytes += (fid.size() + faces.size()) * sizeof(int);
+            P.face_id = fid_dev;
+            P.faces = faces_dev;
+        }
         P.bf16 = c->bf16 ? 1 : 0;
         const size_t es = c->bf16 ? 2 : sizeof(T);     // bytes per stored ghost / edge value
         P.gx1 = (T*)dev_alloc(c, (size_t)2 * NO * P.ns1 * n3 * n2 * 2 * NL * es);
@@ -920,8 +947,9 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     c->probs_host.assign((const char*)probs.data(), (const char*)probs.data() + probs.size() * sizeof(Prob3D<T>));
     int per_sm = 0;
     if constexpr (std::is_same<T, float>::value)
-        e = sweep3d_f32x2_occupancy(c->T1, c->NW, mr2, mr3, c->bf16 ? 1 : 0, c->sub3 ? 1 : 0, c->tau3 ? 1 : 0, &per_sm);
-    else e = sweep3d_occupancy<T>(c->T1, c->NW, mr2, mr3, 0, c->sub3 ? 1 : 0, c->tau3 ? 1 : 0, &per_sm);
+        e = sweep3d_f32x2_occupancy(c->T1, c->NW, mr2, mr3, c->bf16 ? 1 : 0, c->sub3 ? 1 : 0, c->tau3 ? 1 : 0,
+                                    c->spec2 ? 1 : 0, &per_sm);
+    else e = sweep3d_occupancy<T>(c->T1, c->NW, mr2, mr3, 0, c->sub3 ? 1 : 0, c->tau3 ? 1 : 0, c->spec2 ? 1 : 0, &per_sm);
     if (e != cudaSuccess) return cuda_fail(c, e, "occupancy");
     if (per_sm < 1) return fail(c, DVM_EINVAL, "3D sweep kernel does not fit on an SM with these pencils");
     int dev = 0, sms = 0;
@@ -1022,6 +1050,7 @@ dvm_status enqueue_iter_3d(dvm_ctx* c) {
     a.bf16 = c->bf16 ? 1 : 0;
     a.sub = c->sub3 ? 1 : 0;
     a.tau = c->tau3 ? 1 : 0;
+    a.spec = c->spec2 ? 1 : 0;
     a.parity = (int)(c->iters & 1);
     a.ticket = c->counters_dev;
     a.status = c->status_dev;
@@ -1162,6 +1191,10 @@ void state_segs_3d(const Prob3D<T>& P, size_t NL, int par, std::vector<Seg>& out
     const size_t es = P.bf16 ? 2 : sizeof(T);
     out.push_back({P.P, (size_t)8 * P.ngroups * 4 * P.N * sizeof(T)});
     if (P.tau) out.push_back({P.Pt, (size_t)8 * P.ngroups * P.N * sizeof(T)});
+    if (P.spec > 0.0 && P.nfaces > 0) {
+        const size_t fs = (size_t)P.nfaces * 4 * NL;
+        out.push_back({P.F + par * fs, fs * sizeof(T)});
+    }
     out.push_back({(char*)P.gx1 + par * gx * es, gx * es});
     out.push_back({(char*)P.gy + par * gy * es, gy * es});
     out.push_back({(char*)P.gz + par * gz * es, gz * es});
@@ -1318,11 +1351,11 @@ dvm_status dvm_create_batch(int nprob, const dvm_geometry* geoms, const double* 
     c->tau3 = dims == 3 && c->opt.temperature_term != 0;
     if (!(c->opt.specular_fraction >= 0.0 && c->opt.specular_fraction <= 1.0))
         return reject(DVM_EINVAL, "specular_fraction (1 - alpha of Eq. 5) must lie in [0, 1]");
-    if (c->opt.specular_fraction > 0.0 && dims != 2)
-        return reject(DVM_EINVAL, "walls with alpha < 1 are implemented for 2D problems");
+    if (c->opt.specular_fraction > 0.0 && c->opt.precision == DVM_BF16_STORE)
+        return reject(DVM_EINVAL, "BF16 storage is not implemented with alpha < 1");
     if (c->opt.specular_fraction > 0.0 && c->opt.band_pairs)
         return reject(DVM_EINVAL, "band pairs are not implemented with alpha < 1");
-    c->spec2 = dims == 2 && c->opt.specular_fraction > 0.0;
+    c->spec2 = c->opt.specular_fraction > 0.0;
     if (c->opt.group_warps < 0) return reject(DVM_EINVAL, "group_warps must not be negative");
     if (c->opt.band_pairs && (dims != 2 || c->opt.precision != DVM_FP32 || c->opt.subdomains[0] > 1 ||
                               c->opt.subdomains[1] > 1))

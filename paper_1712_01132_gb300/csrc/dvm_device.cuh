@@ -53,6 +53,12 @@ static __device__ bool wait_geq(const int* flag, int target, int* status, long l
     }
 }
 
+// Sign bits of the two axes other than j of octant q, packed (lower axis first): the slot of a wall
+// face store that the octant moving into a face and its mirror image in axis j share.
+__device__ __forceinline__ int other_bits3(int q, int j) {
+    return j == 0 ? (q >> 1) : (j == 1 ? ((q & 1) | ((q >> 1) & 2)) : (q & 3));
+}
+
 template <typename T> struct Vec4;
 template <> struct Vec4<float> {
     using type = float4;

@@ -129,6 +129,14 @@ struct Prob3D {
     double sw2;             // sum over the grid of W |v|^2 (3/2 for a rule exact on v^2)
     T* Pt;                  // [8][G][N] partials of sum W |v|^2 h' (with tau)
     T* srct;                // [N] nu tau of the last iteration, read by the sweep (with tau)
+    // Maxwell walls with alpha < 1 (Eq. 5), as in Prob2D: spec = 1 - alpha; faces are (fluid
+    // point, axis j, side u) with a solid neighbour at x + (2u - 1) e_j
+    double spec;
+    int nfaces;
+    const int* face_id;     // [6][N] face of (axis j, side u) at a point, index 2 j + u, or -1
+    const int* faces;       // [nfaces] point id * 8 + 2 j + u
+    T* F;                   // [2][nfaces][4][NL] h' of the molecules moving into each face (parity,
+                            // face, sign bits of the two other axes, velocity slot)
     // Lagged-halo subdomains (Sec. 3.2): ns_j = c_j blocks along axis j (1: none).  Slot s of a
     // ghost array holds the two layers upstream of oriented block s from the previous iteration
     // (slot 0: the domain's own ghost layers); the last pencil / tile of block s writes slot
@@ -180,6 +188,7 @@ struct SweepArgs3D {
     int bf16;                   // ghosts and pencil edges stored as BF16 (see Prob3D::bf16)
     int sub;                    // lagged-halo subdomains: pencils and tiles from the Prob3D tables
     int tau;                    // temperature term (Prob3D::tau)
+    int spec;                   // specular wall parts (Prob3D::spec > 0)
     int parity;
     int* ticket;
     int* status;

@@ -61,11 +61,12 @@ template <> struct HStore<float, true> {
 
 }  // namespace
 
-template <typename T, int T1, bool BF, bool SUB, bool TAU>
+template <typename T, int T1, bool BF, bool SUB, bool TAU, bool SPEC>
 __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
     using V = typename V4t<T>::type;
     using HS = HStore<T, BF>;
     constexpr int NM = TAU ? 5 : 4;         // moments per point: rho, u1..u3 (, sum W |v|^2 h)
+    constexpr int RW = SPEC ? 24 : kRec3;   // record words (face ids in two more vectors)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
     __shared__ int s_abort;
@@ -74,8 +75,8 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
     const int lane = threadIdx.x & 31;
     const int MR2 = a.maxR2, MR3 = a.maxR3;
     const int MROWS = MR2 * MR3;
-    T* rec = reinterpret_cast<T*>(smem_raw);                         // [MROWS][T1][kRec3]
-    T* part = rec + (size_t)MROWS * T1 * kRec3;                      // [NW][MROWS][T1][NM]
+    T* rec = reinterpret_cast<T*>(smem_raw);                         // [MROWS][T1][RW]
+    T* part = rec + (size_t)MROWS * T1 * RW;                         // [NW][MROWS][T1][NM]
     T* carry = part + (size_t)NW * MROWS * T1 * NM;                  // [NW][MROWS][2][32]
     T* pb = carry + (size_t)NW * MROWS * 2 * 32;                     // [NW][MR2][2][T1][32]
     T* rtab = pb + (size_t)NW * MR2 * 2 * T1 * 32;                   // [NW][8][32]
@@ -121,6 +122,20 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
         const int par = a.parity;
         const int G = P->ngroups;
         int* prog = P->prog + ((size_t)q * G + g) * np3 * np2;
+        // specular wall parts (Eq. 5, alpha < 1): face stores of the previous iteration (read where
+        // an upstream point is solid) and of this one (written where a downstream point is solid)
+        const T* fprev[3] = {nullptr, nullptr, nullptr};
+        T* fnext[3] = {nullptr, nullptr, nullptr};
+        const size_t fstride = 4 * NL;
+        if constexpr (SPEC) {
+            const size_t plane = (size_t)P->nfaces * 4 * NL;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                fprev[j] = P->F + par * plane + (size_t)other_bits3(q, j) * NL + lv;
+                fnext[j] = P->F + (par ^ 1) * plane + (size_t)other_bits3(q, j) * NL + lv;
+            }
+        }
+        const T specT = (T)P->spec;
         // x1 coordinate of oriented column ic (the shift of the BF16 storage)
         const T dxT = (T)P->dx;
         auto x1of = [&](int ic) -> T { return (T)(s1n ? n1 - 1 - ic : ic) * dxT; };
@@ -147,6 +162,7 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                 const int jj = rem / T1;
                 const int i = rem - jj * T1;
                 V r0 = V4t<T>::make(0, 0, 0, 0), r1 = r0, r2 = r0, r3 = r0;
+                V r4 = V4t<T>::make(ibits(T(0), -1), ibits(T(0), -1), ibits(T(0), -1), ibits(T(0), -1)), r5 = r4;
                 if (jj < nr2 && i < width) {
                     const int ic = c0 + i;
                     const int x = s1n ? n1 - 1 - ic : ic;
@@ -172,13 +188,25 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                                           cb == 2 ? T(0) : (cb == 1 ? T(1) : K1o), cb == 0 ? K2o : T(0));
                         r3 = V4t<T>::make(cc == 2 ? T(0) : (cc == 1 ? T(1) : K1o), cc == 0 ? K2o : T(0),
                                           TAU ? P->srct[id] : T(0), T(0));
+                        if constexpr (SPEC) {   // faces: upstream (read) x1 x2 x3, downstream (written)
+                            const int* fi = P->face_id;
+                            const size_t Nn = (size_t)N;
+                            r4 = V4t<T>::make(ibits(T(0), fi[(0 + s1n) * Nn + id]), ibits(T(0), fi[(2 + s2n) * Nn + id]),
+                                              ibits(T(0), fi[(4 + s3n) * Nn + id]), ibits(T(0), fi[(1 - s1n) * Nn + id]));
+                            r5 = V4t<T>::make(ibits(T(0), fi[(3 - s2n) * Nn + id]), ibits(T(0), fi[(5 - s3n) * Nn + id]),
+                                              ibits(T(0), -1), ibits(T(0), -1));
+                        }
                     }
                 }
-                V* R = reinterpret_cast<V*>(rec + (size_t)((kk * MR2 + jj) * T1 + i) * kRec3);
+                V* R = reinterpret_cast<V*>(rec + (size_t)((kk * MR2 + jj) * T1 + i) * RW);
                 R[0] = r0;
                 R[1] = r1;
                 R[2] = r2;
                 R[3] = r3;
+                if constexpr (SPEC) {
+                    R[4] = r4;
+                    R[5] = r5;
+                }
             }
             __syncthreads();
             if (s_abort) return;
@@ -238,7 +266,7 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                     T* cr = carry + ((size_t)(warp * MROWS + kk * MR2 + jj) * 2) * 32 + lane;
                     T hp1 = cr[0], hp2 = cr[32];
                     T* zr = pb + ((((size_t)warp * MR2 + jj) * 2) * T1) * 32 + lane;   // [2][T1][32]
-                    const T* rrow = rec + (size_t)((kk * MR2 + jj) * T1) * kRec3;
+                    const T* rrow = rec + (size_t)((kk * MR2 + jj) * T1) * RW;
                     T* prow = part + ((size_t)(warp * MROWS + kk * MR2 + jj) * T1) * NM;
 #pragma unroll
                     for (int i0 = 0; i0 < T1; i0 += 4) {
@@ -247,17 +275,32 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                         for (int c = 0; c < 4; ++c) {
                             const int i = i0 + c;
                             if (i < width) {
-                                const V* R = reinterpret_cast<const V*>(rrow + i * kRec3);
+                                const V* R = reinterpret_cast<const V*>(rrow + i * RW);
                                 const V A = R[0], B = R[1], C = R[2], D = R[3];
                                 const T z1 = zr[(size_t)i * 32];
                                 const T z2 = zr[((size_t)T1 + i) * 32];
                                 T S = fma(A.w, v3, fma(A.z, v2, fma(A.y, v1, A.x)));
                                 if constexpr (TAU) S = fma(D.z, vq, S);   // nu tau (|v|^2 - 3/2)
-                                const T t1 = fma(C.x, hp1, fma(C.y, hp2, B.x));
-                                const T t2 = fma(C.z, rb1[i], fma(C.w, rb2[i], B.y));
-                                const T t3 = fma(D.x, z1, fma(D.y, z2, B.z));
+                                T t1 = fma(C.x, hp1, fma(C.y, hp2, B.x));
+                                T t2 = fma(C.z, rb1[i], fma(C.w, rb2[i], B.y));
+                                T t3 = fma(D.x, z1, fma(D.y, z2, B.z));
+                                V Fa, Fb;
+                                if constexpr (SPEC) {   // + (1 - alpha) h'(x, reflected v) at walls
+                                    Fa = R[4];
+                                    Fb = R[5];
+                                    const int fu1 = tbits(Fa.x), fu2 = tbits(Fa.y), fu3 = tbits(Fa.z);
+                                    if (fu1 >= 0) t1 = fma(specT, fprev[0][(size_t)fu1 * fstride], t1);
+                                    if (fu2 >= 0) t2 = fma(specT, fprev[1][(size_t)fu2 * fstride], t2);
+                                    if (fu3 >= 0) t3 = fma(specT, fprev[2][(size_t)fu3 * fstride], t3);
+                                }
                                 const T num = fma(a3, t3, fma(a2, t2, fma(a1, t1, S)));
                                 const T h = num * my_rtab[tbits(B.w) * 32];
+                                if constexpr (SPEC) {   // molecules moving into a downstream face
+                                    const int fd1 = tbits(Fa.w), fd2 = tbits(Fb.x), fd3 = tbits(Fb.y);
+                                    if (fd1 >= 0) fnext[0][(size_t)fd1 * fstride] = h;
+                                    if (fd2 >= 0) fnext[1][(size_t)fd2 * fstride] = h;
+                                    if (fd3 >= 0) fnext[2][(size_t)fd3 * fstride] = h;
+                                }
                                 hp2 = hp1;
                                 hp1 = h;
                                 rb2[i] = rb1[i];
@@ -432,7 +475,8 @@ __global__ void __launch_bounds__(256) finalize3d_kernel(const FinArgs3D<T> a) {
                     const int sigma = u ? 1 : -1;
                     double val = 0.0;
                     if (cs == 2) {
-                        val = wall_density3(P, id, j, sigma) + (j == 0 ? sigma * P->dx : 0.0);
+                        // Eq. 5: alpha times the diffuse value (the specular part is added per velocity)
+                        val = (1.0 - P->spec) * wall_density3(P, id, j, sigma) + (j == 0 ? sigma * P->dx : 0.0);
                     }
                     // case 1 (only the second upstream point solid) is first order on the fluid
                     // neighbour: no wall term
@@ -502,6 +546,11 @@ __global__ void init3d_kernel(const Prob3D<T>* P, int NL, const double* qw /*[8]
         const double x1 = (id % n1) * P->dx;
         P->P[idx] = (P->code[id] & kSolidBit) ? T(0) : (T)(x1 * qw[qgm]);
     }
+    if (P->spec > 0.0)   // face stores of both parities: h' = x1 at the face's fluid point
+        for (size_t idx = t0; idx < (size_t)2 * P->nfaces * 4 * nl; idx += stride) {
+            const int id = P->faces[(idx / (4 * nl)) % P->nfaces] >> 3;
+            P->F[idx] = (T)((id % n1) * P->dx);
+        }
     if (P->tau)   // sum W |v|^2 h' of h' = x1
         for (size_t idx = t0; idx < (size_t)8 * G * N; idx += stride) {
             const int id = idx % N;
@@ -565,6 +614,21 @@ __global__ void warm3d_kernel(const Prob3D<T>* P, int NL, int par, const double*
         }
         P->P[idx] = (T)val;
     }
+    // face stores (specular wall parts, Eq. 5): h0' at the face's fluid point for the velocity slot
+    // of the octant moving into the face (s_j = the face side, the other two axes' bits o)
+    if (P->spec > 0.0)
+        for (size_t idx = t0; idx < (size_t)P->nfaces * 4 * nl; idx += stride) {
+            const int l = idx % nl;
+            const int o = (idx / nl) % 4;
+            const int f = P->faces[idx / (4 * nl)];
+            const int id = f >> 3, j = (f >> 1) & 3, u = f & 1;
+            const int qj = (1 - u) << j;
+            const int qw = j == 0 ? (qj | (o << 1)) : (j == 1 ? (qj | (o & 1) | ((o & 2) << 1)) : (qj | o));
+            double x1;
+            const double hv = h0(qw, (qw & 1) ? n1 - 1 - id % n1 : id % n1, (qw & 2) ? n2 - 1 - (id / n1) % n2 : (id / n1) % n2,
+                                 (qw & 4) ? n3 - 1 - id / (n1 * n2) : id / (n1 * n2), vel + ((size_t)qw * nl + l) * 3, x1);
+            P->F[(size_t)par * P->nfaces * 4 * nl + idx] = (T)hv;
+        }
     // temperature term: sum W |v|^2 h0' through qwt[q][g][n] = sum W |v|^2 psi_n, psi = (1, v)
     if (P->tau)
         for (size_t idx = t0; idx < (size_t)8 * G * N; idx += stride) {
@@ -675,50 +739,62 @@ __global__ void wall3d_kernel(const Prob3D<T>* P, double* out) {
 }
 
 template <typename T>
-size_t sweep3d_smem(int T1, int NW, int R2, int R3, int tau) {
+size_t sweep3d_smem(int T1, int NW, int R2, int R3, int tau, int spec) {
     const size_t rows = (size_t)R2 * R3;
-    return sizeof(T) * (rows * T1 * kRec3 + (size_t)NW * rows * T1 * (tau ? 5 : 4) + (size_t)NW * rows * 2 * 32 +
-                        (size_t)NW * R2 * 2 * T1 * 32 + (size_t)NW * 8 * 32);
+    return sizeof(T) * (rows * T1 * (spec ? 24 : kRec3) + (size_t)NW * rows * T1 * (tau ? 5 : 4) +
+                        (size_t)NW * rows * 2 * 32 + (size_t)NW * R2 * 2 * T1 * 32 + (size_t)NW * 8 * 32);
+}
+
+template <typename T, int T1, bool SUB, bool TAU, bool SPEC>
+static cudaError_t occ3(int NW, int R2, int R3, int* blocks_per_sm) {
+    const size_t smem = sweep3d_smem<T>(T1, NW, R2, R3, TAU, SPEC);
+    auto kern = sweep3d_kernel<T, T1, false, SUB, TAU, SPEC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, NW * 32, smem);
 }
 
 template <typename T, int T1, bool SUB, bool TAU>
-static cudaError_t occ3(int NW, int R2, int R3, int* blocks_per_sm) {
-    const size_t smem = sweep3d_smem<T>(T1, NW, R2, R3, TAU);
-    cudaError_t e = cudaFuncSetAttribute(sweep3d_kernel<T, T1, false, SUB, TAU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep3d_kernel<T, T1, false, SUB, TAU>, NW * 32, smem);
+static cudaError_t occ3_s(int NW, int R2, int R3, int spec, int* bps) {
+    return spec ? occ3<T, T1, SUB, TAU, true>(NW, R2, R3, bps) : occ3<T, T1, SUB, TAU, false>(NW, R2, R3, bps);
 }
 
 template <typename T, int T1>
-static cudaError_t occ3_t(int NW, int R2, int R3, int sub, int tau, int* bps) {
-    if (sub) return tau ? occ3<T, T1, true, true>(NW, R2, R3, bps) : occ3<T, T1, true, false>(NW, R2, R3, bps);
-    return tau ? occ3<T, T1, false, true>(NW, R2, R3, bps) : occ3<T, T1, false, false>(NW, R2, R3, bps);
+static cudaError_t occ3_t(int NW, int R2, int R3, int sub, int tau, int spec, int* bps) {
+    if (sub) return tau ? occ3_s<T, T1, true, true>(NW, R2, R3, spec, bps) : occ3_s<T, T1, true, false>(NW, R2, R3, spec, bps);
+    return tau ? occ3_s<T, T1, false, true>(NW, R2, R3, spec, bps) : occ3_s<T, T1, false, false>(NW, R2, R3, spec, bps);
 }
 
 // The scalar kernel serves the FP64 path (FP32 and its BF16-storage ablation use the packed kernel
 // of sweep3d_f32x2.cu); its BF16 flag stays false.  sub: lagged-halo subdomains (table-driven
-// pencils and tiles); tau: the temperature term.
+// pencils and tiles); tau: the temperature term; spec: specular wall parts.
 template <typename T>
-cudaError_t sweep3d_occupancy(int T1, int NW, int R2, int R3, int bf16, int sub, int tau, int* blocks_per_sm) {
+cudaError_t sweep3d_occupancy(int T1, int NW, int R2, int R3, int bf16, int sub, int tau, int spec, int* blocks_per_sm) {
     if (bf16) return cudaErrorInvalidValue;
-    if (T1 == 4) return occ3_t<T, 4>(NW, R2, R3, sub, tau, blocks_per_sm);
-    if (T1 == 8) return occ3_t<T, 8>(NW, R2, R3, sub, tau, blocks_per_sm);
+    if (T1 == 4) return occ3_t<T, 4>(NW, R2, R3, sub, tau, spec, blocks_per_sm);
+    if (T1 == 8) return occ3_t<T, 8>(NW, R2, R3, sub, tau, spec, blocks_per_sm);
     return cudaErrorInvalidValue;
 }
 
-template <typename T, int T1, bool SUB, bool TAU>
+template <typename T, int T1, bool SUB, bool TAU, bool SPEC>
 static cudaError_t launch3(const SweepArgs3D<T>& a, int grid, int NW, cudaStream_t st) {
-    const size_t smem = sweep3d_smem<T>(T1, NW, a.maxR2, a.maxR3, TAU);
-    cudaError_t e = cudaFuncSetAttribute(sweep3d_kernel<T, T1, false, SUB, TAU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = sweep3d_smem<T>(T1, NW, a.maxR2, a.maxR3, TAU, SPEC);
+    auto kern = sweep3d_kernel<T, T1, false, SUB, TAU, SPEC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    sweep3d_kernel<T, T1, false, SUB, TAU><<<grid, NW * 32, smem, st>>>(a);
+    kern<<<grid, NW * 32, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+template <typename T, int T1, bool SUB, bool TAU>
+static cudaError_t launch3_s(const SweepArgs3D<T>& a, int grid, int NW, cudaStream_t st) {
+    return a.spec ? launch3<T, T1, SUB, TAU, true>(a, grid, NW, st) : launch3<T, T1, SUB, TAU, false>(a, grid, NW, st);
 }
 
 template <typename T, int T1>
 static cudaError_t launch3_t(const SweepArgs3D<T>& a, int grid, int NW, cudaStream_t st) {
-    if (a.sub) return a.tau ? launch3<T, T1, true, true>(a, grid, NW, st) : launch3<T, T1, true, false>(a, grid, NW, st);
-    return a.tau ? launch3<T, T1, false, true>(a, grid, NW, st) : launch3<T, T1, false, false>(a, grid, NW, st);
+    if (a.sub) return a.tau ? launch3_s<T, T1, true, true>(a, grid, NW, st) : launch3_s<T, T1, true, false>(a, grid, NW, st);
+    return a.tau ? launch3_s<T, T1, false, true>(a, grid, NW, st) : launch3_s<T, T1, false, false>(a, grid, NW, st);
 }
 
 template <typename T>
@@ -766,8 +842,8 @@ cudaError_t launch_wall3d(const Prob3D<T>* p, double* out, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template size_t sweep3d_smem<double>(int, int, int, int, int);
-template cudaError_t sweep3d_occupancy<double>(int, int, int, int, int, int, int, int*);
+template size_t sweep3d_smem<double>(int, int, int, int, int, int);
+template cudaError_t sweep3d_occupancy<double>(int, int, int, int, int, int, int, int, int*);
 template cudaError_t launch_sweep3d<double>(const SweepArgs3D<double>&, int, int, cudaStream_t);
 
 #define DVM_INSTANTIATE3(T)                                                                                  \

@@ -68,10 +68,11 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 
 }  // namespace
 
-template <int T1, bool BF, bool SUB, bool TAU>
+template <int T1, bool BF, bool SUB, bool TAU, bool SPEC>
 __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<float> a) {
     using PS = PairStore<BF>;
     constexpr int NM = TAU ? 5 : 4;         // moments per point: rho, u1..u3 (, sum W |v|^2 h)
+    constexpr int RF = SPEC ? 24 : kRec;    // record floats (face ids in two more vectors)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
     __shared__ int s_abort;
@@ -80,8 +81,8 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
     const int lane = threadIdx.x & 31;
     const int MR2 = a.maxR2, MR3 = a.maxR3;
     const int MROWS = MR2 * MR3;
-    float* rec = reinterpret_cast<float*>(smem_raw);                      // [MROWS][T1][kRec]
-    float* part = rec + (size_t)MROWS * T1 * kRec;                        // [NW][MROWS][T1][NM]
+    float* rec = reinterpret_cast<float*>(smem_raw);                      // [MROWS][T1][RF]
+    float* part = rec + (size_t)MROWS * T1 * RF;                          // [NW][MROWS][T1][NM]
     float* carry = part + (size_t)NW * MROWS * T1 * NM;                   // [NW][MROWS][2][64]
     float* pb = carry + (size_t)NW * MROWS * 2 * kPL;                     // [NW][MR2][2][T1][64]
     float* eb = pb + (size_t)NW * MR2 * 2 * T1 * kPL;                     // [NW][2][2][T1][64]
@@ -135,6 +136,21 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
         const int par = a.parity;
         const int G = P->ngroups;
         int* prog = P->prog + ((size_t)q * G + g) * np3 * np2;
+        // specular wall parts (Eq. 5, alpha < 1): face stores of the previous iteration (read where
+        // an upstream point is solid) and of this one (written where a downstream point is solid),
+        // at this lane's two slots
+        const float* fprev[3] = {nullptr, nullptr, nullptr};
+        float* fnext[3] = {nullptr, nullptr, nullptr};
+        const size_t fstride = 4 * NL;
+        if constexpr (SPEC) {
+            const size_t plane = (size_t)P->nfaces * 4 * NL;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                fprev[j] = P->F + par * plane + (size_t)other_bits3(q, j) * NL + lv;
+                fnext[j] = P->F + (par ^ 1) * plane + (size_t)other_bits3(q, j) * NL + lv;
+            }
+        }
+        const float2 specP = dup2((float)P->spec);
         const float dxf = (float)P->dx;
         auto x1of = [&](int ic) -> float { return (float)(s1n ? n1 - 1 - ic : ic) * dxf; };
         const float x1g0 = x1of(n1 - 1), x1g1 = x1of(n1 - 2);   // columns of the x1 ghost layers
@@ -169,6 +185,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                 const int jj = rem / T1;
                 const int i = rem - jj * T1;
                 float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
+                int4 r4 = make_int4(-1, -1, -1, -1), r5 = r4;
                 if (jj < nr2 && i < width) {
                     const int ic = c0 + i;
                     const int x = s1n ? n1 - 1 - ic : ic;
@@ -192,14 +209,25 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                                          cb == 2 ? 0.f : (cb == 1 ? 1.f : K1o), cb == 0 ? K2o : 0.f);
                         r3 = make_float4(cc == 2 ? 0.f : (cc == 1 ? 1.f : K1o), cc == 0 ? K2o : 0.f,
                                          TAU ? P->srct[id] : 0.f, 0.f);
+                        if constexpr (SPEC) {   // faces: upstream (read) x1 x2 x3, downstream (written)
+                            const int* fi = P->face_id;
+                            const size_t Nn = (size_t)N;
+                            r4 = make_int4(fi[(0 + s1n) * Nn + id], fi[(2 + s2n) * Nn + id], fi[(4 + s3n) * Nn + id],
+                                           fi[(1 - s1n) * Nn + id]);
+                            r5 = make_int4(fi[(3 - s2n) * Nn + id], fi[(5 - s3n) * Nn + id], -1, -1);
+                        }
                         atomicOr(fm_cur + kk * MR2 + jj, 1u << i);
                     }
                 }
-                float4* R = reinterpret_cast<float4*>(rec + (size_t)((kk * MR2 + jj) * T1 + i) * kRec);
+                float4* R = reinterpret_cast<float4*>(rec + (size_t)((kk * MR2 + jj) * T1 + i) * RF);
                 R[0] = r0;
                 R[1] = r1;
                 R[2] = r2;
                 R[3] = r3;
+                if constexpr (SPEC) {
+                    reinterpret_cast<int4*>(R)[4] = r4;
+                    reinterpret_cast<int4*>(R)[5] = r5;
+                }
             }
             __syncthreads();
             if (s_abort) {
@@ -241,7 +269,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                 ? ((((size_t)par * 8 + q) * P->ns2 + pi2.z) * n3 * n1) * 2 * NL
                 : ((((size_t)q * np3 + p3) * 2 * P->ns2 + (-1 - pi2.z)) * P->R3 * n1) * 2 * NL;
             auto yrow = [&](int kk) -> size_t { return yg ? (size_t)(k0 + kk) * n1 : (size_t)kk * n1; };
-            auto rbuf_rec = [&](int kk, int jj, int i) -> const float* { return rec + (size_t)((kk * MR2 + jj) * T1 + i) * kRec; };
+            auto rbuf_rec = [&](int kk, int jj, int i) -> const float* { return rec + (size_t)((kk * MR2 + jj) * T1 + i) * RF; };
             // FP32: the x2 rows of plane kk go to slot kk & 1, copied while plane kk - 1 is swept
             // Upstream values are fetched only where the stencil of the point that reads them has a
             // nonzero coefficient for them (record K1 / K2 of the first row or plane): values of
@@ -328,7 +356,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                     float2 hp1 = *reinterpret_cast<const float2*>(cr);
                     float2 hp2 = *reinterpret_cast<const float2*>(cr + kPL);
                     float* zr = pb + ((((size_t)warp * MR2 + jj) * 2) * T1) * kPL + 2 * lane;   // [2][T1][64]
-                    const float* rrow = rec + (size_t)((kk * MR2 + jj) * T1) * kRec;
+                    const float* rrow = rec + (size_t)((kk * MR2 + jj) * T1) * RF;
                     float* prow = part + ((size_t)(warp * MROWS + kk * MR2 + jj) * T1) * NM;
 #pragma unroll
                     for (int i0 = 0; i0 < T1; i0 += 4) {
@@ -338,20 +366,33 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                         for (int c = 0; c < 4; ++c) {
                             const int i = i0 + c;
                             if ((fm >> i) & 1u) {
-                                const float4* R = reinterpret_cast<const float4*>(rrow + i * kRec);
+                                const float4* R = reinterpret_cast<const float4*>(rrow + i * RF);
                                 const float4 A = R[0], B = R[1], C = R[2], D = R[3];
                                 const float2 z1 = *reinterpret_cast<const float2*>(zr + (size_t)i * kPL);
                                 const float2 z2 = *reinterpret_cast<const float2*>(zr + ((size_t)T1 + i) * kPL);
                                 const float2 Rk = *reinterpret_cast<const float2*>(my_rtab + __float_as_int(B.w));
                                 float2 S = fma2(dup2(A.w), v3, fma2(dup2(A.z), v2, fma2(dup2(A.y), v1, dup2(A.x))));
                                 if constexpr (TAU) S = fma2(dup2(D.z), vq, S);   // nu tau (|v|^2 - 3/2)
-                                const float2 t1 = fma2(dup2(C.x), hp1, fma2(dup2(C.y), hp2, dup2(B.x)));
-                                const float2 t2 = fma2(dup2(C.z), rb1[i], fma2(dup2(C.w), rb2[i], dup2(B.y)));
-                                const float2 t3 = fma2(dup2(D.x), z1, fma2(dup2(D.y), z2, dup2(B.z)));
+                                float2 t1 = fma2(dup2(C.x), hp1, fma2(dup2(C.y), hp2, dup2(B.x)));
+                                float2 t2 = fma2(dup2(C.z), rb1[i], fma2(dup2(C.w), rb2[i], dup2(B.y)));
+                                float2 t3 = fma2(dup2(D.x), z1, fma2(dup2(D.y), z2, dup2(B.z)));
+                                int4 Fa, Fb;
+                                if constexpr (SPEC) {   // + (1 - alpha) h'(x, reflected v) at walls
+                                    Fa = reinterpret_cast<const int4*>(R)[4];
+                                    Fb = reinterpret_cast<const int4*>(R)[5];
+                                    if (Fa.x >= 0) t1 = fma2(specP, *reinterpret_cast<const float2*>(fprev[0] + (size_t)Fa.x * fstride), t1);
+                                    if (Fa.y >= 0) t2 = fma2(specP, *reinterpret_cast<const float2*>(fprev[1] + (size_t)Fa.y * fstride), t2);
+                                    if (Fa.z >= 0) t3 = fma2(specP, *reinterpret_cast<const float2*>(fprev[2] + (size_t)Fa.z * fstride), t3);
+                                }
                                 // the x1 term (carried from the previous point) enters last: three
                                 // dependent operations per point along the x1 chain
                                 const float2 num = fma2(a1, t1, fma2(a3, t3, fma2(a2, t2, S)));
                                 const float2 h = mul2(num, Rk);
+                                if constexpr (SPEC) {   // molecules moving into a downstream face
+                                    if (Fa.w >= 0) *reinterpret_cast<float2*>(fnext[0] + (size_t)Fa.w * fstride) = h;
+                                    if (Fb.x >= 0) *reinterpret_cast<float2*>(fnext[1] + (size_t)Fb.x * fstride) = h;
+                                    if (Fb.y >= 0) *reinterpret_cast<float2*>(fnext[2] + (size_t)Fb.y * fstride) = h;
+                                }
                                 hp2 = hp1;
                                 hp1 = h;
                                 rb2[i] = rb1[i];
@@ -487,59 +528,73 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
     }
 }
 
-size_t sweep3d_f32x2_smem(int T1, int NW, int R2, int R3, int tau) {
+size_t sweep3d_f32x2_smem(int T1, int NW, int R2, int R3, int tau, int spec) {
     const size_t rows = (size_t)R2 * R3;
-    return sizeof(float) * (rows * T1 * kRec + (size_t)NW * rows * T1 * (tau ? 5 : 4) + (size_t)NW * rows * 2 * kPL +
-                            (size_t)NW * R2 * 2 * T1 * kPL + (size_t)NW * 2 * 2 * T1 * kPL + (size_t)NW * 8 * kPL) +
+    return sizeof(float) * (rows * T1 * (spec ? 24 : kRec) + (size_t)NW * rows * T1 * (tau ? 5 : 4) +
+                            (size_t)NW * rows * 2 * kPL + (size_t)NW * R2 * 2 * T1 * kPL + (size_t)NW * 2 * 2 * T1 * kPL +
+                            (size_t)NW * 8 * kPL) +
            sizeof(unsigned) * 2 * rows;
 }
 
 int sweep3d_f32x2_velocities_per_lane() { return 2; }
 
-template <int T1, bool BF, bool SUB, bool TAU>
+template <int T1, bool BF, bool SUB, bool TAU, bool SPEC>
 static cudaError_t launch_t(const SweepArgs3D<float>& a, int grid, int NW, cudaStream_t st) {
-    const size_t smem = sweep3d_f32x2_smem(T1, NW, a.maxR2, a.maxR3, TAU);
-    cudaError_t e = cudaFuncSetAttribute(sweep3d_f32x2_kernel<T1, BF, SUB, TAU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = sweep3d_f32x2_smem(T1, NW, a.maxR2, a.maxR3, TAU, SPEC);
+    auto kern = sweep3d_f32x2_kernel<T1, BF, SUB, TAU, SPEC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    sweep3d_f32x2_kernel<T1, BF, SUB, TAU><<<grid, NW * 32, smem, st>>>(a);
+    kern<<<grid, NW * 32, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+template <int T1, bool SUB, bool TAU>
+static cudaError_t launch_ts(const SweepArgs3D<float>& a, int grid, int NW, cudaStream_t st) {
+    return a.spec ? launch_t<T1, false, SUB, TAU, true>(a, grid, NW, st) : launch_t<T1, false, SUB, TAU, false>(a, grid, NW, st);
 }
 
 template <int T1>
 static cudaError_t launch_tt(const SweepArgs3D<float>& a, int grid, int NW, cudaStream_t st) {
-    if (a.bf16) return launch_t<T1, true, false, false>(a, grid, NW, st);
-    if (a.sub) return a.tau ? launch_t<T1, false, true, true>(a, grid, NW, st) : launch_t<T1, false, true, false>(a, grid, NW, st);
-    return a.tau ? launch_t<T1, false, false, true>(a, grid, NW, st) : launch_t<T1, false, false, false>(a, grid, NW, st);
+    if (a.bf16) return launch_t<T1, true, false, false, false>(a, grid, NW, st);
+    if (a.sub) return a.tau ? launch_ts<T1, true, true>(a, grid, NW, st) : launch_ts<T1, true, false>(a, grid, NW, st);
+    return a.tau ? launch_ts<T1, false, true>(a, grid, NW, st) : launch_ts<T1, false, false>(a, grid, NW, st);
 }
 
-// instantiations: FP32 with or without subdomains and the temperature term; BF16 storage without
-// either
+// instantiations: FP32 with any combination of subdomains, the temperature term and specular wall
+// parts; BF16 storage with none of them
 cudaError_t launch_sweep3d_f32x2(const SweepArgs3D<float>& a, int grid, int NW, cudaStream_t st) {
-    if (a.bf16 && (a.sub || a.tau)) return cudaErrorInvalidValue;
+    if (a.bf16 && (a.sub || a.tau || a.spec)) return cudaErrorInvalidValue;
     if (a.T1 == 4) return launch_tt<4>(a, grid, NW, st);
     if (a.T1 == 8) return launch_tt<8>(a, grid, NW, st);
     return cudaErrorInvalidValue;
 }
 
-template <int T1, bool BF, bool SUB, bool TAU>
+template <int T1, bool BF, bool SUB, bool TAU, bool SPEC>
 static cudaError_t occ_t(int NW, int R2, int R3, int* blocks_per_sm) {
-    const size_t smem = sweep3d_f32x2_smem(T1, NW, R2, R3, TAU);
-    cudaError_t e = cudaFuncSetAttribute(sweep3d_f32x2_kernel<T1, BF, SUB, TAU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = sweep3d_f32x2_smem(T1, NW, R2, R3, TAU, SPEC);
+    auto kern = sweep3d_f32x2_kernel<T1, BF, SUB, TAU, SPEC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep3d_f32x2_kernel<T1, BF, SUB, TAU>, NW * 32, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, NW * 32, smem);
+}
+
+template <int T1, bool SUB, bool TAU>
+static cudaError_t occ_ts(int NW, int R2, int R3, int spec, int* bps) {
+    return spec ? occ_t<T1, false, SUB, TAU, true>(NW, R2, R3, bps) : occ_t<T1, false, SUB, TAU, false>(NW, R2, R3, bps);
 }
 
 template <int T1>
-static cudaError_t occ_tt(int NW, int R2, int R3, int bf16, int sub, int tau, int* bps) {
-    if (bf16) return occ_t<T1, true, false, false>(NW, R2, R3, bps);
-    if (sub) return tau ? occ_t<T1, false, true, true>(NW, R2, R3, bps) : occ_t<T1, false, true, false>(NW, R2, R3, bps);
-    return tau ? occ_t<T1, false, false, true>(NW, R2, R3, bps) : occ_t<T1, false, false, false>(NW, R2, R3, bps);
+static cudaError_t occ_tt(int NW, int R2, int R3, int bf16, int sub, int tau, int spec, int* bps) {
+    if (bf16) return occ_t<T1, true, false, false, false>(NW, R2, R3, bps);
+    if (sub) return tau ? occ_ts<T1, true, true>(NW, R2, R3, spec, bps) : occ_ts<T1, true, false>(NW, R2, R3, spec, bps);
+    return tau ? occ_ts<T1, false, true>(NW, R2, R3, spec, bps) : occ_ts<T1, false, false>(NW, R2, R3, spec, bps);
 }
 
-cudaError_t sweep3d_f32x2_occupancy(int T1, int NW, int R2, int R3, int bf16, int sub, int tau, int* blocks_per_sm) {
-    if (bf16 && (sub || tau)) return cudaErrorInvalidValue;
-    if (T1 == 4) return occ_tt<4>(NW, R2, R3, bf16, sub, tau, blocks_per_sm);
-    if (T1 == 8) return occ_tt<8>(NW, R2, R3, bf16, sub, tau, blocks_per_sm);
+cudaError_t sweep3d_f32x2_occupancy(int T1, int NW, int R2, int R3, int bf16, int sub, int tau, int spec,
+                                    int* blocks_per_sm) {
+    if (bf16 && (sub || tau || spec)) return cudaErrorInvalidValue;
+    if (T1 == 4) return occ_tt<4>(NW, R2, R3, bf16, sub, tau, spec, blocks_per_sm);
+    if (T1 == 8) return occ_tt<8>(NW, R2, R3, bf16, sub, tau, spec, blocks_per_sm);
     return cudaErrorInvalidValue;
 }
 

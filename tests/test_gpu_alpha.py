@@ -139,4 +139,95 @@ def test_alpha_options_are_validated():
     rock = inputs.gaussian_rock(8, seed=1, corr_len=1.5, porosity=0.6)
     v3, w3 = dvm.dvm_gh_velocity_grid(3, 4)
     with pytest.raises(dvm.DvmError):
-        dvm.Solver(rock, 0.2, v3, w3, specular_fraction=0.5)
+        dvm.Solver(rock, 0.2, v3, w3, precision="bf16_store", specular_fraction=0.5)
+
+
+# ----------------------------------------------------------------------------------------- 3D
+
+def _rock(n3, n2, n1, seed, frac=0.25):
+    rng = np.random.default_rng(seed)
+    solid = rng.random((n3, n2, n1)) < frac
+    solid[:, :, 0] = False
+    return solid
+
+
+def _grid3(n):
+    return dvm.dvm_gh_velocity_grid(3, n), oracle.velocity_grid(3, n)
+
+
+@pytest.mark.parametrize("lateral", ["periodic", "specular"])
+@pytest.mark.parametrize("t1,rows", [(4, 2), (8, 4)])
+def test_alpha_3d_fp64_matches_oracle(lateral, t1, rows):
+    mask = _rock(9, 10, 11, seed=3)
+    (v, w), (vo, wo) = _grid3(8)
+    s = dvm.Solver(mask, 0.4, v, w, precision="fp64", lateral=lateral, tile_x1=t1, band_rows=rows,
+                   specular_fraction=0.4)
+    o = oracle.Oracle(mask, 0.4, vo, wo, lateral=lateral, alpha=0.6)
+    for n in (1, 3):
+        s.step(n)
+        s.sync()
+        o.iterate(n)
+        _compare(s, o)
+
+
+def test_alpha_3d_with_subdomains_tau_and_groups_fp64():
+    """alpha < 1 together with lagged-halo subdomains, the temperature term and two velocity groups
+    per octant."""
+    mask = _rock(7, 8, 9, seed=5, frac=0.2)
+    (v, w), (vo, wo) = _grid3(16)
+    s = dvm.Solver(mask, 0.8, v, w, precision="fp64", lateral="periodic", band_rows=3, subdomains=(2, 1, 2),
+                   temperature_term=True, specular_fraction=0.3)
+    o = oracle.Oracle(mask, 0.8, vo, wo, lateral="periodic", decomposition=(2, 1, 2), tau=True, alpha=0.7)
+    s.step(3)
+    s.sync()
+    o.iterate(3)
+    _compare(s, o)
+    assert np.abs(s.temperature() - o.temperature()).max() < FP64_TOL * max(1.0, np.abs(o.temperature()).max())
+
+
+def test_alpha_3d_warm_start_and_checkpoint_fp64():
+    mask = _rock(8, 9, 10, seed=7)
+    (v, w), (vo, wo) = _grid3(8)
+    rng = np.random.default_rng(4)
+    r0 = 0.2 * rng.standard_normal(mask.shape)
+    u0 = 0.05 * rng.standard_normal((3,) + mask.shape)
+    s = dvm.Solver(mask, 0.3, v, w, precision="fp64", lateral="specular", band_rows=2, specular_fraction=0.5)
+    o = oracle.Oracle(mask, 0.3, vo, wo, lateral="specular", alpha=0.5)
+    s.step(1)
+    s.set_initial(r0, u0)
+    o.set_initial(r0, u0)
+    _compare(s, o)
+    s.step(2)
+    s.sync()
+    o.iterate(2)
+    _compare(s, o)
+    blob = s.get_state()
+    s.step(2)
+    s.sync()
+    ref = s.moments()
+    t = dvm.Solver(mask, 0.3, v, w, precision="fp64", lateral="specular", band_rows=2, specular_fraction=0.5)
+    t.set_state(blob)
+    t.step(2)
+    t.sync()
+    assert np.array_equal(ref[1], t.moments()[1])
+
+
+def test_alpha_3d_fp32_matches_oracle_and_keeps_bits_across_shapes():
+    mask = _rock(10, 12, 13, seed=11, frac=0.3)
+    (v, w), (vo, wo) = _grid3(8)
+    o = oracle.Oracle(mask, 0.2, vo, wo, lateral="periodic", alpha=0.6)
+    o.iterate(3)
+    ref = None
+    for t1, rows, gw in ((4, 3, 0), (8, 2, 0), (4, 5, 4)):
+        s = dvm.Solver(mask, 0.2, v, w, precision="fp32", lateral="periodic", tile_x1=t1, band_rows=rows,
+                       group_warps=gw, specular_fraction=0.4)
+        s.step(3)
+        s.sync()
+        rho, u = s.moments()
+        rho_o, u_o = o.moments()
+        assert _rel(u, u_o) < 1e-4
+        assert np.abs(rho - rho_o).max() < 1e-5 * max(1.0, np.abs(rho_o).max())
+        if ref is None:
+            ref = (rho, u)
+        else:
+            assert np.array_equal(ref[1], u)
