@@ -425,6 +425,7 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         P.dx = H.dx;
         P.dinv[0] = dinv[0];
         P.dinv[1] = dinv[1];
+        for (int j = 0; j < 2; ++j) P.dinvw[j] = (1.0 - c->opt.specular_fraction) * dinv[j];
         const size_t N = H.N;
         uint16_t* code = (uint16_t*)dev_alloc(c, N * sizeof(uint16_t));
         P.src = (T*)dev_alloc(c, N * 4 * sizeof(T));
@@ -790,6 +791,7 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         P.nu = H.nu;
         P.dx = H.dx;
         for (int j = 0; j < 3; ++j) P.dinv[j] = dinv[j];
+        for (int j = 0; j < 3; ++j) P.dinvw[j] = (1.0 - c->opt.specular_fraction) * dinv[j];
         const size_t N = H.N;
         const size_t n1 = P.n1, n2 = P.n2, n3 = P.n3;
         uint16_t* code = (uint16_t*)dev_alloc(c, N * sizeof(uint16_t));

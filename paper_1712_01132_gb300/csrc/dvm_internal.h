@@ -53,6 +53,7 @@ struct Prob2D {
     int order;           // 2 or 1
     double kn, nu, dx;
     double dinv[2];      // reciprocals of the Eq. 6 denominators per axis
+    double dinvw[2];     // alpha dinv: the diffuse part of a wall value (Eq. 5; = dinv for alpha = 1)
     const uint16_t* code;   // [N] stencil cases, see kernels
     T* src;              // [N][4]  (nu rho', 2 nu u1 + 1, 2 nu u2, 0)
     T* E;                // [N][4]  wall terms per (axis j, upstream side u): index 2 j + u
@@ -120,6 +121,7 @@ struct Prob3D {
                             //    (h' - x1 of the point the value belongs to), 2 bytes each
     double kn, nu, dx;
     double dinv[3];
+    double dinvw[3];        // alpha dinv (Eq. 5; = dinv for alpha = 1)
     const uint16_t* code;   // [N]
     T* src;                 // [N][4]  (nu rho', 2 nu u1 + 1, 2 nu u2, 2 nu u3)
     T* E;                   // [N][8]  wall terms, index 2 j + u (6 used)

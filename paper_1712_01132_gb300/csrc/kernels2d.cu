@@ -332,14 +332,14 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs2D<T> a) {
 // rho'_s of face (y, axis j, side sigma) (Eq. 6) in FP64 from the quadrant partials of u_j at y:
 // sum_{sigma v_j > 0} W |v_j| h / D = sigma * sum_{quadrants with sign(v_j) = sigma} P_uj / D.
 template <typename T>
-__device__ __forceinline__ double wall_density(const Prob2D<T>* P, int y, int j, int sigma) {
+__device__ __forceinline__ double wall_density(const Prob2D<T>* P, int y, int j, int sigma, const double* dinv) {
     double num = 0.0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int neg = (q >> j) & 1;
         if (neg == (sigma < 0 ? 1 : 0)) num += (double)P->P[((size_t)q * 3 + 1 + j) * P->N + y];
     }
-    return sigma * num * P->dinv[j];
+    return sigma * num * dinv[j];
 }
 
 template <typename T>
@@ -377,9 +377,9 @@ __global__ void __launch_bounds__(256) finalize2d_kernel(const FinArgs2D<T> a) {
                     if (c == 2) {
                         // first-order stencil: wall value of face (x, j, sigma), shifted by the
                         // source-form offset sigma dx on x1 faces
-                        // (Eq. 5: alpha times the diffuse value; the specular part is added per
-                        // velocity by the sweep)
-                        val = (1.0 - P->spec) * wall_density(P, id, j, sigma) + (j == 0 ? sigma * P->dx : 0.0);
+                        // (Eq. 5: alpha times the diffuse value, through the alpha-scaled
+                        // denominators; the specular part is added per velocity by the sweep)
+                        val = wall_density(P, id, j, sigma, P->dinvw) + (j == 0 ? sigma * P->dx : 0.0);
                     }
                     // case 1 (only the second upstream point solid) is first order on the fluid
                     // neighbour: no wall term
@@ -576,7 +576,7 @@ __global__ void wall2d_kernel(const Prob2D<T>* prob, double* out) {
             for (int u = 0; u < 2; ++u) {
                 double v = 0.0;
                 if (!(code & kSolidBit) && ((code >> (2 * (2 * j + u))) & 3) == 2)
-                    v = wall_density(P, id, j, u ? 1 : -1) - (id % P->n1) * P->dx;
+                    v = wall_density(P, id, j, u ? 1 : -1, P->dinv) - (id % P->n1) * P->dx;
                 out[(size_t)(2 * j + u) * N + id] = v;
             }
     }

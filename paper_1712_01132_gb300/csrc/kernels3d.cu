@@ -423,14 +423,14 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
 
 // rho'_s of face (y, axis j, side sigma) in FP64 from the octant/group partials of u_j at y
 template <typename T>
-__device__ __forceinline__ double wall_density3(const Prob3D<T>* P, int y, int j, int sigma) {
+__device__ __forceinline__ double wall_density3(const Prob3D<T>* P, int y, int j, int sigma, const double* dinv) {
     double num = 0.0;
     const int G = P->ngroups;
     for (int q = 0; q < 8; ++q) {
         if (((q >> j) & 1) != (sigma < 0 ? 1 : 0)) continue;
         for (int g = 0; g < G; ++g) num += (double)P->P[(((size_t)q * G + g) * 4 + 1 + j) * P->N + y];
     }
-    return sigma * num * P->dinv[j];
+    return sigma * num * dinv[j];
 }
 
 template <typename T>
@@ -476,7 +476,8 @@ __global__ void __launch_bounds__(256) finalize3d_kernel(const FinArgs3D<T> a) {
                     double val = 0.0;
                     if (cs == 2) {
                         // Eq. 5: alpha times the diffuse value (the specular part is added per velocity)
-                        val = (1.0 - P->spec) * wall_density3(P, id, j, sigma) + (j == 0 ? sigma * P->dx : 0.0);
+                        // (Eq. 5: alpha times the diffuse value, through the alpha-scaled denominators)
+                        val = wall_density3(P, id, j, sigma, P->dinvw) + (j == 0 ? sigma * P->dx : 0.0);
                     }
                     // case 1 (only the second upstream point solid) is first order on the fluid
                     // neighbour: no wall term
@@ -732,7 +733,7 @@ __global__ void wall3d_kernel(const Prob3D<T>* P, double* out) {
             for (int u = 0; u < 2; ++u) {
                 double v = 0.0;
                 if (!(code & kSolidBit) && ((code >> (2 * (2 * j + u))) & 3) == 2)
-                    v = wall_density3(P, id, j, u ? 1 : -1) - (id % P->n1) * P->dx;
+                    v = wall_density3(P, id, j, u ? 1 : -1, P->dinv) - (id % P->n1) * P->dx;
                 out[(size_t)(2 * j + u) * N + id] = v;
             }
     }
