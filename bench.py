@@ -3,7 +3,7 @@
 One step = one check interval of the source iteration (Sec. 3.1): 100 iterations of sweep +
 quadrature + wall/source update, then the permeability and the Err check of Eq. 15.
 Metric: cell-velocity updates per second = (fluid cells) x (velocities) x (iterations) / time,
-summed over the problems of the batch.
+summed over the problems of the batch; config.full_grid_updates_per_s counts every grid cell.
 
 Workloads (--workload):
   kn_sweep_512  (default) 2D random porous medium, 512 x 512 overlapping discs (seed 0, radii uniform
@@ -19,7 +19,7 @@ Tile shapes are chosen by the library's autotuner before the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
 
---impl reference times the FP64 CPU oracle (the reference arm of this build) on the host cores.
+--impl reference times the FP64 CPU oracle on the host cores (the reference arm).
 """
 import argparse
 import json
@@ -121,10 +121,11 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, directory=None):
+        import tempfile
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % gpu_index)
+        self.path = os.path.join(directory or tempfile.gettempdir(), "clocks_bench_%d.csv" % gpu_index)
 
     def start(self):
         try:
@@ -233,7 +234,7 @@ def run_gpu(args):
         s.iterate(ITERS_PER_STEP, 0.0)
     s.profile_enable(True)                      # per-launch events (launches issued one by one)
     s.profile_read()
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(local, args.clocks_dir)
     sampler.start()
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -297,6 +298,8 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload if args.side == 128 else "%s_side%d" % (args.workload, args.side),
                        "description": W["desc"], "fluid_cells": sum(nfs),
+                       "grid_cells": int(sum(m.size for m in masks)),
+                       "full_grid_updates_per_s": value * sum(m.size for m in masks) / max(sum(nfs), 1),
                        "velocities": nv, "problems": len(masks), "iterations_per_step": ITERS_PER_STEP,
                        "step": "100 source iterations (sweep+quadrature+finalize) + permeability/Err check",
                        "tiles": {"tile_x1": t1, "band_rows": rows, "group_warps": tune.group_warps,
@@ -389,6 +392,8 @@ def main():
     ap.add_argument("--workload", default="kn_sweep_512", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-dir", default=None,
+                    help="directory for the raw nvidia-smi clock samples (default: the temp directory)")
     ap.add_argument("--side", type=int, default=128,
                     help="edge length of the rock_128 geometry (smaller only for profiling captures)")
     args = ap.parse_args()
