@@ -3,9 +3,9 @@
 //
 // Schedule: persistent CTAs take (problem, quadrant, band) items from a ticket counter in band
 // order.  A CTA sweeps its band along x1 in tiles of 8 columns; band b starts tile t once band b-1
-// has published it.  Inside a tile a warp walks its rows in order; every lane carries four
-// velocities as two packed pairs (two independent dependency chains per lane) updated with
-// fma.rn.f32x2.  Per-point arithmetic (Eq. 10 solved for h at the point, upwind stencil of Eq. 9):
+// has published it.  Inside a tile a warp walks its rows two at a time, the upper row one column
+// behind the lower; every lane carries four velocities as two packed pairs updated with
+// fma.rn.f32x2, so each step has four independent dependency chains per lane.  Per-point arithmetic (Eq. 10 solved for h at the point, upwind stencil of Eq. 9):
 //   h = R * [ nu rho' + 2 nu u.v + v1 + a1 (K1x h(x-s1 e1) + K2x h(x-2 s1 e1) + E1)
 //                                     + a2 (K1y h(x-s2 e2) + K2y h(x-2 s2 e2) + E2) ]
 // with a_j = |v_j|/dx, stencil weights (K1, K2) = (2, -1/2) (second order), wall terms E where an
@@ -13,7 +13,7 @@
 //
 // The per-point scalars are broadcast from a 10-word shared-memory record to every lane of the
 // warps of the quadrant; with four velocities per lane each broadcast serves 128 velocities.
-// Solid points carry zero records; tile rows without fluid are skipped.  The next tile's records
+// Solid points carry zero records; pairs of tile rows without fluid are skipped.  The next tile's records
 // are loaded into registers while the current tile is swept, and progress is published as soon as
 // the band edge is stored.  The moment of a point is summed in a fixed order (the lane's four
 // velocities, the lane tree, the warps, the quadrants), so results do not depend on tile shapes.
@@ -185,16 +185,17 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
                         const int yo = row0 + r;
                         const int y = s2neg ? n2 - 1 - yo : yo;
                         const int id = y * n1 + x;
+                        // every load is issued without waiting for the code: a branch on it would
+                        // expose one more global-memory latency per tile (values of solid points
+                        // are loaded and dropped)
                         raw[k].code = P->code[id];
-                        if (!(raw[k].code & kSolidBit)) {
-                            raw[k].s = reinterpret_cast<const float4*>(P->src)[id];
-                            raw[k].e = reinterpret_cast<const float4*>(P->E)[id];
-                            if constexpr (SPEC) {
-                                const int* fi = P->face_id;
-                                const size_t Nn = (size_t)N;
-                                raw[k].f = make_int4(fi[(0 + s1neg) * Nn + id], fi[(2 + s2neg) * Nn + id],
-                                                     fi[(1 - s1neg) * Nn + id], fi[(3 - s2neg) * Nn + id]);
-                            }
+                        raw[k].s = reinterpret_cast<const float4*>(P->src)[id];
+                        raw[k].e = reinterpret_cast<const float4*>(P->E)[id];
+                        if constexpr (SPEC) {
+                            const int* fi = P->face_id;
+                            const size_t Nn = (size_t)N;
+                            raw[k].f = make_int4(fi[(0 + s1neg) * Nn + id], fi[(2 + s2neg) * Nn + id],
+                                                 fi[(1 - s1neg) * Nn + id], fi[(3 - s2neg) * Nn + id]);
                         }
                     }
                 }
@@ -287,73 +288,127 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
                     }
                 }
             }
+            // one point of a row: Eq. 10 for the lane's four velocities, with the x1 upstream values
+            // (hp1, hp2) carried along the row and the x2 upstream values (u1, u2) of its column;
+            // returns the lane's moment sums of the point
+            auto point = [&](const float* rrow, int i, float2 (&hp1)[2], float2 (&hp2)[2], float4& u1, float4& u2,
+                             float& m0, float& m1, float& m2) {
+                const float4* Rp = reinterpret_cast<const float4*>(rrow + i * RF);
+                const float4 A = Rp[0];                 // a b1 b2 roff
+                const float4 B = Rp[1];                 // E1 K1x K2x E2
+                const float2 C = *reinterpret_cast<const float2*>(Rp + 2);   // K1y K2y
+                // specular parts of the upstream wall values: (1 - alpha) h'(x, reflected v)
+                int4 Fi = make_int4(-1, -1, -1, -1);
+                float4 Fx = make_float4(0.f, 0.f, 0.f, 0.f), Fy = Fx;
+                if constexpr (SPEC) {
+                    Fi = reinterpret_cast<const int4*>(Rp)[3];
+                    if (Fi.x >= 0) Fx = *reinterpret_cast<const float4*>(fprev1 + (size_t)Fi.x * 2 * NL);
+                    if (Fi.y >= 0) Fy = *reinterpret_cast<const float4*>(fprev2 + (size_t)Fi.y * 2 * NL);
+                }
+                const float4 Rv = *reinterpret_cast<const float4*>(my_rtab + __float_as_int(A.w));
+                const float2 aP = dup(A.x), b1P = dup(A.y), b2P = dup(A.z);
+                const float2 E1P = dup(B.x), K1xP = dup(B.y), K2xP = dup(B.z), E2P = dup(B.w);
+                const float2 K1yP = dup(C.x), K2yP = dup(C.y);
+                const float2 rb1a = make_float2(u1.x, u1.y), rb1b = make_float2(u1.z, u1.w);
+                const float2 rb2a = make_float2(u2.x, u2.y), rb2b = make_float2(u2.z, u2.w);
+                float2 h[2];
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const float2 up1 = k ? rb1b : rb1a;
+                    const float2 up2 = k ? rb2b : rb2a;
+                    const float2 S = fma2(b2P, L.v2[k], fma2(b1P, L.v1[k], aP));
+                    float2 t2 = fma2(K1yP, up1, fma2(K2yP, up2, E2P));
+                    if constexpr (SPEC) t2 = fma2(specP, k ? make_float2(Fy.z, Fy.w) : make_float2(Fy.x, Fy.y), t2);
+                    const float2 base = fma2(L.a2[k], t2, S);
+                    float2 t1 = fma2(K1xP, hp1[k], fma2(K2xP, hp2[k], E1P));
+                    if constexpr (SPEC) t1 = fma2(specP, k ? make_float2(Fx.z, Fx.w) : make_float2(Fx.x, Fx.y), t1);
+                    const float2 Rk = k ? make_float2(Rv.z, Rv.w) : make_float2(Rv.x, Rv.y);
+                    h[k] = mul2(fma2(L.a1[k], t1, base), Rk);
+                    hp2[k] = hp1[k];
+                    hp1[k] = h[k];
+                }
+                u2 = u1;
+                u1 = make_float4(h[0].x, h[0].y, h[1].x, h[1].y);
+                if constexpr (SPEC) {   // molecules moving into a downstream face
+                    if (Fi.z >= 0) *reinterpret_cast<float4*>(fnext1 + (size_t)Fi.z * 2 * NL) = u1;
+                    if (Fi.w >= 0) *reinterpret_cast<float4*>(fnext2 + (size_t)Fi.w * 2 * NL) = u1;
+                }
+                const float2 p0 = fma2(L.W[1], h[1], mul2(L.W[0], h[0]));
+                const float2 p1 = fma2(L.Wv1[1], h[1], mul2(L.Wv1[0], h[0]));
+                const float2 p2 = fma2(L.Wv2[1], h[1], mul2(L.Wv2[0], h[0]));
+                m0 = p0.x + p0.y;
+                m1 = p1.x + p1.y;
+                m2 = p2.x + p2.y;
+            };
+            auto load_carry = [&](int r, float2 (&hp1)[2], float2 (&hp2)[2]) {
+                const float* cr = carry + ((size_t)(warp * RB + r) * 2) * 128 + 4 * lane;
+                const float4 c1 = *reinterpret_cast<const float4*>(cr);
+                const float4 c2 = *reinterpret_cast<const float4*>(cr + 128);
+                hp1[0] = make_float2(c1.x, c1.y);
+                hp1[1] = make_float2(c1.z, c1.w);
+                hp2[0] = make_float2(c2.x, c2.y);
+                hp2[1] = make_float2(c2.z, c2.w);
+            };
+            auto store_carry = [&](int r, const float2 (&hp1)[2], const float2 (&hp2)[2]) {
+                float* cr = carry + ((size_t)(warp * RB + r) * 2) * 128 + 4 * lane;
+                *reinterpret_cast<float4*>(cr) = make_float4(hp1[0].x, hp1[0].y, hp1[1].x, hp1[1].y);
+                *reinterpret_cast<float4*>(cr + 128) = make_float4(hp2[0].x, hp2[0].y, hp2[1].x, hp2[1].y);
+            };
+            // Rows are walked two at a time, the upper one a column behind the lower (it needs the
+            // lower row's value of the same column), which gives every step two independent points;
+            // the moments of both rows are then reduced together.  A pair is skipped when neither
+            // row has fluid in the tile; an empty row of a pair is swept anyway: its zero records
+            // give h = 0, which no fluid point reads (its code marks that upstream point solid), so
+            // the result is the same as with the row skipped.
             auto walk_rows = [&](auto full_tag) {
                 constexpr bool FULL = decltype(full_tag)::value;
-                for (int r = 0; r < nrows; ++r) {
-                    const unsigned fm = mk[r];
-                    if (fm == 0u) continue;     // no fluid in this tile row: nothing reads it
-                    float* cr = carry + ((size_t)(warp * RB + r) * 2) * 128 + 4 * lane;
-                    const float4 c1 = *reinterpret_cast<const float4*>(cr);
-                    const float4 c2 = *reinterpret_cast<const float4*>(cr + 128);
-                    float2 hp1[2] = {make_float2(c1.x, c1.y), make_float2(c1.z, c1.w)};
-                    float2 hp2[2] = {make_float2(c2.x, c2.y), make_float2(c2.z, c2.w)};
+                int r = 0;
+                for (; r + 1 < nrows; r += 2) {
+                    if ((mk[r] | mk[r + 1]) == 0u) continue;
+                    float2 hA1[2], hA2[2], hB1[2], hB2[2];
+                    load_carry(r, hA1, hA2);
+                    load_carry(r + 1, hB1, hB2);
+                    const float* rowA = rbuf + (size_t)r * T1 * RF;
+                    const float* rowB = rowA + (size_t)T1 * RF;
+                    float m0[2 * T1], m1[2 * T1], m2[2 * T1];
+#pragma unroll
+                    for (int st = 0; st <= T1; ++st) {
+                        if (st < T1) {
+                            const int i = st;
+                            if (FULL || i < width) point(rowA, i, hA1, hA2, rb1[i], rb2[i], m0[i], m1[i], m2[i]);
+                            else m0[i] = m1[i] = m2[i] = 0.f;
+                        }
+                        if (st >= 1) {
+                            const int i = st - 1;
+                            if (FULL || i < width) point(rowB, i, hB1, hB2, rb1[i], rb2[i], m0[T1 + i], m1[T1 + i], m2[T1 + i]);
+                            else m0[T1 + i] = m1[T1 + i] = m2[T1 + i] = 0.f;
+                        }
+                    }
+                    store_carry(r, hA1, hA2);
+                    store_carry(r + 1, hB1, hB2);
+                    const float s0 = reduce_scatter<float, 2 * T1>(m0, lane);
+                    const float s1 = reduce_scatter<float, 2 * T1>(m1, lane);
+                    const float s2 = reduce_scatter<float, 2 * T1>(m2, lane);
+                    // value v of the 2 T1 ends in the lanes v * 32 / (2 T1) onward: row r + v / T1
+                    if ((lane & (kLPP / 2 - 1)) == 0) {
+                        const int v = lane / (kLPP / 2);
+                        float* d = part + ((size_t)(warp * RB + r + v / T1) * T1 + (v % T1)) * 3;
+                        d[0] = s0;
+                        d[1] = s1;
+                        d[2] = s2;
+                    }
+                }
+                if (r < nrows && mk[r] != 0u) {   // the last row of an odd band
+                    float2 hp1[2], hp2[2];
+                    load_carry(r, hp1, hp2);
                     const float* rrow = rbuf + (size_t)r * T1 * RF;
                     float m0[T1], m1[T1], m2[T1];
 #pragma unroll
                     for (int i = 0; i < T1; ++i) {
-                        if (FULL || i < width) {
-                            const float4* Rp = reinterpret_cast<const float4*>(rrow + i * RF);
-                            const float4 A = Rp[0];                 // a b1 b2 roff
-                            const float4 B = Rp[1];                 // E1 K1x K2x E2
-                            const float2 C = *reinterpret_cast<const float2*>(Rp + 2);   // K1y K2y
-                            // specular parts of the upstream wall values: (1 - alpha) h'(x, reflected v)
-                            int4 Fi = make_int4(-1, -1, -1, -1);
-                            float4 Fx = make_float4(0.f, 0.f, 0.f, 0.f), Fy = Fx;
-                            if constexpr (SPEC) {
-                                Fi = reinterpret_cast<const int4*>(Rp)[3];
-                                if (Fi.x >= 0) Fx = *reinterpret_cast<const float4*>(fprev1 + (size_t)Fi.x * 2 * NL);
-                                if (Fi.y >= 0) Fy = *reinterpret_cast<const float4*>(fprev2 + (size_t)Fi.y * 2 * NL);
-                            }
-                            const float4 Rv = *reinterpret_cast<const float4*>(my_rtab + __float_as_int(A.w));
-                            const float2 aP = dup(A.x), b1P = dup(A.y), b2P = dup(A.z);
-                            const float2 E1P = dup(B.x), K1xP = dup(B.y), K2xP = dup(B.z), E2P = dup(B.w);
-                            const float2 K1yP = dup(C.x), K2yP = dup(C.y);
-                            const float2 rb1a = make_float2(rb1[i].x, rb1[i].y), rb1b = make_float2(rb1[i].z, rb1[i].w);
-                            const float2 rb2a = make_float2(rb2[i].x, rb2[i].y), rb2b = make_float2(rb2[i].z, rb2[i].w);
-                            float2 h[2];
-#pragma unroll
-                            for (int k = 0; k < 2; ++k) {
-                                const float2 up1 = k ? rb1b : rb1a;
-                                const float2 up2 = k ? rb2b : rb2a;
-                                const float2 S = fma2(b2P, L.v2[k], fma2(b1P, L.v1[k], aP));
-                                float2 t2 = fma2(K1yP, up1, fma2(K2yP, up2, E2P));
-                                if constexpr (SPEC) t2 = fma2(specP, k ? make_float2(Fy.z, Fy.w) : make_float2(Fy.x, Fy.y), t2);
-                                const float2 base = fma2(L.a2[k], t2, S);
-                                float2 t1 = fma2(K1xP, hp1[k], fma2(K2xP, hp2[k], E1P));
-                                if constexpr (SPEC) t1 = fma2(specP, k ? make_float2(Fx.z, Fx.w) : make_float2(Fx.x, Fx.y), t1);
-                                const float2 Rk = k ? make_float2(Rv.z, Rv.w) : make_float2(Rv.x, Rv.y);
-                                h[k] = mul2(fma2(L.a1[k], t1, base), Rk);
-                                hp2[k] = hp1[k];
-                                hp1[k] = h[k];
-                            }
-                            rb2[i] = rb1[i];
-                            rb1[i] = make_float4(h[0].x, h[0].y, h[1].x, h[1].y);
-                            if constexpr (SPEC) {   // molecules moving into a downstream face
-                                if (Fi.z >= 0) *reinterpret_cast<float4*>(fnext1 + (size_t)Fi.z * 2 * NL) = rb1[i];
-                                if (Fi.w >= 0) *reinterpret_cast<float4*>(fnext2 + (size_t)Fi.w * 2 * NL) = rb1[i];
-                            }
-                            const float2 p0 = fma2(L.W[1], h[1], mul2(L.W[0], h[0]));
-                            const float2 p1 = fma2(L.Wv1[1], h[1], mul2(L.Wv1[0], h[0]));
-                            const float2 p2 = fma2(L.Wv2[1], h[1], mul2(L.Wv2[0], h[0]));
-                            m0[i] = p0.x + p0.y;
-                            m1[i] = p1.x + p1.y;
-                            m2[i] = p2.x + p2.y;
-                        } else {
-                            m0[i] = m1[i] = m2[i] = 0.f;
-                        }
+                        if (FULL || i < width) point(rrow, i, hp1, hp2, rb1[i], rb2[i], m0[i], m1[i], m2[i]);
+                        else m0[i] = m1[i] = m2[i] = 0.f;
                     }
-                    *reinterpret_cast<float4*>(cr) = make_float4(hp1[0].x, hp1[0].y, hp1[1].x, hp1[1].y);
-                    *reinterpret_cast<float4*>(cr + 128) = make_float4(hp2[0].x, hp2[0].y, hp2[1].x, hp2[1].y);
+                    store_carry(r, hp1, hp2);
                     const float s0 = reduce_scatter<float, T1>(m0, lane);
                     const float s1 = reduce_scatter<float, T1>(m1, lane);
                     const float s2 = reduce_scatter<float, T1>(m2, lane);

@@ -144,11 +144,10 @@ __global__ void __launch_bounds__(256) sweep2d_pair_kernel(const SweepArgs2D<flo
                         const int yo = row0 + r;
                         const int y = s2neg ? n2 - 1 - yo : yo;
                         const int id = y * n1 + x;
+                        // issued together: no branch on the code before the other loads
                         raw[k].code = P->code[id];
-                        if (!(raw[k].code & kSolidBit)) {
-                            raw[k].s = reinterpret_cast<const float4*>(P->src)[id];
-                            raw[k].e = reinterpret_cast<const float4*>(P->E)[id];
-                        }
+                        raw[k].s = reinterpret_cast<const float4*>(P->src)[id];
+                        raw[k].e = reinterpret_cast<const float4*>(P->E)[id];
                     }
                 }
             }

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "dvm_device.cuh"
 #include "dvm_internal.h"
@@ -49,6 +50,15 @@ template <> struct PairStore<true> {
 
 __device__ __forceinline__ float2 dup2(float x) { return make_float2(x, x); }
 
+// global data of one point that its record is built from, loaded one tile ahead
+struct RawPoint3 {
+    int code;
+    float4 s, e0, e1;
+    float st;
+    int4 f0, f1;
+};
+constexpr int kRawRounds = 1;   // points per thread held in registers across a tile
+
 // 16-byte asynchronous copy global -> shared that bypasses L1 (pencil edges are written by other
 // SMs during the launch), and its group commit / wait
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
@@ -81,8 +91,8 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
     const int lane = threadIdx.x & 31;
     const int MR2 = a.maxR2, MR3 = a.maxR3;
     const int MROWS = MR2 * MR3;
-    float* rec = reinterpret_cast<float*>(smem_raw);                      // [MROWS][T1][RF]
-    float* part = rec + (size_t)MROWS * T1 * RF;                          // [NW][MROWS][T1][NM]
+    float* rec = reinterpret_cast<float*>(smem_raw);                      // [2][MROWS][T1][RF]
+    float* part = rec + (size_t)2 * MROWS * T1 * RF;                      // [NW][MROWS][T1][NM]
     float* carry = part + (size_t)NW * MROWS * T1 * NM;                   // [NW][MROWS][2][64]
     float* pb = carry + (size_t)NW * MROWS * 2 * kPL;                     // [NW][MR2][2][T1][64]
     float* eb = pb + (size_t)NW * MR2 * 2 * T1 * kPL;                     // [NW][2][2][T1][64]
@@ -160,75 +170,126 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
         const int hl = lane & 15, half = lane >> 4;
         const size_t lw = (size_t)g * a.GL + (size_t)kPL * warp + 4 * hl;
         const int ntiles = SUB ? P->nt1 : (n1 + T1 - 1) / T1;
+        // tile: first oriented column, width, x1 carry-in and carry-out ghost slots (or -1)
+        auto tile_info = [&](int tt) -> int4 {
+            if constexpr (SUB) return P->tiles1[s1n * ntiles + tt];
+            else return make_int4(tt * T1, min(T1, n1 - tt * T1), tt == 0 ? 0 : -1, tt == ntiles - 1 ? 0 : -1);
+        };
+        // records of a tile's points for this octant (shared by all lanes and velocities) and the
+        // fluid bits of every row.  Point idx of a tile is (plane kk, row jj, column i); a thread's
+        // points are loaded for tile t + 1 while tile t is swept (all loads issued together, with
+        // no branch on the code) and written to that tile's record buffer at the end of tile t.
+        const int npts = nr3 * MR2 * T1;
+        auto load_point = [&](const int4& tj, int idx, RawPoint3& r) {
+            r.code = kSolidBit;
+            const int kk = idx / (MR2 * T1);
+            const int rem = idx - kk * MR2 * T1;
+            const int jj = rem / T1;
+            const int i = rem - jj * T1;
+            if (jj < nr2 && i < tj.y) {
+                const int ic = tj.x + i;
+                const int x = s1n ? n1 - 1 - ic : ic;
+                const int y = s2n ? n2 - 1 - (j0 + jj) : (j0 + jj);
+                const int z = s3n ? n3 - 1 - (k0 + kk) : (k0 + kk);
+                const int id = (z * n2 + y) * n1 + x;
+                r.code = P->code[id];
+                r.s = reinterpret_cast<const float4*>(P->src)[id];
+                r.e0 = reinterpret_cast<const float4*>(P->E)[2 * (size_t)id];
+                r.e1 = reinterpret_cast<const float4*>(P->E)[2 * (size_t)id + 1];
+                if constexpr (TAU) r.st = P->srct[id];
+                if constexpr (SPEC) {   // faces: upstream (read) x1 x2 x3, downstream (written)
+                    const int* fi = P->face_id;
+                    const size_t Nn = (size_t)N;
+                    r.f0 = make_int4(fi[(0 + s1n) * Nn + id], fi[(2 + s2n) * Nn + id], fi[(4 + s3n) * Nn + id],
+                                     fi[(1 - s1n) * Nn + id]);
+                    r.f1 = make_int4(fi[(3 - s2n) * Nn + id], fi[(5 - s3n) * Nn + id], -1, -1);
+                }
+            }
+        };
+        auto store_point = [&](int buf, int idx, const RawPoint3& r) {
+            float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
+            int4 r4 = make_int4(-1, -1, -1, -1), r5 = r4;
+            const int kk = idx / (MR2 * T1);
+            const int rem = idx - kk * MR2 * T1;
+            const int jj = rem / T1;
+            const int i = rem - jj * T1;
+            if (!(r.code & kSolidBit)) {
+                const int code = r.code;
+                const int ca = (code >> (2 * (0 + s1n))) & 3;
+                const int cb = (code >> (2 * (2 + s2n))) & 3;
+                const int cc = (code >> (2 * (4 + s3n))) & 3;
+                // first-order denominator when either upstream point is solid (cases 1, 2)
+                const int rs = (ca != 0) | ((cb != 0) << 1) | ((cc != 0) << 2);
+                r0 = r.s;
+                r1 = make_float4(s1n ? r.e0.y : r.e0.x, s2n ? r.e0.w : r.e0.z, s3n ? r.e1.y : r.e1.x,
+                                 __int_as_float(rs * kPL));
+                r2 = make_float4(ca == 2 ? 0.f : (ca == 1 ? 1.f : K1o), ca == 0 ? K2o : 0.f,
+                                 cb == 2 ? 0.f : (cb == 1 ? 1.f : K1o), cb == 0 ? K2o : 0.f);
+                r3 = make_float4(cc == 2 ? 0.f : (cc == 1 ? 1.f : K1o), cc == 0 ? K2o : 0.f, TAU ? r.st : 0.f, 0.f);
+                if constexpr (SPEC) {
+                    r4 = r.f0;
+                    r5 = r.f1;
+                }
+                atomicOr(fmask + buf * MROWS + kk * MR2 + jj, 1u << i);
+            }
+            float4* R = reinterpret_cast<float4*>(rec + (size_t)buf * MROWS * T1 * RF + (size_t)idx * RF);
+            R[0] = r0;
+            R[1] = r1;
+            R[2] = r2;
+            R[3] = r3;
+            if constexpr (SPEC) {
+                reinterpret_cast<int4*>(R)[4] = r4;
+                reinterpret_cast<int4*>(R)[5] = r5;
+            }
+        };
+        auto load_raw = [&](int tt, RawPoint3 (&raw)[kRawRounds]) {
+            const int4 tj = tile_info(tt);
+#pragma unroll
+            for (int k = 0; k < kRawRounds; ++k) {
+                const int idx = k * blockDim.x + threadIdx.x;
+                raw[k].code = kSolidBit;
+                if (idx < npts) load_point(tj, idx, raw[k]);
+            }
+        };
+        // the held points, then the points beyond the register rounds (loaded here)
+        auto store_rec = [&](int tt, int buf, const RawPoint3 (&raw)[kRawRounds]) {
+#pragma unroll
+            for (int k = 0; k < kRawRounds; ++k) {
+                const int idx = k * blockDim.x + threadIdx.x;
+                if (idx < npts) store_point(buf, idx, raw[k]);
+            }
+            if (kRawRounds * (int)blockDim.x < npts) {
+                const int4 tj = tile_info(tt);
+                for (int idx = kRawRounds * blockDim.x + threadIdx.x; idx < npts; idx += blockDim.x) {
+                    RawPoint3 r;
+                    load_point(tj, idx, r);
+                    store_point(buf, idx, r);
+                }
+            }
+        };
+        {   // tile 0 (its masks were cleared before the barrier that started the item)
+            RawPoint3 raw[kRawRounds];
+            load_raw(0, raw);
+            store_rec(0, 0, raw);
+        }
         for (int t = 0; t < ntiles; ++t) {
-            // tile: first oriented column, width, x1 carry-in and carry-out ghost slots (or -1)
-            int4 ti;
-            if constexpr (SUB) ti = P->tiles1[s1n * ntiles + t];
-            else ti = make_int4(t * T1, min(T1, n1 - t * T1), t == 0 ? 0 : -1, t == ntiles - 1 ? 0 : -1);
+            const int4 ti = tile_info(t);
             const int c0 = ti.x;
             const int width = ti.y;
+            RawPoint3 nxt[kRawRounds];
+            if (t + 1 < ntiles) load_raw(t + 1, nxt);
             if (threadIdx.x == 0) {
                 bool ok = true;
                 if (pi2.z < 0) ok = wait_geq(prog + p3 * np2 + p2 - 1, t + 1, a.status, a.timeout_ns);
                 if (ok && pi3.z < 0) ok = wait_geq(prog + (p3 - 1) * np2 + p2, t + 1, a.status, a.timeout_ns);
                 if (!ok) s_abort = 1;
             }
-            // records of the tile's points for this octant (shared by all lanes and velocities) and
-            // the fluid bits of every row; the masks of the next tile are cleared here (their last
-            // reader, the moment loop of the previous tile, is behind the barrier that ended it)
+            // the masks of the next tile are cleared here (their last reader, the moment loop of
+            // the previous tile, is behind the barrier that ended it; they are set at the end of
+            // this tile, behind the barrier below)
             unsigned* fm_cur = fmask + (t & 1) * MROWS;
+            const float* recb = rec + (size_t)(t & 1) * MROWS * T1 * RF;
             for (int r = threadIdx.x; r < MROWS; r += blockDim.x) fmask[((t + 1) & 1) * MROWS + r] = 0u;
-            const int npts = nr3 * MR2 * T1;
-            for (int idx = threadIdx.x; idx < npts; idx += blockDim.x) {
-                const int kk = idx / (MR2 * T1);
-                const int rem = idx - kk * MR2 * T1;
-                const int jj = rem / T1;
-                const int i = rem - jj * T1;
-                float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
-                int4 r4 = make_int4(-1, -1, -1, -1), r5 = r4;
-                if (jj < nr2 && i < width) {
-                    const int ic = c0 + i;
-                    const int x = s1n ? n1 - 1 - ic : ic;
-                    const int y = s2n ? n2 - 1 - (j0 + jj) : (j0 + jj);
-                    const int z = s3n ? n3 - 1 - (k0 + kk) : (k0 + kk);
-                    const int id = (z * n2 + y) * n1 + x;
-                    const uint16_t code = P->code[id];
-                    if (!(code & kSolidBit)) {
-                        const float4 s = reinterpret_cast<const float4*>(P->src)[id];
-                        const float4 e0 = reinterpret_cast<const float4*>(P->E)[2 * (size_t)id];
-                        const float4 e1 = reinterpret_cast<const float4*>(P->E)[2 * (size_t)id + 1];
-                        const int ca = (code >> (2 * (0 + s1n))) & 3;
-                        const int cb = (code >> (2 * (2 + s2n))) & 3;
-                        const int cc = (code >> (2 * (4 + s3n))) & 3;
-                        // first-order denominator when either upstream point is solid (cases 1, 2)
-                        const int rs = (ca != 0) | ((cb != 0) << 1) | ((cc != 0) << 2);
-                        r0 = s;
-                        r1 = make_float4(s1n ? e0.y : e0.x, s2n ? e0.w : e0.z, s3n ? e1.y : e1.x,
-                                         __int_as_float(rs * kPL));
-                        r2 = make_float4(ca == 2 ? 0.f : (ca == 1 ? 1.f : K1o), ca == 0 ? K2o : 0.f,
-                                         cb == 2 ? 0.f : (cb == 1 ? 1.f : K1o), cb == 0 ? K2o : 0.f);
-                        r3 = make_float4(cc == 2 ? 0.f : (cc == 1 ? 1.f : K1o), cc == 0 ? K2o : 0.f,
-                                         TAU ? P->srct[id] : 0.f, 0.f);
-                        if constexpr (SPEC) {   // faces: upstream (read) x1 x2 x3, downstream (written)
-                            const int* fi = P->face_id;
-                            const size_t Nn = (size_t)N;
-                            r4 = make_int4(fi[(0 + s1n) * Nn + id], fi[(2 + s2n) * Nn + id], fi[(4 + s3n) * Nn + id],
-                                           fi[(1 - s1n) * Nn + id]);
-                            r5 = make_int4(fi[(3 - s2n) * Nn + id], fi[(5 - s3n) * Nn + id], -1, -1);
-                        }
-                        atomicOr(fm_cur + kk * MR2 + jj, 1u << i);
-                    }
-                }
-                float4* R = reinterpret_cast<float4*>(rec + (size_t)((kk * MR2 + jj) * T1 + i) * RF);
-                R[0] = r0;
-                R[1] = r1;
-                R[2] = r2;
-                R[3] = r3;
-                if constexpr (SPEC) {
-                    reinterpret_cast<int4*>(R)[4] = r4;
-                    reinterpret_cast<int4*>(R)[5] = r5;
-                }
-            }
             __syncthreads();
             if (s_abort) {
                 cp_async_wait<0>();
@@ -269,7 +330,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                 ? ((((size_t)par * 8 + q) * P->ns2 + pi2.z) * n3 * n1) * 2 * NL
                 : ((((size_t)q * np3 + p3) * 2 * P->ns2 + (-1 - pi2.z)) * P->R3 * n1) * 2 * NL;
             auto yrow = [&](int kk) -> size_t { return yg ? (size_t)(k0 + kk) * n1 : (size_t)kk * n1; };
-            auto rbuf_rec = [&](int kk, int jj, int i) -> const float* { return rec + (size_t)((kk * MR2 + jj) * T1 + i) * RF; };
+            auto rbuf_rec = [&](int kk, int jj, int i) -> const float* { return recb + (size_t)((kk * MR2 + jj) * T1 + i) * RF; };
             // FP32: the x2 rows of plane kk go to slot kk & 1, copied while plane kk - 1 is swept
             // Upstream values are fetched only where the stencil of the point that reads them has a
             // nonzero coefficient for them (record K1 / K2 of the first row or plane): values of
@@ -346,18 +407,138 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                         }
                     }
                 }
-                for (int jj = 0; jj < nr2; ++jj) {
-                    // solid points are not swept: every fluid point downstream of one gives it a zero
-                    // stencil coefficient (its code marks that upstream point solid), so the values
-                    // left in the carries, rows and planes there are never used
+                // one point: Eq. 10 for the lane's velocity pair with the x1 upstream values (hp1,
+                // hp2) of its row, the x2 upstream values rb of its column and the x3 upstream values
+                // of its row's plane staging zr; returns the lane's moment sums of the point
+                auto point = [&](const float* rrow, float* zr, int i, float2& hp1, float2& hp2, float& m0, float& m1,
+                                 float& m2, float& m3, float& m4) {
+                    const float4* R = reinterpret_cast<const float4*>(rrow + i * RF);
+                    const float4 A = R[0], B = R[1], C = R[2], D = R[3];
+                    const float2 z1 = *reinterpret_cast<const float2*>(zr + (size_t)i * kPL);
+                    const float2 z2 = *reinterpret_cast<const float2*>(zr + ((size_t)T1 + i) * kPL);
+                    const float2 Rk = *reinterpret_cast<const float2*>(my_rtab + __float_as_int(B.w));
+                    float2 S = fma2(dup2(A.w), v3, fma2(dup2(A.z), v2, fma2(dup2(A.y), v1, dup2(A.x))));
+                    if constexpr (TAU) S = fma2(dup2(D.z), vq, S);   // nu tau (|v|^2 - 3/2)
+                    float2 t1 = fma2(dup2(C.x), hp1, fma2(dup2(C.y), hp2, dup2(B.x)));
+                    float2 t2 = fma2(dup2(C.z), rb1[i], fma2(dup2(C.w), rb2[i], dup2(B.y)));
+                    float2 t3 = fma2(dup2(D.x), z1, fma2(dup2(D.y), z2, dup2(B.z)));
+                    int4 Fa, Fb;
+                    if constexpr (SPEC) {   // + (1 - alpha) h'(x, reflected v) at walls
+                        Fa = reinterpret_cast<const int4*>(R)[4];
+                        Fb = reinterpret_cast<const int4*>(R)[5];
+                        if (Fa.x >= 0) t1 = fma2(specP, *reinterpret_cast<const float2*>(fprev[0] + (size_t)Fa.x * fstride), t1);
+                        if (Fa.y >= 0) t2 = fma2(specP, *reinterpret_cast<const float2*>(fprev[1] + (size_t)Fa.y * fstride), t2);
+                        if (Fa.z >= 0) t3 = fma2(specP, *reinterpret_cast<const float2*>(fprev[2] + (size_t)Fa.z * fstride), t3);
+                    }
+                    // the x1 term (carried from the previous point) enters last: three dependent
+                    // operations per point along the x1 chain
+                    const float2 num = fma2(a1, t1, fma2(a3, t3, fma2(a2, t2, S)));
+                    const float2 h = mul2(num, Rk);
+                    if constexpr (SPEC) {   // molecules moving into a downstream face
+                        if (Fa.w >= 0) *reinterpret_cast<float2*>(fnext[0] + (size_t)Fa.w * fstride) = h;
+                        if (Fb.x >= 0) *reinterpret_cast<float2*>(fnext[1] + (size_t)Fb.x * fstride) = h;
+                        if (Fb.y >= 0) *reinterpret_cast<float2*>(fnext[2] + (size_t)Fb.y * fstride) = h;
+                    }
+                    hp2 = hp1;
+                    hp1 = h;
+                    rb2[i] = rb1[i];
+                    rb1[i] = h;
+                    *reinterpret_cast<float2*>(zr + ((size_t)T1 + i) * kPL) = z1;
+                    *reinterpret_cast<float2*>(zr + (size_t)i * kPL) = h;
+                    const float2 p0 = mul2(W, h), p1 = mul2(Wv1, h), p2v = mul2(Wv2, h), p3v = mul2(Wv3, h);
+                    m0 = p0.x + p0.y;
+                    m1 = p1.x + p1.y;
+                    m2 = p2v.x + p2v.y;
+                    m3 = p3v.x + p3v.y;
+                    if constexpr (TAU) {
+                        const float2 p4v = mul2(Wvv, h);
+                        m4 = p4v.x + p4v.y;
+                    } else {
+                        m4 = 0.f;
+                    }
+                };
+                auto row_ptrs = [&](int jj, float*& cr, float*& zr, const float*& rrow, float*& prow) {
+                    cr = carry + ((size_t)(warp * MROWS + kk * MR2 + jj) * 2) * kPL + 2 * lane;
+                    zr = pb + ((((size_t)warp * MR2 + jj) * 2) * T1) * kPL + 2 * lane;   // [2][T1][64]
+                    rrow = recb + (size_t)((kk * MR2 + jj) * T1) * RF;
+                    prow = part + ((size_t)(warp * MROWS + kk * MR2 + jj) * T1) * NM;
+                };
+                // solid points are not swept: every fluid point downstream of one gives it a zero
+                // stencil coefficient (its code marks that upstream point solid), so the values left
+                // in the carries, rows and planes there are never used
+                int jj = 0;
+                if constexpr (T1 == 4) {
+                    // rows two at a time, the upper one a column behind the lower (it needs the lower
+                    // row's value of the same column): two independent points per step.  A step with
+                    // a fluid point sweeps both of its points; a solid one has a zero record and gets
+                    // h = 0, which is as unused as the value a skipped point leaves.
+                    // Points beyond the tile width are never swept (their staging is not filled, and
+                    // the x1 carries must end at the last column).
+                    auto walk_pairs = [&](auto full_tag) {
+                    constexpr bool FULL = decltype(full_tag)::value;
+                    for (; jj + 1 < nr2; jj += 2) {
+                        const unsigned fa = fm_cur[kk * MR2 + jj], fb = fm_cur[kk * MR2 + jj + 1];
+                        if ((fa | fb) == 0u) continue;
+                        float *crA, *zrA, *prA, *crB, *zrB, *prB;
+                        const float *rrA, *rrB;
+                        row_ptrs(jj, crA, zrA, rrA, prA);
+                        row_ptrs(jj + 1, crB, zrB, rrB, prB);
+                        float2 hA1 = *reinterpret_cast<const float2*>(crA), hA2 = *reinterpret_cast<const float2*>(crA + kPL);
+                        float2 hB1 = *reinterpret_cast<const float2*>(crB), hB2 = *reinterpret_cast<const float2*>(crB + kPL);
+                        float m0[8], m1[8], m2[8], m3[8], m4[8];
+#pragma unroll
+                        for (int st = 0; st <= 4; ++st) {
+                            const bool onA = st < 4 && ((fa >> st) & 1u);
+                            const bool onB = st >= 1 && ((fb >> (st - 1)) & 1u);
+                            if (onA || onB) {
+                                if (st < 4) {
+                                    if (FULL || st < width) point(rrA, zrA, st, hA1, hA2, m0[st], m1[st], m2[st], m3[st], m4[st]);
+                                    else m0[st] = m1[st] = m2[st] = m3[st] = m4[st] = 0.f;
+                                }
+                                if (st >= 1) {
+                                    if (FULL || st - 1 < width)
+                                        point(rrB, zrB, st - 1, hB1, hB2, m0[3 + st], m1[3 + st], m2[3 + st],
+                                              m3[3 + st], m4[3 + st]);
+                                    else m0[3 + st] = m1[3 + st] = m2[3 + st] = m3[3 + st] = m4[3 + st] = 0.f;
+                                }
+                            } else {
+                                if (st < 4) m0[st] = m1[st] = m2[st] = m3[st] = m4[st] = 0.f;
+                                if (st >= 1) m0[3 + st] = m1[3 + st] = m2[3 + st] = m3[3 + st] = m4[3 + st] = 0.f;
+                            }
+                        }
+                        *reinterpret_cast<float2*>(crA) = hA1;
+                        *reinterpret_cast<float2*>(crA + kPL) = hA2;
+                        *reinterpret_cast<float2*>(crB) = hB1;
+                        *reinterpret_cast<float2*>(crB + kPL) = hB2;
+                        const float r0 = reduce_scatter<float, 8>(m0, lane);
+                        const float r1 = reduce_scatter<float, 8>(m1, lane);
+                        const float r2 = reduce_scatter<float, 8>(m2, lane);
+                        const float r3 = reduce_scatter<float, 8>(m3, lane);
+                        float r4 = 0.f;
+                        if constexpr (TAU) r4 = reduce_scatter<float, 8>(m4, lane);
+                        // value v of the eight ends in lanes 4 v .. 4 v + 3: row jj + v / 4, column v % 4
+                        const int v = lane >> 2;
+                        if ((lane & 3) == 0 && (v & 3) < width) {
+                            float* d = (v < 4 ? prA : prB) + (v & 3) * NM;
+                            d[0] = r0;
+                            d[1] = r1;
+                            d[2] = r2;
+                            d[3] = r3;
+                            if constexpr (TAU) d[4] = r4;
+                        }
+                    }
+                    };
+                    if (width == T1) walk_pairs(std::integral_constant<bool, true>{});
+                    else walk_pairs(std::integral_constant<bool, false>{});
+                }
+                for (; jj < nr2; ++jj) {
                     const unsigned fm = fm_cur[kk * MR2 + jj];
                     if (fm == 0u) continue;
-                    float* cr = carry + ((size_t)(warp * MROWS + kk * MR2 + jj) * 2) * kPL + 2 * lane;
+                    float *cr, *zr, *prow;
+                    const float* rrow;
+                    row_ptrs(jj, cr, zr, rrow, prow);
                     float2 hp1 = *reinterpret_cast<const float2*>(cr);
                     float2 hp2 = *reinterpret_cast<const float2*>(cr + kPL);
-                    float* zr = pb + ((((size_t)warp * MR2 + jj) * 2) * T1) * kPL + 2 * lane;   // [2][T1][64]
-                    const float* rrow = rec + (size_t)((kk * MR2 + jj) * T1) * RF;
-                    float* prow = part + ((size_t)(warp * MROWS + kk * MR2 + jj) * T1) * NM;
 #pragma unroll
                     for (int i0 = 0; i0 < T1; i0 += 4) {
                         if (((fm >> i0) & 15u) == 0u) continue;
@@ -365,54 +546,8 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
                             const int i = i0 + c;
-                            if ((fm >> i) & 1u) {
-                                const float4* R = reinterpret_cast<const float4*>(rrow + i * RF);
-                                const float4 A = R[0], B = R[1], C = R[2], D = R[3];
-                                const float2 z1 = *reinterpret_cast<const float2*>(zr + (size_t)i * kPL);
-                                const float2 z2 = *reinterpret_cast<const float2*>(zr + ((size_t)T1 + i) * kPL);
-                                const float2 Rk = *reinterpret_cast<const float2*>(my_rtab + __float_as_int(B.w));
-                                float2 S = fma2(dup2(A.w), v3, fma2(dup2(A.z), v2, fma2(dup2(A.y), v1, dup2(A.x))));
-                                if constexpr (TAU) S = fma2(dup2(D.z), vq, S);   // nu tau (|v|^2 - 3/2)
-                                float2 t1 = fma2(dup2(C.x), hp1, fma2(dup2(C.y), hp2, dup2(B.x)));
-                                float2 t2 = fma2(dup2(C.z), rb1[i], fma2(dup2(C.w), rb2[i], dup2(B.y)));
-                                float2 t3 = fma2(dup2(D.x), z1, fma2(dup2(D.y), z2, dup2(B.z)));
-                                int4 Fa, Fb;
-                                if constexpr (SPEC) {   // + (1 - alpha) h'(x, reflected v) at walls
-                                    Fa = reinterpret_cast<const int4*>(R)[4];
-                                    Fb = reinterpret_cast<const int4*>(R)[5];
-                                    if (Fa.x >= 0) t1 = fma2(specP, *reinterpret_cast<const float2*>(fprev[0] + (size_t)Fa.x * fstride), t1);
-                                    if (Fa.y >= 0) t2 = fma2(specP, *reinterpret_cast<const float2*>(fprev[1] + (size_t)Fa.y * fstride), t2);
-                                    if (Fa.z >= 0) t3 = fma2(specP, *reinterpret_cast<const float2*>(fprev[2] + (size_t)Fa.z * fstride), t3);
-                                }
-                                // the x1 term (carried from the previous point) enters last: three
-                                // dependent operations per point along the x1 chain
-                                const float2 num = fma2(a1, t1, fma2(a3, t3, fma2(a2, t2, S)));
-                                const float2 h = mul2(num, Rk);
-                                if constexpr (SPEC) {   // molecules moving into a downstream face
-                                    if (Fa.w >= 0) *reinterpret_cast<float2*>(fnext[0] + (size_t)Fa.w * fstride) = h;
-                                    if (Fb.x >= 0) *reinterpret_cast<float2*>(fnext[1] + (size_t)Fb.x * fstride) = h;
-                                    if (Fb.y >= 0) *reinterpret_cast<float2*>(fnext[2] + (size_t)Fb.y * fstride) = h;
-                                }
-                                hp2 = hp1;
-                                hp1 = h;
-                                rb2[i] = rb1[i];
-                                rb1[i] = h;
-                                *reinterpret_cast<float2*>(zr + ((size_t)T1 + i) * kPL) = z1;
-                                *reinterpret_cast<float2*>(zr + (size_t)i * kPL) = h;
-                                const float2 p0 = mul2(W, h), p1 = mul2(Wv1, h), p2v = mul2(Wv2, h), p3v = mul2(Wv3, h);
-                                m0[c] = p0.x + p0.y;
-                                m1[c] = p1.x + p1.y;
-                                m2[c] = p2v.x + p2v.y;
-                                m3[c] = p3v.x + p3v.y;
-                                if constexpr (TAU) {
-                                    const float2 p4v = mul2(Wvv, h);
-                                    m4[c] = p4v.x + p4v.y;
-                                } else {
-                                    m4[c] = 0.f;
-                                }
-                            } else {
-                                m0[c] = m1[c] = m2[c] = m3[c] = m4[c] = 0.f;
-                            }
+                            if ((fm >> i) & 1u) point(rrow, zr, i, hp1, hp2, m0[c], m1[c], m2[c], m3[c], m4[c]);
+                            else m0[c] = m1[c] = m2[c] = m3[c] = m4[c] = 0.f;
                         }
                         const float r0 = reduce_scatter<float, 4>(m0, lane);
                         const float r1 = reduce_scatter<float, 4>(m1, lane);
@@ -499,6 +634,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                         PS::st(P->gx1, gxo + (row * 2 + 1) * NL + lv, *reinterpret_cast<const float2*>(cr + kPL), x1g1);
                     }
             }
+            if (t + 1 < ntiles) store_rec(t + 1, (t + 1) & 1, nxt);
             __syncthreads();
             if (threadIdx.x == 0 && it != a.withhold_item) {
                 publish_gpu(prog + p3 * np2 + p2, t + 1);
@@ -530,7 +666,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
 
 size_t sweep3d_f32x2_smem(int T1, int NW, int R2, int R3, int tau, int spec) {
     const size_t rows = (size_t)R2 * R3;
-    return sizeof(float) * (rows * T1 * (spec ? 24 : kRec) + (size_t)NW * rows * T1 * (tau ? 5 : 4) +
+    return sizeof(float) * (2 * rows * T1 * (spec ? 24 : kRec) + (size_t)NW * rows * T1 * (tau ? 5 : 4) +
                             (size_t)NW * rows * 2 * kPL + (size_t)NW * R2 * 2 * T1 * kPL + (size_t)NW * 2 * 2 * T1 * kPL +
                             (size_t)NW * 8 * kPL) +
            sizeof(unsigned) * 2 * rows;
