@@ -46,7 +46,7 @@ WORKLOADS = {
                 "32x32 Gauss-Hermite velocities, Kn {0.01,0.1,1,10} batched, FP32",
         # source 2 FMA, upwind 2 x (2 FMA) + 2 FMA, reciprocal 1 MUL, quadrature 3 MUL + 3 ADD
         "flops_per_update": 2 * 2 + 6 * 2 + 1 + 3 + 3,
-        "kernel": "dvm::sweep2d_f32x2_kernel",
+        "kernel": "dvm::sweep2d_f32x2_kernel<T1,0,0>",
         "l2": "working set per iteration > L2 (band edges and ghosts ~0.6 GB, moment partials 13 MB)",
     },
     "disc_batch_64": {
@@ -54,7 +54,7 @@ WORKLOADS = {
         "desc": "64 disc packings (seeds 1000+, sides 64-512, porosity 0.4-0.7, r 6-20, "
                 "Kn log-uniform [0.01,10]) batched, 24x24 Gauss-Hermite velocities, FP32",
         "flops_per_update": 2 * 2 + 6 * 2 + 1 + 3 + 3,
-        "kernel": "dvm::sweep2d_f32x2_kernel",
+        "kernel": "dvm::sweep2d_f32x2_kernel<T1,0,0>",
         "l2": "working set per iteration > L2 (band edges and ghosts of 64 problems ~2 GB)",
     },
     "rock_128": {
@@ -63,7 +63,7 @@ WORKLOADS = {
                 "16^3 Gauss-Hermite velocities, Kn 0.5, FP32",
         # source 3 FMA, upwind 3 x (2 FMA) + 3 FMA, reciprocal 1 MUL, quadrature 4 MUL + 4 ADD
         "flops_per_update": 3 * 2 + 9 * 2 + 1 + 4 + 4,
-        "kernel": "dvm::sweep3d_f32x2_kernel<T1,0>",
+        "kernel": "dvm::sweep3d_f32x2_kernel<T1,0,0,0,0>",
         "l2": "working set per iteration > L2 (pencil edges and ghosts ~6 GB)",
     },
 }
