@@ -59,7 +59,8 @@ using namespace dvm;
 
 namespace {
 
-constexpr int kFinBlock = 256;
+constexpr int kFinBlock2 = 1024;  // points per finalize block in 2D (256 threads x 4 points)
+constexpr int kFinBlock3 = 256;   // points per finalize block in 3D (one per thread)
 
 struct Buf {
     void* p;
@@ -435,7 +436,7 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         P.glat = (T*)dev_alloc(c, (size_t)2 * NQ * P.nslots * P.n1 * 2 * NL * sizeof(T));
         P.edge = (T*)dev_alloc(c, (size_t)NQ * 2 * P.nslots * P.n1 * 2 * NL * sizeof(T));
         T* lanec = (T*)dev_alloc(c, (size_t)NQ * NL * kLaneConsts * sizeof(T));
-        P.fin_nblocks = (int)((N + kFinBlock - 1) / kFinBlock);
+        P.fin_nblocks = (int)((N + kFinBlock2 - 1) / kFinBlock2);
         P.fin_block0 = (int)blk_prob.size();
         P.kpart = (double*)dev_alloc(c, (size_t)P.fin_nblocks * sizeof(double));
         P.kval = (double*)dev_alloc(c, 3 * sizeof(double));
@@ -515,7 +516,7 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         if (e != cudaSuccess) return cuda_fail(c, e, "sync");
         for (int k = 0; k < P.fin_nblocks; ++k) {
             blk_prob.push_back(b);
-            blk_start.push_back(k * kFinBlock);
+            blk_start.push_back(k * kFinBlock2);
         }
         c->prog_offset[b] = 1 + prog_total;
         prog_total += NQ * P.nbands;
@@ -845,7 +846,7 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         P.ey = (T*)dev_alloc(c, ey_sz * es);
         P.ez = (T*)dev_alloc(c, ez_sz * es);
         T* lanec = (T*)dev_alloc(c, (size_t)NO * NL * kLaneConsts3 * sizeof(T));
-        P.fin_nblocks = (int)((N + kFinBlock - 1) / kFinBlock);
+        P.fin_nblocks = (int)((N + kFinBlock3 - 1) / kFinBlock3);
         P.fin_block0 = (int)blk_prob.size();
         P.kpart = (double*)dev_alloc(c, (size_t)P.fin_nblocks * sizeof(double));
         P.kval = (double*)dev_alloc(c, 3 * sizeof(double));
@@ -900,7 +901,7 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         c->h2d_bytes += lc.size() * sizeof(T);
         for (int k = 0; k < P.fin_nblocks; ++k) {
             blk_prob.push_back(b);
-            blk_start.push_back(k * kFinBlock);
+            blk_start.push_back(k * kFinBlock3);
         }
         c->prog_offset[b] = 1 + prog_total;
         prog_total += NO * G * P.np3 * P.np2;

@@ -342,6 +342,11 @@ __device__ __forceinline__ double wall_density(const Prob2D<T>* P, int y, int j,
     return sigma * num * dinv[j];
 }
 
+// Points per finalize thread: a block of 256 threads covers 1024 consecutive points, thread t the
+// points t, t + 256, t + 512 and t + 768 of its block (coalesced), with all of their loads issued
+// before any store.
+constexpr int kFinPPT = 4;
+
 template <typename T>
 __global__ void __launch_bounds__(256) finalize2d_kernel(const FinArgs2D<T> a) {
     using V = typename Vec4<T>::type;
@@ -349,37 +354,58 @@ __global__ void __launch_bounds__(256) finalize2d_kernel(const FinArgs2D<T> a) {
     __shared__ int s_last;
     const int b = a.blk_prob[blockIdx.x];
     const Prob2D<T>* __restrict__ P = a.prob + b;
-    const int id = a.blk_start[blockIdx.x] + threadIdx.x;
+    const size_t N = P->N;
     double u1d = 0.0;
-    if (id < P->N) {
-        const uint16_t code = P->code[id];
+    int idk[kFinPPT];
+    uint16_t code[kFinPPT];
+    T pu[kFinPPT][4][3];     // quadrant partials (rho, u1, u2) of each point
+#pragma unroll
+    for (int k = 0; k < kFinPPT; ++k) {
+        idk[k] = a.blk_start[blockIdx.x] + threadIdx.x + k * 256;
+        code[k] = idk[k] < P->N ? P->code[idk[k]] : kSolidBit;
+    }
+#pragma unroll
+    for (int k = 0; k < kFinPPT; ++k)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+                pu[k][q][m] = (code[k] & kSolidBit) ? T(0) : P->P[((size_t)q * 3 + m) * N + idk[k]];
+#pragma unroll
+    for (int k = 0; k < kFinPPT; ++k) {
+        const int id = idk[k];
+        if (id >= P->N) continue;
         V s = Vec4<T>::make(0, 0, 0, 0), e = s;
-        if (!(code & kSolidBit)) {
-            const size_t N = P->N;
+        if (!(code[k] & kSolidBit)) {
             T rho = T(0), u1 = T(0), u2 = T(0);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                rho += P->P[((size_t)q * 3 + 0) * N + id];
-                u1 += P->P[((size_t)q * 3 + 1) * N + id];
-                u2 += P->P[((size_t)q * 3 + 2) * N + id];
+                rho += pu[k][q][0];
+                u1 += pu[k][q][1];
+                u2 += pu[k][q][2];
             }
             const T nu = (T)P->nu;
             s = Vec4<T>::make(nu * rho, T(2) * nu * u1 + T(1), T(2) * nu * u2, T(0));
-            u1d = (double)u1;
+            u1d += (double)u1;
             T ev[4];
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    const int c = (code >> (2 * (2 * j + u))) & 3;
+                    const int c = (code[k] >> (2 * (2 * j + u))) & 3;
                     const int sigma = u ? 1 : -1;
                     double val = 0.0;
                     if (c == 2) {
-                        // first-order stencil: wall value of face (x, j, sigma), shifted by the
-                        // source-form offset sigma dx on x1 faces
+                        // first-order stencil: wall value of face (x, j, sigma) (Eq. 6, rho'_s in
+                        // FP64 from the partials of u_j of the quadrants moving toward the wall:
+                        // sigma * sum / D), shifted by the source-form offset sigma dx on x1 faces
                         // (Eq. 5: alpha times the diffuse value, through the alpha-scaled
                         // denominators; the specular part is added per velocity by the sweep)
-                        val = wall_density(P, id, j, sigma, P->dinvw) + (j == 0 ? sigma * P->dx : 0.0);
+                        double num = 0.0;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (((q >> j) & 1) == (sigma < 0 ? 1 : 0)) num += (double)pu[k][q][1 + j];
+                        val = sigma * num * P->dinvw[j] + (j == 0 ? sigma * P->dx : 0.0);
                     }
                     // case 1 (only the second upstream point solid) is first order on the fluid
                     // neighbour: no wall term

@@ -339,7 +339,8 @@ def solve_to(mask, kn, v, w, tol, max_iter, initial=None, **options):
 def run_pipeline(train=48, side=64, eval_side=128, eval_seeds=(10000, 10001), eval_kns=(0.05, 0.5),
                  levels=4, base=16, steps=1500, lr=2e-3, nv=16, fp64_cap=0, seed=0, log=print, constant_lr=False):
     """The learned-warm-start experiment: solver runs on `train` seeded side^3 Gaussian-field rocks
-    (correlation length 8, porosity 0.35, Kn log-uniform in [0.05, 5], nv^3 velocities, FP32,
+    (correlation length 8, porosity 0.35, seeds 0, 1, ... without the non-percolating ones, Kn
+    log-uniform in [0.05, 5], nv^3 velocities, FP32,
     Err < 1e-6) give the training set; the network is trained with Adam; held-out eval_side^3 rocks
     (seeds eval_seeds) are then solved from the plain start and from the network's prediction (same
     precision, FP32; the warm time includes features, inference and dvm_set_initial) and, when
@@ -353,9 +354,15 @@ def run_pipeline(train=48, side=64, eval_side=128, eval_seeds=(10000, 10001), ev
     rng = np.random.default_rng(seed)
     data = []
     t0 = time.perf_counter()
-    for i in range(train):
+    rock_seed = 0
+    while len(data) < train:
+        # seeds whose field has no percolating pore space (all solid after the cluster filter) are
+        # skipped
+        mask = inputs.gaussian_rock(side, seed=rock_seed, corr_len=8.0, porosity=0.35)
+        rock_seed += 1
+        if mask.all():
+            continue
         kn = float(10 ** rng.uniform(math.log10(0.05), math.log10(5.0)))
-        mask = inputs.gaussian_rock(side, seed=i, corr_len=8.0, porosity=0.35)
         it, dt, k, rho, u, st = solve_to(mask, kn, v, w, 1e-6, 5000, **opts)
         data.append((torch.from_numpy(features(mask, kn)).cuda(), torch.from_numpy(targets(mask, kn, rho, u)).cuda(),
                      torch.from_numpy((~mask).astype(np.float32).ravel()).cuda()))
