@@ -44,6 +44,7 @@ class _Cfg(ctypes.Structure):
         ("dec", ctypes.c_int * 3),
         ("tau", ctypes.c_int),
         ("alpha", ctypes.c_double),
+        ("shakhov_pr", ctypes.c_double),
     ]
 
 
@@ -73,7 +74,7 @@ def _load():
             lib.ora_iter.argtypes = [ctypes.c_void_p]
             for f in ("ora_get_moments",):
                 getattr(lib, f).argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
-            for f in ("ora_get_wall", "ora_get_flux", "ora_get_tau"):
+            for f in ("ora_get_wall", "ora_get_flux", "ora_get_tau", "ora_get_q"):
                 getattr(lib, f).argtypes = [ctypes.c_void_p, ctypes.c_void_p]
             lib.ora_set_uniform.argtypes = [ctypes.c_void_p, ctypes.c_double]
             lib.ora_set_initial.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
@@ -99,10 +100,13 @@ class Oracle:
     paper drops it for its isothermal flows).
     alpha: tangential momentum accommodation coefficient of the Maxwell wall condition (Eq. 5);
     1 (fully diffuse) is the paper's setting.
+    shakhov_pr: 0 for the BGK model (the paper's); a Prandtl number > 0 selects the linearised
+    Shakhov model, whose source adds (4/5)(1 - Pr) q.v (|v|^2 - 5/2) with the heat flux
+    q = sum W v (|v|^2 - 5/2) h (needs tau).
     """
 
     def __init__(self, solid, kn, v, w, *, jump=1.0, order=2, lateral="specular", form="jump",
-                 traversal="raster", decomposition=(1, 1, 1), threads=0, tau=False, alpha=1.0):
+                 traversal="raster", decomposition=(1, 1, 1), threads=0, tau=False, alpha=1.0, shakhov_pr=0.0):
         lib = _load()
         solid = np.ascontiguousarray(np.asarray(solid).astype(np.uint8))
         if solid.ndim not in (2, 3):
@@ -134,6 +138,7 @@ class Oracle:
             cfg.dec[j] = int(dec[j])
         cfg.tau = 1 if tau else 0
         cfg.alpha = float(alpha)
+        cfg.shakhov_pr = float(shakhov_pr)
         self._cfg = cfg
         self._h = lib.ora_create(ctypes.byref(cfg))
         if not self._h:
@@ -193,6 +198,12 @@ class Oracle:
         out = np.zeros(self.solid.size)
         self._lib.ora_get_tau(self._h, _ptr(out))
         return out.reshape(self.shape)
+
+    def heat_flux(self):
+        """Heat flux q [dims, *shape] of the Shakhov option (zero otherwise; solid = 0)."""
+        out = np.zeros(self.solid.size * self.dims)
+        self._lib.ora_get_q(self._h, _ptr(out))
+        return out.reshape((self.dims,) + self.shape)
 
     def flux(self):
         """x1 face fluxes sum_{cross-section} sum_k W_k v1 h_upwind of the last iteration [n1]."""

@@ -19,6 +19,9 @@
  *   (iii) moments rho, u (Eq. 4) and wall densities (Eq. 6); the temperature tau of Eq. 4 and its
  *         source term tau (|v|^2 - 3/2) in Eq. 2 / Eq. 10 are dropped as in Sec. 4 unless the tau
  *         option is set (3D only: Eq. 2 and Eq. 4 are written for three velocity components);
+ *         with the Shakhov option the source also carries the heat-flux term of the linearised
+ *         S model, (4/5)(1 - Pr) q.v (|v|^2 - 5/2) with q = sum W v (|v|^2 - 5/2) h (an
+ *         extension the paper names in Sec. 1 and Sec. 6 without writing it out; it needs tau);
  *   (iv)  permeability k = (2/sqrt(pi)) Kn G_p (Eq. 11-12);
  *   (v)   Err of Eq. 15 is formed by the caller from the k history.
  * Moments, wall densities and all boundary (ghost) data used in a sweep are those of the previous
@@ -80,6 +83,7 @@ typedef struct {
     int dec[3];            /* subdomain counts c1, c2, c3 of the lagged-halo decomposition */
     int tau;               /* 1: keep the temperature term of Eq. 2 (3D only); 0: drop it (Sec. 4) */
     double alpha;          /* tangential momentum accommodation coefficient of Eq. 5 (1: diffuse) */
+    double shakhov_pr;     /* 0: BGK; > 0: linearised Shakhov model with this Prandtl number */
 } ora_cfg;
 
 typedef struct {
@@ -93,6 +97,9 @@ typedef struct {
     double *rho, *u;       /* [N], [d][N] (stored in the working form's variables) */
     double* tau;           /* [N] temperature of Eq. 4 (the same in both forms), with the tau option */
     double sw2;            /* sum_k W_k |v_k|^2 (3/2 when the rule integrates v^2 exactly) */
+    double* q;             /* [3][N] heat flux sum W v (|v|^2 - 5/2) h (paper's variables), Shakhov */
+    double sq[3];          /* sum_k W_k v_jk (|v_k|^2 - 5/2) (0 on a symmetric grid, up to rounding) */
+    double shk;            /* Shakhov coefficient (4/5)(1 - Pr), 0 for BGK */
     double* rhos;          /* [d][2][N] wall density of face (x, j, side) ; side 0: -1, 1: +1 */
     int area[3];           /* transverse face area per axis */
     double* lag[2];        /* [nv][d][2 layers][area] lagged ghost values, current / next */
@@ -197,6 +204,11 @@ static void point_update(const ora* o, int k, const int c[3], double* h) {
         double vv = 0.0;
         for (int j = 0; j < o->d; ++j) vv += vk[j] * vk[j];
         num += o->nu * o->tau[id] * (vv - 1.5);
+        if (o->c.shakhov_pr > 0.0) {
+            double qv = 0.0;
+            for (int j = 0; j < o->d; ++j) qv += o->q[(size_t)j * o->N + id] * vk[j];
+            num += o->nu * o->shk * qv * (vv - 2.5);
+        }
     }
     if (o->c.form == 1) num += o->J * vk[0];
     double den = o->nu;
@@ -299,6 +311,7 @@ static void init_state(ora* o) {
     size_t N = o->N;
     memset(o->u, 0, sizeof(double) * N * o->d);
     memset(o->tau, 0, sizeof(double) * N);   /* tau of h = 0 */
+    memset(o->q, 0, sizeof(double) * 3 * N);  /* heat flux of h = 0 */
     for (int id = 0; id < o->N; ++id) {
         int i1 = id % o->n1;
         double x1 = (o->c.form == 1) ? o->J * i1 * o->dx : 0.0;
@@ -345,6 +358,7 @@ ora* ora_create(const ora_cfg* cfg) {
     if (!cfg || (cfg->dims != 2 && cfg->dims != 3) || cfg->nv <= 0 || cfg->kn <= 0) return NULL;
     if (!(cfg->alpha >= 0.0 && cfg->alpha <= 1.0)) return NULL;
     if (cfg->tau && cfg->dims != 3) return NULL;
+    if (cfg->shakhov_pr < 0.0 || (cfg->shakhov_pr > 0.0 && !cfg->tau)) return NULL;
     ora* o = (ora*)calloc(1, sizeof(ora));
     o->c = *cfg;
     o->d = cfg->dims;
@@ -368,6 +382,16 @@ ora* ora_create(const ora_cfg* cfg) {
     o->sw2 = 0.0;
     for (int k = 0; k < o->nv; ++k)
         for (int j = 0; j < o->d; ++j) o->sw2 += o->w[k] * o->v[(size_t)k * o->d + j] * o->v[(size_t)k * o->d + j];
+    /* S model: the heat-flux moment of the extra term, sum W v_i (|v|^2 - 5/2) A q.v (|v|^2 - 5/2),
+     * is A (5/4) q_i for an exact rule, so q relaxes at the rate nu (1 - 5 A / 4) = Pr nu when
+     * A = (4/5)(1 - Pr) */
+    o->shk = cfg->shakhov_pr > 0.0 ? 0.8 * (1.0 - cfg->shakhov_pr) : 0.0;
+    for (int j = 0; j < 3; ++j) o->sq[j] = 0.0;
+    for (int k = 0; k < o->nv; ++k) {
+        double vv = 0.0;
+        for (int j = 0; j < o->d; ++j) vv += o->v[(size_t)k * o->d + j] * o->v[(size_t)k * o->d + j];
+        for (int j = 0; j < o->d; ++j) o->sq[j] += o->w[k] * o->v[(size_t)k * o->d + j] * (vv - 2.5);
+    }
     o->refl = (int*)malloc(sizeof(int) * 3 * o->nv);
     for (int j = 0; j < 3; ++j)
         for (int k = 0; k < o->nv; ++k) {
@@ -396,6 +420,7 @@ ora* ora_create(const ora_cfg* cfg) {
     o->rho = (double*)calloc(o->N, sizeof(double));
     o->u = (double*)calloc((size_t)o->N * o->d, sizeof(double));
     o->tau = (double*)calloc(o->N, sizeof(double));
+    o->q = (double*)calloc((size_t)3 * o->N, sizeof(double));
     o->rhos = (double*)calloc((size_t)o->N * o->d * 2, sizeof(double));
     o->area[0] = o->n2 * o->n3;
     o->area[1] = o->n1 * o->n3;
@@ -439,7 +464,7 @@ ora* ora_create(const ora_cfg* cfg) {
 void ora_destroy(ora* o) {
     if (!o) return;
     free(o->solid); free(o->v); free(o->w); free(o->refl);
-    free(o->rho); free(o->u); free(o->tau); free(o->rhos);
+    free(o->rho); free(o->u); free(o->tau); free(o->q); free(o->rhos);
     free(o->lag[0]); free(o->lag[1]);
     free(o->full[0]); free(o->full[1]);
     for (int j = 0; j < 3; ++j) free(o->sub[j]);
@@ -479,6 +504,16 @@ static void update_tau(ora* o, const double* e) {
     }
 }
 
+/* q_j = sum W v_j (|v|^2 - 5/2) h from the working-variable sum qn; in the source form
+ * h' = h + J x1, so q_j = qn_j - J x1 sq_j: the paper's q in either form. */
+static void update_q(ora* o, const double* qn) {
+    for (int j = 0; j < o->d; ++j)
+        for (int id = 0; id < o->N; ++id) {
+            double x1 = (o->c.form == 1) ? o->J * (id % o->n1) * o->dx : 0.0;
+            o->q[(size_t)j * o->N + id] = o->solid[id] ? 0.0 : qn[(size_t)j * o->N + id] - x1 * o->sq[j];
+        }
+}
+
 static void iterate_once(ora* o) {
     const size_t N = o->N;
     const int d = o->d;
@@ -486,6 +521,7 @@ static void iterate_once(ora* o) {
     double* u_n = (double*)calloc(N * d, sizeof(double));
     double* num_n = (double*)calloc(N * d * 2, sizeof(double));
     double* e_n = (double*)calloc(N, sizeof(double));          /* sum W |v|^2 h (tau option) */
+    double* q_n = (double*)calloc(N * 3, sizeof(double));      /* heat-flux sums (Shakhov) */
     memset(o->flux, 0, sizeof(double) * o->n1);
     for (int g0 = 0; g0 < o->nv; g0 += ORA_GROUP) {
         int gn = o->nv - g0 < ORA_GROUP ? o->nv - g0 : ORA_GROUP;
@@ -510,6 +546,8 @@ static void iterate_once(ora* o) {
                     double vv = 0.0;
                     for (int j = 0; j < d; ++j) vv += o->v[(size_t)k * d + j] * o->v[(size_t)k * d + j];
                     e_n[id] += wk * vv * hk;
+                    if (o->c.shakhov_pr > 0.0)
+                        for (int j = 0; j < d; ++j) q_n[(size_t)j * N + id] += wk * o->v[(size_t)k * d + j] * (vv - 2.5) * hk;
                 }
                 for (int j = 0; j < d; ++j) {
                     double vj = o->v[(size_t)k * d + j];
@@ -548,9 +586,10 @@ static void iterate_once(ora* o) {
     memcpy(o->rho, rho_n, sizeof(double) * N);
     memcpy(o->u, u_n, sizeof(double) * N * d);
     if (o->c.tau) update_tau(o, e_n);
+    if (o->c.shakhov_pr > 0.0) update_q(o, q_n);
     double* t = o->lag[0]; o->lag[0] = o->lag[1]; o->lag[1] = t;
     if (o->keep_full) { t = o->full[0]; o->full[0] = o->full[1]; o->full[1] = t; }
-    free(rho_n); free(u_n); free(num_n); free(e_n);
+    free(rho_n); free(u_n); free(num_n); free(e_n); free(q_n);
     o->iter++;
 }
 
@@ -600,6 +639,9 @@ void ora_get_flux(const ora* o, double* flux) { memcpy(flux, o->flux, sizeof(dou
 /* Temperature tau of Eq. 4 [N] (zero without the tau option and at solid points). */
 void ora_get_tau(const ora* o, double* tau) { memcpy(tau, o->tau, sizeof(double) * o->N); }
 
+/* Heat flux q [d][N] of the Shakhov option (zero otherwise and at solid points). */
+void ora_get_q(const ora* o, double* q) { memcpy(q, o->q, sizeof(double) * o->N * o->d); }
+
 /* Overwrite the state with a uniform value c in the working variables (jump = 0 tests). */
 void ora_set_uniform(ora* o, double c) {
     for (int id = 0; id < o->N; ++id) {
@@ -610,6 +652,9 @@ void ora_set_uniform(ora* o, double c) {
                 o->rhos[((size_t)j * 2 + sd) * o->N + id] = (o->facemask[id] >> (2 * j + sd) & 1) ? c : 0.0;
     }
     for (int id = 0; id < o->N; ++id) o->tau[id] = o->solid[id] ? 0.0 : c * (2.0 / 3.0 * o->sw2 - 1.0);
+    if (o->c.shakhov_pr > 0.0)
+        for (int j = 0; j < o->d; ++j)
+            for (int id = 0; id < o->N; ++id) o->q[(size_t)j * o->N + id] = o->solid[id] ? 0.0 : c * o->sq[j];
     size_t lagsz = (size_t)o->nv * o->d * 2 * o->area[0];
     for (size_t i = 0; i < lagsz; ++i) o->lag[0][i] = c;
     if (o->keep_full)
@@ -632,6 +677,7 @@ void ora_set_initial(ora* o, const double* rho0, const double* u0) {
     double* u_n = (double*)calloc(N * d, sizeof(double));
     double* num_n = (double*)calloc(N * d * 2, sizeof(double));
     double* e_n = (double*)calloc(N, sizeof(double));
+    double* q_n = (double*)calloc(N * 3, sizeof(double));
     for (int k = 0; k < o->nv; ++k) {
         const double* vk = o->v + (size_t)k * d;
         double vv = 0.0;
@@ -650,6 +696,7 @@ void ora_set_initial(ora* o, const double* rho0, const double* u0) {
             double wk = o->w[k];
             rho_n[id] += wk * h[id];
             e_n[id] += wk * vv * h[id];
+            for (int j = 0; j < d; ++j) q_n[(size_t)j * N + id] += wk * vk[j] * (vv - 2.5) * h[id];
             for (int j = 0; j < d; ++j) u_n[(size_t)j * N + id] += wk * vk[j] * h[id];
             for (int j = 0; j < d; ++j)
                 for (int sd = 0; sd < 2; ++sd) {
@@ -666,9 +713,10 @@ void ora_set_initial(ora* o, const double* rho0, const double* u0) {
     memcpy(o->rho, rho_n, sizeof(double) * N);
     memcpy(o->u, u_n, sizeof(double) * N * d);
     if (o->c.tau) update_tau(o, e_n);
+    if (o->c.shakhov_pr > 0.0) update_q(o, q_n);
     double* t = o->lag[0]; o->lag[0] = o->lag[1]; o->lag[1] = t;
     if (o->keep_full) { t = o->full[0]; o->full[0] = o->full[1]; o->full[1] = t; }
-    free(h); free(rho_n); free(u_n); free(num_n); free(e_n);
+    free(h); free(rho_n); free(u_n); free(num_n); free(e_n); free(q_n);
 }
 
 /* One sweep of velocity k from the current state, without updating the state (point-update

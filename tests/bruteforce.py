@@ -20,11 +20,14 @@ import math
 import numpy as np
 
 
-def solve_dense(solid, kn, v, w, jump=1.0, order=2, lateral="specular", tau=False, alpha=1.0):
+def solve_dense(solid, kn, v, w, jump=1.0, order=2, lateral="specular", tau=False, alpha=1.0, shakhov_pr=0.0):
     """tau: keep the temperature term tau (|v|^2 - 3/2) of Eq. 2 with tau = (2/3) sum W |v|^2 h - rho
     (Eq. 4), a linear functional of the unknowns at the same point like rho and u.
     alpha: Maxwell accommodation of Eq. 5; the wall value of velocity k is alpha rho_s + (1 - alpha)
-    h(x_f, reflected k) with h at the wall's fluid point x_f (lagged, like rho_s)."""
+    h(x_f, reflected k) with h at the wall's fluid point x_f (lagged, like rho_s).
+    shakhov_pr > 0 (with tau): linearised Shakhov model, the source adds
+    (4/5)(1 - Pr) q.v_k (|v_k|^2 - 5/2) with q = sum W v (|v|^2 - 5/2) h at the same point."""
+    assert shakhov_pr == 0.0 or tau
     solid = np.asarray(solid, dtype=bool)
     dims = solid.ndim
     shape = solid.shape
@@ -114,6 +117,10 @@ def solve_dense(solid, kn, v, w, jump=1.0, order=2, lateral="specular", tau=Fals
                 cv = nu * w[kk] * (1.0 + 2.0 * float(np.dot(v[kk], v[k])))
                 if tau:
                     cv += nu * w[kk] * (2.0 / 3.0 * float(np.dot(v[kk], v[kk])) - 1.0) * (vk2 - 1.5)
+                if shakhov_pr > 0.0:
+                    vkk2 = float(np.dot(v[kk], v[kk]))
+                    cv += (nu * 0.8 * (1.0 - shakhov_pr) * w[kk] * float(np.dot(v[kk], v[k]))
+                           * (vkk2 - 2.5) * (vk2 - 2.5))
                 A[row, col(f, kk)] -= cv
                 lag1[row] -= cv
             diag = nu
@@ -150,14 +157,18 @@ def solve_dense(solid, kn, v, w, jump=1.0, order=2, lateral="specular", tau=Fals
     rho = np.zeros(shape)
     u = np.zeros((dims,) + shape)
     temp = np.zeros(shape)
+    heat = np.zeros((dims,) + shape)
     vv = (v * v).sum(axis=1)
     for f, c in enumerate(fluid_coords):
         rho[arr_index(c)] = float(np.dot(w, H[f]))
         temp[arr_index(c)] = 2.0 / 3.0 * float(np.dot(w * vv, H[f])) - rho[arr_index(c)]
         for j in range(dims):
             u[(j,) + arr_index(c)] = float(np.dot(w * v[:, j], H[f]))
+            heat[(j,) + arr_index(c)] = float(np.dot(w * v[:, j] * (vv - 2.5), H[f]))
     k_perm = 2.0 / math.sqrt(math.pi) * kn * float(u[0].sum() / u[0].size)
     resid = float(np.abs(A[:U] @ sol - b[:U]).max())
+    if shakhov_pr > 0.0:
+        return rho, u, k_perm, resid, delta, temp, heat
     if tau:
         return rho, u, k_perm, resid, delta, temp
     return rho, u, k_perm, resid, delta
