@@ -125,6 +125,14 @@ typedef struct {
      * diffuse, the paper's setting (alpha = 1).  Values outside [0, 1], BF16 storage and band
      * pairs reject it with DVM_EINVAL. */
     double specular_fraction;
+    /* 0 (default): the BGK model of Eq. 2, the paper's.  A Prandtl number Pr > 0 selects the
+     * linearised Shakhov (S) model, which the paper names as an extension of its solver (Sec. 1,
+     * Sec. 6): the source also carries (4/5)(1 - Pr) q.v (|v|^2 - 5/2) with the heat flux
+     * q = sum_k W_k v_k (|v_k|^2 - 5/2) h (the coefficient for which q relaxes at Pr times the
+     * collision frequency).  3D with temperature_term only; it runs on the one-velocity-per-lane
+     * sweep kernel in FP32 too.  Negative or non-finite values, 2D, no temperature term,
+     * subdomains, specular_fraction > 0 or BF16 storage: DVM_EINVAL. */
+    double shakhov_prandtl;
 } dvm_options;
 
 /* Fill *opt with the defaults: FP64, second order, specular lateral faces, check interval 100,
@@ -177,6 +185,11 @@ dvm_status dvm_moments_at(dvm_ctx* ctx, int prob, double* rho, double* u, int on
  * points 0), with the temperature term enabled (dvm_options.temperature_term); on_device != 0 means
  * tau is a device pointer.  EINVAL when the term is off. */
 dvm_status dvm_temperature_at(dvm_ctx* ctx, int prob, double* tau, int on_device);
+
+/* Heat flux q = sum_k W_k v_k (|v_k|^2 - 5/2) h of problem prob after the last iteration, [3][N]
+ * doubles (solid points 0), with the Shakhov model enabled (dvm_options.shakhov_prandtl > 0);
+ * on_device != 0 means q is a device pointer.  EINVAL when the model is off. */
+dvm_status dvm_heat_flux_at(dvm_ctx* ctx, int prob, double* q, int on_device);
 
 /* Permeability k = (2/sqrt(pi)) Kn G_p (Eq. 11) and G_p, the mean of u1 over all points (Eq. 12:
  * the cross-section mean, averaged over every x1 cross-section), of the last iteration. */

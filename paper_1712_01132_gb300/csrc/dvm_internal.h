@@ -131,6 +131,13 @@ struct Prob3D {
     double sw2;             // sum over the grid of W |v|^2 (3/2 for a rule exact on v^2)
     T* Pt;                  // [8][G][N] partials of sum W |v|^2 h' (with tau)
     T* srct;                // [N] nu tau of the last iteration, read by the sweep (with tau)
+    // linearised Shakhov model (with tau): the source adds A q.v (|v|^2 - 5/2), A = (4/5)(1 - Pr),
+    // q = sum W v (|v|^2 - 5/2) h
+    int shk;                // 1: Shakhov model
+    double shkA;            // A
+    double sq[3];           // sum over the grid of W v_j (|v|^2 - 5/2): q' = q + x1 sq_j
+    T* Pq;                  // [8][G][3][N] partials of sum W v_j (|v|^2 - 5/2) h' (Shakhov)
+    T* srcq;                // [N][4] nu A q_j of the last iteration, read by the sweep (Shakhov)
     // Maxwell walls with alpha < 1 (Eq. 5), as in Prob2D: spec = 1 - alpha; faces are (fluid
     // point, axis j, side u) with a solid neighbour at x + (2u - 1) e_j
     double spec;
@@ -174,7 +181,9 @@ struct Prob3D {
     unsigned int* fin_counter;
 };
 
-constexpr int kLaneConsts3 = 20;    // v1 v2 v3 a1 a2 a3 W Wv1 Wv2 Wv3 R[8] |v|^2-3/2 W|v|^2
+// v1 v2 v3 a1 a2 a3 W Wv1 Wv2 Wv3 R[8] |v|^2-3/2 W|v|^2, then (Shakhov) g_j = v_j (|v|^2 - 5/2)
+// and W g_j
+constexpr int kLaneConsts3 = 26;
 
 struct SweepItem3 { int prob, oct, p2, p3, group, pad0, pad1, pad2; };
 
@@ -190,6 +199,7 @@ struct SweepArgs3D {
     int bf16;                   // ghosts and pencil edges stored as BF16 (see Prob3D::bf16)
     int sub;                    // lagged-halo subdomains: pencils and tiles from the Prob3D tables
     int tau;                    // temperature term (Prob3D::tau)
+    int shk;                    // Shakhov model (Prob3D::shk; scalar kernel only)
     int spec;                   // specular wall parts (Prob3D::spec > 0)
     int parity;
     int* ticket;

@@ -50,6 +50,7 @@ class dvm_options(ctypes.Structure):
         ("group_warps", ctypes.c_int),
         ("temperature_term", ctypes.c_int),
         ("specular_fraction", ctypes.c_double),
+        ("shakhov_prandtl", ctypes.c_double),
     ]
 
 
@@ -70,6 +71,7 @@ _SIGNATURES = [
     ("dvm_moments", ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     ("dvm_moments_at", ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int]),
     ("dvm_temperature_at", ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int]),
+    ("dvm_heat_flux_at", ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int]),
     ("dvm_permeability", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("dvm_permeability_at", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_double)]),
@@ -207,7 +209,8 @@ class _TorchAllocator:
 
 def make_options(precision="fp64", stencil_order=2, lateral="specular", check_interval=100, stream=None,
                  tile_x1=0, band_rows=0, torch_memory=True, use_graph=False, subdomains=(1, 1, 1),
-                 band_pairs=False, group_warps=0, temperature_term=False, specular_fraction=0.0):
+                 band_pairs=False, group_warps=0, temperature_term=False, specular_fraction=0.0,
+                 shakhov_prandtl=0.0):
     """dvm_options with torch's current stream (unless stream is given) and, by default, torch's
     caching allocator for device memory.  Returns (options, keepalive)."""
     o = dvm_default_options()
@@ -222,6 +225,7 @@ def make_options(precision="fp64", stencil_order=2, lateral="specular", check_in
     o.group_warps = int(group_warps)
     o.temperature_term = 1 if temperature_term else 0
     o.specular_fraction = float(specular_fraction)
+    o.shakhov_prandtl = float(shakhov_prandtl)
     for j in range(3):
         o.subdomains[j] = int(subdomains[j])
     keep = []
@@ -343,6 +347,13 @@ class Solver:
         tau = np.zeros(m.size)
         _check(self._lib.dvm_temperature_at(self._ctx, int(prob), _ptr(tau), 0), self._ctx)
         return tau.reshape(m.shape)
+
+    def heat_flux(self, prob=0):
+        """Heat flux q = sum W v (|v|^2 - 5/2) h [3, *shape] of problem prob; needs shakhov_prandtl > 0."""
+        m = self.masks[prob]
+        q = np.zeros(3 * m.size)
+        _check(self._lib.dvm_heat_flux_at(self._ctx, int(prob), _ptr(q), 0), self._ctx)
+        return q.reshape((3,) + m.shape)
 
     def moments_device(self, prob, rho_ptr, u_ptr):
         _check(self._lib.dvm_moments_at(self._ctx, int(prob), ctypes.c_void_p(rho_ptr), ctypes.c_void_p(u_ptr), 1),
