@@ -45,6 +45,7 @@ class _Cfg(ctypes.Structure):
         ("tau", ctypes.c_int),
         ("alpha", ctypes.c_double),
         ("shakhov_pr", ctypes.c_double),
+        ("es_pr", ctypes.c_double),
     ]
 
 
@@ -74,7 +75,7 @@ def _load():
             lib.ora_iter.argtypes = [ctypes.c_void_p]
             for f in ("ora_get_moments",):
                 getattr(lib, f).argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
-            for f in ("ora_get_wall", "ora_get_flux", "ora_get_tau", "ora_get_q"):
+            for f in ("ora_get_wall", "ora_get_flux", "ora_get_tau", "ora_get_q", "ora_get_pi"):
                 getattr(lib, f).argtypes = [ctypes.c_void_p, ctypes.c_void_p]
             lib.ora_set_uniform.argtypes = [ctypes.c_void_p, ctypes.c_double]
             lib.ora_set_initial.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
@@ -103,10 +104,14 @@ class Oracle:
     shakhov_pr: 0 for the BGK model (the paper's); a Prandtl number > 0 selects the linearised
     Shakhov model, whose source adds (4/5)(1 - Pr) q.v (|v|^2 - 5/2) with the heat flux
     q = sum W v (|v|^2 - 5/2) h (needs tau).
+    es_pr: 0 for the BGK model; a Prandtl number > 0 selects the linearised ES-BGK model: collision
+    frequency Pr nu and the source adds (1 - 1/Pr) sum_ij P_ij v_i v_j with the traceless stress
+    P_ij = 2 sum W (v_i v_j - delta_ij |v|^2 / 3) h (needs tau; not with shakhov_pr).
     """
 
     def __init__(self, solid, kn, v, w, *, jump=1.0, order=2, lateral="specular", form="jump",
-                 traversal="raster", decomposition=(1, 1, 1), threads=0, tau=False, alpha=1.0, shakhov_pr=0.0):
+                 traversal="raster", decomposition=(1, 1, 1), threads=0, tau=False, alpha=1.0, shakhov_pr=0.0,
+                 es_pr=0.0):
         lib = _load()
         solid = np.ascontiguousarray(np.asarray(solid).astype(np.uint8))
         if solid.ndim not in (2, 3):
@@ -139,6 +144,7 @@ class Oracle:
         cfg.tau = 1 if tau else 0
         cfg.alpha = float(alpha)
         cfg.shakhov_pr = float(shakhov_pr)
+        cfg.es_pr = float(es_pr)
         self._cfg = cfg
         self._h = lib.ora_create(ctypes.byref(cfg))
         if not self._h:
@@ -204,6 +210,12 @@ class Oracle:
         out = np.zeros(self.solid.size * self.dims)
         self._lib.ora_get_q(self._h, _ptr(out))
         return out.reshape((self.dims,) + self.shape)
+
+    def stress(self):
+        """Traceless stress [6, *shape] (components 11 22 33 12 13 23) of the ES option."""
+        out = np.zeros(self.solid.size * 6)
+        self._lib.ora_get_pi(self._h, _ptr(out))
+        return out.reshape((6,) + self.shape)
 
     def flux(self):
         """x1 face fluxes sum_{cross-section} sum_k W_k v1 h_upwind of the last iteration [n1]."""

@@ -22,6 +22,9 @@
  *         with the Shakhov option the source also carries the heat-flux term of the linearised
  *         S model, (4/5)(1 - Pr) q.v (|v|^2 - 5/2) with q = sum W v (|v|^2 - 5/2) h (an
  *         extension the paper names in Sec. 1 and Sec. 6 without writing it out; it needs tau);
+ *         with the ES option (the ellipsoidal-statistical BGK model, named in the same places)
+ *         the collision frequency becomes Pr nu and the source carries (1 - 1/Pr) sum_ij P_ij
+ *         v_i v_j with the traceless stress P_ij = 2 sum W (v_i v_j - delta_ij |v|^2 / 3) h;
  *   (iv)  permeability k = (2/sqrt(pi)) Kn G_p (Eq. 11-12);
  *   (v)   Err of Eq. 15 is formed by the caller from the k history.
  * Moments, wall densities and all boundary (ghost) data used in a sweep are those of the previous
@@ -84,6 +87,7 @@ typedef struct {
     int tau;               /* 1: keep the temperature term of Eq. 2 (3D only); 0: drop it (Sec. 4) */
     double alpha;          /* tangential momentum accommodation coefficient of Eq. 5 (1: diffuse) */
     double shakhov_pr;     /* 0: BGK; > 0: linearised Shakhov model with this Prandtl number */
+    double es_pr;          /* 0: BGK; > 0: linearised ES-BGK model with this Prandtl number */
 } ora_cfg;
 
 typedef struct {
@@ -100,6 +104,9 @@ typedef struct {
     double* q;             /* [3][N] heat flux sum W v (|v|^2 - 5/2) h (paper's variables), Shakhov */
     double sq[3];          /* sum_k W_k v_jk (|v_k|^2 - 5/2) (0 on a symmetric grid, up to rounding) */
     double shk;            /* Shakhov coefficient (4/5)(1 - Pr), 0 for BGK */
+    double* pi;            /* [6][N] traceless stress, components 11 22 33 12 13 23 (ES model) */
+    double spi[6];         /* sum_k 2 W_k (v_i v_j - delta_ij |v|^2 / 3) (0 for an isotropic rule) */
+    double esb;            /* ES coefficient 1 - 1/Pr, 0 for BGK */
     double* rhos;          /* [d][2][N] wall density of face (x, j, side) ; side 0: -1, 1: +1 */
     int area[3];           /* transverse face area per axis */
     double* lag[2];        /* [nv][d][2 layers][area] lagged ghost values, current / next */
@@ -209,6 +216,13 @@ static void point_update(const ora* o, int k, const int c[3], double* h) {
             for (int j = 0; j < o->d; ++j) qv += o->q[(size_t)j * o->N + id] * vk[j];
             num += o->nu * o->shk * qv * (vv - 2.5);
         }
+        if (o->c.es_pr > 0.0) {
+            const double* P = o->pi;
+            const size_t Nn = o->N;
+            double pv = P[0 * Nn + id] * vk[0] * vk[0] + P[1 * Nn + id] * vk[1] * vk[1] + P[2 * Nn + id] * vk[2] * vk[2] +
+                        2.0 * (P[3 * Nn + id] * vk[0] * vk[1] + P[4 * Nn + id] * vk[0] * vk[2] + P[5 * Nn + id] * vk[1] * vk[2]);
+            num += o->nu * o->esb * pv;
+        }
     }
     if (o->c.form == 1) num += o->J * vk[0];
     double den = o->nu;
@@ -312,6 +326,7 @@ static void init_state(ora* o) {
     memset(o->u, 0, sizeof(double) * N * o->d);
     memset(o->tau, 0, sizeof(double) * N);   /* tau of h = 0 */
     memset(o->q, 0, sizeof(double) * 3 * N);  /* heat flux of h = 0 */
+    memset(o->pi, 0, sizeof(double) * 6 * N); /* stress of h = 0 */
     for (int id = 0; id < o->N; ++id) {
         int i1 = id % o->n1;
         double x1 = (o->c.form == 1) ? o->J * i1 * o->dx : 0.0;
@@ -359,6 +374,7 @@ ora* ora_create(const ora_cfg* cfg) {
     if (!(cfg->alpha >= 0.0 && cfg->alpha <= 1.0)) return NULL;
     if (cfg->tau && cfg->dims != 3) return NULL;
     if (cfg->shakhov_pr < 0.0 || (cfg->shakhov_pr > 0.0 && !cfg->tau)) return NULL;
+    if (cfg->es_pr < 0.0 || (cfg->es_pr > 0.0 && (!cfg->tau || cfg->shakhov_pr > 0.0))) return NULL;
     ora* o = (ora*)calloc(1, sizeof(ora));
     o->c = *cfg;
     o->d = cfg->dims;
@@ -377,6 +393,10 @@ ora* ora_create(const ora_cfg* cfg) {
     o->c.v = o->v;
     o->c.w = o->w;
     o->nu = sqrt(M_PI) / (2.0 * cfg->kn);     /* collision frequency of Eq. 3 */
+    /* ES model: the stress relaxes at nu_ES (1 - (1 - 1/Pr)) = nu_ES / Pr, so the same viscosity
+     * (the Kn of Eq. 1) needs the collision frequency nu_ES = Pr nu */
+    if (cfg->es_pr > 0.0) o->nu *= cfg->es_pr;
+    o->esb = cfg->es_pr > 0.0 ? 1.0 - 1.0 / cfg->es_pr : 0.0;
     o->dx = 1.0 / o->n1;                       /* L = x1 extent (Sec. 2.1) */
     o->J = cfg->jump;
     o->sw2 = 0.0;
@@ -392,6 +412,19 @@ ora* ora_create(const ora_cfg* cfg) {
         for (int j = 0; j < o->d; ++j) vv += o->v[(size_t)k * o->d + j] * o->v[(size_t)k * o->d + j];
         for (int j = 0; j < o->d; ++j) o->sq[j] += o->w[k] * o->v[(size_t)k * o->d + j] * (vv - 2.5);
     }
+    for (int a = 0; a < 6; ++a) o->spi[a] = 0.0;
+    if (o->d == 3)
+        for (int k = 0; k < o->nv; ++k) {
+            const double* vk = o->v + (size_t)k * 3;
+            const double vv = vk[0] * vk[0] + vk[1] * vk[1] + vk[2] * vk[2];
+            const double wk = o->w[k];
+            o->spi[0] += 2.0 * wk * (vk[0] * vk[0] - vv / 3.0);
+            o->spi[1] += 2.0 * wk * (vk[1] * vk[1] - vv / 3.0);
+            o->spi[2] += 2.0 * wk * (vk[2] * vk[2] - vv / 3.0);
+            o->spi[3] += 2.0 * wk * vk[0] * vk[1];
+            o->spi[4] += 2.0 * wk * vk[0] * vk[2];
+            o->spi[5] += 2.0 * wk * vk[1] * vk[2];
+        }
     o->refl = (int*)malloc(sizeof(int) * 3 * o->nv);
     for (int j = 0; j < 3; ++j)
         for (int k = 0; k < o->nv; ++k) {
@@ -421,6 +454,7 @@ ora* ora_create(const ora_cfg* cfg) {
     o->u = (double*)calloc((size_t)o->N * o->d, sizeof(double));
     o->tau = (double*)calloc(o->N, sizeof(double));
     o->q = (double*)calloc((size_t)3 * o->N, sizeof(double));
+    o->pi = (double*)calloc((size_t)6 * o->N, sizeof(double));
     o->rhos = (double*)calloc((size_t)o->N * o->d * 2, sizeof(double));
     o->area[0] = o->n2 * o->n3;
     o->area[1] = o->n1 * o->n3;
@@ -464,7 +498,7 @@ ora* ora_create(const ora_cfg* cfg) {
 void ora_destroy(ora* o) {
     if (!o) return;
     free(o->solid); free(o->v); free(o->w); free(o->refl);
-    free(o->rho); free(o->u); free(o->tau); free(o->q); free(o->rhos);
+    free(o->rho); free(o->u); free(o->tau); free(o->q); free(o->pi); free(o->rhos);
     free(o->lag[0]); free(o->lag[1]);
     free(o->full[0]); free(o->full[1]);
     for (int j = 0; j < 3; ++j) free(o->sub[j]);
@@ -514,6 +548,29 @@ static void update_q(ora* o, const double* qn) {
         }
 }
 
+/* the six stress components 2 W (v_i v_j - delta_ij |v|^2 / 3) h of velocity k, added to pn at id */
+static void add_stress(const ora* o, int k, double wh, double* pn, size_t id) {
+    const double* vk = o->v + (size_t)k * 3;
+    const double vv = vk[0] * vk[0] + vk[1] * vk[1] + vk[2] * vk[2];
+    const size_t N = o->N;
+    pn[0 * N + id] += 2.0 * wh * (vk[0] * vk[0] - vv / 3.0);
+    pn[1 * N + id] += 2.0 * wh * (vk[1] * vk[1] - vv / 3.0);
+    pn[2 * N + id] += 2.0 * wh * (vk[2] * vk[2] - vv / 3.0);
+    pn[3 * N + id] += 2.0 * wh * vk[0] * vk[1];
+    pn[4 * N + id] += 2.0 * wh * vk[0] * vk[2];
+    pn[5 * N + id] += 2.0 * wh * vk[1] * vk[2];
+}
+
+/* P_ij from the working-variable sums pn; in the source form h' = h + J x1, so P = pn - J x1 spi:
+ * the paper's stress in either form. */
+static void update_pi(ora* o, const double* pn) {
+    for (int a = 0; a < 6; ++a)
+        for (int id = 0; id < o->N; ++id) {
+            double x1 = (o->c.form == 1) ? o->J * (id % o->n1) * o->dx : 0.0;
+            o->pi[(size_t)a * o->N + id] = o->solid[id] ? 0.0 : pn[(size_t)a * o->N + id] - x1 * o->spi[a];
+        }
+}
+
 static void iterate_once(ora* o) {
     const size_t N = o->N;
     const int d = o->d;
@@ -522,6 +579,7 @@ static void iterate_once(ora* o) {
     double* num_n = (double*)calloc(N * d * 2, sizeof(double));
     double* e_n = (double*)calloc(N, sizeof(double));          /* sum W |v|^2 h (tau option) */
     double* q_n = (double*)calloc(N * 3, sizeof(double));      /* heat-flux sums (Shakhov) */
+    double* p_n = (double*)calloc(N * 6, sizeof(double));      /* stress sums (ES) */
     memset(o->flux, 0, sizeof(double) * o->n1);
     for (int g0 = 0; g0 < o->nv; g0 += ORA_GROUP) {
         int gn = o->nv - g0 < ORA_GROUP ? o->nv - g0 : ORA_GROUP;
@@ -548,6 +606,7 @@ static void iterate_once(ora* o) {
                     e_n[id] += wk * vv * hk;
                     if (o->c.shakhov_pr > 0.0)
                         for (int j = 0; j < d; ++j) q_n[(size_t)j * N + id] += wk * o->v[(size_t)k * d + j] * (vv - 2.5) * hk;
+                    if (o->c.es_pr > 0.0) add_stress(o, k, wk * hk, p_n, (size_t)id);
                 }
                 for (int j = 0; j < d; ++j) {
                     double vj = o->v[(size_t)k * d + j];
@@ -587,9 +646,10 @@ static void iterate_once(ora* o) {
     memcpy(o->u, u_n, sizeof(double) * N * d);
     if (o->c.tau) update_tau(o, e_n);
     if (o->c.shakhov_pr > 0.0) update_q(o, q_n);
+    if (o->c.es_pr > 0.0) update_pi(o, p_n);
     double* t = o->lag[0]; o->lag[0] = o->lag[1]; o->lag[1] = t;
     if (o->keep_full) { t = o->full[0]; o->full[0] = o->full[1]; o->full[1] = t; }
-    free(rho_n); free(u_n); free(num_n); free(e_n); free(q_n);
+    free(rho_n); free(u_n); free(num_n); free(e_n); free(q_n); free(p_n);
     o->iter++;
 }
 
@@ -642,6 +702,9 @@ void ora_get_tau(const ora* o, double* tau) { memcpy(tau, o->tau, sizeof(double)
 /* Heat flux q [d][N] of the Shakhov option (zero otherwise and at solid points). */
 void ora_get_q(const ora* o, double* q) { memcpy(q, o->q, sizeof(double) * o->N * o->d); }
 
+/* Traceless stress [6][N] (11 22 33 12 13 23) of the ES option (zero otherwise and at solid points). */
+void ora_get_pi(const ora* o, double* p) { memcpy(p, o->pi, sizeof(double) * o->N * 6); }
+
 /* Overwrite the state with a uniform value c in the working variables (jump = 0 tests). */
 void ora_set_uniform(ora* o, double c) {
     for (int id = 0; id < o->N; ++id) {
@@ -655,6 +718,9 @@ void ora_set_uniform(ora* o, double c) {
     if (o->c.shakhov_pr > 0.0)
         for (int j = 0; j < o->d; ++j)
             for (int id = 0; id < o->N; ++id) o->q[(size_t)j * o->N + id] = o->solid[id] ? 0.0 : c * o->sq[j];
+    if (o->c.es_pr > 0.0)
+        for (int a = 0; a < 6; ++a)
+            for (int id = 0; id < o->N; ++id) o->pi[(size_t)a * o->N + id] = o->solid[id] ? 0.0 : c * o->spi[a];
     size_t lagsz = (size_t)o->nv * o->d * 2 * o->area[0];
     for (size_t i = 0; i < lagsz; ++i) o->lag[0][i] = c;
     if (o->keep_full)
@@ -678,6 +744,7 @@ void ora_set_initial(ora* o, const double* rho0, const double* u0) {
     double* num_n = (double*)calloc(N * d * 2, sizeof(double));
     double* e_n = (double*)calloc(N, sizeof(double));
     double* q_n = (double*)calloc(N * 3, sizeof(double));
+    double* p_n = (double*)calloc(N * 6, sizeof(double));
     for (int k = 0; k < o->nv; ++k) {
         const double* vk = o->v + (size_t)k * d;
         double vv = 0.0;
@@ -697,6 +764,7 @@ void ora_set_initial(ora* o, const double* rho0, const double* u0) {
             rho_n[id] += wk * h[id];
             e_n[id] += wk * vv * h[id];
             for (int j = 0; j < d; ++j) q_n[(size_t)j * N + id] += wk * vk[j] * (vv - 2.5) * h[id];
+            if (o->c.es_pr > 0.0) add_stress(o, k, wk * h[id], p_n, id);
             for (int j = 0; j < d; ++j) u_n[(size_t)j * N + id] += wk * vk[j] * h[id];
             for (int j = 0; j < d; ++j)
                 for (int sd = 0; sd < 2; ++sd) {
@@ -714,9 +782,10 @@ void ora_set_initial(ora* o, const double* rho0, const double* u0) {
     memcpy(o->u, u_n, sizeof(double) * N * d);
     if (o->c.tau) update_tau(o, e_n);
     if (o->c.shakhov_pr > 0.0) update_q(o, q_n);
+    if (o->c.es_pr > 0.0) update_pi(o, p_n);
     double* t = o->lag[0]; o->lag[0] = o->lag[1]; o->lag[1] = t;
     if (o->keep_full) { t = o->full[0]; o->full[0] = o->full[1]; o->full[1] = t; }
-    free(h); free(rho_n); free(u_n); free(num_n); free(e_n); free(q_n);
+    free(h); free(rho_n); free(u_n); free(num_n); free(e_n); free(q_n); free(p_n);
 }
 
 /* One sweep of velocity k from the current state, without updating the state (point-update

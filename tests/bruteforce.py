@@ -20,14 +20,18 @@ import math
 import numpy as np
 
 
-def solve_dense(solid, kn, v, w, jump=1.0, order=2, lateral="specular", tau=False, alpha=1.0, shakhov_pr=0.0):
+def solve_dense(solid, kn, v, w, jump=1.0, order=2, lateral="specular", tau=False, alpha=1.0, shakhov_pr=0.0,
+                es_pr=0.0):
     """tau: keep the temperature term tau (|v|^2 - 3/2) of Eq. 2 with tau = (2/3) sum W |v|^2 h - rho
     (Eq. 4), a linear functional of the unknowns at the same point like rho and u.
     alpha: Maxwell accommodation of Eq. 5; the wall value of velocity k is alpha rho_s + (1 - alpha)
     h(x_f, reflected k) with h at the wall's fluid point x_f (lagged, like rho_s).
     shakhov_pr > 0 (with tau): linearised Shakhov model, the source adds
-    (4/5)(1 - Pr) q.v_k (|v_k|^2 - 5/2) with q = sum W v (|v|^2 - 5/2) h at the same point."""
+    (4/5)(1 - Pr) q.v_k (|v_k|^2 - 5/2) with q = sum W v (|v|^2 - 5/2) h at the same point.
+    es_pr > 0 (with tau): linearised ES-BGK model, collision frequency Pr nu and the source adds
+    (1 - 1/Pr) sum_ij P_ij v_i v_j with P_ij = 2 sum W (v_i v_j - delta_ij |v|^2 / 3) h."""
     assert shakhov_pr == 0.0 or tau
+    assert es_pr == 0.0 or (tau and shakhov_pr == 0.0)
     solid = np.asarray(solid, dtype=bool)
     dims = solid.ndim
     shape = solid.shape
@@ -36,6 +40,8 @@ def solve_dense(solid, kn, v, w, jump=1.0, order=2, lateral="specular", tau=Fals
     w = np.asarray(w, dtype=float)
     nv = len(w)
     nu = math.sqrt(math.pi) / (2.0 * kn)
+    if es_pr > 0.0:
+        nu *= es_pr                      # the same viscosity with the ES model's stress relaxation
     dx = 1.0 / n[0]
 
     def arr_index(c):                    # coordinate tuple (x1, x2, ...) -> numpy index
@@ -121,6 +127,11 @@ def solve_dense(solid, kn, v, w, jump=1.0, order=2, lateral="specular", tau=Fals
                     vkk2 = float(np.dot(v[kk], v[kk]))
                     cv += (nu * 0.8 * (1.0 - shakhov_pr) * w[kk] * float(np.dot(v[kk], v[k]))
                            * (vkk2 - 2.5) * (vk2 - 2.5))
+                if es_pr > 0.0:
+                    vkk2 = float(np.dot(v[kk], v[kk]))
+                    # sum_ij P_ij v_ki v_kj with P_ij = 2 W (v_kk,i v_kk,j - delta_ij |v_kk|^2 / 3)
+                    pv = 2.0 * (float(np.dot(v[kk], v[k])) ** 2 - vkk2 * vk2 / 3.0)
+                    cv += nu * (1.0 - 1.0 / es_pr) * w[kk] * pv
                 A[row, col(f, kk)] -= cv
                 lag1[row] -= cv
             diag = nu
@@ -158,17 +169,25 @@ def solve_dense(solid, kn, v, w, jump=1.0, order=2, lateral="specular", tau=Fals
     u = np.zeros((dims,) + shape)
     temp = np.zeros(shape)
     heat = np.zeros((dims,) + shape)
+    stress = np.zeros((6,) + shape)
     vv = (v * v).sum(axis=1)
+    pairs = ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))
     for f, c in enumerate(fluid_coords):
         rho[arr_index(c)] = float(np.dot(w, H[f]))
         temp[arr_index(c)] = 2.0 / 3.0 * float(np.dot(w * vv, H[f])) - rho[arr_index(c)]
         for j in range(dims):
             u[(j,) + arr_index(c)] = float(np.dot(w * v[:, j], H[f]))
             heat[(j,) + arr_index(c)] = float(np.dot(w * v[:, j] * (vv - 2.5), H[f]))
+        if dims == 3:
+            for a, (i, j) in enumerate(pairs):
+                stress[(a,) + arr_index(c)] = float(np.dot(2.0 * w * (v[:, i] * v[:, j] - (vv / 3.0 if i == j else 0.0)),
+                                                           H[f]))
     k_perm = 2.0 / math.sqrt(math.pi) * kn * float(u[0].sum() / u[0].size)
     resid = float(np.abs(A[:U] @ sol - b[:U]).max())
     if shakhov_pr > 0.0:
         return rho, u, k_perm, resid, delta, temp, heat
+    if es_pr > 0.0:
+        return rho, u, k_perm, resid, delta, temp, stress
     if tau:
         return rho, u, k_perm, resid, delta, temp
     return rho, u, k_perm, resid, delta
