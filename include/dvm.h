@@ -133,6 +133,12 @@ typedef struct {
      * sweep kernel in FP32 too.  Negative or non-finite values, 2D, no temperature term,
      * subdomains, specular_fraction > 0 or BF16 storage: DVM_EINVAL. */
     double shakhov_prandtl;
+    /* 0 (default): BGK.  A Prandtl number Pr > 0 selects the linearised ES-BGK model, the other
+     * extension the paper names: the collision frequency becomes Pr nu (the BGK viscosity, so the
+     * Kn of Eq. 1 keeps its meaning) and the source also carries (1 - 1/Pr) sum_ij P_ij v_i v_j
+     * with the traceless stress P_ij = 2 sum_k W_k (v_ki v_kj - delta_ij |v_k|^2 / 3) h.  The same
+     * restrictions as shakhov_prandtl, and not together with it. */
+    double es_prandtl;
 } dvm_options;
 
 /* Fill *opt with the defaults: FP64, second order, specular lateral faces, check interval 100,
@@ -190,6 +196,12 @@ dvm_status dvm_temperature_at(dvm_ctx* ctx, int prob, double* tau, int on_device
  * doubles (solid points 0), with the Shakhov model enabled (dvm_options.shakhov_prandtl > 0);
  * on_device != 0 means q is a device pointer.  EINVAL when the model is off. */
 dvm_status dvm_heat_flux_at(dvm_ctx* ctx, int prob, double* q, int on_device);
+
+/* Traceless stress P_ij = 2 sum_k W_k (v_ki v_kj - delta_ij |v_k|^2 / 3) h of problem prob after the
+ * last iteration, [6][N] doubles in the order 11 22 33 12 13 23 (solid points 0), with the ES-BGK
+ * model enabled (dvm_options.es_prandtl > 0); on_device != 0 means p is a device pointer.  EINVAL
+ * when the model is off. */
+dvm_status dvm_stress_at(dvm_ctx* ctx, int prob, double* p, int on_device);
 
 /* Permeability k = (2/sqrt(pi)) Kn G_p (Eq. 11) and G_p, the mean of u1 over all points (Eq. 12:
  * the cross-section mean, averaged over every x1 cross-section), of the last iteration. */

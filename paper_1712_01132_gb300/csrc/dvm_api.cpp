@@ -49,13 +49,13 @@ cudaError_t sweep3d_occupancy(int T1, int NW, int R2, int R3, int bf16, int sub,
 template <typename T> cudaError_t launch_sweep3d(const SweepArgs3D<T>&, int grid, int NW, cudaStream_t);
 template <typename T> cudaError_t launch_finalize3d(const FinArgs3D<T>&, int nblocks, cudaStream_t);
 template <typename T>
-cudaError_t launch_init3d(const Prob3D<T>*, int NL, const double* qw, const double* qwt, const double* qwq, cudaStream_t);
-template <typename T> cudaError_t launch_heatflux3d(const Prob3D<T>*, double* q, cudaStream_t);
+cudaError_t launch_init3d(const Prob3D<T>*, int NL, const double* qw, const double* qwt, const double* qwx, cudaStream_t);
+template <typename T> cudaError_t launch_modelmoments3d(const Prob3D<T>*, double* out, cudaStream_t);
 template <typename T> cudaError_t launch_moments3d(const Prob3D<T>*, double* rho, double* u, cudaStream_t);
 template <typename T> cudaError_t launch_temperature3d(const Prob3D<T>*, double* tau, cudaStream_t);
 template <typename T> cudaError_t launch_wall3d(const Prob3D<T>*, double* out, cudaStream_t);
 template <typename T>
-cudaError_t launch_warm3d(const Prob3D<T>*, int NL, int par, const double* qw2, const double* qwt, const double* qwq,
+cudaError_t launch_warm3d(const Prob3D<T>*, int NL, int par, const double* qw2, const double* qwt, const double* qwx,
                           const double* vel, const double* rho0, const double* u0, cudaStream_t);
 }  // namespace dvm
 
@@ -93,11 +93,11 @@ struct dvm_ctx {
     bool pairs = false;              // 2D FP32: two consecutive bands per CTA
     bool sub3 = false;               // 3D lagged-halo subdomains (pencil and tile tables)
     bool tau3 = false;               // 3D temperature term of Eq. 2
-    bool shk3 = false;               // 3D Shakhov model (scalar sweep kernel in both precisions)
+    int nx3 = 0;                     // 3D model moments: 3 Shakhov, 6 ES-BGK (scalar sweep kernel)
     bool packed3 = false;            // 3D FP32 sweep on the packed kernel (FP32 without Shakhov)
     bool spec2 = false;              // Maxwell walls with alpha < 1 (Eq. 5)
     double* qwt_dev = nullptr;       // 3D: [octant][group][4] sums of W |v|^2 (1, v)
-    double* qwq_dev = nullptr;       // 3D Shakhov: [octant][group][3][4] sums of W v_j (|v|^2 - 5/2) (1, v)
+    double* qwx_dev = nullptr;       // 3D model moments: [octant][group][nx][4] sums of W psi_a (1, v)
     int T1 = 8, rows = 8, max_rows = 8;
     std::vector<HostProb> hp;
     std::vector<Buf> bufs;
@@ -652,7 +652,7 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     c->nvq = nvo;
     // FP32 lanes carry two velocity slots (packed f32x2 kernel), FP64 lanes and the Shakhov model's
     // scalar kernel one
-    c->packed3 = c->prec == DVM_FP32 && !c->shk3;
+    c->packed3 = c->prec == DVM_FP32 && c->nx3 == 0;
     const int vpl = c->packed3 ? sweep3d_f32x2_velocities_per_lane() : 1;
     const int warps_total = (nvo + 32 * vpl - 1) / (32 * vpl);
     // at most 8 warps per CTA (group_warps: fewer warps per CTA, more velocity groups)
@@ -679,7 +679,7 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         const size_t lim = (size_t)smem_max - 1024;
         auto smem_of = [&]() -> size_t {
             if (c->packed3) return sweep3d_f32x2_smem(c->T1, c->NW, c->R2, c->R3, c->tau3, c->spec2);
-            return sweep3d_smem<T>(c->T1, c->NW, c->R2, c->R3, c->tau3, c->spec2, c->shk3);
+            return sweep3d_smem<T>(c->T1, c->NW, c->R2, c->R3, c->tau3, c->spec2, c->nx3);
         };
         while (smem_of() > lim) {
             if (c->T1 > 4) c->T1 = 4;
@@ -712,8 +712,24 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     // ---- warm-start tables: lane velocities and group sums of W phi_m psi_n, phi = psi = (1, v)
     // (qwt: the same with phi = |v|^2, for the temperature term; sw2 = sum of W |v|^2 over the grid)
     std::vector<double> qw2((size_t)NO * G * 4 * 4, 0.0), vel((size_t)NO * NL * 3, 0.0), qwt((size_t)NO * G * 4, 0.0);
-    std::vector<double> qwq((size_t)NO * G * 3 * 4, 0.0);   // Shakhov: sum W v_j (|v|^2 - 5/2) psi_n
-    double sq[3] = {0.0, 0.0, 0.0};
+    // model moments: source factors phi_a and moment functions psi_a of a velocity (Shakhov: the
+    // heat flux, ES-BGK: the traceless stress), the group sums of W psi_a (1, v) and the grid sums
+    // of W psi_a (the source-form shift)
+    const int nx = c->nx3;
+    auto model_fns = [nx](const double* v, double* phi, double* psi) {
+        const double vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        if (nx == 3)
+            for (int j = 0; j < 3; ++j) phi[j] = psi[j] = v[j] * (vv - 2.5);
+        if (nx == 6) {
+            const int I[6] = {0, 1, 2, 0, 0, 1}, J[6] = {0, 1, 2, 1, 2, 2};
+            for (int m = 0; m < 6; ++m) {
+                phi[m] = (m < 3 ? 1.0 : 2.0) * v[I[m]] * v[J[m]];
+                psi[m] = 2.0 * (v[I[m]] * v[J[m]] - (m < 3 ? vv / 3.0 : 0.0));
+            }
+        }
+    };
+    std::vector<double> qwx((size_t)NO * G * std::max(nx, 1) * 4, 0.0);
+    double sx[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     for (int q = 0; q < NO; ++q)
         for (int m = 0; m < nvo; ++m) {
             const int k = group[q][m];
@@ -725,32 +741,37 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
                     qw2[(((size_t)q * G + gg) * 4 + a) * 4 + b2] += grid->w[k] * ph[a] * ph[b2];
             const double vv = ph[1] * ph[1] + ph[2] * ph[2] + ph[3] * ph[3];
             for (int b2 = 0; b2 < 4; ++b2) qwt[((size_t)q * G + gg) * 4 + b2] += grid->w[k] * vv * ph[b2];
-            for (int j = 0; j < 3; ++j)
-                for (int b2 = 0; b2 < 4; ++b2)
-                    qwq[(((size_t)q * G + gg) * 3 + j) * 4 + b2] += grid->w[k] * ph[1 + j] * (vv - 2.5) * ph[b2];
+            if (nx) {
+                double phi[6], psi[6];
+                model_fns(grid->v + 3 * k, phi, psi);
+                for (int m = 0; m < nx; ++m)
+                    for (int b2 = 0; b2 < 4; ++b2)
+                        qwx[(((size_t)q * G + gg) * nx + m) * 4 + b2] += grid->w[k] * psi[m] * ph[b2];
+            }
         }
-    for (int k = 0; k < grid->nv; ++k) {
-        const double* vk = grid->v + 3 * k;
-        const double vv = vk[0] * vk[0] + vk[1] * vk[1] + vk[2] * vk[2];
-        for (int j = 0; j < 3; ++j) sq[j] += grid->w[k] * vk[j] * (vv - 2.5);
-    }
+    if (nx)
+        for (int k = 0; k < grid->nv; ++k) {
+            double phi[6], psi[6];
+            model_fns(grid->v + 3 * k, phi, psi);
+            for (int m = 0; m < nx; ++m) sx[m] += grid->w[k] * psi[m];
+        }
     double sw2 = 0.0;
     for (int k = 0; k < grid->nv; ++k)
         for (int j = 0; j < 3; ++j) sw2 += grid->w[k] * grid->v[3 * k + j] * grid->v[3 * k + j];
     c->qw2_dev = (double*)dev_alloc(c, qw2.size() * sizeof(double));
     c->vel_dev = (double*)dev_alloc(c, vel.size() * sizeof(double));
     c->qwt_dev = (double*)dev_alloc(c, qwt.size() * sizeof(double));
-    c->qwq_dev = (double*)dev_alloc(c, qwq.size() * sizeof(double));
-    if (!c->qw2_dev || !c->vel_dev || !c->qwt_dev || !c->qwq_dev) return fail(c, DVM_ENOMEM, "device allocation failed");
+    c->qwx_dev = (double*)dev_alloc(c, qwx.size() * sizeof(double));
+    if (!c->qw2_dev || !c->vel_dev || !c->qwt_dev || !c->qwx_dev) return fail(c, DVM_ENOMEM, "device allocation failed");
     {
         cudaError_t e;
         if ((e = cudaMemcpyAsync(c->qw2_dev, qw2.data(), qw2.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream)) ||
             (e = cudaMemcpyAsync(c->vel_dev, vel.data(), vel.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream)) ||
             (e = cudaMemcpyAsync(c->qwt_dev, qwt.data(), qwt.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream)) ||
-            (e = cudaMemcpyAsync(c->qwq_dev, qwq.data(), qwq.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream)) ||
+            (e = cudaMemcpyAsync(c->qwx_dev, qwx.data(), qwx.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream)) ||
             (e = cudaStreamSynchronize(c->stream)))
             return cuda_fail(c, e, "upload warm-start tables");
-        c->h2d_bytes += (qw2.size() + vel.size() + qwt.size() + qwq.size()) * sizeof(double);
+        c->h2d_bytes += (qw2.size() + vel.size() + qwt.size() + qwx.size()) * sizeof(double);
     }
     std::vector<Prob3D<T>> probs(c->nprob);
     std::vector<SweepItem3> items;
@@ -827,15 +848,16 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
             P.srct = (T*)dev_alloc(c, N * sizeof(T));
             if (!P.Pt || !P.srct) return fail(c, DVM_ENOMEM, "device allocation failed");
         }
-        // linearised Shakhov model: A = (4/5)(1 - Pr), the coefficient for which the heat flux
-        // relaxes at Pr times the collision frequency
-        P.shk = c->shk3 ? 1 : 0;
-        P.shkA = c->shk3 ? 0.8 * (1.0 - c->opt.shakhov_prandtl) : 0.0;
-        for (int j = 0; j < 3; ++j) P.sq[j] = sq[j];
-        if (P.shk) {
-            P.Pq = (T*)dev_alloc(c, (size_t)NO * G * 3 * N * sizeof(T));
-            P.srcq = (T*)dev_alloc(c, N * 4 * sizeof(T));
-            if (!P.Pq || !P.srcq) return fail(c, DVM_ENOMEM, "device allocation failed");
+        // model moments: Shakhov A = (4/5)(1 - Pr), the coefficient for which the heat flux relaxes
+        // at Pr times the collision frequency; ES-BGK 1 - 1/Pr, with the collision frequency Pr nu
+        // (set with the problem's nu) so that the stress relaxes at the BGK rate
+        P.nx = nx;
+        P.xcoef = nx == 3 ? 0.8 * (1.0 - c->opt.shakhov_prandtl) : (nx == 6 ? 1.0 - 1.0 / c->opt.es_prandtl : 0.0);
+        for (int m = 0; m < 6; ++m) P.sx[m] = sx[m];
+        if (nx) {
+            P.Px = (T*)dev_alloc(c, (size_t)NO * G * nx * N * sizeof(T));
+            P.srcx = (T*)dev_alloc(c, N * 8 * sizeof(T));
+            if (!P.Px || !P.srcx) return fail(c, DVM_ENOMEM, "device allocation failed");
         }
         // Maxwell walls with alpha < 1 (Eq. 5): wall faces from the point codes and their store
         P.spec = c->opt.specular_fraction;
@@ -920,9 +942,13 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
                 const double vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
                 d[18] = (T)(vv - 1.5);    // temperature term: |v|^2 - 3/2 and W |v|^2
                 d[19] = (T)(w * vv);
-                for (int j = 0; j < 3; ++j) {   // Shakhov: v_j (|v|^2 - 5/2) and W v_j (|v|^2 - 5/2)
-                    d[20 + j] = (T)(v[j] * (vv - 2.5));
-                    d[23 + j] = (T)(w * v[j] * (vv - 2.5));
+                if (nx) {   // model moments: phi_a and W psi_a
+                    double phi[6], psi[6];
+                    model_fns(v, phi, psi);
+                    for (int m = 0; m < nx; ++m) {
+                        d[20 + m] = (T)phi[m];
+                        d[26 + m] = (T)(w * psi[m]);
+                    }
                 }
                 for (int rs = 0; rs < 8; ++rs) {
                     double den = H.nu;
@@ -988,7 +1014,7 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
         e = sweep3d_f32x2_occupancy(c->T1, c->NW, mr2, mr3, c->bf16 ? 1 : 0, c->sub3 ? 1 : 0, c->tau3 ? 1 : 0,
                                     c->spec2 ? 1 : 0, &per_sm);
     else e = sweep3d_occupancy<T>(c->T1, c->NW, mr2, mr3, 0, c->sub3 ? 1 : 0, c->tau3 ? 1 : 0, c->spec2 ? 1 : 0,
-                                  c->shk3 ? 1 : 0, &per_sm);
+                                  c->nx3, &per_sm);
     if (e != cudaSuccess) return cuda_fail(c, e, "occupancy");
     if (per_sm < 1) return fail(c, DVM_EINVAL, "3D sweep kernel does not fit on an SM with these pencils");
     int dev = 0, sms = 0;
@@ -997,7 +1023,7 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     c->sweep_grid = std::max(1, std::min(c->nitems, per_sm * sms));
     for (int b = 0; b < c->nprob; ++b) {
         const Prob3D<T>* pd = (const Prob3D<T>*)c->probs_dev + b;
-        e = launch_init3d<T>(pd, NL, c->qw_dev + (size_t)b * NO * G * 4, c->qwt_dev, c->qwq_dev, c->stream);
+        e = launch_init3d<T>(pd, NL, c->qw_dev + (size_t)b * NO * G * 4, c->qwt_dev, c->qwx_dev, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
     }
     FinArgs3D<T> fa{(const Prob3D<T>*)c->probs_dev, c->blk_prob_dev, c->blk_start_dev, c->status_dev};
@@ -1090,7 +1116,7 @@ dvm_status enqueue_iter_3d(dvm_ctx* c) {
     a.bf16 = c->bf16 ? 1 : 0;
     a.sub = c->sub3 ? 1 : 0;
     a.tau = c->tau3 ? 1 : 0;
-    a.shk = c->shk3 ? 1 : 0;
+    a.nx = c->nx3;
     a.spec = c->spec2 ? 1 : 0;
     a.parity = (int)(c->iters & 1);
     a.ticket = c->counters_dev;
@@ -1232,7 +1258,7 @@ void state_segs_3d(const Prob3D<T>& P, size_t NL, int par, std::vector<Seg>& out
     const size_t es = P.bf16 ? 2 : sizeof(T);
     out.push_back({P.P, (size_t)8 * P.ngroups * 4 * P.N * sizeof(T)});
     if (P.tau) out.push_back({P.Pt, (size_t)8 * P.ngroups * P.N * sizeof(T)});
-    if (P.shk) out.push_back({P.Pq, (size_t)8 * P.ngroups * 3 * P.N * sizeof(T)});
+    if (P.nx) out.push_back({P.Px, (size_t)8 * P.ngroups * P.nx * P.N * sizeof(T)});
     if (P.spec > 0.0 && P.nfaces > 0) {
         const size_t fs = (size_t)P.nfaces * 4 * NL;
         out.push_back({P.F + par * fs, fs * sizeof(T)});
@@ -1404,7 +1430,15 @@ dvm_status dvm_create_batch(int nprob, const dvm_geometry* geoms, const double* 
         return reject(DVM_EINVAL, "the Shakhov model is implemented for 3D problems with the temperature term");
     if (c->opt.shakhov_prandtl > 0.0 && (c->sub3 || c->spec2 || c->opt.precision == DVM_BF16_STORE))
         return reject(DVM_EINVAL, "the Shakhov model is not implemented with subdomains, alpha < 1 or BF16 storage");
-    c->shk3 = c->opt.shakhov_prandtl > 0.0;
+    if (!(c->opt.es_prandtl >= 0.0) || !std::isfinite(c->opt.es_prandtl))
+        return reject(DVM_EINVAL, "es_prandtl must be 0 (BGK) or a positive Prandtl number");
+    if (c->opt.es_prandtl > 0.0 && (dims != 3 || !c->opt.temperature_term))
+        return reject(DVM_EINVAL, "the ES-BGK model is implemented for 3D problems with the temperature term");
+    if (c->opt.es_prandtl > 0.0 && (c->sub3 || c->spec2 || c->opt.precision == DVM_BF16_STORE))
+        return reject(DVM_EINVAL, "the ES-BGK model is not implemented with subdomains, alpha < 1 or BF16 storage");
+    if (c->opt.es_prandtl > 0.0 && c->opt.shakhov_prandtl > 0.0)
+        return reject(DVM_EINVAL, "choose one model: Shakhov or ES-BGK");
+    c->nx3 = c->opt.shakhov_prandtl > 0.0 ? 3 : (c->opt.es_prandtl > 0.0 ? 6 : 0);
     if (c->opt.group_warps < 0) return reject(DVM_EINVAL, "group_warps must not be negative");
     if (c->opt.band_pairs && (dims != 2 || c->opt.precision != DVM_FP32 || c->opt.subdomains[0] > 1 ||
                               c->opt.subdomains[1] > 1))
@@ -1442,6 +1476,8 @@ dvm_status dvm_create_batch(int nprob, const dvm_geometry* geoms, const double* 
         H.N = (int)N;
         H.kn = kn[b];
         H.nu = std::sqrt(3.14159265358979323846) / (2.0 * kn[b]);
+        // ES-BGK: the collision frequency Pr nu keeps the BGK viscosity (the Kn of Eq. 1)
+        if (c->nx3 == 6) H.nu *= c->opt.es_prandtl;
         H.dx = 1.0 / H.n[0];
         classify(H, dims, g.solid, c->opt.lateral_bc, c->opt.stencil_order);
         long long fluid = 0, faces = 0;
@@ -1582,23 +1618,32 @@ dvm_status dvm_temperature_at(dvm_ctx* c, int prob, double* tau, int on_device) 
     return DVM_OK;
 }
 
-dvm_status dvm_heat_flux_at(dvm_ctx* c, int prob, double* q, int on_device) {
-    if (!c || prob < 0 || prob >= c->nprob || !q) return DVM_EINVAL;
-    if (!c->shk3) return fail(c, DVM_EINVAL, "the Shakhov model is not enabled");
+// model moments [nx][N] of problem prob (heat flux of the Shakhov model, stress of ES-BGK)
+static dvm_status model_moments_at(dvm_ctx* c, int prob, double* out, int on_device, int want_nx, const char* what) {
+    if (!c || prob < 0 || prob >= c->nprob || !out) return DVM_EINVAL;
+    if (c->nx3 != want_nx) return fail(c, DVM_EINVAL, what);
     const size_t N = c->hp[prob].N;
-    double* dq = on_device ? q : c->scratch_dev;
+    double* d = on_device ? out : c->scratch_dev;
     cudaError_t e;
-    if (c->prec == DVM_FP32) e = launch_heatflux3d<float>((const Prob3D<float>*)c->probs_dev + prob, dq, c->stream);
-    else e = launch_heatflux3d<double>((const Prob3D<double>*)c->probs_dev + prob, dq, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "heat-flux kernel");
+    if (c->prec == DVM_FP32) e = launch_modelmoments3d<float>((const Prob3D<float>*)c->probs_dev + prob, d, c->stream);
+    else e = launch_modelmoments3d<double>((const Prob3D<double>*)c->probs_dev + prob, d, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "model-moment kernel");
     if (!on_device) {
-        if ((e = cudaMemcpyAsync(q, dq, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
-            return cuda_fail(c, e, "read heat flux");
-        c->d2h_bytes += (long long)(3 * N * sizeof(double));
+        if ((e = cudaMemcpyAsync(out, d, (size_t)want_nx * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+            return cuda_fail(c, e, "read model moments");
+        c->d2h_bytes += (long long)((size_t)want_nx * N * sizeof(double));
     }
     e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "heat flux");
+    if (e != cudaSuccess) return cuda_fail(c, e, "model moments");
     return DVM_OK;
+}
+
+dvm_status dvm_heat_flux_at(dvm_ctx* c, int prob, double* q, int on_device) {
+    return model_moments_at(c, prob, q, on_device, 3, "the Shakhov model is not enabled");
+}
+
+dvm_status dvm_stress_at(dvm_ctx* c, int prob, double* p, int on_device) {
+    return model_moments_at(c, prob, p, on_device, 6, "the ES-BGK model is not enabled");
 }
 
 dvm_status dvm_wall_density_at(dvm_ctx* c, int prob, double* rhos) {
@@ -1729,9 +1774,9 @@ dvm_status dvm_set_initial_at(dvm_ctx* c, int prob, const double* rho0, const do
     const int par = (int)(c->iters & 1);
     if (c->dims == 3) {
         if (c->prec == DVM_FP32)
-            e = launch_warm3d<float>((const Prob3D<float>*)c->probs_dev + prob, c->NL, par, c->qw2_dev, c->qwt_dev, c->qwq_dev, c->vel_dev, d_rho, d_u, c->stream);
+            e = launch_warm3d<float>((const Prob3D<float>*)c->probs_dev + prob, c->NL, par, c->qw2_dev, c->qwt_dev, c->qwx_dev, c->vel_dev, d_rho, d_u, c->stream);
         else
-            e = launch_warm3d<double>((const Prob3D<double>*)c->probs_dev + prob, c->NL, par, c->qw2_dev, c->qwt_dev, c->qwq_dev, c->vel_dev, d_rho, d_u, c->stream);
+            e = launch_warm3d<double>((const Prob3D<double>*)c->probs_dev + prob, c->NL, par, c->qw2_dev, c->qwt_dev, c->qwx_dev, c->vel_dev, d_rho, d_u, c->stream);
     } else if (c->prec == DVM_FP32) {
         e = launch_warm2d<float>((const Prob2D<float>*)c->probs_dev + prob, c->NL, par, c->qw2_dev, c->vel_dev, d_rho, d_u, c->stream);
     } else {

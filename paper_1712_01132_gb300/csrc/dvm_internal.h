@@ -131,13 +131,16 @@ struct Prob3D {
     double sw2;             // sum over the grid of W |v|^2 (3/2 for a rule exact on v^2)
     T* Pt;                  // [8][G][N] partials of sum W |v|^2 h' (with tau)
     T* srct;                // [N] nu tau of the last iteration, read by the sweep (with tau)
-    // linearised Shakhov model (with tau): the source adds A q.v (|v|^2 - 5/2), A = (4/5)(1 - Pr),
-    // q = sum W v (|v|^2 - 5/2) h
-    int shk;                // 1: Shakhov model
-    double shkA;            // A
-    double sq[3];           // sum over the grid of W v_j (|v|^2 - 5/2): q' = q + x1 sq_j
-    T* Pq;                  // [8][G][3][N] partials of sum W v_j (|v|^2 - 5/2) h' (Shakhov)
-    T* srcq;                // [N][4] nu A q_j of the last iteration, read by the sweep (Shakhov)
+    // model moments of the linearised Shakhov (nx = 3) and ES-BGK (nx = 6) models (with tau): the
+    // source adds xcoef sum_a m_a phi_a(v) with the point's moments m_a = sum W psi_a(v) h;
+    // Shakhov: phi_j = psi_j = v_j (|v|^2 - 5/2) (the heat flux), xcoef = (4/5)(1 - Pr); ES:
+    // phi = (v1^2, v2^2, v3^2, 2 v1 v2, 2 v1 v3, 2 v2 v3), psi_a = 2 (v_i v_j - delta_ij |v|^2 / 3)
+    // (the traceless stress), xcoef = 1 - 1/Pr and the collision frequency Pr nu
+    int nx;                 // 0 (BGK), 3 (Shakhov) or 6 (ES-BGK)
+    double xcoef;
+    double sx[6];           // sum over the grid of W psi_a: m'_a = m_a + x1 sx_a
+    T* Px;                  // [8][G][nx][N] partials of sum W psi_a h'
+    T* srcx;                // [N][8] nu xcoef m_a of the last iteration, read by the sweep
     // Maxwell walls with alpha < 1 (Eq. 5), as in Prob2D: spec = 1 - alpha; faces are (fluid
     // point, axis j, side u) with a solid neighbour at x + (2u - 1) e_j
     double spec;
@@ -181,9 +184,9 @@ struct Prob3D {
     unsigned int* fin_counter;
 };
 
-// v1 v2 v3 a1 a2 a3 W Wv1 Wv2 Wv3 R[8] |v|^2-3/2 W|v|^2, then (Shakhov) g_j = v_j (|v|^2 - 5/2)
-// and W g_j
-constexpr int kLaneConsts3 = 26;
+// v1 v2 v3 a1 a2 a3 W Wv1 Wv2 Wv3 R[8] |v|^2-3/2 W|v|^2, then the model moments' phi_a [20..25]
+// and W psi_a [26..31] (Shakhov, ES-BGK)
+constexpr int kLaneConsts3 = 32;
 
 struct SweepItem3 { int prob, oct, p2, p3, group, pad0, pad1, pad2; };
 
@@ -199,7 +202,7 @@ struct SweepArgs3D {
     int bf16;                   // ghosts and pencil edges stored as BF16 (see Prob3D::bf16)
     int sub;                    // lagged-halo subdomains: pencils and tiles from the Prob3D tables
     int tau;                    // temperature term (Prob3D::tau)
-    int shk;                    // Shakhov model (Prob3D::shk; scalar kernel only)
+    int nx;                     // model moments (Prob3D::nx: Shakhov 3, ES-BGK 6; scalar kernel only)
     int spec;                   // specular wall parts (Prob3D::spec > 0)
     int parity;
     int* ticket;

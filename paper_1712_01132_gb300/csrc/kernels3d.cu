@@ -61,15 +61,16 @@ template <> struct HStore<float, true> {
 
 }  // namespace
 
-template <typename T, int T1, bool BF, bool SUB, bool TAU, bool SPEC, bool SHK>
+template <typename T, int T1, bool BF, bool SUB, bool TAU, bool SPEC, int NX>
 __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
     using V = typename V4t<T>::type;
     using HS = HStore<T, BF>;
-    static_assert(!SHK || (TAU && !SPEC), "the Shakhov source goes with the temperature term, without specular parts");
-    // moments per point: rho, u1..u3 (, sum W |v|^2 h) (, sum W v_j (|v|^2 - 5/2) h: Shakhov)
-    constexpr int NM = SHK ? 8 : (TAU ? 5 : 4);
-    // record words: face ids (specular parts) or nu A q (Shakhov) in more vectors
-    constexpr int RW = SPEC ? 24 : (SHK ? 20 : kRec3);
+    static_assert(NX == 0 || ((NX == 3 || NX == 6) && TAU && !SPEC),
+                  "model moments (Shakhov 3, ES-BGK 6) go with the temperature term, without specular parts");
+    // moments per point: rho, u1..u3 (, sum W |v|^2 h) (, the NX model moments sum W psi_a h)
+    constexpr int NM = NX > 0 ? 5 + NX : (TAU ? 5 : 4);
+    // record words: face ids (specular parts) or nu xcoef m_a (model moments) in more vectors
+    constexpr int RW = SPEC ? 24 : (NX == 3 ? 20 : (NX == 6 ? 24 : kRec3));
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
     __shared__ int s_abort;
@@ -119,8 +120,13 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
         const T v1 = lcp[0], v2 = lcp[1], v3 = lcp[2], a1 = lcp[3], a2 = lcp[4], a3 = lcp[5];
         const T W = lcp[6], Wv1 = lcp[7], Wv2 = lcp[8], Wv3 = lcp[9];
         const T vq = lcp[18], Wvv = lcp[19];             // |v|^2 - 3/2 and W |v|^2 (temperature term)
-        // Shakhov: g_j = v_j (|v|^2 - 5/2) and W g_j
-        const T gs1 = lcp[20], gs2 = lcp[21], gs3 = lcp[22], Wg1 = lcp[23], Wg2 = lcp[24], Wg3 = lcp[25];
+        // model moments: source factors phi_a and quadrature weights W psi_a
+        T xf[NX > 0 ? NX : 1], xw[NX > 0 ? NX : 1];
+#pragma unroll
+        for (int m = 0; m < NX; ++m) {
+            xf[m] = lcp[20 + m];
+            xw[m] = lcp[26 + m];
+        }
         T* my_rtab = rtab + (size_t)warp * 8 * 32 + lane;
 #pragma unroll
         for (int rs = 0; rs < 8; ++rs) my_rtab[rs * 32] = lcp[10 + rs];
@@ -168,7 +174,7 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                 const int i = rem - jj * T1;
                 V r0 = V4t<T>::make(0, 0, 0, 0), r1 = r0, r2 = r0, r3 = r0;
                 V r4 = V4t<T>::make(ibits(T(0), -1), ibits(T(0), -1), ibits(T(0), -1), ibits(T(0), -1)), r5 = r4;
-                if constexpr (SHK) r4 = V4t<T>::make(0, 0, 0, 0);   // no Shakhov source off the fluid
+                if constexpr (NX > 0) r4 = r5 = V4t<T>::make(0, 0, 0, 0);   // no model source off the fluid
                 if (jj < nr2 && i < width) {
                     const int ic = c0 + i;
                     const int x = s1n ? n1 - 1 - ic : ic;
@@ -202,7 +208,10 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                             r5 = V4t<T>::make(ibits(T(0), fi[(3 - s2n) * Nn + id]), ibits(T(0), fi[(5 - s3n) * Nn + id]),
                                               ibits(T(0), -1), ibits(T(0), -1));
                         }
-                        if constexpr (SHK) r4 = reinterpret_cast<const V*>(P->srcq)[id];   // nu A q
+                        if constexpr (NX > 0) {   // nu xcoef m_a
+                            r4 = reinterpret_cast<const V*>(P->srcx)[2 * (size_t)id];
+                            r5 = reinterpret_cast<const V*>(P->srcx)[2 * (size_t)id + 1];
+                        }
                     }
                 }
                 V* R = reinterpret_cast<V*>(rec + (size_t)((kk * MR2 + jj) * T1 + i) * RW);
@@ -214,7 +223,8 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                     R[4] = r4;
                     R[5] = r5;
                 }
-                if constexpr (SHK) R[4] = r4;
+                if constexpr (NX > 0) R[4] = r4;
+                if constexpr (NX > 4) R[5] = r5;
             }
             __syncthreads();
             if (s_abort) return;
@@ -278,7 +288,7 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                     T* prow = part + ((size_t)(warp * MROWS + kk * MR2 + jj) * T1) * NM;
 #pragma unroll
                     for (int i0 = 0; i0 < T1; i0 += 4) {
-                        T m0[4], m1[4], m2[4], m3[4], m4[4], m5[4], m6[4], m7[4];
+                        T m0[4], m1[4], m2[4], m3[4], m4[4], mx[NX > 0 ? NX : 1][4];
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
                             const int i = i0 + c;
@@ -289,9 +299,13 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                                 const T z2 = zr[((size_t)T1 + i) * 32];
                                 T S = fma(A.w, v3, fma(A.z, v2, fma(A.y, v1, A.x)));
                                 if constexpr (TAU) S = fma(D.z, vq, S);   // nu tau (|v|^2 - 3/2)
-                                if constexpr (SHK) {                      // nu A q.v (|v|^2 - 5/2)
-                                    const V Q = R[4];
-                                    S = fma(Q.z, gs3, fma(Q.y, gs2, fma(Q.x, gs1, S)));
+                                if constexpr (NX > 0) {   // nu xcoef sum_a m_a phi_a(v)
+                                    const V X0 = R[4];
+                                    S = fma(X0.z, xf[2], fma(X0.y, xf[1], fma(X0.x, xf[0], S)));
+                                    if constexpr (NX == 6) {
+                                        const V X1 = R[5];
+                                        S = fma(X1.y, xf[5], fma(X1.x, xf[4], fma(X0.w, xf[3], S)));
+                                    }
                                 }
                                 T t1 = fma(C.x, hp1, fma(C.y, hp2, B.x));
                                 T t2 = fma(C.z, rb1[i], fma(C.w, rb2[i], B.y));
@@ -324,24 +338,22 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                                 m2[c] = Wv2 * h;
                                 m3[c] = Wv3 * h;
                                 m4[c] = Wvv * h;
-                                m5[c] = Wg1 * h;
-                                m6[c] = Wg2 * h;
-                                m7[c] = Wg3 * h;
+#pragma unroll
+                                for (int m = 0; m < NX; ++m) mx[m][c] = xw[m] * h;
                             } else {
-                                m0[c] = m1[c] = m2[c] = m3[c] = m4[c] = m5[c] = m6[c] = m7[c] = T(0);
+                                m0[c] = m1[c] = m2[c] = m3[c] = m4[c] = T(0);
+#pragma unroll
+                                for (int m = 0; m < NX; ++m) mx[m][c] = T(0);
                             }
                         }
                         const T r0 = reduce_scatter<T, 4>(m0, lane);
                         const T r1 = reduce_scatter<T, 4>(m1, lane);
                         const T r2 = reduce_scatter<T, 4>(m2, lane);
                         const T r3 = reduce_scatter<T, 4>(m3, lane);
-                        T r4 = T(0), r5 = T(0), r6 = T(0), r7 = T(0);
+                        T r4 = T(0), rx[NX > 0 ? NX : 1];
                         if constexpr (TAU) r4 = reduce_scatter<T, 4>(m4, lane);
-                        if constexpr (SHK) {
-                            r5 = reduce_scatter<T, 4>(m5, lane);
-                            r6 = reduce_scatter<T, 4>(m6, lane);
-                            r7 = reduce_scatter<T, 4>(m7, lane);
-                        }
+#pragma unroll
+                        for (int m = 0; m < NX; ++m) rx[m] = reduce_scatter<T, 4>(mx[m], lane);
                         const int p = lane >> 3;
                         if ((lane & 7) == 0 && i0 + p < width) {
                             T* d = prow + (i0 + p) * NM;
@@ -350,11 +362,8 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                             d[2] = r2;
                             d[3] = r3;
                             if constexpr (TAU) d[4] = r4;
-                            if constexpr (SHK) {
-                                d[5] = r5;
-                                d[6] = r6;
-                                d[7] = r7;
-                            }
+#pragma unroll
+                            for (int m = 0; m < NX; ++m) d[5 + m] = rx[m];
                         }
                     }
                     cr[0] = hp1;
@@ -441,7 +450,7 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                 const size_t pid = ((size_t)z * n2 + y) * n1 + x;
                 if (mm < 4) P->P[(((size_t)q * G + g) * 4 + mm) * N + pid] = s;
                 else if (mm == 4) P->Pt[((size_t)q * G + g) * N + pid] = s;
-                else P->Pq[(((size_t)q * G + g) * 3 + (mm - 5)) * N + pid] = s;
+                else P->Px[(((size_t)q * G + g) * NX + (mm - 5)) * N + pid] = s;
             }
             __syncthreads();
         }
@@ -492,18 +501,19 @@ __global__ void __launch_bounds__(256) finalize3d_kernel(const FinArgs3D<T> a) {
                 const T x1 = (T)((id % P->n1) * P->dx);
                 const T tau = T(2.0 / 3.0) * e - mo[0] + x1 * (T)(1.0 - 2.0 / 3.0 * P->sw2);
                 P->srct[id] = nu * tau;
-                if (P->shk) {
-                    // heat flux q_j = sum W v_j (|v|^2 - 5/2) h = q'_j - x1 sq_j; the source carries
-                    // nu A q_j
-                    T qv[3];
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        T qs = T(0);
+                if (P->nx) {
+                    // model moments m_a = sum W psi_a h = m'_a - x1 sx_a (heat flux, stress); the
+                    // source carries nu xcoef m_a
+                    const int nx = P->nx;
+                    T xv[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+                    for (int m = 0; m < nx; ++m) {
+                        T xs = T(0);
                         for (int q = 0; q < 8; ++q)
-                            for (int g = 0; g < G; ++g) qs += P->Pq[(((size_t)q * G + g) * 3 + j) * N + id];
-                        qv[j] = nu * (T)P->shkA * (qs - x1 * (T)P->sq[j]);
+                            for (int g = 0; g < G; ++g) xs += P->Px[(((size_t)q * G + g) * nx + m) * N + id];
+                        xv[m] = nu * (T)P->xcoef * (xs - x1 * (T)P->sx[m]);
                     }
-                    reinterpret_cast<V*>(P->srcq)[id] = V4t<T>::make(qv[0], qv[1], qv[2], T(0));
+                    reinterpret_cast<V*>(P->srcx)[2 * (size_t)id] = V4t<T>::make(xv[0], xv[1], xv[2], xv[3]);
+                    reinterpret_cast<V*>(P->srcx)[2 * (size_t)id + 1] = V4t<T>::make(xv[4], xv[5], T(0), T(0));
                 }
             }
             T ev[6];
@@ -577,7 +587,7 @@ __device__ __forceinline__ void put_h(const Prob3D<T>* P, T* base, size_t i, dou
 template <typename T>
 __global__ void init3d_kernel(const Prob3D<T>* P, int NL, const double* qw /*[8][G][4]*/,
                               const double* qwt /*[8][G][4]: sum W |v|^2 (1, v)*/,
-                              const double* qwq /*[8][G][3][4]: sum W v_j (|v|^2 - 5/2) (1, v)*/) {
+                              const double* qwx /*[8][G][nx][4]: sum W psi_a (1, v)*/) {
     const int n1 = P->n1, n2 = P->n2, n3 = P->n3, N = P->N, G = P->ngroups;
     const size_t nl = NL;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -599,11 +609,11 @@ __global__ void init3d_kernel(const Prob3D<T>* P, int NL, const double* qw /*[8]
             const double x1 = (id % n1) * P->dx;
             P->Pt[idx] = (P->code[id] & kSolidBit) ? T(0) : (T)(x1 * qwt[(idx / N) * 4]);
         }
-    if (P->shk)   // sum W v_j (|v|^2 - 5/2) h' of h' = x1
-        for (size_t idx = t0; idx < (size_t)8 * G * 3 * N; idx += stride) {
+    if (P->nx)   // model moments sum W psi_a h' of h' = x1
+        for (size_t idx = t0; idx < (size_t)8 * G * P->nx * N; idx += stride) {
             const int id = idx % N;
             const double x1 = (id % n1) * P->dx;
-            P->Pq[idx] = (P->code[id] & kSolidBit) ? T(0) : (T)(x1 * qwq[(idx / N) * 4]);
+            P->Px[idx] = (P->code[id] & kSolidBit) ? T(0) : (T)(x1 * qwx[(idx / N) * 4]);
         }
     // ghost slot s of the x1 ghosts holds the two columns before oriented column slot_col1[s]
     const int ns1 = P->ns1, ns2 = P->ns2, ns3 = P->ns3;
@@ -635,7 +645,7 @@ __global__ void init3d_kernel(const Prob3D<T>* P, int NL, const double* qw /*[8]
 // `par` hold h0' where the sweep would have captured them (same slot layout as the sweep writes).
 template <typename T>
 __global__ void warm3d_kernel(const Prob3D<T>* P, int NL, int par, const double* __restrict__ qw2,
-                              const double* __restrict__ qwt, const double* __restrict__ qwq,
+                              const double* __restrict__ qwt, const double* __restrict__ qwx,
                               const double* __restrict__ vel,
                               const double* __restrict__ rho0, const double* __restrict__ u0) {
     const int n1 = P->n1, n2 = P->n2, n3 = P->n3, N = P->N, G = P->ngroups;
@@ -690,17 +700,17 @@ __global__ void warm3d_kernel(const Prob3D<T>* P, int NL, int par, const double*
             }
             P->Pt[idx] = (T)val;
         }
-    // Shakhov: sum W v_j (|v|^2 - 5/2) h0' through qwq[q][g][j][n]
-    if (P->shk)
-        for (size_t idx = t0; idx < (size_t)8 * G * 3 * N; idx += stride) {
+    // model moments: sum W psi_a h0' through qwx[q][g][a][n]
+    if (P->nx)
+        for (size_t idx = t0; idx < (size_t)8 * G * P->nx * N; idx += stride) {
             const size_t id = idx % N;
             double val = 0.0;
             if (!(P->code[id] & kSolidBit)) {
-                const double* c = qwq + (idx / N) * 4;
+                const double* c = qwx + (idx / N) * 4;
                 const double r = rho0[id] + (id % n1) * P->dx;
                 val = r * c[0] + 2.0 * (u0[id] * c[1] + u0[N + id] * c[2] + u0[2 * (size_t)N + id] * c[3]);
             }
-            P->Pq[idx] = (T)val;
+            P->Px[idx] = (T)val;
         }
     const int ns1 = P->ns1, ns2 = P->ns2, ns3 = P->ns3;
     // x1 ghosts: (q, slot s, oriented row (k, j), layer) holds h at oriented column
@@ -784,20 +794,20 @@ __global__ void temperature3d_kernel(const Prob3D<T>* P, double* tau) {
     }
 }
 
-// Heat flux of the Shakhov model per point (FP64 sums of the partials): q_j = q'_j - x1 sq_j
-// (solid points 0), [3][N].
+// Model moments per point (FP64 sums of the partials): m_a = m'_a - x1 sx_a (solid points 0),
+// [nx][N]: the heat flux of the Shakhov model, the traceless stress of the ES-BGK model.
 template <typename T>
-__global__ void heatflux3d_kernel(const Prob3D<T>* P, double* qout) {
-    const int N = P->N, G = P->ngroups;
+__global__ void modelmoments3d_kernel(const Prob3D<T>* P, double* out) {
+    const int N = P->N, G = P->ngroups, nx = P->nx;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const bool solid = (P->code[id] & kSolidBit) != 0;
         const double x1 = (id % P->n1) * P->dx;
-        for (int j = 0; j < 3; ++j) {
-            double qs = 0.0;
+        for (int m = 0; m < nx; ++m) {
+            double xs = 0.0;
             if (!solid)
                 for (int q = 0; q < 8; ++q)
-                    for (int g = 0; g < G; ++g) qs += (double)P->Pq[(((size_t)q * G + g) * 3 + j) * N + id];
-            qout[(size_t)j * N + id] = solid ? 0.0 : qs - x1 * P->sq[j];
+                    for (int g = 0; g < G; ++g) xs += (double)P->Px[(((size_t)q * G + g) * nx + m) * N + id];
+            out[(size_t)m * N + id] = solid ? 0.0 : xs - x1 * P->sx[m];
         }
     }
 }
@@ -818,16 +828,17 @@ __global__ void wall3d_kernel(const Prob3D<T>* P, double* out) {
 }
 
 template <typename T>
-size_t sweep3d_smem(int T1, int NW, int R2, int R3, int tau, int spec, int shk) {
+size_t sweep3d_smem(int T1, int NW, int R2, int R3, int tau, int spec, int nx) {
     const size_t rows = (size_t)R2 * R3;
-    return sizeof(T) * (rows * T1 * (spec ? 24 : (shk ? 20 : kRec3)) + (size_t)NW * rows * T1 * (shk ? 8 : (tau ? 5 : 4)) +
+    const size_t rw = spec ? 24 : (nx == 3 ? 20 : (nx == 6 ? 24 : kRec3));
+    return sizeof(T) * (rows * T1 * rw + (size_t)NW * rows * T1 * (nx ? 5 + nx : (tau ? 5 : 4)) +
                         (size_t)NW * rows * 2 * 32 + (size_t)NW * R2 * 2 * T1 * 32 + (size_t)NW * 8 * 32);
 }
 
-template <typename T, int T1, bool SUB, bool TAU, bool SPEC, bool SHK = false>
+template <typename T, int T1, bool SUB, bool TAU, bool SPEC, int NX = 0>
 static cudaError_t occ3(int NW, int R2, int R3, int* blocks_per_sm) {
-    const size_t smem = sweep3d_smem<T>(T1, NW, R2, R3, TAU, SPEC, SHK);
-    auto kern = sweep3d_kernel<T, T1, false, SUB, TAU, SPEC, SHK>;
+    const size_t smem = sweep3d_smem<T>(T1, NW, R2, R3, TAU, SPEC, NX);
+    auto kern = sweep3d_kernel<T, T1, false, SUB, TAU, SPEC, NX>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, NW * 32, smem);
@@ -844,29 +855,36 @@ static cudaError_t occ3_t(int NW, int R2, int R3, int sub, int tau, int spec, in
     return tau ? occ3_s<T, T1, false, true>(NW, R2, R3, spec, bps) : occ3_s<T, T1, false, false>(NW, R2, R3, spec, bps);
 }
 
-// The scalar kernel serves the FP64 path and the Shakhov model in both precisions (FP32 and its
-// BF16-storage ablation otherwise use the packed kernel of sweep3d_f32x2.cu); its BF16 flag stays
-// false.  sub: lagged-halo subdomains (table-driven pencils and tiles); tau: the temperature term;
-// spec: specular wall parts; shk: the Shakhov source (with tau, without sub and spec).
+// model-moment kernels (Shakhov nx = 3, ES-BGK nx = 6): with tau, without sub and spec
 template <typename T>
-cudaError_t sweep3d_occupancy(int T1, int NW, int R2, int R3, int bf16, int sub, int tau, int spec, int shk,
+static cudaError_t occ3_x(int T1, int NW, int R2, int R3, int nx, int* bps) {
+    if (T1 == 4) return nx == 3 ? occ3<T, 4, false, true, false, 3>(NW, R2, R3, bps) : occ3<T, 4, false, true, false, 6>(NW, R2, R3, bps);
+    if (T1 == 8) return nx == 3 ? occ3<T, 8, false, true, false, 3>(NW, R2, R3, bps) : occ3<T, 8, false, true, false, 6>(NW, R2, R3, bps);
+    return cudaErrorInvalidValue;
+}
+
+// The scalar kernel serves the FP64 path and the Shakhov and ES-BGK models in both precisions
+// (FP32 and its BF16-storage ablation otherwise use the packed kernel of sweep3d_f32x2.cu); its
+// BF16 flag stays false.  sub: lagged-halo subdomains (table-driven pencils and tiles); tau: the
+// temperature term; spec: specular wall parts; nx: model moments (3 or 6; with tau, without sub
+// and spec).
+template <typename T>
+cudaError_t sweep3d_occupancy(int T1, int NW, int R2, int R3, int bf16, int sub, int tau, int spec, int nx,
                               int* blocks_per_sm) {
     if (bf16) return cudaErrorInvalidValue;
-    if (shk) {
-        if (sub || !tau || spec) return cudaErrorInvalidValue;
-        if (T1 == 4) return occ3<T, 4, false, true, false, true>(NW, R2, R3, blocks_per_sm);
-        if (T1 == 8) return occ3<T, 8, false, true, false, true>(NW, R2, R3, blocks_per_sm);
-        return cudaErrorInvalidValue;
+    if (nx) {
+        if (sub || !tau || spec || (nx != 3 && nx != 6)) return cudaErrorInvalidValue;
+        return occ3_x<T>(T1, NW, R2, R3, nx, blocks_per_sm);
     }
     if (T1 == 4) return occ3_t<T, 4>(NW, R2, R3, sub, tau, spec, blocks_per_sm);
     if (T1 == 8) return occ3_t<T, 8>(NW, R2, R3, sub, tau, spec, blocks_per_sm);
     return cudaErrorInvalidValue;
 }
 
-template <typename T, int T1, bool SUB, bool TAU, bool SPEC, bool SHK = false>
+template <typename T, int T1, bool SUB, bool TAU, bool SPEC, int NX = 0>
 static cudaError_t launch3(const SweepArgs3D<T>& a, int grid, int NW, cudaStream_t st) {
-    const size_t smem = sweep3d_smem<T>(T1, NW, a.maxR2, a.maxR3, TAU, SPEC, SHK);
-    auto kern = sweep3d_kernel<T, T1, false, SUB, TAU, SPEC, SHK>;
+    const size_t smem = sweep3d_smem<T>(T1, NW, a.maxR2, a.maxR3, TAU, SPEC, NX);
+    auto kern = sweep3d_kernel<T, T1, false, SUB, TAU, SPEC, NX>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, NW * 32, smem, st>>>(a);
@@ -885,14 +903,19 @@ static cudaError_t launch3_t(const SweepArgs3D<T>& a, int grid, int NW, cudaStre
 }
 
 template <typename T>
+static cudaError_t launch3_x(const SweepArgs3D<T>& a, int grid, int NW, cudaStream_t st) {
+    if (a.sub || !a.tau || a.spec) return cudaErrorInvalidValue;
+    if (a.T1 == 4 && a.nx == 3) return launch3<T, 4, false, true, false, 3>(a, grid, NW, st);
+    if (a.T1 == 4 && a.nx == 6) return launch3<T, 4, false, true, false, 6>(a, grid, NW, st);
+    if (a.T1 == 8 && a.nx == 3) return launch3<T, 8, false, true, false, 3>(a, grid, NW, st);
+    if (a.T1 == 8 && a.nx == 6) return launch3<T, 8, false, true, false, 6>(a, grid, NW, st);
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
 cudaError_t launch_sweep3d(const SweepArgs3D<T>& a, int grid, int NW, cudaStream_t st) {
     if (a.bf16) return cudaErrorInvalidValue;
-    if (a.shk) {
-        if (a.sub || !a.tau || a.spec) return cudaErrorInvalidValue;
-        if (a.T1 == 4) return launch3<T, 4, false, true, false, true>(a, grid, NW, st);
-        if (a.T1 == 8) return launch3<T, 8, false, true, false, true>(a, grid, NW, st);
-        return cudaErrorInvalidValue;
-    }
+    if (a.nx) return launch3_x<T>(a, grid, NW, st);
     if (a.T1 == 4) return launch3_t<T, 4>(a, grid, NW, st);
     if (a.T1 == 8) return launch3_t<T, 8>(a, grid, NW, st);
     return cudaErrorInvalidValue;
@@ -905,17 +928,17 @@ cudaError_t launch_finalize3d(const FinArgs3D<T>& a, int nblocks, cudaStream_t s
 }
 
 template <typename T>
-cudaError_t launch_init3d(const Prob3D<T>* p, int NL, const double* qw, const double* qwt, const double* qwq,
+cudaError_t launch_init3d(const Prob3D<T>* p, int NL, const double* qw, const double* qwt, const double* qwx,
                           cudaStream_t st) {
-    init3d_kernel<T><<<608, 256, 0, st>>>(p, NL, qw, qwt, qwq);
+    init3d_kernel<T><<<608, 256, 0, st>>>(p, NL, qw, qwt, qwx);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_warm3d(const Prob3D<T>* p, int NL, int par, const double* qw2, const double* qwt,
-                          const double* qwq, const double* vel, const double* rho0, const double* u0,
+                          const double* qwx, const double* vel, const double* rho0, const double* u0,
                           cudaStream_t st) {
-    warm3d_kernel<T><<<608, 256, 0, st>>>(p, NL, par, qw2, qwt, qwq, vel, rho0, u0);
+    warm3d_kernel<T><<<608, 256, 0, st>>>(p, NL, par, qw2, qwt, qwx, vel, rho0, u0);
     return cudaGetLastError();
 }
 
@@ -932,8 +955,8 @@ cudaError_t launch_temperature3d(const Prob3D<T>* p, double* tau, cudaStream_t s
 }
 
 template <typename T>
-cudaError_t launch_heatflux3d(const Prob3D<T>* p, double* q, cudaStream_t st) {
-    heatflux3d_kernel<T><<<608, 256, 0, st>>>(p, q);
+cudaError_t launch_modelmoments3d(const Prob3D<T>* p, double* out, cudaStream_t st) {
+    modelmoments3d_kernel<T><<<608, 256, 0, st>>>(p, out);
     return cudaGetLastError();
 }
 
@@ -947,21 +970,17 @@ template size_t sweep3d_smem<double>(int, int, int, int, int, int, int);
 template size_t sweep3d_smem<float>(int, int, int, int, int, int, int);
 template cudaError_t sweep3d_occupancy<double>(int, int, int, int, int, int, int, int, int, int*);
 template cudaError_t launch_sweep3d<double>(const SweepArgs3D<double>&, int, int, cudaStream_t);
-// FP32 with the Shakhov model (the scalar kernel's only FP32 use)
+// FP32 with the Shakhov or ES-BGK model (the scalar kernel's only FP32 use)
 template <>
-cudaError_t sweep3d_occupancy<float>(int T1, int NW, int R2, int R3, int bf16, int sub, int tau, int spec, int shk,
+cudaError_t sweep3d_occupancy<float>(int T1, int NW, int R2, int R3, int bf16, int sub, int tau, int spec, int nx,
                                      int* blocks_per_sm) {
-    if (bf16 || !shk || sub || !tau || spec) return cudaErrorInvalidValue;
-    if (T1 == 4) return occ3<float, 4, false, true, false, true>(NW, R2, R3, blocks_per_sm);
-    if (T1 == 8) return occ3<float, 8, false, true, false, true>(NW, R2, R3, blocks_per_sm);
-    return cudaErrorInvalidValue;
+    if (bf16 || (nx != 3 && nx != 6) || sub || !tau || spec) return cudaErrorInvalidValue;
+    return occ3_x<float>(T1, NW, R2, R3, nx, blocks_per_sm);
 }
 template <>
 cudaError_t launch_sweep3d<float>(const SweepArgs3D<float>& a, int grid, int NW, cudaStream_t st) {
-    if (a.bf16 || !a.shk || a.sub || !a.tau || a.spec) return cudaErrorInvalidValue;
-    if (a.T1 == 4) return launch3<float, 4, false, true, false, true>(a, grid, NW, st);
-    if (a.T1 == 8) return launch3<float, 8, false, true, false, true>(a, grid, NW, st);
-    return cudaErrorInvalidValue;
+    if (a.bf16 || !a.nx) return cudaErrorInvalidValue;
+    return launch3_x<float>(a, grid, NW, st);
 }
 
 #define DVM_INSTANTIATE3(T)                                                                                  \
@@ -971,7 +990,7 @@ cudaError_t launch_sweep3d<float>(const SweepArgs3D<float>& a, int grid, int NW,
     template cudaError_t launch_warm3d<T>(const Prob3D<T>*, int, int, const double*, const double*,          \
                                           const double*, const double*, const double*, const double*,        \
                                           cudaStream_t);                                                     \
-    template cudaError_t launch_heatflux3d<T>(const Prob3D<T>*, double*, cudaStream_t);                      \
+    template cudaError_t launch_modelmoments3d<T>(const Prob3D<T>*, double*, cudaStream_t);                  \
     template cudaError_t launch_moments3d<T>(const Prob3D<T>*, double*, double*, cudaStream_t);              \
     template cudaError_t launch_temperature3d<T>(const Prob3D<T>*, double*, cudaStream_t);                   \
     template cudaError_t launch_wall3d<T>(const Prob3D<T>*, double*, cudaStream_t);

@@ -51,6 +51,7 @@ class dvm_options(ctypes.Structure):
         ("temperature_term", ctypes.c_int),
         ("specular_fraction", ctypes.c_double),
         ("shakhov_prandtl", ctypes.c_double),
+        ("es_prandtl", ctypes.c_double),
     ]
 
 
@@ -72,6 +73,7 @@ _SIGNATURES = [
     ("dvm_moments_at", ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int]),
     ("dvm_temperature_at", ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int]),
     ("dvm_heat_flux_at", ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int]),
+    ("dvm_stress_at", ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int]),
     ("dvm_permeability", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("dvm_permeability_at", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_double)]),
@@ -210,7 +212,7 @@ class _TorchAllocator:
 def make_options(precision="fp64", stencil_order=2, lateral="specular", check_interval=100, stream=None,
                  tile_x1=0, band_rows=0, torch_memory=True, use_graph=False, subdomains=(1, 1, 1),
                  band_pairs=False, group_warps=0, temperature_term=False, specular_fraction=0.0,
-                 shakhov_prandtl=0.0):
+                 shakhov_prandtl=0.0, es_prandtl=0.0):
     """dvm_options with torch's current stream (unless stream is given) and, by default, torch's
     caching allocator for device memory.  Returns (options, keepalive)."""
     o = dvm_default_options()
@@ -226,6 +228,7 @@ def make_options(precision="fp64", stencil_order=2, lateral="specular", check_in
     o.temperature_term = 1 if temperature_term else 0
     o.specular_fraction = float(specular_fraction)
     o.shakhov_prandtl = float(shakhov_prandtl)
+    o.es_prandtl = float(es_prandtl)
     for j in range(3):
         o.subdomains[j] = int(subdomains[j])
     keep = []
@@ -354,6 +357,13 @@ class Solver:
         q = np.zeros(3 * m.size)
         _check(self._lib.dvm_heat_flux_at(self._ctx, int(prob), _ptr(q), 0), self._ctx)
         return q.reshape((3,) + m.shape)
+
+    def stress(self, prob=0):
+        """Traceless stress [6, *shape] (11 22 33 12 13 23) of problem prob; needs es_prandtl > 0."""
+        m = self.masks[prob]
+        p = np.zeros(6 * m.size)
+        _check(self._lib.dvm_stress_at(self._ctx, int(prob), _ptr(p), 0), self._ctx)
+        return p.reshape((6,) + m.shape)
 
     def moments_device(self, prob, rho_ptr, u_ptr):
         _check(self._lib.dvm_moments_at(self._ctx, int(prob), ctypes.c_void_p(rho_ptr), ctypes.c_void_p(u_ptr), 1),
