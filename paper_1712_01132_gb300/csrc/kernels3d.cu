@@ -7,10 +7,11 @@
 //             (p2-1, p3) and (p2, p3-1), which carry lower tickets, so the persistent schedule
 //             cannot deadlock.  One discrete velocity per lane.  Inside a tile the rows are walked
 //             plane by plane (x3), row by row (x2), x1 fastest: every value a point reads is final,
-//             so the result equals the paper's raster scan.
+//             so the result equals the paper's raster scan.  Serves FP64, and both precisions of
+//             the Shakhov and ES-BGK model variants (NX = 3 or 6 model moments per point).
 // finalize3d: sums the octant/group moment partials, forms the FP64 wall densities (Eq. 6), the
 //             next sources and wall terms, and the FP64 sum of u1 for Eq. 11-12.
-// init3d, moments3d, wall3d: start state and readouts.
+// init3d, warm3d, moments3d, temperature3d, modelmoments3d, wall3d: start states and readouts.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
