@@ -85,8 +85,19 @@ def layer_shapes(levels, base, cin, cout):
     return shapes
 
 
-def forward(params, x, levels):
-    """Returns (y, cache) with the activations the backward pass needs."""
+def round_bf16(a):
+    """The values a float32 tensor would carry after rounding to bfloat16 (round to nearest even),
+    as float64: the operands of a BF16 tensor-core product."""
+    u = np.ascontiguousarray(np.asarray(a, dtype=np.float32)).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return u.view(np.float32).astype(np.float64)
+
+
+def forward(params, x, levels, bf16_operands=False):
+    """Returns (y, cache) with the activations the backward pass needs.  bf16_operands: every
+    convolution reads its input rounded to bfloat16 (the weights are expected BF16-representable
+    already), as a BF16 tensor-core convolution with FP32 accumulation does."""
+    rb = round_bf16 if bf16_operands else (lambda t: t)
     cache = []
     kept = []
     h = x
@@ -94,7 +105,7 @@ def forward(params, x, levels):
     for l in range(levels):
         for _ in range(2):
             w, b = params[p]
-            a = np.maximum(conv3d(h, w, b), 0.0)
+            a = np.maximum(conv3d(rb(h), w, b), 0.0)
             cache.append(("conv_relu", h, a))
             h = a
             p += 1
@@ -108,12 +119,12 @@ def forward(params, x, levels):
         h = np.concatenate([kept[l], u], axis=0)
         for _ in range(2):
             w, b = params[p]
-            a = np.maximum(conv3d(h, w, b), 0.0)
+            a = np.maximum(conv3d(rb(h), w, b), 0.0)
             cache.append(("conv_relu", h, a))
             h = a
             p += 1
     w, b = params[p]
-    y = conv3d(h, w, b)
+    y = conv3d(rb(h), w, b)
     cache.append(("conv", h))
     return y, cache
 
@@ -126,13 +137,15 @@ def masked_mse(y, t, mask):
     return float((r * r).sum() / count), 2.0 * r / count
 
 
-def backward(params, cache, dy, levels):
-    """Gradients [(dw, db)] in parameter order for the output gradient dy."""
+def backward(params, cache, dy, levels, bf16_operands=False):
+    """Gradients [(dw, db)] in parameter order for the output gradient dy.  bf16_operands: every
+    data gradient reads its input gradient rounded to bfloat16 (the weight gradients stay exact)."""
+    rb = round_bf16 if bf16_operands else (lambda t: t)
     grads = [None] * len(params)
     p = len(params) - 1
     kind, h = cache[-1]
     grads[p] = conv3d_wgrad(h, dy)
-    g = conv3d_dgrad(dy, params[p][0])
+    g = conv3d_dgrad(rb(dy), params[p][0])
     p -= 1
     skip_grads = {}
     idx = len(cache) - 2
@@ -142,7 +155,7 @@ def backward(params, cache, dy, levels):
             _, hin, a = cache[idx]
             g = g * (a > 0)
             grads[p] = conv3d_wgrad(hin, g)
-            g = conv3d_dgrad(g, params[p][0])
+            g = conv3d_dgrad(rb(g), params[p][0])
             p -= 1
             idx -= 1
         _, nkept = cache[idx]
@@ -158,7 +171,7 @@ def backward(params, cache, dy, levels):
             _, hin, a = cache[idx]
             g = g * (a > 0)
             grads[p] = conv3d_wgrad(hin, g)
-            g = conv3d_dgrad(g, params[p][0])
+            g = conv3d_dgrad(rb(g), params[p][0])
             p -= 1
             idx -= 1
     return grads

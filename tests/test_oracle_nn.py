@@ -1,8 +1,9 @@
 """Pins of the FP64 network reference used to check the warm-start kernels (CPU only).
 
 Each part is pinned by something other than itself: the convolution by scipy's correlate with
-periodic wrap, every linear piece by its adjoint identity, and the whole backward pass by central
-finite differences of the loss."""
+periodic wrap, every linear piece by its adjoint identity, the whole backward pass by central
+finite differences of the loss, and the BF16 rounding of tensor-core operands by torch's
+conversion."""
 import numpy as np
 import pytest
 
@@ -81,3 +82,13 @@ def test_network_gradients_match_finite_differences(levels):
                 fd = (lp - lm) / (2 * h)
                 an = grads[li][which][idx]
                 assert abs(fd - an) <= 1e-6 * max(1e-3, abs(fd)) + 1e-9, (li, which, idx, fd, an)
+
+
+def test_bf16_rounding_matches_torch():
+    """The reference's BF16 rounding (round to nearest even, on the float32 value) is torch's."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    a = np.concatenate([rng.standard_normal(20000) * 10.0 ** rng.integers(-6, 6, 20000),
+                        np.array([1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -(1.0 + 2.0 ** -8), 0.0, -0.0])])
+    want = torch.tensor(a.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(nn.round_bf16(a), want)
