@@ -1,7 +1,10 @@
 """GPU parity of the warm-start network kernels (through the C ABI) with the FP64 reference
 `oracle.nn_reference`: each kernel, then the whole U-Net forward and backward pass with the same
-(BF16-rounded) parameters.  FP32 accumulation: tolerance 1e-5 relative on outputs, 1e-4 on
-gradients."""
+(BF16-rounded) parameters.  The convolutions and data gradients run on the BF16 tensor cores, so
+the reference rounds their operands to BF16 the same way; products are then exact and only the
+FP32 accumulation differs: 1e-5 relative per kernel.  Through the whole network the GPU's FP32
+activations and the reference's FP64 ones can round to neighbouring BF16 values at a rare element,
+which the looser whole-network bounds (1e-3 outputs, 1e-2 gradients) allow for."""
 import ctypes
 
 import numpy as np
@@ -44,10 +47,14 @@ def test_conv_kernels_match_reference(cin, cout, dims):
     xd, wd, bd, gd = _dev(x), _dev(w), _dev(b), _dev(g)
     y = torch.empty((cout,) + dims, device="cuda")
     assert lib.dvm_nn_conv3d(_p(xd), _p(wd), _p(bd), _p(y), cin, cout, *dims, 0, _s()) == 0
-    assert _rel(y.cpu().numpy(), ref.conv3d(x.astype(np.float64), w.astype(np.float64), b.astype(np.float64))) < 1e-5
+    xr, wr, gr = ref.round_bf16(x), ref.round_bf16(w), ref.round_bf16(g)     # tensor-core operands
+    assert _rel(y.cpu().numpy(), ref.conv3d(xr, wr, b.astype(np.float64))) < 1e-5
     dx = torch.empty((cin,) + dims, device="cuda")
     assert lib.dvm_nn_conv3d_dgrad(_p(gd), _p(wd), _p(dx), cin, cout, *dims, 0, _s()) == 0
-    assert _rel(dx.cpu().numpy(), ref.conv3d_dgrad(g.astype(np.float64), w.astype(np.float64))) < 1e-5
+    assert _rel(dx.cpu().numpy(), ref.conv3d_dgrad(gr, wr)) < 1e-5
+    y2 = y.clone()                                   # accumulate = 1 adds to the old values
+    assert lib.dvm_nn_conv3d(_p(xd), _p(wd), _p(bd), _p(y2), cin, cout, *dims, 1, _s()) == 0
+    assert _rel(y2.cpu().numpy(), 2.0 * y.cpu().numpy()) < 1e-6
     n = lib.dvm_nn_wgrad_scratch_floats(cin, cout, *dims)
     scratch = torch.empty(n, device="cuda")
     dw = torch.full((cout, cin, 27), 0.5, device="cuda")
@@ -109,14 +116,15 @@ def test_unet_forward_and_backward_match_reference(levels, base, n):
     net.zero_grad()
     net.backward(dy)
     params = net.parameters_for_reference()
-    ry, cache = ref.forward(params, x.astype(np.float64), levels)
+    ry, cache = ref.forward(params, x.astype(np.float64), levels, bf16_operands=True)
     rloss, rdy = ref.masked_mse(ry, t.astype(np.float64), mask)
-    grads = ref.backward(params, cache, rdy, levels)
-    assert _rel(y.cpu().numpy(), ry) < 1e-5
-    assert loss == pytest.approx(rloss, rel=1e-5)
-    for i, (gw, gb) in enumerate(grads):
-        assert _rel(net.dw[i].cpu().numpy(), gw) < 1e-4, i
-        assert _rel(net.db[i].cpu().numpy(), gb) < 1e-4, i
+    grads = ref.backward(params, cache, rdy, levels, bf16_operands=True)
+    ey = _rel(y.cpu().numpy(), ry)
+    eg = max(max(_rel(net.dw[i].cpu().numpy(), gw), _rel(net.db[i].cpu().numpy(), gb)) for i, (gw, gb) in enumerate(grads))
+    print("U-Net levels %d base %d n %d: output rel err %.2e, worst gradient rel err %.2e" % (levels, base, n, ey, eg))
+    assert ey < 1e-3
+    assert loss == pytest.approx(rloss, rel=1e-3)
+    assert eg < 1e-2
 
 
 def test_adam_step_and_bf16_rounding():
