@@ -424,6 +424,40 @@ def run_pipeline(train=48, side=64, eval_side=128, eval_seeds=(10000, 10001), ev
     return res
 
 
+def time_step(levels=3, base=24, side=64, steps=50, seed=0):
+    """Time one training step (forward, masked loss, backward, Adam) and one forward pass of the
+    network on a random side^3 input: returns milliseconds per step and per forward pass."""
+    import time
+    import torch
+    net = UNet(levels=levels, base=base, seed=seed)
+    rng = np.random.default_rng(seed)
+    x = torch.tensor(rng.standard_normal((3, side, side, side)).astype(np.float32), device="cuda")
+    t = torch.tensor(rng.standard_normal((4, side, side, side)).astype(np.float32), device="cuda")
+    m = torch.tensor((rng.random(side ** 3) > 0.6).astype(np.float32), device="cuda")
+
+    def step():
+        net.zero_grad()
+        y = net.forward(x)
+        _, dy = net.loss_and_grad(y, t, m)
+        net.backward(dy)
+        net.step(lr=1e-4)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    ms_step = (time.perf_counter() - t0) / steps * 1e3
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        net.forward(x)
+    torch.cuda.synchronize()
+    ms_fwd = (time.perf_counter() - t0) / steps * 1e3
+    return {"levels": levels, "base": base, "side": side, "ms_per_train_step": ms_step, "ms_per_forward": ms_fwd}
+
+
 def main():
     import argparse
     import json
@@ -441,7 +475,13 @@ def main():
     ap.add_argument("--fp64-cap", type=int, default=0)
     ap.add_argument("--constant-lr", action="store_true")
     ap.add_argument("--out", default=None)
+    ap.add_argument("--time-step", action="store_true",
+                    help="only time a training step and a forward pass of the network (--levels, --base, --side)")
     a = ap.parse_args()
+    if a.time_step:
+        import json
+        print(json.dumps(time_step(a.levels, a.base, a.side)))
+        return
     res = run_pipeline(a.train, a.side, a.eval_side, tuple(a.eval_seeds), tuple(a.eval_kns), a.levels, a.base,
                        a.steps, a.lr, a.nv, a.fp64_cap, constant_lr=a.constant_lr)
     text = json.dumps(res, indent=1)
