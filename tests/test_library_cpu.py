@@ -140,3 +140,27 @@ def test_asymmetric_velocity_grid_is_rejected():
 
 def test_destroy_null_is_noop():
     dvm.load().dvm_destroy(None)
+
+
+def test_model_variant_options_are_validated_before_device_work():
+    v3, w3 = dvm.dvm_gh_velocity_grid(3, 4)
+    rock = np.zeros((4, 4, 4), bool)
+    rock[1:3, 1:3, 1:3] = True
+    for name in ("shakhov_prandtl", "es_prandtl"):
+        for bad in (-0.5, float("nan"), float("inf")):
+            st, ctx, msg = _create(rock, 0.1, v3, w3, temperature_term=1, **{name: bad})
+            assert st == dvm.DVM_EINVAL and not ctx.value and "Prandtl" in msg, (name, bad)
+        st, ctx, msg = _create(rock, 0.1, v3, w3, **{name: 2.0 / 3.0})             # no temperature term
+        assert st == dvm.DVM_EINVAL and "temperature term" in msg
+        st, ctx, msg = _create(rock, 0.1, v3, w3, temperature_term=1, specular_fraction=0.2, **{name: 2.0 / 3.0})
+        assert st == dvm.DVM_EINVAL and "not implemented" in msg
+        sub = (ctypes.c_int * 3)(2, 1, 1)
+        st, ctx, msg = _create(rock, 0.1, v3, w3, temperature_term=1, subdomains=sub, **{name: 2.0 / 3.0})
+        assert st == dvm.DVM_EINVAL and "not implemented" in msg
+    st, ctx, msg = _create(rock, 0.1, v3, w3, temperature_term=1, shakhov_prandtl=2.0 / 3.0, es_prandtl=2.0 / 3.0)
+    assert st == dvm.DVM_EINVAL and "one model" in msg
+    v2, w2 = dvm.dvm_gh_velocity_grid(2, 8)
+    flat = np.zeros((8, 8), bool)
+    flat[3:5, 3:5] = True
+    st, ctx, msg = _create(flat, 0.1, v2, w2, shakhov_prandtl=2.0 / 3.0)
+    assert st == dvm.DVM_EINVAL and not ctx.value
