@@ -152,6 +152,13 @@ void dvm_default_options(dvm_options* opt);
  * dvm_velocity_grid, sum = 1).  Host only; needs no GPU.  EINVAL on bad arguments. */
 dvm_status dvm_gh_velocity_grid(int dims, int n_per_axis, double* v, double* w);
 
+/* Effective pore size of a medium (Eq. 14, Sec. 4): the ratio r = Lstar / L is sqrt(12 k_inf / eps)
+ * in 2D (the channel with the medium's continuum permeability) and sqrt(8 k_inf / (pi eps)) in 3D
+ * (the tube), from the continuum-limit permeability k_inf (in units of L^2) and the porosity eps;
+ * the effective Knudsen number is Kn / r.  *ratio receives r.  Host only; needs no GPU.  EINVAL
+ * when dims is not 2 or 3, k_inf <= 0 or eps is outside (0, 1]. */
+dvm_status dvm_effective_pore_size(int dims, double k_inf, double porosity, double* ratio);
+
 /* Create a context for one problem (Sec. 2.1): geometry, Knudsen number kn > 0 (Eq. 1, reference
  * length = x1 extent, so dx = 1/n1 and nu = sqrt(pi)/(2 kn) in Eq. 3) and velocity grid.  The
  * state is the zero perturbation h = 0 with boundary data derived from it (the inflow ghosts of

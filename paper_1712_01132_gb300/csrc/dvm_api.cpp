@@ -1348,6 +1348,14 @@ void dvm_default_options(dvm_options* o) {
     o->check_interval = 100;
 }
 
+dvm_status dvm_effective_pore_size(int dims, double k_inf, double porosity, double* ratio) {
+    if (!ratio || (dims != 2 && dims != 3) || !(k_inf > 0.0) || !std::isfinite(k_inf) || !(porosity > 0.0) ||
+        !(porosity <= 1.0))
+        return DVM_EINVAL;
+    *ratio = dims == 2 ? std::sqrt(12.0 * k_inf / porosity) : std::sqrt(8.0 * k_inf / (3.14159265358979323846 * porosity));
+    return DVM_OK;
+}
+
 dvm_status dvm_gh_velocity_grid(int dims, int n, double* v, double* w) {
     if ((dims != 2 && dims != 3) || n < 2 || n > 128 || (n & 1) || !v || !w) return DVM_EINVAL;
     const int m = n / 2;

@@ -60,6 +60,7 @@ _P = ctypes.c_void_p
 _SIGNATURES = [
     ("dvm_default_options", None, [ctypes.POINTER(dvm_options)]),
     ("dvm_gh_velocity_grid", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P]),
+    ("dvm_effective_pore_size", ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, _P]),
     ("dvm_create", ctypes.c_int, [ctypes.POINTER(dvm_geometry), ctypes.c_double, ctypes.POINTER(dvm_velocity_grid),
                                   ctypes.POINTER(dvm_options), ctypes.POINTER(_P)]),
     ("dvm_create_batch", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(dvm_geometry), _P,
@@ -161,6 +162,14 @@ def dvm_default_options():
     o = dvm_options()
     load().dvm_default_options(ctypes.byref(o))
     return o
+
+
+def effective_pore_size(dims, k_inf, porosity):
+    """L*/L of Eq. 14 from the continuum permeability k_inf and the porosity (library routine);
+    the effective Knudsen number is Kn / (L*/L)."""
+    r = ctypes.c_double()
+    _check(load().dvm_effective_pore_size(int(dims), float(k_inf), float(porosity), ctypes.byref(r)))
+    return r.value
 
 
 def dvm_gh_velocity_grid(dims, n_per_axis):

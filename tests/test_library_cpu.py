@@ -164,3 +164,16 @@ def test_model_variant_options_are_validated_before_device_work():
     flat[3:5, 3:5] = True
     st, ctx, msg = _create(flat, 0.1, v2, w2, shakhov_prandtl=2.0 / 3.0)
     assert st == dvm.DVM_EINVAL and not ctx.value
+
+
+def test_effective_pore_size_reproduces_the_printed_effective_knudsen_factors():
+    """Eq. 14: Kn*/Kn = 1/(L*/L) for the four media of Sec. 4 (factors printed in the paper)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")
+    for row in json.load(open(path))["effective_knudsen"]:
+        r = dvm.effective_pore_size(row["dims"], row["k_inf"], row["porosity"])
+        assert 1.0 / r == pytest.approx(row["factor"], abs=0.006), row["geometry"]
+    for bad in ((4, 1e-3, 0.5), (2, 0.0, 0.5), (3, 1e-3, 0.0), (3, 1e-3, 1.5)):
+        with pytest.raises(dvm.DvmError):
+            dvm.effective_pore_size(*bad)
