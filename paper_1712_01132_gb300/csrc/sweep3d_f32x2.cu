@@ -10,6 +10,9 @@
 //               + a2 (K1y ... + E2) + a3 (K1z ... + E3) ],  S = a + b1 v1 + b2 v2 + b3 v3
 // (Eq. 10 solved for h with the upwind stencil of Eq. 9, source form).  The moment sums of a point
 // are formed in a fixed order (pair, lane tree, warps), independent of tile and pencil shapes.
+// Solid points are not swept; upstream data is staged per warp with cp.async; with 4-column tiles
+// the rows of a plane are walked two at a time, the upper row a column behind the lower; the next
+// tile's point data is loaded while the current tile is swept.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
