@@ -6,16 +6,20 @@ Metric: cell-velocity updates per second = (fluid cells) x (velocities) x (itera
 summed over the problems of the batch; config.full_grid_updates_per_s counts every grid cell.
 
 Workloads (--workload):
-  kn_sweep_512  (default) 2D random porous medium, 512 x 512 overlapping discs (seed 0, radii uniform
+  rock_128      (default) 3D Gaussian-field rock 128^3 (seed 0, correlation length 8, porosity 0.35,
+                percolating cluster), 16^3 = 4096 velocities, Kn = 0.5, FP32: the largest
+                configuration that runs on one GPU.
+  kn_sweep_512  2D random porous medium, 512 x 512 overlapping discs (seed 0, radii uniform
                 in [6, 20] cells, solid fraction 0.5, periodic, non-percolating fluid filled),
                 32 x 32 half-range Gauss-Hermite velocities (1024), Kn in {0.01, 0.1, 1, 10} as one
                 batched context; FP32 h and moments, FP64 wall sums, G_p and Err.
   disc_batch_64 64 seeded disc packings (seeds from 1000, sides uniform in 64..512, porosity
                 0.4-0.7, radii 6-20, Kn log-uniform in [0.01, 10]) in one batched context,
                 24 x 24 velocities, FP32.
-  rock_128      3D Gaussian-field rock 128^3 (seed 0, correlation length 8, porosity 0.35,
-                percolating cluster), 16^3 = 4096 velocities, Kn = 0.5, FP32.
-Tile shapes are chosen by the library's autotuner before the timed region.
+Tile shapes are chosen by the library's autotuner before the timed region.  The timed steps run
+the production loop: dvm_iterate with the CUDA-graph replay of each 100-iteration run; the graph
+carries event-record nodes around every sweep and finalize launch, from which the roofline's
+per-launch kernel time is read (same stream, same timed region).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
 
@@ -37,7 +41,7 @@ if ROOT not in sys.path:
 
 ITERS_PER_STEP = 100
 METRIC = "cell·velocity updates/s"
-SMS, FP32_LANES_PER_SM = 152, 128
+FP32_LANES_PER_SM = 128      # FP32 FMA lanes per SM on sm_100-family GPUs
 
 WORKLOADS = {
     "kn_sweep_512": {
@@ -230,9 +234,9 @@ def run_gpu(args):
 
     # ---------------- device-resident timing: inputs already in HBM
     s = dvm.Solver(masks, kns, v, w, **opts)
-    for _ in range(args.warmup):
+    s.profile_enable(True)                      # event nodes inside the captured graphs
+    for _ in range(args.warmup):                # (the first step captures the graph)
         s.iterate(ITERS_PER_STEP, 0.0)
-    s.profile_enable(True)                      # per-launch events (launches issued one by one)
     s.profile_read()
     sampler = ClockSampler(local, args.clocks_dir)
     sampler.start()
@@ -277,7 +281,8 @@ def run_gpu(args):
     # ---------------- roofline of the dominant kernel (sweep), FP32 ALU bound
     peaks = _peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    peak_tflops = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     sweep_avg_s = (sweep_ms / max(sweep_n, 1)) * 1e-3
     achieved = updates_per_iter * W["flops_per_update"] / sweep_avg_s / 1e12
     kernel = W["kernel"].replace("T1", str(t1))
@@ -286,8 +291,10 @@ def run_gpu(args):
                 "traffic": measured_traffic(args.workload if args.side == 128 else "", (t1, rows)),
                 "kernel": kernel, "avg_launch_ms": round(sweep_avg_s * 1e3, 4),
                 "share_of_step": round(sweep_ms / max(sweep_ms + fin_ms, 1e-9), 4),
-                "peak_basis": "FP32 FMA issue, 152 SMs x 128 lanes x 2 flop x %.0f MHz (derived from the "
-                              "measured max SM clock in MEASURED_PEAKS.json)" % sm_max,
+                "peak_basis": "FP32 FMA issue, %d SMs x 128 lanes x 2 flop x %.0f MHz (SM count from the "
+                              "device, max SM clock measured in MEASURED_PEAKS.json)" % (sms, sm_max),
+                "timing": "CUDA events recorded by the captured graph around every sweep launch, "
+                          "summed over the timed steps",
                 "flops_per_update": W["flops_per_update"], "updates_per_launch": updates_per_iter}
 
     out = None
@@ -389,7 +396,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="kn_sweep_512", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="rock_128", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clocks-dir", default=None,

@@ -86,25 +86,21 @@ typedef struct {
     void* alloc_user;
     /* Nonzero: dvm_iterate and dvm_step capture each run of iterations between two convergence
      * checks (memset, sweep and finalize launches) into a CUDA graph once and replay it (one graph
-     * per run length and starting ghost parity, kept until the context is destroyed).  Needs a
-     * non-NULL stream (the legacy default stream cannot be captured) and is not used while kernel
-     * timing is enabled; in both cases the launches are issued one by one.  The results are the
-     * same bits either way. */
+     * per run length, starting ghost parity and kernel-timing state, kept until the context is
+     * destroyed).  Needs a non-NULL stream (the legacy default stream cannot be captured; with
+     * NULL the launches are issued one by one).  With kernel timing enabled (dvm_profile_enable)
+     * the captured graph also records its own timing events around every sweep and finalize
+     * launch.  The results are the same bits either way. */
     int use_graph;
     /* Lagged-halo domain decomposition of Sec. 3.2 (the paper's MPI subdomains, emulated): the
      * domain is cut into c1 x c2 x c3 blocks (block s along axis j holds the points l with
      * floor(l c_j / n_j) = s); an upstream point in another block takes its value from the previous
      * iteration instead of the current sweep, so blocks sweep independently.  This changes the
      * iteration history (more iterations to converge) but not the fixed point.  0 or 1 = no cut
-     * (the exact serial iteration, the default).  Implemented: c1 and c2 in 2D, each block at least
-     * two points wide; c3 and 3D cuts are rejected with DVM_EINVAL. */
+     * (the exact serial iteration, the default).  Implemented: c1 x c2 in 2D and c1 x c2 x c3 in 3D,
+     * each block at least two points wide along every cut axis (DVM_EINVAL otherwise); 2D problems
+     * reject c3 > 1, and BF16 storage and the Shakhov / ES-BGK models reject any cut. */
     int subdomains[3];
-    /* Nonzero (2D FP32 without subdomains, at most 512 velocities per quadrant): every CTA of the
-     * sweep takes two consecutive bands, the upper one sweeping one tile behind the lower, and the
-     * lower band's top edge reaches the upper band through shared memory instead of HBM and a
-     * progress flag.  No counterpart in the paper; the same arithmetic in the same order, so the
-     * same result bits.  0 (default): one band per CTA.  Other configurations: DVM_EINVAL. */
-    int band_pairs;
     /* 3D: at most this many warps per sweep CTA (1..8; 0 = automatic, 8).  The velocities of an
      * octant are split into groups of 64 (FP32) or 32 (FP64) slots per warp, one CTA per group and
      * pencil, so fewer warps per CTA mean more, smaller CTAs per SM (more pencils in flight) at the
@@ -174,10 +170,18 @@ dvm_status dvm_create_batch(int nprob, const dvm_geometry* geometries, const dou
                             const dvm_velocity_grid* grid, const dvm_options* opt, dvm_ctx** out);
 
 /* Run iterations (Sec. 3.1) until every problem satisfies Err < tol at a check (Eq. 15 with the
- * check interval of the options) or max_iter iterations have run in this call.  iters_done (may
- * be NULL) receives the iterations run by this call, err_out (may be NULL) the largest Err at the
- * last check (HUGE_VAL before the first).  Returns DVM_OK when converged, DVM_NOT_CONVERGED at the
- * cap, ETIMEOUT/ECUDA/ENUMERIC on failure.  Synchronises the stream at every check. */
+ * check interval ci of the options) or max_iter iterations have run in this call.  Checks fall on
+ * the iteration counts that are multiples of ci (counted from context creation).  At a check of
+ * iteration l, Err = |k(l) - k(l')| / ((l - l') |k(l)|) with l' the previous check of the problem,
+ * so l - l' = ci as in Eq. 15, except after dvm_step moved the count past a multiple of ci without
+ * a check or after a warm start (then l' is the iteration of that event).  k(l') at the first
+ * check is the k of the start state: 0 for the zero start h = 0 (so the first Err is exactly 1/ci:
+ * a tolerance >= 1/ci stops at the first check), the warm start's own k after
+ * dvm_set_initial_at.  A problem with k(l) = 0 has Err = 0 if k(l') = 0 too (no flow path).
+ * iters_done (may be NULL) receives the iterations run by this call, err_out (may be NULL) the
+ * largest Err at the last check (HUGE_VAL before the first).  Returns DVM_OK when converged,
+ * DVM_NOT_CONVERGED at the cap, ETIMEOUT/ECUDA/ENUMERIC on failure.  Synchronises the stream at
+ * every check. */
 dvm_status dvm_iterate(dvm_ctx* ctx, int max_iter, double tol, int* iters_done, double* err_out);
 
 /* Enqueue n iterations on the stream without convergence checks or host synchronisation (the
@@ -245,8 +249,9 @@ dvm_status dvm_autotune(int nprob, const dvm_geometry* geometries, const double*
  * rho0: HOST pointer to [N] doubles, u0: HOST pointer to [dims][N] doubles, both in the paper's
  * variables (the layout dvm_moments returns; values at solid points are ignored).  The
  * caller keeps both buffers.  The context's iteration count keeps running; the next convergence
- * check of this problem compares with k = 0 (a restart of the Eq. 15 history).  Synchronises the
- * stream.  EINVAL (bad prob, NULL, non-finite value at a fluid point), ECUDA. */
+ * check of this problem compares with the k of the warm-start state, over the iterations run
+ * since (a restart of the Eq. 15 history).  Synchronises the stream.  EINVAL (bad prob, NULL,
+ * non-finite value at a fluid point), ECUDA. */
 dvm_status dvm_set_initial(dvm_ctx* ctx, const double* rho0, const double* u0);
 dvm_status dvm_set_initial_at(dvm_ctx* ctx, int prob, const double* rho0, const double* u0);
 
@@ -274,7 +279,10 @@ const char* dvm_last_error(const dvm_ctx* ctx);
 void dvm_destroy(dvm_ctx* ctx);
 
 /* Kernel timing (measurement support, not part of the method).  When enabled, every iteration
- * records CUDA events on the context's stream around its sweep and finalize launches.
+ * records CUDA events on the context's stream around its sweep and finalize launches (with
+ * use_graph, as event-record nodes of the captured graph: the graph path stays the one that runs;
+ * a replay's events are read at the next convergence check, dvm_sync or dvm_profile_read, and
+ * before the next replay of a timed graph, which then waits for the stream).
  * dvm_profile_read synchronises the stream, returns the summed event durations (milliseconds) and
  * launch counts since the last read (any pointer may be NULL) and restarts the accumulation. */
 dvm_status dvm_profile_enable(dvm_ctx* ctx, int on);
@@ -295,7 +303,10 @@ dvm_status dvm_transfer_bytes(const dvm_ctx* ctx, int64_t* h2d, int64_t* d2h);
  * Scratch: a file-scope device array sized for at most 2,097,152 points (8192 blocks of 256); larger
  * n returns DVM_EINVAL.  Each GPU that loads the library holds the array until the process exits.
  * The first call on a device looks up the array's address (cudaGetSymbolAddress) and caches it;
- * make that first call before any stream capture.  Calls share the array: calls whose kernels can
+ * make that first call before any stream capture.  The cached address belongs to the device's
+ * current context: after cudaDeviceReset (or any other re-creation of the primary context) it is
+ * stale, so do not call this function again in that process.  The result agrees with the k of the
+ * solver's own reduction to FP64 rounding (other block grouping).  Calls share the array: calls whose kernels can
  * overlap on the GPU race, so order them on one stream.  Calls no cudaMalloc/cudaFree.  Errors:
  * DVM_EINVAL (null pointer, n out of range, bad kn), DVM_ECUDA; message in
  * dvm_noalloc_last_error(). */

@@ -151,6 +151,10 @@ class Oracle:
             raise ValueError("oracle rejected the configuration")
         self._lib = lib
         self.k_history = []    # k after every iteration
+        # Eq. 15 history: k at the last check (or of the start state, 0 for h = 0) and its iteration
+        self.k_check = 0.0
+        self.it_check = 0
+        self.err = math.inf
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -171,19 +175,32 @@ class Oracle:
         return np.array(ks)
 
     def run(self, tol, max_iter, check_interval=100):
-        """Iterate until Err of Eq. 15 (checked every check_interval iterations) drops below tol or
-        max_iter iterations have run.  Returns (iterations, k, Err)."""
-        k_prev = self.permeability() if self.iterations else 0.0
-        err = math.inf
+        """Iterate until Err of Eq. 15 drops below tol at a check, or until the iteration count
+        reaches max_iter.  Returns (iterations, k, Err of the last check).
+
+        Sec. 3.1 steps iv-v: every check_interval iterations the permeability k(l) is evaluated and
+        Err(l) = |k(l) - k(l - check_interval)| / (check_interval |k(l)|).  Checks fall on the
+        iteration counts that are multiples of check_interval; k(l - check_interval) is the k of the
+        previous check, at the first check the k of the start state (0 for h = 0).  After a warm
+        start (set_initial) the previous check is the warm state, and the divisor becomes the
+        iterations actually run since it.  k(l) = 0 gives Err = 0 when the previous k is 0 as well
+        (no flow path), else infinity."""
         while self.iterations < max_iter:
-            n = min(check_interval, max_iter - self.iterations)
+            n = check_interval - self.iterations % check_interval
+            n = min(n, max_iter - self.iterations)
             ks = self.iterate(n)
-            k = ks[-1]
-            err = abs((k - k_prev) / k) / check_interval if k != 0 else math.inf
-            k_prev = k
-            if err < tol:
+            if self.iterations % check_interval != 0:
                 break
-        return self.iterations, self.permeability(), err
+            k = float(ks[-1])
+            gap = self.iterations - self.it_check
+            if k != 0.0:
+                self.err = abs((k - self.k_check) / k) / gap
+            else:
+                self.err = 0.0 if self.k_check == 0.0 else math.inf
+            self.k_check, self.it_check = k, self.iterations
+            if self.err < tol:
+                break
+        return self.iterations, self.permeability(), self.err
 
     def moments(self):
         """(rho [shape], u [dims, *shape]) in the paper's (jump-form) variables; solid = 0."""
@@ -230,6 +247,7 @@ class Oracle:
 
     def set_uniform(self, c):
         self._lib.ora_set_uniform(self._h, float(c))
+        self.k_check, self.it_check = self.permeability(), self.iterations
 
     def set_initial(self, rho0, u0):
         """Warm start: the state left by an iteration that produced h0 = rho0 + 2 u0 . v at every
@@ -238,6 +256,7 @@ class Oracle:
         u = np.ascontiguousarray(np.asarray(u0, dtype=np.float64).reshape(-1))
         assert r.size == self.solid.size and u.size == self.solid.size * self.dims
         self._lib.ora_set_initial(self._h, _ptr(r), _ptr(u))
+        self.k_check, self.it_check = self.permeability(), self.iterations
 
     def sweep_one(self, k):
         """Sweep velocity k from the current state without changing it; returns h [shape]."""

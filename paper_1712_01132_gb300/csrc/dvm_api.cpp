@@ -35,8 +35,6 @@ cudaError_t launch_warm2d(const Prob2D<T>*, int NL, int par, const double* qw2, 
 cudaError_t launch_sweep2d_f32x2(const SweepArgs2D<float>&, int T1, int xs, int grid, int NW, cudaStream_t);
 cudaError_t sweep2d_f32x2_occupancy(int T1, int xs, int spec, int NW, int max_rows, int* blocks_per_sm);
 int sweep2d_f32x2_max_rows(int T1, int NW);
-cudaError_t launch_sweep2d_pair(const SweepArgs2D<float>&, int T1, int grid, int NW, cudaStream_t);
-cudaError_t sweep2d_pair_occupancy(int T1, int NW, int max_rows, int NL, int* blocks_per_sm);
 int sweep2d_f32x2_velocities_per_lane();
 template <typename T> size_t sweep3d_smem(int T1, int NW, int R2, int R3, int tau, int spec, int shk);
 size_t sweep3d_f32x2_smem(int T1, int NW, int R2, int R3, int tau, int spec);
@@ -90,7 +88,6 @@ struct dvm_ctx {
     int prec = DVM_FP64;             // arithmetic precision (BF16 storage computes in FP32)
     bool bf16 = false;               // 3D ghosts and pencil edges stored as BF16
     bool xsub = false;               // 2D x1 subdomains (tile tables, lagged x1 halos)
-    bool pairs = false;              // 2D FP32: two consecutive bands per CTA
     bool sub3 = false;               // 3D lagged-halo subdomains (pencil and tile tables)
     bool tau3 = false;               // 3D temperature term of Eq. 2
     int nx3 = 0;                     // 3D model moments: 3 Shakhov, 6 ES-BGK (scalar sweep kernel)
@@ -122,7 +119,8 @@ struct dvm_ctx {
     int* status_host = nullptr;
     // iteration state
     long long iters = 0;
-    std::vector<double> k_check;     // k at the last check, per problem
+    std::vector<double> k_check;     // k at the last check (or at the start state), per problem
+    std::vector<long long> it_check; // iteration count of that k, per problem
     double last_err = HUGE_VAL;
     int sweep_grid = 1;
     long long timeout_ns = kDefaultTimeoutNs;
@@ -136,12 +134,20 @@ struct dvm_ctx {
     std::vector<cudaEvent_t> ev_pool;      // events owned by the context
     std::vector<cudaEvent_t> ev_marks;     // [3 per profiled iteration] before sweep, after sweep, after finalize
     long long h2d_bytes = 0, d2h_bytes = 0;
-    // CUDA graphs of runs of iterations, keyed by run length and starting ghost parity
+    // CUDA graphs of runs of iterations, keyed by run length, starting ghost parity and whether
+    // kernel timing was on at capture (then the graph records its own events, 3 per iteration)
     struct Graph {
         int n, parity;
+        bool prof;
         cudaGraphExec_t exec;
+        std::vector<cudaEvent_t> marks;
     };
     std::vector<Graph> graphs;
+    bool capturing = false;                  // inside the stream capture of a profiled graph
+    std::vector<cudaEvent_t> capture_marks;  // events recorded into the graph being captured
+    const std::vector<cudaEvent_t>* graph_pending = nullptr;   // marks of a replay not yet read
+    double acc_sweep_ms = 0.0, acc_fin_ms = 0.0;                 // timings read from graph replays
+    int64_t acc_sweep_n = 0, acc_fin_n = 0;
 };
 
 namespace {
@@ -264,7 +270,6 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     c->NL = 32 * vpl * c->NW;
     const int NL = c->NL;
     if (c->NW > 16) return fail(c, DVM_EINVAL, "too many velocities per quadrant");
-    if (c->pairs && 2 * c->NW > 8) return fail(c, DVM_EINVAL, "band pairs need at most 512 velocities per quadrant");
     // ---- tiles
     c->T1 = c->opt.tile_x1 ? c->opt.tile_x1 : 8;
     if (c->prec == DVM_FP32) {               // the packed FP32 kernel has 4- and 8-column tiles
@@ -532,12 +537,10 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     // ---- work items in band order (a band only waits for lower bands: deadlock-free tickets)
     int maxb = 0;
     for (int b = 0; b < c->nprob; ++b) maxb = std::max(maxb, probs[b].nbands);
-    // (with band pairs an item is the pair of bands 2 band, 2 band + 1)
-    const int step = c->pairs ? 2 : 1;
-    for (int band = 0; band * step < maxb; ++band)
+    for (int band = 0; band < maxb; ++band)
         for (int b = 0; b < c->nprob; ++b)
             for (int q = 0; q < NQ; ++q)
-                if (band * step < c->hp[b].qbands[q]) items.push_back({b, q, band, 0});
+                if (band < c->hp[b].qbands[q]) items.push_back({b, q, band, 0});
     c->nitems = (int)items.size();
     c->counters_bytes = sizeof(int) * (size_t)(1 + prog_total);
     c->counters_dev = (int*)dev_alloc(c, c->counters_bytes);
@@ -570,8 +573,7 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     c->probs_host.assign((const char*)probs.data(), (const char*)probs.data() + probs.size() * sizeof(Prob2D<T>));
     // ---- persistent grid size
     int per_sm = 0;
-    if (c->pairs) e = sweep2d_pair_occupancy(c->T1, 2 * c->NW, c->max_rows, c->NL, &per_sm);
-    else if (c->prec == DVM_FP32) e = sweep2d_f32x2_occupancy(c->T1, c->xsub, c->spec2 ? 1 : 0, c->NW, c->max_rows, &per_sm);
+    if (c->prec == DVM_FP32) e = sweep2d_f32x2_occupancy(c->T1, c->xsub, c->spec2 ? 1 : 0, c->NW, c->max_rows, &per_sm);
     else e = sweep2d_occupancy<T>(c->T1, c->xsub, c->spec2 ? 1 : 0, c->NW, c->max_rows, &per_sm);
     if (e != cudaSuccess) return cuda_fail(c, e, "occupancy");
     if (per_sm < 1) return fail(c, DVM_EINVAL, "sweep kernel does not fit on an SM with these tiles");
@@ -1048,6 +1050,13 @@ cudaEvent_t take_event(dvm_ctx* c) {
 
 cudaError_t mark(dvm_ctx* c) {
     if (!c->profile) return cudaSuccess;
+    if (c->capturing) {   // an event record node of the graph: recorded at every replay
+        cudaEvent_t ev = nullptr;
+        cudaError_t e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return e;
+        c->capture_marks.push_back(ev);
+        return cudaEventRecordWithFlags(ev, c->stream, cudaEventRecordExternal);
+    }
     cudaEvent_t ev = take_event(c);
     if (!ev) return cudaErrorMemoryAllocation;
     c->ev_marks.push_back(ev);
@@ -1055,7 +1064,6 @@ cudaError_t mark(dvm_ctx* c) {
 }
 
 cudaError_t sweep_launch(const SweepArgs2D<float>& a, dvm_ctx* c) {
-    if (c->pairs) return launch_sweep2d_pair(a, c->T1, c->sweep_grid, 2 * c->NW, c->stream);
     return launch_sweep2d_f32x2(a, c->T1, c->xsub, c->sweep_grid, c->NW, c->stream);
 }
 
@@ -1140,15 +1148,38 @@ dvm_status enqueue_iter(dvm_ctx* c) {
     return c->prec == DVM_FP32 ? enqueue_iter_2d<float>(c) : enqueue_iter_2d<double>(c);
 }
 
+// add the kernel times of the last profiled graph replay (its stream work must be complete)
+cudaError_t drain_graph_marks(dvm_ctx* c) {
+    if (!c->graph_pending) return cudaSuccess;
+    const std::vector<cudaEvent_t>& m = *c->graph_pending;
+    c->graph_pending = nullptr;
+    for (size_t i = 0; i + 2 < m.size(); i += 3) {
+        float a = 0.f, b = 0.f;
+        cudaError_t e;
+        if ((e = cudaEventElapsedTime(&a, m[i], m[i + 1])) != cudaSuccess ||
+            (e = cudaEventElapsedTime(&b, m[i + 1], m[i + 2])) != cudaSuccess)
+            return e;
+        c->acc_sweep_ms += a;
+        c->acc_fin_ms += b;
+        ++c->acc_sweep_n;
+        ++c->acc_fin_n;
+    }
+    return cudaSuccess;
+}
+
 void drop_graphs(dvm_ctx* c) {
-    for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graph_pending = nullptr;
+    for (auto& g : c->graphs) {
+        cudaGraphExecDestroy(g.exec);
+        for (cudaEvent_t ev : g.marks) cudaEventDestroy(ev);
+    }
     c->graphs.clear();
 }
 
 // n iterations: one by one, or through a captured CUDA graph (same launches, same bits)
 dvm_status run_iterations(dvm_ctx* c, int n) {
     if (n <= 0) return DVM_OK;
-    if (!c->opt.use_graph || c->profile || c->stream == nullptr) {
+    if (!c->opt.use_graph || c->stream == nullptr) {
         for (int i = 0; i < n; ++i) {
             dvm_status s = enqueue_iter(c);
             if (s != DVM_OK) return s;
@@ -1157,31 +1188,42 @@ dvm_status run_iterations(dvm_ctx* c, int n) {
     }
     const int par = (int)(c->iters & 1);
     cudaError_t e;
+    // a profiled graph re-records its own events: read the previous replay's first
+    if (c->graph_pending) {
+        if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "stream");
+        if ((e = drain_graph_marks(c)) != cudaSuccess) return cuda_fail(c, e, "event timing");
+    }
     for (auto& g : c->graphs)
-        if (g.n == n && g.parity == par) {
+        if (g.n == n && g.parity == par && g.prof == c->profile) {
             if ((e = cudaGraphLaunch(g.exec, c->stream)) != cudaSuccess) return cuda_fail(c, e, "graph launch");
+            if (g.prof) c->graph_pending = &g.marks;
             c->iters += n;
             return DVM_OK;
         }
     const long long it0 = c->iters;
     if ((e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
         return cuda_fail(c, e, "begin capture");
+    c->capturing = c->profile;
+    c->capture_marks.clear();
     dvm_status s = DVM_OK;
     for (int i = 0; i < n && s == DVM_OK; ++i) s = enqueue_iter(c);
+    c->capturing = false;
+    std::vector<cudaEvent_t> marks;
+    marks.swap(c->capture_marks);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(c->stream, &graph);
     c->iters = it0;     // the captured launches have not run yet
-    if (s != DVM_OK) {
-        if (graph) cudaGraphDestroy(graph);
-        return s;
-    }
-    if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
     cudaGraphExec_t exec = nullptr;
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
-    c->graphs.push_back({n, par, exec});
+    if (s == DVM_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (s != DVM_OK || e != cudaSuccess) {
+        for (cudaEvent_t ev : marks) cudaEventDestroy(ev);
+        if (s != DVM_OK) return s;
+        return cuda_fail(c, e, "graph capture");
+    }
+    c->graphs.push_back({n, par, c->profile, exec, std::move(marks)});
     if ((e = cudaGraphLaunch(exec, c->stream)) != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    if (c->profile) c->graph_pending = &c->graphs.back().marks;
     c->iters += n;
     return DVM_OK;
 }
@@ -1199,6 +1241,7 @@ dvm_status collect(dvm_ctx* c) {
     c->d2h_bytes += (long long)c->nprob * 3 * sizeof(double) + sizeof(int);
     e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "stream");
+    if ((e = drain_graph_marks(c)) != cudaSuccess) return cuda_fail(c, e, "event timing");
     if (*c->status_host != 0) {
         const int st = *c->status_host;
         cudaMemsetAsync(c->status_dev, 0, sizeof(int), c->stream);
@@ -1292,6 +1335,7 @@ struct StateHeader {
 struct StateProb {
     int64_t n[3];
     double kn, k_check;
+    int64_t it_check;
 };
 
 constexpr char kStateMagic[8] = {'D', 'V', 'M', 'S', 'T', 'A', 'T', 'E'};
@@ -1300,7 +1344,7 @@ StateHeader state_header(const dvm_ctx* c) {
     StateHeader h;
     std::memset(&h, 0, sizeof(h));
     std::memcpy(h.magic, kStateMagic, 8);
-    h.version = 1;
+    h.version = 2;
     h.dims = c->dims;
     h.precision = c->opt.precision;
     h.nprob = c->nprob;
@@ -1429,8 +1473,6 @@ dvm_status dvm_create_batch(int nprob, const dvm_geometry* geoms, const double* 
         return reject(DVM_EINVAL, "specular_fraction (1 - alpha of Eq. 5) must lie in [0, 1]");
     if (c->opt.specular_fraction > 0.0 && c->opt.precision == DVM_BF16_STORE)
         return reject(DVM_EINVAL, "BF16 storage is not implemented with alpha < 1");
-    if (c->opt.specular_fraction > 0.0 && c->opt.band_pairs)
-        return reject(DVM_EINVAL, "band pairs are not implemented with alpha < 1");
     c->spec2 = c->opt.specular_fraction > 0.0;
     if (!(c->opt.shakhov_prandtl >= 0.0) || !std::isfinite(c->opt.shakhov_prandtl))
         return reject(DVM_EINVAL, "shakhov_prandtl must be 0 (BGK) or a positive Prandtl number");
@@ -1448,10 +1490,6 @@ dvm_status dvm_create_batch(int nprob, const dvm_geometry* geoms, const double* 
         return reject(DVM_EINVAL, "choose one model: Shakhov or ES-BGK");
     c->nx3 = c->opt.shakhov_prandtl > 0.0 ? 3 : (c->opt.es_prandtl > 0.0 ? 6 : 0);
     if (c->opt.group_warps < 0) return reject(DVM_EINVAL, "group_warps must not be negative");
-    if (c->opt.band_pairs && (dims != 2 || c->opt.precision != DVM_FP32 || c->opt.subdomains[0] > 1 ||
-                              c->opt.subdomains[1] > 1))
-        return reject(DVM_EINVAL, "band pairs are implemented for 2D FP32 problems without subdomains");
-    c->pairs = c->opt.band_pairs != 0;
     c->dims = dims;
     c->nprob = nprob;
     c->prec = c->opt.precision == DVM_BF16_STORE ? DVM_FP32 : c->opt.precision;
@@ -1515,7 +1553,8 @@ dvm_status dvm_create_batch(int nprob, const dvm_geometry* geoms, const double* 
         delete c;
         return s;
     }
-    c->k_check.assign(nprob, 0.0);
+    c->k_check.assign(nprob, 0.0);   // k of the zero start h = 0
+    c->it_check.assign(nprob, 0);
     *out = c;
     return DVM_OK;
 }
@@ -1561,10 +1600,14 @@ dvm_status dvm_iterate(dvm_ctx* c, int max_iter, double tol, int* iters_done, do
                 if (iters_done) *iters_done = done;
                 return fail(c, DVM_ENUMERIC, "permeability is not finite");
             }
-            // Eq. 15: Err = |k(l) - k(l - ci)| / (ci |k(l)|)
-            const double err = (k != 0.0) ? std::fabs((k - c->k_check[b]) / k) / ci : (c->k_check[b] == 0.0 ? 0.0 : HUGE_VAL);
+            // Eq. 15: Err = |k(l) - k(l - ci)| / (ci |k(l)|), k(l - ci) the k of the previous check
+            // (of the start state at the first one).  Checks fall on multiples of ci; when
+            // dvm_step or a warm start moved the previous one, ci becomes the actual gap.
+            const double gap = (double)std::max(1LL, c->iters - c->it_check[b]);
+            const double err = (k != 0.0) ? std::fabs((k - c->k_check[b]) / k) / gap : (c->k_check[b] == 0.0 ? 0.0 : HUGE_VAL);
             worst = std::max(worst, err);
             c->k_check[b] = k;
+            c->it_check[b] = c->iters;
         }
         c->last_err = worst;
         if (worst < tol) {
@@ -1794,7 +1837,11 @@ dvm_status dvm_set_initial_at(dvm_ctx* c, int prob, const double* rho0, const do
     dvm_status s = run_finalize(c);
     if (s != DVM_OK) return s;
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "warm start");
-    c->k_check[prob] = 0.0;
+    // the next Eq. 15 check compares with the k of the warm-start state
+    s = collect(c);
+    if (s != DVM_OK) return s;
+    c->k_check[prob] = c->kval_host[3 * prob];
+    c->it_check[prob] = c->iters;
     return DVM_OK;
 }
 
@@ -1824,6 +1871,7 @@ dvm_status dvm_get_state(dvm_ctx* c, void* buf, size_t* bytes) {
         for (int j = 0; j < 3; ++j) sp.n[j] = c->hp[b].n[j];
         sp.kn = c->hp[b].kn;
         sp.k_check = c->k_check[b];
+        sp.it_check = c->it_check[b];
         std::memcpy(out, &sp, sizeof(sp));
         out += sizeof(sp);
     }
@@ -1846,12 +1894,13 @@ dvm_status dvm_set_state(dvm_ctx* c, const void* buf, size_t bytes) {
     std::memcpy(&h, in, sizeof(h));
     in += sizeof(h);
     const StateHeader mine = state_header(c);
-    if (std::memcmp(h.magic, kStateMagic, 8) != 0 || h.version != 1)
+    if (std::memcmp(h.magic, kStateMagic, 8) != 0 || h.version != 2)
         return fail(c, DVM_EINVAL, "not a state written by dvm_get_state");
     if (h.dims != mine.dims || h.precision != mine.precision || h.nprob != mine.nprob || h.nv != mine.nv ||
         h.NL != mine.NL || h.G != mine.G || h.order != mine.order || h.lateral != mine.lateral || h.iters < 0)
         return fail(c, DVM_EINVAL, "state was written by a context with other options or velocity grid");
     std::vector<double> kc(c->nprob);
+    std::vector<long long> ic(c->nprob);
     for (int b = 0; b < c->nprob; ++b) {
         StateProb sp;
         std::memcpy(&sp, in, sizeof(sp));
@@ -1859,7 +1908,9 @@ dvm_status dvm_set_state(dvm_ctx* c, const void* buf, size_t bytes) {
         for (int j = 0; j < 3; ++j)
             if (sp.n[j] != c->hp[b].n[j]) return fail(c, DVM_EINVAL, "state was written for other geometries");
         if (sp.kn != c->hp[b].kn) return fail(c, DVM_EINVAL, "state was written for other Knudsen numbers");
+        if (sp.it_check < 0 || sp.it_check > h.iters) return fail(c, DVM_EINVAL, "corrupt state (check iteration)");
         kc[b] = sp.k_check;
+        ic[b] = sp.it_check;
     }
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "set state");
@@ -1875,6 +1926,7 @@ dvm_status dvm_set_state(dvm_ctx* c, const void* buf, size_t bytes) {
     c->iters = h.iters;
     c->last_err = h.last_err;
     c->k_check = kc;
+    c->it_check = ic;
     return DVM_OK;
 }
 
@@ -1897,8 +1949,11 @@ dvm_status dvm_profile_read(dvm_ctx* c, double* sweep_ms, int64_t* sweep_n, doub
     if (!c) return DVM_EINVAL;
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "profile sync");
-    double ts = 0.0, tf = 0.0;
-    int64_t ns = 0, nf = 0;
+    if ((e = drain_graph_marks(c)) != cudaSuccess) return cuda_fail(c, e, "event timing");
+    double ts = c->acc_sweep_ms, tf = c->acc_fin_ms;
+    int64_t ns = c->acc_sweep_n, nf = c->acc_fin_n;
+    c->acc_sweep_ms = c->acc_fin_ms = 0.0;
+    c->acc_sweep_n = c->acc_fin_n = 0;
     for (size_t i = 0; i + 2 < c->ev_marks.size(); i += 3) {
         float a = 0.f, b = 0.f;
         if ((e = cudaEventElapsedTime(&a, c->ev_marks[i], c->ev_marks[i + 1])) != cudaSuccess ||

@@ -5,9 +5,11 @@
 // not allowed in every capture mode), code inside a framework or plugin whose caching allocator
 // must own every byte of device memory, and allocation-free steady-state loops with a fixed memory
 // budget.  dvm_permeability_noalloc serves them: it reduces a device array u1 to the permeability
-// k = (2/sqrt(pi)) Kn G_p and G_p (the mean of u1) with the same fixed-order FP64 two-stage
-// reduction as the solver's finalize step, but keeps its scratch (one FP64 partial sum per block
-// and a done-counter) in a file-scope device array instead of allocated memory.
+// k = (2/sqrt(pi)) Kn G_p and G_p (the mean of u1) with a fixed-order FP64 two-stage reduction
+// (block sums of 256 points, then the block sums in block order), and keeps its scratch (one FP64
+// partial sum per block and a done-counter) in a file-scope device array instead of allocated
+// memory.  The solver's finalize step has the same two stages with another block grouping (1024
+// points per block), so the two results agree to FP64 rounding, not bit for bit.
 //
 // The scratch array holds kMaxBlocks block sums, so one call accepts at most
 // kMaxBlocks * kBlock = 2,097,152 points (a 128^3 grid).  Every GPU that loads the library keeps

@@ -46,7 +46,6 @@ class dvm_options(ctypes.Structure):
         ("alloc_user", ctypes.c_void_p),
         ("use_graph", ctypes.c_int),
         ("subdomains", ctypes.c_int * 3),
-        ("band_pairs", ctypes.c_int),
         ("group_warps", ctypes.c_int),
         ("temperature_term", ctypes.c_int),
         ("specular_fraction", ctypes.c_double),
@@ -220,7 +219,7 @@ class _TorchAllocator:
 
 def make_options(precision="fp64", stencil_order=2, lateral="specular", check_interval=100, stream=None,
                  tile_x1=0, band_rows=0, torch_memory=True, use_graph=False, subdomains=(1, 1, 1),
-                 band_pairs=False, group_warps=0, temperature_term=False, specular_fraction=0.0,
+                 group_warps=0, temperature_term=False, specular_fraction=0.0,
                  shakhov_prandtl=0.0, es_prandtl=0.0):
     """dvm_options with torch's current stream (unless stream is given) and, by default, torch's
     caching allocator for device memory.  Returns (options, keepalive)."""
@@ -232,7 +231,6 @@ def make_options(precision="fp64", stencil_order=2, lateral="specular", check_in
     o.tile_x1 = int(tile_x1)
     o.band_rows = int(band_rows)
     o.use_graph = 1 if use_graph else 0
-    o.band_pairs = 1 if band_pairs else 0
     o.group_warps = int(group_warps)
     o.temperature_term = 1 if temperature_term else 0
     o.specular_fraction = float(specular_fraction)

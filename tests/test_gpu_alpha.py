@@ -134,8 +134,6 @@ def test_alpha_options_are_validated():
     for bad in (-0.1, 1.5, float("nan")):
         with pytest.raises(dvm.DvmError):
             dvm.Solver(mask, 0.2, v, w, specular_fraction=bad)
-    with pytest.raises(dvm.DvmError):
-        dvm.Solver(mask, 0.2, v, w, precision="fp32", band_pairs=True, specular_fraction=0.5)
     rock = inputs.gaussian_rock(8, seed=1, corr_len=1.5, porosity=0.6)
     v3, w3 = dvm.dvm_gh_velocity_grid(3, 4)
     with pytest.raises(dvm.DvmError):

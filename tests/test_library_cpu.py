@@ -110,20 +110,6 @@ def test_create_rejects_invalid_input_before_device_work():
     assert st == dvm.DVM_EINVAL
 
 
-def test_band_pairs_outside_2d_fp32_are_rejected_before_device_work():
-    v, w = dvm.dvm_gh_velocity_grid(2, 8)
-    mask = np.zeros((8, 8), bool)
-    mask[3:5, 3:5] = True
-    st, ctx, msg = _create(mask, 0.1, v, w, band_pairs=1)            # FP64
-    assert st == dvm.DVM_EINVAL and not ctx.value and "band pairs" in msg
-    sub = (ctypes.c_int * 3)(1, 2, 1)
-    st, ctx, msg = _create(mask, 0.1, v, w, band_pairs=1, precision=dvm.DVM_FP32, subdomains=sub)
-    assert st == dvm.DVM_EINVAL and "band pairs" in msg
-    v3, w3 = dvm.dvm_gh_velocity_grid(3, 4)
-    st, ctx, msg = _create(mask[None].repeat(4, 0), 0.1, v3, w3, band_pairs=1, precision=dvm.DVM_FP32)
-    assert st == dvm.DVM_EINVAL and "band pairs" in msg
-
-
 def test_asymmetric_velocity_grid_is_rejected():
     lib = dvm.load()
     v, w = dvm.dvm_gh_velocity_grid(2, 8)
