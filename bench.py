@@ -321,9 +321,35 @@ def run_gpu(args):
             "clocks": clocks,
             "permeability": [float(k) for k in ks] if len(ks) > 8 else dict(zip([str(k) for k in kns], ks)),
         }
+    if rank == 0 and ws == 1 and args.workload == "rock_128" and not args.no_time_to_tol:
+        out["config"]["time_to_tolerance"] = time_to_tolerance_section(args, opts)
     if ws > 1:
         dist.destroy_process_group()
     return out
+
+
+def time_to_tolerance_section(args, opts):
+    """The metric's second part on the learned-warm-start configuration: a 3D U-Net trained in this
+    run by the library's kernels on solver runs of seeded 64^3 rocks (Kn log-uniform in [0.05, 5]),
+    then on the held-out 128^3 rock (seed 10000, Kn 0.5) the iterations and wall time to Err < 1e-6
+    of the plain FP32, plain FP64 and network-warm FP32 starts, each with its true k error."""
+    import time
+    import torch
+    from paper_1712_01132_gb300 import inputs, warmstart
+    t0 = time.perf_counter()
+    data, t_data = warmstart.training_set(args.ttt_train, side=64, nv=16, log=lambda *a: None)
+    net, info = warmstart.train_network(data, levels=args.ttt_levels, base=args.ttt_base, steps=args.ttt_steps,
+                                        lr=2e-3, log=lambda *a: None)
+    del data
+    mask = inputs.gaussian_rock(128, seed=10000, corr_len=8.0, porosity=0.35)
+    fp32 = {k: opts[k] for k in ("tile_x1", "band_rows", "group_warps")}
+    res = warmstart.time_to_tolerance(mask, 0.5, 16, net=net, tol=1e-6, ref_tol=1e-8, fp64=True, max_iter=3000,
+                                      fp32_options=fp32)
+    torch.cuda.synchronize()
+    res.update({"geometry": "gaussian_rock(128, seed=10000, corr_len=8, porosity=0.35), held out",
+                "network": dict(info, train_runs=args.ttt_train, train_side=64, data_seconds=round(t_data, 1)),
+                "section_seconds": round(time.perf_counter() - t0, 1)})
+    return res
 
 
 def _oracle_sample(name, budget_iters=None):
@@ -370,6 +396,10 @@ def run_reference(args):
     sample, _, _ = _oracle_sample(args.workload, budget_iters=1)
     if args.workload == "disc_batch_64":
         sample = sample[:8]                       # a bounded slice of the batch per step
+    if args.workload == "rock_128":
+        # a slab of the rock (its first 16 x3 planes, all 4096 velocities) per step: one iteration
+        # of the whole rock takes ~16 s on 16 cores, too long for K + W steps
+        sample = [(sample[0][0][:16], sample[0][1])]
     for _ in range(args.warmup):
         _time_oracle(sample[:1], 1, W["dims"], W["n_axis"])
     units, dt = 0, 0.0
@@ -380,7 +410,8 @@ def run_reference(args):
     value = units / dt
     text = "per step one FP64 oracle iteration of %s" % (
         "the Kn=0.1 problem" if args.workload == "kn_sweep_512" else
-        "problems 0-7 of the batch" if args.workload == "disc_batch_64" else "the 128^3 rock")
+        "problems 0-7 of the batch" if args.workload == "disc_batch_64" else
+        "a 128 x 128 x 16 slab (x3 planes 0-15) of the 128^3 rock, 4096 velocities")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -403,6 +434,12 @@ def main():
                     help="directory for the raw nvidia-smi clock samples (default: the temp directory)")
     ap.add_argument("--side", type=int, default=128,
                     help="edge length of the rock_128 geometry (smaller only for profiling captures)")
+    ap.add_argument("--no-time-to-tol", action="store_true",
+                    help="skip the time-to-tolerance section (plain FP32 / FP64 / warm FP32 starts)")
+    ap.add_argument("--ttt-train", type=int, default=16, help="solver runs in the in-run training set")
+    ap.add_argument("--ttt-steps", type=int, default=400, help="training steps of the in-run network")
+    ap.add_argument("--ttt-levels", type=int, default=3)
+    ap.add_argument("--ttt-base", type=int, default=16)
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)

@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
     __shared__ int s_abort;
+    __shared__ int s_pre;      // the next tile's first upstream copies are already in flight
     const int NW = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -107,6 +108,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
         if (threadIdx.x == 0) {
             s_item = ld_volatile(a.status) ? a.nitems : atomicAdd(a.ticket, 1);
             s_abort = 0;
+            s_pre = 0;
         }
         for (int r = threadIdx.x; r < MROWS; r += blockDim.x) fmask[r] = 0u;    // masks of tile 0
         __syncthreads();
@@ -275,13 +277,56 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
             load_raw(0, raw);
             store_rec(0, 0, raw);
         }
+        // upstream data of a tile: x3 planes of its first plane (the pencil below in x3, ring slot,
+        // or ghost slot pi3.z: the x3 ghost layers, periodic or specular, Eq. 8, or the lagged halo
+        // of the block below) and x2 rows of each plane (likewise with pi2.z)
+        const bool zg = pi3.z >= 0, yg = pi2.z >= 0;
+        const float* zb = zg ? P->gz : P->ez;
+        const size_t zo = zg
+            ? ((((size_t)par * 8 + q) * P->ns3 + pi3.z) * n2 * n1) * 2 * NL
+            : ((((size_t)q * np2 + p2) * 2 * P->ns3 + (-1 - pi3.z)) * P->R2 * n1) * 2 * NL;
+        const float* yb = yg ? P->gy : P->ey;
+        const size_t yo = yg
+            ? ((((size_t)par * 8 + q) * P->ns2 + pi2.z) * n3 * n1) * 2 * NL
+            : ((((size_t)q * np3 + p3) * 2 * P->ns2 + (-1 - pi2.z)) * P->R3 * n1) * 2 * NL;
+        auto yrow = [&](int kk) -> size_t { return yg ? (size_t)(k0 + kk) * n1 : (size_t)kk * n1; };
+        // FP32: the x2 rows of plane kk go to slot kk & 1, copied while plane kk - 1 is swept (the
+        // tile's columns cc0 .. cc0 + wd - 1, records rb).  Upstream values are fetched only where
+        // the stencil of the point that reads them has a nonzero coefficient for them (record K1 /
+        // K2 of the first row or plane): values of solid points are never used, so they are neither
+        // stored nor fetched, and the staging holds zeros there.
+        auto issue_y = [&](int kk, int cc0, int wd, const float* rb) {
+            const size_t rb0 = yrow(kk);
+            for (int m = half; m < 2 * wd; m += 2) {
+                const int layer = m / wd;
+                const int i = m - layer * wd;
+                const bool need = rb[(size_t)(kk * MR2 * T1 + i) * RF + 10 + layer] != 0.f;
+                cp_async16_or_zero(eb + ((((size_t)warp * 2 + (kk & 1)) * 2 + layer) * T1 + i) * kPL + 4 * hl,
+                                   yb + yo + ((rb0 + cc0 + i) * 2 + layer) * NL + lw, need);
+            }
+            cp_async_commit();
+        };
+        // the x3 planes below the tile's first plane into the plane staging (committed with y(0))
+        auto issue_z = [&](int cc0, int wd, const float* rb) {
+            for (int m = half; m < nr2 * 2 * wd; m += 2) {
+                const int jl = m / wd;               // jj * 2 + layer
+                const int i = m - jl * wd;
+                const size_t row = zg ? ((size_t)(j0 + (jl >> 1)) * n1 + (cc0 + i)) : ((size_t)(jl >> 1) * n1 + (cc0 + i));
+                const bool need = rb[(size_t)((jl >> 1) * T1 + i) * RF + 12 + (jl & 1)] != 0.f;
+                cp_async16_or_zero(pb + (((size_t)warp * MR2 * 2 + jl) * T1 + i) * kPL + 4 * hl,
+                                   zb + zo + (row * 2 + (jl & 1)) * NL + lw, need);
+            }
+        };
         for (int t = 0; t < ntiles; ++t) {
             const int4 ti = tile_info(t);
             const int c0 = ti.x;
             const int width = ti.y;
             RawPoint3 nxt[kRawRounds];
             if (t + 1 < ntiles) load_raw(t + 1, nxt);
-            if (threadIdx.x == 0) {
+            // z and y(0) of this tile were issued at the end of the previous one (its neighbours had
+            // already published this tile then)
+            const bool pre = s_pre != 0;
+            if (threadIdx.x == 0 && !pre) {
                 bool ok = true;
                 if (pi2.z < 0) ok = wait_geq(prog + p3 * np2 + p2 - 1, t + 1, a.status, a.timeout_ns);
                 if (ok && pi3.z < 0) ok = wait_geq(prog + (p3 - 1) * np2 + p2, t + 1, a.status, a.timeout_ns);
@@ -310,6 +355,10 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                         cp_async16(carry + ((size_t)(warp * MROWS + kk * MR2 + (jl >> 1)) * 2 + (jl & 1)) * kPL + 4 * hl,
                                    P->gx1 + gxo + (row * 2 + (jl & 1)) * NL + lw);
                     }
+                    if (pre) {   // the first group is already committed: complete these copies here
+                        cp_async_commit();
+                        cp_async_wait<0>();
+                    }
                 } else {
                     for (int kk = 0; kk < nr3; ++kk)
                         for (int jj = 0; jj < nr2; ++jj) {
@@ -320,36 +369,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                         }
                 }
             }
-            // upstream data of the tile: x3 planes of its first plane (the pencil below in x3, ring
-            // slot, or ghost slot pi3.z: the x3 ghost layers, periodic or specular, Eq. 8, or the
-            // lagged halo of the block below) and x2 rows of each plane (likewise with pi2.z)
-            const bool zg = pi3.z >= 0, yg = pi2.z >= 0;
-            const float* zb = zg ? P->gz : P->ez;
-            const size_t zo = zg
-                ? ((((size_t)par * 8 + q) * P->ns3 + pi3.z) * n2 * n1) * 2 * NL
-                : ((((size_t)q * np2 + p2) * 2 * P->ns3 + (-1 - pi3.z)) * P->R2 * n1) * 2 * NL;
-            const float* yb = yg ? P->gy : P->ey;
-            const size_t yo = yg
-                ? ((((size_t)par * 8 + q) * P->ns2 + pi2.z) * n3 * n1) * 2 * NL
-                : ((((size_t)q * np3 + p3) * 2 * P->ns2 + (-1 - pi2.z)) * P->R3 * n1) * 2 * NL;
-            auto yrow = [&](int kk) -> size_t { return yg ? (size_t)(k0 + kk) * n1 : (size_t)kk * n1; };
             auto rbuf_rec = [&](int kk, int jj, int i) -> const float* { return recb + (size_t)((kk * MR2 + jj) * T1 + i) * RF; };
-            // FP32: the x2 rows of plane kk go to slot kk & 1, copied while plane kk - 1 is swept
-            // Upstream values are fetched only where the stencil of the point that reads them has a
-            // nonzero coefficient for them (record K1 / K2 of the first row or plane): values of
-            // solid points are never used, so they are neither stored nor fetched, and the staging
-            // holds zeros there.
-            auto issue_y = [&](int kk) {
-                const size_t rb0 = yrow(kk);
-                for (int m = half; m < 2 * width; m += 2) {
-                    const int layer = m / width;
-                    const int i = m - layer * width;
-                    const bool need = rbuf_rec(kk, 0, i)[10 + layer] != 0.f;
-                    cp_async16_or_zero(eb + ((((size_t)warp * 2 + (kk & 1)) * 2 + layer) * T1 + i) * kPL + 4 * hl,
-                                       yb + yo + ((rb0 + c0 + i) * 2 + layer) * NL + lw, need);
-                }
-                cp_async_commit();
-            };
             if constexpr (BF) {
                 for (int jj = 0; jj < nr2; ++jj)
                     for (int i = 0; i < width; ++i) {
@@ -361,16 +381,9 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                         *reinterpret_cast<float2*>(d + (size_t)T1 * kPL) =
                             rc[13] != 0.f ? PS::ld(zb, zo + (row * 2 + 1) * NL + lv, xs) : make_float2(0.f, 0.f);
                     }
-            } else {
-                for (int m = half; m < nr2 * 2 * width; m += 2) {
-                    const int jl = m / width;            // jj * 2 + layer
-                    const int i = m - jl * width;
-                    const size_t row = zg ? ((size_t)(j0 + (jl >> 1)) * n1 + (c0 + i)) : ((size_t)(jl >> 1) * n1 + (c0 + i));
-                    const bool need = rbuf_rec(0, jl >> 1, i)[12 + (jl & 1)] != 0.f;
-                    cp_async16_or_zero(pb + (((size_t)warp * MR2 * 2 + jl) * T1 + i) * kPL + 4 * hl,
-                                       zb + zo + (row * 2 + (jl & 1)) * NL + lw, need);
-                }
-                issue_y(0);
+            } else if (!pre) {
+                issue_z(c0, width, recb);
+                issue_y(0, c0, width, recb);
             }
             for (int kk = 0; kk < nr3; ++kk) {
                 // x2 upstream rows of the first row of this plane
@@ -392,7 +405,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                 } else {
                     __syncwarp();                        // slot (kk + 1) & 1 was last read at plane kk - 1
                     if (kk + 1 < nr3) {
-                        issue_y(kk + 1);
+                        issue_y(kk + 1, c0, width, recb);
                         cp_async_wait<1>();              // all but the copies of plane kk + 1
                     } else {
                         cp_async_wait<0>();
@@ -638,9 +651,28 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                     }
             }
             if (t + 1 < ntiles) store_rec(t + 1, (t + 1) & 1, nxt);
+            if (threadIdx.x == 0) {   // have the neighbours published the next tile already? (one poll)
+                int ready = 0;
+                if (!BF && t + 1 < ntiles) {
+                    ready = 1;
+                    if (pi2.z < 0 && ld_acquire_gpu(prog + p3 * np2 + p2 - 1) < t + 2) ready = 0;
+                    if (ready && pi3.z < 0 && ld_acquire_gpu(prog + (p3 - 1) * np2 + p2) < t + 2) ready = 0;
+                }
+                s_pre = ready;
+            }
             __syncthreads();
             if (threadIdx.x == 0 && it != a.withhold_item) {
                 publish_gpu(prog + p3 * np2 + p2, t + 1);
+            }
+            if constexpr (!BF) {
+                // the plane staging and y slot 0 are free (the x3 edges were stored from the staging
+                // before the barrier): start the next tile's first copies now
+                if (s_pre) {
+                    const int4 tn = tile_info(t + 1);
+                    const float* rbn = rec + (size_t)((t + 1) & 1) * MROWS * T1 * RF;
+                    issue_z(tn.x, tn.y, rbn);
+                    issue_y(0, tn.x, tn.y, rbn);
+                }
             }
             // moment partials of this octant and group: warp sums in warp order
             const int tot = nr3 * nr2 * width * NM;
@@ -651,9 +683,10 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                 const int r = pi / width;
                 const int jj = r % nr2;
                 const int kk = r / nr2;
+                // solid points keep the zero partials of the start state (no reader uses them)
+                if (!((fm_cur[kk * MR2 + jj] >> i) & 1u)) continue;
                 float s = 0.f;
-                if ((fm_cur[kk * MR2 + jj] >> i) & 1u)
-                    for (int w = 0; w < NW; ++w) s += part[((size_t)(w * MROWS + kk * MR2 + jj) * T1 + i) * NM + mm];
+                for (int w = 0; w < NW; ++w) s += part[((size_t)(w * MROWS + kk * MR2 + jj) * T1 + i) * NM + mm];
                 const int ic = c0 + i;
                 const int x = s1n ? n1 - 1 - ic : ic;
                 const int y = s2n ? n2 - 1 - (j0 + jj) : (j0 + jj);

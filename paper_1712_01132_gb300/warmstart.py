@@ -336,16 +336,11 @@ def solve_to(mask, kn, v, w, tol, max_iter, initial=None, **options):
     return it, dt, k, rho, u, st
 
 
-def run_pipeline(train=48, side=64, eval_side=128, eval_seeds=(10000, 10001), eval_kns=(0.05, 0.5),
-                 levels=4, base=16, steps=1500, lr=2e-3, nv=16, fp64_cap=0, seed=0, log=print, constant_lr=False):
-    """The learned-warm-start experiment: solver runs on `train` seeded side^3 Gaussian-field rocks
-    (correlation length 8, porosity 0.35, seeds 0, 1, ... without the non-percolating ones, Kn
-    log-uniform in [0.05, 5], nv^3 velocities, FP32,
-    Err < 1e-6) give the training set; the network is trained with Adam; held-out eval_side^3 rocks
-    (seeds eval_seeds) are then solved from the plain start and from the network's prediction (same
-    precision, FP32; the warm time includes features, inference and dvm_set_initial) and, when
-    fp64_cap > 0, from the plain start in FP64 for at most fp64_cap iterations (time per iteration
-    measured).  Returns a dict of the results."""
+def training_set(train=48, side=64, nv=16, seed=0, kn_range=(0.05, 5.0), log=print):
+    """Solver runs that make the training set: `train` seeded side^3 Gaussian-field rocks
+    (correlation length 8, porosity 0.35, seeds 0, 1, ... without the non-percolating ones), Kn
+    log-uniform in kn_range, nv^3 velocities, FP32, Err < 1e-6.  Returns (list of (features, target,
+    fluid mask) device tensors, seconds)."""
     import time
     import torch
     from . import inputs
@@ -362,19 +357,27 @@ def run_pipeline(train=48, side=64, eval_side=128, eval_seeds=(10000, 10001), ev
         rock_seed += 1
         if mask.all():
             continue
-        kn = float(10 ** rng.uniform(math.log10(0.05), math.log10(5.0)))
+        kn = float(10 ** rng.uniform(math.log10(kn_range[0]), math.log10(kn_range[1])))
         it, dt, k, rho, u, st = solve_to(mask, kn, v, w, 1e-6, 5000, **opts)
         data.append((torch.from_numpy(features(mask, kn)).cuda(), torch.from_numpy(targets(mask, kn, rho, u)).cuda(),
                      torch.from_numpy((~mask).astype(np.float32).ravel()).cuda()))
     t_data = time.perf_counter() - t0
     log("training set: %d runs in %.1f s" % (train, t_data))
+    return data, t_data
+
+
+def train_network(data, levels=4, base=16, steps=1500, lr=2e-3, constant_lr=False, seed=0, log=print):
+    """Adam on the masked MSE of the standardised targets, one sample per step in turn.  Returns
+    (network, dict with the step count, seconds and mean loss of the first and last epochs)."""
+    import time
+    import torch
     net = UNet(levels=levels, base=base, seed=seed)
     net.set_standardisation([(t.cpu().numpy(), m.cpu().numpy()) for _, t, m in data])
     data = [(x, net.standardise(t), m) for x, t, m in data]
     losses = []
     t0 = time.perf_counter()
     for step in range(steps):
-        x, t, m = data[step % train]
+        x, t, m = data[step % len(data)]
         net.zero_grad()
         y = net.forward(x)
         loss, dy = net.loss_and_grad(y, t, m)
@@ -384,41 +387,82 @@ def run_pipeline(train=48, side=64, eval_side=128, eval_seeds=(10000, 10001), ev
         if step % 200 == 0:
             log("step %d loss %.4e" % (step, loss))
     torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
-    res = {"train_runs": train, "train_side": side, "levels": levels, "base": base, "steps": steps,
-           "train_seconds": t_train, "data_seconds": t_data,
-           "loss_first_epoch": float(np.mean(losses[:train])), "loss_last_epoch": float(np.mean(losses[-train:])),
-           "eval": []}
+    n = len(data)
+    return net, {"levels": levels, "base": base, "steps": steps, "train_seconds": time.perf_counter() - t0,
+                 "loss_first_epoch": float(np.mean(losses[:n])), "loss_last_epoch": float(np.mean(losses[-n:]))}
+
+
+def time_to_tolerance(mask, kn, nv=16, net=None, tol=1e-6, ref_tol=1e-9, fp64=True, max_iter=20000,
+                      fp32_options=None):
+    """Iterations and wall time to Err < tol (Eq. 15, every 100 iterations) of the plain FP32 start,
+    the plain FP64 start and (with a network) the warm FP32 start, on one geometry.  Wall time is
+    the time of dvm_iterate (plus features, inference and dvm_set_initial for the warm start);
+    context creation is reported separately.  The true permeability error of each stop
+    (|k - k_ref| / k_ref, k_ref from the plain FP32 run continued to Err < ref_tol) shows whether
+    Err < tol stopped near the fixed point."""
+    import time
+    import torch
+    v, w = dvm.dvm_gh_velocity_grid(3, nv)
+    o32 = dict(precision="fp32", lateral="periodic", use_graph=True)
+    o32.update(fp32_options or {})
+    out = {"tol": tol, "kn": kn, "fluid_cells": int((~np.asarray(mask, bool)).sum()), "velocities": len(w)}
+
+    def run(opts, initial_fn=None, continue_to=None):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = dvm.Solver(mask, kn, v, w, **opts)
+        torch.cuda.synchronize()
+        setup = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        extra = 0.0
+        if initial_fn is not None:
+            s.set_initial(*initial_fn())
+            extra = time.perf_counter() - t0
+        st, it, err = s.iterate(max_iter, tol)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        row = {"iterations": it, "seconds": dt, "setup_seconds": setup, "k": s.permeability()[0], "err": err,
+               "converged": st == dvm.DVM_OK}
+        if initial_fn is not None:
+            row["features_inference_seconds"] = extra
+        if continue_to is not None:
+            st2, it2, err2 = s.iterate(max_iter, continue_to)
+            row["k_ref"] = s.permeability()[0]
+            row["k_ref_iterations"] = it + it2
+            row["k_ref_err"] = err2
+        s.close()
+        return row
+
+    plain = run(o32, continue_to=ref_tol)
+    k_ref = plain.pop("k_ref")
+    out["k_ref"] = {"k": k_ref, "iterations": plain.pop("k_ref_iterations"), "err": plain.pop("k_ref_err"),
+                    "how": "plain FP32 run continued to Err < %g" % ref_tol}
+    out["plain_fp32"] = plain
+    if fp64:
+        out["plain_fp64"] = run(dict(precision="fp64", lateral="periodic", use_graph=True))
+    if net is not None:
+        out["warm_fp32"] = run(o32, initial_fn=lambda: to_initial(mask, kn, predict(net, mask, kn)))
+    for key in ("plain_fp32", "plain_fp64", "warm_fp32"):
+        if key in out:
+            out[key]["true_k_error"] = abs(out[key]["k"] - k_ref) / abs(k_ref)
+    return out
+
+
+def run_pipeline(train=48, side=64, eval_side=128, eval_seeds=(10000, 10001), eval_kns=(0.05, 0.5),
+                 levels=4, base=16, steps=1500, lr=2e-3, nv=16, fp64=False, seed=0, log=print, constant_lr=False):
+    """The learned-warm-start experiment: training set (training_set), network (train_network), then
+    on held-out eval_side^3 rocks (seeds eval_seeds, Kn eval_kns) the plain and warm starts to
+    Err < 1e-6 (time_to_tolerance, with the plain FP64 start when fp64 is set)."""
+    from . import inputs
+    data, t_data = training_set(train, side, nv, seed, log=log)
+    net, info = train_network(data, levels, base, steps, lr, constant_lr, seed, log=log)
+    res = dict(info, train_runs=train, train_side=side, data_seconds=t_data, eval=[])
     for sd in eval_seeds:
         mask = inputs.gaussian_rock(eval_side, seed=sd, corr_len=8.0, porosity=0.35)
         for kn in eval_kns:
-            it0, dt0, k0, rho_c, u_c, st0 = solve_to(mask, kn, v, w, 1e-6, 20000, **opts)
-            torch.cuda.synchronize()
-            ta = time.perf_counter()
-            init = to_initial(mask, kn, predict(net, mask, kn))
-            torch.cuda.synchronize()
-            t_inf = time.perf_counter() - ta
+            row = time_to_tolerance(mask, kn, nv, net=net, fp64=fp64)
+            row["seed"] = sd
             fl = ~mask
-            x1 = np.broadcast_to(np.arange(mask.shape[-1]) / mask.shape[-1], mask.shape)
-            rc = (rho_c + x1)[fl]
-            rp = (init[0] + x1)[fl]
-            pred_err = {"u": float(np.linalg.norm((init[1] - u_c)[:, fl]) / np.linalg.norm(u_c[:, fl])),
-                        "rho": float(np.linalg.norm((rp - rp.mean()) - (rc - rc.mean())) / np.linalg.norm(rc - rc.mean())),
-                        "k_pred_over_k": float(init[1][0].mean() / u_c[0].mean())}
-            it1, dt1, k1, _, _, st1 = solve_to(mask, kn, v, w, 1e-6, 20000, initial=init, **opts)
-            row = {"seed": sd, "kn": kn, "plain_fp32": {"iterations": it0, "seconds": dt0, "k": k0, "status": st0},
-                   "warm_fp32": {"iterations": it1, "seconds": dt1 + t_inf, "inference_seconds": t_inf, "k": k1,
-                                 "status": st1}, "k_rel_diff": abs(k1 - k0) / abs(k0), "prediction_error": pred_err}
-            if fp64_cap > 0:
-                s = dvm.Solver(mask, kn, v, w, precision="fp64", lateral="periodic")
-                torch.cuda.synchronize()
-                tb = time.perf_counter()
-                st2, it2, err2 = s.iterate(fp64_cap, 1e-6)
-                torch.cuda.synchronize()
-                dt2 = time.perf_counter() - tb
-                row["plain_fp64"] = {"iterations_run": it2, "seconds": dt2, "status": st2, "err": err2,
-                                     "seconds_per_iteration": dt2 / max(it2, 1)}
-                s.close()
             log(row)
             res["eval"].append(row)
     return res
@@ -472,7 +516,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1500)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--nv", type=int, default=16)
-    ap.add_argument("--fp64-cap", type=int, default=0)
+    ap.add_argument("--fp64", action="store_true", help="also time the plain FP64 start to tolerance")
     ap.add_argument("--constant-lr", action="store_true")
     ap.add_argument("--out", default=None)
     ap.add_argument("--time-step", action="store_true",
@@ -483,7 +527,7 @@ def main():
         print(json.dumps(time_step(a.levels, a.base, a.side)))
         return
     res = run_pipeline(a.train, a.side, a.eval_side, tuple(a.eval_seeds), tuple(a.eval_kns), a.levels, a.base,
-                       a.steps, a.lr, a.nv, a.fp64_cap, constant_lr=a.constant_lr)
+                       a.steps, a.lr, a.nv, a.fp64, constant_lr=a.constant_lr)
     text = json.dumps(res, indent=1)
     if a.out:
         with open(a.out, "w") as f:
