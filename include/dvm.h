@@ -319,17 +319,30 @@ const char* dvm_noalloc_last_error(void);
  * only where the source iteration of Sec. 3.1 starts, never its fixed point.  All pointers are
  * DEVICE pointers to FP32 single-sample tensors in channel-major layout t[c][z][y][x] (x fastest,
  * d x h x w voxels); work is enqueued on `stream` (cudaStream_t, NULL = legacy default stream) and
- * nothing is allocated.  Convolutions are 3 x 3 x 3 with periodic padding, weights w[co][ci][27]
+ * nothing is allocated (the callers pass scratch buffers).  Convolutions are 3 x 3 x 3 with periodic padding, weights w[co][ci][27]
  * with tap index (kz * 3 + ky) * 3 + kx for offsets kz, ky, kx in -1..1, biases b[co] (may be
  * NULL), FP32 accumulation.  accumulate != 0 adds into the output instead of overwriting it.
  * Errors: DVM_EINVAL (NULL pointer, non-positive size, odd extent for the 2x resampling, scratch
  * too small), DVM_ECUDA (launch failure). */
-/* y = conv(x, w) + b: y[co][v] = b[co] + sum_ci sum_k w[co][ci][k] x[ci][v + off(k)] */
+/* y = conv(x, w) + b: y[co][v] = b[co] + sum_ci sum_k w[co][ci][k] x[ci][v + off(k)].  Runs on the
+ * tcgen05 tensor cores with BF16 operands (x and w rounded to nearest even) and FP32 accumulation.
+ * scratch: DEVICE buffer of at least dvm_nn_conv3d_scratch_bytes(cin, cout, d, h, w_) bytes (the
+ * padded BF16 copy of x and the BF16 weights; any alignment), reused by the next call on the same
+ * stream.  w_ (the x extent) must be at most 128 (DVM_EINVAL otherwise). */
 dvm_status dvm_nn_conv3d(const float* x, const float* w, const float* b, float* y, int cin, int cout,
-                         int d, int h, int w_, int accumulate, void* stream);
-/* data gradient: dx[ci][v] (+)= sum_co sum_k w[co][ci][k] dy[co][v - off(k)] */
+                         int d, int h, int w_, int accumulate, void* scratch, int64_t scratch_bytes,
+                         void* stream);
+/* data gradient: dx[ci][v] (+)= sum_co sum_k w[co][ci][k] dy[co][v - off(k)], the same tensor-core
+ * convolution of dy with the channel roles transposed and the taps mirrored; scratch as above. */
 dvm_status dvm_nn_conv3d_dgrad(const float* dy, const float* w, float* dx, int cin, int cout, int d,
-                               int h, int w_, int accumulate, void* stream);
+                               int h, int w_, int accumulate, void* scratch, int64_t scratch_bytes,
+                               void* stream);
+/* scratch bytes that serve both dvm_nn_conv3d and dvm_nn_conv3d_dgrad of this shape (0 for a
+ * non-positive size) */
+int64_t dvm_nn_conv3d_scratch_bytes(int cin, int cout, int d, int h, int w_);
+/* Synchronises the stream and returns the convolutions' device status word: 0, or DVM_ETIMEOUT when
+ * a bounded wait inside a convolution expired (its output is then not written).  Clears it. */
+int dvm_nn_status(void* stream);
 /* weight and bias gradients: dw[co][ci][k] (+)= sum_v dy[co][v] x[ci][v + off(k)], db[co] (+)=
  * sum_v dy[co][v] (db may be NULL); summed in a fixed order.  scratch: device buffer of at least
  * dvm_nn_wgrad_scratch_floats(...) floats. */

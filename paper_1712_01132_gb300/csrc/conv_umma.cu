@@ -1,0 +1,425 @@
+// conv_umma.cu -- the warm-start network's 3 x 3 x 3 periodic convolutions as implicit GEMMs on the
+// fifth-generation tensor cores (tcgen05.mma, BF16 operands, FP32 accumulators in tensor memory).
+//
+//   y[co][v] (+)= b[co] + sum_ci sum_k w[co][ci][k] x[ci][v + off(k)]
+//
+// GEMM view: M = voxels (a tile of `by` whole x rows of one z plane, at most 128 voxels, one per
+// TMEM lane), N = output channels (a tile of BN), K = 27 taps x input channels (chunks of 32).
+// Before the GEMM the input is written once as a BF16, channels-last copy with a one-voxel
+// periodic halo, xp[z + 1][y + 1][x + 1][c] (channels padded to a multiple of 32 with zeros), and
+// the weights as BF16 wb[tap][co][ci] (padded likewise): the A operand of a tap and channel chunk
+// is then one box of xp (32 channels x W x by x 1) and the B operand one box of wb (32 x BN x 1),
+// both brought to shared memory by the tensor memory accelerator (cp.async.bulk.tensor, 64-byte
+// swizzle, the K-major layout tcgen05.mma reads).  One thread streams the boxes through a ring of
+// stages, one thread issues the MMAs (K = 16 each, accumulating in TMEM) and releases a stage when
+// its MMAs complete (tcgen05.commit); the four warps then read the accumulators back (tcgen05.ld,
+// each warp its 32 lanes) and write y channel-major.  Every wait is bounded (a device status word
+// records an expiry and the CTA returns after releasing its tensor memory).
+//
+// The data gradient is the same convolution of dy with the transposed channel roles and mirrored
+// taps (wb[tap][ci][co] = w[co][ci][26 - tap]).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+
+namespace dvm_nn {
+
+constexpr int kBM = 128;       // GEMM rows per tile (TMEM lanes)
+constexpr int kBK = 32;        // input channels per K chunk: 64-byte rows
+constexpr int kStages = 4;
+constexpr int kThreads = 128;
+constexpr long long kTimeoutNs = 2000000000LL;
+
+struct ConvGeom {
+    int cin, cout;        // channels of this convolution's input and output
+    int D, H, W;
+    int cinp, coutp;      // padded to multiples of kBK and of BN
+    int by, ytiles;       // x rows per tile, tiles per z plane
+    int nk;               // K chunks per tap
+    int accumulate;
+};
+
+__device__ int g_conv_status;   // nonzero after a bounded wait expired
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtime() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// bounded wait for the phase with the given parity to complete; false on expiry
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    const unsigned a = smem_u32(bar);
+    unsigned long long t0 = 0;
+    for (unsigned it = 0;; ++it) {
+        unsigned done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(a), "r"(parity) : "memory");
+        if (done) return true;
+        if ((it & 255u) == 0u) {
+            const unsigned long long t = gtime();
+            if (it == 0) t0 = t;
+            else if ((long long)(t - t0) > kTimeoutNs) return false;
+            if (*reinterpret_cast<volatile int*>(&g_conv_status) != 0 && it > 0) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4, %5}], [%6];"
+                 ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+                   "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, uint64_t* bar) {
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4}], [%5];"
+                 ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2),
+                   "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// shared-memory matrix descriptor of a K-major operand in the 64-byte swizzled layout: rows of 64
+// bytes, eight-row groups 512 bytes apart (stride byte offset), descriptor version 1
+__device__ __forceinline__ uint64_t smem_desc_sw64(const void* p) {
+    const uint64_t addr = (smem_u32(p) >> 4) & 0x3FFFu;
+    return addr | (1ull << 16) | ((uint64_t)(512 >> 4) << 32) | (1ull << 46) | (4ull << 61);
+}
+
+// instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, M = 128, N = BN
+template <int BN>
+__device__ __forceinline__ unsigned idesc_bf16() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(BN >> 3) << 17) | ((unsigned)(kBM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(unsigned tmem_d, uint64_t adesc, uint64_t bdesc, unsigned idesc, int acc) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                 ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+                 : "memory");
+}
+
+// the mbarrier completes one phase when every MMA this thread issued so far has finished
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// MT row tiles per CTA share every B box and write MT accumulators (TMEM columns t BN .. t BN + BN - 1)
+template <int BN, int MT>
+__global__ void __launch_bounds__(kThreads) conv3d_umma_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                               const __grid_constant__ CUtensorMap tmB,
+                                                               const float* __restrict__ bias, float* __restrict__ y,
+                                                               const ConvGeom g) {
+    constexpr int kABytes = kBM * kBK * 2;            // 8 KB per row tile
+    constexpr int kBBytes = BN * kBK * 2;
+    constexpr int kStageBytes = MT * kABytes + kBBytes;   // a multiple of 1024 (BN multiple of 16)
+    constexpr unsigned kTmemCols = MT * BN <= 32 ? 32u : (MT * BN <= 64 ? 64u : (MT * BN <= 128 ? 128u : 256u));
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* sbase = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+    __shared__ unsigned s_tmem;
+    __shared__ int s_fail;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n0 = blockIdx.y * BN;
+    const int rows = g.by * g.W;                      // valid GEMM rows of a tile (<= 128)
+    int tz[MT], ty0[MT];                              // row tile t: z plane and first y row
+#pragma unroll
+    for (int t = 0; t < MT; ++t) {
+        const int tile = blockIdx.x * MT + t;         // beyond the grid: z >= D, never written
+        tz[t] = tile / g.ytiles;
+        ty0[t] = (tile - tz[t] * g.ytiles) * g.by;
+    }
+
+    if (rows < kBM) {   // rows beyond the boxes stay zero in every stage (the boxes never write them)
+        for (int i = threadIdx.x * 16; i < kStages * kStageBytes; i += kThreads * 16)
+            *reinterpret_cast<uint4*>(sbase + i) = make_uint4(0u, 0u, 0u, 0u);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // before the tensor cores read them
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(kTmemCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem_d = s_tmem;
+    const int niter = 27 * g.nk;
+    const unsigned box_bytes = (unsigned)(MT * kBK * 2 * g.W * g.by + kBBytes);
+
+    if (warp == 0 && lane == 0) {
+        // producer: the A box of (tap, chunk) and the B box of the same (tap, chunk) per stage
+        for (int i = 0; i < niter; ++i) {
+            const int s = i % kStages;
+            if (i >= kStages && !mbar_wait(&empty[s], ((i / kStages) - 1) & 1)) {
+                s_fail = 1;
+                break;
+            }
+            const int tap = i / g.nk, kc = i - tap * g.nk;
+            const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+            unsigned char* st = sbase + (size_t)s * kStageBytes;
+            mbar_expect_tx(&full[s], box_bytes);
+#pragma unroll
+            for (int t = 0; t < MT; ++t)
+                tma_load_4d(st + t * kABytes, &tmA, kc * kBK, 1 + dx, ty0[t] + 1 + dy, tz[t] + 1 + dz, &full[s]);
+            tma_load_3d(st + MT * kABytes, &tmB, kc * kBK, n0, tap, &full[s]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: K = 16 per instruction, two per chunk; the first one overwrites the accumulator
+        const unsigned idesc = idesc_bf16<BN>();
+        for (int i = 0; i < niter; ++i) {
+            const int s = i % kStages;
+            if (!mbar_wait(&full[s], (i / kStages) & 1)) {
+                s_fail = 1;
+                break;
+            }
+            tc_fence_after();
+            const unsigned char* st = sbase + (size_t)s * kStageBytes;
+            const uint64_t bd = smem_desc_sw64(st + MT * kABytes);
+#pragma unroll
+            for (int t = 0; t < MT; ++t) {
+                const uint64_t ad = smem_desc_sw64(st + t * kABytes);
+#pragma unroll
+                for (int kk = 0; kk < kBK / 16; ++kk)    // 32 bytes of K per step: +2 in the 16-byte address field
+                    umma_bf16(tmem_d + t * BN, ad + 2 * kk, bd + 2 * kk, idesc, (i > 0 || kk > 0) ? 1 : 0);
+            }
+            umma_commit(&empty[s]);
+        }
+        umma_commit(&done);
+    }
+    __syncwarp();
+    const bool ok = mbar_wait(&done, 0);
+    tc_fence_after();
+    if (!ok || s_fail) {
+        if (threadIdx.x == 0) atomicCAS(&g_conv_status, 0, -4);
+    } else {
+        // accumulator row r of tile t = voxel r of the tile (TMEM lane r), column t BN + j = output
+        // channel n0 + j
+        const int r = warp * 32 + lane;
+        const long long V = (long long)g.D * g.H * g.W;
+#pragma unroll
+        for (int t = 0; t < MT; ++t) {
+        const int yy = ty0[t] + r / g.W, xx = r % g.W;
+        const bool valid = r < rows && yy < g.H && tz[t] < g.D;
+        const long long v = ((long long)tz[t] * g.H + yy) * g.W + xx;
+#pragma unroll
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            unsigned a[16];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                         "%13, %14, %15}, [%16];"
+                         : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]),
+                           "=r"(a[7]), "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]),
+                           "=r"(a[14]), "=r"(a[15])
+                         : "r"(tmem_d + ((unsigned)(32 * warp) << 16) + (unsigned)(t * BN + c0))
+                         : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (valid) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int co = n0 + c0 + j;
+                    if (co < g.cout) {
+                        const float val = __uint_as_float(a[j]) + (bias ? bias[co] : 0.f);
+                        float* d = y + (long long)co * V + v;
+                        *d = g.accumulate ? *d + val : val;
+                    }
+                }
+            }
+        }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_d), "r"(kTmemCols) : "memory");
+}
+
+// xp[pz][py][px][c] = bf16(x[c][pz - 1][py - 1][px - 1]) with periodic wrap, zero for c >= cin.  A
+// block transposes 32 padded voxels of one x row by 32 channels through shared memory, so that both
+// the channel-major reads and the channels-last writes are coalesced.
+__global__ void __launch_bounds__(256) pad_bf16_kernel(const float* __restrict__ x, __nv_bfloat16* __restrict__ xp,
+                                                       int cin, int cinp, int D, int H, int W) {
+    __shared__ float t[32][33];
+    const int px0 = blockIdx.x * 32;
+    const int prow = blockIdx.y;                        // padded (pz, py)
+    const int py = prow % (H + 2), pz = prow / (H + 2);
+    const int c0 = blockIdx.z * 32;
+    const int sy = py == 0 ? H - 1 : (py == H + 1 ? 0 : py - 1);
+    const int sz = pz == 0 ? D - 1 : (pz == D + 1 ? 0 : pz - 1);
+    const long long V = (long long)D * H * W;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    {
+        const int px = px0 + tx;
+        const int sx = px == 0 ? W - 1 : (px == W + 1 ? 0 : px - 1);
+        for (int cc = ty; cc < 32; cc += 8) {
+            const int c = c0 + cc;
+            t[cc][tx] = (c < cin && px < W + 2) ? x[(long long)c * V + ((long long)sz * H + sy) * W + sx] : 0.f;
+        }
+    }
+    __syncthreads();
+    for (int vv = ty; vv < 32; vv += 8) {
+        const int px = px0 + vv;
+        if (px < W + 2)
+            xp[(((long long)pz * (H + 2) + py) * (W + 2) + px) * cinp + c0 + tx] = __float2bfloat16_rn(t[tx][vv]);
+    }
+}
+
+// wb[tap][n][c] = bf16(w[n sn + c sc + (flip ? 26 - tap : tap)]) for n < nout, c < nin, else 0
+__global__ void weights_bf16_kernel(const float* __restrict__ w, __nv_bfloat16* __restrict__ wb, int nout, int nin,
+                                    int noutp, int ninp, int sn, int sc, int flip) {
+    const long long total = 27LL * noutp * ninp;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int c = (int)(i % ninp);
+    const int n = (int)((i / ninp) % noutp);
+    const int tap = (int)(i / ((long long)ninp * noutp));
+    float val = 0.f;
+    if (n < nout && c < nin) val = w[(long long)n * sn + (long long)c * sc + (flip ? 26 - tap : tap)];
+    wb[i] = __float2bfloat16_rn(val);
+}
+
+using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
+
+EncodeFn encode_fn() {
+    static EncodeFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+    });
+    return fn;
+}
+
+inline int bn_for(int cout) { return cout <= 32 ? 32 : (cout <= 64 ? 64 : 128); }
+inline long long align1k(long long b) { return (b + 1023) & ~1023LL; }
+
+template <int BN, int MT>
+cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const float* bias, float* y, const ConvGeom& g,
+                      cudaStream_t st) {
+    constexpr int kStageBytes = MT * kBM * kBK * 2 + BN * kBK * 2;
+    const int smem = kStages * kStageBytes + 1024;
+    auto kern = conv3d_umma_kernel<BN, MT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int tiles = g.D * g.ytiles;
+    dim3 grid((unsigned)((tiles + MT - 1) / MT), (unsigned)(g.coutp / BN));
+    kern<<<grid, kThreads, smem, st>>>(ta, tb, bias, y, g);
+    return cudaGetLastError();
+}
+
+}  // namespace dvm_nn
+
+// Scratch bytes of one convolution with nin input and nout output channels on a d x h x w grid: the
+// padded BF16 input copy and the BF16 weights, each 1 KB aligned.
+long long conv_umma_scratch_bytes(int nin, int nout, int d, int h, int w) {
+    using namespace dvm_nn;
+    const int cinp = (nin + kBK - 1) / kBK * kBK;
+    const int bn = bn_for(nout);
+    const int coutp = (nout + bn - 1) / bn * bn;
+    return align1k((long long)(d + 2) * (h + 2) * (w + 2) * cinp * 2) + align1k(27LL * coutp * cinp * 2) + 1024;
+}
+
+// One convolution (flip = 0: y = conv(x, w) + b with w[nout][nin][27]; flip = 1: the data gradient,
+// nout = the forward input channels, w[nin][nout][27] read with mirrored taps).  Returns a CUDA error,
+// cudaErrorInvalidValue for a grid wider than 128 voxels, or cudaErrorNotSupported when the driver
+// lacks the tensor-map encoder.
+cudaError_t conv_umma(const float* x, const float* w, const float* bias, float* y, int nin, int nout, int d, int h,
+                      int w_, int flip, int accumulate, void* scratch, long long scratch_bytes, cudaStream_t st) {
+    using namespace dvm_nn;
+    if (w_ > kBM || scratch_bytes < conv_umma_scratch_bytes(nin, nout, d, h, w_)) return cudaErrorInvalidValue;
+    EncodeFn enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    ConvGeom g;
+    g.cin = nin;
+    g.cout = nout;
+    g.D = d;
+    g.H = h;
+    g.W = w_;
+    g.cinp = (nin + kBK - 1) / kBK * kBK;
+    const int bn = bn_for(nout);
+    g.coutp = (nout + bn - 1) / bn * bn;
+    g.by = kBM / w_ < h ? kBM / w_ : h;
+    g.ytiles = (h + g.by - 1) / g.by;
+    g.nk = g.cinp / kBK;
+    g.accumulate = accumulate;
+    const uintptr_t base = (reinterpret_cast<uintptr_t>(scratch) + 1023) & ~uintptr_t(1023);
+    __nv_bfloat16* xp = reinterpret_cast<__nv_bfloat16*>(base);
+    __nv_bfloat16* wb =
+        reinterpret_cast<__nv_bfloat16*>(base + align1k((long long)(d + 2) * (h + 2) * (w_ + 2) * g.cinp * 2));
+    pad_bf16_kernel<<<dim3((unsigned)((w_ + 2 + 31) / 32), (unsigned)((d + 2) * (h + 2)), (unsigned)(g.cinp / 32)), 256, 0,
+                      st>>>(x, xp, nin, g.cinp, d, h, w_);
+    const int sn = flip ? 27 : nin * 27;     // forward: w[n][c][k]; gradient: w[c][n][26 - k]
+    const int sc = flip ? nout * 27 : 27;
+    weights_bf16_kernel<<<(unsigned)((27LL * g.coutp * g.cinp + 255) / 256), 256, 0, st>>>(w, wb, nout, nin, g.coutp,
+                                                                                          g.cinp, sn, sc, flip);
+    CUtensorMap ta, tb;
+    {
+        const cuuint64_t dims[4] = {(cuuint64_t)g.cinp, (cuuint64_t)(w_ + 2), (cuuint64_t)(h + 2), (cuuint64_t)(d + 2)};
+        const cuuint64_t strides[3] = {(cuuint64_t)g.cinp * 2, (cuuint64_t)g.cinp * 2 * (w_ + 2),
+                                       (cuuint64_t)g.cinp * 2 * (w_ + 2) * (h + 2)};
+        const cuuint32_t box[4] = {(cuuint32_t)kBK, (cuuint32_t)w_, (cuuint32_t)g.by, 1u};
+        const cuuint32_t es[4] = {1u, 1u, 1u, 1u};
+        if (enc(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, xp, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+            CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    {
+        const cuuint64_t dims[3] = {(cuuint64_t)g.cinp, (cuuint64_t)g.coutp, 27u};
+        const cuuint64_t strides[2] = {(cuuint64_t)g.cinp * 2, (cuuint64_t)g.cinp * 2 * g.coutp};
+        const cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)bn, 1u};
+        const cuuint32_t es[3] = {1u, 1u, 1u};
+        if (enc(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, wb, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+            CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    if (bn == 32) return launch_bn<32, 2>(ta, tb, bias, y, g, st);
+    if (bn == 64) return launch_bn<64, 2>(ta, tb, bias, y, g, st);
+    return launch_bn<128, 1>(ta, tb, bias, y, g, st);
+}
+
+// the device status word of the convolutions (nonzero after a bounded wait expired); cleared on read
+int conv_umma_status(cudaStream_t st) {
+    int v = 0;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return -3;
+    if (cudaMemcpyFromSymbol(&v, dvm_nn::g_conv_status, sizeof(int)) != cudaSuccess) return -3;
+    if (v) {
+        const int zero = 0;
+        cudaMemcpyToSymbol(dvm_nn::g_conv_status, &zero, sizeof(int));
+    }
+    return v;
+}

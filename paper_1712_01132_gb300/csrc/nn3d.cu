@@ -7,9 +7,10 @@
 // Convolutions are 3 x 3 x 3 with periodic padding (the media are periodic), weights w[co][ci][27]
 // (tap index (kz * 3 + ky) * 3 + kx, offsets -1..1).  The network keeps FP32 master weights and
 // runs forward and backward on their BF16 roundings (see dvm_nn_adam).  The convolutions and their
-// data gradients are implicit GEMMs on the BF16 tensor cores (mma.sync m16n8k16, FP32
-// accumulation: the input activations or gradients are rounded to BF16 on their way into shared
-// memory); the weight gradients are FP32 reductions on the CUDA cores.
+// data gradients are implicit GEMMs on the fifth-generation tensor cores (conv_umma.cu: tcgen05.mma
+// with BF16 operands brought in by the tensor memory accelerator, FP32 accumulators in tensor
+// memory; the input activations or gradients are rounded to BF16 once, into a padded copy); the
+// weight gradients are FP32 reductions on the CUDA cores.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -17,110 +18,16 @@
 
 #include "../../include/dvm.h"
 
+long long conv_umma_scratch_bytes(int nin, int nout, int d, int h, int w);
+cudaError_t conv_umma(const float* x, const float* w, const float* bias, float* y, int nin, int nout, int d, int h,
+                      int w_, int flip, int accumulate, void* scratch, long long scratch_bytes, cudaStream_t st);
+int conv_umma_status(cudaStream_t st);
+
 namespace {
 
 constexpr int kBlock = 256;
 
 __device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
-
-// y[co][v] = b[co] + sum_ci sum_k w[co][ci][k] x[ci][v + off(k)]   (periodic); flip != 0 uses the
-// mirrored taps w[..][26 - k] (the data gradient of the forward convolution); accumulate != 0 adds
-// to y instead of overwriting it.  An implicit GEMM on the BF16 tensor cores: a CTA computes 128
-// voxels x 32 output channels (M x N), looping over 16 input channels x one tap at a time (K).  Per step the
-// 128 x 16 slice of the input at the tap's offset (A, one voxel per thread) and the 16 x 32 slice of
-// the weights (B) are rounded to BF16 into shared memory; each of the four warps multiplies its 32
-// voxels by the 32 channels with eight mma.sync.m16n8k16 (FP32 accumulators in registers).
-constexpr int kTcM = 128;      // voxels per CTA (4 warps x 32)
-constexpr int kTcN = 32;       // output channels per CTA
-constexpr int kTcK = 16;       // input channels per step
-constexpr int kTcRow = 24;     // bf16 per shared-memory row (16 used, padded against bank conflicts)
-
-__device__ __forceinline__ uint32_t lds_u32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
-
-__device__ __forceinline__ void mma_bf16_16816(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                               uint32_t b0, uint32_t b1) {
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};"
-                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-__global__ void __launch_bounds__(kTcM) conv3d_tc_kernel(const float* __restrict__ x, const float* __restrict__ w,
-                                                         const float* __restrict__ b, float* __restrict__ y, int cin,
-                                                         int cout, int D, int H, int W, int wco_stride,
-                                                         int wci_stride, int flip, int accumulate) {
-    __shared__ __align__(16) __nv_bfloat16 As[kTcM][kTcRow];   // A[voxel][input channel]
-    __shared__ __align__(16) __nv_bfloat16 Bs[kTcN][kTcRow];   // B[output channel][input channel]
-    const long long V = (long long)D * H * W;
-    const long long v0 = (long long)blockIdx.x * kTcM;
-    const int co0 = blockIdx.y * kTcN;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = lane >> 2, t4 = lane & 3;
-    const long long vt = v0 + tid;          // the voxel this thread stages
-    const bool vin = vt < V;
-    int xi = 0, yi = 0, zi = 0;
-    if (vin) {
-        xi = (int)(vt % W);
-        yi = (int)((vt / W) % H);
-        zi = (int)(vt / ((long long)W * H));
-    }
-    float acc[2][kTcN / 8][4];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < kTcN / 8; ++nt)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) acc[mt][nt][i] = 0.f;
-    for (int ci0 = 0; ci0 < cin; ci0 += kTcK) {
-        for (int k = 0; k < 27; ++k) {
-            const int dz = k / 9 - 1, dy = (k / 3) % 3 - 1, dx = k % 3 - 1;
-            const long long nb = vin ? ((long long)wrap(zi + dz, D) * H + wrap(yi + dy, H)) * W + wrap(xi + dx, W) : 0;
-            const int kk = flip ? 26 - k : k;
-#pragma unroll
-            for (int c2 = 0; c2 < kTcK; c2 += 2) {
-                const int ci = ci0 + c2;
-                const float va = (vin && ci < cin) ? __ldg(x + (long long)ci * V + nb) : 0.f;
-                const float vb = (vin && ci + 1 < cin) ? __ldg(x + (long long)(ci + 1) * V + nb) : 0.f;
-                *reinterpret_cast<__nv_bfloat162*>(&As[tid][c2]) = __floats2bfloat162_rn(va, vb);
-            }
-            for (int e = tid; e < kTcN * kTcK; e += kTcM) {
-                const int n = e / kTcK, c = e % kTcK;
-                const int co = co0 + n, ci = ci0 + c;
-                const float wv = (co < cout && ci < cin)
-                    ? __ldg(w + (long long)co * wco_stride + (long long)ci * wci_stride + kk) : 0.f;
-                Bs[n][c] = __float2bfloat16_rn(wv);
-            }
-            __syncthreads();
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int r0 = warp * 32 + mt * 16;
-                const uint32_t a0 = lds_u32(&As[r0 + g][2 * t4]), a1 = lds_u32(&As[r0 + g + 8][2 * t4]);
-                const uint32_t a2 = lds_u32(&As[r0 + g][2 * t4 + 8]), a3 = lds_u32(&As[r0 + g + 8][2 * t4 + 8]);
-#pragma unroll
-                for (int nt = 0; nt < kTcN / 8; ++nt) {
-                    const uint32_t b0 = lds_u32(&Bs[nt * 8 + g][2 * t4]), b1 = lds_u32(&Bs[nt * 8 + g][2 * t4 + 8]);
-                    mma_bf16_16816(acc[mt][nt], a0, a1, a2, a3, b0, b1);
-                }
-            }
-            __syncthreads();
-        }
-    }
-    // accumulator element i of tile (mt, nt): voxel row g (+8 for i >= 2), channel 2 t4 + (i & 1)
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < kTcN / 8; ++nt)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const long long v = v0 + warp * 32 + mt * 16 + g + (i >= 2 ? 8 : 0);
-                const int co = co0 + nt * 8 + 2 * t4 + (i & 1);
-                if (v < V && co < cout) {
-                    const float val = acc[mt][nt][i] + (b ? b[co] : 0.f);
-                    float* d = y + (long long)co * V + v;
-                    *d = accumulate ? *d + val : val;
-                }
-            }
-}
 
 // partial weight gradients: part[(co * cin + ci) * nchunk + chunk][27] = sum over the chunk's voxels v
 // of dy[co][v] x[ci][v + off(k)]; one block per (co, ci, chunk)
@@ -315,27 +222,32 @@ inline unsigned nblk(long long n, int b = kBlock) { return (unsigned)((n + b - 1
 
 extern "C" {
 
+int64_t dvm_nn_conv3d_scratch_bytes(int cin, int cout, int d, int h, int w_) {
+    if (cin < 1 || cout < 1 || d < 1 || h < 1 || w_ < 1) return 0;
+    const long long f = conv_umma_scratch_bytes(cin, cout, d, h, w_);     // forward: cin -> cout
+    const long long g = conv_umma_scratch_bytes(cout, cin, d, h, w_);     // data gradient: cout -> cin
+    return f > g ? f : g;
+}
+
 dvm_status dvm_nn_conv3d(const float* x, const float* w, const float* b, float* y, int cin, int cout, int d, int h,
-                         int w_, int accumulate, void* stream) {
-    if (!x || !w || !y || cin < 1 || cout < 1 || d < 1 || h < 1 || w_ < 1) return DVM_EINVAL;
-    const long long V = (long long)d * h * w_;
-    dim3 grid((unsigned)((V + kTcM - 1) / kTcM), (cout + kTcN - 1) / kTcN);
-    conv3d_tc_kernel<<<grid, kTcM, 0, (cudaStream_t)stream>>>(x, w, b, y, cin, cout, d, h, w_, cin * 27, 27, 0,
-                                                             accumulate);
-    return status_of(cudaGetLastError());
+                         int w_, int accumulate, void* scratch, int64_t scratch_bytes, void* stream) {
+    if (!x || !w || !y || !scratch || cin < 1 || cout < 1 || d < 1 || h < 1 || w_ < 1 || w_ > 128) return DVM_EINVAL;
+    if (scratch_bytes < conv_umma_scratch_bytes(cin, cout, d, h, w_)) return DVM_EINVAL;
+    return status_of(conv_umma(x, w, b, y, cin, cout, d, h, w_, 0, accumulate, scratch, scratch_bytes,
+                               (cudaStream_t)stream));
 }
 
 dvm_status dvm_nn_conv3d_dgrad(const float* dy, const float* w, float* dx, int cin, int cout, int d, int h, int w_,
-                               int accumulate, void* stream) {
-    if (!dy || !w || !dx || cin < 1 || cout < 1 || d < 1 || h < 1 || w_ < 1) return DVM_EINVAL;
+                               int accumulate, void* scratch, int64_t scratch_bytes, void* stream) {
+    if (!dy || !w || !dx || !scratch || cin < 1 || cout < 1 || d < 1 || h < 1 || w_ < 1 || w_ > 128) return DVM_EINVAL;
     // dx[ci][v] = sum_co sum_k w[co][ci][k] dy[co][v - off(k)]: a convolution of dy with the
     // transposed channel roles and mirrored taps
-    const long long V = (long long)d * h * w_;
-    dim3 grid((unsigned)((V + kTcM - 1) / kTcM), (cin + kTcN - 1) / kTcN);
-    conv3d_tc_kernel<<<grid, kTcM, 0, (cudaStream_t)stream>>>(dy, w, nullptr, dx, cout, cin, d, h, w_, 27, cin * 27, 1,
-                                                             accumulate);
-    return status_of(cudaGetLastError());
+    if (scratch_bytes < conv_umma_scratch_bytes(cout, cin, d, h, w_)) return DVM_EINVAL;
+    return status_of(conv_umma(dy, w, nullptr, dx, cout, cin, d, h, w_, 1, accumulate, scratch, scratch_bytes,
+                               (cudaStream_t)stream));
 }
+
+int dvm_nn_status(void* stream) { return conv_umma_status((cudaStream_t)stream); }
 
 dvm_status dvm_nn_conv3d_wgrad(const float* x, const float* dy, float* dw, float* db, float* scratch,
                                int64_t scratch_floats, int cin, int cout, int d, int h, int w_, int accumulate,

@@ -93,8 +93,10 @@ _SIGNATURES = [
     ("dvm_get_state", ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
     ("dvm_set_state", ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     ("dvm_permeability_noalloc", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double, _P, _P]),
-    ("dvm_nn_conv3d", ctypes.c_int, [_P, _P, _P, _P] + [ctypes.c_int] * 6 + [_P]),
-    ("dvm_nn_conv3d_dgrad", ctypes.c_int, [_P, _P, _P] + [ctypes.c_int] * 6 + [_P]),
+    ("dvm_nn_conv3d", ctypes.c_int, [_P, _P, _P, _P] + [ctypes.c_int] * 6 + [_P, ctypes.c_int64, _P]),
+    ("dvm_nn_conv3d_dgrad", ctypes.c_int, [_P, _P, _P] + [ctypes.c_int] * 6 + [_P, ctypes.c_int64, _P]),
+    ("dvm_nn_conv3d_scratch_bytes", ctypes.c_int64, [ctypes.c_int] * 5),
+    ("dvm_nn_status", ctypes.c_int, [_P]),
     ("dvm_nn_conv3d_wgrad", ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int64] + [ctypes.c_int] * 6 + [_P]),
     ("dvm_nn_wgrad_scratch_floats", ctypes.c_int64, [ctypes.c_int] * 5),
     ("dvm_nn_relu", ctypes.c_int, [_P, ctypes.c_int64, _P]),

@@ -139,11 +139,19 @@ class UNet:
     def _empty(self, c, dims):
         return self.torch.empty((c,) + tuple(dims), dtype=self.torch.float32, device="cuda")
 
+    def _conv_scratch(self, ci, co, d, h, w):
+        """The convolutions' scratch (padded BF16 input copy and BF16 weights), grown on demand."""
+        n = int(self.lib.dvm_nn_conv3d_scratch_bytes(ci, co, d, h, w))
+        if getattr(self, "_cscratch", None) is None or self._cscratch.numel() < n:
+            self._cscratch = self.torch.empty(n, dtype=self.torch.uint8, device="cuda")
+        return self._cscratch
+
     def _conv(self, x, p, y, relu):
         ci, co = self.shapes[p]
         d, h, w = x.shape[1:]
+        sc = self._conv_scratch(ci, co, d, h, w)
         self._chk(self.lib.dvm_nn_conv3d(_ptr(x), _ptr(self.wq[p]), _ptr(self.bq[p]), _ptr(y), ci, co, d, h, w, 0,
-                                         self.stream))
+                                         _ptr(sc), sc.numel(), self.stream))
         if relu:
             self._chk(self.lib.dvm_nn_relu(_ptr(y), y.numel(), self.stream))
 
@@ -207,7 +215,9 @@ class UNet:
         ci, co = self.shapes[p]
         d, h, w = g.shape[1:]
         dx = self._empty(ci, like)
-        self._chk(self.lib.dvm_nn_conv3d_dgrad(_ptr(g), _ptr(self.wq[p]), _ptr(dx), ci, co, d, h, w, 0, self.stream))
+        sc = self._conv_scratch(ci, co, d, h, w)
+        self._chk(self.lib.dvm_nn_conv3d_dgrad(_ptr(g), _ptr(self.wq[p]), _ptr(dx), ci, co, d, h, w, 0, _ptr(sc),
+                                               sc.numel(), self.stream))
         return dx
 
     def backward(self, dy):

@@ -36,7 +36,11 @@ def _s():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-@pytest.mark.parametrize("cin,cout,dims", [(5, 7, (6, 8, 10)), (3, 16, (4, 4, 4)), (17, 9, (8, 2, 6))])
+@pytest.mark.parametrize("cin,cout,dims", [(5, 7, (6, 8, 10)), (3, 16, (4, 4, 4)), (17, 9, (8, 2, 6)),
+                                           # channel counts of the warm-start network (base 32): full
+                                           # 128-voxel x 32-channel tiles, many CTAs per channel block
+                                           (32, 32, (16, 16, 16)), (64, 64, (16, 16, 16)),
+                                           (96, 32, (16, 16, 16)), (32, 96, (8, 16, 32))])
 def test_conv_kernels_match_reference(cin, cout, dims):
     lib = dvm.load()
     rng = np.random.default_rng(cin * 100 + cout)
@@ -46,14 +50,19 @@ def test_conv_kernels_match_reference(cin, cout, dims):
     g = rng.standard_normal((cout,) + dims).astype(np.float32)
     xd, wd, bd, gd = _dev(x), _dev(w), _dev(b), _dev(g)
     y = torch.empty((cout,) + dims, device="cuda")
-    assert lib.dvm_nn_conv3d(_p(xd), _p(wd), _p(bd), _p(y), cin, cout, *dims, 0, _s()) == 0
+    nsc = lib.dvm_nn_conv3d_scratch_bytes(cin, cout, *dims)
+    sc = torch.empty(nsc + 3, dtype=torch.uint8, device="cuda")[3:]     # any alignment
+    assert lib.dvm_nn_conv3d(_p(xd), _p(wd), _p(bd), _p(y), cin, cout, *dims, 0, _p(sc), nsc, _s()) == 0
+    assert lib.dvm_nn_status(_s()) == 0
     xr, wr, gr = ref.round_bf16(x), ref.round_bf16(w), ref.round_bf16(g)     # tensor-core operands
     assert _rel(y.cpu().numpy(), ref.conv3d(xr, wr, b.astype(np.float64))) < 1e-5
     dx = torch.empty((cin,) + dims, device="cuda")
-    assert lib.dvm_nn_conv3d_dgrad(_p(gd), _p(wd), _p(dx), cin, cout, *dims, 0, _s()) == 0
+    assert lib.dvm_nn_conv3d_dgrad(_p(gd), _p(wd), _p(dx), cin, cout, *dims, 0, _p(sc), nsc, _s()) == 0
+    assert lib.dvm_nn_status(_s()) == 0
     assert _rel(dx.cpu().numpy(), ref.conv3d_dgrad(gr, wr)) < 1e-5
     y2 = y.clone()                                   # accumulate = 1 adds to the old values
-    assert lib.dvm_nn_conv3d(_p(xd), _p(wd), _p(bd), _p(y2), cin, cout, *dims, 1, _s()) == 0
+    assert lib.dvm_nn_conv3d(_p(xd), _p(wd), _p(bd), _p(y2), cin, cout, *dims, 1, _p(sc), nsc, _s()) == 0
+    assert lib.dvm_nn_conv3d(_p(xd), _p(wd), _p(bd), _p(y2), cin, cout, *dims, 1, _p(sc), 1024, _s()) != 0   # too small
     assert _rel(y2.cpu().numpy(), 2.0 * y.cpu().numpy()) < 1e-6
     n = lib.dvm_nn_wgrad_scratch_floats(cin, cout, *dims)
     scratch = torch.empty(n, device="cuda")
