@@ -343,9 +343,11 @@ int64_t dvm_nn_conv3d_scratch_bytes(int cin, int cout, int d, int h, int w_);
 /* Synchronises the stream and returns the convolutions' device status word: 0, or DVM_ETIMEOUT when
  * a bounded wait inside a convolution expired (its output is then not written).  Clears it. */
 int dvm_nn_status(void* stream);
-/* weight and bias gradients: dw[co][ci][k] (+)= sum_v dy[co][v] x[ci][v + off(k)], db[co] (+)=
- * sum_v dy[co][v] (db may be NULL); summed in a fixed order.  scratch: device buffer of at least
- * dvm_nn_wgrad_scratch_floats(...) floats. */
+/* weight and bias gradients: dw[co][ci][k] (+)= sum_v dy[co][v] x[ci][v + off(k)] on the tcgen05
+ * tensor cores (x and dy rounded to BF16, FP32 accumulation, the voxel sum split over CTAs and the
+ * splits added in a fixed order), db[co] (+)= sum_v dy[co][v] in FP32 (db may be NULL).  scratch:
+ * DEVICE buffer of at least dvm_nn_wgrad_scratch_floats(...) floats (BF16 copies of x and dy and the
+ * split partials). */
 dvm_status dvm_nn_conv3d_wgrad(const float* x, const float* dy, float* dw, float* db, float* scratch,
                                int64_t scratch_floats, int cin, int cout, int d, int h, int w_,
                                int accumulate, void* stream);

@@ -137,14 +137,22 @@ def masked_mse(y, t, mask):
     return float((r * r).sum() / count), 2.0 * r / count
 
 
+def _wgrad(x, dy, rb):
+    """(dw, db) with dw from the rounded operands rb(x), rb(dy) and db from dy itself."""
+    dw, _ = conv3d_wgrad(rb(x), rb(dy))
+    return dw, dy.sum(axis=(1, 2, 3))
+
+
 def backward(params, cache, dy, levels, bf16_operands=False):
     """Gradients [(dw, db)] in parameter order for the output gradient dy.  bf16_operands: every
-    data gradient reads its input gradient rounded to bfloat16 (the weight gradients stay exact)."""
+    data gradient reads its input gradient rounded to bfloat16, and every weight gradient reads the
+    layer input and the output gradient rounded to bfloat16 (the operands of BF16 tensor-core
+    products with FP32 accumulation); the bias gradients stay exact."""
     rb = round_bf16 if bf16_operands else (lambda t: t)
     grads = [None] * len(params)
     p = len(params) - 1
     kind, h = cache[-1]
-    grads[p] = conv3d_wgrad(h, dy)
+    grads[p] = _wgrad(h, dy, rb)
     g = conv3d_dgrad(rb(dy), params[p][0])
     p -= 1
     skip_grads = {}
@@ -154,7 +162,7 @@ def backward(params, cache, dy, levels, bf16_operands=False):
         for _ in range(2):
             _, hin, a = cache[idx]
             g = g * (a > 0)
-            grads[p] = conv3d_wgrad(hin, g)
+            grads[p] = _wgrad(hin, g, rb)
             g = conv3d_dgrad(rb(g), params[p][0])
             p -= 1
             idx -= 1
@@ -170,7 +178,7 @@ def backward(params, cache, dy, levels, bf16_operands=False):
         for _ in range(2):
             _, hin, a = cache[idx]
             g = g * (a > 0)
-            grads[p] = conv3d_wgrad(hin, g)
+            grads[p] = _wgrad(hin, g, rb)
             g = conv3d_dgrad(rb(g), params[p][0])
             p -= 1
             idx -= 1

@@ -97,6 +97,15 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
                  : "memory");
 }
 
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
+                                            uint64_t* bar) {
+    asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+                 ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4),
+                   "r"(smem_u32(bar))
+                 : "memory");
+}
+
 // shared-memory matrix descriptor of a K-major operand in the 64-byte swizzled layout: rows of 64
 // bytes, eight-row groups 512 bytes apart (stride byte offset), descriptor version 1
 __device__ __forceinline__ uint64_t smem_desc_sw64(const void* p) {
@@ -410,6 +419,305 @@ cudaError_t conv_umma(const float* x, const float* w, const float* bias, float* 
     if (bn == 32) return launch_bn<32, 2>(ta, tb, bias, y, g, st);
     if (bn == 64) return launch_bn<64, 2>(ta, tb, bias, y, g, st);
     return launch_bn<128, 1>(ta, tb, bias, y, g, st);
+}
+
+namespace dvm_nn {
+
+// ---------------------------------------------------------------------------- weight gradients
+//
+//   dw[co][ci][k] (+)= sum_v dy[co][v] x[ci][v + off(k)]
+//
+// GEMM view: M = (tap, input channel) rows in sub-blocks of 32 (sub-block sb = tap * cinp / 32 +
+// channel chunk, four per 128-row tile), N = output channels (BN), K = voxels (chunks of 32 along
+// x of one (z, y) row; x padded to a multiple of 32 with zeros).  The A rows of a sub-block are x
+// shifted by the tap's offset: three BF16 copies of x (one per x offset dx = -1, 0, 1, already
+// shifted along x, with a periodic one-row halo in y and z) make every box start at an x that is a
+// multiple of 32; B is a BF16 copy of dy.  Every CTA sums its own range of K chunks (split K) into a
+// partial [32 sb rows][coutp] block per sub-block; a second kernel adds the partials of the splits
+// in split order (deterministic) into dw.
+
+struct WgradGeom {
+    int cin, cout, D, H, W, Wp;      // Wp: x extent padded to a multiple of 32
+    int cinp, coutp;
+    int nsb;                         // sub-blocks = 27 * cinp / 32
+    int nchunks, chunks_per_split;   // K chunks (D * H * Wp / 32) and chunks per CTA
+};
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads) wgrad_umma_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                              const __grid_constant__ CUtensorMap tmG,
+                                                              float* __restrict__ part, const WgradGeom g) {
+    constexpr int kABytes = kBM * kBK * 2;            // four 32-row sub-blocks of 64-byte rows
+    constexpr int kBBytes = BN * kBK * 2;
+    constexpr int kStageBytes = kABytes + kBBytes;
+    constexpr unsigned kTmemCols = BN < 32 ? 32u : (unsigned)BN;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* sbase = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+    __shared__ unsigned s_tmem;
+    __shared__ int s_fail;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mt = blockIdx.x, n0 = blockIdx.y * BN, split = blockIdx.z;
+    const int c_begin = split * g.chunks_per_split;
+    const int c_end = min(g.nchunks, c_begin + g.chunks_per_split);
+    const int nsub = min(4, g.nsb - mt * 4);          // sub-blocks of this tile
+    const int ncc = g.cinp / 32;
+    const int xchunks = g.Wp / 32;
+
+    if (nsub < 4) {   // rows of missing sub-blocks stay zero (their boxes are never loaded)
+        for (int i = threadIdx.x * 16; i < kStages * kStageBytes; i += kThreads * 16)
+            *reinterpret_cast<uint4*>(sbase + i) = make_uint4(0u, 0u, 0u, 0u);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(kTmemCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem_d = s_tmem;
+    const int niter = c_end - c_begin;
+    const unsigned box_bytes = (unsigned)(nsub * 32 * kBK * 2 + kBBytes);
+
+    if (warp == 0 && lane == 0) {
+        for (int i = 0; i < niter; ++i) {
+            const int s = i % kStages;
+            if (i >= kStages && !mbar_wait(&empty[s], ((i / kStages) - 1) & 1)) {
+                s_fail = 1;
+                break;
+            }
+            const int ch = c_begin + i;                 // K chunk: 32 voxels of the (z, y) row
+            const int x0 = (ch % xchunks) * 32;
+            const int row = ch / xchunks;
+            const int y = row % g.H, z = row / g.H;
+            unsigned char* st = sbase + (size_t)s * kStageBytes;
+            mbar_expect_tx(&full[s], box_bytes);
+            for (int j = 0; j < nsub; ++j) {
+                const int sb = mt * 4 + j;
+                const int tap = sb / ncc, cc = sb - tap * ncc;
+                const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+                tma_load_5d(st + j * 32 * kBK * 2, &tmX, x0, y + 1 + dy, z + 1 + dz, cc * 32, dx + 1, &full[s]);
+            }
+            tma_load_4d(st + kABytes, &tmG, x0, y, z, n0, &full[s]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        const unsigned idesc = idesc_bf16<BN>();
+        for (int i = 0; i < niter; ++i) {
+            const int s = i % kStages;
+            if (!mbar_wait(&full[s], (i / kStages) & 1)) {
+                s_fail = 1;
+                break;
+            }
+            tc_fence_after();
+            const unsigned char* st = sbase + (size_t)s * kStageBytes;
+            const uint64_t ad = smem_desc_sw64(st), bd = smem_desc_sw64(st + kABytes);
+#pragma unroll
+            for (int kk = 0; kk < kBK / 16; ++kk)
+                umma_bf16(tmem_d, ad + 2 * kk, bd + 2 * kk, idesc, (i > 0 || kk > 0) ? 1 : 0);
+            umma_commit(&empty[s]);
+        }
+        umma_commit(&done);
+    }
+    __syncwarp();
+    const bool ok = mbar_wait(&done, 0);
+    tc_fence_after();
+    if (!ok || s_fail) {
+        if (threadIdx.x == 0) atomicCAS(&g_conv_status, 0, -4);
+    } else {
+        // accumulator row r = (sub-block mt * 4 + r / 32, row r % 32), column j = output channel n0 + j
+        const int r = warp * 32 + lane;
+        const int sb = mt * 4 + r / 32;
+#pragma unroll
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            unsigned a[16];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                         "%13, %14, %15}, [%16];"
+                         : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]),
+                           "=r"(a[7]), "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]),
+                           "=r"(a[14]), "=r"(a[15])
+                         : "r"(tmem_d + ((unsigned)(32 * warp) << 16) + (unsigned)c0)
+                         : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (sb < g.nsb) {
+                float* d = part + (((size_t)split * g.nsb + sb) * 32 + (r & 31)) * g.coutp + n0 + c0;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) d[j] = niter > 0 ? __uint_as_float(a[j]) : 0.f;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_d), "r"(kTmemCols) : "memory");
+}
+
+// xs[dx + 1][c][pz][py][x] = bf16(x[c][pz - 1][py - 1][x + dx]) (periodic in every axis), zero for
+// c >= cin or x >= W; one thread per element, x fastest
+__global__ void shift_bf16_kernel(const float* __restrict__ x, __nv_bfloat16* __restrict__ xs, int cin, int cinp, int D,
+                                  int H, int W, int Wp) {
+    const long long per = (long long)cinp * (D + 2) * (H + 2) * Wp;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * per) return;
+    const int dx = (int)(i / per) - 1;
+    long long r = i - (long long)(dx + 1) * per;
+    const int xx = (int)(r % Wp);
+    r /= Wp;
+    const int py = (int)(r % (H + 2));
+    r /= (H + 2);
+    const int pz = (int)(r % (D + 2));
+    const int c = (int)(r / (D + 2));
+    float val = 0.f;
+    if (c < cin && xx < W) {
+        const int sx = (xx + dx + W) % W;
+        const int sy = py == 0 ? H - 1 : (py == H + 1 ? 0 : py - 1);
+        const int sz = pz == 0 ? D - 1 : (pz == D + 1 ? 0 : pz - 1);
+        val = x[(long long)c * D * H * W + ((long long)sz * H + sy) * W + sx];
+    }
+    xs[i] = __float2bfloat16_rn(val);
+}
+
+// gb[co][z][y][x] = bf16(dy[co][z][y][x]), zero for co >= cout or x >= W
+__global__ void grad_bf16_kernel(const float* __restrict__ dy, __nv_bfloat16* __restrict__ gb, int cout, int coutp,
+                                 int D, int H, int W, int Wp) {
+    const long long total = (long long)coutp * D * H * Wp;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int xx = (int)(i % Wp);
+    const long long rest = i / Wp;                      // (co, z, y)
+    const long long row = rest % ((long long)D * H);
+    const int co = (int)(rest / ((long long)D * H));
+    float val = 0.f;
+    if (co < cout && xx < W) val = dy[(long long)co * D * H * W + row * W + xx];
+    gb[i] = __float2bfloat16_rn(val);
+}
+
+// dw[co][ci][k] (+)= sum over splits, in split order, of part[split][sb(k, ci)][ci % 32][co]
+__global__ void wgrad_reduce_kernel(const float* __restrict__ part, float* __restrict__ dw, int cin, int cout,
+                                    int cinp, int coutp, int nsb, int nsplit, int accumulate) {
+    const long long total = (long long)cout * cin * 27;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int k = (int)(i % 27);
+    const int ci = (int)((i / 27) % cin);
+    const int co = (int)(i / (27LL * cin));
+    const int sb = k * (cinp / 32) + ci / 32;
+    const size_t off = ((size_t)sb * 32 + (ci & 31)) * coutp + co;
+    const size_t stride = (size_t)nsb * 32 * coutp;
+    float s = 0.f;
+    for (int sp = 0; sp < nsplit; ++sp) s += part[off + (size_t)sp * stride];
+    dw[i] = accumulate ? dw[i] + s : s;
+}
+
+constexpr int kWgradChunksPerSplit = 64;   // 2048 voxels of K per CTA
+
+template <int BN>
+cudaError_t launch_wgrad_bn(const CUtensorMap& tx, const CUtensorMap& tg, float* part, const WgradGeom& g,
+                            int nsplit, cudaStream_t st) {
+    constexpr int kStageBytes = kBM * kBK * 2 + BN * kBK * 2;
+    const int smem = kStages * kStageBytes + 1024;
+    auto kern = wgrad_umma_kernel<BN>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((g.nsb + 3) / 4), (unsigned)(g.coutp / BN), (unsigned)nsplit);
+    kern<<<grid, kThreads, smem, st>>>(tx, tg, part, g);
+    return cudaGetLastError();
+}
+
+WgradGeom wgrad_geom(int cin, int cout, int d, int h, int w) {
+    WgradGeom g;
+    g.cin = cin;
+    g.cout = cout;
+    g.D = d;
+    g.H = h;
+    g.W = w;
+    g.Wp = (w + 31) / 32 * 32;
+    g.cinp = (cin + 31) / 32 * 32;
+    const int bn = bn_for(cout);
+    g.coutp = (cout + bn - 1) / bn * bn;
+    g.nsb = 27 * g.cinp / 32;
+    g.nchunks = d * h * (g.Wp / 32);
+    g.chunks_per_split = kWgradChunksPerSplit;
+    return g;
+}
+
+}  // namespace dvm_nn
+
+// Scratch bytes of one weight gradient: the three shifted BF16 copies of x, the BF16 copy of dy and
+// the split partials, each 1 KB aligned.
+long long wgrad_umma_scratch_bytes(int cin, int cout, int d, int h, int w) {
+    using namespace dvm_nn;
+    const WgradGeom g = wgrad_geom(cin, cout, d, h, w);
+    const long long nsplit = (g.nchunks + g.chunks_per_split - 1) / g.chunks_per_split;
+    return align1k(3LL * g.cinp * (d + 2) * (h + 2) * g.Wp * 2) + align1k((long long)g.coutp * d * h * g.Wp * 2) +
+           align1k(nsplit * g.nsb * 32 * g.coutp * 4) + 1024;
+}
+
+// dw (+)= the weight gradient of y = conv(x, w) for the output gradient dy (see above); the bias
+// gradient is not formed here.
+cudaError_t wgrad_umma(const float* x, const float* dy, float* dw, int cin, int cout, int d, int h, int w, int accumulate,
+                       void* scratch, long long scratch_bytes, cudaStream_t st) {
+    using namespace dvm_nn;
+    if (scratch_bytes < wgrad_umma_scratch_bytes(cin, cout, d, h, w)) return cudaErrorInvalidValue;
+    EncodeFn enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const WgradGeom g = wgrad_geom(cin, cout, d, h, w);
+    const int bn = bn_for(cout);
+    const int nsplit = (g.nchunks + g.chunks_per_split - 1) / g.chunks_per_split;
+    const uintptr_t base = (reinterpret_cast<uintptr_t>(scratch) + 1023) & ~uintptr_t(1023);
+    const long long xs_bytes = align1k(3LL * g.cinp * (d + 2) * (h + 2) * g.Wp * 2);
+    const long long gb_bytes = align1k((long long)g.coutp * d * h * g.Wp * 2);
+    __nv_bfloat16* xs = reinterpret_cast<__nv_bfloat16*>(base);
+    __nv_bfloat16* gb = reinterpret_cast<__nv_bfloat16*>(base + xs_bytes);
+    float* part = reinterpret_cast<float*>(base + xs_bytes + gb_bytes);
+    {
+        const long long n = 3LL * g.cinp * (d + 2) * (h + 2) * g.Wp;
+        shift_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, xs, cin, g.cinp, d, h, w, g.Wp);
+        const long long m = (long long)g.coutp * d * h * g.Wp;
+        grad_bf16_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(dy, gb, cout, g.coutp, d, h, w, g.Wp);
+    }
+    CUtensorMap tx, tg;
+    {
+        const cuuint64_t dims[5] = {(cuuint64_t)g.Wp, (cuuint64_t)(h + 2), (cuuint64_t)(d + 2), (cuuint64_t)g.cinp, 3u};
+        const cuuint64_t strides[4] = {(cuuint64_t)g.Wp * 2, (cuuint64_t)g.Wp * 2 * (h + 2),
+                                       (cuuint64_t)g.Wp * 2 * (h + 2) * (d + 2),
+                                       (cuuint64_t)g.Wp * 2 * (h + 2) * (d + 2) * g.cinp};
+        const cuuint32_t box[5] = {32u, 1u, 1u, 32u, 1u};
+        const cuuint32_t es[5] = {1u, 1u, 1u, 1u, 1u};
+        if (enc(&tx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, xs, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+            CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    {
+        const cuuint64_t dims[4] = {(cuuint64_t)g.Wp, (cuuint64_t)h, (cuuint64_t)d, (cuuint64_t)g.coutp};
+        const cuuint64_t strides[3] = {(cuuint64_t)g.Wp * 2, (cuuint64_t)g.Wp * 2 * h, (cuuint64_t)g.Wp * 2 * h * d};
+        const cuuint32_t box[4] = {32u, 1u, 1u, (cuuint32_t)bn};
+        const cuuint32_t es[4] = {1u, 1u, 1u, 1u};
+        if (enc(&tg, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, gb, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+            CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    cudaError_t e;
+    if (bn == 32) e = launch_wgrad_bn<32>(tx, tg, part, g, nsplit, st);
+    else if (bn == 64) e = launch_wgrad_bn<64>(tx, tg, part, g, nsplit, st);
+    else e = launch_wgrad_bn<128>(tx, tg, part, g, nsplit, st);
+    if (e != cudaSuccess) return e;
+    const long long total = (long long)cout * cin * 27;
+    wgrad_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(part, dw, cin, cout, g.cinp, g.coutp, g.nsb,
+                                                                         nsplit, accumulate);
+    return cudaGetLastError();
 }
 
 // the device status word of the convolutions (nonzero after a bounded wait expired); cleared on read

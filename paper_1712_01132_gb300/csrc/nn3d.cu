@@ -10,7 +10,8 @@
 // data gradients are implicit GEMMs on the fifth-generation tensor cores (conv_umma.cu: tcgen05.mma
 // with BF16 operands brought in by the tensor memory accelerator, FP32 accumulators in tensor
 // memory; the input activations or gradients are rounded to BF16 once, into a padded copy); the
-// weight gradients are FP32 reductions on the CUDA cores.
+// weight gradients are tensor-core GEMMs over the voxels as well (BF16 operands, FP32 accumulation,
+// split over the voxels and summed in a fixed order); the bias gradients are FP32 channel sums.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -22,64 +23,15 @@ long long conv_umma_scratch_bytes(int nin, int nout, int d, int h, int w);
 cudaError_t conv_umma(const float* x, const float* w, const float* bias, float* y, int nin, int nout, int d, int h,
                       int w_, int flip, int accumulate, void* scratch, long long scratch_bytes, cudaStream_t st);
 int conv_umma_status(cudaStream_t st);
+long long wgrad_umma_scratch_bytes(int cin, int cout, int d, int h, int w);
+cudaError_t wgrad_umma(const float* x, const float* dy, float* dw, int cin, int cout, int d, int h, int w, int accumulate,
+                       void* scratch, long long scratch_bytes, cudaStream_t st);
 
 namespace {
 
 constexpr int kBlock = 256;
 
 __device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
-
-// partial weight gradients: part[(co * cin + ci) * nchunk + chunk][27] = sum over the chunk's voxels v
-// of dy[co][v] x[ci][v + off(k)]; one block per (co, ci, chunk)
-__global__ void __launch_bounds__(kBlock) conv3d_wgrad_kernel(const float* __restrict__ x, const float* __restrict__ dy,
-                                                              float* __restrict__ part, int cin, int D, int H, int W,
-                                                              int chunk) {
-    __shared__ float s_red[kBlock / 32][27];
-    const long long V = (long long)D * H * W;
-    const int pair = blockIdx.x;
-    const int co = pair / cin, ci = pair % cin;
-    const long long v0 = (long long)blockIdx.y * chunk;
-    const long long v1 = min(V, v0 + chunk);
-    float acc[27];
-#pragma unroll
-    for (int k = 0; k < 27; ++k) acc[k] = 0.f;
-    const float* xc = x + (long long)ci * V;
-    const float* g = dy + (long long)co * V;
-    for (long long v = v0 + threadIdx.x; v < v1; v += kBlock) {
-        const float gv = g[v];
-        const int xi = (int)(v % W), yi = (int)((v / W) % H), zi = (int)(v / ((long long)W * H));
-#pragma unroll
-        for (int k = 0; k < 27; ++k) {
-            const int dz = k / 9 - 1, dyy = (k / 3) % 3 - 1, dx = k % 3 - 1;
-            const long long n = ((long long)wrap(zi + dz, D) * H + wrap(yi + dyy, H)) * W + wrap(xi + dx, W);
-            acc[k] = fmaf(gv, __ldg(xc + n), acc[k]);
-        }
-    }
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < 27; ++k) {
-        float a = acc[k];
-        for (int off = 16; off >= 1; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
-        if (lane == 0) s_red[wp][k] = a;
-    }
-    __syncthreads();
-    if (threadIdx.x < 27) {
-        float s = 0.f;
-        for (int i = 0; i < kBlock / 32; ++i) s += s_red[i][threadIdx.x];
-        part[((long long)pair * gridDim.y + blockIdx.y) * 27 + threadIdx.x] = s;
-    }
-}
-
-// dw[pair][k] (+)= sum over chunks in order (deterministic)
-__global__ void conv3d_wgrad_sum_kernel(const float* __restrict__ part, float* __restrict__ dw, int npairs, int nchunk,
-                                        int accumulate) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= npairs * 27) return;
-    const int pair = i / 27, k = i % 27;
-    float s = 0.f;
-    for (int c = 0; c < nchunk; ++c) s += part[((long long)pair * nchunk + c) * 27 + k];
-    dw[i] = accumulate ? dw[i] + s : s;
-}
 
 // db[c] (+)= sum_v dy[c][v]; one block per channel, fixed-order tree
 __global__ void __launch_bounds__(kBlock) channel_sum_kernel(const float* __restrict__ dy, float* __restrict__ db,
@@ -253,22 +205,18 @@ dvm_status dvm_nn_conv3d_wgrad(const float* x, const float* dy, float* dw, float
                                int64_t scratch_floats, int cin, int cout, int d, int h, int w_, int accumulate,
                                void* stream) {
     if (!x || !dy || !dw || !scratch || cin < 1 || cout < 1 || d < 1 || h < 1 || w_ < 1) return DVM_EINVAL;
-    const long long V = (long long)d * h * w_;
-    const int chunk = 8192;
-    const int nchunk = (int)((V + chunk - 1) / chunk);
-    const long long need = (long long)cout * cin * nchunk * 27;
-    if (scratch_floats < need) return DVM_EINVAL;
+    if (scratch_floats * 4 < wgrad_umma_scratch_bytes(cin, cout, d, h, w_)) return DVM_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    conv3d_wgrad_kernel<<<dim3(cout * cin, nchunk), kBlock, 0, st>>>(x, dy, scratch, cin, d, h, w_, chunk);
-    conv3d_wgrad_sum_kernel<<<nblk((long long)cout * cin * 27), kBlock, 0, st>>>(scratch, dw, cout * cin, nchunk,
-                                                                                  accumulate);
+    const cudaError_t e = wgrad_umma(x, dy, dw, cin, cout, d, h, w_, accumulate, scratch, scratch_floats * 4, st);
+    if (e != cudaSuccess) return status_of(e);
+    const long long V = (long long)d * h * w_;
     if (db) channel_sum_kernel<<<cout, kBlock, 0, st>>>(dy, db, V, accumulate);
     return status_of(cudaGetLastError());
 }
 
 int64_t dvm_nn_wgrad_scratch_floats(int cin, int cout, int d, int h, int w_) {
-    const long long V = (long long)d * h * w_;
-    return (long long)cout * cin * ((V + 8191) / 8192) * 27;
+    if (cin < 1 || cout < 1 || d < 1 || h < 1 || w_ < 1) return 0;
+    return (wgrad_umma_scratch_bytes(cin, cout, d, h, w_) + 3) / 4;
 }
 
 dvm_status dvm_nn_relu(float* y, int64_t n, void* stream) {

@@ -69,7 +69,8 @@ def test_conv_kernels_match_reference(cin, cout, dims):
     dw = torch.full((cout, cin, 27), 0.5, device="cuda")
     db = torch.full((cout,), 0.25, device="cuda")
     assert lib.dvm_nn_conv3d_wgrad(_p(xd), _p(gd), _p(dw), _p(db), _p(scratch), n, cin, cout, *dims, 1, _s()) == 0
-    rdw, rdb = ref.conv3d_wgrad(x.astype(np.float64), g.astype(np.float64))
+    rdw, _ = ref.conv3d_wgrad(xr, gr)                    # tensor-core operands (BF16-rounded)
+    _, rdb = ref.conv3d_wgrad(x.astype(np.float64), g.astype(np.float64))
     assert _rel(dw.cpu().numpy(), rdw + 0.5) < 1e-5      # accumulate = 1 adds to the old values
     assert _rel(db.cpu().numpy(), rdb + 0.25) < 1e-5
     assert lib.dvm_nn_conv3d_wgrad(_p(xd), _p(gd), _p(dw), None, _p(scratch), n - 1, cin, cout, *dims, 0, _s()) != 0
