@@ -436,10 +436,10 @@ def main():
                     help="edge length of the rock_128 geometry (smaller only for profiling captures)")
     ap.add_argument("--no-time-to-tol", action="store_true",
                     help="skip the time-to-tolerance section (plain FP32 / FP64 / warm FP32 starts)")
-    ap.add_argument("--ttt-train", type=int, default=16, help="solver runs in the in-run training set")
-    ap.add_argument("--ttt-steps", type=int, default=400, help="training steps of the in-run network")
-    ap.add_argument("--ttt-levels", type=int, default=3)
-    ap.add_argument("--ttt-base", type=int, default=16)
+    ap.add_argument("--ttt-train", type=int, default=32, help="solver runs in the in-run training set")
+    ap.add_argument("--ttt-steps", type=int, default=1500, help="training steps of the in-run network")
+    ap.add_argument("--ttt-levels", type=int, default=4)
+    ap.add_argument("--ttt-base", type=int, default=32)
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)

@@ -563,28 +563,32 @@ __global__ void __launch_bounds__(kThreads) wgrad_umma_kernel(const __grid_const
 }
 
 // xs[dx + 1][c][pz][py][x] = bf16(x[c][pz - 1][py - 1][x + dx]) (periodic in every axis), zero for
-// c >= cin or x >= W; one thread per element, x fastest
-__global__ void shift_bf16_kernel(const float* __restrict__ x, __nv_bfloat16* __restrict__ xs, int cin, int cinp, int D,
-                                  int H, int W, int Wp) {
-    const long long per = (long long)cinp * (D + 2) * (H + 2) * Wp;
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 3 * per) return;
-    const int dx = (int)(i / per) - 1;
-    long long r = i - (long long)(dx + 1) * per;
-    const int xx = (int)(r % Wp);
-    r /= Wp;
-    const int py = (int)(r % (H + 2));
-    r /= (H + 2);
-    const int pz = (int)(r % (D + 2));
-    const int c = (int)(r / (D + 2));
-    float val = 0.f;
-    if (c < cin && xx < W) {
-        const int sx = (xx + dx + W) % W;
-        const int sy = py == 0 ? H - 1 : (py == H + 1 ? 0 : py - 1);
-        const int sz = pz == 0 ? D - 1 : (pz == D + 1 ? 0 : pz - 1);
-        val = x[(long long)c * D * H * W + ((long long)sz * H + sy) * W + sx];
+// c >= cin or x >= W; one warp per (dx, c, pz, py) row, lanes along x
+__global__ void __launch_bounds__(256) shift_bf16_kernel(const float* __restrict__ x, __nv_bfloat16* __restrict__ xs,
+                                                         int cin, int cinp, int D, int H, int W, int Wp) {
+    const long long nrows = 3LL * cinp * (D + 2) * (H + 2);
+    const long long row = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (row >= nrows) return;
+    const int lane = threadIdx.x & 31;
+    const int py = (int)(row % (H + 2));
+    const long long r2 = row / (H + 2);
+    const int pz = (int)(r2 % (D + 2));
+    const long long r3 = r2 / (D + 2);
+    const int c = (int)(r3 % cinp);
+    const int dx = (int)(r3 / cinp) - 1;
+    const int sy = py == 0 ? H - 1 : (py == H + 1 ? 0 : py - 1);
+    const int sz = pz == 0 ? D - 1 : (pz == D + 1 ? 0 : pz - 1);
+    const float* src = x + (long long)c * D * H * W + ((long long)sz * H + sy) * W;
+    __nv_bfloat16* dst = xs + row * Wp;
+    for (int xx = lane; xx < Wp; xx += 32) {
+        float val = 0.f;
+        if (c < cin && xx < W) {
+            int sx = xx + dx;
+            sx = sx < 0 ? sx + W : (sx >= W ? sx - W : sx);
+            val = src[sx];
+        }
+        dst[xx] = __float2bfloat16_rn(val);
     }
-    xs[i] = __float2bfloat16_rn(val);
 }
 
 // gb[co][z][y][x] = bf16(dy[co][z][y][x]), zero for co >= cout or x >= W
@@ -681,8 +685,8 @@ cudaError_t wgrad_umma(const float* x, const float* dy, float* dw, int cin, int 
     __nv_bfloat16* gb = reinterpret_cast<__nv_bfloat16*>(base + xs_bytes);
     float* part = reinterpret_cast<float*>(base + xs_bytes + gb_bytes);
     {
-        const long long n = 3LL * g.cinp * (d + 2) * (h + 2) * g.Wp;
-        shift_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, xs, cin, g.cinp, d, h, w, g.Wp);
+        const long long rows = 3LL * g.cinp * (d + 2) * (h + 2);
+        shift_bf16_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(x, xs, cin, g.cinp, d, h, w, g.Wp);
         const long long m = (long long)g.coutp * d * h * g.Wp;
         grad_bf16_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(dy, gb, cout, g.coutp, d, h, w, g.Wp);
     }
