@@ -83,3 +83,75 @@ def test_err_survives_a_checkpoint():
     assert it_b == 50 and err_b == err_a
     a.close()
     b.close()
+
+
+# ------------------------------------------------------------------ reduced precision at convergence
+#
+# The FP32 path (FP32 h and moments, FP64 wall sums, G_p and Err) run to Err < 1e-8, against the
+# FP64 oracle converged to Err < 1e-10 (tests/golden, written by make_convergence_golden.py, which
+# calls only the oracle): permeability within 1e-4 relative, u within 1e-3 of its max-norm, and rho
+# (fluid mean removed: the iteration fixes it only up to a constant) within 1e-3 of its max-norm.
+# The cases cover the ends of the benchmark's Kn sweep (0.01 and 10) on a 192^2 disc medium with
+# 32^2 velocities, two problems of the batched generator (24^2 velocities) in one context, and a
+# Gaussian-field rock with the 3D workload's 16^3 velocities.
+
+import json
+import os
+import sys
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+if GOLD not in sys.path:
+    sys.path.insert(0, GOLD)
+
+FP32_TOL = 1e-8
+
+
+def _golden(name):
+    with open(os.path.join(GOLD, "convergence_%s.json" % name)) as f:
+        meta = json.load(f)
+    d = np.load(os.path.join(GOLD, "convergence_%s.npz" % name))
+    return meta, d["rho"].astype(np.float64), d["u"].astype(np.float64)
+
+
+def _cases():
+    import make_convergence_golden
+    return make_convergence_golden.cases()
+
+
+def _check(mask, s, prob, meta, rho_o, u_o):
+    k, _ = s.permeability(prob)
+    rho, u = s.moments(prob)
+    fl = ~mask
+    d = (rho - rho[fl].mean()) * fl
+    true_err = abs(k - meta["k"]) / abs(meta["k"])
+    print("%s: k %.10e oracle %.10e, |dk|/k %.2e" % (meta["case"], k, meta["k"], true_err))
+    assert true_err <= 1e-4
+    assert np.abs(u - u_o).max() <= 1e-3 * np.abs(u_o).max()
+    assert np.abs(d - rho_o).max() <= 1e-3 * np.abs(rho_o).max()
+
+
+@pytest.mark.parametrize("name", ["discs192_kn0.01", "discs192_kn10", "rock24_kn0.5"])
+def test_fp32_converged_matches_converged_oracle(name):
+    meta, rho_o, u_o = _golden(name)
+    mask, kn, n_axis, _ = _cases()[name]
+    v, w = dvm.dvm_gh_velocity_grid(mask.ndim, n_axis)
+    s = dvm.Solver(mask, kn, v, w, precision="fp32", lateral="periodic", use_graph=True)
+    st, it, err = s.iterate(100000, FP32_TOL)
+    assert st == dvm.DVM_OK and err < FP32_TOL
+    _check(mask, s, 0, meta, rho_o, u_o)
+    s.close()
+
+
+def test_fp32_batch_of_generated_problems_converges_to_the_oracle():
+    names = ["c3_seed1000", "c3_seed1004"]
+    gold = [_golden(n) for n in names]
+    cs = _cases()
+    masks = [cs[n][0] for n in names]
+    kns = [cs[n][1] for n in names]
+    v, w = dvm.dvm_gh_velocity_grid(2, 24)
+    s = dvm.Solver(masks, kns, v, w, precision="fp32", lateral="periodic", use_graph=True)
+    st, it, err = s.iterate(100000, FP32_TOL)       # every problem of the batch below tol
+    assert st == dvm.DVM_OK and err < FP32_TOL
+    for b, (meta, rho_o, u_o) in enumerate(gold):
+        _check(masks[b], s, b, meta, rho_o, u_o)
+    s.close()
