@@ -283,6 +283,7 @@ def run_gpu(args):
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    fma_measured = dvm.alu_peak("fp32")          # microbenchmark cross-check of the derived peak
     sweep_avg_s = (sweep_ms / max(sweep_n, 1)) * 1e-3
     achieved = updates_per_iter * W["flops_per_update"] / sweep_avg_s / 1e12
     kernel = W["kernel"].replace("T1", str(t1))
@@ -295,6 +296,7 @@ def run_gpu(args):
                               "device, max SM clock measured in MEASURED_PEAKS.json)" % (sms, sm_max),
                 "timing": "CUDA events recorded by the captured graph around every sweep launch, "
                           "summed over the timed steps",
+                "peak_fma_microbenchmark": round(fma_measured, 2),
                 "flops_per_update": W["flops_per_update"], "updates_per_launch": updates_per_iter}
 
     out = None

@@ -289,6 +289,14 @@ dvm_status dvm_profile_enable(dvm_ctx* ctx, int on);
 dvm_status dvm_profile_read(dvm_ctx* ctx, double* sweep_ms, int64_t* sweep_launches,
                             double* finalize_ms, int64_t* finalize_launches);
 
+/* Measured FMA throughput of the current device in TFLOP/s (measurement support for the sweep
+ * kernels' roofline, which is ALU issue; not part of the method): every thread of eight 256-thread
+ * CTAs per SM runs independent FMA chains, packed fma.rn.f32x2 for DVM_FP32 (the sweep kernels'
+ * instruction) or fma.rn.f64 for DVM_FP64, timed with CUDA events on `stream` after one warm-up
+ * launch.  scratch: DEVICE buffer of at least 8 x SMs x 256 x 8 bytes for the chains' results.
+ * Synchronises the stream.  Errors: EINVAL (NULL, other precision, scratch too small), ECUDA. */
+dvm_status dvm_alu_peak(int precision, void* scratch, int64_t scratch_bytes, void* stream, double* tflops);
+
 /* Bytes copied host->device and device->host by this context since creation (inputs, setup
  * tables, readouts, permeability and status words). */
 dvm_status dvm_transfer_bytes(const dvm_ctx* ctx, int64_t* h2d, int64_t* d2h);

@@ -111,6 +111,7 @@ _SIGNATURES = [
                                    ctypes.c_float, ctypes.c_float, ctypes.c_int64, ctypes.c_float, _P]),
     ("dvm_nn_round_bf16", ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
     ("dvm_noalloc_last_error", ctypes.c_char_p, []),
+    ("dvm_alu_peak", ctypes.c_int, [ctypes.c_int, _P, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_double)]),
 ]
 
 _lib = None
@@ -217,6 +218,19 @@ class _TorchAllocator:
 
         self.alloc_fn = ALLOC_FN(alloc)
         self.free_fn = FREE_FN(free)
+
+
+def alu_peak(precision="fp32"):
+    """dvm_alu_peak: measured FMA throughput (TFLOP/s) of the current device, FP32 (packed) or FP64."""
+    import torch
+    lib = load()
+    n = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count * 8 * 256 * 8
+    buf = torch.empty(n, dtype=torch.uint8, device="cuda")
+    out = ctypes.c_double(0.0)
+    st = torch.cuda.current_stream().cuda_stream
+    _check(lib.dvm_alu_peak({"fp64": DVM_FP64, "fp32": DVM_FP32}[precision], ctypes.c_void_p(buf.data_ptr()), n,
+                            ctypes.c_void_p(st), ctypes.byref(out)), None)
+    return out.value
 
 
 def make_options(precision="fp64", stencil_order=2, lateral="specular", check_interval=100, stream=None,
