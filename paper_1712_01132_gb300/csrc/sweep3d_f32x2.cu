@@ -317,6 +317,13 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                                    zb + zo + (row * 2 + (jl & 1)) * NL + lw, need);
             }
         };
+        // does a tile (its fluid bits) hold a fluid point?  (the same answer in every warp)
+        auto tile_fluid = [&](const unsigned* fm) -> bool {
+            unsigned any = 0u;
+            for (int r = lane; r < MROWS; r += 32) any |= fm[r];
+            return __any_sync(0xffffffffu, any != 0u);
+        };
+        bool pre_next = false;
         for (int t = 0; t < ntiles; ++t) {
             const int4 ti = tile_info(t);
             const int c0 = ti.x;
@@ -324,8 +331,8 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
             RawPoint3 nxt[kRawRounds];
             if (t + 1 < ntiles) load_raw(t + 1, nxt);
             // z and y(0) of this tile were issued at the end of the previous one (its neighbours had
-            // already published this tile then)
-            const bool pre = s_pre != 0;
+            // already published this tile then, and it holds fluid)
+            const bool pre = pre_next;
             if (threadIdx.x == 0 && !pre) {
                 bool ok = true;
                 if (pi2.z < 0) ok = wait_geq(prog + p3 * np2 + p2 - 1, t + 1, a.status, a.timeout_ns);
@@ -343,6 +350,11 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                 cp_async_wait<0>();
                 return;
             }
+            // A tile without fluid points is not swept: nothing it would compute, copy or store is
+            // read (every fluid reader of one of its points has a zero coefficient for it, and the
+            // carries, staging and ghosts it leaves as they were hold finite values).  It still
+            // waits for its neighbours and publishes, which keeps the ring slots' order.
+            const bool tfl = tile_fluid(fm_cur);
             // x1 upstream of the tile's first column when it starts a block: x1 ghost layers of
             // the previous iteration in slot ti.z (oriented rows (k, j))
             if (ti.z >= 0) {
@@ -370,6 +382,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                 }
             }
             auto rbuf_rec = [&](int kk, int jj, int i) -> const float* { return recb + (size_t)((kk * MR2 + jj) * T1 + i) * RF; };
+            if (tfl) {
             if constexpr (BF) {
                 for (int jj = 0; jj < nr2; ++jj)
                     for (int i = 0; i < width; ++i) {
@@ -640,7 +653,12 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                     }
                 }
             }
-            if (ti.w >= 0) {   // x1 carry into ghost slot ti.w of the next iteration
+            }   // tfl
+            else if (ti.z >= 0 && !BF) {   // the x1 carry-in of a tile without fluid: complete it here
+                cp_async_commit();
+                cp_async_wait<0>();
+            }
+            if (ti.w >= 0 && tfl) {   // x1 carry into ghost slot ti.w of the next iteration
                 const size_t gxo = ((((size_t)(par ^ 1) * 8 + q) * P->ns1 + ti.w) * n3 * n2) * 2 * NL;
                 for (int kk = 0; kk < nr3; ++kk)
                     for (int jj = 0; jj < nr2; ++jj) {
@@ -664,10 +682,11 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
             if (threadIdx.x == 0 && it != a.withhold_item) {
                 publish_gpu(prog + p3 * np2 + p2, t + 1);
             }
+            pre_next = s_pre != 0 && tile_fluid(fmask + ((t + 1) & 1) * MROWS);
             if constexpr (!BF) {
                 // the plane staging and y slot 0 are free (the x3 edges were stored from the staging
                 // before the barrier): start the next tile's first copies now
-                if (s_pre) {
+                if (pre_next) {
                     const int4 tn = tile_info(t + 1);
                     const float* rbn = rec + (size_t)((t + 1) & 1) * MROWS * T1 * RF;
                     issue_z(tn.x, tn.y, rbn);
@@ -675,7 +694,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                 }
             }
             // moment partials of this octant and group: warp sums in warp order
-            const int tot = nr3 * nr2 * width * NM;
+            const int tot = tfl ? nr3 * nr2 * width * NM : 0;
             for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
                 const int mm = idx % NM;
                 const int pi = idx / NM;
