@@ -168,6 +168,7 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
             }
             // records of the tile's points for this octant
             const int npts = nr3 * MR2 * T1;
+            int anyf = 0;                         // a fluid point among this thread's
             for (int idx = threadIdx.x; idx < npts; idx += blockDim.x) {
                 const int kk = idx / (MR2 * T1);
                 const int rem = idx - kk * MR2 * T1;
@@ -184,6 +185,7 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                     const int id = (z * n2 + y) * n1 + x;
                     const uint16_t code = P->code[id];
                     if (!(code & kSolidBit)) {
+                        anyf = 1;
                         const V s = reinterpret_cast<const V*>(P->src)[id];
                         const V e0 = reinterpret_cast<const V*>(P->E)[2 * (size_t)id];
                         const V e1 = reinterpret_cast<const V*>(P->E)[2 * (size_t)id + 1];
@@ -227,7 +229,11 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                 if constexpr (NX > 0) R[4] = r4;
                 if constexpr (NX > 4) R[5] = r5;
             }
-            __syncthreads();
+            // A tile without fluid points is not swept: nothing it would compute or store is read
+            // (every fluid reader of one of its points has a zero coefficient for it, and the
+            // carries, planes, edges and ghost layers it leaves as they were hold finite values).
+            // It still waits for its neighbours and publishes, which keeps the ring slots' order.
+            const bool tfl = __syncthreads_or(anyf) != 0;
             if (s_abort) return;
             // x1 upstream of the tile's first column when it starts a block: x1 ghost layers of
             // the previous iteration in slot ti.z (oriented rows (k, j))
@@ -241,6 +247,7 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                         cr[32] = HS::ld(P->gx1, gxo + (row * 2 + 1) * NL + lv, x1g1);
                     }
             }
+            if (tfl) {
             // x3 upstream planes of the first plane of the pencil: the pencil below in x3 (ring
             // slot) or ghost slot pi3.z (x3 ghost layers, periodic or specular, Eq. 8, or the
             // lagged halo of the block below)
@@ -419,7 +426,8 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
                         HS::st(et, eo + (row * 2 + 1) * NL + lv, s[(size_t)T1 * 32], xs);
                     }
             }
-            if (ti.w >= 0) {   // x1 carry into ghost slot ti.w of the next iteration
+            }   // tfl
+            if (ti.w >= 0 && tfl) {   // x1 carry into ghost slot ti.w of the next iteration
                 const size_t gxo = ((((size_t)(par ^ 1) * 8 + q) * P->ns1 + ti.w) * n3 * n2) * 2 * NL;
                 for (int kk = 0; kk < nr3; ++kk)
                     for (int jj = 0; jj < nr2; ++jj) {
@@ -433,8 +441,9 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
             if (threadIdx.x == 0 && it != a.withhold_item) {
                 publish_gpu(prog + p3 * np2 + p2, t + 1);
             }
-            // moment partials of this octant and group: warp sums in warp order
-            const int tot = nr3 * nr2 * width * NM;
+            // moment partials of this octant and group: warp sums in warp order (a tile without
+            // fluid keeps the zero partials of its solid points)
+            const int tot = tfl ? nr3 * nr2 * width * NM : 0;
             for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
                 const int mm = idx % NM;
                 const int pi = idx / NM;
