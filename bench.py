@@ -341,7 +341,7 @@ def time_to_tolerance_section(args, opts):
     t0 = time.perf_counter()
     data, t_data = warmstart.training_set(args.ttt_train, side=64, nv=16, log=lambda *a: None)
     net, info = warmstart.train_network(data, levels=args.ttt_levels, base=args.ttt_base, steps=args.ttt_steps,
-                                        lr=2e-3, log=lambda *a: None)
+                                        lr=5e-4, constant_lr=True, log=lambda *a: None)
     del data
     mask = inputs.gaussian_rock(128, seed=10000, corr_len=8.0, porosity=0.35)
     fp32 = {k: opts[k] for k in ("tile_x1", "band_rows", "group_warps")}
