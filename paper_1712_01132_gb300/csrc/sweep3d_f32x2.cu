@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
     float* eb = pb + (size_t)NW * MR2 * 2 * T1 * kPL;                     // [NW][2][2][T1][64]
     float* rtab = eb + (size_t)NW * 2 * 2 * T1 * kPL;                     // [NW][8][64]
     unsigned* fmask = reinterpret_cast<unsigned*>(rtab + (size_t)NW * 8 * kPL);   // [2][MROWS] fluid bits
+    int* rowoff = reinterpret_cast<int*>(fmask + 2 * MROWS);   // [MROWS] first point of a row, or -1
     const size_t NL = (size_t)a.NL;
 
     for (;;) {
@@ -133,6 +134,19 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                             p3 == np3 - 1 ? 0 : -1 - (p3 & 1));
         }
         const int j0 = pi2.x, nr2 = pi2.y, k0 = pi3.x, nr3 = pi3.y;
+        // point index (z n2 + y) n1 of the first column of pencil row r = kk MR2 + jj, or -1 for a
+        // row outside the pencil: per thread for the point it loads each tile (thread idx holds
+        // point idx = (r, i) = (idx / T1, idx % T1)), in shared memory for the moment partials
+        auto row_first = [&](int r) -> int {
+            const int kk = r / MR2, jj = r - kk * MR2;
+            if (kk >= nr3 || jj >= nr2) return -1;
+            const int y = s2n ? n2 - 1 - (j0 + jj) : (j0 + jj);
+            const int z = s3n ? n3 - 1 - (k0 + kk) : (k0 + kk);
+            return (z * n2 + y) * n1;
+        };
+        for (int r = threadIdx.x; r < MROWS; r += blockDim.x) rowoff[r] = row_first(r);
+        const int my_r = (int)threadIdx.x / T1, my_i = (int)threadIdx.x % T1;
+        const int my_off = my_r < MROWS ? row_first(my_r) : -1;
         const float K1o = P->order == 2 ? 2.f : 1.f;
         const float K2o = P->order == 2 ? -0.5f : 0.f;
         const int lv = g * a.GL + kPL * warp + 2 * lane;      // first velocity slot of this lane
@@ -185,18 +199,13 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
         // points are loaded for tile t + 1 while tile t is swept (all loads issued together, with
         // no branch on the code) and written to that tile's record buffer at the end of tile t.
         const int npts = nr3 * MR2 * T1;
-        auto load_point = [&](const int4& tj, int idx, RawPoint3& r) {
+        // point (row first index off, column i) of a tile (first column, width: tj.x, tj.y)
+        auto load_point = [&](const int4& tj, int off, int i, RawPoint3& r) {
             r.code = kSolidBit;
-            const int kk = idx / (MR2 * T1);
-            const int rem = idx - kk * MR2 * T1;
-            const int jj = rem / T1;
-            const int i = rem - jj * T1;
-            if (jj < nr2 && i < tj.y) {
+            if (off >= 0 && i < tj.y) {
                 const int ic = tj.x + i;
                 const int x = s1n ? n1 - 1 - ic : ic;
-                const int y = s2n ? n2 - 1 - (j0 + jj) : (j0 + jj);
-                const int z = s3n ? n3 - 1 - (k0 + kk) : (k0 + kk);
-                const int id = (z * n2 + y) * n1 + x;
+                const int id = off + x;
                 r.code = P->code[id];
                 r.s = reinterpret_cast<const float4*>(P->src)[id];
                 r.e0 = reinterpret_cast<const float4*>(P->E)[2 * (size_t)id];
@@ -214,10 +223,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
         auto store_point = [&](int buf, int idx, const RawPoint3& r) {
             float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
             int4 r4 = make_int4(-1, -1, -1, -1), r5 = r4;
-            const int kk = idx / (MR2 * T1);
-            const int rem = idx - kk * MR2 * T1;
-            const int jj = rem / T1;
-            const int i = rem - jj * T1;
+            const int i = idx % T1;
             if (!(r.code & kSolidBit)) {
                 const int code = r.code;
                 const int ca = (code >> (2 * (0 + s1n))) & 3;
@@ -235,7 +241,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                     r4 = r.f0;
                     r5 = r.f1;
                 }
-                atomicOr(fmask + buf * MROWS + kk * MR2 + jj, 1u << i);
+                atomicOr(fmask + buf * MROWS + idx / T1, 1u << i);
             }
             float4* R = reinterpret_cast<float4*>(rec + (size_t)buf * MROWS * T1 * RF + (size_t)idx * RF);
             R[0] = r0;
@@ -247,14 +253,11 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                 reinterpret_cast<int4*>(R)[5] = r5;
             }
         };
+        static_assert(kRawRounds == 1, "one register round: the thread's own point");
         auto load_raw = [&](int tt, RawPoint3 (&raw)[kRawRounds]) {
             const int4 tj = tile_info(tt);
-#pragma unroll
-            for (int k = 0; k < kRawRounds; ++k) {
-                const int idx = k * blockDim.x + threadIdx.x;
-                raw[k].code = kSolidBit;
-                if (idx < npts) load_point(tj, idx, raw[k]);
-            }
+            raw[0].code = kSolidBit;
+            if ((int)threadIdx.x < npts) load_point(tj, my_off, my_i, raw[0]);
         };
         // the held points, then the points beyond the register rounds (loaded here)
         auto store_rec = [&](int tt, int buf, const RawPoint3 (&raw)[kRawRounds]) {
@@ -267,7 +270,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                 const int4 tj = tile_info(tt);
                 for (int idx = kRawRounds * blockDim.x + threadIdx.x; idx < npts; idx += blockDim.x) {
                     RawPoint3 r;
-                    load_point(tj, idx, r);
+                    load_point(tj, row_first(idx / T1), idx % T1, r);
                     store_point(buf, idx, r);
                 }
             }
@@ -295,26 +298,36 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
         // the stencil of the point that reads them has a nonzero coefficient for them (record K1 /
         // K2 of the first row or plane): values of solid points are never used, so they are neither
         // stored nor fetched, and the staging holds zeros there.
+        // (copy m = layer T1 + i of a row's 2 T1 goes to lane half m & 1; columns i >= wd are not
+        // copied)
         auto issue_y = [&](int kk, int cc0, int wd, const float* rb) {
-            const size_t rb0 = yrow(kk);
-            for (int m = half; m < 2 * wd; m += 2) {
-                const int layer = m / wd;
-                const int i = m - layer * wd;
-                const bool need = rb[(size_t)(kk * MR2 * T1 + i) * RF + 10 + layer] != 0.f;
-                cp_async16_or_zero(eb + ((((size_t)warp * 2 + (kk & 1)) * 2 + layer) * T1 + i) * kPL + 4 * hl,
-                                   yb + yo + ((rb0 + cc0 + i) * 2 + layer) * NL + lw, need);
+            const float* ys = yb + yo + (yrow(kk) + cc0) * 2 * NL + lw;
+            float* yd = eb + (((size_t)warp * 2 + (kk & 1)) * 2 * T1) * kPL + 4 * hl;
+            const float* yr = rb + (size_t)kk * MR2 * T1 * RF + 10;
+#pragma unroll
+            for (int u = 0; u < T1; ++u) {
+                const int m = half + 2 * u;
+                const int layer = m / T1, i = m % T1;
+                if (i < wd)
+                    cp_async16_or_zero(yd + (size_t)m * kPL, ys + (size_t)(i * 2 + layer) * NL, yr[i * RF + layer] != 0.f);
             }
             cp_async_commit();
         };
         // the x3 planes below the tile's first plane into the plane staging (committed with y(0))
         auto issue_z = [&](int cc0, int wd, const float* rb) {
-            for (int m = half; m < nr2 * 2 * wd; m += 2) {
-                const int jl = m / wd;               // jj * 2 + layer
-                const int i = m - jl * wd;
-                const size_t row = zg ? ((size_t)(j0 + (jl >> 1)) * n1 + (cc0 + i)) : ((size_t)(jl >> 1) * n1 + (cc0 + i));
-                const bool need = rb[(size_t)((jl >> 1) * T1 + i) * RF + 12 + (jl & 1)] != 0.f;
-                cp_async16_or_zero(pb + (((size_t)warp * MR2 * 2 + jl) * T1 + i) * kPL + 4 * hl,
-                                   zb + zo + (row * 2 + (jl & 1)) * NL + lw, need);
+            const float* zs = zb + zo + ((size_t)(zg ? j0 : 0) * n1 + cc0) * 2 * NL + lw;
+            float* zd = pb + ((size_t)warp * MR2 * 2 * T1) * kPL + 4 * hl;
+            const size_t zstride = (size_t)n1 * 2 * NL;
+            for (int jj = 0; jj < nr2; ++jj) {
+                const float* zr = rb + (size_t)jj * T1 * RF + 12;
+#pragma unroll
+                for (int u = 0; u < T1; ++u) {
+                    const int m = half + 2 * u;
+                    const int layer = m / T1, i = m % T1;
+                    if (i < wd)
+                        cp_async16_or_zero(zd + ((size_t)(jj * 2 + layer) * T1 + i) * kPL,
+                                           zs + jj * zstride + (size_t)(i * 2 + layer) * NL, zr[i * RF + layer] != 0.f);
+                }
             }
         };
         // does a tile (its fluid bits) hold a fluid point?  (the same answer in every warp)
@@ -641,15 +654,20 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                     et = P->gz;
                     eo = ((((size_t)(par ^ 1) * 8 + qz) * P->ns3 + pi3.w) * n2 * n1) * 2 * NL;
                 }
+                const size_t ebase = eo + ((size_t)(last ? j0 : 0) * n1 + c0) * 2 * NL + lv;
                 for (int jj = 0; jj < nr2; ++jj) {
                     const unsigned f0 = fm_cur[(nr3 - 1) * MR2 + jj];
                     const unsigned f1 = nr3 >= 2 ? fm_cur[(nr3 - 2) * MR2 + jj] : 0xffffffffu;
-                    for (int i = 0; i < width; ++i) {
-                        const size_t row = last ? ((size_t)(j0 + jj) * n1 + (c0 + i)) : ((size_t)jj * n1 + (c0 + i));
-                        const float* s = pb + ((((size_t)warp * MR2 + jj) * 2) * T1 + i) * kPL + 2 * lane;
-                        const float xs = x1of(c0 + i);
-                        if ((f0 >> i) & 1u) PS::st(et, eo + (row * 2 + 0) * NL + lv, *reinterpret_cast<const float2*>(s), xs);
-                        if ((f1 >> i) & 1u) PS::st(et, eo + (row * 2 + 1) * NL + lv, *reinterpret_cast<const float2*>(s + (size_t)T1 * kPL), xs);
+                    const size_t eb0 = ebase + (size_t)jj * n1 * 2 * NL;
+                    const float* s = pb + ((((size_t)warp * MR2 + jj) * 2) * T1) * kPL + 2 * lane;
+#pragma unroll
+                    for (int i = 0; i < T1; ++i) {
+                        if (i < width) {
+                            const float xs = x1of(c0 + i);
+                            if ((f0 >> i) & 1u) PS::st(et, eb0 + (size_t)(i * 2 + 0) * NL, *reinterpret_cast<const float2*>(s + (size_t)i * kPL), xs);
+                            if ((f1 >> i) & 1u)
+                                PS::st(et, eb0 + (size_t)(i * 2 + 1) * NL, *reinterpret_cast<const float2*>(s + ((size_t)T1 + i) * kPL), xs);
+                        }
                     }
                 }
             }
@@ -694,24 +712,22 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                 }
             }
             // moment partials of this octant and group: warp sums in warp order
-            const int tot = tfl ? nr3 * nr2 * width * NM : 0;
+            // (idx = (r T1 + i) NM + mm over the pencil's row slots; only fluid points have bits)
+            const int tot = tfl ? MROWS * T1 * NM : 0;
+            const int wstride = MROWS * T1 * NM;
             for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
                 const int mm = idx % NM;
-                const int pi = idx / NM;
-                const int i = pi % width;
-                const int r = pi / width;
-                const int jj = r % nr2;
-                const int kk = r / nr2;
+                const int pt = idx / NM;
+                const int i = pt % T1;
+                const int r = pt / T1;
                 // solid points keep the zero partials of the start state (no reader uses them)
-                if (!((fm_cur[kk * MR2 + jj] >> i) & 1u)) continue;
+                if (!((fm_cur[r] >> i) & 1u)) continue;
                 float s = 0.f;
-                for (int w = 0; w < NW; ++w) s += part[((size_t)(w * MROWS + kk * MR2 + jj) * T1 + i) * NM + mm];
+                for (int w = 0; w < NW; ++w) s += part[(size_t)w * wstride + idx];
                 const int ic = c0 + i;
-                const int x = s1n ? n1 - 1 - ic : ic;
-                const int y = s2n ? n2 - 1 - (j0 + jj) : (j0 + jj);
-                const int z = s3n ? n3 - 1 - (k0 + kk) : (k0 + kk);
-                if (!TAU || mm < 4) P->P[(((size_t)q * G + g) * 4 + mm) * N + ((size_t)z * n2 + y) * n1 + x] = s;
-                else P->Pt[((size_t)q * G + g) * N + ((size_t)z * n2 + y) * n1 + x] = s;
+                const size_t pid = (size_t)rowoff[r] + (s1n ? n1 - 1 - ic : ic);
+                if (!TAU || mm < 4) P->P[(((size_t)q * G + g) * 4 + mm) * N + pid] = s;
+                else P->Pt[((size_t)q * G + g) * N + pid] = s;
             }
             __syncthreads();
         }
@@ -724,7 +740,7 @@ size_t sweep3d_f32x2_smem(int T1, int NW, int R2, int R3, int tau, int spec) {
     return sizeof(float) * (2 * rows * T1 * (spec ? 24 : kRec) + (size_t)NW * rows * T1 * (tau ? 5 : 4) +
                             (size_t)NW * rows * 2 * kPL + (size_t)NW * R2 * 2 * T1 * kPL + (size_t)NW * 2 * 2 * T1 * kPL +
                             (size_t)NW * 8 * kPL) +
-           sizeof(unsigned) * 2 * rows;
+           sizeof(unsigned) * 2 * rows + sizeof(int) * rows;
 }
 
 int sweep3d_f32x2_velocities_per_lane() { return 2; }
