@@ -104,6 +104,10 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
     unsigned* fmask = reinterpret_cast<unsigned*>(rtab + (size_t)NW * 8 * kPL);   // [2][MROWS] fluid bits
     int* rowoff = reinterpret_cast<int*>(fmask + 2 * MROWS);   // [MROWS] first point of a row, or -1
     const size_t NL = (size_t)a.NL;
+    // When the CTA has a thread for every point of a tile, a tile's fluid bits are formed by warp
+    // votes and written whole (no clearing, no atomics, and no barrier between the moment partials
+    // of one tile and the next tile); otherwise they are cleared and set with atomicOr.
+    const bool bmask = MROWS * T1 <= (int)blockDim.x;
 
     for (;;) {
         if (threadIdx.x == 0) {
@@ -111,7 +115,8 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
             s_abort = 0;
             s_pre = 0;
         }
-        for (int r = threadIdx.x; r < MROWS; r += blockDim.x) fmask[r] = 0u;    // masks of tile 0
+        if (!bmask)
+            for (int r = threadIdx.x; r < MROWS; r += blockDim.x) fmask[r] = 0u;    // masks of tile 0
         __syncthreads();
         const int it = s_item;
         if (it >= a.nitems) return;
@@ -241,7 +246,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                     r4 = r.f0;
                     r5 = r.f1;
                 }
-                atomicOr(fmask + buf * MROWS + idx / T1, 1u << i);
+                if (!bmask) atomicOr(fmask + buf * MROWS + idx / T1, 1u << i);
             }
             float4* R = reinterpret_cast<float4*>(rec + (size_t)buf * MROWS * T1 * RF + (size_t)idx * RF);
             R[0] = r0;
@@ -265,6 +270,10 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
             for (int k = 0; k < kRawRounds; ++k) {
                 const int idx = k * blockDim.x + threadIdx.x;
                 if (idx < npts) store_point(buf, idx, raw[k]);
+            }
+            if (bmask) {   // row my_r's bits come from lanes my_r T1 .. my_r T1 + T1 - 1 (T1 divides 32)
+                const unsigned b = __ballot_sync(0xffffffffu, !(raw[0].code & kSolidBit));
+                if (my_i == 0 && my_r < MROWS) fmask[buf * MROWS + my_r] = (b >> lane) & ((1u << T1) - 1u);
             }
             if (kRawRounds * (int)blockDim.x < npts) {
                 const int4 tj = tile_info(tt);
@@ -357,7 +366,8 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
             // this tile, behind the barrier below)
             unsigned* fm_cur = fmask + (t & 1) * MROWS;
             const float* recb = rec + (size_t)(t & 1) * MROWS * T1 * RF;
-            for (int r = threadIdx.x; r < MROWS; r += blockDim.x) fmask[((t + 1) & 1) * MROWS + r] = 0u;
+            if (!bmask)
+                for (int r = threadIdx.x; r < MROWS; r += blockDim.x) fmask[((t + 1) & 1) * MROWS + r] = 0u;
             __syncthreads();
             if (s_abort) {
                 cp_async_wait<0>();
@@ -729,7 +739,9 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                 if (!TAU || mm < 4) P->P[(((size_t)q * G + g) * 4 + mm) * N + pid] = s;
                 else P->Pt[((size_t)q * G + g) * N + pid] = s;
             }
-            __syncthreads();
+            // (with masks by vote the next writers of part and of these masks are behind the next
+            // tile's first barrier; cleared masks need this one)
+            if (!bmask) __syncthreads();
         }
         __syncthreads();
     }
