@@ -74,11 +74,13 @@ typedef struct {
     int lateral_bc;      /* DVM_LATERAL_SPECULAR (Eq. 8) or DVM_LATERAL_PERIODIC */
     int check_interval;  /* iterations between permeability/Err evaluations (Sec. 3.1: 100) */
     void* stream;        /* cudaStream_t, or NULL for the legacy default stream */
-    int tile_x1;         /* sweep tile width along x1: 2D FP64 8 or 16, 2D FP32 4 or 8, 3D 4 or 8;
-                            0 = automatic (8 in 2D, 4 in 3D) */
+    int tile_x1;         /* sweep tile width along x1: 2D FP64 8 or 16, 2D FP32 4 or 8, 3D 4 or 8
+                            (3D FP32 sweeps an 8-column tile as two 4-column sub-tiles between one
+                            neighbour wait and one publish); 0 = automatic (8 in 2D, 8 in 3D FP32,
+                            4 in 3D FP64) */
     int band_rows;       /* rows per sweep band in 2D, pencil rows R2 = R3 in 3D (0 = automatic:
-                            8 in 2D, 3D 8 for FP32 and 4 for FP64; reduced until the tile fits
-                            shared memory) */
+                            8 in 2D, 4 in 3D; in 3D the tile width, then the rows, are reduced
+                            until the CTA fits shared memory) */
     /* Optional device allocator (e.g. the caller's caching allocator).  When alloc is NULL the
      * library uses cudaMalloc/cudaFree.  alloc returns NULL on failure. */
     void* (*alloc)(size_t bytes, void* user);
@@ -118,8 +120,8 @@ typedef struct {
     /* Maxwell diffuse-specular walls (Eq. 5): 1 - alpha, the specular fraction of the molecules
      * leaving a wall, whose h is h(v - 2 n (v.n)) of the molecules reaching it (taken, like the
      * wall density, at the wall's fluid point from the previous iteration).  0 (default): fully
-     * diffuse, the paper's setting (alpha = 1).  Values outside [0, 1], BF16 storage and band
-     * pairs reject it with DVM_EINVAL. */
+     * diffuse, the paper's setting (alpha = 1).  Values outside [0, 1] and BF16 storage reject it
+     * with DVM_EINVAL. */
     double specular_fraction;
     /* 0 (default): the BGK model of Eq. 2, the paper's.  A Prandtl number Pr > 0 selects the
      * linearised Shakhov (S) model, which the paper names as an extension of its solver (Sec. 1,

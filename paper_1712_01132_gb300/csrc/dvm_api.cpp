@@ -664,13 +664,11 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     c->GL = 32 * vpl * c->NW;                             // velocity slots per group
     c->NL = c->GL * c->G;
     const int NL = c->NL, G = c->G;
-    // 4-column x1 tiles by default: on a 128^3 medium with 16^3 velocities they sweep 1.4x faster
-    // than 8-column tiles (more pencils in flight per level, half the carry registers)
-    c->T1 = (c->opt.tile_x1 == 8) ? 8 : 4;
-    // default pencils: FP32 asks for 8 x 8 rows, shrunk below to the largest that fits shared
-    // memory (5 x 5 with 512 velocities per octant: 1.19x faster than 4 x 4 on a 128^3 rock);
-    // FP64 4 x 4
-    const int R = c->opt.band_rows ? c->opt.band_rows : (c->prec == DVM_FP32 ? 8 : 4);
+    // default tiles: FP32 (packed kernel) 8 columns, swept as two 4-column sub-tiles (one wait and
+    // one publish per 8 columns: 1.12x faster than 4-column tiles on a 128^3 rock with 16^3
+    // velocities); FP64 4 columns.  Default pencils 4 x 4 rows.
+    c->T1 = c->opt.tile_x1 == 8 ? 8 : (c->opt.tile_x1 == 4 ? 4 : (c->packed3 ? 8 : 4));
+    const int R = c->opt.band_rows ? c->opt.band_rows : 4;
     c->R2 = c->R3 = std::max(1, R);
     {
         // shrink the tile, then the pencil, until the CTA's shared memory fits the device limit

@@ -10,9 +10,11 @@
 //               + a2 (K1y ... + E2) + a3 (K1z ... + E3) ],  S = a + b1 v1 + b2 v2 + b3 v3
 // (Eq. 10 solved for h with the upwind stencil of Eq. 9, source form).  The moment sums of a point
 // are formed in a fixed order (pair, lane tree, warps), independent of tile and pencil shapes.
-// Solid points are not swept; upstream data is staged per warp with cp.async; with 4-column tiles
-// the rows of a plane are walked two at a time, the upper row a column behind the lower; the next
-// tile's point data is loaded while the current tile is swept.
+// Solid points are not swept; upstream data is staged per warp with cp.async; a tile of T1 = 4 or
+// 8 columns is swept as 4-column sub-tiles (one neighbour wait, one publish, one record load and
+// one pass of moment partials per tile); the rows of a plane are walked two at a time, the upper
+// row a column behind the lower; the next tile's point data is loaded while the current tile is
+// swept.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -28,6 +30,7 @@ namespace {
 
 constexpr int kRec = 16;    // record floats: {a b1 b2 b3} {E1 E2 E3 rsel} {K1x K2x K1y K2y} {K1z K2z - -}
 constexpr int kPL = 64;     // velocity slots per warp (32 lanes x 2)
+constexpr int kSubW = 4;    // columns of a sub-tile: the upstream staging and the skewed row-pair walk
 
 // transient h in HBM (ghost layers, pencil edges) as float pairs, or the BF16 deviations from the
 // x1 ramp (the BF16-storage ablation): h' - x1 of the point the pair belongs to
@@ -86,6 +89,9 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
     using PS = PairStore<BF>;
     constexpr int NM = TAU ? 5 : 4;         // moments per point: rho, u1..u3 (, sum W |v|^2 h)
     constexpr int RF = SPEC ? 24 : kRec;    // record floats (face ids in two more vectors)
+    constexpr int SW = kSubW;               // columns of a sub-tile (staging width)
+    constexpr int NSUB = T1 / SW;           // sub-tiles per tile
+    static_assert(T1 % SW == 0 && T1 <= 32 && 32 % T1 == 0, "tile width: a multiple of the sub-tile width, dividing 32");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
     __shared__ int s_abort;
@@ -98,9 +104,9 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
     float* rec = reinterpret_cast<float*>(smem_raw);                      // [2][MROWS][T1][RF]
     float* part = rec + (size_t)2 * MROWS * T1 * RF;                      // [NW][MROWS][T1][NM]
     float* carry = part + (size_t)NW * MROWS * T1 * NM;                   // [NW][MROWS][2][64]
-    float* pb = carry + (size_t)NW * MROWS * 2 * kPL;                     // [NW][MR2][2][T1][64]
-    float* eb = pb + (size_t)NW * MR2 * 2 * T1 * kPL;                     // [NW][2][2][T1][64]
-    float* rtab = eb + (size_t)NW * 2 * 2 * T1 * kPL;                     // [NW][8][64]
+    float* pb = carry + (size_t)NW * MROWS * 2 * kPL;                     // [NW][MR2][2][SW][64]
+    float* eb = pb + (size_t)NW * MR2 * 2 * SW * kPL;                     // [NW][2][2][SW][64]
+    float* rtab = eb + (size_t)NW * 2 * 2 * SW * kPL;                     // [NW][8][64]
     unsigned* fmask = reinterpret_cast<unsigned*>(rtab + (size_t)NW * 8 * kPL);   // [2][MROWS] fluid bits
     int* rowoff = reinterpret_cast<int*>(fmask + 2 * MROWS);   // [MROWS] first point of a row, or -1
     const size_t NL = (size_t)a.NL;
@@ -303,20 +309,20 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
             : ((((size_t)q * np3 + p3) * 2 * P->ns2 + (-1 - pi2.z)) * P->R3 * n1) * 2 * NL;
         auto yrow = [&](int kk) -> size_t { return yg ? (size_t)(k0 + kk) * n1 : (size_t)kk * n1; };
         // FP32: the x2 rows of plane kk go to slot kk & 1, copied while plane kk - 1 is swept (the
-        // tile's columns cc0 .. cc0 + wd - 1, records rb).  Upstream values are fetched only where
-        // the stencil of the point that reads them has a nonzero coefficient for them (record K1 /
-        // K2 of the first row or plane): values of solid points are never used, so they are neither
-        // stored nor fetched, and the staging holds zeros there.
-        // (copy m = layer T1 + i of a row's 2 T1 goes to lane half m & 1; columns i >= wd are not
+        // sub-tile's columns cc0 .. cc0 + wd - 1, records rb: its first column in row 0).  Upstream
+        // values are fetched only where the stencil of the point that reads them has a nonzero
+        // coefficient for them (record K1 / K2 of the first row or plane): values of solid points
+        // are never used, so they are neither stored nor fetched, and the staging holds zeros there.
+        // (copy m = layer SW + i of a row's 2 SW goes to lane half m & 1; columns i >= wd are not
         // copied)
         auto issue_y = [&](int kk, int cc0, int wd, const float* rb) {
             const float* ys = yb + yo + (yrow(kk) + cc0) * 2 * NL + lw;
-            float* yd = eb + (((size_t)warp * 2 + (kk & 1)) * 2 * T1) * kPL + 4 * hl;
+            float* yd = eb + (((size_t)warp * 2 + (kk & 1)) * 2 * SW) * kPL + 4 * hl;
             const float* yr = rb + (size_t)kk * MR2 * T1 * RF + 10;
 #pragma unroll
-            for (int u = 0; u < T1; ++u) {
+            for (int u = 0; u < SW; ++u) {
                 const int m = half + 2 * u;
-                const int layer = m / T1, i = m % T1;
+                const int layer = m / SW, i = m % SW;
                 if (i < wd)
                     cp_async16_or_zero(yd + (size_t)m * kPL, ys + (size_t)(i * 2 + layer) * NL, yr[i * RF + layer] != 0.f);
             }
@@ -325,24 +331,26 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
         // the x3 planes below the tile's first plane into the plane staging (committed with y(0))
         auto issue_z = [&](int cc0, int wd, const float* rb) {
             const float* zs = zb + zo + ((size_t)(zg ? j0 : 0) * n1 + cc0) * 2 * NL + lw;
-            float* zd = pb + ((size_t)warp * MR2 * 2 * T1) * kPL + 4 * hl;
+            float* zd = pb + ((size_t)warp * MR2 * 2 * SW) * kPL + 4 * hl;
             const size_t zstride = (size_t)n1 * 2 * NL;
             for (int jj = 0; jj < nr2; ++jj) {
                 const float* zr = rb + (size_t)jj * T1 * RF + 12;
 #pragma unroll
-                for (int u = 0; u < T1; ++u) {
+                for (int u = 0; u < SW; ++u) {
                     const int m = half + 2 * u;
-                    const int layer = m / T1, i = m % T1;
+                    const int layer = m / SW, i = m % SW;
                     if (i < wd)
-                        cp_async16_or_zero(zd + ((size_t)(jj * 2 + layer) * T1 + i) * kPL,
+                        cp_async16_or_zero(zd + ((size_t)(jj * 2 + layer) * SW + i) * kPL,
                                            zs + jj * zstride + (size_t)(i * 2 + layer) * NL, zr[i * RF + layer] != 0.f);
                 }
             }
         };
-        // does a tile (its fluid bits) hold a fluid point?  (the same answer in every warp)
-        auto tile_fluid = [&](const unsigned* fm) -> bool {
+        // does sub-tile u of a tile (its fluid bits) hold a fluid point?  (the same answer in every
+        // warp; u = -1: the whole tile)
+        auto has_fluid = [&](const unsigned* fm, int u) -> bool {
+            const unsigned sel = u < 0 ? ((T1 == 32) ? 0xffffffffu : ((1u << T1) - 1u)) : (((1u << SW) - 1u) << (u * SW));
             unsigned any = 0u;
-            for (int r = lane; r < MROWS; r += 32) any |= fm[r];
+            for (int r = lane; r < MROWS; r += 32) any |= fm[r] & sel;
             return __any_sync(0xffffffffu, any != 0u);
         };
         bool pre_next = false;
@@ -352,8 +360,8 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
             const int width = ti.y;
             RawPoint3 nxt[kRawRounds];
             if (t + 1 < ntiles) load_raw(t + 1, nxt);
-            // z and y(0) of this tile were issued at the end of the previous one (its neighbours had
-            // already published this tile then, and it holds fluid)
+            // z and y(0) of this tile's first sub-tile were issued at the end of the previous tile
+            // (its neighbours had already published this tile then, and the sub-tile holds fluid)
             const bool pre = pre_next;
             if (threadIdx.x == 0 && !pre) {
                 bool ok = true;
@@ -373,11 +381,11 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                 cp_async_wait<0>();
                 return;
             }
-            // A tile without fluid points is not swept: nothing it would compute, copy or store is
-            // read (every fluid reader of one of its points has a zero coefficient for it, and the
-            // carries, staging and ghosts it leaves as they were hold finite values).  It still
-            // waits for its neighbours and publishes, which keeps the ring slots' order.
-            const bool tfl = tile_fluid(fm_cur);
+            // A tile (or sub-tile) without fluid points is not swept: nothing it would compute, copy
+            // or store is read (every fluid reader of one of its points has a zero coefficient for
+            // it, and the carries, staging and ghosts it leaves as they were hold finite values).  A
+            // tile still waits for its neighbours and publishes, which keeps the ring slots' order.
+            const bool tfl = has_fluid(fm_cur, -1);
             // x1 upstream of the tile's first column when it starts a block: x1 ghost layers of
             // the previous iteration in slot ti.z (oriented rows (k, j))
             if (ti.z >= 0) {
@@ -390,7 +398,9 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                         cp_async16(carry + ((size_t)(warp * MROWS + kk * MR2 + (jl >> 1)) * 2 + (jl & 1)) * kPL + 4 * hl,
                                    P->gx1 + gxo + (row * 2 + (jl & 1)) * NL + lw);
                     }
-                    if (pre) {   // the first group is already committed: complete these copies here
+                    // complete them here when the first group is already committed, or when no
+                    // sub-tile will commit them
+                    if (pre || !tfl) {
                         cp_async_commit();
                         cp_async_wait<0>();
                     }
@@ -404,288 +414,290 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                         }
                 }
             }
-            auto rbuf_rec = [&](int kk, int jj, int i) -> const float* { return recb + (size_t)((kk * MR2 + jj) * T1 + i) * RF; };
-            if (tfl) {
-            if constexpr (BF) {
-                for (int jj = 0; jj < nr2; ++jj)
-                    for (int i = 0; i < width; ++i) {
-                        const size_t row = zg ? ((size_t)(j0 + jj) * n1 + (c0 + i)) : ((size_t)jj * n1 + (c0 + i));
-                        float* d = pb + ((((size_t)warp * MR2 + jj) * 2) * T1 + i) * kPL + 2 * lane;
-                        const float xs = x1of(c0 + i);
-                        const float* rc = rbuf_rec(0, jj, i);
-                        *reinterpret_cast<float2*>(d) = rc[12] != 0.f ? PS::ld(zb, zo + (row * 2 + 0) * NL + lv, xs) : make_float2(0.f, 0.f);
-                        *reinterpret_cast<float2*>(d + (size_t)T1 * kPL) =
-                            rc[13] != 0.f ? PS::ld(zb, zo + (row * 2 + 1) * NL + lv, xs) : make_float2(0.f, 0.f);
-                    }
-            } else if (!pre) {
-                issue_z(c0, width, recb);
-                issue_y(0, c0, width, recb);
-            }
-            for (int kk = 0; kk < nr3; ++kk) {
-                // x2 upstream rows of the first row of this plane
-                float2 rb1[T1], rb2[T1];
+            // Sub-tiles of SW columns, swept one after the other with the same staging (the x1
+            // carries pass between them in shared memory, as between tiles).
+            for (int u = 0; u < NSUB && tfl; ++u) {
+                const int cs = c0 + u * SW;                       // first column of the sub-tile
+                const int wsub = min(SW, width - u * SW);         // its width
+                if (wsub <= 0) break;
+                // (a sub-tile 0 without fluid leaves its carry-in copies, if any, to the group of
+                // sub-tile 1, which then holds fluid)
+                if (NSUB > 1 && !has_fluid(fm_cur, u)) continue;
+                const int us = u * SW;                            // bit / record column offset
+                const float* recs = recb + (size_t)us * RF;       // record of (row 0, column cs)
+                auto rbuf_rec = [&](int kk, int jj, int i) -> const float* { return recs + (size_t)((kk * MR2 + jj) * T1 + i) * RF; };
+                auto fbits = [&](int r) -> unsigned { return (fm_cur[r] >> us) & ((1u << SW) - 1u); };
                 if constexpr (BF) {
-                    const size_t rowbase = yrow(kk);
-#pragma unroll
-                    for (int i = 0; i < T1; ++i) {
-                        if (i < width) {
-                            const float xs = x1of(c0 + i);
-                            const float* rc = rbuf_rec(kk, 0, i);
-                            rb1[i] = rc[10] != 0.f ? PS::ld(yb, yo + ((rowbase + c0 + i) * 2 + 0) * NL + lv, xs) : make_float2(0.f, 0.f);
-                            rb2[i] = rc[11] != 0.f ? PS::ld(yb, yo + ((rowbase + c0 + i) * 2 + 1) * NL + lv, xs) : make_float2(0.f, 0.f);
-                        } else {
-                            rb1[i] = make_float2(0.f, 0.f);
-                            rb2[i] = rb1[i];
+                    for (int jj = 0; jj < nr2; ++jj)
+                        for (int i = 0; i < wsub; ++i) {
+                            const size_t row = zg ? ((size_t)(j0 + jj) * n1 + (cs + i)) : ((size_t)jj * n1 + (cs + i));
+                            float* d = pb + ((((size_t)warp * MR2 + jj) * 2) * SW + i) * kPL + 2 * lane;
+                            const float xs = x1of(cs + i);
+                            const float* rc = rbuf_rec(0, jj, i);
+                            *reinterpret_cast<float2*>(d) = rc[12] != 0.f ? PS::ld(zb, zo + (row * 2 + 0) * NL + lv, xs) : make_float2(0.f, 0.f);
+                            *reinterpret_cast<float2*>(d + (size_t)SW * kPL) =
+                                rc[13] != 0.f ? PS::ld(zb, zo + (row * 2 + 1) * NL + lv, xs) : make_float2(0.f, 0.f);
                         }
-                    }
-                } else {
-                    __syncwarp();                        // slot (kk + 1) & 1 was last read at plane kk - 1
-                    if (kk + 1 < nr3) {
-                        issue_y(kk + 1, c0, width, recb);
-                        cp_async_wait<1>();              // all but the copies of plane kk + 1
-                    } else {
-                        cp_async_wait<0>();
-                    }
-                    __syncwarp();
-                    const float* e0 = eb + ((((size_t)warp * 2 + (kk & 1)) * 2) * T1) * kPL + 2 * lane;
-#pragma unroll
-                    for (int i = 0; i < T1; ++i) {
-                        if (i < width) {
-                            rb1[i] = *reinterpret_cast<const float2*>(e0 + (size_t)i * kPL);
-                            rb2[i] = *reinterpret_cast<const float2*>(e0 + ((size_t)T1 + i) * kPL);
-                        } else {
-                            rb1[i] = make_float2(0.f, 0.f);
-                            rb2[i] = rb1[i];
-                        }
-                    }
+                } else if (!(pre && u == 0)) {
+                    __syncwarp();                            // the staging's last readers are done
+                    issue_z(cs, wsub, recs);
+                    issue_y(0, cs, wsub, recs);
                 }
-                // one point: Eq. 10 for the lane's velocity pair with the x1 upstream values (hp1,
-                // hp2) of its row, the x2 upstream values rb of its column and the x3 upstream values
-                // of its row's plane staging zr; returns the lane's moment sums of the point
-                auto point = [&](const float* rrow, float* zr, int i, float2& hp1, float2& hp2, float& m0, float& m1,
-                                 float& m2, float& m3, float& m4) {
-                    const float4* R = reinterpret_cast<const float4*>(rrow + i * RF);
-                    const float4 A = R[0], B = R[1], C = R[2], D = R[3];
-                    const float2 z1 = *reinterpret_cast<const float2*>(zr + (size_t)i * kPL);
-                    const float2 z2 = *reinterpret_cast<const float2*>(zr + ((size_t)T1 + i) * kPL);
-                    const float2 Rk = *reinterpret_cast<const float2*>(my_rtab + __float_as_int(B.w));
-                    float2 S = fma2(dup2(A.w), v3, fma2(dup2(A.z), v2, fma2(dup2(A.y), v1, dup2(A.x))));
-                    if constexpr (TAU) S = fma2(dup2(D.z), vq, S);   // nu tau (|v|^2 - 3/2)
-                    float2 t1 = fma2(dup2(C.x), hp1, fma2(dup2(C.y), hp2, dup2(B.x)));
-                    float2 t2 = fma2(dup2(C.z), rb1[i], fma2(dup2(C.w), rb2[i], dup2(B.y)));
-                    float2 t3 = fma2(dup2(D.x), z1, fma2(dup2(D.y), z2, dup2(B.z)));
-                    int4 Fa, Fb;
-                    if constexpr (SPEC) {   // + (1 - alpha) h'(x, reflected v) at walls
-                        Fa = reinterpret_cast<const int4*>(R)[4];
-                        Fb = reinterpret_cast<const int4*>(R)[5];
-                        if (Fa.x >= 0) t1 = fma2(specP, *reinterpret_cast<const float2*>(fprev[0] + (size_t)Fa.x * fstride), t1);
-                        if (Fa.y >= 0) t2 = fma2(specP, *reinterpret_cast<const float2*>(fprev[1] + (size_t)Fa.y * fstride), t2);
-                        if (Fa.z >= 0) t3 = fma2(specP, *reinterpret_cast<const float2*>(fprev[2] + (size_t)Fa.z * fstride), t3);
-                    }
-                    // the x1 term (carried from the previous point) enters last: three dependent
-                    // operations per point along the x1 chain
-                    const float2 num = fma2(a1, t1, fma2(a3, t3, fma2(a2, t2, S)));
-                    const float2 h = mul2(num, Rk);
-                    if constexpr (SPEC) {   // molecules moving into a downstream face
-                        if (Fa.w >= 0) *reinterpret_cast<float2*>(fnext[0] + (size_t)Fa.w * fstride) = h;
-                        if (Fb.x >= 0) *reinterpret_cast<float2*>(fnext[1] + (size_t)Fb.x * fstride) = h;
-                        if (Fb.y >= 0) *reinterpret_cast<float2*>(fnext[2] + (size_t)Fb.y * fstride) = h;
-                    }
-                    hp2 = hp1;
-                    hp1 = h;
-                    rb2[i] = rb1[i];
-                    rb1[i] = h;
-                    *reinterpret_cast<float2*>(zr + ((size_t)T1 + i) * kPL) = z1;
-                    *reinterpret_cast<float2*>(zr + (size_t)i * kPL) = h;
-                    const float2 p0 = mul2(W, h), p1 = mul2(Wv1, h), p2v = mul2(Wv2, h), p3v = mul2(Wv3, h);
-                    m0 = p0.x + p0.y;
-                    m1 = p1.x + p1.y;
-                    m2 = p2v.x + p2v.y;
-                    m3 = p3v.x + p3v.y;
-                    if constexpr (TAU) {
-                        const float2 p4v = mul2(Wvv, h);
-                        m4 = p4v.x + p4v.y;
-                    } else {
-                        m4 = 0.f;
-                    }
-                };
-                auto row_ptrs = [&](int jj, float*& cr, float*& zr, const float*& rrow, float*& prow) {
-                    cr = carry + ((size_t)(warp * MROWS + kk * MR2 + jj) * 2) * kPL + 2 * lane;
-                    zr = pb + ((((size_t)warp * MR2 + jj) * 2) * T1) * kPL + 2 * lane;   // [2][T1][64]
-                    rrow = recb + (size_t)((kk * MR2 + jj) * T1) * RF;
-                    prow = part + ((size_t)(warp * MROWS + kk * MR2 + jj) * T1) * NM;
-                };
-                // solid points are not swept: every fluid point downstream of one gives it a zero
-                // stencil coefficient (its code marks that upstream point solid), so the values left
-                // in the carries, rows and planes there are never used
-                int jj = 0;
-                if constexpr (T1 == 4) {
-                    // rows two at a time, the upper one a column behind the lower (it needs the lower
-                    // row's value of the same column): two independent points per step.  A step with
-                    // a fluid point sweeps both of its points; a solid one has a zero record and gets
-                    // h = 0, which is as unused as the value a skipped point leaves.
-                    // Points beyond the tile width are never swept (their staging is not filled, and
-                    // the x1 carries must end at the last column).
-                    auto walk_pairs = [&](auto full_tag) {
-                    constexpr bool FULL = decltype(full_tag)::value;
-                    for (; jj + 1 < nr2; jj += 2) {
-                        const unsigned fa = fm_cur[kk * MR2 + jj], fb = fm_cur[kk * MR2 + jj + 1];
-                        if ((fa | fb) == 0u) continue;
-                        float *crA, *zrA, *prA, *crB, *zrB, *prB;
-                        const float *rrA, *rrB;
-                        row_ptrs(jj, crA, zrA, rrA, prA);
-                        row_ptrs(jj + 1, crB, zrB, rrB, prB);
-                        float2 hA1 = *reinterpret_cast<const float2*>(crA), hA2 = *reinterpret_cast<const float2*>(crA + kPL);
-                        float2 hB1 = *reinterpret_cast<const float2*>(crB), hB2 = *reinterpret_cast<const float2*>(crB + kPL);
-                        float m0[8], m1[8], m2[8], m3[8], m4[8];
+                for (int kk = 0; kk < nr3; ++kk) {
+                    // x2 upstream rows of the first row of this plane
+                    float2 rb1[SW], rb2[SW];
+                    if constexpr (BF) {
+                        const size_t rowbase = yrow(kk);
 #pragma unroll
-                        for (int st = 0; st <= 4; ++st) {
-                            const bool onA = st < 4 && ((fa >> st) & 1u);
-                            const bool onB = st >= 1 && ((fb >> (st - 1)) & 1u);
-                            if (onA || onB) {
-                                if (st < 4) {
-                                    if (FULL || st < width) point(rrA, zrA, st, hA1, hA2, m0[st], m1[st], m2[st], m3[st], m4[st]);
-                                    else m0[st] = m1[st] = m2[st] = m3[st] = m4[st] = 0.f;
-                                }
-                                if (st >= 1) {
-                                    if (FULL || st - 1 < width)
-                                        point(rrB, zrB, st - 1, hB1, hB2, m0[3 + st], m1[3 + st], m2[3 + st],
-                                              m3[3 + st], m4[3 + st]);
-                                    else m0[3 + st] = m1[3 + st] = m2[3 + st] = m3[3 + st] = m4[3 + st] = 0.f;
-                                }
+                        for (int i = 0; i < SW; ++i) {
+                            if (i < wsub) {
+                                const float xs = x1of(cs + i);
+                                const float* rc = rbuf_rec(kk, 0, i);
+                                rb1[i] = rc[10] != 0.f ? PS::ld(yb, yo + ((rowbase + cs + i) * 2 + 0) * NL + lv, xs) : make_float2(0.f, 0.f);
+                                rb2[i] = rc[11] != 0.f ? PS::ld(yb, yo + ((rowbase + cs + i) * 2 + 1) * NL + lv, xs) : make_float2(0.f, 0.f);
                             } else {
-                                if (st < 4) m0[st] = m1[st] = m2[st] = m3[st] = m4[st] = 0.f;
-                                if (st >= 1) m0[3 + st] = m1[3 + st] = m2[3 + st] = m3[3 + st] = m4[3 + st] = 0.f;
+                                rb1[i] = make_float2(0.f, 0.f);
+                                rb2[i] = rb1[i];
                             }
                         }
-                        *reinterpret_cast<float2*>(crA) = hA1;
-                        *reinterpret_cast<float2*>(crA + kPL) = hA2;
-                        *reinterpret_cast<float2*>(crB) = hB1;
-                        *reinterpret_cast<float2*>(crB + kPL) = hB2;
-                        const float r0 = reduce_scatter<float, 8>(m0, lane);
-                        const float r1 = reduce_scatter<float, 8>(m1, lane);
-                        const float r2 = reduce_scatter<float, 8>(m2, lane);
-                        const float r3 = reduce_scatter<float, 8>(m3, lane);
-                        float r4 = 0.f;
-                        if constexpr (TAU) r4 = reduce_scatter<float, 8>(m4, lane);
-                        // value v of the eight ends in lanes 4 v .. 4 v + 3: row jj + v / 4, column v % 4
-                        const int v = lane >> 2;
-                        if ((lane & 3) == 0 && (v & 3) < width) {
-                            float* d = (v < 4 ? prA : prB) + (v & 3) * NM;
-                            d[0] = r0;
-                            d[1] = r1;
-                            d[2] = r2;
-                            d[3] = r3;
-                            if constexpr (TAU) d[4] = r4;
+                    } else {
+                        __syncwarp();                        // slot (kk + 1) & 1 was last read at plane kk - 1
+                        if (kk + 1 < nr3) {
+                            issue_y(kk + 1, cs, wsub, recs);
+                            cp_async_wait<1>();              // all but the copies of plane kk + 1
+                        } else {
+                            cp_async_wait<0>();
+                        }
+                        __syncwarp();
+                        const float* e0 = eb + ((((size_t)warp * 2 + (kk & 1)) * 2) * SW) * kPL + 2 * lane;
+#pragma unroll
+                        for (int i = 0; i < SW; ++i) {
+                            if (i < wsub) {
+                                rb1[i] = *reinterpret_cast<const float2*>(e0 + (size_t)i * kPL);
+                                rb2[i] = *reinterpret_cast<const float2*>(e0 + ((size_t)SW + i) * kPL);
+                            } else {
+                                rb1[i] = make_float2(0.f, 0.f);
+                                rb2[i] = rb1[i];
+                            }
                         }
                     }
+                    // one point: Eq. 10 for the lane's velocity pair with the x1 upstream values (hp1,
+                    // hp2) of its row, the x2 upstream values rb of its column and the x3 upstream
+                    // values of its row's plane staging zr; returns the lane's moment sums of the point
+                    auto point = [&](const float* rrow, float* zr, int i, float2& hp1, float2& hp2, float& m0, float& m1,
+                                     float& m2, float& m3, float& m4) {
+                        const float4* R = reinterpret_cast<const float4*>(rrow + i * RF);
+                        const float4 A = R[0], B = R[1], C = R[2], D = R[3];
+                        const float2 z1 = *reinterpret_cast<const float2*>(zr + (size_t)i * kPL);
+                        const float2 z2 = *reinterpret_cast<const float2*>(zr + ((size_t)SW + i) * kPL);
+                        const float2 Rk = *reinterpret_cast<const float2*>(my_rtab + __float_as_int(B.w));
+                        float2 S = fma2(dup2(A.w), v3, fma2(dup2(A.z), v2, fma2(dup2(A.y), v1, dup2(A.x))));
+                        if constexpr (TAU) S = fma2(dup2(D.z), vq, S);   // nu tau (|v|^2 - 3/2)
+                        float2 t1 = fma2(dup2(C.x), hp1, fma2(dup2(C.y), hp2, dup2(B.x)));
+                        float2 t2 = fma2(dup2(C.z), rb1[i], fma2(dup2(C.w), rb2[i], dup2(B.y)));
+                        float2 t3 = fma2(dup2(D.x), z1, fma2(dup2(D.y), z2, dup2(B.z)));
+                        int4 Fa, Fb;
+                        if constexpr (SPEC) {   // + (1 - alpha) h'(x, reflected v) at walls
+                            Fa = reinterpret_cast<const int4*>(R)[4];
+                            Fb = reinterpret_cast<const int4*>(R)[5];
+                            if (Fa.x >= 0) t1 = fma2(specP, *reinterpret_cast<const float2*>(fprev[0] + (size_t)Fa.x * fstride), t1);
+                            if (Fa.y >= 0) t2 = fma2(specP, *reinterpret_cast<const float2*>(fprev[1] + (size_t)Fa.y * fstride), t2);
+                            if (Fa.z >= 0) t3 = fma2(specP, *reinterpret_cast<const float2*>(fprev[2] + (size_t)Fa.z * fstride), t3);
+                        }
+                        // the x1 term (carried from the previous point) enters last: three dependent
+                        // operations per point along the x1 chain
+                        const float2 num = fma2(a1, t1, fma2(a3, t3, fma2(a2, t2, S)));
+                        const float2 h = mul2(num, Rk);
+                        if constexpr (SPEC) {   // molecules moving into a downstream face
+                            if (Fa.w >= 0) *reinterpret_cast<float2*>(fnext[0] + (size_t)Fa.w * fstride) = h;
+                            if (Fb.x >= 0) *reinterpret_cast<float2*>(fnext[1] + (size_t)Fb.x * fstride) = h;
+                            if (Fb.y >= 0) *reinterpret_cast<float2*>(fnext[2] + (size_t)Fb.y * fstride) = h;
+                        }
+                        hp2 = hp1;
+                        hp1 = h;
+                        rb2[i] = rb1[i];
+                        rb1[i] = h;
+                        *reinterpret_cast<float2*>(zr + ((size_t)SW + i) * kPL) = z1;
+                        *reinterpret_cast<float2*>(zr + (size_t)i * kPL) = h;
+                        const float2 p0 = mul2(W, h), p1 = mul2(Wv1, h), p2v = mul2(Wv2, h), p3v = mul2(Wv3, h);
+                        m0 = p0.x + p0.y;
+                        m1 = p1.x + p1.y;
+                        m2 = p2v.x + p2v.y;
+                        m3 = p3v.x + p3v.y;
+                        if constexpr (TAU) {
+                            const float2 p4v = mul2(Wvv, h);
+                            m4 = p4v.x + p4v.y;
+                        } else {
+                            m4 = 0.f;
+                        }
                     };
-                    if (width == T1) walk_pairs(std::integral_constant<bool, true>{});
-                    else walk_pairs(std::integral_constant<bool, false>{});
-                }
-                for (; jj < nr2; ++jj) {
-                    const unsigned fm = fm_cur[kk * MR2 + jj];
-                    if (fm == 0u) continue;
-                    float *cr, *zr, *prow;
-                    const float* rrow;
-                    row_ptrs(jj, cr, zr, rrow, prow);
-                    float2 hp1 = *reinterpret_cast<const float2*>(cr);
-                    float2 hp2 = *reinterpret_cast<const float2*>(cr + kPL);
+                    auto row_ptrs = [&](int jj, float*& cr, float*& zr, const float*& rrow, float*& prow) {
+                        cr = carry + ((size_t)(warp * MROWS + kk * MR2 + jj) * 2) * kPL + 2 * lane;
+                        zr = pb + ((((size_t)warp * MR2 + jj) * 2) * SW) * kPL + 2 * lane;   // [2][SW][64]
+                        rrow = recs + (size_t)((kk * MR2 + jj) * T1) * RF;
+                        prow = part + ((size_t)(warp * MROWS + kk * MR2 + jj) * T1 + us) * NM;
+                    };
+                    // solid points are not swept: every fluid point downstream of one gives it a zero
+                    // stencil coefficient (its code marks that upstream point solid), so the values
+                    // left in the carries, rows and planes there are never used.
+                    // Rows two at a time, the upper one a column behind the lower (it needs the lower
+                    // row's value of the same column): two independent points per step.  A step with
+                    // a fluid point sweeps both of its points; a solid one has a zero record and gets
+                    // h = 0, which is as unused as the value a skipped point leaves.  Points beyond
+                    // the sub-tile width are never swept (their staging is not filled, and the x1
+                    // carries must end at the last column).
+                    int jj = 0;
+                    auto walk_pairs = [&](auto full_tag) {
+                        constexpr bool FULL = decltype(full_tag)::value;
+                        for (; jj + 1 < nr2; jj += 2) {
+                            const unsigned fa = fbits(kk * MR2 + jj), fb = fbits(kk * MR2 + jj + 1);
+                            if ((fa | fb) == 0u) continue;
+                            float *crA, *zrA, *prA, *crB, *zrB, *prB;
+                            const float *rrA, *rrB;
+                            row_ptrs(jj, crA, zrA, rrA, prA);
+                            row_ptrs(jj + 1, crB, zrB, rrB, prB);
+                            float2 hA1 = *reinterpret_cast<const float2*>(crA), hA2 = *reinterpret_cast<const float2*>(crA + kPL);
+                            float2 hB1 = *reinterpret_cast<const float2*>(crB), hB2 = *reinterpret_cast<const float2*>(crB + kPL);
+                            float m0[8], m1[8], m2[8], m3[8], m4[8];
 #pragma unroll
-                    for (int i0 = 0; i0 < T1; i0 += 4) {
-                        if (((fm >> i0) & 15u) == 0u) continue;
-                        float m0[4], m1[4], m2[4], m3[4], m4[4];
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            const int i = i0 + c;
-                            if ((fm >> i) & 1u) point(rrow, zr, i, hp1, hp2, m0[c], m1[c], m2[c], m3[c], m4[c]);
-                            else m0[c] = m1[c] = m2[c] = m3[c] = m4[c] = 0.f;
+                            for (int st = 0; st <= SW; ++st) {
+                                const bool onA = st < SW && ((fa >> st) & 1u);
+                                const bool onB = st >= 1 && ((fb >> (st - 1)) & 1u);
+                                if (onA || onB) {
+                                    if (st < SW) {
+                                        if (FULL || st < wsub) point(rrA, zrA, st, hA1, hA2, m0[st], m1[st], m2[st], m3[st], m4[st]);
+                                        else m0[st] = m1[st] = m2[st] = m3[st] = m4[st] = 0.f;
+                                    }
+                                    if (st >= 1) {
+                                        if (FULL || st - 1 < wsub)
+                                            point(rrB, zrB, st - 1, hB1, hB2, m0[3 + st], m1[3 + st], m2[3 + st],
+                                                  m3[3 + st], m4[3 + st]);
+                                        else m0[3 + st] = m1[3 + st] = m2[3 + st] = m3[3 + st] = m4[3 + st] = 0.f;
+                                    }
+                                } else {
+                                    if (st < SW) m0[st] = m1[st] = m2[st] = m3[st] = m4[st] = 0.f;
+                                    if (st >= 1) m0[3 + st] = m1[3 + st] = m2[3 + st] = m3[3 + st] = m4[3 + st] = 0.f;
+                                }
+                            }
+                            *reinterpret_cast<float2*>(crA) = hA1;
+                            *reinterpret_cast<float2*>(crA + kPL) = hA2;
+                            *reinterpret_cast<float2*>(crB) = hB1;
+                            *reinterpret_cast<float2*>(crB + kPL) = hB2;
+                            const float r0 = reduce_scatter<float, 8>(m0, lane);
+                            const float r1 = reduce_scatter<float, 8>(m1, lane);
+                            const float r2 = reduce_scatter<float, 8>(m2, lane);
+                            const float r3 = reduce_scatter<float, 8>(m3, lane);
+                            float r4 = 0.f;
+                            if constexpr (TAU) r4 = reduce_scatter<float, 8>(m4, lane);
+                            // value v of the eight ends in lanes 4 v .. 4 v + 3: row jj + v / 4, column v % 4
+                            const int v = lane >> 2;
+                            if ((lane & 3) == 0 && (v & 3) < wsub) {
+                                float* d = (v < 4 ? prA : prB) + (v & 3) * NM;
+                                d[0] = r0;
+                                d[1] = r1;
+                                d[2] = r2;
+                                d[3] = r3;
+                                if constexpr (TAU) d[4] = r4;
+                            }
                         }
-                        const float r0 = reduce_scatter<float, 4>(m0, lane);
-                        const float r1 = reduce_scatter<float, 4>(m1, lane);
-                        const float r2 = reduce_scatter<float, 4>(m2, lane);
-                        const float r3 = reduce_scatter<float, 4>(m3, lane);
-                        float r4 = 0.f;
-                        if constexpr (TAU) r4 = reduce_scatter<float, 4>(m4, lane);
-                        const int p = lane >> 3;
-                        if ((lane & 7) == 0 && i0 + p < width) {
-                            float* d = prow + (i0 + p) * NM;
-                            d[0] = r0;
-                            d[1] = r1;
-                            d[2] = r2;
-                            d[3] = r3;
-                            if constexpr (TAU) d[4] = r4;
+                    };
+                    if (wsub == SW) walk_pairs(std::integral_constant<bool, true>{});
+                    else walk_pairs(std::integral_constant<bool, false>{});
+                    if (jj < nr2) {   // the last row of an odd row count
+                        const unsigned fm = fbits(kk * MR2 + jj);
+                        if (fm != 0u) {
+                            float *cr, *zr, *prow;
+                            const float* rrow;
+                            row_ptrs(jj, cr, zr, rrow, prow);
+                            float2 hp1 = *reinterpret_cast<const float2*>(cr);
+                            float2 hp2 = *reinterpret_cast<const float2*>(cr + kPL);
+                            float m0[4], m1[4], m2[4], m3[4], m4[4];
+#pragma unroll
+                            for (int c = 0; c < SW; ++c) {
+                                if ((fm >> c) & 1u) point(rrow, zr, c, hp1, hp2, m0[c], m1[c], m2[c], m3[c], m4[c]);
+                                else m0[c] = m1[c] = m2[c] = m3[c] = m4[c] = 0.f;
+                            }
+                            const float r0 = reduce_scatter<float, 4>(m0, lane);
+                            const float r1 = reduce_scatter<float, 4>(m1, lane);
+                            const float r2 = reduce_scatter<float, 4>(m2, lane);
+                            const float r3 = reduce_scatter<float, 4>(m3, lane);
+                            float r4 = 0.f;
+                            if constexpr (TAU) r4 = reduce_scatter<float, 4>(m4, lane);
+                            const int p = lane >> 3;
+                            if ((lane & 7) == 0 && p < wsub) {
+                                float* d = prow + p * NM;
+                                d[0] = r0;
+                                d[1] = r1;
+                                d[2] = r2;
+                                d[3] = r3;
+                                if constexpr (TAU) d[4] = r4;
+                            }
+                            *reinterpret_cast<float2*>(cr) = hp1;
+                            *reinterpret_cast<float2*>(cr + kPL) = hp2;
                         }
                     }
-                    *reinterpret_cast<float2*>(cr) = hp1;
-                    *reinterpret_cast<float2*>(cr + kPL) = hp2;
+                    // x2 edge of this plane for the pencil above in x2 (ring slot), or ghost slot pi2.w
+                    // of the next iteration: the halo of the next block, or at the domain face the x2
+                    // ghost layers (periodic: same octant; specular: s2 flipped)
+                    {
+                        float* et;
+                        size_t eo, rowbase;
+                        if (pi2.w < 0) {
+                            et = P->ey;
+                            eo = ((((size_t)q * np3 + p3) * 2 * P->ns2 + (-1 - pi2.w)) * P->R3 * n1) * 2 * NL;
+                            rowbase = (size_t)kk * n1;
+                        } else {
+                            const int qy = (pi2.w > 0 || P->lateral == 1) ? q : (q ^ 2);
+                            et = P->gy;
+                            eo = ((((size_t)(par ^ 1) * 8 + qy) * P->ns2 + pi2.w) * n3 * n1) * 2 * NL;
+                            rowbase = (size_t)(k0 + kk) * n1;
+                        }
+                        // only values of fluid points are stored (layer 1 of a one-row pencil passes
+                        // the fetched upstream value through and is always stored)
+                        const unsigned f0 = fbits(kk * MR2 + nr2 - 1);
+                        const unsigned f1 = nr2 >= 2 ? fbits(kk * MR2 + nr2 - 2) : 0xffffffffu;
+#pragma unroll
+                        for (int i = 0; i < SW; ++i) {
+                            if (i < wsub) {
+                                const float xs = x1of(cs + i);
+                                if ((f0 >> i) & 1u) PS::st(et, eo + ((rowbase + cs + i) * 2 + 0) * NL + lv, rb1[i], xs);
+                                if ((f1 >> i) & 1u) PS::st(et, eo + ((rowbase + cs + i) * 2 + 1) * NL + lv, rb2[i], xs);
+                            }
+                        }
+                    }
                 }
-                // x2 edge of this plane for the pencil above in x2 (ring slot), or ghost slot pi2.w
-                // of the next iteration: the halo of the next block, or at the domain face the x2
-                // ghost layers (periodic: same octant; specular: s2 flipped)
+                // x3 edge for the pencil above in x3 (ring slot), or ghost slot pi3.w of the next
+                // iteration
                 {
                     float* et;
-                    size_t eo, rowbase;
-                    if (pi2.w < 0) {
-                        et = P->ey;
-                        eo = ((((size_t)q * np3 + p3) * 2 * P->ns2 + (-1 - pi2.w)) * P->R3 * n1) * 2 * NL;
-                        rowbase = (size_t)kk * n1;
+                    size_t eo;
+                    const bool last = pi3.w >= 0;
+                    if (!last) {
+                        et = P->ez;
+                        eo = ((((size_t)q * np2 + p2) * 2 * P->ns3 + (-1 - pi3.w)) * P->R2 * n1) * 2 * NL;
                     } else {
-                        const int qy = (pi2.w > 0 || P->lateral == 1) ? q : (q ^ 2);
-                        et = P->gy;
-                        eo = ((((size_t)(par ^ 1) * 8 + qy) * P->ns2 + pi2.w) * n3 * n1) * 2 * NL;
-                        rowbase = (size_t)(k0 + kk) * n1;
+                        const int qz = (pi3.w > 0 || P->lateral == 1) ? q : (q ^ 4);
+                        et = P->gz;
+                        eo = ((((size_t)(par ^ 1) * 8 + qz) * P->ns3 + pi3.w) * n2 * n1) * 2 * NL;
                     }
-                    // only values of fluid points are stored (layer 1 of a one-row pencil passes the
-                    // fetched upstream value through and is always stored)
-                    const unsigned f0 = fm_cur[kk * MR2 + nr2 - 1];
-                    const unsigned f1 = nr2 >= 2 ? fm_cur[kk * MR2 + nr2 - 2] : 0xffffffffu;
+                    const size_t ebase = eo + ((size_t)(last ? j0 : 0) * n1 + cs) * 2 * NL + lv;
+                    for (int jj = 0; jj < nr2; ++jj) {
+                        const unsigned f0 = fbits((nr3 - 1) * MR2 + jj);
+                        const unsigned f1 = nr3 >= 2 ? fbits((nr3 - 2) * MR2 + jj) : 0xffffffffu;
+                        const size_t eb0 = ebase + (size_t)jj * n1 * 2 * NL;
+                        const float* s = pb + ((((size_t)warp * MR2 + jj) * 2) * SW) * kPL + 2 * lane;
 #pragma unroll
-                    for (int i = 0; i < T1; ++i) {
-                        if (i < width) {
-                            const float xs = x1of(c0 + i);
-                            if ((f0 >> i) & 1u) PS::st(et, eo + ((rowbase + c0 + i) * 2 + 0) * NL + lv, rb1[i], xs);
-                            if ((f1 >> i) & 1u) PS::st(et, eo + ((rowbase + c0 + i) * 2 + 1) * NL + lv, rb2[i], xs);
+                        for (int i = 0; i < SW; ++i) {
+                            if (i < wsub) {
+                                const float xs = x1of(cs + i);
+                                if ((f0 >> i) & 1u) PS::st(et, eb0 + (size_t)(i * 2 + 0) * NL, *reinterpret_cast<const float2*>(s + (size_t)i * kPL), xs);
+                                if ((f1 >> i) & 1u)
+                                    PS::st(et, eb0 + (size_t)(i * 2 + 1) * NL, *reinterpret_cast<const float2*>(s + ((size_t)SW + i) * kPL), xs);
+                            }
                         }
                     }
                 }
-            }
-            // x3 edge for the pencil above in x3 (ring slot), or ghost slot pi3.w of the next
-            // iteration
-            {
-                float* et;
-                size_t eo;
-                const bool last = pi3.w >= 0;
-                if (!last) {
-                    et = P->ez;
-                    eo = ((((size_t)q * np2 + p2) * 2 * P->ns3 + (-1 - pi3.w)) * P->R2 * n1) * 2 * NL;
-                } else {
-                    const int qz = (pi3.w > 0 || P->lateral == 1) ? q : (q ^ 4);
-                    et = P->gz;
-                    eo = ((((size_t)(par ^ 1) * 8 + qz) * P->ns3 + pi3.w) * n2 * n1) * 2 * NL;
-                }
-                const size_t ebase = eo + ((size_t)(last ? j0 : 0) * n1 + c0) * 2 * NL + lv;
-                for (int jj = 0; jj < nr2; ++jj) {
-                    const unsigned f0 = fm_cur[(nr3 - 1) * MR2 + jj];
-                    const unsigned f1 = nr3 >= 2 ? fm_cur[(nr3 - 2) * MR2 + jj] : 0xffffffffu;
-                    const size_t eb0 = ebase + (size_t)jj * n1 * 2 * NL;
-                    const float* s = pb + ((((size_t)warp * MR2 + jj) * 2) * T1) * kPL + 2 * lane;
-#pragma unroll
-                    for (int i = 0; i < T1; ++i) {
-                        if (i < width) {
-                            const float xs = x1of(c0 + i);
-                            if ((f0 >> i) & 1u) PS::st(et, eb0 + (size_t)(i * 2 + 0) * NL, *reinterpret_cast<const float2*>(s + (size_t)i * kPL), xs);
-                            if ((f1 >> i) & 1u)
-                                PS::st(et, eb0 + (size_t)(i * 2 + 1) * NL, *reinterpret_cast<const float2*>(s + ((size_t)T1 + i) * kPL), xs);
-                        }
-                    }
-                }
-            }
-            }   // tfl
-            else if (ti.z >= 0 && !BF) {   // the x1 carry-in of a tile without fluid: complete it here
-                cp_async_commit();
-                cp_async_wait<0>();
-            }
+            }   // sub-tiles
             if (ti.w >= 0 && tfl) {   // x1 carry into ghost slot ti.w of the next iteration
                 const size_t gxo = ((((size_t)(par ^ 1) * 8 + q) * P->ns1 + ti.w) * n3 * n2) * 2 * NL;
                 for (int kk = 0; kk < nr3; ++kk)
@@ -710,15 +722,15 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
             if (threadIdx.x == 0 && it != a.withhold_item) {
                 publish_gpu(prog + p3 * np2 + p2, t + 1);
             }
-            pre_next = s_pre != 0 && tile_fluid(fmask + ((t + 1) & 1) * MROWS);
+            pre_next = s_pre != 0 && has_fluid(fmask + ((t + 1) & 1) * MROWS, 0);
             if constexpr (!BF) {
                 // the plane staging and y slot 0 are free (the x3 edges were stored from the staging
                 // before the barrier): start the next tile's first copies now
                 if (pre_next) {
                     const int4 tn = tile_info(t + 1);
                     const float* rbn = rec + (size_t)((t + 1) & 1) * MROWS * T1 * RF;
-                    issue_z(tn.x, tn.y, rbn);
-                    issue_y(0, tn.x, tn.y, rbn);
+                    issue_z(tn.x, min(SW, tn.y), rbn);
+                    issue_y(0, tn.x, min(SW, tn.y), rbn);
                 }
             }
             // moment partials of this octant and group: warp sums in warp order
@@ -750,7 +762,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
 size_t sweep3d_f32x2_smem(int T1, int NW, int R2, int R3, int tau, int spec) {
     const size_t rows = (size_t)R2 * R3;
     return sizeof(float) * (2 * rows * T1 * (spec ? 24 : kRec) + (size_t)NW * rows * T1 * (tau ? 5 : 4) +
-                            (size_t)NW * rows * 2 * kPL + (size_t)NW * R2 * 2 * T1 * kPL + (size_t)NW * 2 * 2 * T1 * kPL +
+                            (size_t)NW * rows * 2 * kPL + (size_t)NW * R2 * 2 * kSubW * kPL + (size_t)NW * 2 * 2 * kSubW * kPL +
                             (size_t)NW * 8 * kPL) +
            sizeof(unsigned) * 2 * rows + sizeof(int) * rows;
 }
