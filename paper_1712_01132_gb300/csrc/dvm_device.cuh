@@ -112,6 +112,16 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
     return d;
 }
 
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    float2 d;
+    asm("{.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) {
     float2 d;
     asm("{.reg .b64 ra, rb, rd;\n\t"
@@ -120,6 +130,31 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) {
         : "=f"(d.x), "=f"(d.y)
         : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
     return d;
+}
+
+// reduce_scatter for pairs of values (two moments per element): the same lane tree, each level's
+// two additions done by one packed instruction.
+template <int NP>
+__device__ __forceinline__ float2 reduce_scatter2(float2 (&v)[NP], int lane) {
+    constexpr int LOG = (NP == 16) ? 4 : (NP == 8 ? 3 : (NP == 4 ? 2 : 1));
+#pragma unroll
+    for (int s = 0; s < LOG; ++s) {
+        const int off = 16 >> s;
+        const int cnt = NP >> s;
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int k = 0; k < cnt / 2; ++k) {
+            const float2 send = up ? v[k] : v[k + cnt / 2];
+            const float2 keep = up ? v[k + cnt / 2] : v[k];
+            const float2 recv = make_float2(__shfl_xor_sync(0xffffffffu, send.x, off), __shfl_xor_sync(0xffffffffu, send.y, off));
+            v[k] = add2(keep, recv);
+        }
+    }
+    float2 r = v[0];
+#pragma unroll
+    for (int off = 16 >> LOG; off >= 1; off >>= 1)
+        r = add2(r, make_float2(__shfl_xor_sync(0xffffffffu, r.x, off), __shfl_xor_sync(0xffffffffu, r.y, off)));
+    return r;
 }
 
 }  // namespace dvm

@@ -167,6 +167,9 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
         const float2 a1 = make_float2(la[3], lb[3]), a2 = make_float2(la[4], lb[4]), a3 = make_float2(la[5], lb[5]);
         const float2 W = make_float2(la[6], lb[6]), Wv1 = make_float2(la[7], lb[7]);
         const float2 Wv2 = make_float2(la[8], lb[8]), Wv3 = make_float2(la[9], lb[9]);
+        // moment weights regrouped by velocity slot: (rho, u1) and (u2, u3) of slot 2 l and of 2 l + 1
+        const float2 Wa01 = make_float2(W.x, Wv1.x), Wb01 = make_float2(W.y, Wv1.y);
+        const float2 Wa23 = make_float2(Wv2.x, Wv3.x), Wb23 = make_float2(Wv2.y, Wv3.y);
         // temperature term: |v|^2 - 3/2 and W |v|^2
         const float2 vq = make_float2(la[18], lb[18]), Wvv = make_float2(la[19], lb[19]);
         float* my_rtab = rtab + (size_t)warp * 8 * kPL + 2 * lane;
@@ -483,9 +486,10 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                     }
                     // one point: Eq. 10 for the lane's velocity pair with the x1 upstream values (hp1,
                     // hp2) of its row, the x2 upstream values rb of its column and the x3 upstream
-                    // values of its row's plane staging zr; returns the lane's moment sums of the point
-                    auto point = [&](const float* rrow, float* zr, int i, float2& hp1, float2& hp2, float& m0, float& m1,
-                                     float& m2, float& m3, float& m4) {
+                    // values of its row's plane staging zr; returns the lane's moment sums of the
+                    // point: (rho, u1), (u2, u3) and the temperature moment
+                    auto point = [&](const float* rrow, float* zr, int i, float2& hp1, float2& hp2, float2& M01,
+                                     float2& M23, float& m4) {
                         const float4* R = reinterpret_cast<const float4*>(rrow + i * RF);
                         const float4 A = R[0], B = R[1], C = R[2], D = R[3];
                         const float2 z1 = *reinterpret_cast<const float2*>(zr + (size_t)i * kPL);
@@ -519,11 +523,8 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                         rb1[i] = h;
                         *reinterpret_cast<float2*>(zr + ((size_t)SW + i) * kPL) = z1;
                         *reinterpret_cast<float2*>(zr + (size_t)i * kPL) = h;
-                        const float2 p0 = mul2(W, h), p1 = mul2(Wv1, h), p2v = mul2(Wv2, h), p3v = mul2(Wv3, h);
-                        m0 = p0.x + p0.y;
-                        m1 = p1.x + p1.y;
-                        m2 = p2v.x + p2v.y;
-                        m3 = p3v.x + p3v.y;
+                        M01 = fma2(Wb01, dup2(h.y), mul2(Wa01, dup2(h.x)));
+                        M23 = fma2(Wb23, dup2(h.y), mul2(Wa23, dup2(h.x)));
                         if constexpr (TAU) {
                             const float2 p4v = mul2(Wvv, h);
                             m4 = p4v.x + p4v.y;
@@ -558,46 +559,48 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                             row_ptrs(jj + 1, crB, zrB, rrB, prB);
                             float2 hA1 = *reinterpret_cast<const float2*>(crA), hA2 = *reinterpret_cast<const float2*>(crA + kPL);
                             float2 hB1 = *reinterpret_cast<const float2*>(crB), hB2 = *reinterpret_cast<const float2*>(crB + kPL);
-                            float m0[8], m1[8], m2[8], m3[8], m4[8];
+                            float2 M01[8], M23[8];
+                            float m4[8];
+                            const float2 z2 = make_float2(0.f, 0.f);
 #pragma unroll
                             for (int st = 0; st <= SW; ++st) {
                                 const bool onA = st < SW && ((fa >> st) & 1u);
                                 const bool onB = st >= 1 && ((fb >> (st - 1)) & 1u);
                                 if (onA || onB) {
                                     if (st < SW) {
-                                        if (FULL || st < wsub) point(rrA, zrA, st, hA1, hA2, m0[st], m1[st], m2[st], m3[st], m4[st]);
-                                        else m0[st] = m1[st] = m2[st] = m3[st] = m4[st] = 0.f;
+                                        if (FULL || st < wsub) point(rrA, zrA, st, hA1, hA2, M01[st], M23[st], m4[st]);
+                                        else { M01[st] = M23[st] = z2; m4[st] = 0.f; }
                                     }
                                     if (st >= 1) {
-                                        if (FULL || st - 1 < wsub)
-                                            point(rrB, zrB, st - 1, hB1, hB2, m0[3 + st], m1[3 + st], m2[3 + st],
-                                                  m3[3 + st], m4[3 + st]);
-                                        else m0[3 + st] = m1[3 + st] = m2[3 + st] = m3[3 + st] = m4[3 + st] = 0.f;
+                                        if (FULL || st - 1 < wsub) point(rrB, zrB, st - 1, hB1, hB2, M01[3 + st], M23[3 + st], m4[3 + st]);
+                                        else { M01[3 + st] = M23[3 + st] = z2; m4[3 + st] = 0.f; }
                                     }
                                 } else {
-                                    if (st < SW) m0[st] = m1[st] = m2[st] = m3[st] = m4[st] = 0.f;
-                                    if (st >= 1) m0[3 + st] = m1[3 + st] = m2[3 + st] = m3[3 + st] = m4[3 + st] = 0.f;
+                                    if (st < SW) { M01[st] = M23[st] = z2; m4[st] = 0.f; }
+                                    if (st >= 1) { M01[3 + st] = M23[3 + st] = z2; m4[3 + st] = 0.f; }
                                 }
                             }
                             *reinterpret_cast<float2*>(crA) = hA1;
                             *reinterpret_cast<float2*>(crA + kPL) = hA2;
                             *reinterpret_cast<float2*>(crB) = hB1;
                             *reinterpret_cast<float2*>(crB + kPL) = hB2;
-                            const float r0 = reduce_scatter<float, 8>(m0, lane);
-                            const float r1 = reduce_scatter<float, 8>(m1, lane);
-                            const float r2 = reduce_scatter<float, 8>(m2, lane);
-                            const float r3 = reduce_scatter<float, 8>(m3, lane);
+                            const float2 r01 = reduce_scatter2<8>(M01, lane);
+                            const float2 r23 = reduce_scatter2<8>(M23, lane);
                             float r4 = 0.f;
                             if constexpr (TAU) r4 = reduce_scatter<float, 8>(m4, lane);
                             // value v of the eight ends in lanes 4 v .. 4 v + 3: row jj + v / 4, column v % 4
                             const int v = lane >> 2;
                             if ((lane & 3) == 0 && (v & 3) < wsub) {
                                 float* d = (v < 4 ? prA : prB) + (v & 3) * NM;
-                                d[0] = r0;
-                                d[1] = r1;
-                                d[2] = r2;
-                                d[3] = r3;
-                                if constexpr (TAU) d[4] = r4;
+                                if constexpr (TAU) {
+                                    d[0] = r01.x;
+                                    d[1] = r01.y;
+                                    d[2] = r23.x;
+                                    d[3] = r23.y;
+                                    d[4] = r4;
+                                } else {
+                                    *reinterpret_cast<float4*>(d) = make_float4(r01.x, r01.y, r23.x, r23.y);
+                                }
                             }
                         }
                     };
@@ -611,25 +614,27 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                             row_ptrs(jj, cr, zr, rrow, prow);
                             float2 hp1 = *reinterpret_cast<const float2*>(cr);
                             float2 hp2 = *reinterpret_cast<const float2*>(cr + kPL);
-                            float m0[4], m1[4], m2[4], m3[4], m4[4];
+                            float2 M01[4], M23[4];
+                            float m4[4];
 #pragma unroll
                             for (int c = 0; c < SW; ++c) {
-                                if ((fm >> c) & 1u) point(rrow, zr, c, hp1, hp2, m0[c], m1[c], m2[c], m3[c], m4[c]);
-                                else m0[c] = m1[c] = m2[c] = m3[c] = m4[c] = 0.f;
+                                if ((fm >> c) & 1u) point(rrow, zr, c, hp1, hp2, M01[c], M23[c], m4[c]);
+                                else {
+                                    M01[c] = M23[c] = make_float2(0.f, 0.f);
+                                    m4[c] = 0.f;
+                                }
                             }
-                            const float r0 = reduce_scatter<float, 4>(m0, lane);
-                            const float r1 = reduce_scatter<float, 4>(m1, lane);
-                            const float r2 = reduce_scatter<float, 4>(m2, lane);
-                            const float r3 = reduce_scatter<float, 4>(m3, lane);
+                            const float2 r01 = reduce_scatter2<4>(M01, lane);
+                            const float2 r23 = reduce_scatter2<4>(M23, lane);
                             float r4 = 0.f;
                             if constexpr (TAU) r4 = reduce_scatter<float, 4>(m4, lane);
                             const int p = lane >> 3;
                             if ((lane & 7) == 0 && p < wsub) {
                                 float* d = prow + p * NM;
-                                d[0] = r0;
-                                d[1] = r1;
-                                d[2] = r2;
-                                d[3] = r3;
+                                d[0] = r01.x;
+                                d[1] = r01.y;
+                                d[2] = r23.x;
+                                d[3] = r23.y;
                                 if constexpr (TAU) d[4] = r4;
                             }
                             *reinterpret_cast<float2*>(cr) = hp1;
