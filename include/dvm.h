@@ -74,10 +74,10 @@ typedef struct {
     int lateral_bc;      /* DVM_LATERAL_SPECULAR (Eq. 8) or DVM_LATERAL_PERIODIC */
     int check_interval;  /* iterations between permeability/Err evaluations (Sec. 3.1: 100) */
     void* stream;        /* cudaStream_t, or NULL for the legacy default stream */
-    int tile_x1;         /* sweep tile width along x1: 2D FP64 8 or 16, 2D FP32 4 or 8, 3D 4 or 8
-                            (3D FP32 sweeps an 8-column tile as two 4-column sub-tiles between one
-                            neighbour wait and one publish); 0 = automatic (8 in 2D, 8 in 3D FP32,
-                            4 in 3D FP64) */
+    int tile_x1;         /* sweep tile width along x1: 2D FP64 8 or 16, 2D FP32 4, 8 or 16, 3D 4
+                            or 8 (FP32 sweeps a 16-column 2D tile as two 8-column sub-tiles and an
+                            8-column 3D tile as two 4-column sub-tiles, between one neighbour wait
+                            and one publish); 0 = automatic (8 in 2D, 8 in 3D FP32, 4 in 3D FP64) */
     int band_rows;       /* rows per sweep band in 2D, pencil rows R2 = R3 in 3D (0 = automatic:
                             8 in 2D, 4 in 3D; in 3D the tile width, then the rows, are reduced
                             until the CTA fits shared memory) */
@@ -228,7 +228,7 @@ dvm_status dvm_wall_density_at(dvm_ctx* ctx, int prob, double* rhos);
 /* Tile autotuner (no counterpart in the paper, whose kernel has no tiles): times `iters`
  * iterations (after two untimed ones) of every candidate sweep tile shape on the given problems,
  * with the options in *opt otherwise, and writes the fastest into opt->tile_x1 and
- * opt->band_rows (and, in 3D, opt->group_warps).  Candidates: 2D FP32 x1 tile {8, 4} x band rows
+ * opt->band_rows (and, in 3D, opt->group_warps).  Candidates: 2D FP32 x1 tile {16, 8, 4} x band rows
  * {4, 8, 12, 16}; 2D FP64 x1 tile {8, 16} x band rows {4, 8, 12, 16}; 3D x1 tile {4, 8} x pencil
  * rows {2, 3, 4, 5, 6} x warps per CTA {8, 4} (only the caller's value when opt->group_warps is
  * nonzero); shapes that do not fit the device are skipped.  Because every tile shape runs the same dependency-exact

@@ -272,8 +272,8 @@ dvm_status build_2d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     if (c->NW > 16) return fail(c, DVM_EINVAL, "too many velocities per quadrant");
     // ---- tiles
     c->T1 = c->opt.tile_x1 ? c->opt.tile_x1 : 8;
-    if (c->prec == DVM_FP32) {               // the packed FP32 kernel has 4- and 8-column tiles
-        if (c->T1 != 4 && c->T1 != 8) return fail(c, DVM_EINVAL, "tile_x1 must be 4 or 8 for FP32");
+    if (c->prec == DVM_FP32) {               // the packed FP32 kernel: 4-, 8- and 16-column tiles
+        if (c->T1 != 4 && c->T1 != 8 && c->T1 != 16) return fail(c, DVM_EINVAL, "tile_x1 must be 4, 8 or 16 for FP32");
     } else if (c->T1 != 8 && c->T1 != 16) {
         return fail(c, DVM_EINVAL, "tile_x1 must be 8 or 16 for FP64");
     }
@@ -1739,7 +1739,7 @@ dvm_status dvm_autotune(int nprob, const dvm_geometry* geoms, const double* kn, 
                 for (int r : {2, 3, 4, 5, 6}) cand.push_back({t, r, gw0 > 0 ? gw0 : w});
         }
     } else if (opt->precision == DVM_FP32) {
-        for (int t : {8, 4})
+        for (int t : {16, 8, 4})
             for (int r : {4, 8, 12, 16}) cand.push_back({t, r, gw0});
     } else {
         for (int t : {8, 16})

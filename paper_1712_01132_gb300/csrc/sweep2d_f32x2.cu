@@ -36,6 +36,7 @@ constexpr int kMaxRounds = 2;
 
 struct LaneQ {
     float2 v1[2], v2[2], a1[2], a2[2], W[2], Wv1[2], Wv2[2];
+    float2 Wx[4];   // (W, W v1) of the lane's four velocities, for the packed (rho, u1) sums
 };
 
 struct RawPoint {           // global data of one point needed to build its record
@@ -50,7 +51,12 @@ __device__ __forceinline__ float2 dup(float x) { return make_float2(x, x); }
 
 template <int T1, bool XS, bool SPEC>
 __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<float> a) {
-    constexpr int kLPP = 32 / T1;               // lanes per point after the reduce-scatter
+    // a tile of T1 columns (one wait, one publish, one record load) is swept as sub-tiles of SW
+    // columns, whose x2 upstream values are held in registers
+    constexpr int SW = T1 > 8 ? 8 : T1;
+    constexpr int NSUB = T1 / SW;
+    static_assert(T1 % SW == 0 && 32 % T1 == 0, "tile width: 4, 8 or 16 columns");
+    constexpr int kLPP = 32 / SW;               // lanes per point after the reduce-scatter
     constexpr int RF = SPEC ? 16 : kRecF;       // record floats (face ids in the last four)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
@@ -111,6 +117,8 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
                 L.W[k] = make_float2(la[4], lb[4]);
                 L.Wv1[k] = make_float2(la[5], lb[5]);
                 L.Wv2[k] = make_float2(la[6], lb[6]);
+                L.Wx[2 * k] = make_float2(la[4], la[5]);
+                L.Wx[2 * k + 1] = make_float2(lb[4], lb[5]);
             }
             float* rt = rtab + (size_t)warp * 4 * 128 + 4 * lane;
 #pragma unroll
@@ -270,18 +278,33 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
             if (s_abort) return;
             const float* rbuf = rec + (size_t)buf * RB * T1 * RF;
             const unsigned* mk = rmask + buf * RB;
+            for (int u = 0; u < NSUB; ++u) {
+            const int cs = c0 + u * SW;                       // first column of the sub-tile
+            const int wsub = min(SW, width - u * SW);         // its width
+            if (wsub <= 0) break;
+            const int us = u * SW;
+            // fluid bits of row r in this sub-tile
+            auto fbits = [&](int r) -> unsigned { return (mk[r] >> us) & ((1u << SW) - 1u); };
+            if constexpr (NSUB > 1) {
+                // a sub-tile without fluid is not swept (its edge and carries are read by no fluid
+                // point: every fluid reader has a zero coefficient for them)
+                unsigned any = 0u;
+                for (int r = lane; r < nrows; r += 32) any |= fbits(r);
+                if (!__any_sync(0xffffffffu, any != 0u)) continue;
+            }
+            const float* rsub = rbuf + (size_t)us * RF;       // record of (row 0, column cs)
             // the two rows below: previous band's top edge or the x2 ghost layers
-            float4 rb1[T1], rb2[T1];
+            float4 rb1[SW], rb2[SW];
             {
                 const int below = s_binfo[2];
                 const float* eb = (below >= 0)
                     ? P->glat + (((size_t)(par * 4 + q) * P->nslots + below) * n1) * 2 * NL
                     : P->edge + ((size_t)(q * 2 * P->nslots + (-1 - below)) * n1) * 2 * NL;
 #pragma unroll
-                for (int i = 0; i < T1; ++i) {
-                    if (i < width) {
-                        rb1[i] = __ldcg(reinterpret_cast<const float4*>(eb + ((size_t)(c0 + i) * 2 + 0) * NL + kVL * wl));
-                        rb2[i] = __ldcg(reinterpret_cast<const float4*>(eb + ((size_t)(c0 + i) * 2 + 1) * NL + kVL * wl));
+                for (int i = 0; i < SW; ++i) {
+                    if (i < wsub) {
+                        rb1[i] = __ldcg(reinterpret_cast<const float4*>(eb + ((size_t)(cs + i) * 2 + 0) * NL + kVL * wl));
+                        rb2[i] = __ldcg(reinterpret_cast<const float4*>(eb + ((size_t)(cs + i) * 2 + 1) * NL + kVL * wl));
                     } else {
                         rb1[i] = make_float4(0.f, 0.f, 0.f, 0.f);
                         rb2[i] = rb1[i];
@@ -290,9 +313,9 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
             }
             // one point of a row: Eq. 10 for the lane's four velocities, with the x1 upstream values
             // (hp1, hp2) carried along the row and the x2 upstream values (u1, u2) of its column;
-            // returns the lane's moment sums of the point
+            // returns the lane's moment sums of the point: (rho, u1) and u2
             auto point = [&](const float* rrow, int i, float2 (&hp1)[2], float2 (&hp2)[2], float4& u1, float4& u2,
-                             float& m0, float& m1, float& m2) {
+                             float2& M01, float& m2) {
                 const float4* Rp = reinterpret_cast<const float4*>(rrow + i * RF);
                 const float4 A = Rp[0];                 // a b1 b2 roff
                 const float4 B = Rp[1];                 // E1 K1x K2x E2
@@ -333,11 +356,8 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
                     if (Fi.z >= 0) *reinterpret_cast<float4*>(fnext1 + (size_t)Fi.z * 2 * NL) = u1;
                     if (Fi.w >= 0) *reinterpret_cast<float4*>(fnext2 + (size_t)Fi.w * 2 * NL) = u1;
                 }
-                const float2 p0 = fma2(L.W[1], h[1], mul2(L.W[0], h[0]));
-                const float2 p1 = fma2(L.Wv1[1], h[1], mul2(L.Wv1[0], h[0]));
+                M01 = fma2(L.Wx[3], dup(h[1].y), fma2(L.Wx[2], dup(h[1].x), fma2(L.Wx[1], dup(h[0].y), mul2(L.Wx[0], dup(h[0].x)))));
                 const float2 p2 = fma2(L.Wv2[1], h[1], mul2(L.Wv2[0], h[0]));
-                m0 = p0.x + p0.y;
-                m1 = p1.x + p1.y;
                 m2 = p2.x + p2.y;
             };
             auto load_carry = [&](int r, float2 (&hp1)[2], float2 (&hp2)[2]) {
@@ -357,70 +377,79 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
             // Rows are walked two at a time, the upper one a column behind the lower (it needs the
             // lower row's value of the same column), which gives every step two independent points;
             // the moments of both rows are then reduced together.  A pair is skipped when neither
-            // row has fluid in the tile; an empty row of a pair is swept anyway: its zero records
-            // give h = 0, which no fluid point reads (its code marks that upstream point solid), so
-            // the result is the same as with the row skipped.
+            // row has fluid in the sub-tile; an empty row of a pair is swept anyway: its zero
+            // records give h = 0, which no fluid point reads (its code marks that upstream point
+            // solid), so the result is the same as with the row skipped.
             auto walk_rows = [&](auto full_tag) {
                 constexpr bool FULL = decltype(full_tag)::value;
                 int r = 0;
                 for (; r + 1 < nrows; r += 2) {
-                    if ((mk[r] | mk[r + 1]) == 0u) continue;
+                    if ((fbits(r) | fbits(r + 1)) == 0u) continue;
                     float2 hA1[2], hA2[2], hB1[2], hB2[2];
                     load_carry(r, hA1, hA2);
                     load_carry(r + 1, hB1, hB2);
-                    const float* rowA = rbuf + (size_t)r * T1 * RF;
+                    const float* rowA = rsub + (size_t)r * T1 * RF;
                     const float* rowB = rowA + (size_t)T1 * RF;
-                    float m0[2 * T1], m1[2 * T1], m2[2 * T1];
+                    float2 M01[2 * SW];
+                    float m2[2 * SW];
 #pragma unroll
-                    for (int st = 0; st <= T1; ++st) {
-                        if (st < T1) {
+                    for (int st = 0; st <= SW; ++st) {
+                        if (st < SW) {
                             const int i = st;
-                            if (FULL || i < width) point(rowA, i, hA1, hA2, rb1[i], rb2[i], m0[i], m1[i], m2[i]);
-                            else m0[i] = m1[i] = m2[i] = 0.f;
+                            if (FULL || i < wsub) point(rowA, i, hA1, hA2, rb1[i], rb2[i], M01[i], m2[i]);
+                            else {
+                                M01[i] = make_float2(0.f, 0.f);
+                                m2[i] = 0.f;
+                            }
                         }
                         if (st >= 1) {
                             const int i = st - 1;
-                            if (FULL || i < width) point(rowB, i, hB1, hB2, rb1[i], rb2[i], m0[T1 + i], m1[T1 + i], m2[T1 + i]);
-                            else m0[T1 + i] = m1[T1 + i] = m2[T1 + i] = 0.f;
+                            if (FULL || i < wsub) point(rowB, i, hB1, hB2, rb1[i], rb2[i], M01[SW + i], m2[SW + i]);
+                            else {
+                                M01[SW + i] = make_float2(0.f, 0.f);
+                                m2[SW + i] = 0.f;
+                            }
                         }
                     }
                     store_carry(r, hA1, hA2);
                     store_carry(r + 1, hB1, hB2);
-                    const float s0 = reduce_scatter<float, 2 * T1>(m0, lane);
-                    const float s1 = reduce_scatter<float, 2 * T1>(m1, lane);
-                    const float s2 = reduce_scatter<float, 2 * T1>(m2, lane);
-                    // value v of the 2 T1 ends in the lanes v * 32 / (2 T1) onward: row r + v / T1
+                    const float2 s01 = reduce_scatter2<2 * SW>(M01, lane);
+                    const float s2 = reduce_scatter<float, 2 * SW>(m2, lane);
+                    // value v of the 2 SW ends in the lanes v * 32 / (2 SW) onward: row r + v / SW
                     if ((lane & (kLPP / 2 - 1)) == 0) {
                         const int v = lane / (kLPP / 2);
-                        float* d = part + ((size_t)(warp * RB + r + v / T1) * T1 + (v % T1)) * 3;
-                        d[0] = s0;
-                        d[1] = s1;
+                        float* d = part + ((size_t)(warp * RB + r + v / SW) * T1 + us + (v % SW)) * 3;
+                        d[0] = s01.x;
+                        d[1] = s01.y;
                         d[2] = s2;
                     }
                 }
-                if (r < nrows && mk[r] != 0u) {   // the last row of an odd band
+                if (r < nrows && fbits(r) != 0u) {   // the last row of an odd band
                     float2 hp1[2], hp2[2];
                     load_carry(r, hp1, hp2);
-                    const float* rrow = rbuf + (size_t)r * T1 * RF;
-                    float m0[T1], m1[T1], m2[T1];
+                    const float* rrow = rsub + (size_t)r * T1 * RF;
+                    float2 M01[SW];
+                    float m2[SW];
 #pragma unroll
-                    for (int i = 0; i < T1; ++i) {
-                        if (FULL || i < width) point(rrow, i, hp1, hp2, rb1[i], rb2[i], m0[i], m1[i], m2[i]);
-                        else m0[i] = m1[i] = m2[i] = 0.f;
+                    for (int i = 0; i < SW; ++i) {
+                        if (FULL || i < wsub) point(rrow, i, hp1, hp2, rb1[i], rb2[i], M01[i], m2[i]);
+                        else {
+                            M01[i] = make_float2(0.f, 0.f);
+                            m2[i] = 0.f;
+                        }
                     }
                     store_carry(r, hp1, hp2);
-                    const float s0 = reduce_scatter<float, T1>(m0, lane);
-                    const float s1 = reduce_scatter<float, T1>(m1, lane);
-                    const float s2 = reduce_scatter<float, T1>(m2, lane);
+                    const float2 s01 = reduce_scatter2<SW>(M01, lane);
+                    const float s2 = reduce_scatter<float, SW>(m2, lane);
                     if ((lane & (kLPP - 1)) == 0) {
-                        float* d = part + ((size_t)(warp * RB + r) * T1 + lane / kLPP) * 3;
-                        d[0] = s0;
-                        d[1] = s1;
+                        float* d = part + ((size_t)(warp * RB + r) * T1 + us + lane / kLPP) * 3;
+                        d[0] = s01.x;
+                        d[1] = s01.y;
                         d[2] = s2;
                     }
                 }
             };
-            if (width == T1) walk_rows(std::integral_constant<bool, true>{});
+            if (wsub == SW) walk_rows(std::integral_constant<bool, true>{});
             else walk_rows(std::integral_constant<bool, false>{});
             // band edge for the band above, or the x2 ghost layers of the next iteration (Eq. 8 /
             // periodic: the reflected quadrant reads the same lane)
@@ -434,33 +463,38 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
                     et = P->glat + (((size_t)((par ^ 1) * 4 + qd) * P->nslots + above) * n1) * 2 * NL;
                 }
 #pragma unroll
-                for (int i = 0; i < T1; ++i) {
-                    if (i < width) {
-                        *reinterpret_cast<float4*>(et + ((size_t)(c0 + i) * 2 + 0) * NL + kVL * wl) = rb1[i];
-                        *reinterpret_cast<float4*>(et + ((size_t)(c0 + i) * 2 + 1) * NL + kVL * wl) = rb2[i];
+                for (int i = 0; i < SW; ++i) {
+                    if (i < wsub) {
+                        *reinterpret_cast<float4*>(et + ((size_t)(cs + i) * 2 + 0) * NL + kVL * wl) = rb1[i];
+                        *reinterpret_cast<float4*>(et + ((size_t)(cs + i) * 2 + 1) * NL + kVL * wl) = rb2[i];
                     }
                 }
             }
+            }   // sub-tiles
             // x1 ghost layers of the next iteration (periodic in x1, same quadrant) or the halo of
             // the next x1 subdomain
             if (cout_slot >= 0) carry_out(cout_slot);
             if (t + 1 < ntiles) store_rec(buf ^ 1, nxt);
             __syncthreads();
             if (threadIdx.x == 0 && it != a.withhold_item) publish_gpu(P->prog + q * nb + band, t + 1);
-            // moment partials of this quadrant: sum of the warps' lane sums, in warp order
-            for (int idx = threadIdx.x; idx < nrows * width * 3; idx += blockDim.x) {
-                const int m = idx % 3;
-                const int pi = idx / 3;
-                const int rr = pi / width;
-                const int i = pi - rr * width;
-                float s = 0.f;
-                if ((mk[rr] >> i) & 1u)
-                    for (int w = 0; w < NW; ++w) s += part[((size_t)(w * RB + rr) * T1 + i) * 3 + m];
-                const int ic = c0 + i;
-                const int x = s1neg ? n1 - 1 - ic : ic;
-                const int yo = row0 + rr;
-                const int y = s2neg ? n2 - 1 - yo : yo;
-                P->P[((size_t)q * 3 + m) * N + (size_t)y * n1 + x] = s;
+            // moment partials of this quadrant: sum of the warps' lane sums, in warp order (idx =
+            // (rr T1 + i) 3 + m; only fluid points have bits, and only their partials are read)
+            {
+                const unsigned* mk = rmask + buf * RB;
+                for (int idx = threadIdx.x; idx < nrows * T1 * 3; idx += blockDim.x) {
+                    const int m = idx % 3;
+                    const int pi = idx / 3;
+                    const int rr = pi / T1;
+                    const int i = pi % T1;
+                    if (!((mk[rr] >> i) & 1u)) continue;
+                    float s = 0.f;
+                    for (int w = 0; w < NW; ++w) s += part[((size_t)(w * RB) * T1) * 3 + idx];
+                    const int ic = c0 + i;
+                    const int x = s1neg ? n1 - 1 - ic : ic;
+                    const int yo = row0 + rr;
+                    const int y = s2neg ? n2 - 1 - yo : yo;
+                    P->P[((size_t)q * 3 + m) * N + (size_t)y * n1 + x] = s;
+                }
             }
         }
         __syncthreads();
@@ -494,6 +528,7 @@ static cudaError_t launch_f32x2_tt(const SweepArgs2D<float>& a, int xs, int grid
 
 // xs: x1 subdomains (tile tables and lagged x1 halos); a.spec: specular wall parts
 cudaError_t launch_sweep2d_f32x2(const SweepArgs2D<float>& a, int T1, int xs, int grid, int NW, cudaStream_t st) {
+    if (T1 == 16) return launch_f32x2_tt<16>(a, xs, grid, NW, st);
     if (T1 == 8) return launch_f32x2_tt<8>(a, xs, grid, NW, st);
     if (T1 == 4) return launch_f32x2_tt<4>(a, xs, grid, NW, st);
     return cudaErrorInvalidValue;
@@ -514,6 +549,7 @@ static cudaError_t occupancy_f32x2_tt(int xs, int spec, int NW, int max_rows, in
 }
 
 cudaError_t sweep2d_f32x2_occupancy(int T1, int xs, int spec, int NW, int max_rows, int* blocks_per_sm) {
+    if (T1 == 16) return occupancy_f32x2_tt<16>(xs, spec, NW, max_rows, blocks_per_sm);
     if (T1 == 8) return occupancy_f32x2_tt<8>(xs, spec, NW, max_rows, blocks_per_sm);
     if (T1 == 4) return occupancy_f32x2_tt<4>(xs, spec, NW, max_rows, blocks_per_sm);
     return cudaErrorInvalidValue;

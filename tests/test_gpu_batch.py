@@ -87,7 +87,7 @@ def test_autotuner_picks_a_candidate_with_identical_results(precision):
     t1, rows, _, ms = dvm.autotune(masks, kns, v, w, iters=5, precision=precision, lateral="periodic")
     assert ms > 0
     if precision == "fp32":
-        assert t1 in (4, 8) and rows in (4, 8, 12, 16)
+        assert t1 in (4, 8, 16) and rows in (4, 8, 12, 16)
     else:
         assert t1 in (8, 16) and rows in (4, 8, 12, 16)
     a = dvm.Solver(masks, kns, v, w, precision=precision, lateral="periodic")

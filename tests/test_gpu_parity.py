@@ -118,7 +118,7 @@ def test_tile_and_band_shapes_give_identical_bits():
     (v, w), _ = _grid(2, 16)
     ref = None
     shapes = {"fp64": ((8, 8), (16, 3), (8, 35), (16, 1), (8, 17)),
-              "fp32": ((8, 8), (4, 3), (8, 35), (4, 1), (8, 17), (4, 32))}
+              "fp32": ((8, 8), (4, 3), (8, 35), (4, 1), (8, 17), (4, 32), (16, 8), (16, 3), (16, 1))}
     for prec in ("fp64", "fp32"):
         ref = None
         for t1, rows in shapes[prec]:
