@@ -331,7 +331,9 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
             }
             cp_async_commit();
         };
-        // the x3 planes below the tile's first plane into the plane staging (committed with y(0))
+        // the x3 planes below the tile's first plane into the plane staging (committed with y(0)):
+        // the plane just below (edge layer 0) into staging layer 1 and the one below it into layer
+        // 0, where plane 0 reads them (the staging layer of plane kk - 1 is (kk + 1) & 1)
         auto issue_z = [&](int cc0, int wd, const float* rb) {
             const float* zs = zb + zo + ((size_t)(zg ? j0 : 0) * n1 + cc0) * 2 * NL + lw;
             float* zd = pb + ((size_t)warp * MR2 * 2 * SW) * kPL + 4 * hl;
@@ -343,7 +345,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                     const int m = half + 2 * u;
                     const int layer = m / SW, i = m % SW;
                     if (i < wd)
-                        cp_async16_or_zero(zd + ((size_t)(jj * 2 + layer) * SW + i) * kPL,
+                        cp_async16_or_zero(zd + ((size_t)(jj * 2 + 1 - layer) * SW + i) * kPL,
                                            zs + jj * zstride + (size_t)(i * 2 + layer) * NL, zr[i * RF + layer] != 0.f);
                 }
             }
@@ -437,9 +439,9 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                             float* d = pb + ((((size_t)warp * MR2 + jj) * 2) * SW + i) * kPL + 2 * lane;
                             const float xs = x1of(cs + i);
                             const float* rc = rbuf_rec(0, jj, i);
-                            *reinterpret_cast<float2*>(d) = rc[12] != 0.f ? PS::ld(zb, zo + (row * 2 + 0) * NL + lv, xs) : make_float2(0.f, 0.f);
                             *reinterpret_cast<float2*>(d + (size_t)SW * kPL) =
-                                rc[13] != 0.f ? PS::ld(zb, zo + (row * 2 + 1) * NL + lv, xs) : make_float2(0.f, 0.f);
+                                rc[12] != 0.f ? PS::ld(zb, zo + (row * 2 + 0) * NL + lv, xs) : make_float2(0.f, 0.f);
+                            *reinterpret_cast<float2*>(d) = rc[13] != 0.f ? PS::ld(zb, zo + (row * 2 + 1) * NL + lv, xs) : make_float2(0.f, 0.f);
                         }
                 } else if (!(pre && u == 0)) {
                     __syncwarp();                            // the staging's last readers are done
@@ -484,6 +486,9 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                             }
                         }
                     }
+                    // plane staging of a row: [2][SW][64], plane kk - 1 in layer (kk + 1) & 1 and plane
+                    // kk - 2 in layer kk & 1, which plane kk's value then replaces
+                    const size_t zl1 = (size_t)(((kk + 1) & 1) * SW) * kPL, zl2 = (size_t)((kk & 1) * SW) * kPL;
                     // one point: Eq. 10 for the lane's velocity pair with the x1 upstream values (hp1,
                     // hp2) of its row, the x2 upstream values rb of its column and the x3 upstream
                     // values of its row's plane staging zr; returns the lane's moment sums of the
@@ -492,8 +497,8 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                                      float2& M23, float& m4) {
                         const float4* R = reinterpret_cast<const float4*>(rrow + i * RF);
                         const float4 A = R[0], B = R[1], C = R[2], D = R[3];
-                        const float2 z1 = *reinterpret_cast<const float2*>(zr + (size_t)i * kPL);
-                        const float2 z2 = *reinterpret_cast<const float2*>(zr + ((size_t)SW + i) * kPL);
+                        const float2 z1 = *reinterpret_cast<const float2*>(zr + zl1 + (size_t)i * kPL);
+                        const float2 z2 = *reinterpret_cast<const float2*>(zr + zl2 + (size_t)i * kPL);
                         const float2 Rk = *reinterpret_cast<const float2*>(my_rtab + __float_as_int(B.w));
                         float2 S = fma2(dup2(A.w), v3, fma2(dup2(A.z), v2, fma2(dup2(A.y), v1, dup2(A.x))));
                         if constexpr (TAU) S = fma2(dup2(D.z), vq, S);   // nu tau (|v|^2 - 3/2)
@@ -521,8 +526,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                         hp1 = h;
                         rb2[i] = rb1[i];
                         rb1[i] = h;
-                        *reinterpret_cast<float2*>(zr + ((size_t)SW + i) * kPL) = z1;
-                        *reinterpret_cast<float2*>(zr + (size_t)i * kPL) = h;
+                        *reinterpret_cast<float2*>(zr + zl2 + (size_t)i * kPL) = h;
                         M01 = fma2(Wb01, dup2(h.y), mul2(Wa01, dup2(h.x)));
                         M23 = fma2(Wb23, dup2(h.y), mul2(Wa23, dup2(h.x)));
                         if constexpr (TAU) {
@@ -686,6 +690,9 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                         eo = ((((size_t)(par ^ 1) * 8 + qz) * P->ns3 + pi3.w) * n2 * n1) * 2 * NL;
                     }
                     const size_t ebase = eo + ((size_t)(last ? j0 : 0) * n1 + cs) * 2 * NL + lv;
+                    // the top plane nr3 - 1 in staging layer (nr3 - 1) & 1, the plane below it (or,
+                    // in a one-plane pencil, the fetched upstream plane) in layer nr3 & 1
+                    const size_t zlt = (size_t)(((nr3 - 1) & 1) * SW) * kPL, zlb = (size_t)((nr3 & 1) * SW) * kPL;
                     for (int jj = 0; jj < nr2; ++jj) {
                         const unsigned f0 = fbits((nr3 - 1) * MR2 + jj);
                         const unsigned f1 = nr3 >= 2 ? fbits((nr3 - 2) * MR2 + jj) : 0xffffffffu;
@@ -695,9 +702,9 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                         for (int i = 0; i < SW; ++i) {
                             if (i < wsub) {
                                 const float xs = x1of(cs + i);
-                                if ((f0 >> i) & 1u) PS::st(et, eb0 + (size_t)(i * 2 + 0) * NL, *reinterpret_cast<const float2*>(s + (size_t)i * kPL), xs);
+                                if ((f0 >> i) & 1u) PS::st(et, eb0 + (size_t)(i * 2 + 0) * NL, *reinterpret_cast<const float2*>(s + zlt + (size_t)i * kPL), xs);
                                 if ((f1 >> i) & 1u)
-                                    PS::st(et, eb0 + (size_t)(i * 2 + 1) * NL, *reinterpret_cast<const float2*>(s + ((size_t)SW + i) * kPL), xs);
+                                    PS::st(et, eb0 + (size_t)(i * 2 + 1) * NL, *reinterpret_cast<const float2*>(s + zlb + (size_t)i * kPL), xs);
                             }
                         }
                     }
