@@ -95,7 +95,6 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
     __shared__ int s_abort;
-    __shared__ int s_pre;      // the next tile's first upstream copies are already in flight
     const int NW = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -119,7 +118,6 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
         if (threadIdx.x == 0) {
             s_item = ld_volatile(a.status) ? a.nitems : atomicAdd(a.ticket, 1);
             s_abort = 0;
-            s_pre = 0;
         }
         if (!bmask)
             for (int r = threadIdx.x; r < MROWS; r += blockDim.x) fmask[r] = 0u;    // masks of tile 0
@@ -358,17 +356,13 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
             for (int r = lane; r < MROWS; r += 32) any |= fm[r] & sel;
             return __any_sync(0xffffffffu, any != 0u);
         };
-        bool pre_next = false;
         for (int t = 0; t < ntiles; ++t) {
             const int4 ti = tile_info(t);
             const int c0 = ti.x;
             const int width = ti.y;
             RawPoint3 nxt[kRawRounds];
             if (t + 1 < ntiles) load_raw(t + 1, nxt);
-            // z and y(0) of this tile's first sub-tile were issued at the end of the previous tile
-            // (its neighbours had already published this tile then, and the sub-tile holds fluid)
-            const bool pre = pre_next;
-            if (threadIdx.x == 0 && !pre) {
+            if (threadIdx.x == 0) {
                 bool ok = true;
                 if (pi2.z < 0) ok = wait_geq(prog + p3 * np2 + p2 - 1, t + 1, a.status, a.timeout_ns);
                 if (ok && pi3.z < 0) ok = wait_geq(prog + (p3 - 1) * np2 + p2, t + 1, a.status, a.timeout_ns);
@@ -403,9 +397,8 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                         cp_async16(carry + ((size_t)(warp * MROWS + kk * MR2 + (jl >> 1)) * 2 + (jl & 1)) * kPL + 4 * hl,
                                    P->gx1 + gxo + (row * 2 + (jl & 1)) * NL + lw);
                     }
-                    // complete them here when the first group is already committed, or when no
-                    // sub-tile will commit them
-                    if (pre || !tfl) {
+                    // complete them here when no sub-tile will commit them
+                    if (!tfl) {
                         cp_async_commit();
                         cp_async_wait<0>();
                     }
@@ -443,7 +436,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                                 rc[12] != 0.f ? PS::ld(zb, zo + (row * 2 + 0) * NL + lv, xs) : make_float2(0.f, 0.f);
                             *reinterpret_cast<float2*>(d) = rc[13] != 0.f ? PS::ld(zb, zo + (row * 2 + 1) * NL + lv, xs) : make_float2(0.f, 0.f);
                         }
-                } else if (!(pre && u == 0)) {
+                } else {
                     __syncwarp();                            // the staging's last readers are done
                     issue_z(cs, wsub, recs);
                     issue_y(0, cs, wsub, recs);
@@ -590,7 +583,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                             *reinterpret_cast<float2*>(crB + kPL) = hB2;
                             const float2 r01 = reduce_scatter2<8>(M01, lane);
                             const float2 r23 = reduce_scatter2<8>(M23, lane);
-                            float r4 = 0.f;
+                            [[maybe_unused]] float r4 = 0.f;
                             if constexpr (TAU) r4 = reduce_scatter<float, 8>(m4, lane);
                             // value v of the eight ends in lanes 4 v .. 4 v + 3: row jj + v / 4, column v % 4
                             const int v = lane >> 2;
@@ -630,7 +623,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                             }
                             const float2 r01 = reduce_scatter2<4>(M01, lane);
                             const float2 r23 = reduce_scatter2<4>(M23, lane);
-                            float r4 = 0.f;
+                            [[maybe_unused]] float r4 = 0.f;
                             if constexpr (TAU) r4 = reduce_scatter<float, 4>(m4, lane);
                             const int p = lane >> 3;
                             if ((lane & 7) == 0 && p < wsub) {
@@ -721,29 +714,9 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                     }
             }
             if (t + 1 < ntiles) store_rec(t + 1, (t + 1) & 1, nxt);
-            if (threadIdx.x == 0) {   // have the neighbours published the next tile already? (one poll)
-                int ready = 0;
-                if (!BF && t + 1 < ntiles) {
-                    ready = 1;
-                    if (pi2.z < 0 && ld_acquire_gpu(prog + p3 * np2 + p2 - 1) < t + 2) ready = 0;
-                    if (ready && pi3.z < 0 && ld_acquire_gpu(prog + (p3 - 1) * np2 + p2) < t + 2) ready = 0;
-                }
-                s_pre = ready;
-            }
             __syncthreads();
             if (threadIdx.x == 0 && it != a.withhold_item) {
                 publish_gpu(prog + p3 * np2 + p2, t + 1);
-            }
-            pre_next = s_pre != 0 && has_fluid(fmask + ((t + 1) & 1) * MROWS, 0);
-            if constexpr (!BF) {
-                // the plane staging and y slot 0 are free (the x3 edges were stored from the staging
-                // before the barrier): start the next tile's first copies now
-                if (pre_next) {
-                    const int4 tn = tile_info(t + 1);
-                    const float* rbn = rec + (size_t)((t + 1) & 1) * MROWS * T1 * RF;
-                    issue_z(tn.x, min(SW, tn.y), rbn);
-                    issue_y(0, tn.x, min(SW, tn.y), rbn);
-                }
             }
             // moment partials of this octant and group: warp sums in warp order
             // (idx = (r T1 + i) NM + mm over the pencil's row slots; only fluid points have bits)
