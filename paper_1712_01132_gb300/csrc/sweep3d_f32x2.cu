@@ -309,6 +309,32 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
             ? ((((size_t)par * 8 + q) * P->ns2 + pi2.z) * n3 * n1) * 2 * NL
             : ((((size_t)q * np3 + p3) * 2 * P->ns2 + (-1 - pi2.z)) * P->R3 * n1) * 2 * NL;
         auto yrow = [&](int kk) -> size_t { return yg ? (size_t)(k0 + kk) * n1 : (size_t)kk * n1; };
+        // where the pencil's top layers go, computed once per pencil: the x2 edge of plane kk, column
+        // c, layer l at et2[eo2 + kk rowS + c colS + l NL] (the ring slot for the pencil above in x2,
+        // or ghost slot pi2.w of the next iteration: the halo of the next block, or at the domain
+        // face the x2 ghost layers, periodic: same octant, specular: s2 flipped); the x3 edge of row
+        // jj at et3[eo3 + jj rowS + c colS + l NL] (likewise with pi3.w and s3)
+        const size_t colS = 2 * NL, rowS = (size_t)n1 * colS;
+        float* et2;
+        size_t eo2;
+        if (pi2.w < 0) {
+            et2 = P->ey;
+            eo2 = ((((size_t)q * np3 + p3) * 2 * P->ns2 + (-1 - pi2.w)) * P->R3 * n1) * 2 * NL + lv;
+        } else {
+            const int qy = (pi2.w > 0 || P->lateral == 1) ? q : (q ^ 2);
+            et2 = P->gy;
+            eo2 = ((((size_t)(par ^ 1) * 8 + qy) * P->ns2 + pi2.w) * n3 * n1) * 2 * NL + (size_t)k0 * rowS + lv;
+        }
+        float* et3;
+        size_t eo3;
+        if (pi3.w < 0) {
+            et3 = P->ez;
+            eo3 = ((((size_t)q * np2 + p2) * 2 * P->ns3 + (-1 - pi3.w)) * P->R2 * n1) * 2 * NL + lv;
+        } else {
+            const int qz = (pi3.w > 0 || P->lateral == 1) ? q : (q ^ 4);
+            et3 = P->gz;
+            eo3 = ((((size_t)(par ^ 1) * 8 + qz) * P->ns3 + pi3.w) * n2 * n1) * 2 * NL + (size_t)j0 * rowS + lv;
+        }
         // FP32: the x2 rows of plane kk go to slot kk & 1, copied while plane kk - 1 is swept (the
         // sub-tile's columns cc0 .. cc0 + wd - 1, records rb: its first column in row 0).  Upstream
         // values are fetched only where the stencil of the point that reads them has a nonzero
@@ -638,68 +664,48 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                             *reinterpret_cast<float2*>(cr + kPL) = hp2;
                         }
                     }
-                    // x2 edge of this plane for the pencil above in x2 (ring slot), or ghost slot pi2.w
-                    // of the next iteration: the halo of the next block, or at the domain face the x2
-                    // ghost layers (periodic: same octant; specular: s2 flipped)
+                    // x2 edge of this plane: only values of fluid points are stored (layer 1 of a
+                    // one-row pencil passes the fetched upstream value through and is always stored)
                     {
-                        float* et;
-                        size_t eo, rowbase;
-                        if (pi2.w < 0) {
-                            et = P->ey;
-                            eo = ((((size_t)q * np3 + p3) * 2 * P->ns2 + (-1 - pi2.w)) * P->R3 * n1) * 2 * NL;
-                            rowbase = (size_t)kk * n1;
-                        } else {
-                            const int qy = (pi2.w > 0 || P->lateral == 1) ? q : (q ^ 2);
-                            et = P->gy;
-                            eo = ((((size_t)(par ^ 1) * 8 + qy) * P->ns2 + pi2.w) * n3 * n1) * 2 * NL;
-                            rowbase = (size_t)(k0 + kk) * n1;
-                        }
-                        // only values of fluid points are stored (layer 1 of a one-row pencil passes
-                        // the fetched upstream value through and is always stored)
                         const unsigned f0 = fbits(kk * MR2 + nr2 - 1);
                         const unsigned f1 = nr2 >= 2 ? fbits(kk * MR2 + nr2 - 2) : 0xffffffffu;
+                        size_t o = eo2 + (size_t)kk * rowS + (size_t)cs * colS;
 #pragma unroll
                         for (int i = 0; i < SW; ++i) {
                             if (i < wsub) {
                                 const float xs = x1of(cs + i);
-                                if ((f0 >> i) & 1u) PS::st(et, eo + ((rowbase + cs + i) * 2 + 0) * NL + lv, rb1[i], xs);
-                                if ((f1 >> i) & 1u) PS::st(et, eo + ((rowbase + cs + i) * 2 + 1) * NL + lv, rb2[i], xs);
+                                if ((f0 >> i) & 1u) PS::st(et2, o, rb1[i], xs);
+                                if ((f1 >> i) & 1u) PS::st(et2, o + NL, rb2[i], xs);
                             }
+                            o += colS;
                         }
                     }
                 }
-                // x3 edge for the pencil above in x3 (ring slot), or ghost slot pi3.w of the next
-                // iteration
+                // x3 edge: the top plane nr3 - 1 in staging layer (nr3 - 1) & 1, the plane below it
+                // (or, in a one-plane pencil, the fetched upstream plane) in layer nr3 & 1
                 {
-                    float* et;
-                    size_t eo;
-                    const bool last = pi3.w >= 0;
-                    if (!last) {
-                        et = P->ez;
-                        eo = ((((size_t)q * np2 + p2) * 2 * P->ns3 + (-1 - pi3.w)) * P->R2 * n1) * 2 * NL;
-                    } else {
-                        const int qz = (pi3.w > 0 || P->lateral == 1) ? q : (q ^ 4);
-                        et = P->gz;
-                        eo = ((((size_t)(par ^ 1) * 8 + qz) * P->ns3 + pi3.w) * n2 * n1) * 2 * NL;
-                    }
-                    const size_t ebase = eo + ((size_t)(last ? j0 : 0) * n1 + cs) * 2 * NL + lv;
-                    // the top plane nr3 - 1 in staging layer (nr3 - 1) & 1, the plane below it (or,
-                    // in a one-plane pencil, the fetched upstream plane) in layer nr3 & 1
-                    const size_t zlt = (size_t)(((nr3 - 1) & 1) * SW) * kPL, zlb = (size_t)((nr3 & 1) * SW) * kPL;
+                    const float* s = pb + ((size_t)warp * MR2 * 2 * SW) * kPL + 2 * lane;
+                    const float* st0 = s + (size_t)(((nr3 - 1) & 1) * SW) * kPL;
+                    const float* st1 = s + (size_t)((nr3 & 1) * SW) * kPL;
+                    const unsigned* ft0 = fm_cur + (nr3 - 1) * MR2;
+                    const unsigned* ft1 = fm_cur + (nr3 >= 2 ? (nr3 - 2) * MR2 : 0);
+                    size_t ob = eo3 + (size_t)cs * colS;
                     for (int jj = 0; jj < nr2; ++jj) {
-                        const unsigned f0 = fbits((nr3 - 1) * MR2 + jj);
-                        const unsigned f1 = nr3 >= 2 ? fbits((nr3 - 2) * MR2 + jj) : 0xffffffffu;
-                        const size_t eb0 = ebase + (size_t)jj * n1 * 2 * NL;
-                        const float* s = pb + ((((size_t)warp * MR2 + jj) * 2) * SW) * kPL + 2 * lane;
+                        const unsigned f0 = (ft0[jj] >> us) & ((1u << SW) - 1u);
+                        const unsigned f1 = nr3 >= 2 ? ((ft1[jj] >> us) & ((1u << SW) - 1u)) : 0xffffffffu;
+                        size_t o = ob;
 #pragma unroll
                         for (int i = 0; i < SW; ++i) {
                             if (i < wsub) {
                                 const float xs = x1of(cs + i);
-                                if ((f0 >> i) & 1u) PS::st(et, eb0 + (size_t)(i * 2 + 0) * NL, *reinterpret_cast<const float2*>(s + zlt + (size_t)i * kPL), xs);
-                                if ((f1 >> i) & 1u)
-                                    PS::st(et, eb0 + (size_t)(i * 2 + 1) * NL, *reinterpret_cast<const float2*>(s + zlb + (size_t)i * kPL), xs);
+                                if ((f0 >> i) & 1u) PS::st(et3, o, *reinterpret_cast<const float2*>(st0 + (size_t)i * kPL), xs);
+                                if ((f1 >> i) & 1u) PS::st(et3, o + NL, *reinterpret_cast<const float2*>(st1 + (size_t)i * kPL), xs);
                             }
+                            o += colS;
                         }
+                        ob += rowS;
+                        st0 += (size_t)2 * SW * kPL;
+                        st1 += (size_t)2 * SW * kPL;
                     }
                 }
             }   // sub-tiles
