@@ -211,6 +211,11 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
         // points are loaded for tile t + 1 while tile t is swept (all loads issued together, with
         // no branch on the code) and written to that tile's record buffer at the end of tile t.
         const int npts = nr3 * MR2 * T1;
+        // the problem's per-point arrays and this octant's and group's moment partials
+        const uint16_t* __restrict__ pcode = P->code;
+        const float4* __restrict__ psrc = reinterpret_cast<const float4*>(P->src);
+        const float4* __restrict__ pE = reinterpret_cast<const float4*>(P->E);
+        float* __restrict__ Pq = P->P + ((size_t)q * G + g) * 4 * (size_t)N;
         // point (row first index off, column i) of a tile (first column, width: tj.x, tj.y)
         auto load_point = [&](const int4& tj, int off, int i, RawPoint3& r) {
             r.code = kSolidBit;
@@ -218,10 +223,10 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                 const int ic = tj.x + i;
                 const int x = s1n ? n1 - 1 - ic : ic;
                 const int id = off + x;
-                r.code = P->code[id];
-                r.s = reinterpret_cast<const float4*>(P->src)[id];
-                r.e0 = reinterpret_cast<const float4*>(P->E)[2 * (size_t)id];
-                r.e1 = reinterpret_cast<const float4*>(P->E)[2 * (size_t)id + 1];
+                r.code = pcode[id];
+                r.s = psrc[id];
+                r.e0 = pE[2 * (size_t)id];
+                r.e1 = pE[2 * (size_t)id + 1];
                 if constexpr (TAU) r.st = P->srct[id];
                 if constexpr (SPEC) {   // faces: upstream (read) x1 x2 x3, downstream (written)
                     const int* fi = P->face_id;
@@ -315,6 +320,10 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
         // face the x2 ghost layers, periodic: same octant, specular: s2 flipped); the x3 edge of row
         // jj at et3[eo3 + jj rowS + c colS + l NL] (likewise with pi3.w and s3)
         const size_t colS = 2 * NL, rowS = (size_t)n1 * colS;
+        // the copies' sources (lane offset lw included): x2 rows of plane kk at yb[yo2 + kk rowS + ...],
+        // x3 planes of row jj at zb[zo2 + jj rowS + ...]
+        const size_t yo2 = yo + (yg ? (size_t)k0 * rowS : 0) + lw;
+        const size_t zo2 = zo + (zg ? (size_t)j0 * rowS : 0) + lw;
         float* et2;
         size_t eo2;
         if (pi2.w < 0) {
@@ -343,7 +352,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
         // (copy m = layer SW + i of a row's 2 SW goes to lane half m & 1; columns i >= wd are not
         // copied)
         auto issue_y = [&](int kk, int cc0, int wd, const float* rb) {
-            const float* ys = yb + yo + (yrow(kk) + cc0) * 2 * NL + lw;
+            const float* ys = yb + yo2 + (size_t)kk * rowS + (size_t)cc0 * colS;
             float* yd = eb + (((size_t)warp * 2 + (kk & 1)) * 2 * SW) * kPL + 4 * hl;
             const float* yr = rb + (size_t)kk * MR2 * T1 * RF + 10;
 #pragma unroll
@@ -359,9 +368,9 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
         // the plane just below (edge layer 0) into staging layer 1 and the one below it into layer
         // 0, where plane 0 reads them (the staging layer of plane kk - 1 is (kk + 1) & 1)
         auto issue_z = [&](int cc0, int wd, const float* rb) {
-            const float* zs = zb + zo + ((size_t)(zg ? j0 : 0) * n1 + cc0) * 2 * NL + lw;
+            const float* zs = zb + zo2 + (size_t)cc0 * colS;
             float* zd = pb + ((size_t)warp * MR2 * 2 * SW) * kPL + 4 * hl;
-            const size_t zstride = (size_t)n1 * 2 * NL;
+            const size_t zstride = rowS;
             for (int jj = 0; jj < nr2; ++jj) {
                 const float* zr = rb + (size_t)jj * T1 * RF + 12;
 #pragma unroll
@@ -739,7 +748,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                 for (int w = 0; w < NW; ++w) s += part[(size_t)w * wstride + idx];
                 const int ic = c0 + i;
                 const size_t pid = (size_t)rowoff[r] + (s1n ? n1 - 1 - ic : ic);
-                if (!TAU || mm < 4) P->P[(((size_t)q * G + g) * 4 + mm) * N + pid] = s;
+                if (!TAU || mm < 4) Pq[(size_t)mm * N + pid] = s;
                 else P->Pt[((size_t)q * G + g) * N + pid] = s;
             }
             // (with masks by vote the next writers of part and of these masks are behind the next
