@@ -349,18 +349,19 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
         // values are fetched only where the stencil of the point that reads them has a nonzero
         // coefficient for them (record K1 / K2 of the first row or plane): values of solid points
         // are never used, so they are neither stored nor fetched, and the staging holds zeros there.
-        // (copy m = layer SW + i of a row's 2 SW goes to lane half m & 1; columns i >= wd are not
-        // copied)
+        // (lane half h copies both layers of columns h, h + 2, ...; columns i >= wd are not copied)
         auto issue_y = [&](int kk, int cc0, int wd, const float* rb) {
             const float* ys = yb + yo2 + (size_t)kk * rowS + (size_t)cc0 * colS;
             float* yd = eb + (((size_t)warp * 2 + (kk & 1)) * 2 * SW) * kPL + 4 * hl;
             const float* yr = rb + (size_t)kk * MR2 * T1 * RF + 10;
 #pragma unroll
-            for (int u = 0; u < SW; ++u) {
-                const int m = half + 2 * u;
-                const int layer = m / SW, i = m % SW;
-                if (i < wd)
-                    cp_async16_or_zero(yd + (size_t)m * kPL, ys + (size_t)(i * 2 + layer) * NL, yr[i * RF + layer] != 0.f);
+            for (int u = 0; u < SW / 2; ++u) {
+                const int i = half + 2 * u;
+                if (i < wd) {
+                    const float2 K = *reinterpret_cast<const float2*>(yr + i * RF);   // K1y, K2y
+                    cp_async16_or_zero(yd + (size_t)i * kPL, ys + (size_t)(i * 2) * NL, K.x != 0.f);
+                    cp_async16_or_zero(yd + (size_t)(SW + i) * kPL, ys + (size_t)(i * 2 + 1) * NL, K.y != 0.f);
+                }
             }
             cp_async_commit();
         };
@@ -374,12 +375,15 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
             for (int jj = 0; jj < nr2; ++jj) {
                 const float* zr = rb + (size_t)jj * T1 * RF + 12;
 #pragma unroll
-                for (int u = 0; u < SW; ++u) {
-                    const int m = half + 2 * u;
-                    const int layer = m / SW, i = m % SW;
-                    if (i < wd)
-                        cp_async16_or_zero(zd + ((size_t)(jj * 2 + 1 - layer) * SW + i) * kPL,
-                                           zs + jj * zstride + (size_t)(i * 2 + layer) * NL, zr[i * RF + layer] != 0.f);
+                for (int u = 0; u < SW / 2; ++u) {
+                    const int i = half + 2 * u;
+                    if (i < wd) {
+                        const float2 K = *reinterpret_cast<const float2*>(zr + i * RF);   // K1z, K2z
+                        cp_async16_or_zero(zd + ((size_t)(jj * 2 + 1) * SW + i) * kPL, zs + jj * zstride + (size_t)(i * 2) * NL,
+                                           K.x != 0.f);
+                        cp_async16_or_zero(zd + ((size_t)(jj * 2) * SW + i) * kPL, zs + jj * zstride + (size_t)(i * 2 + 1) * NL,
+                                           K.y != 0.f);
+                    }
                 }
             }
         };
@@ -735,8 +739,28 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
             }
             // moment partials of this octant and group: warp sums in warp order
             // (idx = (r T1 + i) NM + mm over the pencil's row slots; only fluid points have bits)
-            const int tot = tfl ? MROWS * T1 * NM : 0;
             const int wstride = MROWS * T1 * NM;
+            if constexpr (!TAU) {   // a thread per point, its four moments as one vector
+                for (int pt = threadIdx.x; tfl && pt < MROWS * T1; pt += blockDim.x) {
+                    const int i = pt % T1, r = pt / T1;
+                    if (!((fm_cur[r] >> i) & 1u)) continue;   // solid: the start state's zeros stay
+                    float4 sv = *reinterpret_cast<const float4*>(part + (size_t)pt * 4);
+                    for (int w = 1; w < NW; ++w) {
+                        const float4 o = *reinterpret_cast<const float4*>(part + (size_t)w * wstride + (size_t)pt * 4);
+                        sv.x += o.x;
+                        sv.y += o.y;
+                        sv.z += o.z;
+                        sv.w += o.w;
+                    }
+                    const int ic = c0 + i;
+                    float* d = Pq + (size_t)rowoff[r] + (s1n ? n1 - 1 - ic : ic);
+                    d[0] = sv.x;
+                    d[N] = sv.y;
+                    d[2 * (size_t)N] = sv.z;
+                    d[3 * (size_t)N] = sv.w;
+                }
+            }
+            const int tot = (tfl && TAU) ? MROWS * T1 * NM : 0;
             for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
                 const int mm = idx % NM;
                 const int pt = idx / NM;
