@@ -568,11 +568,16 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                             m4 = 0.f;
                         }
                     };
+                    // the plane's row 0: x1 carries, plane staging [2][SW][64], records, partials
+                    float* const cr0 = carry + ((size_t)(warp * MROWS + kk * MR2) * 2) * kPL + 2 * lane;
+                    float* const zr0 = pb + ((size_t)warp * MR2 * 2 * SW) * kPL + 2 * lane;
+                    const float* const rr0 = recs + (size_t)(kk * MR2 * T1) * RF;
+                    float* const pr0 = part + ((size_t)(warp * MROWS + kk * MR2) * T1 + us) * NM;
                     auto row_ptrs = [&](int jj, float*& cr, float*& zr, const float*& rrow, float*& prow) {
-                        cr = carry + ((size_t)(warp * MROWS + kk * MR2 + jj) * 2) * kPL + 2 * lane;
-                        zr = pb + ((((size_t)warp * MR2 + jj) * 2) * SW) * kPL + 2 * lane;   // [2][SW][64]
-                        rrow = recs + (size_t)((kk * MR2 + jj) * T1) * RF;
-                        prow = part + ((size_t)(warp * MROWS + kk * MR2 + jj) * T1 + us) * NM;
+                        cr = cr0 + jj * (2 * kPL);
+                        zr = zr0 + jj * (2 * SW * kPL);
+                        rrow = rr0 + jj * (T1 * RF);
+                        prow = pr0 + jj * (T1 * NM);
                     };
                     // solid points are not swept: every fluid point downstream of one gives it a zero
                     // stencil coefficient (its code marks that upstream point solid), so the values
