@@ -67,8 +67,8 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
     const int lane = threadIdx.x & 31;
     const int RB = a.max_rows;
     float* rec = reinterpret_cast<float*>(smem_raw);                    // [2][RB][T1][RF]
-    float* part = rec + (size_t)2 * RB * T1 * RF;                        // [NW][RB][T1][3]
-    float* carry = part + (size_t)NW * RB * T1 * 3;                      // [NW][RB][2][128]
+    float* part = rec + (size_t)2 * RB * T1 * RF;                        // [NW][RB][T1][4]: rho u1 u2 -
+    float* carry = part + (size_t)NW * RB * T1 * 4;                      // [NW][RB][2][128]
     float* rtab = carry + (size_t)NW * RB * 2 * 128;                     // [NW][4][128]
     unsigned* rmask = reinterpret_cast<unsigned*>(rtab + (size_t)NW * 4 * 128);  // [2][RB]
     const int wl = warp * 32 + lane;            // lane index; velocities 4 wl .. 4 wl + 3
@@ -418,10 +418,8 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
                     // value v of the 2 SW ends in the lanes v * 32 / (2 SW) onward: row r + v / SW
                     if ((lane & (kLPP / 2 - 1)) == 0) {
                         const int v = lane / (kLPP / 2);
-                        float* d = part + ((size_t)(warp * RB + r + v / SW) * T1 + us + (v % SW)) * 3;
-                        d[0] = s01.x;
-                        d[1] = s01.y;
-                        d[2] = s2;
+                        float* d = part + ((size_t)(warp * RB + r + v / SW) * T1 + us + (v % SW)) * 4;
+                        *reinterpret_cast<float4*>(d) = make_float4(s01.x, s01.y, s2, 0.f);
                     }
                 }
                 if (r < nrows && fbits(r) != 0u) {   // the last row of an odd band
@@ -442,10 +440,8 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
                     const float2 s01 = reduce_scatter2<SW>(M01, lane);
                     const float s2 = reduce_scatter<float, SW>(m2, lane);
                     if ((lane & (kLPP - 1)) == 0) {
-                        float* d = part + ((size_t)(warp * RB + r) * T1 + us + lane / kLPP) * 3;
-                        d[0] = s01.x;
-                        d[1] = s01.y;
-                        d[2] = s2;
+                        float* d = part + ((size_t)(warp * RB + r) * T1 + us + lane / kLPP) * 4;
+                        *reinterpret_cast<float4*>(d) = make_float4(s01.x, s01.y, s2, 0.f);
                     }
                 }
             };
@@ -477,23 +473,29 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
             if (t + 1 < ntiles) store_rec(buf ^ 1, nxt);
             __syncthreads();
             if (threadIdx.x == 0 && it != a.withhold_item) publish_gpu(P->prog + q * nb + band, t + 1);
-            // moment partials of this quadrant: sum of the warps' lane sums, in warp order (idx =
-            // (rr T1 + i) 3 + m; only fluid points have bits, and only their partials are read)
+            // moment partials of this quadrant: sum of the warps' lane sums, in warp order, a thread
+            // per point (pt = rr T1 + i; only fluid points have bits, and only their partials are read)
             {
                 const unsigned* mk = rmask + buf * RB;
-                for (int idx = threadIdx.x; idx < nrows * T1 * 3; idx += blockDim.x) {
-                    const int m = idx % 3;
-                    const int pi = idx / 3;
-                    const int rr = pi / T1;
-                    const int i = pi % T1;
+                for (int pt = threadIdx.x; pt < nrows * T1; pt += blockDim.x) {
+                    const int rr = pt / T1;
+                    const int i = pt % T1;
                     if (!((mk[rr] >> i) & 1u)) continue;
-                    float s = 0.f;
-                    for (int w = 0; w < NW; ++w) s += part[((size_t)(w * RB) * T1) * 3 + idx];
+                    float4 sv = *reinterpret_cast<const float4*>(part + (size_t)pt * 4);
+                    for (int w = 1; w < NW; ++w) {
+                        const float4 o = *reinterpret_cast<const float4*>(part + ((size_t)w * RB * T1 + pt) * 4);
+                        sv.x += o.x;
+                        sv.y += o.y;
+                        sv.z += o.z;
+                    }
                     const int ic = c0 + i;
                     const int x = s1neg ? n1 - 1 - ic : ic;
                     const int yo = row0 + rr;
                     const int y = s2neg ? n2 - 1 - yo : yo;
-                    P->P[((size_t)q * 3 + m) * N + (size_t)y * n1 + x] = s;
+                    float* d = P->P + (size_t)q * 3 * N + (size_t)y * n1 + x;
+                    d[0] = sv.x;
+                    d[N] = sv.y;
+                    d[2 * (size_t)N] = sv.z;
                 }
             }
         }
@@ -502,7 +504,7 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
 }
 
 size_t sweep2d_f32x2_smem(int T1, int NW, int max_rows, int spec) {
-    return sizeof(float) * ((size_t)2 * max_rows * T1 * (spec ? 16 : kRecF) + (size_t)NW * max_rows * T1 * 3 +
+    return sizeof(float) * ((size_t)2 * max_rows * T1 * (spec ? 16 : kRecF) + (size_t)NW * max_rows * T1 * 4 +
                             (size_t)NW * max_rows * 2 * 128 + (size_t)NW * 4 * 128) +
            sizeof(unsigned) * (size_t)2 * max_rows;
 }
