@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(256) finalize2d_kernel(const FinArgs2D<T> a) {
         for (int q = 0; q < 4; ++q)
 #pragma unroll
             for (int m = 0; m < 3; ++m)
-                pu[k][q][m] = (code[k] & kSolidBit) ? T(0) : P->P[((size_t)q * 3 + m) * N + idk[k]];
+                pu[k][q][m] = idk[k] < P->N ? P->P[((size_t)q * 3 + m) * N + idk[k]] : T(0);   // zero at solid points
 #pragma unroll
     for (int k = 0; k < kFinPPT; ++k) {
         const int id = idk[k];

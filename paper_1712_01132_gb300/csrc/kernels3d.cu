@@ -490,15 +490,19 @@ __global__ void __launch_bounds__(256) finalize3d_kernel(const FinArgs3D<T> a) {
     double u1d = 0.0;
     if (id < P->N) {
         const uint16_t code = P->code[id];
+        // the moment partials are loaded before the code is known (a solid point's partials are
+        // the start state's zeros), so both loads overlap
+        const size_t N = P->N;
+        const int G = P->ngroups;
+        T mo[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+#pragma unroll 2
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int mm = 0; mm < 4; ++mm) mo[mm] += P->P[(((size_t)q * G + g) * 4 + mm) * N + id];
         V s = V4t<T>::make(0, 0, 0, 0), e0 = s, e1 = s;
         if (!(code & kSolidBit)) {
-            const size_t N = P->N;
-            const int G = P->ngroups;
-            T mo[4] = {T(0), T(0), T(0), T(0)};
-            for (int q = 0; q < 8; ++q)
-                for (int g = 0; g < G; ++g)
-#pragma unroll
-                    for (int mm = 0; mm < 4; ++mm) mo[mm] += P->P[(((size_t)q * G + g) * 4 + mm) * N + id];
             const T nu = (T)P->nu;
             s = V4t<T>::make(nu * mo[0], T(2) * nu * mo[1] + T(1), T(2) * nu * mo[2], T(2) * nu * mo[3]);
             u1d = (double)mo[1];
