@@ -53,6 +53,16 @@ static __device__ bool wait_geq(const int* flag, int target, int* status, long l
     }
 }
 
+// The same wait, returning the flag value it observed (>= target), or -1 when it gave up.  A caller
+// that keeps the value can skip the next waits for targets up to it: the acquire that read it
+// already ordered everything the writer published before.
+static __device__ int wait_geq_value(const int* flag, int target, int* status, long long timeout_ns) {
+    int v = ld_acquire_gpu(flag);
+    if (v >= target) return v;
+    if (!wait_geq(flag, target, status, timeout_ns)) return -1;
+    return target;
+}
+
 // Sign bits of the two axes other than j of octant q, packed (lower axis first): the slot of a wall
 // face store that the octant moving into a face and its mirror image in axis j share.
 __device__ __forceinline__ int other_bits3(int q, int j) {

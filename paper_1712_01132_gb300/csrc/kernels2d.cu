@@ -205,6 +205,9 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs2D<T> a) {
         };
         if constexpr (!XS) carry_in(0);
         const int ntiles = XS ? P->ntq[q] : (n1 + T1 - 1) / T1;
+        // progress of the band below that thread 0 has already observed with an acquire (tiles up
+        // to it need no new wait)
+        int seenb = -1;
         for (int t = 0; t < ntiles; ++t) {
             int4 tcur;
             if constexpr (XS) {
@@ -215,8 +218,9 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs2D<T> a) {
             }
             const int c0 = tcur.x;
             const int width = tcur.y;
-            if (threadIdx.x == 0 && below < 0) {
-                if (!wait_geq(P->prog + q * nb + band - 1, t + 1, a.status, a.timeout_ns)) s_abort = 1;
+            if (threadIdx.x == 0 && below < 0 && seenb < t + 1) {
+                seenb = wait_geq_value(P->prog + q * nb + band - 1, t + 1, a.status, a.timeout_ns);
+                if (seenb < 0) s_abort = 1;
             }
             // per-point records of this quadrant: source, stencil coefficients, wall terms
             for (int idx = threadIdx.x; idx < nrows * T1; idx += blockDim.x) {

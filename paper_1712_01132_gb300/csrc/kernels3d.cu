@@ -153,6 +153,9 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
         auto x1of = [&](int ic) -> T { return (T)(s1n ? n1 - 1 - ic : ic) * dxT; };
         const T x1g0 = x1of(n1 - 1), x1g1 = x1of(n1 - 2);   // columns of the x1 ghost layers
         const int ntiles = SUB ? P->nt1 : (n1 + T1 - 1) / T1;
+        // neighbour progress thread 0 has already observed with an acquire (tiles up to it need no
+        // new wait)
+        int seen2 = pi2.z < 0 ? -1 : ntiles, seen3 = pi3.z < 0 ? -1 : ntiles;
         for (int t = 0; t < ntiles; ++t) {
             // tile: first oriented column, width, x1 carry-in and carry-out ghost slots (or -1)
             int4 ti;
@@ -161,10 +164,9 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const SweepArgs3D<T> a) {
             const int c0 = ti.x;
             const int width = ti.y;
             if (threadIdx.x == 0) {
-                bool ok = true;
-                if (pi2.z < 0) ok = wait_geq(prog + p3 * np2 + p2 - 1, t + 1, a.status, a.timeout_ns);
-                if (ok && pi3.z < 0) ok = wait_geq(prog + (p3 - 1) * np2 + p2, t + 1, a.status, a.timeout_ns);
-                if (!ok) s_abort = 1;
+                if (seen2 < t + 1) seen2 = wait_geq_value(prog + p3 * np2 + p2 - 1, t + 1, a.status, a.timeout_ns);
+                if (seen2 >= 0 && seen3 < t + 1) seen3 = wait_geq_value(prog + (p3 - 1) * np2 + p2, t + 1, a.status, a.timeout_ns);
+                if (seen2 < 0 || seen3 < 0) s_abort = 1;
             }
             // records of the tile's points for this octant
             const int npts = nr3 * MR2 * T1;

@@ -255,6 +255,9 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
             load_raw(0, raw);
             store_rec(0, raw);
         }
+        // progress of the band below that thread 0 has already observed with an acquire (tiles up
+        // to it need no new wait)
+        int seenb = -1;
         for (int t = 0; t < ntiles; ++t) {
             int c0, width, cout_slot;
             if constexpr (XS) {
@@ -271,8 +274,9 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
             const int buf = t & 1;
             RawPoint nxt[kMaxRounds];
             if (t + 1 < ntiles) load_raw(t + 1, nxt);
-            if (threadIdx.x == 0 && s_binfo[2] < 0) {
-                if (!wait_geq(P->prog + q * nb + band - 1, t + 1, a.status, a.timeout_ns)) s_abort = 1;
+            if (threadIdx.x == 0 && s_binfo[2] < 0 && seenb < t + 1) {
+                seenb = wait_geq_value(P->prog + q * nb + band - 1, t + 1, a.status, a.timeout_ns);
+                if (seenb < 0) s_abort = 1;
             }
             __syncthreads();
             if (s_abort) return;

@@ -395,6 +395,9 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
             for (int r = lane; r < MROWS; r += 32) any |= fm[r] & sel;
             return __any_sync(0xffffffffu, any != 0u);
         };
+        // neighbour progress thread 0 has already observed with an acquire (tiles up to it need no
+        // new wait: the release that published it covered every earlier tile's edges)
+        int seen2 = pi2.z < 0 ? -1 : ntiles, seen3 = pi3.z < 0 ? -1 : ntiles;
         for (int t = 0; t < ntiles; ++t) {
             const int4 ti = tile_info(t);
             const int c0 = ti.x;
@@ -402,10 +405,9 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
             RawPoint3 nxt[kRawRounds];
             if (t + 1 < ntiles) load_raw(t + 1, nxt);
             if (threadIdx.x == 0) {
-                bool ok = true;
-                if (pi2.z < 0) ok = wait_geq(prog + p3 * np2 + p2 - 1, t + 1, a.status, a.timeout_ns);
-                if (ok && pi3.z < 0) ok = wait_geq(prog + (p3 - 1) * np2 + p2, t + 1, a.status, a.timeout_ns);
-                if (!ok) s_abort = 1;
+                if (seen2 < t + 1) seen2 = wait_geq_value(prog + p3 * np2 + p2 - 1, t + 1, a.status, a.timeout_ns);
+                if (seen2 >= 0 && seen3 < t + 1) seen3 = wait_geq_value(prog + (p3 - 1) * np2 + p2, t + 1, a.status, a.timeout_ns);
+                if (seen2 < 0 || seen3 < 0) s_abort = 1;
             }
             // the masks of the next tile are cleared here (their last reader, the moment loop of
             // the previous tile, is behind the barrier that ended it; they are set at the end of
