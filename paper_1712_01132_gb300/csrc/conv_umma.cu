@@ -273,6 +273,139 @@ __global__ void __launch_bounds__(kThreads) conv3d_umma_kernel(const __grid_cons
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_d), "r"(kTmemCols) : "memory");
 }
 
+// The same convolution with the A operand shared by the three y taps: when a tile is whole x rows
+// (W a multiple of 8 dividing 128, by = 128 / W rows) and a CTA's MT tiles are consecutive rows of
+// one z plane, one box of MT by + 2 rows (the tiles' rows and a halo row on each side) per (dz, dx,
+// channel chunk) holds the A rows of all three dy taps: tap dy of tile t starts (t by + dy + 1) W
+// rows into the box, a multiple of eight 64-byte rows, so it is a plain shift of the swizzled
+// operand's start address.  A stage is that box and the three dy taps' B boxes: 9 stages per chunk
+// instead of 27, and a third of the A bytes per tap.
+template <int BN, int MT, int NST>
+__global__ void __launch_bounds__(kThreads) conv3d_umma_dy_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                  const __grid_constant__ CUtensorMap tmB,
+                                                                  const float* __restrict__ bias, float* __restrict__ y,
+                                                                  const ConvGeom g, int abox_bytes, int stage_bytes) {
+    constexpr int kBBytes = BN * kBK * 2;
+    constexpr unsigned kTmemCols = MT * BN <= 32 ? 32u : (MT * BN <= 64 ? 64u : (MT * BN <= 128 ? 128u : 256u));
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* sbase = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t full[NST], empty[NST], done;
+    __shared__ unsigned s_tmem;
+    __shared__ int s_fail;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n0 = blockIdx.y * BN;
+    const int tile0 = blockIdx.x * MT;                // first tile: z plane, first y row
+    const int z = tile0 / g.ytiles;
+    const int yb = (tile0 - z * g.ytiles) * g.by;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(kTmemCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem_d = s_tmem;
+    const int niter = 9 * g.nk;                       // (dz, dx) x channel chunks
+    const unsigned box_bytes = (unsigned)(abox_bytes + 3 * kBBytes);
+
+    if (warp == 0 && lane == 0) {
+        // producer: the A box of (dz, dx, chunk) and the B boxes of its three dy taps per stage
+        for (int i = 0; i < niter; ++i) {
+            const int s = i % NST;
+            if (i >= NST && !mbar_wait(&empty[s], ((i / NST) - 1) & 1)) {
+                s_fail = 1;
+                break;
+            }
+            const int zx = i / g.nk, kc = i - zx * g.nk;
+            const int dz = zx / 3 - 1, dx = zx % 3 - 1;
+            unsigned char* st = sbase + (size_t)s * stage_bytes;
+            mbar_expect_tx(&full[s], box_bytes);
+            tma_load_4d(st, &tmA, kc * kBK, 1 + dx, yb, z + 1 + dz, &full[s]);   // padded rows yb .. yb + MT by + 1
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                tma_load_3d(st + abox_bytes + j * kBBytes, &tmB, kc * kBK, n0, (dz + 1) * 9 + j * 3 + (dx + 1), &full[s]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: per stage, for each dy tap and row tile two K = 16 steps
+        const unsigned idesc = idesc_bf16<BN>();
+        for (int i = 0; i < niter; ++i) {
+            const int s = i % NST;
+            if (!mbar_wait(&full[s], (i / NST) & 1)) {
+                s_fail = 1;
+                break;
+            }
+            tc_fence_after();
+            const unsigned char* st = sbase + (size_t)s * stage_bytes;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const uint64_t bd = smem_desc_sw64(st + abox_bytes + j * kBBytes);
+#pragma unroll
+                for (int t = 0; t < MT; ++t) {
+                    const uint64_t ad = smem_desc_sw64(st + (size_t)((t * g.by + j) * g.W) * (kBK * 2));
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 16; ++kk)
+                        umma_bf16(tmem_d + t * BN, ad + 2 * kk, bd + 2 * kk, idesc, (i > 0 || j > 0 || kk > 0) ? 1 : 0);
+                }
+            }
+            umma_commit(&empty[s]);
+        }
+        umma_commit(&done);
+    }
+    __syncwarp();
+    const bool ok = mbar_wait(&done, 0);
+    tc_fence_after();
+    if (!ok || s_fail) {
+        if (threadIdx.x == 0) atomicCAS(&g_conv_status, 0, -4);
+    } else {
+        // accumulator row r of tile t = voxel r of the tile (TMEM lane r), column t BN + j = output
+        // channel n0 + j; every row of every tile is a voxel (by W = 128, whole tiles)
+        const int r = warp * 32 + lane;
+        const long long V = (long long)g.D * g.H * g.W;
+#pragma unroll
+        for (int t = 0; t < MT; ++t) {
+            const int yy = yb + t * g.by + r / g.W, xx = r % g.W;
+            const long long v = ((long long)z * g.H + yy) * g.W + xx;
+#pragma unroll
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                unsigned a[16];
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                             "%13, %14, %15}, [%16];"
+                             : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]),
+                               "=r"(a[7]), "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]),
+                               "=r"(a[14]), "=r"(a[15])
+                             : "r"(tmem_d + ((unsigned)(32 * warp) << 16) + (unsigned)(t * BN + c0))
+                             : "memory");
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (yy < g.H) {
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) {
+                        const int co = n0 + c0 + jj;
+                        if (co < g.cout) {
+                            const float val = __uint_as_float(a[jj]) + (bias ? bias[co] : 0.f);
+                            float* d = y + (long long)co * V + v;
+                            *d = g.accumulate ? *d + val : val;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_d), "r"(kTmemCols) : "memory");
+}
+
 // xp[pz][py][px][c] = bf16(x[c][pz - 1][py - 1][px - 1]) with periodic wrap, zero for c >= cin.  A
 // block transposes 32 padded voxels of one x row by 32 channels through shared memory, so that both
 // the channel-major reads and the channels-last writes are coalesced.
@@ -349,6 +482,20 @@ cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const float*
     return cudaGetLastError();
 }
 
+template <int BN, int MT, int NST>
+cudaError_t launch_dy(const CUtensorMap& ta, const CUtensorMap& tb, const float* bias, float* y, const ConvGeom& g,
+                      cudaStream_t st) {
+    const int abox = (MT * g.by + 2) * g.W * kBK * 2;
+    const int stage = (abox + 3 * BN * kBK * 2 + 1023) / 1024 * 1024;
+    const int smem = NST * stage + 1024;
+    auto kern = conv3d_umma_dy_kernel<BN, MT, NST>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)(g.D * g.ytiles / MT), (unsigned)(g.coutp / BN));
+    kern<<<grid, kThreads, smem, st>>>(ta, tb, bias, y, g, abox, stage);
+    return cudaGetLastError();
+}
+
 }  // namespace dvm_nn
 
 // Scratch bytes of one convolution with nin input and nout output channels on a d x h x w grid: the
@@ -415,6 +562,23 @@ cudaError_t conv_umma(const float* x, const float* w, const float* bias, float* 
                 CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
             CUDA_SUCCESS)
             return cudaErrorInvalidValue;
+    }
+    // whole-row tiles of 128 voxels, two per CTA in one z plane: the A box shared by the dy taps
+    const int mt = bn == 128 ? 1 : 2;
+    if (w_ % 8 == 0 && kBM % w_ == 0 && g.by * w_ == kBM && h % g.by == 0 && g.ytiles % mt == 0) {
+        CUtensorMap td;
+        const cuuint64_t dims[4] = {(cuuint64_t)g.cinp, (cuuint64_t)(w_ + 2), (cuuint64_t)(h + 2), (cuuint64_t)(d + 2)};
+        const cuuint64_t strides[3] = {(cuuint64_t)g.cinp * 2, (cuuint64_t)g.cinp * 2 * (w_ + 2),
+                                       (cuuint64_t)g.cinp * 2 * (w_ + 2) * (h + 2)};
+        const cuuint32_t box[4] = {(cuuint32_t)kBK, (cuuint32_t)w_, (cuuint32_t)(mt * g.by + 2), 1u};
+        const cuuint32_t es[4] = {1u, 1u, 1u, 1u};
+        if (enc(&td, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, xp, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+            CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+        if (bn == 32) return launch_dy<32, 2, 3>(td, tb, bias, y, g, st);
+        if (bn == 64) return launch_dy<64, 2, 3>(td, tb, bias, y, g, st);
+        return launch_dy<128, 1, 3>(td, tb, bias, y, g, st);
     }
     if (bn == 32) return launch_bn<32, 2>(ta, tb, bias, y, g, st);
     if (bn == 64) return launch_bn<64, 2>(ta, tb, bias, y, g, st);
