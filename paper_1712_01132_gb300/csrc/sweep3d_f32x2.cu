@@ -523,12 +523,16 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                     // plane staging of a row: [2][SW][64], plane kk - 1 in layer (kk + 1) & 1 and plane
                     // kk - 2 in layer kk & 1, which plane kk's value then replaces
                     const size_t zl1 = (size_t)(((kk + 1) & 1) * SW) * kPL, zl2 = (size_t)((kk & 1) * SW) * kPL;
+                    // FP32 pencils of two or more planes store their x3 edge as the last two planes
+                    // are swept (layer 0: plane nr3 - 1, layer 1: plane nr3 - 2; fluid points only)
+                    const bool e3 = !BF && nr3 >= 2 && kk >= nr3 - 2;
+                    const size_t e3o = eo3 + (size_t)cs * colS + (size_t)(nr3 - 1 - kk) * NL;
                     // one point: Eq. 10 for the lane's velocity pair with the x1 upstream values (hp1,
                     // hp2) of its row, the x2 upstream values rb of its column and the x3 upstream
                     // values of its row's plane staging zr; returns the lane's moment sums of the
                     // point: (rho, u1), (u2, u3) and the temperature moment
                     auto point = [&](const float* rrow, float* zr, int i, float2& hp1, float2& hp2, float2& M01,
-                                     float2& M23, float& m4) {
+                                     float2& M23, float& m4, bool st3, size_t o3) {
                         const float4* R = reinterpret_cast<const float4*>(rrow + i * RF);
                         const float4 A = R[0], B = R[1], C = R[2], D = R[3];
                         const float2 z1 = *reinterpret_cast<const float2*>(zr + zl1 + (size_t)i * kPL);
@@ -556,6 +560,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                             if (Fb.x >= 0) *reinterpret_cast<float2*>(fnext[1] + (size_t)Fb.x * fstride) = h;
                             if (Fb.y >= 0) *reinterpret_cast<float2*>(fnext[2] + (size_t)Fb.y * fstride) = h;
                         }
+                        if (st3) PS::st(et3, o3 + (size_t)i * colS, h, 0.f);
                         hp2 = hp1;
                         hp1 = h;
                         rb2[i] = rb1[i];
@@ -600,6 +605,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                             const float *rrA, *rrB;
                             row_ptrs(jj, crA, zrA, rrA, prA);
                             row_ptrs(jj + 1, crB, zrB, rrB, prB);
+                            const size_t o3A = e3o + (size_t)jj * rowS;
                             float2 hA1 = *reinterpret_cast<const float2*>(crA), hA2 = *reinterpret_cast<const float2*>(crA + kPL);
                             float2 hB1 = *reinterpret_cast<const float2*>(crB), hB2 = *reinterpret_cast<const float2*>(crB + kPL);
                             float2 M01[8], M23[8];
@@ -611,11 +617,11 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                                 const bool onB = st >= 1 && ((fb >> (st - 1)) & 1u);
                                 if (onA || onB) {
                                     if (st < SW) {
-                                        if (FULL || st < wsub) point(rrA, zrA, st, hA1, hA2, M01[st], M23[st], m4[st]);
+                                        if (FULL || st < wsub) point(rrA, zrA, st, hA1, hA2, M01[st], M23[st], m4[st], e3 && onA, o3A);
                                         else { M01[st] = M23[st] = z2; m4[st] = 0.f; }
                                     }
                                     if (st >= 1) {
-                                        if (FULL || st - 1 < wsub) point(rrB, zrB, st - 1, hB1, hB2, M01[3 + st], M23[3 + st], m4[3 + st]);
+                                        if (FULL || st - 1 < wsub) point(rrB, zrB, st - 1, hB1, hB2, M01[3 + st], M23[3 + st], m4[3 + st], e3 && onB, o3A + rowS);
                                         else { M01[3 + st] = M23[3 + st] = z2; m4[3 + st] = 0.f; }
                                     }
                                 } else {
@@ -661,7 +667,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                             float m4[4];
 #pragma unroll
                             for (int c = 0; c < SW; ++c) {
-                                if ((fm >> c) & 1u) point(rrow, zr, c, hp1, hp2, M01[c], M23[c], m4[c]);
+                                if ((fm >> c) & 1u) point(rrow, zr, c, hp1, hp2, M01[c], M23[c], m4[c], e3, e3o + (size_t)jj * rowS);
                                 else {
                                     M01[c] = M23[c] = make_float2(0.f, 0.f);
                                     m4[c] = 0.f;
@@ -701,9 +707,10 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                         }
                     }
                 }
-                // x3 edge: the top plane nr3 - 1 in staging layer (nr3 - 1) & 1, the plane below it
+                // x3 edge of BF16 storage or one-plane pencils (FP32 pencils stored it during the last two
+                // planes): the top plane nr3 - 1 in staging layer (nr3 - 1) & 1, the plane below it
                 // (or, in a one-plane pencil, the fetched upstream plane) in layer nr3 & 1
-                {
+                if (BF || nr3 < 2) {
                     const float* s = pb + ((size_t)warp * MR2 * 2 * SW) * kPL + 2 * lane;
                     const float* st0 = s + (size_t)(((nr3 - 1) & 1) * SW) * kPL;
                     const float* st1 = s + (size_t)((nr3 & 1) * SW) * kPL;
