@@ -527,12 +527,16 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                     // are swept (layer 0: plane nr3 - 1, layer 1: plane nr3 - 2; fluid points only)
                     const bool e3 = !BF && nr3 >= 2 && kk >= nr3 - 2;
                     const size_t e3o = eo3 + (size_t)cs * colS + (size_t)(nr3 - 1 - kk) * NL;
+                    // likewise the x2 edge of this plane as rows nr2 - 2 (layer 1) and nr2 - 1 (layer 0)
+                    // are swept, in pencils of two or more rows
+                    const bool e2 = !BF && nr2 >= 2;
+                    const size_t e2o = eo2 + (size_t)kk * rowS + (size_t)cs * colS;
                     // one point: Eq. 10 for the lane's velocity pair with the x1 upstream values (hp1,
                     // hp2) of its row, the x2 upstream values rb of its column and the x3 upstream
                     // values of its row's plane staging zr; returns the lane's moment sums of the
                     // point: (rho, u1), (u2, u3) and the temperature moment
                     auto point = [&](const float* rrow, float* zr, int i, float2& hp1, float2& hp2, float2& M01,
-                                     float2& M23, float& m4, bool st3, size_t o3) {
+                                     float2& M23, float& m4, bool st3, size_t o3, bool st2, size_t o2) {
                         const float4* R = reinterpret_cast<const float4*>(rrow + i * RF);
                         const float4 A = R[0], B = R[1], C = R[2], D = R[3];
                         const float2 z1 = *reinterpret_cast<const float2*>(zr + zl1 + (size_t)i * kPL);
@@ -561,6 +565,7 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                             if (Fb.y >= 0) *reinterpret_cast<float2*>(fnext[2] + (size_t)Fb.y * fstride) = h;
                         }
                         if (st3) PS::st(et3, o3 + (size_t)i * colS, h, 0.f);
+                        if (st2) PS::st(et2, o2 + (size_t)i * colS, h, 0.f);
                         hp2 = hp1;
                         hp1 = h;
                         rb2[i] = rb1[i];
@@ -606,6 +611,9 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                             row_ptrs(jj, crA, zrA, rrA, prA);
                             row_ptrs(jj + 1, crB, zrB, rrB, prB);
                             const size_t o3A = e3o + (size_t)jj * rowS;
+                            // rows nr2 - 2 and nr2 - 1 give the x2 edge's layers 1 and 0
+                            const bool x2A = e2 && jj >= nr2 - 2, x2B = e2 && jj + 1 >= nr2 - 2;
+                            const size_t o2A = e2o + (size_t)(nr2 - 1 - jj) * NL, o2B = e2o + (size_t)(nr2 - 2 - jj) * NL;
                             float2 hA1 = *reinterpret_cast<const float2*>(crA), hA2 = *reinterpret_cast<const float2*>(crA + kPL);
                             float2 hB1 = *reinterpret_cast<const float2*>(crB), hB2 = *reinterpret_cast<const float2*>(crB + kPL);
                             float2 M01[8], M23[8];
@@ -617,11 +625,11 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                                 const bool onB = st >= 1 && ((fb >> (st - 1)) & 1u);
                                 if (onA || onB) {
                                     if (st < SW) {
-                                        if (FULL || st < wsub) point(rrA, zrA, st, hA1, hA2, M01[st], M23[st], m4[st], e3 && onA, o3A);
+                                        if (FULL || st < wsub) point(rrA, zrA, st, hA1, hA2, M01[st], M23[st], m4[st], e3 && onA, o3A, x2A && onA, o2A);
                                         else { M01[st] = M23[st] = z2; m4[st] = 0.f; }
                                     }
                                     if (st >= 1) {
-                                        if (FULL || st - 1 < wsub) point(rrB, zrB, st - 1, hB1, hB2, M01[3 + st], M23[3 + st], m4[3 + st], e3 && onB, o3A + rowS);
+                                        if (FULL || st - 1 < wsub) point(rrB, zrB, st - 1, hB1, hB2, M01[3 + st], M23[3 + st], m4[3 + st], e3 && onB, o3A + rowS, x2B && onB, o2B);
                                         else { M01[3 + st] = M23[3 + st] = z2; m4[3 + st] = 0.f; }
                                     }
                                 } else {
@@ -667,7 +675,9 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                             float m4[4];
 #pragma unroll
                             for (int c = 0; c < SW; ++c) {
-                                if ((fm >> c) & 1u) point(rrow, zr, c, hp1, hp2, M01[c], M23[c], m4[c], e3, e3o + (size_t)jj * rowS);
+                                if ((fm >> c) & 1u)
+                                    point(rrow, zr, c, hp1, hp2, M01[c], M23[c], m4[c], e3, e3o + (size_t)jj * rowS, e2 && jj >= nr2 - 2,
+                                          e2o + (size_t)(nr2 - 1 - jj) * NL);
                                 else {
                                     M01[c] = M23[c] = make_float2(0.f, 0.f);
                                     m4[c] = 0.f;
@@ -690,9 +700,10 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                             *reinterpret_cast<float2*>(cr + kPL) = hp2;
                         }
                     }
-                    // x2 edge of this plane: only values of fluid points are stored (layer 1 of a
-                    // one-row pencil passes the fetched upstream value through and is always stored)
-                    {
+                    // x2 edge of this plane in BF16 storage or one-row pencils (FP32 pencils stored it as
+                    // the rows were swept): only values of fluid points are stored (layer 1 of a one-row
+                    // pencil passes the fetched upstream value through and is always stored)
+                    if (!e2) {
                         const unsigned f0 = fbits(kk * MR2 + nr2 - 1);
                         const unsigned f1 = nr2 >= 2 ? fbits(kk * MR2 + nr2 - 2) : 0xffffffffu;
                         size_t o = eo2 + (size_t)kk * rowS + (size_t)cs * colS;
