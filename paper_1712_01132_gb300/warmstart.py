@@ -512,6 +512,40 @@ def time_step(levels=3, base=24, side=64, steps=50, seed=0):
     return {"levels": levels, "base": base, "side": side, "ms_per_train_step": ms_step, "ms_per_forward": ms_fwd}
 
 
+def time_convolutions(shapes=((32, 32, 64), (64, 64, 32), (128, 128, 16), (256, 256, 8), (96, 32, 64), (32, 64, 64)),
+                      reps=20):
+    """Time the library's convolution (dvm_nn_conv3d, its padded-copy and weight-copy kernels
+    included) at the network's channel counts and grid sides (cin, cout, side): CUDA events around
+    `reps` calls after three warm-ups.  Returns [{cin, cout, side, ms, tflops}]."""
+    import torch
+    lib = dvm.load()
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    out = []
+    for ci, co, n in shapes:
+        x = torch.randn(ci, n, n, n, device="cuda")
+        w = torch.randn(co, ci, 27, device="cuda") * 0.05
+        b = torch.randn(co, device="cuda")
+        y = torch.empty(co, n, n, n, device="cuda")
+        nsc = lib.dvm_nn_conv3d_scratch_bytes(ci, co, n, n, n)
+        sc = torch.empty(nsc, dtype=torch.uint8, device="cuda")
+        args = [ctypes.c_void_p(t.data_ptr()) for t in (x, w, b, y)] + [ci, co, n, n, n, 0, ctypes.c_void_p(sc.data_ptr()),
+                                                                        nsc, st]
+        for _ in range(3):
+            dvm._check(lib.dvm_nn_conv3d(*args), None)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            lib.dvm_nn_conv3d(*args)
+        e1.record()
+        torch.cuda.synchronize()
+        if lib.dvm_nn_status(st) != 0:
+            raise RuntimeError("convolution wait expired")
+        ms = e0.elapsed_time(e1) / reps
+        out.append({"cin": ci, "cout": co, "side": n, "ms": round(ms, 4),
+                    "tflops": round(2.0 * n ** 3 * ci * co * 27 / ms / 1e9, 1)})
+    return out
+
+
 def main():
     import argparse
     import json
@@ -531,7 +565,13 @@ def main():
     ap.add_argument("--out", default=None)
     ap.add_argument("--time-step", action="store_true",
                     help="only time a training step and a forward pass of the network (--levels, --base, --side)")
+    ap.add_argument("--time-conv", action="store_true",
+                    help="only time the convolution entry point at the network's channel counts")
     a = ap.parse_args()
+    if a.time_conv:
+        for row in time_convolutions():
+            print(json.dumps(row))
+        return
     if a.time_step:
         import json
         print(json.dumps(time_step(a.levels, a.base, a.side)))
