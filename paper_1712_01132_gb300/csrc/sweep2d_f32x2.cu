@@ -474,9 +474,11 @@ __global__ void __launch_bounds__(256) sweep2d_f32x2_kernel(const SweepArgs2D<fl
             // x1 ghost layers of the next iteration (periodic in x1, same quadrant) or the halo of
             // the next x1 subdomain
             if (cout_slot >= 0) carry_out(cout_slot);
-            if (t + 1 < ntiles) store_rec(buf ^ 1, nxt);
             __syncthreads();
             if (threadIdx.x == 0 && it != a.withhold_item) publish_gpu(P->prog + q * nb + band, t + 1);
+            // (the next tile's records after the publish: its readers are behind the next tile's
+            // first barrier)
+            if (t + 1 < ntiles) store_rec(buf ^ 1, nxt);
             // moment partials of this quadrant: sum of the warps' lane sums, in warp order, a thread
             // per point (pt = rr T1 + i; only fluid points have bits, and only their partials are read)
             {

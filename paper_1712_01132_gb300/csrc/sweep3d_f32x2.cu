@@ -757,11 +757,13 @@ __global__ void __launch_bounds__(256) sweep3d_f32x2_kernel(const SweepArgs3D<fl
                         PS::st(P->gx1, gxo + (row * 2 + 1) * NL + lv, *reinterpret_cast<const float2*>(cr + kPL), x1g1);
                     }
             }
-            if (t + 1 < ntiles) store_rec(t + 1, (t + 1) & 1, nxt);
             __syncthreads();
             if (threadIdx.x == 0 && it != a.withhold_item) {
                 publish_gpu(prog + p3 * np2 + p2, t + 1);
             }
+            // (the next tile's records after the publish: its readers are behind the next tile's
+            // first barrier)
+            if (t + 1 < ntiles) store_rec(t + 1, (t + 1) & 1, nxt);
             // moment partials of this octant and group: warp sums in warp order
             // (idx = (r T1 + i) NM + mm over the pencil's row slots; only fluid points have bits)
             const int wstride = MROWS * T1 * NM;
