@@ -88,26 +88,35 @@ def _peaks():
         return {}
 
 
-KERNEL_SOURCES = ("paper_1712_01132_gb300/csrc/sweep2d_f32x2.cu", "paper_1712_01132_gb300/csrc/dvm_device.cuh",
-                  "paper_1712_01132_gb300/csrc/dvm_internal.h")
+# workload -> (committed ncu summary holding the sweep's DRAM bytes per launch, kernel sources it was
+# taken with)
+TRAFFIC_PROFILES = {
+    "kn_sweep_512": ("sweep2d_f32x2_kn_sweep_512.md", ("paper_1712_01132_gb300/csrc/sweep2d_f32x2.cu",
+                                                       "paper_1712_01132_gb300/csrc/dvm_device.cuh",
+                                                       "paper_1712_01132_gb300/csrc/dvm_internal.h")),
+    "rock_128": ("sweep3d_f32x2_rock_128_launches.md", ("paper_1712_01132_gb300/csrc/sweep3d_f32x2.cu",
+                                                        "paper_1712_01132_gb300/csrc/dvm_device.cuh",
+                                                        "paper_1712_01132_gb300/csrc/dvm_internal.h")),
+}
 
 
 def measured_traffic(workload, tiles):
-    """DRAM bytes per sweep launch from the committed ncu summary of the default workload, or None
-    when the workload or tile shape differs or the kernel sources changed since the capture."""
+    """DRAM bytes per sweep launch from the committed ncu summary of the workload, or None when there
+    is none, the tile shape differs or the kernel sources changed since the capture."""
     import hashlib
-    if workload != "kn_sweep_512":
+    if workload not in TRAFFIC_PROFILES:
         return None
+    fname, sources = TRAFFIC_PROFILES[workload]
     try:
-        text = open(os.path.join(ROOT, "profiles", "sweep2d_f32x2_kn_sweep_512.md")).read()
+        text = open(os.path.join(ROOT, "profiles", fname)).read()
         fields = dict(line.split(": ", 1) for line in text.splitlines() if line.startswith("traffic_"))
         h = hashlib.sha256()
-        for f in KERNEL_SOURCES:
+        for f in sources:
             with open(os.path.join(ROOT, f), "rb") as fh:
                 h.update(fh.read())
         if fields.get("traffic_source_sha256") != h.hexdigest():
             return None
-        if fields.get("traffic_tiles") != "%d %d" % tiles:
+        if fields.get("traffic_tiles") != " ".join(str(int(x)) for x in tiles):
             return None
         return int(fields["traffic_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
@@ -289,7 +298,8 @@ def run_gpu(args):
     kernel = W["kernel"].replace("T1", str(t1))
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 2), "unit": "TFLOP/s",
                 "frac": round(achieved / peak_tflops, 4),
-                "traffic": measured_traffic(args.workload if args.side == 128 else "", (t1, rows)),
+                "traffic": measured_traffic(args.workload if args.side == 128 else "",
+                                            (t1, rows, tune.group_warps) if W["dims"] == 3 else (t1, rows)),
                 "kernel": kernel, "avg_launch_ms": round(sweep_avg_s * 1e3, 4),
                 "share_of_step": round(sweep_ms / max(sweep_ms + fin_ms, 1e-9), 4),
                 "peak_basis": "FP32 FMA issue, %d SMs x 128 lanes x 2 flop x %.0f MHz (SM count from the "

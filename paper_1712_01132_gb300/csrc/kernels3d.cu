@@ -599,59 +599,76 @@ __device__ __forceinline__ void put_h(const Prob3D<T>* P, T* base, size_t i, dou
     else base[i] = (T)hp;
 }
 
-// Zero-perturbation start in the kernels' source-form variables (h' = x1).
+// Zero-perturbation start in the kernels' source-form variables (h' = x1).  Arrays of per-point values
+// are filled point-major within each (octant, group, moment) plane; ghost layers row by row, one warp
+// per row of nl velocity slots that all hold the same value (the row's x1), with no per-element index
+// division.
+template <typename T>
+__device__ __forceinline__ void fill_row(const Prob3D<T>* P, T* base, size_t row, size_t nl, int lane, double x1) {
+    T* d = base + row * nl;
+    if (P->bf16) {
+        for (size_t l = lane; l < nl; l += 32) put_h(P, base, row * nl + l, x1, x1);
+    } else {
+        for (size_t l = lane; l < nl; l += 32) d[l] = (T)x1;
+    }
+}
+
 template <typename T>
 __global__ void init3d_kernel(const Prob3D<T>* P, int NL, const double* qw /*[8][G][4]*/,
                               const double* qwt /*[8][G][4]: sum W |v|^2 (1, v)*/,
                               const double* qwx /*[8][G][nx][4]: sum W psi_a (1, v)*/) {
     const int n1 = P->n1, n2 = P->n2, n3 = P->n3, N = P->N, G = P->ngroups;
     const size_t nl = NL;
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    for (size_t idx = t0; idx < (size_t)8 * G * 4 * N; idx += stride) {
-        const int id = idx % N;
-        const size_t qgm = idx / N;
-        const double x1 = (id % n1) * P->dx;
-        P->P[idx] = (P->code[id] & kSolidBit) ? T(0) : (T)(x1 * qw[qgm]);
-    }
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nth = gridDim.x * blockDim.x;
+    for (int qgm = 0; qgm < 8 * G * 4; ++qgm)
+        for (int id = tid; id < N; id += nth) {
+            const double x1 = (id % n1) * P->dx;
+            P->P[(size_t)qgm * N + id] = (P->code[id] & kSolidBit) ? T(0) : (T)(x1 * qw[qgm]);
+        }
     if (P->spec > 0.0)   // face stores of both parities: h' = x1 at the face's fluid point
-        for (size_t idx = t0; idx < (size_t)2 * P->nfaces * 4 * nl; idx += stride) {
+        for (size_t idx = tid; idx < (size_t)2 * P->nfaces * 4 * nl; idx += nth) {
             const int id = P->faces[(idx / (4 * nl)) % P->nfaces] >> 3;
             P->F[idx] = (T)((id % n1) * P->dx);
         }
     if (P->tau)   // sum W |v|^2 h' of h' = x1
-        for (size_t idx = t0; idx < (size_t)8 * G * N; idx += stride) {
-            const int id = idx % N;
-            const double x1 = (id % n1) * P->dx;
-            P->Pt[idx] = (P->code[id] & kSolidBit) ? T(0) : (T)(x1 * qwt[(idx / N) * 4]);
-        }
+        for (int qg = 0; qg < 8 * G; ++qg)
+            for (int id = tid; id < N; id += nth) {
+                const double x1 = (id % n1) * P->dx;
+                P->Pt[(size_t)qg * N + id] = (P->code[id] & kSolidBit) ? T(0) : (T)(x1 * qwt[qg * 4]);
+            }
     if (P->nx)   // model moments sum W psi_a h' of h' = x1
-        for (size_t idx = t0; idx < (size_t)8 * G * P->nx * N; idx += stride) {
-            const int id = idx % N;
-            const double x1 = (id % n1) * P->dx;
-            P->Px[idx] = (P->code[id] & kSolidBit) ? T(0) : (T)(x1 * qwx[(idx / N) * 4]);
-        }
-    // ghost slot s of the x1 ghosts holds the two columns before oriented column slot_col1[s]
+        for (int qgx = 0; qgx < 8 * G * P->nx; ++qgx)
+            for (int id = tid; id < N; id += nth) {
+                const double x1 = (id % n1) * P->dx;
+                P->Px[(size_t)qgx * N + id] = (P->code[id] & kSolidBit) ? T(0) : (T)(x1 * qwx[qgx * 4]);
+            }
+    // ghost rows: one warp per row of nl slots
+    const int lane = threadIdx.x & 31;
+    const size_t gw = (size_t)tid >> 5, nw = (size_t)nth >> 5;
     const int ns1 = P->ns1, ns2 = P->ns2, ns3 = P->ns3;
-    for (size_t idx = t0; idx < (size_t)2 * 8 * ns1 * n3 * n2 * 2 * nl; idx += stride) {
-        const int layer = (idx / nl) % 2;
-        const int slot = (idx / (nl * 2 * n3 * n2)) % ns1;
-        const int q = (idx / (nl * 2 * n3 * n2 * ns1)) % 8;
+    // x1 ghosts, rows (par, q, slot, k, j, layer): slot s holds the two columns before oriented
+    // column slot_col1[s]
+    for (size_t row = gw; row < (size_t)2 * 8 * ns1 * n3 * n2 * 2; row += nw) {
+        const int layer = (int)(row % 2);
+        const int slot = (int)((row / ((size_t)2 * n3 * n2)) % ns1);
+        const int q = (int)((row / ((size_t)2 * n3 * n2 * ns1)) % 8);
         const int ico = P->slot_col1[(q & 1) * ns1 + slot] - 1 - layer;
         const int col = (q & 1) ? n1 - 1 - ico : ico;
-        put_h(P, P->gx1, idx, col * P->dx, col * P->dx);
+        fill_row(P, P->gx1, row, nl, lane, col * P->dx);
     }
-    for (size_t idx = t0; idx < (size_t)2 * 8 * ns2 * n3 * n1 * 2 * nl; idx += stride) {
-        const int ic = (idx / (nl * 2)) % n1;
-        const int q = (idx / (nl * 2 * n3 * n1 * ns2)) % 8;
+    // x2 ghosts, rows (par, q, slot, k, i, layer); x3 ghosts, rows (par, q, slot, j, i, layer)
+    for (size_t row = gw; row < (size_t)2 * 8 * ns2 * n3 * n1 * 2; row += nw) {
+        const int ic = (int)((row / 2) % n1);
+        const int q = (int)((row / ((size_t)2 * n3 * n1 * ns2)) % 8);
         const int col = (q & 1) ? n1 - 1 - ic : ic;
-        put_h(P, P->gy, idx, col * P->dx, col * P->dx);
+        fill_row(P, P->gy, row, nl, lane, col * P->dx);
     }
-    for (size_t idx = t0; idx < (size_t)2 * 8 * ns3 * n2 * n1 * 2 * nl; idx += stride) {
-        const int ic = (idx / (nl * 2)) % n1;
-        const int q = (idx / (nl * 2 * n2 * n1 * ns3)) % 8;
+    for (size_t row = gw; row < (size_t)2 * 8 * ns3 * n2 * n1 * 2; row += nw) {
+        const int ic = (int)((row / 2) % n1);
+        const int q = (int)((row / ((size_t)2 * n2 * n1 * ns3)) % 8);
         const int col = (q & 1) ? n1 - 1 - ic : ic;
-        put_h(P, P->gz, idx, col * P->dx, col * P->dx);
+        fill_row(P, P->gz, row, nl, lane, col * P->dx);
     }
 }
 
