@@ -14,7 +14,8 @@
 // 8 columns is swept as 4-column sub-tiles (one neighbour wait, one publish, one record load and
 // one pass of moment partials per tile); the rows of a plane are walked two at a time, the upper
 // row a column behind the lower; the next tile's point data is loaded while the current tile is
-// swept.
+// swept; the pencil's top two rows and planes go to the neighbours' edge rings as they are swept;
+// thread 0 re-reads a neighbour's progress flag only for tiles beyond the value it last observed.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
