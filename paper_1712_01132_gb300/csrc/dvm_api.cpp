@@ -62,7 +62,7 @@ using namespace dvm;
 namespace {
 
 constexpr int kFinBlock2 = 1024;  // points per finalize block in 2D (256 threads x 4 points)
-constexpr int kFinBlock3 = 256;   // points per finalize block in 3D (one per thread)
+constexpr int kFinBlock3 = 1024;  // points per finalize block in 3D (256 threads x 4 points)
 
 struct Buf {
     void* p;

@@ -481,6 +481,8 @@ __device__ __forceinline__ double wall_density3(const Prob3D<T>* P, int y, int j
     return sigma * num * dinv[j];
 }
 
+constexpr int kFinPPT3 = 4;   // points per finalize thread in 3D
+
 template <typename T>
 __global__ void __launch_bounds__(256) finalize3d_kernel(const FinArgs3D<T> a) {
     using V = typename V4t<T>::type;
@@ -488,74 +490,80 @@ __global__ void __launch_bounds__(256) finalize3d_kernel(const FinArgs3D<T> a) {
     __shared__ int s_last;
     const int b = a.blk_prob[blockIdx.x];
     const Prob3D<T>* __restrict__ P = a.prob + b;
-    const int id = a.blk_start[blockIdx.x] + threadIdx.x;
+    // kFinPPT3 points per thread (threadIdx.x + k 256 of the block's points): the FP64 work of
+    // the block sums, a large part of this kernel on GB300's FP64 unit, is shared by four points
     double u1d = 0.0;
-    if (id < P->N) {
-        const uint16_t code = P->code[id];
-        // the moment partials are loaded before the code is known (a solid point's partials are
-        // the start state's zeros), so both loads overlap
-        const size_t N = P->N;
-        const int G = P->ngroups;
-        T mo[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-#pragma unroll 2
-            for (int g = 0; g < G; ++g)
-#pragma unroll
-                for (int mm = 0; mm < 4; ++mm) mo[mm] += P->P[(((size_t)q * G + g) * 4 + mm) * N + id];
-        V s = V4t<T>::make(0, 0, 0, 0), e0 = s, e1 = s;
-        if (!(code & kSolidBit)) {
-            const T nu = (T)P->nu;
-            s = V4t<T>::make(nu * mo[0], T(2) * nu * mo[1] + T(1), T(2) * nu * mo[2], T(2) * nu * mo[3]);
-            u1d = (double)mo[1];
-            if (P->tau) {
-                // tau = (2/3) e - rho (Eq. 4) from the shifted moments e' = sum W |v|^2 h' and rho':
-                // tau = (2/3) e' - rho' + x1 (1 - (2/3) sum W |v|^2), the same in both forms
-                T e = T(0);
-                for (int q = 0; q < 8; ++q)
-                    for (int g = 0; g < G; ++g) e += P->Pt[((size_t)q * G + g) * N + id];
-                const T x1 = (T)((id % P->n1) * P->dx);
-                const T tau = T(2.0 / 3.0) * e - mo[0] + x1 * (T)(1.0 - 2.0 / 3.0 * P->sw2);
-                P->srct[id] = nu * tau;
-                if (P->nx) {
-                    // model moments m_a = sum W psi_a h = m'_a - x1 sx_a (heat flux, stress); the
-                    // source carries nu xcoef m_a
-                    const int nx = P->nx;
-                    T xv[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
-                    for (int m = 0; m < nx; ++m) {
-                        T xs = T(0);
-                        for (int q = 0; q < 8; ++q)
-                            for (int g = 0; g < G; ++g) xs += P->Px[(((size_t)q * G + g) * nx + m) * N + id];
-                        xv[m] = nu * (T)P->xcoef * (xs - x1 * (T)P->sx[m]);
+#pragma unroll 1
+    for (int kq = 0; kq < kFinPPT3; ++kq) {
+        const int id = a.blk_start[blockIdx.x] + threadIdx.x + kq * 256;
+        if (id < P->N) {
+            const uint16_t code = P->code[id];
+            // the moment partials are loaded before the code is known (a solid point's partials are
+            // the start state's zeros), so both loads overlap
+            const size_t N = P->N;
+            const int G = P->ngroups;
+            T mo[4] = {T(0), T(0), T(0), T(0)};
+    #pragma unroll
+            for (int q = 0; q < 8; ++q)
+    #pragma unroll 2
+                for (int g = 0; g < G; ++g)
+    #pragma unroll
+                    for (int mm = 0; mm < 4; ++mm) mo[mm] += P->P[(((size_t)q * G + g) * 4 + mm) * N + id];
+            V s = V4t<T>::make(0, 0, 0, 0), e0 = s, e1 = s;
+            if (!(code & kSolidBit)) {
+                const T nu = (T)P->nu;
+                s = V4t<T>::make(nu * mo[0], T(2) * nu * mo[1] + T(1), T(2) * nu * mo[2], T(2) * nu * mo[3]);
+                u1d += (double)mo[1];
+                if (P->tau) {
+                    // tau = (2/3) e - rho (Eq. 4) from the shifted moments e' = sum W |v|^2 h' and rho':
+                    // tau = (2/3) e' - rho' + x1 (1 - (2/3) sum W |v|^2), the same in both forms
+                    T e = T(0);
+                    for (int q = 0; q < 8; ++q)
+                        for (int g = 0; g < G; ++g) e += P->Pt[((size_t)q * G + g) * N + id];
+                    const T x1 = (T)((id % P->n1) * P->dx);
+                    const T tau = T(2.0 / 3.0) * e - mo[0] + x1 * (T)(1.0 - 2.0 / 3.0 * P->sw2);
+                    P->srct[id] = nu * tau;
+                    if (P->nx) {
+                        // model moments m_a = sum W psi_a h = m'_a - x1 sx_a (heat flux, stress); the
+                        // source carries nu xcoef m_a
+                        const int nx = P->nx;
+                        T xv[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+                        for (int m = 0; m < nx; ++m) {
+                            T xs = T(0);
+                            for (int q = 0; q < 8; ++q)
+                                for (int g = 0; g < G; ++g) xs += P->Px[(((size_t)q * G + g) * nx + m) * N + id];
+                            xv[m] = nu * (T)P->xcoef * (xs - x1 * (T)P->sx[m]);
+                        }
+                        reinterpret_cast<V*>(P->srcx)[2 * (size_t)id] = V4t<T>::make(xv[0], xv[1], xv[2], xv[3]);
+                        reinterpret_cast<V*>(P->srcx)[2 * (size_t)id + 1] = V4t<T>::make(xv[4], xv[5], T(0), T(0));
                     }
-                    reinterpret_cast<V*>(P->srcx)[2 * (size_t)id] = V4t<T>::make(xv[0], xv[1], xv[2], xv[3]);
-                    reinterpret_cast<V*>(P->srcx)[2 * (size_t)id + 1] = V4t<T>::make(xv[4], xv[5], T(0), T(0));
                 }
-            }
-            T ev[6];
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int cs = (code >> (2 * (2 * j + u))) & 3;
-                    const int sigma = u ? 1 : -1;
-                    double val = 0.0;
-                    if (cs == 2) {
-                        // Eq. 5: alpha times the diffuse value (the specular part is added per velocity)
-                        // (Eq. 5: alpha times the diffuse value, through the alpha-scaled denominators)
-                        val = wall_density3(P, id, j, sigma, P->dinvw) + (j == 0 ? sigma * P->dx : 0.0);
+                T ev[6];
+    #pragma unroll
+                for (int j = 0; j < 3; ++j) {
+    #pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int cs = (code >> (2 * (2 * j + u))) & 3;
+                        const int sigma = u ? 1 : -1;
+                        double val = 0.0;
+                        if (cs == 2) {
+                            // Eq. 5: alpha times the diffuse value (the specular part is added per velocity)
+                            // (Eq. 5: alpha times the diffuse value, through the alpha-scaled denominators)
+                            val = wall_density3(P, id, j, sigma, P->dinvw) + (j == 0 ? sigma * P->dx : 0.0);
+                        }
+                        // case 1 (only the second upstream point solid) is first order on the fluid
+                        // neighbour: no wall term
+                        ev[2 * j + u] = (T)val;
                     }
-                    // case 1 (only the second upstream point solid) is first order on the fluid
-                    // neighbour: no wall term
-                    ev[2 * j + u] = (T)val;
                 }
+                e0 = V4t<T>::make(ev[0], ev[1], ev[2], ev[3]);
+                e1 = V4t<T>::make(ev[4], ev[5], T(0), T(0));
             }
-            e0 = V4t<T>::make(ev[0], ev[1], ev[2], ev[3]);
-            e1 = V4t<T>::make(ev[4], ev[5], T(0), T(0));
+            reinterpret_cast<V*>(P->src)[id] = s;
+            reinterpret_cast<V*>(P->E)[2 * (size_t)id] = e0;
+            reinterpret_cast<V*>(P->E)[2 * (size_t)id + 1] = e1;
+    
         }
-        reinterpret_cast<V*>(P->src)[id] = s;
-        reinterpret_cast<V*>(P->E)[2 * (size_t)id] = e0;
-        reinterpret_cast<V*>(P->E)[2 * (size_t)id + 1] = e1;
     }
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) u1d += __shfl_xor_sync(0xffffffffu, u1d, off);
