@@ -79,8 +79,8 @@ typedef struct {
                             8-column 3D tile as two 4-column sub-tiles, between one neighbour wait
                             and one publish); 0 = automatic (8 in 2D, 8 in 3D FP32, 4 in 3D FP64) */
     int band_rows;       /* rows per sweep band in 2D, pencil rows R2 = R3 in 3D (0 = automatic:
-                            8 in 2D, 4 in 3D; in 3D the tile width, then the rows, are reduced
-                            until the CTA fits shared memory) */
+                            8 in 2D, 4 in 3D FP32, 2 in 3D FP64; in 3D the tile width, then the
+                            rows, are reduced until the CTA fits shared memory) */
     /* Optional device allocator (e.g. the caller's caching allocator).  When alloc is NULL the
      * library uses cudaMalloc/cudaFree.  alloc returns NULL on failure. */
     void* (*alloc)(size_t bytes, void* user);
@@ -103,10 +103,10 @@ typedef struct {
      * each block at least two points wide along every cut axis (DVM_EINVAL otherwise); 2D problems
      * reject c3 > 1, and BF16 storage and the Shakhov / ES-BGK models reject any cut. */
     int subdomains[3];
-    /* 3D: at most this many warps per sweep CTA (1..8; 0 = automatic, 8).  The velocities of an
-     * octant are split into groups of 64 (FP32) or 32 (FP64) slots per warp, one CTA per group and
-     * pencil, so fewer warps per CTA mean more, smaller CTAs per SM (more pencils in flight) at the
-     * price of building every point's record once per group.  The moments are summed per group and
+    /* 3D: at most this many warps per sweep CTA (1..8; 0 = automatic: 8, or 4 for FP64).  The
+     * velocities of an octant are split into groups of 64 (FP32) or 32 (FP64) slots per warp, one
+     * CTA per group and pencil, so fewer warps per CTA mean more, smaller CTAs per SM (more pencils
+     * in flight) at the price of building every point's record once per group.  The moments are summed per group and
      * then over groups, so this choice changes their summation order (results agree to rounding,
      * and for a fixed choice they are the same bits for every tile and pencil shape).  Ignored in
      * 2D. */

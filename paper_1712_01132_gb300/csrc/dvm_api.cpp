@@ -658,7 +658,9 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     const int vpl = c->packed3 ? sweep3d_f32x2_velocities_per_lane() : 1;
     const int warps_total = (nvo + 32 * vpl - 1) / (32 * vpl);
     // at most 8 warps per CTA (group_warps: fewer warps per CTA, more velocity groups)
-    const int wmax = (c->opt.group_warps > 0) ? std::min(8, c->opt.group_warps) : 8;
+    // (FP64 default: 4 warps per CTA, with the 2 x 2 pencils below 1.24x faster than 8 warps and
+    // 4 x 4 pencils on a 128^3 rock with 16^3 velocities)
+    const int wmax = (c->opt.group_warps > 0) ? std::min(8, c->opt.group_warps) : (c->prec == DVM_FP64 ? 4 : 8);
     c->G = (warps_total + wmax - 1) / wmax;
     c->NW = (warps_total + c->G - 1) / c->G;
     c->GL = 32 * vpl * c->NW;                             // velocity slots per group
@@ -666,9 +668,9 @@ dvm_status build_3d(dvm_ctx* c, const dvm_geometry* geoms, const dvm_velocity_gr
     const int NL = c->NL, G = c->G;
     // default tiles: FP32 (packed kernel) 8 columns, swept as two 4-column sub-tiles (one wait and
     // one publish per 8 columns: 1.12x faster than 4-column tiles on a 128^3 rock with 16^3
-    // velocities); FP64 4 columns.  Default pencils 4 x 4 rows.
+    // velocities); FP64 4 columns.  Default pencils 4 x 4 rows, FP64 2 x 2.
     c->T1 = c->opt.tile_x1 == 8 ? 8 : (c->opt.tile_x1 == 4 ? 4 : (c->packed3 ? 8 : 4));
-    const int R = c->opt.band_rows ? c->opt.band_rows : 4;
+    const int R = c->opt.band_rows ? c->opt.band_rows : (c->prec == DVM_FP64 ? 2 : 4);
     c->R2 = c->R3 = std::max(1, R);
     {
         // shrink the tile, then the pencil, until the CTA's shared memory fits the device limit
