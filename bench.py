@@ -123,6 +123,34 @@ def measured_traffic(workload, tiles):
         return None
 
 
+HBM_FALLBACK_GBS = 6800.0   # one earlier copy-bandwidth measurement on a GB300
+
+
+def hbm_fractions(peaks, dims, cells, sweep_s, iter_s, traffic):
+    """The path against the HBM roofline, next to the ALU one.  The method keeps no bulk h between
+    iterations (Sec. 3.1): per iteration and grid cell it must read a code byte and d + 1 FP64
+    moments and write 2^d (d + 1) FP32 quadrant/octant moment partials, 1 + 8 (d + 1) + 4 (d + 1) 2^d
+    bytes, over the time of the iteration's sweep and finalize.  `traffic` is the measured DRAM bytes
+    of one sweep launch (or None), over the sweep's own time."""
+    peak = float(peaks.get("hbm_gbs") or HBM_FALLBACK_GBS)
+    per_cell = 1 + 8 * (dims + 1) + 4 * (dims + 1) * 2 ** dims
+    alg = per_cell * cells
+    alg_gbs = alg / iter_s / 1e9
+    out = {"peak_gbs": peak,
+           "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json)" if peaks.get("hbm_gbs")
+                         else "fallback 6.8 TB/s",
+           "algorithmic_bytes_per_cell": per_cell,
+           "algorithmic_bytes_per_iteration": alg,
+           "algorithmic_gbs": round(alg_gbs, 1),
+           "algorithmic_frac": round(alg_gbs / peak, 5),
+           "dram_gbs": None, "dram_frac": None}
+    if traffic:
+        dram_gbs = traffic / sweep_s / 1e9
+        out["dram_gbs"] = round(dram_gbs, 1)
+        out["dram_frac"] = round(dram_gbs / peak, 4)
+    return out
+
+
 def _cores():
     return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
 
@@ -296,10 +324,13 @@ def run_gpu(args):
     sweep_avg_s = (sweep_ms / max(sweep_n, 1)) * 1e-3
     achieved = updates_per_iter * W["flops_per_update"] / sweep_avg_s / 1e12
     kernel = W["kernel"].replace("T1", str(t1))
+    traffic = measured_traffic(args.workload if args.side == 128 else "",
+                               (t1, rows, tune.group_warps) if W["dims"] == 3 else (t1, rows))
+    hbm = hbm_fractions(peaks, W["dims"], int(sum(m.size for m in masks)), sweep_avg_s,
+                        ((sweep_ms + fin_ms) / max(sweep_n, 1)) * 1e-3, traffic)
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 2), "unit": "TFLOP/s",
                 "frac": round(achieved / peak_tflops, 4),
-                "traffic": measured_traffic(args.workload if args.side == 128 else "",
-                                            (t1, rows, tune.group_warps) if W["dims"] == 3 else (t1, rows)),
+                "traffic": traffic,
                 "kernel": kernel, "avg_launch_ms": round(sweep_avg_s * 1e3, 4),
                 "share_of_step": round(sweep_ms / max(sweep_ms + fin_ms, 1e-9), 4),
                 "peak_basis": "FP32 FMA issue, %d SMs x 128 lanes x 2 flop x %.0f MHz (SM count from the "
@@ -307,7 +338,8 @@ def run_gpu(args):
                 "timing": "CUDA events recorded by the captured graph around every sweep launch, "
                           "summed over the timed steps",
                 "peak_fma_microbenchmark": round(fma_measured, 2),
-                "flops_per_update": W["flops_per_update"], "updates_per_launch": updates_per_iter}
+                "flops_per_update": W["flops_per_update"], "updates_per_launch": updates_per_iter,
+                "hbm": hbm}
 
     out = None
     if rank == 0:
