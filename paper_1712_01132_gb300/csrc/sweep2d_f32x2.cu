@@ -2,8 +2,8 @@
 // Sec. 3.1 step i with the quadrature of step iii fused), four discrete velocities per lane.
 //
 // Schedule: persistent CTAs take (problem, quadrant, band) items from a ticket counter in band
-// order.  A CTA sweeps its band along x1 in tiles of 8 columns; band b starts tile t once band b-1
-// has published it.  Inside a tile a warp walks its rows two at a time, the upper row one column
+// order.  A CTA sweeps its band along x1 in tiles of 4, 8 (the default) or 16 columns, the last as
+// two 8-column sub-tiles; band b starts tile t once band b-1 has published it.  Inside a tile a warp walks its rows two at a time, the upper row one column
 // behind the lower; every lane carries four velocities as two packed pairs updated with
 // fma.rn.f32x2, so each step has four independent dependency chains per lane.  Per-point arithmetic (Eq. 10 solved for h at the point, upwind stencil of Eq. 9):
 //   h = R * [ nu rho' + 2 nu u.v + v1 + a1 (K1x h(x-s1 e1) + K2x h(x-2 s1 e1) + E1)
