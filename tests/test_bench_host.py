@@ -70,3 +70,42 @@ def test_committed_traffic_profiles_parse():
         assert len(fields["traffic_source_sha256"]) == 64
         for f in sources:
             assert os.path.exists(os.path.join(bench.ROOT, f))
+
+
+_SMI = [
+    "0, 2070, 2070, 812.40, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+    "0, 2055, 2070, 1302.11, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+    "0, 2070, 2070, 1390.00, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+    "0, 345, 2070, 110.20, 0x0000000000000001, Not Active, Not Active, Not Active, Not Active",
+    "[N/A], [N/A]",
+    "0, [N/A], 2070, 100.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+]
+
+
+def test_parse_clocks_takes_the_median_under_load_and_every_active_reason():
+    c = bench.parse_clocks(_SMI)
+    assert c["samples"] == 4                       # malformed and N/A lines are skipped
+    assert c["sm_max_mhz"] == 2070.0
+    assert c["sm_mhz"] == 2070.0                   # median of 2070, 2055, 2070 (345 MHz idle sample left out)
+    assert c["reasons"] == ["sw_power_cap"]
+    hot = _SMI[0].replace("Not Active, Not Active, Not Active, Not Active",
+                          "Active, Active, Not Active, Not Active")
+    assert bench.parse_clocks([hot])["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
+    assert bench.parse_clocks([]) == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_clock_sampler_stop_parses_its_file(tmp_path):
+    import subprocess
+    s = bench.ClockSampler(0, str(tmp_path))
+    with open(s.path, "w") as f:
+        f.write("\n".join(_SMI) + "\n")
+    s.fh = open(os.devnull, "w")
+    s.proc = subprocess.Popen(["sleep", "30"])    # stands in for the sampling process
+    c = s.stop()
+    assert s.proc.poll() is not None
+    assert c["samples"] == 4 and c["sm_mhz"] == 2070.0 and c["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_sampler_without_nvidia_smi_says_so(tmp_path):
+    s = bench.ClockSampler(0, str(tmp_path))
+    assert s.stop()["reasons"] == ["nvidia-smi unavailable"]
