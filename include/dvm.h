@@ -77,7 +77,8 @@ typedef struct {
     int tile_x1;         /* sweep tile width along x1: 2D FP64 8 or 16, 2D FP32 4, 8 or 16, 3D 4
                             or 8 (FP32 sweeps a 16-column 2D tile as two 8-column sub-tiles and an
                             8-column 3D tile as two 4-column sub-tiles, between one neighbour wait
-                            and one publish); 0 = automatic (8 in 2D, 8 in 3D FP32, 4 in 3D FP64) */
+                            and one publish); 0 = automatic (8 in 2D; in 3D 8 for FP32 and BF16 storage, 4 for FP64 and
+                            for the Shakhov and ES-BGK models) */
     int band_rows;       /* rows per sweep band in 2D, pencil rows R2 = R3 in 3D (0 = automatic:
                             8 in 2D, 4 in 3D FP32, 2 in 3D FP64; in 3D the tile width, then the
                             rows, are reduced until the CTA fits shared memory) */
